@@ -1,0 +1,821 @@
+"""Plain, slow FP64 CPU oracle for the FE-DVR second-Born Matsubara method.
+
+TEST INFRASTRUCTURE ONLY. This module is the independent reference that the
+CUDA library is checked against. Only the test suite, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py`` may import it; the library and its
+Python binding never do, and it imports nothing from them.
+
+It follows Balzer, Bauch & Bonitz, "Finite elements and the discrete variable
+representation in nonequilibrium Green's function calculations" (arXiv
+0911.4348), step by step in the paper's order and notation:
+
+* Sec. 2.1, Eqs. (xim), (wim) and the GLL definitions: ``gll``, ``fedvr_basis``.
+* Sec. 2.2, Eqs. (vmat), (tmat): ``potential``, ``kinetic``.
+* Sec. 2.2, Eqs. (umat)-(umatsep): ``interaction`` and ``interaction_eigen_route``.
+* Sec. 2.3, Eq. (sigmahf): ``hf_selfenergy``; Eqs. (hamhf), (hfgf): ``hf_scf``,
+  ``chemical_potential``, ``g0_mesh``.
+* Sec. 2.3, Eq. (sigma2ndb): ``sigma2`` (two-index form) and
+  ``sigma2_bruteforce`` (general four-index form, tiny n only).
+* Sec. 2.3, Eq. (deq): ``conv1`` (I^(1)), ``conv2`` (I^(2)), ``solve_2b``.
+* Sec. 3.1 (uniform power mesh, 2up+1 points): ``power_mesh``, ``lag_table``.
+* Sec. 2.3 (total energy "as in" the cited references): ``energy``
+  (Galitskii-Migdal form).
+* Pins only: ``mp2`` (closed-shell MP2) and ``exact_ground`` (exact
+  two-electron ground state on the same grid).
+
+Where the paper is silent or garbled the oracle takes one stated reading; each
+is marked "Reading:" below. Every floating-point step of the basis, mesh and
+lag-table construction uses only IEEE +, -, *, / and sqrt in a fixed order
+(Python scalar arithmetic never fuses multiply-adds), so those results are
+reproducible bit for bit by any implementation that performs the same
+operations in the same order.
+
+Every function is pinned by a test under ``tests/`` against something other
+than itself (closed forms, special cases, brute force, printed paper values);
+none is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1: Gauss-Lobatto-Legendre points and weights
+# ---------------------------------------------------------------------------
+
+
+def _legendre(N: int, x: float) -> tuple[float, float]:
+    """(P_N(x), P_{N-1}(x)) by the three-term recurrence.
+
+    P_{k+1} = ((2k+1) x P_k - k P_{k-1}) / (k+1), evaluated in exactly this
+    order: a = (2k+1)*x; b = a*P_k; c = k*P_{k-1}; P_{k+1} = (b - c)/(k+1).
+    """
+    if N == 0:
+        return 1.0, 0.0
+    pm1, p = 1.0, x
+    for k in range(1, N):
+        a = float(2 * k + 1) * x
+        b = a * p
+        c = float(k) * pm1
+        pm1, p = p, (b - c) / float(k + 1)
+    return p, pm1
+
+
+def _dlegendre(N: int, x: float) -> float:
+    """P'_N(x) for |x| < 1 from (1 - x^2) P'_N = N (P_{N-1} - x P_N)."""
+    p, pm1 = _legendre(N, x)
+    num = float(N) * (pm1 - x * p)
+    den = 1.0 - x * x
+    return num / den
+
+
+def _bisect_root(N: int, lo: float, hi: float, dlo: float) -> float:
+    """Bisection for a sign change of P'_N in (lo, hi); stops when the
+    midpoint can no longer move (the bracket is one ulp wide)."""
+    mid = 0.5 * (lo + hi)
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        if not (lo < mid < hi):
+            break
+        dm = _dlegendre(N, mid)
+        if dm == 0.0:
+            break
+        if (dm > 0.0) == (dlo > 0.0):
+            lo = mid
+        else:
+            hi = mid
+    return mid
+
+
+GLL_SCAN_CELLS = 4096
+
+
+def gll(order: int) -> tuple[np.ndarray, np.ndarray]:
+    """Gauss-Lobatto-Legendre points xi_m and weights omega_m, m = 0..order.
+
+    Sec. 2.1: the points are the roots of dP_{n_g}/dx plus the two end points
+    +-1; the weights are omega_m = 2 / (n_g (n_g + 1) P_{n_g}(xi_m)^2).
+
+    Reading (the paper's n_g): the root and weight formulas are those of the
+    order-n_g rule, which has n_g + 1 points per element; with that reading
+    n_b = n_e n_g - 1 (Eq. basisdim) reproduces the paper's 29*7-1 = 202 and
+    13*11-1 = 142. ``order`` is therefore the polynomial order n_g and the
+    element holds order + 1 points.
+
+    Roots: P'_N is evaluated on the 4095 interior boundaries of a uniform
+    4096-cell scan of [-1, 1]; an exact zero is a root, a strict sign change
+    between neighbours is bisected to one ulp.
+    """
+    N = int(order)
+    if N < 1:
+        raise ValueError("order must be >= 1")
+    roots: list[float] = []
+    prev_x = prev_d = None
+    for c in range(1, GLL_SCAN_CELLS):
+        x = -1.0 + (2.0 * c) / GLL_SCAN_CELLS
+        d = _dlegendre(N, x)
+        if d == 0.0:
+            roots.append(x)
+        elif prev_d is not None and prev_d != 0.0 and ((d > 0.0) != (prev_d > 0.0)):
+            roots.append(_bisect_root(N, prev_x, x, prev_d))
+        prev_x, prev_d = x, d
+    if len(roots) != N - 1:
+        raise RuntimeError(f"GLL scan found {len(roots)} roots for order {N}")
+    xi = [-1.0] + roots + [1.0]
+    om = []
+    nn1 = float(N * (N + 1))
+    for x in xi:
+        p, _ = _legendre(N, x)
+        om.append(2.0 / (nn1 * (p * p)))
+    return np.array(xi), np.array(om)
+
+
+def lagrange_deriv(xi: np.ndarray) -> np.ndarray:
+    """d[m, k] = f'_m(xi_k) for the Lagrange (Lobatto shape) functions of Sec. 2.1.
+
+    k != m: (1/(xi_m - xi_k)) * prod_{l != m,k} (xi_k - xi_l)/(xi_m - xi_l), l ascending.
+    k == m: sum_{l != m} 1/(xi_m - xi_l), l ascending.
+    """
+    xs = [float(v) for v in xi]
+    n = len(xs)
+    d = np.zeros((n, n))
+    for m in range(n):
+        for k in range(n):
+            if k == m:
+                s = 0.0
+                for l in range(n):
+                    if l != m:
+                        s = s + 1.0 / (xs[m] - xs[l])
+                d[m, k] = s
+            else:
+                prod = 1.0 / (xs[m] - xs[k])
+                for l in range(n):
+                    if l != m and l != k:
+                        prod = prod * ((xs[k] - xs[l]) / (xs[m] - xs[l]))
+                d[m, k] = prod
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1 / Sec. 3.1: finite elements, nodes, weights, index map
+# ---------------------------------------------------------------------------
+
+
+def element_widths_graded(n_elem: int, L: float) -> list[float]:
+    """Case II partition (Sec. 3.1): a central element 1 a.u. wide and widths
+    growing linearly towards both box ends.
+
+    Reading (the paper gives no law): odd n_e: K = (n_e-1)/2 elements per side
+    of width 1 + k*delta (k = 1..K), delta = (L - 1 - 2K) / (K(K+1)); even n_e:
+    K = n_e/2 per side of width 1 + (k-1)*delta, delta = (L/2 - K) / (K(K-1)/2).
+    Widths are listed from the left box end to the right one.
+    """
+    ne = int(n_elem)
+    if ne == 1:
+        return [L]
+    if ne % 2 == 1:
+        K = (ne - 1) // 2
+        delta = (L - 1.0 - 2.0 * K) / float(K * (K + 1))
+        side = [1.0 + float(k) * delta for k in range(1, K + 1)]
+        return side[::-1] + [1.0] + side
+    K = ne // 2
+    if K == 1:
+        return [0.5 * L, 0.5 * L]
+    delta = (0.5 * L - float(K)) / float((K * (K - 1)) // 2)
+    side = [1.0 + float(k - 1) * delta for k in range(1, K + 1)]
+    return side[::-1] + side
+
+
+def element_edges(n_elem: int, xmin: float, xmax: float, grid_kind: int = 0) -> list[float]:
+    """Element boundaries x^0 = xmin < ... < x^{n_e} = xmax (Sec. 2.1, Fig. 1).
+
+    Case I (grid_kind 0, Sec. 3.1): e_i = xmin + (i * L) / n_e, e_{n_e} = xmax.
+    Case II (grid_kind 1): e_0 = xmin, e_{i+1} = e_i + width_i, e_{n_e} = xmax.
+    """
+    ne = int(n_elem)
+    L = xmax - xmin
+    if grid_kind == 0:
+        e = [xmin + (float(i) * L) / float(ne) for i in range(ne)]
+    elif grid_kind == 1:
+        wid = element_widths_graded(ne, L)
+        if min(wid) <= 0.0:
+            raise ValueError("graded widths must be positive")
+        e = [xmin]
+        for i in range(ne - 1):
+            e.append(e[-1] + wid[i])
+    else:
+        raise ValueError("grid_kind must be 0 or 1")
+    e.append(xmax)
+    return e
+
+
+def fedvr_basis(n_elem: int, order: int, xmin: float, xmax: float, grid_kind: int = 0) -> dict:
+    """FE-DVR nodes, weights and index map (Sec. 2.1, Eqs. xim, wim, basis, basisdim).
+
+    Global node q = i*order + m (element i, local point m = 0..order); the node
+    shared by elements i and i+1 is element i+1's m = 0, i.e. exactly the edge
+    e_{i+1}. Interior points: x = e_i + ((xi_m + 1) * h_i) * 0.5 with
+    h_i = e_{i+1} - e_i (Eq. xim rearranged). The two box ends carry no basis
+    function (G vanishes outside the interval), so the basis is q = 1 ..
+    n_e*order - 1 and n_b = n_e n_g - 1 (Eq. basisdim); basis index a = q - 1.
+
+    Element weight w^i_m = (omega_m * h_i) * 0.5 (Eq. wim); a bridge function
+    carries W = w^i_{order} + w^{i+1}_0 (the normalisation in Eq. basis;
+    Reading: the paper's f^i_{n_g-1} and w^i_{n_g-1} are the element's last
+    point, index ``order`` here).
+    """
+    ne, N = int(n_elem), int(order)
+    xi, om = gll(N)
+    e = element_edges(ne, xmin, xmax, grid_kind)
+    h = [e[i + 1] - e[i] for i in range(ne)]
+    nq = ne * N + 1
+    xq = [0.0] * nq
+    for i in range(ne):
+        xq[i * N] = e[i]
+        for m in range(1, N):
+            xq[i * N + m] = e[i] + ((float(xi[m]) + 1.0) * h[i]) * 0.5
+    xq[ne * N] = e[ne]
+    wloc = [[(float(om[m]) * h[i]) * 0.5 for m in range(N + 1)] for i in range(ne)]
+    n = ne * N - 1
+    X = np.zeros(n)
+    W = np.zeros(n)
+    elem = np.zeros(n, dtype=np.int32)
+    local = np.zeros(n, dtype=np.int32)
+    for a in range(n):
+        q = a + 1
+        i, m = divmod(q, N)
+        X[a] = xq[q]
+        if m == 0:  # bridge between elements i-1 and i
+            W[a] = wloc[i - 1][N] + wloc[i][0]
+            elem[a], local[a] = i - 1, N
+        else:
+            W[a] = wloc[i][m]
+            elem[a], local[a] = i, m
+    return dict(n=n, order=N, n_elem=ne, xi=xi, omega=om, edges=np.array(e),
+                h=np.array(h), wloc=np.array(wloc), nodes=X, weights=W,
+                elem=elem, local=local)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: one- and two-body matrices
+# ---------------------------------------------------------------------------
+
+
+def kinetic(basis: dict) -> np.ndarray:
+    """Kinetic matrix T (Sec. 2.2, Eq. tmat) assembled element by element.
+
+    Element matrix t~^i_{m1 m2} = sum_k D^i_{m1 k} D^i_{m2 k} w^i_k with
+    D^i = (2/h_i) d (d from ``lagrange_deriv``), k ascending. Then
+    T_ab = (0.5 * S_ab) / sqrt(W_a * W_b), S_ab = sum of t~^i over the elements
+    i that contain both nodes, i ascending. This is the paper's four-case table
+    written as one assembly rule (Reading: the table's deltas and weight
+    normalisations are those of the bridge/element functions of Eq. basis).
+    """
+    ne, N, n = basis["n_elem"], basis["order"], basis["n"]
+    d = lagrange_deriv(basis["xi"])
+    S = np.zeros((n, n))
+    for i in range(ne):
+        hi = float(basis["h"][i])
+        s = 2.0 / hi
+        D = [[s * float(d[m, k]) for k in range(N + 1)] for m in range(N + 1)]
+        wk = [float(basis["wloc"][i][k]) for k in range(N + 1)]
+        for m1 in range(N + 1):
+            qa = i * N + m1
+            if qa < 1 or qa > ne * N - 1:
+                continue
+            for m2 in range(N + 1):
+                qb = i * N + m2
+                if qb < 1 or qb > ne * N - 1:
+                    continue
+                acc = 0.0
+                for k in range(N + 1):
+                    acc = acc + (D[m1][k] * D[m2][k]) * wk[k]
+                S[qa - 1, qb - 1] = S[qa - 1, qb - 1] + acc
+    W = basis["weights"]
+    T = np.zeros((n, n))
+    for a in range(n):
+        for b in range(n):
+            if S[a, b] != 0.0:
+                T[a, b] = (0.5 * float(S[a, b])) / math.sqrt(float(W[a]) * float(W[b]))
+    return T
+
+
+def potential(nodes: np.ndarray, Z, R, soft_en: float) -> np.ndarray:
+    """Diagonal potential v_a (Sec. 2.2, Eq. vmat; Sec. 3 model potentials).
+
+    v_a = sum_A (-Z_A) / sqrt((X_a - R_A)^2 + soft_en), A ascending. At a
+    bridge both terms of the paper's weighted average sample v at the same
+    point, so v~ = v(node) exactly (Reading).
+    """
+    v = np.zeros(len(nodes))
+    for a, x in enumerate(nodes):
+        acc = 0.0
+        for z, r in zip(Z, R):
+            dx = float(x) - float(r)
+            acc = acc + (-float(z)) / math.sqrt(dx * dx + float(soft_en))
+        v[a] = acc
+    return v
+
+
+def interaction(nodes: np.ndarray, soft_ee: float) -> np.ndarray:
+    """Two-index interaction V_ab = u(|x_a - x_b|) = 1/sqrt((x_a-x_b)^2 + soft_ee).
+
+    Sec. 2.2, Eqs. (umat1)-(umatsep): the four-index integrals collapse to
+    delta delta u~ and, in exact arithmetic, u~_ab = u(|x_a - x_b|) (Reading;
+    ``interaction_eigen_route`` computes the paper's route for the check).
+    """
+    x = np.asarray(nodes, dtype=np.float64)
+    dx = x[:, None] - x[None, :]
+    return 1.0 / np.sqrt(dx * dx + float(soft_ee))
+
+
+def interaction_eigen_route(basis: dict, soft_ee: float) -> np.ndarray:
+    """u~ by the paper's separable route (Eqs. umatred, umatsep): diagonalise U
+    over the element-local point list, average the two coincident bridge rows
+    with the element weights, and sum alpha beta beta."""
+    ne, N = basis["n_elem"], basis["order"]
+    e, xi = basis["edges"], basis["xi"]
+    pts = []
+    for i in range(ne):
+        hi = e[i + 1] - e[i]
+        for m in range(N + 1):
+            if m == 0:
+                pts.append(e[i])
+            elif m == N:
+                pts.append(e[i + 1])
+            else:
+                pts.append(e[i] + ((xi[m] + 1.0) * hi) * 0.5)
+    pts = np.array(pts)
+    U = 1.0 / np.sqrt((pts[:, None] - pts[None, :]) ** 2 + soft_ee)
+    alpha, Bt = np.linalg.eigh(U)
+    n = basis["n"]
+    beta = np.zeros((n, len(pts)))
+    wl = basis["wloc"]
+    for a in range(n):
+        i, m = basis["elem"][a], basis["local"][a]
+        if m == N:  # bridge: average rows (i, N) and (i+1, 0)
+            r1, r2 = i * (N + 1) + N, (i + 1) * (N + 1)
+            beta[a] = (Bt[r1] * wl[i][N] + Bt[r2] * wl[i + 1][0]) / (wl[i][N] + wl[i + 1][0])
+        else:
+            beta[a] = Bt[i * (N + 1) + m]
+    return (beta * alpha) @ beta.T
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3: Hartree-Fock, chemical potential, HF Matsubara Green's function
+# ---------------------------------------------------------------------------
+
+
+def hf_selfenergy(rho: np.ndarray, V: np.ndarray, sigma: float) -> np.ndarray:
+    """Sigma^HF[rho] = sigma diag(V diag rho) - V o rho (Sec. 2.3, Eq. sigmahf).
+
+    Reading: g(t, t^+) in Eq. (sigmahf) is the density matrix rho = g(0^-) of
+    the Matsubara branch; the -i prefactor belongs to the real-time contour.
+    """
+    hartree = V @ np.diag(rho)
+    return sigma * np.diag(hartree) - V * rho
+
+
+def fermi(y: np.ndarray, beta: float) -> np.ndarray:
+    """Fermi function f_beta(y) = 1/(exp(beta y) + 1) in overflow-free form."""
+    y = np.asarray(y, dtype=np.float64)
+    out = np.empty_like(y)
+    pos = beta * y > 0.0
+    e = np.exp(-beta * y[pos])
+    out[pos] = e / (1.0 + e)
+    out[~pos] = 1.0 / (1.0 + np.exp(beta * y[~pos]))
+    return out
+
+
+def _softplus(z: float) -> float:
+    return max(z, 0.0) + math.log1p(math.exp(-abs(z)))
+
+
+def _lse(vals: list[float]) -> float:
+    m = max(vals)
+    s = 0.0
+    for v in vals:
+        s = s + math.exp(v - m)
+    return m + math.log(s)
+
+
+def _balance(mu: float, eps: np.ndarray, nocc: int, beta: float) -> float:
+    holes = [-_softplus(beta * (mu - float(e))) for e in eps[:nocc]]
+    parts = [-_softplus(beta * (float(e) - mu)) for e in eps[nocc:]]
+    return _lse(holes) - _lse(parts)
+
+
+def chemical_potential(eps: np.ndarray, nocc: int, beta: float) -> float:
+    """mu from the Fermi normalisation N/sigma = sum_a f_beta(eps_a - mu) (Sec. 2.3).
+
+    Reading: the equation is solved in its balanced form, holes = particles,
+    sum_{a<nocc} f(mu - eps_a) = sum_{a>=nocc} f(eps_a - mu), compared as
+    log-sum-exps. It is the same equation rearranged; in the direct form the
+    residual changes by ~1e-14 per unit mu inside the HOMO-LUMO gap at
+    beta = 100, so FP64 cannot locate mu there, while the balanced form has
+    slope ~ -2 beta. Bisection on [eps_min - 1, eps_max + 1] until the midpoint
+    no longer moves. ``eps`` must be ascending.
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    if not (0 < nocc < len(eps)):
+        raise ValueError("need 0 < nocc < n")
+    lo, hi = float(eps[0]) - 1.0, float(eps[-1]) + 1.0
+    mid = 0.5 * (lo + hi)
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        if not (lo < mid < hi):
+            break
+        if _balance(mid, eps, nocc, beta) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return mid
+
+
+def hf_energy(h: np.ndarray, V: np.ndarray, rho: np.ndarray, sigma: float) -> float:
+    """E_HF = sigma Tr[h rho] + (sigma/2) Tr[Sigma^HF[rho] rho]."""
+    return float(sigma * np.sum(h * rho) + 0.5 * sigma * np.sum(hf_selfenergy(rho, V, sigma) * rho))
+
+
+def hf_scf(h: np.ndarray, V: np.ndarray, sigma: float, nocc: int, beta: float,
+           tol: float = 1e-12, max_iter: int = 500, mixing: float = 0.5) -> dict:
+    """Self-consistent HF at inverse temperature beta (Sec. 2.3, Eq. hamhf).
+
+    Reading (start, mixing and stop are not given): rho starts as the
+    projector on the nocc lowest eigenvectors of h; each step builds
+    F = h + Sigma^HF[rho], diagonalises it, fixes mu, forms
+    rho' = C diag f C^T; stop when max|rho' - rho| < tol, otherwise
+    rho <- (1 - a) rho + a rho'. The returned eps, C, mu, F belong to the last
+    rho; rho0 = C diag f C^T = g^0(0^-) and Sigma0 = F - h.
+    """
+    eps, C = np.linalg.eigh(h)
+    rho = C[:, :nocc] @ C[:, :nocc].T
+    it = 0
+    for it in range(1, max_iter + 1):
+        F = h + hf_selfenergy(rho, V, sigma)
+        eps, C = np.linalg.eigh(F)
+        mu = chemical_potential(eps, nocc, beta)
+        f = fermi(eps - mu, beta)
+        rho_new = (C * f) @ C.T
+        r = float(np.max(np.abs(rho_new - rho)))
+        if r < tol:
+            break
+        rho = (1.0 - mixing) * rho + mixing * rho_new
+    else:
+        raise RuntimeError("HF did not converge")
+    return dict(eps=eps, C=C, mu=mu, f=f, F=F, Sigma0=F - h, rho0=rho_new,
+                E_hf=hf_energy(h, V, rho_new, sigma), iters=it)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1: uniform power mesh on [-beta, 0]
+# ---------------------------------------------------------------------------
+
+
+def power_mesh(beta: float, u: int, p: int) -> dict:
+    """Uniform power mesh with 2up + 1 points (Sec. 3.1, Fig. 2b).
+
+    Reading (the mesh is defined only by reference): offsets s on [0, beta/2]:
+    B_p = beta/2, B_{k-1} = 0.5 B_k, B_0 = 0; segment k = 1..p spans
+    [B_{k-1}, B_k] (width B_1 for k = 1, else B_{k-1}) and is cut into u
+    equal parts: s = B_{k-1} + (width * r) / u, r = 1..u. Then
+    tau_j = -beta + s_j for j <= up and tau_{M-1-m} = -s_m: the mesh is dense
+    at both ends and tau_{M-1-j} = -beta - tau_j holds bit for bit.
+
+    Weights: trapezoid w_j = (tau_{j+1} - tau_{j-1}) * 0.5 (one-sided at the
+    ends), and the halves wm_j = (tau_j - tau_{j-1}) * 0.5,
+    wp_j = (tau_{j+1} - tau_j) * 0.5 used where the integrand jumps.
+    """
+    u, p = int(u), int(p)
+    if u < 1 or p < 1:
+        raise ValueError("u, p >= 1")
+    half = 0.5 * beta
+    B = [0.0] * (p + 1)
+    B[p] = half
+    for k in range(p, 1, -1):
+        B[k - 1] = 0.5 * B[k]
+    s = [0.0]
+    for k in range(1, p + 1):
+        width = B[1] if k == 1 else B[k - 1]
+        for r in range(1, u + 1):
+            s.append(B[k - 1] + (width * float(r)) / float(u))
+    up = u * p
+    M = 2 * up + 1
+    tau = [0.0] * M
+    for j in range(up + 1):
+        tau[j] = -beta + s[j]
+    for m in range(up + 1):
+        tau[M - 1 - m] = -s[m]
+    w = [0.0] * M
+    wm = [0.0] * M
+    wp = [0.0] * M
+    for j in range(M):
+        if j > 0:
+            wm[j] = (tau[j] - tau[j - 1]) * 0.5
+        if j < M - 1:
+            wp[j] = (tau[j + 1] - tau[j]) * 0.5
+        if j == 0:
+            w[j] = (tau[1] - tau[0]) * 0.5
+        elif j == M - 1:
+            w[j] = (tau[M - 1] - tau[M - 2]) * 0.5
+        else:
+            w[j] = (tau[j + 1] - tau[j - 1]) * 0.5
+    return dict(tau=np.array(tau), w=np.array(w), wm=np.array(wm), wp=np.array(wp), M=M)
+
+
+def lag_point(tau: np.ndarray, beta: float, i: int, j: int) -> tuple[float, float]:
+    """Mesh argument y in [-beta, 0] and sign for the lag tau_i - tau_j, i != j.
+
+    Reading (the Dyson integrals run over a full period, Eq. deq): functions
+    are extended anti-periodically, F(x) = -F(x - beta) for x in (0, beta].
+    j > i: x = tau_i - tau_j < 0, y = x, sign +1; j < i: y = (tau_i - tau_j) - beta,
+    sign -1.
+    """
+    x = float(tau[i]) - float(tau[j])
+    if j > i:
+        return x, 1.0
+    return x - beta, -1.0
+
+
+def bracket(tau: np.ndarray, y: float) -> tuple[int, float]:
+    """k = largest index in [0, M-2] with tau_k <= y (binary search) and the
+    linear-interpolation weight t = (y - tau_k) / (tau_{k+1} - tau_k)."""
+    lo, hi = 0, len(tau) - 1
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if float(tau[mid]) <= y:
+            lo = mid
+        else:
+            hi = mid
+    t = (y - float(tau[lo])) / (float(tau[lo + 1]) - float(tau[lo]))
+    return lo, t
+
+
+def lag_table(tau: np.ndarray, beta: float) -> dict:
+    """(k, t, sign) for every off-diagonal pair (i, j); diagonal entries are
+    k = -1, t = 0, sign = 0 (the jump at lag 0 is handled separately)."""
+    M = len(tau)
+    K = np.full((M, M), -1, dtype=np.int32)
+    T = np.zeros((M, M))
+    S = np.zeros((M, M))
+    for i in range(M):
+        for j in range(M):
+            if i == j:
+                continue
+            y, sg = lag_point(tau, beta, i, j)
+            k, t = bracket(tau, y)
+            K[i, j], T[i, j], S[i, j] = k, t, sg
+    return dict(k=K, t=T, s=S)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3, Eq. (hfgf): HF Matsubara Green's function
+# ---------------------------------------------------------------------------
+
+
+def phi(x: float, y: np.ndarray, beta: float) -> np.ndarray:
+    """Eigenbasis factor of Eq. (hfgf): phi_a(x) = f_beta(y_a) exp(-x y_a),
+    x in [-beta, 0], y_a = eps_a - mu, in the overflow-free forms
+    y >= 0: exp(-(beta + x) y) / (1 + exp(-beta y)); y < 0: exp(-x y)/(1 + exp(beta y))."""
+    y = np.asarray(y, dtype=np.float64)
+    out = np.empty_like(y)
+    pos = y >= 0.0
+    yp, yn = y[pos], y[~pos]
+    out[pos] = np.exp(-((beta + x) * yp)) / (1.0 + np.exp(-(beta * yp)))
+    out[~pos] = np.exp(-(x * yn)) / (1.0 + np.exp(beta * yn))
+    return out
+
+
+def g0_mesh(eps: np.ndarray, C: np.ndarray, mu: float, tau: np.ndarray, beta: float) -> np.ndarray:
+    """g^0(tau_j) = C diag(phi(tau_j)) C^T for every mesh point (Eq. hfgf)."""
+    y = np.asarray(eps) - mu
+    return np.stack([(C * phi(float(t), y, beta)) @ C.T for t in tau])
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3, Eq. (sigma2ndb): second-Born self-energy
+# ---------------------------------------------------------------------------
+
+
+def sigma2_tau(g: np.ndarray, gb: np.ndarray, V: np.ndarray, sigma: float) -> np.ndarray:
+    """Sigma^corr at one mesh point from g = g(tau_j) and gb = g(-beta - tau_j).
+
+    Direct term sigma g o (V Q V) with the polarisation Q = g o gb, and the
+    second-order exchange X_ab = sum_{k,l} V_ak V_bl g_al gb_lk g_kb;
+    Sigma^corr = sigma g o (V Q V) - X.
+
+    Reading (Eq. sigma2ndb prints u_14 u_23 with g(t,t') and g(t',t); the
+    interaction is instantaneous, so the time-consistent pairing is u_13 u_24,
+    which leaves the direct term unchanged and makes the exchange the diagram
+    above, O(n_b^2) per element as the paper states). Sign: with the paper's
+    g > 0 on [-beta, 0] the direct term enters with + and the exchange with -
+    (the Hubbard-atom and MP2 pins fix this).
+    """
+    Q = g * gb
+    D = sigma * g * (V @ Q @ V)
+    n = g.shape[0]
+    X = np.empty_like(g)
+    for b in range(n):
+        P = g @ (V[b][:, None] * gb)      # P_ak = sum_l g_al V_bl gb_lk
+        X[:, b] = (V * P) @ g[:, b]       # X_ab = sum_k V_ak P_ak g_kb
+    return D - X
+
+
+def sigma2(G: np.ndarray, V: np.ndarray, sigma: float) -> np.ndarray:
+    """Sigma^corr(tau_j) for every j; gb_j = G[M-1-j] (mesh mirror symmetry)."""
+    M = G.shape[0]
+    return np.stack([sigma2_tau(G[j], G[M - 1 - j], V, sigma) for j in range(M)])
+
+
+def sigma2_bruteforce(g: np.ndarray, gb: np.ndarray, eri: np.ndarray, sigma: float) -> np.ndarray:
+    """General-basis second Born with all four-index integrals (chemist
+    notation eri[a,b,c,d] = (ab|cd)), O(n^6) (Sec. 2.3 text after Eq.
+    sigma2ndb):
+
+    Sigma_ij = sum_{abcdef} (ia|cd)(bj|ef) [sigma g_ab g_de gb_fc - g_ae gb_fc g_db].
+    With (ab|cd) = delta_ab delta_cd V_ac (Eq. umat1) it must equal ``sigma2_tau``.
+    """
+    direct = sigma * np.einsum("iacd,bjef,ab,de,fc->ij", eri, eri, g, g, gb, optimize=True)
+    exch = np.einsum("iacd,bjef,ae,fc,db->ij", eri, eri, g, gb, g, optimize=True)
+    return direct - exch
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3, Eq. (deq): the two tau-convolutions
+# ---------------------------------------------------------------------------
+
+
+def conv1(dHF: np.ndarray, A: np.ndarray, G: np.ndarray, mesh: dict, beta: float,
+          lag: dict, rows=None) -> np.ndarray:
+    """I^(1)(tau_i) = (Sigma^HF - Sigma^0) g(tau_i) + int Sigma^corr(tau_i - t) g(t) dt.
+
+    Eq. (deq), second line. Reading (the quadrature of the "direct
+    integration" is not given): trapezoid on the mesh, split at t = tau_i
+    where Sigma^corr jumps: for j != i the weight is w_j and Sigma^corr at the
+    lag is linearly interpolated on the mesh (anti-periodic beyond 0); at
+    j = i the left half-interval uses Sigma^corr(0^+) = -A_0 with weight wm_i
+    and the right one Sigma^corr(0^-) = A_{M-1} with weight wp_i.
+    ``rows`` restricts the output to a subset of i (sampled checks).
+    """
+    M = G.shape[0]
+    w, wm, wp = mesh["w"], mesh["wm"], mesh["wp"]
+    rows = range(M) if rows is None else rows
+    out = []
+    for i in rows:
+        acc = dHF @ G[i]
+        acc = acc + (-wm[i] * A[0] + wp[i] * A[M - 1]) @ G[i]
+        for j in range(M):
+            if j == i:
+                continue
+            k, t, s = int(lag["k"][i, j]), float(lag["t"][i, j]), float(lag["s"][i, j])
+            B = (s * w[j]) * ((1.0 - t) * A[k] + t * A[k + 1])
+            acc = acc + B @ G[j]
+        out.append(acc)
+    return np.stack(out)
+
+
+def conv2(I1: np.ndarray, eps: np.ndarray, C: np.ndarray, mu: float, mesh: dict,
+          beta: float, rows=None) -> np.ndarray:
+    """I^(2)(tau_i) = int g^0(tau_i - t) I^(1)(t) dt (Eq. deq, first integral).
+
+    Same split trapezoid as ``conv1``; g^0 at every lag is evaluated from
+    Eq. (hfgf) (no interpolation): lag < 0 gives C phi(lag) C^T, lag > 0 gives
+    -C phi(lag - beta) C^T; at j = i the halves use g^0(0^+) = -g^0(-beta) and
+    g^0(0^-). Plain O(M^2 n^3) loop.
+    """
+    tau, w, wm, wp = mesh["tau"], mesh["w"], mesh["wm"], mesh["wp"]
+    M = len(tau)
+    y = np.asarray(eps) - mu
+    g0_0m = (C * phi(0.0, y, beta)) @ C.T          # g^0(0^-)
+    g0_0p = -((C * phi(-beta, y, beta)) @ C.T)     # g^0(0^+)
+    rows = range(M) if rows is None else rows
+    out = []
+    for i in rows:
+        acc = (wm[i] * g0_0p + wp[i] * g0_0m) @ I1[i]
+        for j in range(M):
+            if j == i:
+                continue
+            yl, sg = lag_point(tau, beta, i, j)
+            gl = sg * ((C * phi(yl, y, beta)) @ C.T)
+            acc = acc + (w[j] * gl) @ I1[j]
+        out.append(acc)
+    return np.stack(out)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3: total energy and the self-consistency loop
+# ---------------------------------------------------------------------------
+
+
+def energy(h: np.ndarray, V: np.ndarray, sigma: float, G: np.ndarray, A: np.ndarray,
+           w: np.ndarray) -> float:
+    """Galitskii-Migdal energy (the paper computes it "as in" its refs; Reading):
+
+    E0 = sigma Tr[h rho] + (sigma/2) Tr[Sigma^HF[rho] rho]
+         - (sigma/2) sum_j w_j Tr[Sigma^corr(tau_{M-1-j}) g(tau_j)],  rho = g(0^-).
+
+    The last term is (sigma/2) Tr[(Sigma^corr * g)(0^-)]: the lag 0^- - tau_j
+    is positive, so Sigma^corr there is -Sigma^corr(-beta - tau_j), which is
+    the mirrored mesh point. E0 excludes the nuclear repulsion.
+    """
+    M = G.shape[0]
+    rho = G[M - 1]
+    e = sigma * float(np.sum(h * rho))
+    e += 0.5 * sigma * float(np.sum(hf_selfenergy(rho, V, sigma) * rho))
+    ec = 0.0
+    for j in range(M):
+        ec += float(w[j]) * float(np.sum(A[M - 1 - j] * G[j]))
+    return e - 0.5 * sigma * ec
+
+
+def dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=None) -> dict:
+    """One step of the second-Born self-consistency (Eq. deq):
+    A = Sigma^corr[g] (unless given), dHF = Sigma^HF[g(0^-)] - Sigma^0,
+    I1 = conv1, I2 = conv2, g_new = g^0 + I2, g' = (1 - a) g + a sym(g_new),
+    r = max|g' - g|, E0 and N from (g, A).
+
+    Reading: G(tau) of a real symmetric Hamiltonian is a symmetric matrix; the
+    sequential direct integration g^0 * (Sigma * g) breaks that at the level
+    of the quadrature error, so the update takes the symmetric part
+    sym(X)_ab = 0.5 (X_ab + X_ba) of g_new. The jump invariant
+    g(0^-) + g(-beta) = 1 is unaffected."""
+    M = G.shape[0]
+    if A is None:
+        A = sigma2(G, V, sigma)
+    dHF = hf_selfenergy(G[M - 1], V, sigma) - hf["Sigma0"]
+    E = energy(h, V, sigma, G, A, mesh["w"])
+    Nel = sigma * float(np.trace(G[M - 1]))
+    I1 = conv1(dHF, A, G, mesh, beta, lag)
+    I2 = conv2(I1, hf["eps"], hf["C"], hf["mu"], mesh, beta)
+    Gnew = G0 + I2
+    Gnew = 0.5 * (Gnew + Gnew.transpose(0, 2, 1))
+    Gnext = (1.0 - mixing) * G + mixing * Gnew
+    r = float(np.max(np.abs(Gnext - G)))
+    return dict(G=Gnext, Sigma=A, E0=E, N=Nel, res=r, I1=I1, I2=I2)
+
+
+def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
+             sigma_init=None) -> dict:
+    """Second-Born Matsubara self-consistency (Sec. 2.3 and 3.1).
+
+    Reading (the iteration scheme is not given): start from g = g^0; linear
+    mixing of g with weight ``mixing``; stop when max|g_{k+1} - g_k| < tol.
+    ``sigma_init`` replaces Sigma^corr[g^0] in the first iteration only (warm
+    start). Returns the final g_{k+1}, Sigma_k = Sigma^corr[g_k], and E0 and N
+    evaluated on (g_k, Sigma_k).
+    """
+    mesh = power_mesh(beta, u, p)
+    lag = lag_table(mesh["tau"], beta)
+    G0 = g0_mesh(hf["eps"], hf["C"], hf["mu"], mesh["tau"], beta)
+    G = G0.copy()
+    hist = []
+    step = None
+    converged = False
+    for it in range(max_iter):
+        step = dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing,
+                               A=sigma_init if (it == 0 and sigma_init is not None) else None)
+        hist.append((it, step["res"], step["E0"], step["N"]))
+        G = step["G"]
+        if step["res"] < tol:
+            converged = True
+            break
+    return dict(G=G, Sigma=step["Sigma"], E0=step["E0"], N=step["N"], iters=len(hist),
+                converged=converged, history=hist, mesh=mesh, G0=G0)
+
+
+# ---------------------------------------------------------------------------
+# Pins: MP2 and the exact two-electron ground state on the same grid
+# ---------------------------------------------------------------------------
+
+
+def mp2(eps: np.ndarray, C: np.ndarray, V: np.ndarray, nocc: int) -> float:
+    """Closed-shell MP2 energy with FE-DVR integrals (pq|rs) = delta_pq delta_rs V_pr:
+    E = sum_{ij occ, ab virt} (ia|jb) [2 (ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b),
+    (ia|jb) = sum_{pq} C_pi C_pa V_pq C_qj C_qb."""
+    occ, vir = C[:, :nocc], C[:, nocc:]
+    L = np.einsum("pi,pa->iap", occ, vir)
+    ovov = np.einsum("iap,pq,jbq->iajb", L, V, L, optimize=True)
+    eo, ev = eps[:nocc], eps[nocc:]
+    den = eo[:, None, None, None] - ev[None, :, None, None] + eo[None, None, :, None] - ev[None, None, None, :]
+    return float(np.sum(ovov * (2.0 * ovov - ovov.transpose(0, 3, 2, 1)) / den))
+
+
+def exact_ground(T: np.ndarray, v: np.ndarray, V: np.ndarray) -> float:
+    """Lowest eigenvalue of the two-electron grid Hamiltonian
+    H = T (x) 1 + 1 (x) T + diag(v_a + v_b + V_ab) on n^2 product points.
+    In 1D the spatially symmetric (singlet) state is the ground state."""
+    n = T.shape[0]
+    diag = (v[:, None] + v[None, :] + V).ravel()
+    if n <= 40:
+        I = np.eye(n)
+        H = np.kron(T, I) + np.kron(I, T) + np.diag(diag)
+        return float(np.linalg.eigvalsh(H)[0])
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    Ts = sp.csr_matrix(T)
+    I = sp.identity(n, format="csr")
+    H = sp.kron(Ts, I) + sp.kron(I, Ts) + sp.diags(diag)
+    val = spl.eigsh(H.tocsr(), k=1, which="SA", tol=1e-12)[0]
+    return float(val[0])

@@ -1,0 +1,111 @@
+"""Pins for the oracle's HF, chemical potential and g^0 (Sec. 2.3, Eqs. sigmahf, hamhf, hfgf)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import fedvr_oracle as O
+from paper_0911_4348_gb300 import workloads as W
+from tests.conftest import load_golden
+
+PAPER = load_golden("paper_values.txt")
+
+
+def _system(s):
+    b = O.fedvr_basis(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    T = O.kinetic(b)
+    v = O.potential(b["nodes"], s.Z, s.R, s.soft_en)
+    V = O.interaction(b["nodes"], s.soft_ee)
+    return b, T, v, V
+
+
+@pytest.fixture(scope="module")
+def he_small():
+    s = W.he_small()
+    b, T, v, V = _system(s)
+    h = T + np.diag(v)
+    hf = O.hf_scf(h, V, 2.0, 1, s.beta, tol=1e-13)
+    return s, b, T, v, V, h, hf
+
+
+def test_balanced_mu_equals_direct_normalisation_when_well_conditioned():
+    rng = np.random.default_rng(5)
+    eps = np.sort(rng.uniform(-2, 2, 9))
+    beta = 1.5  # small beta: the direct form sum f = nocc is well conditioned
+    mu = O.chemical_potential(eps, 3, beta)
+    lo, hi = -10.0, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.sum(1.0 / (np.exp(beta * (eps - mid)) + 1.0)) < 3.0:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(mu - lo) < 1e-13
+
+
+def test_mu_normalises_and_sits_in_gap(he_small):
+    s, b, T, v, V, h, hf = he_small
+    eps, mu = hf["eps"], hf["mu"]
+    assert eps[0] < mu < eps[1]
+    f = O.fermi(eps - mu, s.beta)
+    assert abs(2.0 * f.sum() - 2.0) < 1e-13
+    # holes = particles at the root, both tiny but resolved
+    holes = 1.0 - f[0]
+    parts = f[1:].sum()
+    assert abs(holes - parts) <= 1e-10 * parts
+
+
+def test_hf_closed_shell_identity(he_small):
+    # two electrons in one spatial orbital: E_HF = 2 h_11 + J_11
+    s, b, T, v, V, h, hf = he_small
+    c = hf["C"][:, 0]
+    J = float(c ** 2 @ V @ c ** 2)
+    E = 2.0 * float(c @ h @ c) + J
+    assert abs(E - hf["E_hf"]) < 1e-12
+    # self-consistency: the Fock matrix of rho0 has the same eigenvectors
+    F = h + O.hf_selfenergy(hf["rho0"], V, 2.0)
+    assert np.max(np.abs(F - hf["F"])) < 1e-11
+
+
+def test_hf_selfenergy_structure():
+    rng = np.random.default_rng(1)
+    n = 5
+    V = W.random_symmetric(rng, n)
+    rho = W.random_symmetric(rng, n)
+    S = O.hf_selfenergy(rho, V, 2.0)
+    for a in range(n):
+        for c in range(n):
+            hart = 2.0 * sum(V[a, k] * rho[k, k] for k in range(n)) if a == c else 0.0
+            assert abs(S[a, c] - (hart - V[a, c] * rho[a, c])) < 1e-14
+
+
+def test_g0_identities(he_small):
+    s, b, T, v, V, h, hf = he_small
+    mesh = O.power_mesh(s.beta, s.u, s.p)
+    G0 = O.g0_mesh(hf["eps"], hf["C"], hf["mu"], mesh["tau"], s.beta)
+    n = b["n"]
+    # g(0^-) + g(-beta) = 1 and sigma Tr g(0^-) = N
+    assert np.max(np.abs(G0[-1] + G0[0] - np.eye(n))) < 1e-14
+    assert abs(2.0 * np.trace(G0[-1]) - 2.0) < 1e-12
+    # g^0(tau) = expm(-tau (F - mu)) g^0(0^-) (Eq. hfgf solves this ODE)
+    for j in (mesh["M"] - 2, mesh["M"] - 10, mesh["M"] - 30):
+        tau = mesh["tau"][j]
+        if tau < -5.0:
+            continue
+        ref = scipy.linalg.expm(-tau * (hf["F"] - hf["mu"] * np.eye(n))) @ G0[-1]
+        assert np.max(np.abs(ref - G0[j])) < 1e-11
+
+
+def test_paper_hf_limit_and_exact_energy_case2_grid():
+    # Sec. 3.1: case II grid, 200 a.u., n_e = 29, n_g = 7 (n_b = 202)
+    b = O.fedvr_basis(29, 7, -100.0, 100.0, 1)
+    T = O.kinetic(b)
+    v = O.potential(b["nodes"], [2.0], [0.0], 1.0)
+    V = O.interaction(b["nodes"], 1.0)
+    hf = O.hf_scf(T + np.diag(v), V, 2.0, 1, 100.0, tol=1e-12)
+    assert abs(hf["E_hf"] - PAPER["he_hf_limit_Ha"]) < 5e-7
+    Eex = O.exact_ground(T, v, V)
+    assert abs(Eex - PAPER["he_exact_Ha"]) < 2e-7
+    # exact energy is below HF (correlation energy negative)
+    assert Eex < hf["E_hf"]
