@@ -51,7 +51,7 @@ def test_mu_normalises_and_sits_in_gap(he_small):
     f = O.fermi(eps - mu, s.beta)
     assert abs(2.0 * f.sum() - 2.0) < 1e-13
     # holes = particles at the root, both tiny but resolved
-    holes = 1.0 - f[0]
+    holes = O.fermi(np.array([mu - eps[0]]), s.beta)[0]   # 1 - f(eps_0 - mu), resolved
     parts = f[1:].sum()
     assert abs(holes - parts) <= 1e-10 * parts
 
