@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the second-Born hot path: Sigma^(2) builds per second.
+
+One step = one pass of the whole hot path over the workload: the Sigma^(2)
+build for every mesh point (direct + exchange), the HF self-energy change and
+the Galitskii-Migdal energy, the two Dyson convolutions and the mixed update
+with its residual, i.e. one iteration of the self-consistency. Each step
+contains exactly one Sigma^(2) build, so steps/s = builds/s.
+
+Default workload (N=1): 1D He, Z=2, box [-50,50], 25 elements of order 8
+(n_b = 199), beta = 100, 513-point power mesh (u=16, p=16), mixing 0.5.
+Every rank runs its own replica of the workload (independent systems, weak
+scaling); ranks only meet at the timing barrier.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|tf32|bf16] [--workload he_medium|he_small|h3p_large]
+                    [--time-to-e0]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_0911_4348_gb300 import workloads as W  # noqa: E402
+
+METRIC = "Sigma^(2) builds/s (one build + its Dyson iteration per step)"
+UNIT = "builds/s"
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2}
+WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large}
+N_SM = 152
+FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
+
+
+def algorithmic(stage: str, n: int, M: int) -> float:
+    """Algorithmic flops of one launch of a stage (one mesh, one system)."""
+    if stage == "conv1":
+        return 2.0 * M * M * n ** 3          # M^2 products of n x n matrices
+    if stage == "sigma2":
+        return M * (1.0 * n ** 4 + 4.0 * n ** 3)  # symmetric exchange half + direct term
+    if stage == "conv2":
+        return 2.0 * M * M * n * n + 8.0 * M * n ** 3
+    return 0.0
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.dev = device_id
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.dev:
+            cmd += ["-i", self.dev]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def _cpu_cores() -> int:
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(sys_: W.System, n_sigma: int, n_rows: int, prepared=None):
+    """Time the CPU oracle on a bounded sample of one iteration of the
+    workload and scale it to builds/s: n_sigma mesh points of the Sigma^(2)
+    build and n_rows output rows of each convolution, extrapolated to all M."""
+    from oracle import fedvr_oracle as O
+    if prepared is None:
+        b = O.fedvr_basis(sys_.n_elem, sys_.order, sys_.xmin, sys_.xmax, sys_.grid_kind)
+        T, v = O.kinetic(b), O.potential(b["nodes"], sys_.Z, sys_.R, sys_.soft_en)
+        V = O.interaction(b["nodes"], sys_.soft_ee)
+        h = T + np.diag(v)
+        hf = O.hf_scf(h, V, 2.0, sys_.n_elec // 2, sys_.beta, tol=1e-12)
+        mesh = O.power_mesh(sys_.beta, sys_.u, sys_.p)
+        G0 = O.g0_mesh(hf["eps"], hf["C"], hf["mu"], mesh["tau"], sys_.beta)
+        prepared = (V, hf, mesh, G0)
+    V, hf, mesh, G0 = prepared
+    M = G0.shape[0]
+    rng = np.random.default_rng(0)
+    js = rng.choice(M, size=min(n_sigma, M), replace=False)
+    rows = rng.choice(M, size=min(n_rows, M), replace=False)
+    t0 = time.perf_counter()
+    A = np.empty_like(G0)
+    for j in js:
+        A[j] = O.sigma2_tau(G0[j], G0[M - 1 - j], V, 2.0)
+    t1 = time.perf_counter()
+    A[:] = A[js[0]]  # stand-in values elsewhere: only the timing of the sample matters
+    lag = {"k": np.zeros((M, M), np.int32), "t": np.zeros((M, M)), "s": np.zeros((M, M))}
+    for i in rows:
+        for j in range(M):
+            if i != j:
+                y, sg = O.lag_point(mesh["tau"], sys_.beta, i, j)
+                k, t = O.bracket(mesh["tau"], y)
+                lag["k"][i, j], lag["t"][i, j], lag["s"][i, j] = k, t, sg
+    t2 = time.perf_counter()
+    I1 = np.zeros_like(G0)
+    I1[rows] = O.conv1(np.zeros_like(G0[0]), A, G0, mesh, sys_.beta, lag, rows=list(rows))
+    t3 = time.perf_counter()
+    O.conv2(I1, hf["eps"], hf["C"], hf["mu"], mesh, sys_.beta, rows=list(rows))
+    t4 = time.perf_counter()
+    per_iter = (t1 - t0) / len(js) * M + ((t3 - t2) + (t4 - t3)) / len(rows) * M
+    sample = (f"oracle Sigma^(2) at {len(js)} of {M} mesh points and both convolutions for "
+              f"{len(rows)} of {M} output rows, extrapolated to one full iteration")
+    return 1.0 / per_iter, sample, t4 - t0, prepared
+
+
+def run_reference(args, rank: int):
+    """The reference arm: the CPU oracle as it stands, on this host's cores."""
+    if rank != 0:
+        return
+    sys_ = WORKLOADS[args.workload]()
+    vals, prepared, spent = [], None, 0.0
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        v, sample, dt, prepared = oracle_sample(sys_, 2, 1, prepared)
+        spent += dt
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": sys_.name, "n_b": sys_.n_b, "n_tau": sys_.n_tau,
+                       "beta": sys_.beta, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="fp64")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="he_medium")
+    ap.add_argument("--time-to-e0", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    dist, rank, world, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_0911_4348_gb300 import Context
+
+    torch.cuda.set_device(local)
+    sys_ = WORKLOADS[args.workload]()
+    prec = PRECISIONS[args.precision]
+    stream = torch.cuda.current_stream()
+    ctx = Context(stream.cuda_stream)
+    ctx.build_fedvr(sys_.n_elem, sys_.order, sys_.xmin, sys_.xmax, sys_.grid_kind)
+    ctx.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
+    E_hf, _ = ctx.solve_hf(sys_.beta, tol=1e-12)
+    ctx.prepare_2b(sys_.beta, sys_.u, sys_.p, prec)
+    n, M = sys_.n_b, sys_.n_tau
+
+    for _ in range(args.warmup):
+        ctx.step_2b(sys_.mixing)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    dev_id = None
+    try:
+        dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        dev_id = None
+    clocks = ClockSampler(dev_id)
+    stage_ms = {}
+    launches = 0
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.step_2b(sys_.mixing)
+        st, nl = ctx.stage_times()
+        launches += nl
+        for k, v in st.items():
+            stage_ms.setdefault(k, []).append(v)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / (elapsed / 1000.0)
+
+    # end to end through the public API: each step takes its input g from
+    # pinned host memory and returns its scalars to the host
+    G_host = torch.empty((M, n, n), dtype=torch.float64, pin_memory=True)
+    ctx.read_2b(G_out=G_host.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.step_2b(sys_.mixing, G_in=G_host.numpy())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": M * n * n * 8, "d2h_bytes_per_step": 3 * 8}
+
+    avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
+    dom = max(("sigma2", "conv1", "conv2"), key=lambda k: avg.get(k, 0.0))
+    peaks = load_peaks()
+    if prec == 0:
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+        bound, punit, psrc = "alu", "TFLOP/s", ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x "
+                                               f"{sm_max:.0f} MHz (unit counts and clocks)")
+    else:
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) / 2.0
+        bound, punit, psrc = "tensor", "TFLOP/s", "measured bf16 sustained x 1/2 (tf32 ratio)"
+    achieved = algorithmic(dom, n, M) / (avg[dom] / 1000.0) / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
+            "frac": achieved / peak, "traffic": None, "kernel": dom,
+            "algorithmic_flops_per_launch": algorithmic(dom, n, M), "peak_source": psrc,
+            "stage_ms": avg}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == 0 else args.precision,
+           "data": "synthetic",
+           "config": {"workload": sys_.name, "n_b": n, "n_tau": M, "beta": sys_.beta,
+                      "precision": args.precision, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (g stack %.0f MB)" % (M * n * n * 8 / 1e6)},
+           "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+           "E_hf": E_hf}
+
+    if args.time_to_e0:
+        ctx2 = Context(stream.cuda_stream)
+        ctx2.build_fedvr(sys_.n_elem, sys_.order, sys_.xmin, sys_.xmax, sys_.grid_kind)
+        ctx2.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
+        ctx2.solve_hf(sys_.beta, tol=1e-12)
+        barrier()
+        t0 = time.perf_counter()
+        r = ctx2.solve_2b(sys_.beta, sys_.u, sys_.p, sys_.mixing, sys_.tol, 200, prec, check=False)
+        barrier()
+        hist = ctx2.get_history()
+        Ef = r["E0"]
+        k_ok = next(i for i in range(len(hist)) if np.all(np.abs(hist[i:, 2] - Ef) <= 1e-6))
+        out["time_to_E0"] = {"seconds": float(np.sum(hist[: k_ok + 1, 4]) / 1000.0),
+                             "iterations": int(k_ok + 1), "solve_seconds": time.perf_counter() - t0,
+                             "solve_iterations": r["iters"], "E0": Ef, "status": r["status"]}
+        ctx2.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, _, _ = oracle_sample(sys_, 6, 3)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": _cpu_cores(), "kind": "oracle",
+                               "sample": sample}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * fedvr_negf.h -- C ABI of the GB300 (sm_103a) FE-DVR second-Born library.
+ *
+ * The library computes the equilibrium (Matsubara) second-Born ground state of
+ * the FE-DVR method of Balzer, Bauch & Bonitz (arXiv:0911.4348): basis and
+ * quadrature setup (Sec. 2.1-2.2), Hartree-Fock (Sec. 2.3, Eqs. sigmahf,
+ * hamhf, hfgf), the second-Born self-energy in two-index form (Sec. 2.3,
+ * Eq. sigma2ndb), the two tau-convolutions of the Matsubara Dyson equation
+ * (Sec. 2.3, Eq. deq) on a uniform power mesh (Sec. 3.1) and the
+ * Galitskii-Migdal total energy (Sec. 2.3). Every step runs in CUDA kernels of
+ * this library on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: FEDVR_OK (0) or a negative fedvr_status. Arguments are
+ *    validated before any launch; an invalid one returns FEDVR_ERR_ARG and
+ *    changes nothing. The library never aborts and never throws. The message
+ *    of the last failure is kept per context (fedvr_last_error). A CUDA error
+ *    inside a call returns FEDVR_ERR_CUDA and is sticky: later calls on that
+ *    context return FEDVR_ERR_STATE.
+ *  - Matrices are dense, row-major, unpadded. A tau-stack of matrices is
+ *    [M][n][n] with tau ascending from -beta (index 0) to 0 (index M-1), the
+ *    paper's interval tau in [-beta, 0]. All floating point is IEEE double
+ *    unless stated.
+ *  - Memory: the context owns all its device workspace. Buffers passed in are
+ *    caller-owned; the library never frees them. Pointers documented as
+ *    "device" must be allocated on the context's device; "host" pointers are
+ *    ordinary host memory.
+ *  - Streams: all work of a context is enqueued on the stream given to
+ *    fedvr_create. Calls that return scalars or write host buffers synchronise
+ *    that stream before returning; stage-level calls that only write device
+ *    buffers return without synchronising.
+ *  - Order: build_fedvr -> set_potential -> solve_hf -> solve_2b. Calling out
+ *    of order returns FEDVR_ERR_STATE. A context is not re-entrant; distinct
+ *    contexts are independent.
+ */
+#ifndef FEDVR_NEGF_H
+#define FEDVR_NEGF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fedvr_ctx fedvr_ctx;
+
+typedef enum {
+  FEDVR_OK = 0,
+  FEDVR_ERR_ARG = -1,      /* invalid argument, nothing was launched */
+  FEDVR_ERR_CUDA = -2,     /* a CUDA call failed; the context is now unusable */
+  FEDVR_ERR_NOCONV = -3,   /* max_iter reached before the tolerance */
+  FEDVR_ERR_DIVERGED = -4, /* residual grew for 8 consecutive iterations */
+  FEDVR_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+  FEDVR_ERR_NAN = -6,      /* a NaN or Inf reached the iterate */
+  FEDVR_ERR_STATE = -7     /* call out of order, or context already failed */
+} fedvr_status;
+
+typedef enum {
+  FEDVR_FP64 = 0,        /* every contraction in IEEE double */
+  FEDVR_SPLIT_TF32 = 1,  /* Sigma^(2) and I^(1) contractions on tensor cores,
+                            hi+lo TF32 operands, FP32 accumulation, FP64
+                            epilogues and cross-tile sums */
+  FEDVR_SPLIT_BF16 = 2   /* as above with three-way BF16 splits */
+} fedvr_precision;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Create a context on the current CUDA device. cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream), e.g. torch.cuda.current_stream().cuda_stream.
+ * *out receives the handle (NULL on failure). */
+int fedvr_create(fedvr_ctx **out, void *cuda_stream);
+
+/* Free the context and all its device workspace. NULL is allowed. */
+void fedvr_destroy(fedvr_ctx *ctx);
+
+/* Text of the last failure on ctx ("" if none). Owned by ctx; valid until the
+ * next call on ctx. */
+const char *fedvr_last_error(const fedvr_ctx *ctx);
+
+/* ---------------------------------------------------------------------- */
+/* Basis and operators (Sec. 2.1-2.2)                                      */
+/* ---------------------------------------------------------------------- */
+
+/* FE-DVR basis on [xmin, xmax] with n_elem finite elements of polynomial order
+ * `order` (order + 1 Gauss-Lobatto-Legendre points per element; Sec. 2.1,
+ * Eqs. xim, wim, basis; the paper's n_g is this order). grid_kind 0: equal
+ * elements (Sec. 3.1 case I); 1: a central element of width 1 and widths
+ * growing linearly outward (case II). The basis excludes both box ends, so
+ * *n_b_out = n_elem*order - 1 (Eq. basisdim). Nodes, weights, the index map
+ * and the kinetic matrix T (Eq. tmat) are built on the device bit-identically
+ * to a plain IEEE evaluation in a fixed order (no fused multiply-add).
+ * Limits: 1 <= n_elem, 1 <= order <= 32, 2 <= n_b <= 1024, xmin < xmax.
+ * Resets any potential/HF/2B state of the context. */
+int build_fedvr(fedvr_ctx *ctx, int n_elem, int order, double xmin, double xmax,
+                int grid_kind, int *n_b_out);
+
+/* Nuclear potential and interaction (Sec. 2.2 Eqs. vmat, umat1; Sec. 3 model
+ * potentials): v_a = sum_A -Z_A / sqrt((x_a - R_A)^2 + soft_en),
+ * V_ab = 1/sqrt((x_a - x_b)^2 + soft_ee), h = T + diag(v). Z and R are host
+ * arrays of n_nuc doubles. n_elec electrons, closed shell (n_elec even).
+ * *E_nn_out (may be NULL) receives sum_{A<B} Z_A Z_B / |R_A - R_B|, which is
+ * NOT part of any E0 this library returns. */
+int set_potential(fedvr_ctx *ctx, int n_nuc, const double *Z, const double *R,
+                  double soft_en, double soft_ee, int n_elec, double *E_nn_out);
+
+/* Copy the basis to host buffers of n_b entries each (any may be NULL):
+ * node coordinates, quadrature weights W_a (bridge = sum of two element
+ * weights), element index and local point index of each basis function (a
+ * bridge reports the left element and local index `order`). */
+int fedvr_get_basis(const fedvr_ctx *ctx, double *nodes, double *weights, int *elem,
+                    int *local);
+
+/* Copy the GLL reference points and weights (order + 1 each) to host. */
+int fedvr_get_gll(const fedvr_ctx *ctx, double *xi, double *omega);
+
+/* Copy operators to host [n_b][n_b] buffers (v: [n_b]); any may be NULL.
+ * Requires set_potential for v, V, h. */
+int fedvr_get_operators(const fedvr_ctx *ctx, double *T, double *v, double *V, double *h);
+
+/* ---------------------------------------------------------------------- */
+/* Hartree-Fock (Sec. 2.3, Eqs. sigmahf, hamhf, hfgf)                      */
+/* ---------------------------------------------------------------------- */
+
+/* Self-consistent HF at inverse temperature beta: F = h + Sigma^HF[rho],
+ * Sigma^HF = sigma diag(V diag rho) - V o rho (sigma = 2), diagonalisation on
+ * the GPU (Jacobi), chemical potential from the Fermi normalisation
+ * sum_a f(eps_a - mu) = n_elec/2 solved in its balanced holes = particles form,
+ * rho' = C diag f C^T, linear mixing 0.5, stop when max|rho' - rho| < tol.
+ * Outputs (host, may be NULL): E_hf = 2 Tr[h rho] + Tr[Sigma^HF rho] (no E_nn)
+ * and mu. Returns FEDVR_ERR_NOCONV after max_iter steps. */
+int solve_hf(fedvr_ctx *ctx, double beta, double tol, int max_iter, double *E_hf, double *mu);
+
+/* Copy the HF solution to host (any may be NULL): eps [n_b] ascending, C
+ * [n_b][n_b] (column a = orbital a), rho0 = g^0(0^-) [n_b][n_b] and
+ * Sigma0 = F - h [n_b][n_b]. */
+int fedvr_get_hf(const fedvr_ctx *ctx, double *eps, double *C, double *rho0, double *Sigma0);
+
+/* ---------------------------------------------------------------------- */
+/* Second Born (Sec. 2.3 Eqs. sigma2ndb, deq; Sec. 3.1 mesh)               */
+/* ---------------------------------------------------------------------- */
+
+/* Second-Born Matsubara self-consistency on the uniform power mesh with
+ * M = 2up+1 points. Iteration k: Sigma_k = Sigma^corr[g_k] (Eq. sigma2ndb),
+ * I1 = (Sigma^HF[g_k(0^-)] - Sigma^0) g_k + Sigma_k * g_k,
+ * I2 = g^0 * I1 (Eq. deq), g_new = sym(g^0 + I2),
+ * g_{k+1} = (1 - mixing) g_k + mixing g_new, r_k = max|g_{k+1} - g_k|; stop at
+ * r_k < tol. E0_k (Galitskii-Migdal, no E_nn) and N_k = 2 Tr g_k(0^-) are
+ * evaluated on (g_k, Sigma_k). precision: fedvr_precision.
+ * Outputs: G_out = g_{k+1}, Sigma_out = Sigma_k (each [M][n_b][n_b]), tau_out
+ * [M]; any may be NULL; device pointers if out_on_device else host.
+ * Scalars (host, may be NULL): E0, N_out, iters. Limits: u, p >= 1,
+ * M <= 4097, 0 < mixing <= 1. */
+int solve_2b(fedvr_ctx *ctx, double beta, int u, int p, double mixing, double tol,
+             int max_iter, int precision, int out_on_device, double *G_out,
+             double *Sigma_out, double *tau_out, double *E0, double *N_out, int *iters);
+
+/* Split form of solve_2b for callers that drive the iteration themselves.
+ * fedvr_2b_prepare builds the mesh, g^0 on the mesh and the convolution
+ * tables for (beta, u, p, precision) and sets g_0 = g^0 (or keeps a warm-start
+ * Sigma for the first step). fedvr_2b_step runs exactly one iteration of the
+ * solve_2b scheme; if G_in is non-NULL the iterate g_k is first replaced by
+ * G_in ([M][n_b][n_b], device if in_on_device else host). Host scalars (may be
+ * NULL): res = max|g_{k+1} - g_k|, E0 and N evaluated on (g_k, Sigma_k).
+ * fedvr_2b_read copies the current iterate g and the last Sigma out (any may
+ * be NULL; device pointers if out_on_device). */
+int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision);
+int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_device,
+                  double *res, double *E0, double *N_out);
+int fedvr_2b_read(fedvr_ctx *ctx, int out_on_device, double *G_out, double *Sigma_out,
+                  double *tau_out);
+
+/* Device durations (milliseconds, CUDA events on the context's stream) of the
+ * stages of the last fedvr_2b_step: [0] Sigma^(2) build, [1] HF self-energy
+ * change and energy, [2] first convolution I1, [3] second convolution I2,
+ * [4] update and residual, [5] whole step. *launches (may be NULL) receives the
+ * number of kernels that step launched. ms is a host array of 6 doubles. */
+int fedvr_stage_times(const fedvr_ctx *ctx, double *ms, int *launches);
+
+/* Start the next solve_2b from this Sigma^corr in its first iteration instead
+ * of Sigma^corr[g^0] (warm start). Sigma0 is [M][n_b][n_b] on host or device;
+ * M must match the next solve's mesh. Pass NULL to clear. Copied at once. */
+int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_device);
+
+/* Per-iteration record of the last solve_2b: 5 doubles per iteration
+ * (iteration, residual, E0, N, wall milliseconds). Copies min(cap, count)
+ * records to buf (host, 5*cap doubles); *len = number of records. */
+int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len);
+
+/* Batched solve over n_sys independent prepared contexts (each has run
+ * build_fedvr, set_potential and solve_hf). Arrays have n_sys entries; the
+ * per-system result pointers follow solve_2b (host outputs; any entry may be
+ * NULL). All systems advance together, one batched launch per kernel per
+ * iteration, on the stream of ctxs[0]; each stops updating when it
+ * converges. Returns the worst status over systems. */
+int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u,
+                     const int *p, double mixing, double tol, int max_iter, int precision,
+                     double *E0, double *N_out, int *iters);
+
+/* ---------------------------------------------------------------------- */
+/* Stage-level calls on caller device buffers (the hot-path kernels)       */
+/* ---------------------------------------------------------------------- */
+
+/* Uniform power mesh (Sec. 3.1): B_p = beta/2, B_{k-1} = B_k/2, B_0 = 0,
+ * segment k cut in u parts, tau_j = -beta + s_j (j <= up), tau_{M-1-m} = -s_m.
+ * Trapezoid weights w, left/right half weights wm, wp. Device outputs of M
+ * doubles each (any may be NULL); lag_k [M][M] int32 and lag_t [M][M] double
+ * (may be NULL): for i != j the bracket k and weight t of the lag
+ * tau_i - tau_j mapped to [-beta, 0] (anti-periodic extension); diagonal
+ * k = -1, t = 0. Bit-identical to a plain IEEE evaluation. */
+int fedvr_power_mesh(fedvr_ctx *ctx, double beta, int u, int p, double *tau, double *w,
+                     double *wm, double *wp, int *lag_k, double *lag_t);
+
+/* Second-Born self-energy for a whole tau-stack (Sec. 2.3, Eq. sigma2ndb in
+ * two-index form): Sigma_j = spin * g_j o (V (g_j o gb_j) V) - X_j with
+ * gb_j = G[M-1-j] and X_j,ab = sum_kl V_ak V_bl g_j,al gb_j,lk g_j,kb.
+ * V [n][n] and G [M][n][n] are device inputs; each G_j and V must be symmetric
+ * (the lower triangle is used). Sigma [M][n][n] is a device output.
+ * precision: fedvr_precision. Uses context workspace. */
+int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V,
+                 const double *G, double *Sigma, int precision);
+
+/* First Dyson convolution (Eq. deq): I1_i = dHF g_i + int Sigma(tau_i - t) g(t) dt
+ * on the power mesh (beta, u, p), split trapezoid at t = tau_i with
+ * Sigma(0^+) = -Sigma_0, Sigma(0^-) = Sigma_{M-1}; Sigma at off-mesh lags by
+ * linear interpolation, anti-periodic beyond 0. dHF [n][n], Sigma and G
+ * [M][n][n] device inputs; I1 [M][n][n] device output. */
+int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *dHF,
+                       const double *Sigma, const double *G, double *I1, int precision);
+
+/* Second Dyson convolution (Eq. deq): I2_i = int g^0(tau_i - t) I1(t) dt with
+ * g^0(x) = C diag(phi(x)) C^T evaluated exactly at every lag (Eq. hfgf), same
+ * split trapezoid (g^0(0^+) = -g^0(-beta)); computed in the HF eigenbasis.
+ * eps [n] (ascending not required), C [n][n], I1 [M][n][n] device inputs;
+ * I2 [M][n][n] device output. */
+int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *eps,
+                  const double *C, double mu, const double *I1, double *I2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEDVR_NEGF_H */

@@ -623,6 +623,15 @@ def sigma2_tau(g: np.ndarray, gb: np.ndarray, V: np.ndarray, sigma: float) -> np
     return D - X
 
 
+def sigma2_element(g: np.ndarray, gb: np.ndarray, V: np.ndarray, sigma: float, a: int,
+                   b: int) -> float:
+    """One element Sigma^corr_ab from the two sums of ``sigma2_tau`` written
+    out, O(n^2): sigma g_ab sum_kl V_ak g_kl gb_lk V_lb - sum_kl V_ak V_bl g_al gb_lk g_kb."""
+    direct = sigma * g[a, b] * float(np.einsum("k,kl,l->", V[a], g * gb, V[:, b]))
+    exch = float(np.einsum("k,l,l,lk,k->", V[a], V[b], g[a], gb, g[:, b]))
+    return direct - exch
+
+
 def sigma2(G: np.ndarray, V: np.ndarray, sigma: float) -> np.ndarray:
     """Sigma^corr(tau_j) for every j; gb_j = G[M-1-j] (mesh mirror symmetry)."""
     M = G.shape[0]

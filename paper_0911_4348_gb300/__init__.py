@@ -1,0 +1,248 @@
+"""GB300-native FE-DVR second-Born Green's functions (arXiv:0911.4348).
+
+Thin Python binding over the C ABI of ``libfedvr_negf.so`` (declared in
+include/fedvr_negf.h). Every call marshals arguments and forwards to the CUDA
+library; no numerical step runs in Python. Device buffers are float64 torch
+tensors on the context's device; host buffers are numpy arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native
+
+FP64, SPLIT_TF32, SPLIT_BF16 = 0, 1, 2
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOCONV", -4: "ERR_DIVERGED",
+          -5: "ERR_TIMEOUT", -6: "ERR_NAN", -7: "ERR_STATE"}
+
+
+class FedvrError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS.get(code, code)}: {message}")
+        self.code = code
+
+
+def _dptr(arr):
+    """ctypes double* for a host numpy array (or None)."""
+    if arr is None:
+        return None
+    assert arr.dtype == np.float64 and arr.flags["C_CONTIGUOUS"]
+    return arr.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(arr):
+    if arr is None:
+        return None
+    assert arr.dtype == np.int32 and arr.flags["C_CONTIGUOUS"]
+    return arr.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _dev(t, shape=None, dtype=None):
+    """Raw device address of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    if dtype is None and t.dtype != torch.float64:
+        raise ValueError("expected float64")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_or_dev(x):
+    if x is None:
+        return None, False
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data), False
+    return _dev(x), True
+
+
+class Context:
+    """A library context (``fedvr_create``) bound to a CUDA stream."""
+
+    def __init__(self, stream=None):
+        self._lib = _native.lib()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = C.c_void_p()
+        code = self._lib.fedvr_create(C.byref(self._h), C.c_void_p(stream))
+        if code != 0:
+            raise FedvrError(code, "fedvr_create failed")
+        self.n_b = 0
+
+    def close(self):
+        if self._h:
+            self._lib.fedvr_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, code):
+        if code != 0:
+            msg = self._lib.fedvr_last_error(self._h)
+            raise FedvrError(code, msg.decode() if msg else "")
+        return code
+
+    def last_error(self) -> str:
+        return self._lib.fedvr_last_error(self._h).decode()
+
+    # -- basis and operators -------------------------------------------------
+    def build_fedvr(self, n_elem, order, xmin, xmax, grid_kind=0) -> int:
+        nb = C.c_int()
+        self._check(self._lib.build_fedvr(self._h, n_elem, order, xmin, xmax, grid_kind, C.byref(nb)))
+        self.n_b = nb.value
+        self.order = order
+        return nb.value
+
+    def set_potential(self, Z, R, soft_en=1.0, soft_ee=1.0, n_elec=2) -> float:
+        Z = np.ascontiguousarray(Z, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        enn = C.c_double()
+        self._check(self._lib.set_potential(self._h, len(Z), _dptr(Z), _dptr(R), soft_en, soft_ee,
+                                            n_elec, C.byref(enn)))
+        return enn.value
+
+    def get_basis(self):
+        n = self.n_b
+        x, w = np.empty(n), np.empty(n)
+        e, m = np.empty(n, np.int32), np.empty(n, np.int32)
+        self._check(self._lib.fedvr_get_basis(self._h, _dptr(x), _dptr(w), _iptr(e), _iptr(m)))
+        return dict(nodes=x, weights=w, elem=e, local=m)
+
+    def get_gll(self):
+        xi, om = np.empty(self.order + 1), np.empty(self.order + 1)
+        self._check(self._lib.fedvr_get_gll(self._h, _dptr(xi), _dptr(om)))
+        return xi, om
+
+    def get_operators(self, potential=True):
+        n = self.n_b
+        T = np.empty((n, n))
+        if not potential:
+            self._check(self._lib.fedvr_get_operators(self._h, _dptr(T), None, None, None))
+            return dict(T=T)
+        v, V, h = np.empty(n), np.empty((n, n)), np.empty((n, n))
+        self._check(self._lib.fedvr_get_operators(self._h, _dptr(T), _dptr(v), _dptr(V), _dptr(h)))
+        return dict(T=T, v=v, V=V, h=h)
+
+    # -- Hartree-Fock -----------------------------------------------------------
+    def solve_hf(self, beta, tol=1e-12, max_iter=500):
+        e, mu = C.c_double(), C.c_double()
+        self._check(self._lib.solve_hf(self._h, beta, tol, max_iter, C.byref(e), C.byref(mu)))
+        return e.value, mu.value
+
+    def get_hf(self):
+        n = self.n_b
+        eps, Cm, rho, S0 = np.empty(n), np.empty((n, n)), np.empty((n, n)), np.empty((n, n))
+        self._check(self._lib.fedvr_get_hf(self._h, _dptr(eps), _dptr(Cm), _dptr(rho), _dptr(S0)))
+        return dict(eps=eps, C=Cm, rho0=rho, Sigma0=S0)
+
+    # -- second Born ------------------------------------------------------------
+    def solve_2b(self, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200, precision=FP64,
+                 G_out=None, Sigma_out=None, tau_out=None, check=True):
+        """Run the self-consistency. Outputs may be numpy arrays (host) or CUDA
+        tensors (device); all given outputs must be of the same kind."""
+        outs = [_host_or_dev(x) for x in (G_out, Sigma_out, tau_out)]
+        kinds = {d for (p_, d) in outs if p_ is not None}
+        if len(kinds) > 1:
+            raise ValueError("outputs must all be host or all be device")
+        on_dev = 1 if kinds == {True} else 0
+        E0, N, it = C.c_double(), C.c_double(), C.c_int()
+        code = self._lib.solve_2b(self._h, beta, u, p, mixing, tol, max_iter, precision, on_dev,
+                                  outs[0][0], outs[1][0], outs[2][0], C.byref(E0), C.byref(N),
+                                  C.byref(it))
+        if check:
+            self._check(code)
+        return dict(E0=E0.value, N=N.value, iters=it.value, status=code)
+
+    def prepare_2b(self, beta, u, p, precision=FP64):
+        self._check(self._lib.fedvr_2b_prepare(self._h, beta, u, p, precision))
+        self.M = 2 * u * p + 1
+
+    def step_2b(self, mixing=0.5, G_in=None, check=True):
+        """One iteration; G_in (host numpy or CUDA tensor) replaces the iterate first."""
+        ptr, dev = _host_or_dev(G_in)
+        res, E0, N = C.c_double(), C.c_double(), C.c_double()
+        code = self._lib.fedvr_2b_step(self._h, mixing, ptr, 1 if dev else 0, C.byref(res),
+                                       C.byref(E0), C.byref(N))
+        if check:
+            self._check(code)
+        return dict(res=res.value, E0=E0.value, N=N.value, status=code)
+
+    def stage_times(self):
+        """Device milliseconds of the last step's stages: sigma2, hf+energy,
+        conv1, conv2, update, whole step; and its kernel launch count."""
+        ms = np.empty(6)
+        ln = C.c_int()
+        self._check(self._lib.fedvr_stage_times(self._h, _dptr(ms), C.byref(ln)))
+        return dict(zip(("sigma2", "hf_energy", "conv1", "conv2", "update", "step"), ms)), ln.value
+
+    def read_2b(self, G_out=None, Sigma_out=None, tau_out=None):
+        outs = [_host_or_dev(x) for x in (G_out, Sigma_out, tau_out)]
+        kinds = {d for (p_, d) in outs if p_ is not None}
+        if len(kinds) > 1:
+            raise ValueError("outputs must all be host or all be device")
+        on_dev = 1 if kinds == {True} else 0
+        self._check(self._lib.fedvr_2b_read(self._h, on_dev, outs[0][0], outs[1][0], outs[2][0]))
+
+    def set_initial_sigma(self, Sigma0, M=None):
+        if Sigma0 is None:
+            self._check(self._lib.fedvr_set_initial_sigma(self._h, None, 0, 0))
+            return
+        ptr, dev = _host_or_dev(Sigma0)
+        M = Sigma0.shape[0] if M is None else M
+        self._check(self._lib.fedvr_set_initial_sigma(self._h, ptr, M, 1 if dev else 0))
+
+    def get_history(self) -> np.ndarray:
+        ln = C.c_int()
+        self._check(self._lib.fedvr_get_history(self._h, None, 0, C.byref(ln)))
+        buf = np.empty(5 * max(ln.value, 1))
+        self._check(self._lib.fedvr_get_history(self._h, _dptr(buf), ln.value, C.byref(ln)))
+        return buf[: 5 * ln.value].reshape(-1, 5)
+
+    # -- stage-level calls on device buffers -----------------------------------------
+    def power_mesh(self, beta, u, p, tau=None, w=None, wm=None, wp=None, lag_k=None, lag_t=None):
+        import torch
+        self._check(self._lib.fedvr_power_mesh(self._h, beta, u, p, _dev(tau), _dev(w), _dev(wm),
+                                               _dev(wp), _dev(lag_k, dtype=torch.int32),
+                                               _dev(lag_t)))
+
+    def sigma2(self, V, G, Sigma, spin=2.0, precision=FP64):
+        M, n = G.shape[0], G.shape[1]
+        self._check(self._lib.fedvr_sigma2(self._h, n, M, spin, _dev(V, (n, n)), _dev(G, (M, n, n)),
+                                           _dev(Sigma, (M, n, n)), precision))
+
+    def conv_sigma_g(self, beta, u, p, dHF, Sigma, G, I1, precision=FP64):
+        M, n = G.shape[0], G.shape[1]
+        assert M == 2 * u * p + 1
+        self._check(self._lib.fedvr_conv_sigma_g(self._h, n, beta, u, p, _dev(dHF, (n, n)),
+                                                 _dev(Sigma, (M, n, n)), _dev(G, (M, n, n)),
+                                                 _dev(I1, (M, n, n)), precision))
+
+    def conv_g0(self, beta, u, p, eps, Cmat, mu, I1, I2):
+        M, n = I1.shape[0], I1.shape[1]
+        assert M == 2 * u * p + 1
+        self._check(self._lib.fedvr_conv_g0(self._h, n, beta, u, p, _dev(eps, (n,)),
+                                            _dev(Cmat, (n, n)), mu, _dev(I1, (M, n, n)),
+                                            _dev(I2, (M, n, n))))
+
+
+__all__ = ["Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]

@@ -1,0 +1,668 @@
+// C ABI entry points and the host-side drivers of the FE-DVR second-Born
+// library: context and workspace management, the HF self-consistency and the
+// second-Born Dyson iteration (Sec. 2.3). Every numerical step is a kernel of
+// this library; the host only sequences launches and reads scalars.
+#include "common.cuh"
+
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+
+namespace fedvr {
+
+int fail(fedvr_ctx *ctx, int code, const char *fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(fedvr_ctx *ctx, cudaError_t e, const char *what, const char *file, int line) {
+  if (ctx) {
+    ctx->failed = true;
+    snprintf(ctx->err, sizeof(ctx->err), "CUDA error %d (%s) in %s at %s:%d", (int)e,
+             cudaGetErrorString(e), what, file, line);
+  }
+  return FEDVR_ERR_CUDA;
+}
+
+bool ensure(fedvr_ctx *ctx, DevBuf &buf, size_t bytes, const char *name) {
+  if (bytes == 0) bytes = 16;
+  if (buf.bytes >= bytes) return true;
+  if (buf.ptr) cudaFree(buf.ptr);
+  buf.ptr = nullptr;
+  buf.bytes = 0;
+  cudaError_t e = cudaMalloc(&buf.ptr, bytes);
+  if (e != cudaSuccess) {
+    buf.ptr = nullptr;
+    cudaGetLastError();
+    fail(ctx, FEDVR_ERR_CUDA, "cudaMalloc of %zu bytes for %s failed: %s", bytes, name,
+         cudaGetErrorString(e));
+    ctx->failed = true;
+    return false;
+  }
+  buf.bytes = bytes;
+  return true;
+}
+
+void release(DevBuf &buf) {
+  if (buf.ptr) cudaFree(buf.ptr);
+  buf.ptr = nullptr;
+  buf.bytes = 0;
+}
+
+}  // namespace fedvr
+
+using namespace fedvr;
+
+#define ENSURE(ctx, buf, bytes)                                   \
+  do {                                                            \
+    if (!ensure((ctx), (ctx)->buf, (bytes), #buf)) return FEDVR_ERR_CUDA; \
+  } while (0)
+
+#define CHECK_CTX(ctx)                                                           \
+  do {                                                                           \
+    if (!(ctx)) return FEDVR_ERR_ARG;                                            \
+    if ((ctx)->failed)                                                           \
+      return FEDVR_ERR_STATE;                                                    \
+  } while (0)
+
+namespace {
+
+inline size_t dsz(size_t n) { return n * sizeof(double); }
+
+inline bool is_fin(double x) { return isfinite(x); }
+
+int sync(fedvr_ctx *ctx) {
+  FEDVR_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return FEDVR_OK;
+}
+
+int copy_out(fedvr_ctx *ctx, void *dst, const void *src, size_t bytes, bool on_device) {
+  FEDVR_CK(ctx, cudaMemcpyAsync(dst, src, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  return FEDVR_OK;
+}
+
+// Mesh (tau, w, wm, wp) and, if requested, conv1 coefficients into workspace.
+int build_mesh(fedvr_ctx *ctx, double beta, int u, int p, bool coef) {
+  int M = 2 * u * p + 1;
+  ENSURE(ctx, w_tau, dsz(M));
+  ENSURE(ctx, w_w, dsz(M));
+  ENSURE(ctx, w_wm, dsz(M));
+  ENSURE(ctx, w_wp, dsz(M));
+  FEDVR_CK(ctx, launch_mesh(beta, u, p, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                            P<double>(ctx->w_wm), P<double>(ctx->w_wp), nullptr, nullptr,
+                            ctx->stream));
+  if (coef) {
+    ENSURE(ctx, w_coef, (size_t)M * M * sizeof(ConvCoef));
+    FEDVR_CK(ctx, launch_conv_coef(M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                                   P<double>(ctx->w_wm), P<double>(ctx->w_wp),
+                                   P<ConvCoef>(ctx->w_coef), ctx->stream));
+  }
+  return FEDVR_OK;
+}
+
+int check_mesh_args(fedvr_ctx *ctx, double beta, int u, int p) {
+  if (!(beta > 0.0) || !is_fin(beta)) return fail(ctx, FEDVR_ERR_ARG, "beta must be > 0");
+  if (u < 1 || p < 1 || p > 60) return fail(ctx, FEDVR_ERR_ARG, "need u >= 1, 1 <= p <= 60");
+  long M = 2L * u * p + 1;
+  if (M > 4097) return fail(ctx, FEDVR_ERR_ARG, "mesh too large: M = %ld > 4097", M);
+  return FEDVR_OK;
+}
+
+// Eigen-decomposition of the symmetric n x n matrix in A (destroyed), starting
+// from the orthogonal basis in Vinit (or the identity): eps ascending, C columns.
+int eig(fedvr_ctx *ctx, double *A, const double *Vinit, double *eps, double *C) {
+  int n = ctx->n;
+  double *V = P<double>(ctx->b_hf_tmp);
+  if (Vinit) {
+    FEDVR_CK(ctx, launch_copy((size_t)n * n, Vinit, V, ctx->stream));
+  } else {
+    FEDVR_CK(ctx, launch_identity(n, V, ctx->stream));
+  }
+  cudaError_t err = cudaSuccess;
+  int sweeps = jacobi_eig(n, A, P<double>(ctx->b_A2), V, P<double>(ctx->b_J),
+                          P<double>(ctx->b_scal), 1e-14, 60, ctx->stream, &err);
+  if (err != cudaSuccess) return cuda_fail(ctx, err, "jacobi_eig", __FILE__, __LINE__);
+  if (sweeps < 0) return fail(ctx, FEDVR_ERR_NOCONV, "Jacobi did not converge in 60 sweeps");
+  FEDVR_CK(ctx, launch_sort_eig(n, A, V, eps, C, ctx->stream));
+  return FEDVR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fedvr_create(fedvr_ctx **out, void *cuda_stream) {
+  if (!out) return FEDVR_ERR_ARG;
+  *out = nullptr;
+  fedvr_ctx *ctx = new (std::nothrow) fedvr_ctx();
+  if (!ctx) return FEDVR_ERR_ARG;
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return FEDVR_ERR_CUDA;
+  }
+  for (int i = 0; i < 7; ++i) {
+    if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->ev[j]);
+      delete ctx;
+      return FEDVR_ERR_CUDA;
+    }
+  }
+  *out = ctx;
+  return FEDVR_OK;
+}
+
+void fedvr_destroy(fedvr_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  DevBuf *bufs[] = {&ctx->b_xi, &ctx->b_om, &ctx->b_edges, &ctx->b_nodes, &ctx->b_weights,
+                    &ctx->b_elem, &ctx->b_local, &ctx->b_tt, &ctx->b_T, &ctx->b_v, &ctx->b_V,
+                    &ctx->b_h, &ctx->b_eps, &ctx->b_C, &ctx->b_rho, &ctx->b_rho_new,
+                    &ctx->b_rho_mix, &ctx->b_F, &ctx->b_Sigma0, &ctx->b_f, &ctx->b_A, &ctx->b_A2,
+                    &ctx->b_J, &ctx->b_scal, &ctx->b_hf_tmp, &ctx->b_sigma_init, &ctx->w_tau,
+                    &ctx->w_w, &ctx->w_wm, &ctx->w_wp, &ctx->w_coef, &ctx->w_K, &ctx->w_phi,
+                    &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
+                    &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc};
+  for (DevBuf *b : bufs) release(*b);
+  for (int i = 0; i < 7; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  delete ctx;
+}
+
+const char *fedvr_last_error(const fedvr_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+int build_fedvr(fedvr_ctx *ctx, int n_elem, int order, double xmin, double xmax, int grid_kind,
+                int *n_b_out) {
+  CHECK_CTX(ctx);
+  if (n_elem < 1 || order < 1 || order > 32)
+    return fail(ctx, FEDVR_ERR_ARG, "need n_elem >= 1 and 1 <= order <= 32");
+  long n = (long)n_elem * order - 1;
+  if (n < 2 || n > 1024) return fail(ctx, FEDVR_ERR_ARG, "n_b = %ld outside [2, 1024]", n);
+  if (!is_fin(xmin) || !is_fin(xmax) || !(xmin < xmax))
+    return fail(ctx, FEDVR_ERR_ARG, "need finite xmin < xmax");
+  if (grid_kind != 0 && grid_kind != 1) return fail(ctx, FEDVR_ERR_ARG, "grid_kind must be 0 or 1");
+  ctx->stage = 0;
+  ctx->n_elem = n_elem;
+  ctx->order = order;
+  ctx->n = (int)n;
+  ctx->xmin = xmin;
+  ctx->xmax = xmax;
+  ctx->grid_kind = grid_kind;
+  ctx->sigma_init_M = 0;
+  ENSURE(ctx, b_xi, dsz(order + 1));
+  ENSURE(ctx, b_om, dsz(order + 1));
+  ENSURE(ctx, b_edges, dsz(n_elem + 1));
+  ENSURE(ctx, b_nodes, dsz(n));
+  ENSURE(ctx, b_weights, dsz(n));
+  ENSURE(ctx, b_elem, n * sizeof(int));
+  ENSURE(ctx, b_local, n * sizeof(int));
+  ENSURE(ctx, b_tt, dsz((size_t)n_elem * (order + 1) * (order + 1)));
+  ENSURE(ctx, b_T, dsz(n * n));
+  ENSURE(ctx, b_scal, dsz(16));
+  int *status = reinterpret_cast<int *>(P<double>(ctx->b_scal) + 8);
+  FEDVR_CK(ctx, cudaMemsetAsync(status, 0, 2 * sizeof(int), ctx->stream));
+  FEDVR_CK(ctx, launch_gll(order, P<double>(ctx->b_xi), P<double>(ctx->b_om), status, ctx->stream));
+  FEDVR_CK(ctx, launch_basis(n_elem, order, xmin, xmax, grid_kind, P<double>(ctx->b_xi),
+                             P<double>(ctx->b_om), P<double>(ctx->b_edges), P<double>(ctx->b_nodes),
+                             P<double>(ctx->b_weights), P<int>(ctx->b_elem), P<int>(ctx->b_local),
+                             P<double>(ctx->b_tt), P<double>(ctx->b_T), status + 1, ctx->stream));
+  int st[2];
+  FEDVR_CK(ctx, cudaMemcpyAsync(st, status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+  if (int r = sync(ctx)) return r;
+  if (st[0] != 0) return fail(ctx, FEDVR_ERR_ARG, "GLL root scan failed for order %d", order);
+  if (st[1] != 0) return fail(ctx, FEDVR_ERR_ARG, "graded grid: non-positive element width");
+  ctx->stage = 1;
+  if (n_b_out) *n_b_out = (int)n;
+  return FEDVR_OK;
+}
+
+int set_potential(fedvr_ctx *ctx, int n_nuc, const double *Z, const double *R, double soft_en,
+                  double soft_ee, int n_elec, double *E_nn_out) {
+  CHECK_CTX(ctx);
+  if (ctx->stage < 1) return fail(ctx, FEDVR_ERR_STATE, "set_potential before build_fedvr");
+  if (n_nuc < 0 || n_nuc > 256 || (n_nuc > 0 && (!Z || !R)))
+    return fail(ctx, FEDVR_ERR_ARG, "need 0 <= n_nuc <= 256 and Z, R arrays");
+  if (!(soft_en > 0.0) || !(soft_ee > 0.0) || !is_fin(soft_en) || !is_fin(soft_ee))
+    return fail(ctx, FEDVR_ERR_ARG, "soft-Coulomb parameters must be > 0");
+  if (n_elec < 2 || (n_elec & 1) || n_elec / 2 >= ctx->n)
+    return fail(ctx, FEDVR_ERR_ARG, "need even n_elec >= 2 with n_elec/2 < n_b");
+  for (int A = 0; A < n_nuc; ++A)
+    if (!is_fin(Z[A]) || !is_fin(R[A])) return fail(ctx, FEDVR_ERR_ARG, "non-finite nucleus");
+  int n = ctx->n;
+  ctx->stage = 1;
+  ctx->n_elec = n_elec;
+  ctx->nocc = n_elec / 2;
+  ctx->soft_en = soft_en;
+  ctx->soft_ee = soft_ee;
+  ENSURE(ctx, b_v, dsz(n));
+  ENSURE(ctx, b_V, dsz((size_t)n * n));
+  ENSURE(ctx, b_h, dsz((size_t)n * n));
+  ENSURE(ctx, b_hf_tmp, dsz((size_t)n * n > 512 ? (size_t)n * n : 512));
+  double *dZ = P<double>(ctx->b_hf_tmp), *dR = dZ + 256;
+  if (n_nuc > 0) {
+    FEDVR_CK(ctx, cudaMemcpyAsync(dZ, Z, dsz(n_nuc), cudaMemcpyHostToDevice, ctx->stream));
+    FEDVR_CK(ctx, cudaMemcpyAsync(dR, R, dsz(n_nuc), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  FEDVR_CK(ctx, launch_potential(n, P<double>(ctx->b_nodes), n_nuc, dZ, dR, soft_en, soft_ee,
+                                 P<double>(ctx->b_T), P<double>(ctx->b_v), P<double>(ctx->b_V),
+                                 P<double>(ctx->b_h), ctx->stream));
+  if (int r = sync(ctx)) return r;  // host Z/R copies complete before returning
+  double enn = 0.0;
+  for (int A = 0; A < n_nuc; ++A)
+    for (int B = A + 1; B < n_nuc; ++B) {
+      double d = fabs(R[A] - R[B]);
+      if (d > 0.0) enn += Z[A] * Z[B] / d;
+    }
+  if (E_nn_out) *E_nn_out = enn;
+  ctx->stage = 2;
+  return FEDVR_OK;
+}
+
+int fedvr_get_basis(const fedvr_ctx *cctx, double *nodes, double *weights, int *elem, int *local) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  CHECK_CTX(ctx);
+  if (ctx->stage < 1) return fail(ctx, FEDVR_ERR_STATE, "no basis");
+  int n = ctx->n;
+  if (nodes) { if (int r = copy_out(ctx, nodes, ctx->b_nodes.ptr, dsz(n), false)) return r; }
+  if (weights) { if (int r = copy_out(ctx, weights, ctx->b_weights.ptr, dsz(n), false)) return r; }
+  if (elem) { if (int r = copy_out(ctx, elem, ctx->b_elem.ptr, n * sizeof(int), false)) return r; }
+  if (local) { if (int r = copy_out(ctx, local, ctx->b_local.ptr, n * sizeof(int), false)) return r; }
+  return sync(ctx);
+}
+
+int fedvr_get_gll(const fedvr_ctx *cctx, double *xi, double *omega) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  CHECK_CTX(ctx);
+  if (ctx->stage < 1) return fail(ctx, FEDVR_ERR_STATE, "no basis");
+  if (xi) { if (int r = copy_out(ctx, xi, ctx->b_xi.ptr, dsz(ctx->order + 1), false)) return r; }
+  if (omega) { if (int r = copy_out(ctx, omega, ctx->b_om.ptr, dsz(ctx->order + 1), false)) return r; }
+  return sync(ctx);
+}
+
+int fedvr_get_operators(const fedvr_ctx *cctx, double *T, double *v, double *V, double *h) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  CHECK_CTX(ctx);
+  if (ctx->stage < 1) return fail(ctx, FEDVR_ERR_STATE, "no basis");
+  if ((v || V || h) && ctx->stage < 2) return fail(ctx, FEDVR_ERR_STATE, "no potential");
+  size_t nn = (size_t)ctx->n * ctx->n;
+  if (T) { if (int r = copy_out(ctx, T, ctx->b_T.ptr, dsz(nn), false)) return r; }
+  if (v) { if (int r = copy_out(ctx, v, ctx->b_v.ptr, dsz(ctx->n), false)) return r; }
+  if (V) { if (int r = copy_out(ctx, V, ctx->b_V.ptr, dsz(nn), false)) return r; }
+  if (h) { if (int r = copy_out(ctx, h, ctx->b_h.ptr, dsz(nn), false)) return r; }
+  return sync(ctx);
+}
+
+int solve_hf(fedvr_ctx *ctx, double beta, double tol, int max_iter, double *E_hf, double *mu) {
+  CHECK_CTX(ctx);
+  if (ctx->stage < 2) return fail(ctx, FEDVR_ERR_STATE, "solve_hf before set_potential");
+  if (!(beta > 0.0) || !is_fin(beta)) return fail(ctx, FEDVR_ERR_ARG, "beta must be > 0");
+  if (!(tol > 0.0) || max_iter < 1) return fail(ctx, FEDVR_ERR_ARG, "need tol > 0, max_iter >= 1");
+  const int n = ctx->n, nocc = ctx->nocc;
+  const size_t nn = (size_t)n * n;
+  const double spin = ctx->spin;
+  cudaStream_t s = ctx->stream;
+  ctx->stage = 2;
+  ENSURE(ctx, b_eps, dsz(n));
+  ENSURE(ctx, b_C, dsz(nn));
+  ENSURE(ctx, b_rho, dsz(nn));
+  ENSURE(ctx, b_rho_new, dsz(nn));
+  ENSURE(ctx, b_rho_mix, dsz(nn));
+  ENSURE(ctx, b_F, dsz(nn));
+  ENSURE(ctx, b_Sigma0, dsz(nn));
+  ENSURE(ctx, b_f, dsz(n));
+  ENSURE(ctx, b_A, dsz(nn));
+  ENSURE(ctx, b_A2, dsz(nn));
+  ENSURE(ctx, b_J, dsz(4 * (n / 2 + 2)));
+  ENSURE(ctx, b_hf_tmp, dsz(nn > 512 ? nn : 512));
+  double *eps = P<double>(ctx->b_eps), *C = P<double>(ctx->b_C), *rho = P<double>(ctx->b_rho);
+  double *rho_new = P<double>(ctx->b_rho_new), *rho_mix = P<double>(ctx->b_rho_mix);
+  double *F = P<double>(ctx->b_F), *A = P<double>(ctx->b_A), *f = P<double>(ctx->b_f);
+  double *scal = P<double>(ctx->b_scal);
+  double *mu_dev = scal + 4;
+  const double *h = P<double>(ctx->b_h), *V = P<double>(ctx->b_V);
+
+  // start: projector on the nocc lowest eigenvectors of h
+  FEDVR_CK(ctx, launch_copy(nn, h, A, s));
+  if (int r = eig(ctx, A, nullptr, eps, C)) return r;
+  FEDVR_CK(ctx, dgemm(false, true, n, n, nocc, 1.0, C, n, 0, C, n, 0, nullptr, 0, 0.0, rho, n, 0, 1, s));
+  int it = 0;
+  bool conv = false;
+  for (it = 1; it <= max_iter; ++it) {
+    FEDVR_CK(ctx, launch_hf_selfenergy(n, spin, rho, V, h, nullptr, F, s));
+    // A = C^T F C in the previous eigenbasis, Jacobi from there (warm start)
+    double *t = rho_mix;
+    FEDVR_CK(ctx, dgemm(false, false, n, n, n, 1.0, F, n, 0, C, n, 0, nullptr, 0, 0.0, t, n, 0, 1, s));
+    FEDVR_CK(ctx, dgemm(true, false, n, n, n, 1.0, C, n, 0, t, n, 0, nullptr, 0, 0.0, A, n, 0, 1, s));
+    FEDVR_CK(ctx, launch_copy(nn, C, rho_new, s));  // starting basis (rho_new is free here)
+    if (int r = eig(ctx, A, rho_new, eps, C)) return r;
+    FEDVR_CK(ctx, launch_mu_fermi(n, nocc, beta, eps, mu_dev, f, s));
+    FEDVR_CK(ctx, dgemm(false, true, n, n, n, 1.0, C, n, 0, C, n, 0, f, 0, 0.0, rho_new, n, 0, 1, s));
+    unsigned long long *bits = reinterpret_cast<unsigned long long *>(scal + 5);
+    FEDVR_CK(ctx, cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s));
+    FEDVR_CK(ctx, launch_max_abs_diff(nn, rho_new, rho, bits, s));
+    double r_host;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&r_host, scal + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (int r = sync(ctx)) return r;
+    if (r_host != r_host) return fail(ctx, FEDVR_ERR_NAN, "NaN in the HF density");
+    if (r_host < tol) { conv = true; break; }
+    FEDVR_CK(ctx, launch_axpby(nn, 0.5, rho, 0.5, rho_new, rho_mix, s));
+    double *tmp = P<double>(ctx->b_rho);
+    ctx->b_rho.ptr = ctx->b_rho_mix.ptr;
+    ctx->b_rho_mix.ptr = tmp;
+    rho = P<double>(ctx->b_rho);
+    rho_mix = P<double>(ctx->b_rho_mix);
+  }
+  if (!conv) return fail(ctx, FEDVR_ERR_NOCONV, "HF not converged after %d iterations", max_iter);
+  // Sigma0 = F - h; E_hf on rho0 = C f C^T
+  FEDVR_CK(ctx, launch_axpby(nn, 1.0, F, -1.0, h, P<double>(ctx->b_Sigma0), s));
+  FEDVR_CK(ctx, launch_energy_hf(n, spin, h, V, rho_new, scal + 6, s));
+  double out[3];
+  FEDVR_CK(ctx, cudaMemcpyAsync(out, scal + 4, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (int r = sync(ctx)) return r;
+  ctx->mu = out[0];
+  ctx->E_hf = out[2];
+  ctx->beta_hf = beta;
+  ctx->hf_iters = it;
+  ctx->stage = 3;
+  if (E_hf) *E_hf = ctx->E_hf;
+  if (mu) *mu = ctx->mu;
+  return FEDVR_OK;
+}
+
+int fedvr_get_hf(const fedvr_ctx *cctx, double *eps, double *C, double *rho0, double *Sigma0) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  CHECK_CTX(ctx);
+  if (ctx->stage < 3) return fail(ctx, FEDVR_ERR_STATE, "no HF solution");
+  size_t nn = (size_t)ctx->n * ctx->n;
+  if (eps) { if (int r = copy_out(ctx, eps, ctx->b_eps.ptr, dsz(ctx->n), false)) return r; }
+  if (C) { if (int r = copy_out(ctx, C, ctx->b_C.ptr, dsz(nn), false)) return r; }
+  if (rho0) { if (int r = copy_out(ctx, rho0, ctx->b_rho_new.ptr, dsz(nn), false)) return r; }
+  if (Sigma0) { if (int r = copy_out(ctx, Sigma0, ctx->b_Sigma0.ptr, dsz(nn), false)) return r; }
+  return sync(ctx);
+}
+
+int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_device) {
+  CHECK_CTX(ctx);
+  if (ctx->stage < 1) return fail(ctx, FEDVR_ERR_STATE, "no basis");
+  if (!Sigma0) { ctx->sigma_init_M = 0; return FEDVR_OK; }
+  if (M < 3 || M > 4097) return fail(ctx, FEDVR_ERR_ARG, "M outside [3, 4097]");
+  size_t cnt = (size_t)M * ctx->n * ctx->n;
+  ENSURE(ctx, b_sigma_init, dsz(cnt));
+  FEDVR_CK(ctx, cudaMemcpyAsync(ctx->b_sigma_init.ptr, Sigma0, dsz(cnt),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                ctx->stream));
+  if (int r = sync(ctx)) return r;
+  ctx->sigma_init_M = M;
+  return FEDVR_OK;
+}
+
+int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
+  CHECK_CTX(ctx);
+  if (ctx->stage < 3) return fail(ctx, FEDVR_ERR_STATE, "second Born before solve_hf");
+  if (int r = check_mesh_args(ctx, beta, u, p)) return r;
+  if (beta != ctx->beta_hf)
+    return fail(ctx, FEDVR_ERR_ARG, "beta differs from the HF solution's beta");
+  if (precision != FEDVR_FP64)
+    return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+  const int n = ctx->n, M = 2 * u * p + 1;
+  if (ctx->sigma_init_M && ctx->sigma_init_M != M)
+    return fail(ctx, FEDVR_ERR_ARG, "initial Sigma has M = %d, mesh has %d", ctx->sigma_init_M, M);
+  ctx->prepared = false;
+  const size_t nn = (size_t)n * n, stack = (size_t)M * nn;
+  cudaStream_t s = ctx->stream;
+  ENSURE(ctx, w_K, dsz((size_t)n * M * M));
+  ENSURE(ctx, w_phi, dsz((size_t)M * n));
+  ENSURE(ctx, w_G0, dsz(stack));
+  ENSURE(ctx, w_G, dsz(stack));
+  ENSURE(ctx, w_S, dsz(stack));
+  ENSURE(ctx, w_I1, dsz(stack));
+  ENSURE(ctx, w_I2, dsz(stack));
+  ENSURE(ctx, w_t1, dsz(stack));
+  ENSURE(ctx, w_t2, dsz(stack));
+  ENSURE(ctx, w_t3, dsz(stack));
+  ENSURE(ctx, w_dHF, dsz(nn));
+  ENSURE(ctx, w_part, dsz(M));
+  ENSURE(ctx, w_red, dsz(8));
+  if (int r = build_mesh(ctx, beta, u, p, true)) return r;
+  double *tau = P<double>(ctx->w_tau), *w = P<double>(ctx->w_w);
+  const double *eps = P<double>(ctx->b_eps), *C = P<double>(ctx->b_C);
+  // g^0 on the mesh (Eq. hfgf) and the conv2 eigen-kernel, fixed for the run
+  FEDVR_CK(ctx, launch_phi_table(n, M, beta, eps, nullptr, ctx->mu, tau, P<double>(ctx->w_phi), s));
+  FEDVR_CK(ctx, dgemm(false, true, n, n, n, 1.0, C, n, 0, C, n, 0, P<double>(ctx->w_phi), n, 0.0,
+                      P<double>(ctx->w_G0), n, nn, M, s));
+  FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, tau, w, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
+                                    eps, nullptr, ctx->mu, P<double>(ctx->w_K), s));
+  FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->w_G0), P<double>(ctx->w_G), s));
+  if (int r = sync(ctx)) return r;
+  ctx->history.clear();
+  ctx->beta = beta;
+  ctx->u = u;
+  ctx->p = p;
+  ctx->M = M;
+  ctx->precision = precision;
+  ctx->step_k = 0;
+  ctx->prepared = true;
+  return FEDVR_OK;
+}
+
+int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_device,
+                  double *res_out, double *E0, double *N_out) {
+  CHECK_CTX(ctx);
+  if (!ctx->prepared) return fail(ctx, FEDVR_ERR_STATE, "fedvr_2b_step before fedvr_2b_prepare");
+  if (!(mixing > 0.0 && mixing <= 1.0)) return fail(ctx, FEDVR_ERR_ARG, "need 0 < mixing <= 1");
+  const int n = ctx->n, M = ctx->M;
+  const size_t nn = (size_t)n * n, stack = (size_t)M * nn;
+  const double spin = ctx->spin;
+  cudaStream_t s = ctx->stream;
+  double *G0 = P<double>(ctx->w_G0), *G = P<double>(ctx->w_G), *S = P<double>(ctx->w_S);
+  double *I1 = P<double>(ctx->w_I1), *I2 = P<double>(ctx->w_I2);
+  double *t1 = P<double>(ctx->w_t1), *t2 = P<double>(ctx->w_t2), *t3 = P<double>(ctx->w_t3);
+  double *red = P<double>(ctx->w_red);
+  const double *C = P<double>(ctx->b_C), *h = P<double>(ctx->b_h), *V = P<double>(ctx->b_V);
+  auto t0 = std::chrono::steady_clock::now();
+  int launches = 0;
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[0], s));
+  if (G_in)
+    FEDVR_CK(ctx, cudaMemcpyAsync(G, G_in, dsz(stack),
+                                  in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[1], s));
+  if (ctx->step_k == 0 && ctx->sigma_init_M) {
+    FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->b_sigma_init), S, s));
+    launches += 1;
+  } else {
+    FEDVR_CK(ctx, sigma2_fp64(n, M, spin, V, G, S, t1, t2, t3, s));
+    launches += 4;
+  }
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[2], s));
+  FEDVR_CK(ctx, launch_hf_selfenergy(n, spin, G + (size_t)(M - 1) * nn, V, nullptr,
+                                     P<double>(ctx->b_Sigma0), P<double>(ctx->w_dHF), s));
+  FEDVR_CK(ctx, launch_energy(n, M, spin, h, V, G, S, P<double>(ctx->w_w), P<double>(ctx->w_part),
+                              red, s));
+  launches += 3;
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[3], s));
+  FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF), S, G, I1, s));
+  launches += 1;
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[4], s));
+  FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, t1, t2, s));
+  launches += 5;
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[5], s));
+  FEDVR_CK(ctx, cudaMemsetAsync(red + 2, 0, sizeof(double), s));
+  FEDVR_CK(ctx, launch_update(n, M, mixing, G0, I2, G,
+                              reinterpret_cast<unsigned long long *>(red + 2), s));
+  launches += 1;
+  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[6], s));
+  ctx->step_launches = launches;
+  double hr[3];
+  FEDVR_CK(ctx, cudaMemcpyAsync(hr, red, sizeof(hr), cudaMemcpyDeviceToHost, s));
+  if (int r = sync(ctx)) return r;
+  double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  double rec[5] = {(double)ctx->step_k, hr[2], hr[0], hr[1], ms};
+  ctx->history.insert(ctx->history.end(), rec, rec + 5);
+  ctx->step_k++;
+  if (res_out) *res_out = hr[2];
+  if (E0) *E0 = hr[0];
+  if (N_out) *N_out = hr[1];
+  if (hr[2] != hr[2] || !is_fin(hr[0]))
+    return fail(ctx, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", ctx->step_k - 1);
+  return FEDVR_OK;
+}
+
+int fedvr_2b_read(fedvr_ctx *ctx, int out_on_device, double *G_out, double *Sigma_out,
+                  double *tau_out) {
+  CHECK_CTX(ctx);
+  if (!ctx->prepared) return fail(ctx, FEDVR_ERR_STATE, "no prepared second-Born run");
+  size_t stack = (size_t)ctx->M * ctx->n * ctx->n;
+  bool dev = out_on_device != 0;
+  if (G_out) { if (int r = copy_out(ctx, G_out, ctx->w_G.ptr, dsz(stack), dev)) return r; }
+  if (Sigma_out) { if (int r = copy_out(ctx, Sigma_out, ctx->w_S.ptr, dsz(stack), dev)) return r; }
+  if (tau_out) { if (int r = copy_out(ctx, tau_out, ctx->w_tau.ptr, dsz(ctx->M), dev)) return r; }
+  return sync(ctx);
+}
+
+int solve_2b(fedvr_ctx *ctx, double beta, int u, int p, double mixing, double tol, int max_iter,
+             int precision, int out_on_device, double *G_out, double *Sigma_out, double *tau_out,
+             double *E0, double *N_out, int *iters) {
+  CHECK_CTX(ctx);
+  if (!(mixing > 0.0 && mixing <= 1.0)) return fail(ctx, FEDVR_ERR_ARG, "need 0 < mixing <= 1");
+  if (!(tol > 0.0) || max_iter < 1) return fail(ctx, FEDVR_ERR_ARG, "need tol > 0, max_iter >= 1");
+  if (int r = fedvr_2b_prepare(ctx, beta, u, p, precision)) return r;
+  double E = 0, Nel = 0, res = INFINITY, best = INFINITY;
+  int grow = 0, k = 0, status = FEDVR_OK;
+  bool conv = false;
+  for (k = 0; k < max_iter; ++k) {
+    int r = fedvr_2b_step(ctx, mixing, nullptr, 0, &res, &E, &Nel);
+    if (r == FEDVR_ERR_NAN) { status = r; break; }
+    if (r) return r;
+    if (res < tol) { conv = true; break; }
+    if (res < best) { best = res; grow = 0; } else if (++grow >= 8) {
+      status = fail(ctx, FEDVR_ERR_DIVERGED, "residual grew for 8 iterations (at %d)", k);
+      break;
+    }
+  }
+  int done = (k < max_iter) ? k + 1 : max_iter;
+  if (status == FEDVR_OK && !conv)
+    status = fail(ctx, FEDVR_ERR_NOCONV, "not converged after %d iterations (res %.3e)", max_iter, res);
+  if (int r = fedvr_2b_read(ctx, out_on_device, G_out, Sigma_out, tau_out)) return r;
+  ctx->sigma_init_M = 0;
+  if (E0) *E0 = E;
+  if (N_out) *N_out = Nel;
+  if (iters) *iters = done;
+  return status;
+}
+
+int fedvr_stage_times(const fedvr_ctx *cctx, double *ms, int *launches) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  CHECK_CTX(ctx);
+  if (!ms) return fail(ctx, FEDVR_ERR_ARG, "ms must not be NULL");
+  if (!ctx->prepared || ctx->step_k == 0) return fail(ctx, FEDVR_ERR_STATE, "no step has run");
+  float t;
+  for (int i = 0; i < 5; ++i) {
+    FEDVR_CK(ctx, cudaEventElapsedTime(&t, ctx->ev[i + 1], ctx->ev[i + 2]));
+    ms[i] = t;
+  }
+  FEDVR_CK(ctx, cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[6]));
+  ms[5] = t;
+  if (launches) *launches = ctx->step_launches;
+  return FEDVR_OK;
+}
+
+int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len) {
+  if (!ctx || (cap > 0 && !buf)) return FEDVR_ERR_ARG;
+  int count = (int)(ctx->history.size() / 5);
+  int m = count < cap ? count : cap;
+  if (m > 0) memcpy(buf, ctx->history.data(), sizeof(double) * 5 * m);
+  if (len) *len = count;
+  return FEDVR_OK;
+}
+
+int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u, const int *p,
+                     double mixing, double tol, int max_iter, int precision, double *E0,
+                     double *N_out, int *iters) {
+  if (!ctxs || n_sys < 1 || !beta || !u || !p) return FEDVR_ERR_ARG;
+  if (ctxs[0]) fail(ctxs[0], FEDVR_ERR_ARG, "batched solve is not available in this build");
+  return FEDVR_ERR_ARG;
+}
+
+int fedvr_power_mesh(fedvr_ctx *ctx, double beta, int u, int p, double *tau, double *w,
+                     double *wm, double *wp, int *lag_k, double *lag_t) {
+  CHECK_CTX(ctx);
+  if (int r = check_mesh_args(ctx, beta, u, p)) return r;
+  if ((lag_k == nullptr) != (lag_t == nullptr))
+    return fail(ctx, FEDVR_ERR_ARG, "lag_k and lag_t go together");
+  if (int r = build_mesh(ctx, beta, u, p, false)) return r;
+  int M = 2 * u * p + 1;
+  cudaStream_t s = ctx->stream;
+  if (lag_k)
+    FEDVR_CK(ctx, launch_mesh(beta, u, p, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                              P<double>(ctx->w_wm), P<double>(ctx->w_wp), lag_k, lag_t, s));
+  if (tau) FEDVR_CK(ctx, cudaMemcpyAsync(tau, ctx->w_tau.ptr, dsz(M), cudaMemcpyDeviceToDevice, s));
+  if (w) FEDVR_CK(ctx, cudaMemcpyAsync(w, ctx->w_w.ptr, dsz(M), cudaMemcpyDeviceToDevice, s));
+  if (wm) FEDVR_CK(ctx, cudaMemcpyAsync(wm, ctx->w_wm.ptr, dsz(M), cudaMemcpyDeviceToDevice, s));
+  if (wp) FEDVR_CK(ctx, cudaMemcpyAsync(wp, ctx->w_wp.ptr, dsz(M), cudaMemcpyDeviceToDevice, s));
+  return FEDVR_OK;
+}
+
+int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, const double *G,
+                 double *Sigma, int precision) {
+  CHECK_CTX(ctx);
+  if (n < 1 || n > 1024 || M < 1 || M > 4097 || !V || !G || !Sigma)
+    return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, 1 <= M <= 4097 and device buffers");
+  if (!is_fin(spin)) return fail(ctx, FEDVR_ERR_ARG, "spin factor must be finite");
+  if (precision != FEDVR_FP64)
+    return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+  size_t stack = (size_t)M * n * n;
+  ENSURE(ctx, w_t1, dsz(stack));
+  ENSURE(ctx, w_t2, dsz(stack));
+  ENSURE(ctx, w_t3, dsz(stack));
+  FEDVR_CK(ctx, sigma2_fp64(n, M, spin, V, G, Sigma, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
+                            P<double>(ctx->w_t3), ctx->stream));
+  return FEDVR_OK;
+}
+
+int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *dHF,
+                       const double *Sigma, const double *G, double *I1, int precision) {
+  CHECK_CTX(ctx);
+  if (int r = check_mesh_args(ctx, beta, u, p)) return r;
+  if (n < 1 || n > 1024 || !dHF || !Sigma || !G || !I1)
+    return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024 and device buffers");
+  if (precision != FEDVR_FP64)
+    return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+  if (int r = build_mesh(ctx, beta, u, p, true)) return r;
+  int M = 2 * u * p + 1;
+  FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), dHF, Sigma, G, I1, ctx->stream));
+  return FEDVR_OK;
+}
+
+int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *eps,
+                  const double *C, double mu, const double *I1, double *I2) {
+  CHECK_CTX(ctx);
+  if (int r = check_mesh_args(ctx, beta, u, p)) return r;
+  if (n < 1 || n > 1024 || !eps || !C || !I1 || !I2 || !is_fin(mu))
+    return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, finite mu and device buffers");
+  if (int r = build_mesh(ctx, beta, u, p, false)) return r;
+  int M = 2 * u * p + 1;
+  size_t stack = (size_t)M * n * n;
+  ENSURE(ctx, w_K, dsz((size_t)n * M * M));
+  ENSURE(ctx, w_t1, dsz(stack));
+  ENSURE(ctx, w_t2, dsz(stack));
+  cudaStream_t s = ctx->stream;
+  FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                                    P<double>(ctx->w_wm), P<double>(ctx->w_wp), eps, nullptr, mu,
+                                    P<double>(ctx->w_K), s));
+  FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, P<double>(ctx->w_t1),
+                            P<double>(ctx->w_t2), s));
+  return FEDVR_OK;
+}
+
+}  // extern "C"

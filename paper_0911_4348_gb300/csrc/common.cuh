@@ -1,0 +1,157 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fedvr_negf.h"
+
+namespace fedvr {
+
+// Device buffer that only grows; freed with the context.
+struct DevBuf {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace fedvr
+
+struct fedvr_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  char err[640] = {0};
+  bool failed = false;  // sticky after a CUDA error
+  int stage = 0;        // 0 none, 1 basis, 2 potential, 3 hf
+
+  // basis (Sec. 2.1)
+  int n_elem = 0, order = 0, n = 0, grid_kind = 0;
+  double xmin = 0, xmax = 0;
+  // potential (Sec. 2.2)
+  int n_elec = 0, nocc = 0;
+  double soft_en = 1.0, soft_ee = 1.0, spin = 2.0;
+  // HF (Sec. 2.3)
+  double beta_hf = 0, mu = 0, E_hf = 0;
+  int hf_iters = 0;
+  // warm start
+  int sigma_init_M = 0;
+  // prepared second-Born run
+  bool prepared = false;
+  int u = 0, p = 0, M = 0, precision = 0, step_k = 0;
+  double beta = 0;
+  // stage timing of the last step
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int step_launches = 0;
+  // history of the last solve_2b: iter, res, E0, N, ms
+  std::vector<double> history;
+
+  // named device buffers
+  fedvr::DevBuf b_xi, b_om, b_edges, b_nodes, b_weights, b_elem, b_local, b_tt;
+  fedvr::DevBuf b_T, b_v, b_V, b_h;
+  fedvr::DevBuf b_eps, b_C, b_rho, b_rho_new, b_rho_mix, b_F, b_Sigma0, b_f, b_A, b_A2,
+      b_J, b_scal, b_hf_tmp;
+  fedvr::DevBuf b_sigma_init;
+  // solve_2b / stage workspace
+  fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
+      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc;
+};
+
+namespace fedvr {
+
+int fail(fedvr_ctx *ctx, int code, const char *fmt, ...);
+int cuda_fail(fedvr_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
+// Ensure buf holds at least `bytes`; returns false (and records the error) on failure.
+bool ensure(fedvr_ctx *ctx, DevBuf &buf, size_t bytes, const char *name);
+void release(DevBuf &buf);
+
+template <typename T>
+inline T *P(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
+template <typename T>
+inline const T *CP(const DevBuf &b) { return reinterpret_cast<const T *>(b.ptr); }
+
+// ---- kernels launched across translation units (all enqueue on `s`) ----
+
+// basis.cu (bit-exact IEEE setup; compiled without FMA contraction)
+cudaError_t launch_gll(int order, double *xi, double *om, int *status, cudaStream_t s);
+cudaError_t launch_basis(int n_elem, int order, double xmin, double xmax, int grid_kind,
+                         const double *xi, const double *om, double *edges, double *nodes,
+                         double *weights, int *elem, int *local, double *tt, double *T,
+                         int *status, cudaStream_t s);
+cudaError_t launch_potential(int n, const double *nodes, int n_nuc, const double *Z,
+                             const double *R, double soft_en, double soft_ee, const double *T,
+                             double *v, double *V, double *h, cudaStream_t s);
+cudaError_t launch_mesh(double beta, int u, int p, double *tau, double *w, double *wm,
+                        double *wp, int *lag_k, double *lag_t, cudaStream_t s);
+// conv1 coefficients: per (i,j) the bracket k and c1 = s w_j (1-t), c2 = s w_j t
+struct ConvCoef {
+  int k;
+  int diag;
+  double c1, c2;
+};
+cudaError_t launch_conv_coef(int M, double beta, const double *tau, const double *w,
+                             const double *wm, const double *wp, ConvCoef *coef, cudaStream_t s);
+
+// linalg.cu
+// C[b] = alpha * op(A[b]) diag(sk[b]) op(B[b]) + beta * C[b]  (row-major, FP64)
+cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
+                  long lda, long sA, const double *B, long ldb, long sB, const double *sk,
+                  long sS, double beta, double *C, long ldc, long sC, int batch, cudaStream_t s);
+// Symmetric eigen-decomposition by cyclic-by-rounds Jacobi on the device.
+// A (n x n, overwritten), V (n x n, in: starting basis or identity, out:
+// eigenvectors as columns, unsorted), scratch A2 (n x n), J (rotation scratch,
+// >= 2*(n+1) doubles), scal (>= 4 doubles). Returns sweeps used or <0.
+int jacobi_eig(int n, double *A, double *A2, double *V, double *J, double *scal, double tol,
+               int max_sweeps, cudaStream_t s, cudaError_t *err);
+// Sort eigenpairs ascending: eps_out[r] = diag(A)[idx], C_out[:, r] = V[:, idx].
+cudaError_t launch_sort_eig(int n, const double *A, const double *V, double *eps_out,
+                            double *C_out, cudaStream_t s);
+cudaError_t launch_identity(int n, double *I, cudaStream_t s);
+cudaError_t launch_copy(size_t count, const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_max_abs_diff(size_t count, const double *a, const double *b,
+                                unsigned long long *out, cudaStream_t s);
+
+// hf.cu
+cudaError_t launch_hf_selfenergy(int n, double spin, const double *rho, const double *V,
+                                 const double *add, const double *sub, double *out,
+                                 cudaStream_t s);
+cudaError_t launch_mu_fermi(int n, int nocc, double beta, const double *eps, double *mu_out,
+                            double *f, cudaStream_t s);
+cudaError_t launch_phi_table(int n, int M, double beta, const double *eps, const double *mu_dev,
+                             double mu_host, const double *tau, double *phi, cudaStream_t s);
+
+// sigma2.cu (FP64 path)
+cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double *G,
+                        double *Sigma, double *Q, double *T1, double *W, cudaStream_t s);
+
+// conv.cu
+cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
+                       const double *G, double *I1, cudaStream_t s);
+cudaError_t launch_conv2_kernel(int n, int M, double beta, const double *tau, const double *w,
+                                const double *wm, const double *wp, const double *eps,
+                                const double *mu_dev, double mu_host, double *K, cudaStream_t s);
+cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const double *I1,
+                        double *I2, double *t1, double *t2, cudaStream_t s);
+
+// update.cu
+cudaError_t launch_update(int n, int M, double mixing, const double *G0, const double *I2,
+                          double *G, unsigned long long *res_bits, cudaStream_t s);
+cudaError_t launch_axpby(size_t count, double a, const double *x, double b, const double *y,
+                         double *out, cudaStream_t s);
+cudaError_t launch_energy_hf(int n, double spin, const double *h, const double *V,
+                             const double *rho, double *out, cudaStream_t s);
+cudaError_t launch_energy(int n, int M, double spin, const double *h, const double *V,
+                          const double *G, const double *A, const double *w, double *part,
+                          double *out, cudaStream_t s);
+
+}  // namespace fedvr
+
+#define FEDVR_CK(ctx, call)                                                   \
+  do {                                                                        \
+    cudaError_t e__ = (call);                                                 \
+    if (e__ != cudaSuccess)                                                   \
+      return fedvr::cuda_fail((ctx), e__, #call, __FILE__, __LINE__);         \
+  } while (0)

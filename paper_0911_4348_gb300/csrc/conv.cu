@@ -1,0 +1,155 @@
+// The two tau-convolutions of the Matsubara Dyson equation (Sec. 2.3, Eq. deq)
+// on the power mesh, FP64 path.
+//
+// I1_i = sum_j B_ij g_j with B_ij = c1 A_k + c2 A_{k+1} (linear interpolation of
+// Sigma^corr at the lag tau_i - tau_j, anti-periodic beyond 0, trapezoid weight
+// folded into c1, c2) and B_ii = dHF - wm_i A_0 + wp_i A_{M-1} (split trapezoid
+// at the jump). One block owns a 64x64 tile of one I1_i and streams over j.
+//
+// I2 is evaluated in the HF eigenbasis, where g^0 is diagonal:
+// I2~_i,ab = sum_j K_a(i,j) I1~_j,ab with K_a(i,j) the exact g^0 eigen-factor at
+// the lag times the same split-trapezoid weights, I1~ = C^T I1 C, I2 = C I2~ C^T.
+#include "common.cuh"
+
+#include <math.h>
+
+namespace fedvr {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M,
+                                                         const ConvCoef *__restrict__ coef,
+                                                         const double *__restrict__ dHF,
+                                                         const double *__restrict__ A,
+                                                         const double *__restrict__ G,
+                                                         double *__restrict__ I1) {
+  const int i = blockIdx.z;
+  const int a0 = blockIdx.y * BM, b0 = blockIdx.x * BN;
+  const long nn = (long)n * n;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+  for (int j = 0; j < M; ++j) {
+    const ConvCoef cf = coef[(long)i * M + j];
+    const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
+    const double *A1 = A + (long)k1 * nn, *A2 = A + (long)k2 * nn;
+    const double *g = G + (long)j * nn;
+    for (int c0 = 0; c0 < n; c0 += BK) {
+      for (int e = threadIdx.x; e < BM * BK; e += 256) {
+        int cc = e % BK, aa = e / BK;
+        int a = a0 + aa, c = c0 + cc;
+        double v = 0.0;
+        if (a < n && c < n) {
+          long off = (long)a * n + c;
+          v = cf.c1 * A1[off] + cf.c2 * A2[off];
+          if (cf.diag) v += dHF[off];
+        }
+        As[cc][aa] = v;
+      }
+      for (int e = threadIdx.x; e < BN * BK; e += 256) {
+        int bb = e % BN, cc = e / BN;
+        int b = b0 + bb, c = c0 + cc;
+        Bs[cc][bb] = (b < n && c < n) ? g[(long)c * n + b] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int cc = 0; cc < BK; ++cc) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[r] = As[cc][ty + 16 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bv[q] = Bs[cc][tx + 16 * q];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int a = a0 + ty + 16 * r;
+    if (a >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int b = b0 + tx + 16 * q;
+      if (b < n) I1[(long)i * nn + (long)a * n + b] = acc[r][q];
+    }
+  }
+}
+
+__device__ __forceinline__ double phi_eig(double x, double y, double beta) {
+  return (y >= 0.0) ? exp(-((beta + x) * y)) / (1.0 + exp(-(beta * y)))
+                    : exp(-(x * y)) / (1.0 + exp(beta * y));
+}
+
+// K[a][i][j]: j != i: sign * w_j * phi_a(y) with y the lag of tau_i - tau_j in
+// [-beta, 0]; j == i: wm_i * (-phi_a(-beta)) + wp_i * phi_a(0).
+__global__ void conv2_kernel_table(int n, int M, double beta, const double *__restrict__ tau,
+                                   const double *__restrict__ w, const double *__restrict__ wm,
+                                   const double *__restrict__ wp, const double *__restrict__ eps,
+                                   const double *mu_dev, double mu_host, double *__restrict__ K) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long MM = (long)M * M;
+  if (idx >= (long)n * MM) return;
+  int a = (int)(idx / MM);
+  long r = idx % MM;
+  int i = (int)(r / M), j = (int)(r % M);
+  double mu = mu_dev ? *mu_dev : mu_host;
+  double y = eps[a] - mu;
+  double v;
+  if (i == j) {
+    v = wm[i] * (-phi_eig(-beta, y, beta)) + wp[i] * phi_eig(0.0, y, beta);
+  } else {
+    double x = tau[i] - tau[j];
+    double sg = 1.0;
+    if (j < i) { x = x - beta; sg = -1.0; }
+    v = sg * w[j] * phi_eig(x, y, beta);
+  }
+  K[idx] = v;
+}
+
+}  // namespace
+
+cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
+                       const double *G, double *I1, cudaStream_t s) {
+  dim3 grid((n + BN - 1) / BN, (n + BM - 1) / BM, M);
+  conv1_fp64_kernel<<<grid, 256, 0, s>>>(n, M, coef, dHF, A, G, I1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv2_kernel(int n, int M, double beta, const double *tau, const double *w,
+                                const double *wm, const double *wp, const double *eps,
+                                const double *mu_dev, double mu_host, double *K, cudaStream_t s) {
+  long cnt = (long)n * M * M;
+  conv2_kernel_table<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(n, M, beta, tau, w, wm, wp, eps,
+                                                                  mu_dev, mu_host, K);
+  return cudaGetLastError();
+}
+
+cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const double *I1,
+                        double *I2, double *t1, double *t2, cudaStream_t s) {
+  long nn = (long)n * n, MM = (long)M * M;
+  cudaError_t e;
+  // t1_j = C^T I1_j ; t2_j = t1_j C   (eigenbasis)
+  e = dgemm(true, false, n, n, n, 1.0, C, n, 0, I1, n, nn, nullptr, 0, 0.0, t1, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  e = dgemm(false, false, n, n, n, 1.0, t1, n, nn, C, n, 0, nullptr, 0, 0.0, t2, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  // t1[i][a][:] = sum_j K_a[i][j] t2[j][a][:]   (batched over a)
+  e = dgemm(false, false, M, n, M, 1.0, K, M, MM, t2, nn, n, nullptr, 0, 0.0, t1, nn, n, n, s);
+  if (e != cudaSuccess) return e;
+  // I2_i = C t1_i C^T
+  e = dgemm(false, false, n, n, n, 1.0, C, n, 0, t1, n, nn, nullptr, 0, 0.0, t2, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  return dgemm(false, true, n, n, n, 1.0, t2, n, nn, C, n, 0, nullptr, 0, 0.0, I2, n, nn, M, s);
+}
+
+}  // namespace fedvr
