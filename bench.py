@@ -256,6 +256,7 @@ def main():
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     for _ in range(args.steps):
         ctx.step_2b(sys_.mixing)
@@ -264,6 +265,7 @@ def main():
         for k, v in st.items():
             stage_ms.setdefault(k, []).append(v)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1)

@@ -219,6 +219,32 @@ int fedvr_power_mesh(fedvr_ctx *ctx, double beta, int u, int p, double *tau, dou
 int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V,
                  const double *G, double *Sigma, int precision);
 
+/* Allocation-free Sigma^(2) build. The paper has no counterpart: this is a
+ * service for callers that cannot let the library allocate device memory --
+ * processes whose device memory belongs to another allocator (a framework's
+ * caching allocator that reserves the pool), or loops that cannot accept the
+ * device synchronisation cudaMalloc/cudaFree imply. It computes exactly what
+ * fedvr_sigma2 computes with precision FEDVR_FP64 (same kernels), needs no
+ * context, and calls no cudaMalloc, cudaFree or allocating library routine:
+ * its workspace is a fixed 12 MiB device array inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *  - Limit: M * n * n <= 524288 (2^19), 1 <= n <= 1024, 1 <= M <= 4097;
+ *    larger sizes return FEDVR_ERR_ARG.
+ *  - V [n][n], G [M][n][n] (symmetric) and Sigma [M][n][n] are caller-owned
+ *    device buffers on the current device; work is enqueued on cuda_stream
+ *    (a cudaStream_t, NULL = legacy default stream) without synchronising.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress, with that device current); make that first
+ *    call before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind; nothing in
+ *    it needs to start at zero (every workspace element is written before it
+ *    is read). Calls that overlap on the GPU (concurrent streams or threads)
+ *    race on the array and give wrong results; serialise them.
+ *  - Errors: FEDVR_ERR_ARG for invalid arguments or sizes beyond the limit,
+ *    FEDVR_ERR_CUDA if the address lookup or a launch fails. */
+int fedvr_sigma2_noalloc(int n, int M, double spin, const double *V, const double *G,
+                         double *Sigma, void *cuda_stream);
+
 /* First Dyson convolution (Eq. deq): I1_i = dHF g_i + int Sigma(tau_i - t) g(t) dt
  * on the power mesh (beta, u, p), split trapezoid at t = tau_i with
  * Sigma(0^+) = -Sigma_0, Sigma(0^-) = Sigma_{M-1}; Sigma at off-mesh lags by

@@ -245,4 +245,18 @@ class Context:
                                             _dev(I2, (M, n, n))))
 
 
-__all__ = ["Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]
+def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
+    """Allocation-free FP64 Sigma^(2) build (``fedvr_sigma2_noalloc``) for callers
+    that cannot let the library allocate device memory. Limit M*n*n <= 2^19;
+    concurrent calls race on the library's one workspace array."""
+    M, n = G.shape[0], G.shape[1]
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    code = _native.lib().fedvr_sigma2_noalloc(n, M, spin, _dev(V, (n, n)), _dev(G, (M, n, n)),
+                                              _dev(Sigma, (M, n, n)), C.c_void_p(stream))
+    if code != 0:
+        raise FedvrError(code, "fedvr_sigma2_noalloc failed")
+
+
+__all__ = ["sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]

@@ -40,6 +40,7 @@ SIGNATURES = {
     "fedvr_power_mesh": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
                                    _vp]),
     "fedvr_sigma2": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int]),
+    "fedvr_sigma2_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, _vp]),
     "fedvr_conv_sigma_g": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp,
                                      _vp, C.c_int]),
     "fedvr_conv_g0": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, _vp, _vp, C.c_double,

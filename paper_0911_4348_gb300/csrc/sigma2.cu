@@ -9,6 +9,8 @@
 // rows a >= b are formed and the result is mirrored.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace fedvr {
 namespace {
 
@@ -128,3 +130,65 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
 }
 
 }  // namespace fedvr
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP64 Sigma^(2) build.
+//
+// Some callers cannot let a library call cudaMalloc: processes whose device
+// memory is owned entirely by another allocator (a framework's caching
+// allocator that reserves the pool up front), or loops where the implicit
+// device synchronisation of cudaMalloc/cudaFree is not acceptable. For them
+// this entry point runs the same kernels as fedvr_sigma2 with its workspace
+// (the polarisation Q, the product Q V and V Q V) in a fixed device array
+// declared below, so it allocates nothing. The array is a static device
+// symbol: every GPU that loads this library holds it until the process
+// exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocStack = size_t(1) << 19;  // max M * n * n per workspace matrix stack
+static __device__ __align__(256) double g_sigma2_scratch[3 * kNoAllocStack];  // 12 MiB
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (the host-side name of a __device__ array is not a device address).
+cudaError_t scratch_on_current_device(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_sigma2_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = static_cast<double *>(ptr);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int fedvr_sigma2_noalloc(int n, int M, double spin, const double *V, const double *G,
+                                    double *Sigma, void *cuda_stream) {
+  if (n < 1 || n > 1024 || M < 1 || M > 4097 || !V || !G || !Sigma || !isfinite(spin))
+    return FEDVR_ERR_ARG;
+  if ((size_t)M * (size_t)n * (size_t)n > kNoAllocStack) return FEDVR_ERR_ARG;
+  double *scratch = nullptr;
+  if (scratch_on_current_device(&scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return FEDVR_ERR_CUDA;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = fedvr::sigma2_fp64(n, M, spin, V, G, Sigma, scratch, scratch + kNoAllocStack,
+                                     scratch + 2 * kNoAllocStack, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FEDVR_ERR_CUDA;
+  }
+  return FEDVR_OK;
+}
