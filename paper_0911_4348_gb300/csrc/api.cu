@@ -136,6 +136,30 @@ int eig(fedvr_ctx *ctx, double *A, const double *Vinit, double *eps, double *C) 
   return FEDVR_OK;
 }
 
+// Workspace of the tensor-core Sigma^(2) build: split operands, QV, V32, an
+// FP32 copy of Sigma (for the tensor-core convolution) and the error flag.
+int tc_workspace(fedvr_ctx *ctx, int n, int M, float **ws, float **S32, int **err) {
+  const size_t ld = (size_t)(n + 31) / 32 * 32;
+  const size_t stack = (size_t)M * n * ld;
+  const size_t floats = 5 * stack + (size_t)n * ld + 64;
+  ENSURE(ctx, w_tc, floats * sizeof(float));
+  float *base = P<float>(ctx->w_tc);
+  *ws = base;
+  *S32 = base + 4 * stack + (size_t)n * ld;
+  *err = reinterpret_cast<int *>(base + 5 * stack + (size_t)n * ld);
+  return FEDVR_OK;
+}
+
+int check_precision(fedvr_ctx *ctx, int precision, int n) {
+  if (precision == FEDVR_FP64) return FEDVR_OK;
+  if (precision == FEDVR_SPLIT_TF32) {
+    if (n > sigma2_tc_max_n())
+      return fail(ctx, FEDVR_ERR_ARG, "split-TF32 path supports n_b <= %d", sigma2_tc_max_n());
+    return FEDVR_OK;
+  }
+  return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+}
+
 }  // namespace
 
 extern "C" {
@@ -147,6 +171,12 @@ int fedvr_create(fedvr_ctx **out, void *cuda_stream) {
   if (!ctx) return FEDVR_ERR_ARG;
   ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return FEDVR_ERR_CUDA;
+  }
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+      cudaSuccess) {
     cudaGetLastError();
     delete ctx;
     return FEDVR_ERR_CUDA;
@@ -413,8 +443,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   if (int r = check_mesh_args(ctx, beta, u, p)) return r;
   if (beta != ctx->beta_hf)
     return fail(ctx, FEDVR_ERR_ARG, "beta differs from the HF solution's beta");
-  if (precision != FEDVR_FP64)
-    return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+  if (int r = check_precision(ctx, precision, ctx->n)) return r;
   const int n = ctx->n, M = 2 * u * p + 1;
   if (ctx->sigma_init_M && ctx->sigma_init_M != M)
     return fail(ctx, FEDVR_ERR_ARG, "initial Sigma has M = %d, mesh has %d", ctx->sigma_init_M, M);
@@ -434,6 +463,12 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ENSURE(ctx, w_dHF, dsz(nn));
   ENSURE(ctx, w_part, dsz(M));
   ENSURE(ctx, w_red, dsz(8));
+  if (precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+  }
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
   double *tau = P<double>(ctx->w_tau), *w = P<double>(ctx->w_w);
   const double *eps = P<double>(ctx->b_eps), *C = P<double>(ctx->b_C);
@@ -480,6 +515,12 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   if (ctx->step_k == 0 && ctx->sigma_init_M) {
     FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->b_sigma_init), S, s));
     launches += 1;
+  } else if (ctx->precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    FEDVR_CK(ctx, sigma2_tc(n, M, spin, V, G, S, S32, ws, err, ctx->num_sms, s));
+    launches += 5;
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, spin, V, G, S, t1, t2, t3, s));
     launches += 4;
@@ -504,8 +545,16 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[6], s));
   ctx->step_launches = launches;
   double hr[3];
+  int tc_err = 0;
   FEDVR_CK(ctx, cudaMemcpyAsync(hr, red, sizeof(hr), cudaMemcpyDeviceToHost, s));
+  if (ctx->precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
   if (int r = sync(ctx)) return r;
+  if (tc_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
   double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   double rec[5] = {(double)ctx->step_k, hr[2], hr[0], hr[1], ms};
   ctx->history.insert(ctx->history.end(), rec, rec + 5);
@@ -619,8 +668,19 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
   if (n < 1 || n > 1024 || M < 1 || M > 4097 || !V || !G || !Sigma)
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, 1 <= M <= 4097 and device buffers");
   if (!is_fin(spin)) return fail(ctx, FEDVR_ERR_ARG, "spin factor must be finite");
-  if (precision != FEDVR_FP64)
-    return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+  if (int r = check_precision(ctx, precision, n)) return r;
+  if (precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    FEDVR_CK(ctx, sigma2_tc(n, M, spin, V, G, Sigma, nullptr, ws, err, ctx->num_sms, ctx->stream));
+    int h_err = 0;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (int r = sync(ctx)) return r;
+    if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+    return FEDVR_OK;
+  }
   size_t stack = (size_t)M * n * n;
   ENSURE(ctx, w_t1, dsz(stack));
   ENSURE(ctx, w_t2, dsz(stack));

@@ -46,6 +46,7 @@ struct fedvr_ctx {
   // stage timing of the last step
   cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int step_launches = 0;
+  int num_sms = 0;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
 
@@ -126,6 +127,15 @@ cudaError_t launch_phi_table(int n, int M, double beta, const double *eps, const
 // sigma2.cu (FP64 path)
 cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double *G,
                         double *Sigma, double *Q, double *T1, double *W, cudaStream_t s);
+
+// sigma2_tc.cu (tensor cores, split TF32). ws holds 4 * M*n*ld + n*ld floats
+// (ld = n rounded up to 32); S32 (may be NULL) receives Sigma in FP32 with row
+// pitch ld; *err is set to 1 if a bounded device-side wait gave up.
+size_t sigma2_tc_smem_bytes(int n);
+int sigma2_tc_max_n();
+cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *G,
+                      double *Sigma, float *S32, float *ws, int *err, int num_sms,
+                      cudaStream_t s);
 
 // conv.cu
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,

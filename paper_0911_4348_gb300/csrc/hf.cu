@@ -68,12 +68,10 @@ __device__ double lse_group(const double *eps, int lo, int hi, double mu, double
 __global__ void mu_fermi_kernel(int n, int nocc, double beta, const double *eps, double *mu_out,
                                 double *f) {
   __shared__ double sh[32];
-  __shared__ double s_lo, s_hi, s_mid;
-  __shared__ int s_done;
+  __shared__ double s_lo, s_hi;
   if (threadIdx.x == 0) {
     s_lo = eps[0] - 1.0;
     s_hi = eps[n - 1] + 1.0;
-    s_done = 0;
   }
   __syncthreads();
   for (int it = 0; it < 400; ++it) {

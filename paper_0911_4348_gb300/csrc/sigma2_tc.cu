@@ -1,0 +1,322 @@
+// Second-Born self-energy on the tensor cores (Sec. 2.3, Eq. sigma2ndb in
+// two-index form), split-TF32 precision:
+//
+//   Sigma_ab = sum_k V_ak [ sigma g_ab (Q V)_kb - g_kb P^(b)_ak ],
+//   P^(b) = g diag(V_b,:) gb,  Q = g o gb,  g = G[j], gb = G[M-1-j].
+//
+// The first bracket term is the direct term sigma g o (V Q V), the second the
+// second-order exchange X. P^(b) is the only O(n^3)-per-column contraction
+// (O(n^4) per mesh point): it runs as tcgen05.mma kind::tf32 with 128 rows a
+// per tile, all k in one or two N tiles and the contraction over l in
+// 32-wide chunks, each operand split as x = hi + lo (TF32) and the product
+// taken as hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM. The A operand
+// g_al V_bl is formed by the CUDA cores while the previous chunk multiplies;
+// the epilogue reads P from TMEM and folds the k-sum in FP32. Only rows a >= b
+// are formed; the symmetric result is mirrored.
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace fedvr {
+namespace {
+
+constexpr int kThreads = 384;                 // 12 warps produce; warps 0-3 also drain TMEM
+constexpr uint64_t kWaitNs = 2000000000ull;   // bound on every mbarrier wait (2 s)
+constexpr uint32_t kTileA = 128 * 128;        // bytes of one 128-row x 32-col fp32 operand half
+
+// g32 = (float)g; gh, gl = TF32 split of g (hi = tf32(g), lo = tf32(g - hi));
+// rows padded to ld floats with zeros.
+__global__ void split_kernel(int n, long rows, int ld, const double *__restrict__ G,
+                             float *__restrict__ g32, float *__restrict__ gh,
+                             float *__restrict__ gl) {
+  const long total = rows * ld;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long row = idx / ld;
+    const int c = (int)(idx % ld);
+    float a = 0.f, h = 0.f, l = 0.f;
+    if (c < n) {
+      const double x = G[row * n + c];
+      a = (float)x;
+      h = tc::tf32_rna(a);
+      l = tc::tf32_rna((float)(x - (double)h));
+    }
+    if (g32) g32[idx] = a;
+    if (gh) gh[idx] = h;
+    if (gl) gl[idx] = l;
+  }
+}
+
+// QV[j] = (g32[j] o g32[M-1-j]) V32 in FP32, padded rows of ld (64x64 tiles).
+__global__ void __launch_bounds__(256) qv_kernel(int n, int M, int ld,
+                                                 const float *__restrict__ g32,
+                                                 const float *__restrict__ V32,
+                                                 float *__restrict__ QV) {
+  const int j = blockIdx.z;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const float *g = g32 + (long)j * n * ld, *gb = g32 + (long)(M - 1 - j) * n * ld;
+  __shared__ float As[16][65], Bs[16][65];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int kk = e % 16, rr = e / 16, r = r0 + rr, k = k0 + kk;
+      As[kk][rr] = (r < n && k < n) ? g[(long)r * ld + k] * gb[(long)r * ld + k] : 0.f;
+      int cc = e % 64, k2 = e / 64, c = c0 + cc, kq = k0 + k2;
+      Bs[k2][cc] = (c < n && kq < n) ? V32[(long)kq * ld + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], b[q], acc[i][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = r0 + ty + 16 * i;
+    if (r >= n) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int c = c0 + tx + 16 * q;
+      if (c < ld) QV[((long)j * n + r) * ld + c] = (c < n) ? acc[i][q] : 0.f;
+    }
+  }
+}
+
+struct XParams {
+  int n, M, ld, MT, NT, Np, KC;
+  int n0[2], nsz[2];
+  float spin;
+  const float *g32, *gh, *gl, *V32, *QV;
+  double *Sigma;
+  float *S32;
+  int *err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) exchange_tc_kernel(const XParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  const int n = P.n, ld = P.ld;
+  const uint32_t tileB = (uint32_t)P.Np * 128;
+  const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);  // free[2], full, drain
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  float *gcol = reinterpret_cast<float *>(tmem_slot + 4);
+  float *qcol = gcol + ld;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tc::mbar_init(&bars[i], 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  uint32_t cc = 0, tiles = 0;
+  bool issued = false;
+  const long items = (long)P.M * n;
+  for (long w = blockIdx.x; w < items; w += gridDim.x) {
+    const int j = (int)(w / n), b = (int)(w % n);
+    const float *gA = P.g32 + (long)j * n * ld;
+    const float *ghB = P.gh + (long)(P.M - 1 - j) * n * ld;
+    const float *glB = P.gl + (long)(P.M - 1 - j) * n * ld;
+    const float *Vb = P.V32 + (long)b * ld;
+    for (int k = tid; k < n; k += kThreads) {
+      gcol[k] = gA[(long)k * ld + b];
+      qcol[k] = P.QV[((long)j * n + k) * ld + b];
+    }
+    for (int mt = b >> 7; mt < P.MT; ++mt) {
+      for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+        const int s = cc & 1;
+        const uint32_t use = cc >> 1;
+        if (use > 0 && !tc::mbar_wait(&bars[s], (use - 1) & 1, kWaitNs)) *abort_flag = 1;
+        __syncthreads();
+        if (*abort_flag) goto finish;
+        uint8_t *st = smem + s * stage_bytes;
+        const int l0 = kc * 32;
+        for (int u = tid; u < 128 * 8; u += kThreads) {
+          const int r = u >> 3, c = u & 7, a = mt * 128 + r;
+          float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+          if (a < n) {
+            const float4 gv = *reinterpret_cast<const float4 *>(gA + (long)a * ld + l0 + 4 * c);
+            const float4 vv = *reinterpret_cast<const float4 *>(Vb + l0 + 4 * c);
+            const float x0 = gv.x * vv.x, x1 = gv.y * vv.y, x2 = gv.z * vv.z, x3 = gv.w * vv.w;
+            hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2), tc::tf32_rna(x3));
+            lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
+                             tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
+          }
+          const uint32_t off = tc::sw128_offset(r, c);
+          *reinterpret_cast<float4 *>(st + off) = hi;
+          *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+        }
+        for (int u = tid; u < P.Np * 8; u += kThreads) {
+          const int r = u >> 3, c = u & 7;
+          float4 hv = make_float4(0.f, 0.f, 0.f, 0.f), lv = hv;
+          if (r < n) {
+            hv = *reinterpret_cast<const float4 *>(ghB + (long)r * ld + l0 + 4 * c);
+            lv = *reinterpret_cast<const float4 *>(glB + (long)r * ld + l0 + 4 * c);
+          }
+          const uint32_t off = tc::sw128_offset(r, c);
+          *reinterpret_cast<float4 *>(st + 2 * kTileA + off) = hv;
+          *reinterpret_cast<float4 *>(st + 2 * kTileA + tileB + off) = lv;
+        }
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(st);
+          const int ksteps = min(4, (n - l0 + 7) / 8);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+            const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+            for (int nt = 0; nt < P.NT; ++nt) {
+              const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
+              const uint64_t bh = tc::sdesc_k128(sa + boff);
+              const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+              const uint32_t d = tmem + (uint32_t)P.n0[nt];
+              const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
+              tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_tf32(d, ah, bl, idesc, 1u);
+              tc::mma_tf32(d, al, bh, idesc, 1u);
+            }
+          }
+          tc::mma_commit(&bars[s]);
+          if (kc == P.KC - 1) tc::mma_commit(&bars[2]);
+          issued = true;
+        }
+      }
+      if (!tc::mbar_wait(&bars[2], tiles & 1, kWaitNs)) *abort_flag = 1;
+      ++tiles;
+      __syncthreads();
+      if (*abort_flag) goto finish;
+      tc::fence_after_sync();
+      if (warp < 4) {
+        const int a = mt * 128 + warp * 32 + lane;
+        const bool live = a < n;
+        const float gab = live ? gA[(long)a * ld + b] : 0.f;
+        const float sg = P.spin * gab;
+        float acc = 0.f;
+        for (int c0 = 0; c0 < n; c0 += 16) {
+          float pv[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, pv);
+          if (live) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int k = c0 + i;
+              if (k < n) acc = fmaf(P.V32[(long)k * ld + a], sg * qcol[k] - gcol[k] * pv[i], acc);
+            }
+          }
+        }
+        if (live && a >= b) {
+          const long nn = (long)n * n;
+          P.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
+          P.Sigma[(long)j * nn + (long)b * n + a] = (double)acc;
+          if (P.S32) {
+            P.S32[((long)j * n + a) * ld + b] = acc;
+            P.S32[((long)j * n + b) * ld + a] = acc;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+  }
+finish:
+  __syncthreads();
+  if (*abort_flag) {
+    // let any MMAs still in flight finish (bounded) before the TMEM goes away
+    if (tid == 0) {
+      if (issued) tc::mma_commit(&bars[3]);
+      atomicExch(P.err, 1);
+    }
+    if (issued) tc::mbar_wait(&bars[3], 0, kWaitNs);
+    __syncthreads();
+  }
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+size_t sigma2_tc_smem_bytes(int n) {
+  const int Np = (n + 15) / 16 * 16;
+  const int ld = (n + 31) / 32 * 32;
+  return 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np * 128) + 64 + 2 * (size_t)ld * 4;
+}
+
+int sigma2_tc_max_n() {
+  int n = 16;
+  while (sigma2_tc_smem_bytes(n + 16) <= 232448 && n + 16 <= 512) n += 16;
+  return n;
+}
+
+cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *G,
+                      double *Sigma, float *S32, float *ws, int *err, int num_sms,
+                      cudaStream_t s) {
+  const int ld = (n + 31) / 32 * 32;
+  const long stack = (long)M * n * ld;
+  float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *QV = ws + 3 * stack;
+  float *V32 = ws + 4 * stack;
+  split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, gh, gl);
+  split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
+  dim3 gq((ld + 63) / 64, (n + 63) / 64, M);
+  qv_kernel<<<gq, 256, 0, s>>>(n, M, ld, g32, V32, QV);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  XParams P{};
+  P.n = n;
+  P.M = M;
+  P.ld = ld;
+  P.MT = (n + 127) / 128;
+  P.Np = (n + 15) / 16 * 16;
+  P.KC = (n + 31) / 32;
+  if (P.Np <= 256) {
+    P.NT = 1;
+    P.n0[0] = 0;
+    P.nsz[0] = P.Np;
+    P.n0[1] = P.nsz[1] = 0;
+  } else {
+    P.NT = 2;
+    const int half = ((P.Np / 2) + 15) / 16 * 16;
+    P.n0[0] = 0;
+    P.nsz[0] = half;
+    P.n0[1] = half;
+    P.nsz[1] = P.Np - half;
+  }
+  P.spin = (float)spin;
+  P.g32 = g32;
+  P.gh = gh;
+  P.gl = gl;
+  P.V32 = V32;
+  P.QV = QV;
+  P.Sigma = Sigma;
+  P.S32 = S32;
+  P.err = err;
+  const size_t smem = sigma2_tc_smem_bytes(n);
+  e = cudaFuncSetAttribute(exchange_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  long items = (long)M * n;
+  int grid = (int)(items < num_sms ? items : num_sms);
+  exchange_tc_kernel<<<grid, kThreads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace fedvr
