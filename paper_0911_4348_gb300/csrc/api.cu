@@ -512,7 +512,8 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
     FEDVR_CK(ctx, cudaMemcpyAsync(G, G_in, dsz(stack),
                                   in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[1], s));
-  if (ctx->step_k == 0 && ctx->sigma_init_M) {
+  const bool warm = ctx->step_k == 0 && ctx->sigma_init_M;
+  if (warm) {
     FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->b_sigma_init), S, s));
     launches += 1;
   } else if (ctx->precision == FEDVR_SPLIT_TF32) {
@@ -532,7 +533,21 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
                               red, s));
   launches += 3;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[3], s));
-  FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF), S, G, I1, s));
+  if (ctx->precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
+    if (warm) {  // the Sigma build was skipped: split g and convert Sigma here
+      FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
+      FEDVR_CK(ctx, launch_sigma_to_f32(n, M, S, S32, s));
+      launches += 2;
+    }
+    FEDVR_CK(ctx, conv1_tc(n, M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF), S32,
+                           ws + tstack, ws + 2 * tstack, I1, err, ctx->num_sms, s));
+  } else {
+    FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF), S, G, I1, s));
+  }
   launches += 1;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[4], s));
   FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, t1, t2, s));
@@ -696,10 +711,26 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
   if (int r = check_mesh_args(ctx, beta, u, p)) return r;
   if (n < 1 || n > 1024 || !dHF || !Sigma || !G || !I1)
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024 and device buffers");
-  if (precision != FEDVR_FP64)
-    return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+  if (int r = check_precision(ctx, precision, n)) return r;
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
   int M = 2 * u * p + 1;
+  if (precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
+    cudaStream_t s = ctx->stream;
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
+    FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s));
+    FEDVR_CK(ctx, conv1_tc(n, M, P<ConvCoef>(ctx->w_coef), dHF, S32, ws + tstack, ws + 2 * tstack,
+                           I1, err, ctx->num_sms, s));
+    int h_err = 0;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (int r = sync(ctx)) return r;
+    if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+    return FEDVR_OK;
+  }
   FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), dHF, Sigma, G, I1, ctx->stream));
   return FEDVR_OK;
 }

@@ -137,6 +137,17 @@ cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *
                       double *Sigma, float *S32, float *ws, int *err, int num_sms,
                       cudaStream_t s);
 
+// g32 = (float)G, gh/gl = TF32 hi/lo of G, rows padded to ld = n rounded up to 32.
+cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh, float *gl,
+                           cudaStream_t s);
+
+// conv_tc.cu (tensor cores, split TF32): S32 = Sigma in FP32 (pitch ld); gh/gl
+// are the split copies of G from launch_split_g / sigma2_tc.
+cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s);
+cudaError_t conv1_tc(int n, int M, const ConvCoef *coef, const double *dHF, const float *S32,
+                     const float *gh, const float *gl, double *I1, int *err, int num_sms,
+                     cudaStream_t s);
+
 // conv.cu
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
                        const double *G, double *I1, cudaStream_t s);

@@ -1,0 +1,254 @@
+// First Dyson convolution on the tensor cores (Sec. 2.3, Eq. deq), split TF32:
+//
+//   I1_i = sum_j B_ij g_j,  B_ij = c1 Sigma_k + c2 Sigma_{k+1}   (j != i)
+//                           B_ii = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1}
+//
+// with the lag bracket k and the trapezoid/interpolation weights c1, c2 of the
+// FP64 path (FP64 tables, applied here in FP32). One tile = one output mesh
+// point i and 128 rows a; all columns b sit in one or two N tiles. The
+// contraction runs over (j, c) in 32-wide chunks: the A operand B_ij(a, c) is
+// formed by the CUDA cores and split as hi + lo (TF32); B = g_j(b, c) comes
+// from the split copy of g. Products hi*hi + hi*lo + lo*hi accumulate in FP32 in
+// TMEM over a block of mesh points (about 4096 contraction terms) and each block
+// is then added into the FP64 result, so rounding does not grow with M.
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace fedvr {
+namespace {
+
+constexpr int kThreads = 384;
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint32_t kTileA = 128 * 128;
+
+struct C1Params {
+  int n, M, ld, MT, NT, Np, KC, JB;
+  int n0[2], nsz[2];
+  const float *S32, *gh, *gl;
+  const double *dHF;
+  const ConvCoef *coef;
+  double *I1;
+  int *err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) conv1_tc_kernel(const C1Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  const int n = P.n, ld = P.ld, M = P.M;
+  const uint32_t tileB = (uint32_t)P.Np * 128;
+  const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);  // free[2], full, drain
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long nld = (long)n * ld;
+
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) tc::mbar_init(&bars[q], 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  uint32_t cc = 0, blocks = 0;
+  bool issued = false;
+  const long items = (long)M * P.MT;
+  for (long w = blockIdx.x; w < items; w += gridDim.x) {
+    const int i = (int)(w / P.MT), mt = (int)(w % P.MT);
+    for (int j0 = 0; j0 < M; j0 += P.JB) {
+      const int j1 = min(M, j0 + P.JB);
+      for (int j = j0; j < j1; ++j) {
+        const ConvCoef cf = P.coef[(long)i * M + j];
+        const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
+        const float c1 = (float)cf.c1, c2 = (float)cf.c2;
+        const bool diag = cf.diag != 0;
+        const float *S1 = P.S32 + (long)k1 * nld, *S2 = P.S32 + (long)k2 * nld;
+        const float *ghB = P.gh + (long)j * nld, *glB = P.gl + (long)j * nld;
+        for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+          const int s = cc & 1;
+          const uint32_t use = cc >> 1;
+          if (use > 0 && !tc::mbar_wait(&bars[s], (use - 1) & 1, kWaitNs)) *abort_flag = 1;
+          __syncthreads();
+          if (*abort_flag) goto finish;
+          uint8_t *st = smem + s * stage_bytes;
+          const int l0 = kc * 32;
+          for (int u = tid; u < 128 * 8; u += kThreads) {
+            const int r = u >> 3, c = u & 7, a = mt * 128 + r;
+            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            if (a < n) {
+              const float4 s1 = *reinterpret_cast<const float4 *>(S1 + (long)a * ld + l0 + 4 * c);
+              const float4 s2 = *reinterpret_cast<const float4 *>(S2 + (long)a * ld + l0 + 4 * c);
+              x[0] = fmaf(c1, s1.x, c2 * s2.x);
+              x[1] = fmaf(c1, s1.y, c2 * s2.y);
+              x[2] = fmaf(c1, s1.z, c2 * s2.z);
+              x[3] = fmaf(c1, s1.w, c2 * s2.w);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int l = l0 + 4 * c + q;
+                if (l >= n) x[q] = 0.f;
+                else if (diag) x[q] += (float)P.dHF[(long)a * n + l];
+              }
+            }
+            float4 hi, lo;
+            hi.x = tc::tf32_rna(x[0]);
+            hi.y = tc::tf32_rna(x[1]);
+            hi.z = tc::tf32_rna(x[2]);
+            hi.w = tc::tf32_rna(x[3]);
+            lo.x = tc::tf32_rna(x[0] - hi.x);
+            lo.y = tc::tf32_rna(x[1] - hi.y);
+            lo.z = tc::tf32_rna(x[2] - hi.z);
+            lo.w = tc::tf32_rna(x[3] - hi.w);
+            const uint32_t off = tc::sw128_offset(r, c);
+            *reinterpret_cast<float4 *>(st + off) = hi;
+            *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+          }
+          for (int u = tid; u < P.Np * 8; u += kThreads) {
+            const int r = u >> 3, c = u & 7;
+            float4 hv = make_float4(0.f, 0.f, 0.f, 0.f), lv = hv;
+            if (r < n) {
+              hv = *reinterpret_cast<const float4 *>(ghB + (long)r * ld + l0 + 4 * c);
+              lv = *reinterpret_cast<const float4 *>(glB + (long)r * ld + l0 + 4 * c);
+            }
+            const uint32_t off = tc::sw128_offset(r, c);
+            *reinterpret_cast<float4 *>(st + 2 * kTileA + off) = hv;
+            *reinterpret_cast<float4 *>(st + 2 * kTileA + tileB + off) = lv;
+          }
+          tc::fence_smem_to_async();
+          __syncthreads();
+          if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(st);
+            const int ksteps = min(4, (n - l0 + 7) / 8);
+            const bool fresh = (j == j0 && kc == 0);
+            for (int kk = 0; kk < ksteps; ++kk) {
+              const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+              const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+              for (int nt = 0; nt < P.NT; ++nt) {
+                const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
+                const uint64_t bh = tc::sdesc_k128(sa + boff);
+                const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+                const uint32_t d = tmem + (uint32_t)P.n0[nt];
+                const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
+                tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
+                tc::mma_tf32(d, ah, bl, idesc, 1u);
+                tc::mma_tf32(d, al, bh, idesc, 1u);
+              }
+            }
+            tc::mma_commit(&bars[s]);
+            if (j == j1 - 1 && kc == P.KC - 1) tc::mma_commit(&bars[2]);
+            issued = true;
+          }
+        }
+      }
+      // add this block of mesh points into the FP64 result
+      if (!tc::mbar_wait(&bars[2], blocks & 1, kWaitNs)) *abort_flag = 1;
+      ++blocks;
+      __syncthreads();
+      if (*abort_flag) goto finish;
+      tc::fence_after_sync();
+      {
+        const int wq = warp & 3, grp = warp >> 2;  // 3 warpgroups share the columns
+        const int a = mt * 128 + wq * 32 + lane;
+        const bool live = a < n;
+        double *row = P.I1 + ((long)i * n + (live ? a : 0)) * n;
+        int q = 0;
+        for (int c0 = 0; c0 < n; c0 += 16, ++q) {
+          if (q % 3 != grp) continue;
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
+          if (live) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const int b = c0 + t;
+              if (b < n) row[b] = (j0 == 0) ? (double)v[t] : row[b] + (double)v[t];
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+  }
+finish:
+  __syncthreads();
+  if (*abort_flag) {
+    if (tid == 0) {
+      if (issued) tc::mma_commit(&bars[3]);
+      atomicExch(P.err, 1);
+    }
+    if (issued) tc::mbar_wait(&bars[3], 0, kWaitNs);
+    __syncthreads();
+  }
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// S32 = (float)Sigma with rows padded to ld (zeros beyond n).
+__global__ void sigma_to_f32_kernel(int n, long rows, int ld, const double *__restrict__ S,
+                                    float *__restrict__ S32) {
+  const long total = rows * ld;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long row = idx / ld;
+    const int c = (int)(idx % ld);
+    S32[idx] = (c < n) ? (float)S[row * n + c] : 0.f;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s) {
+  const int ld = (n + 31) / 32 * 32;
+  sigma_to_f32_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, S, S32);
+  return cudaGetLastError();
+}
+
+cudaError_t conv1_tc(int n, int M, const ConvCoef *coef, const double *dHF, const float *S32,
+                     const float *gh, const float *gl, double *I1, int *err, int num_sms,
+                     cudaStream_t s) {
+  C1Params P{};
+  P.n = n;
+  P.M = M;
+  P.ld = (n + 31) / 32 * 32;
+  P.MT = (n + 127) / 128;
+  P.Np = (n + 15) / 16 * 16;
+  P.KC = (n + 31) / 32;
+  P.JB = 4096 / n > 1 ? 4096 / n : 1;
+  if (P.Np <= 256) {
+    P.NT = 1;
+    P.n0[0] = 0;
+    P.nsz[0] = P.Np;
+  } else {
+    P.NT = 2;
+    const int half = ((P.Np / 2) + 15) / 16 * 16;
+    P.n0[0] = 0;
+    P.nsz[0] = half;
+    P.n0[1] = half;
+    P.nsz[1] = P.Np - half;
+  }
+  P.S32 = S32;
+  P.gh = gh;
+  P.gl = gl;
+  P.dHF = dHF;
+  P.coef = coef;
+  P.I1 = I1;
+  P.err = err;
+  const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)P.Np * 128) + 64;
+  cudaError_t e = cudaFuncSetAttribute(conv1_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long items = (long)M * P.MT;
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace fedvr

@@ -255,6 +255,13 @@ finish:
 
 }  // namespace
 
+cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh, float *gl,
+                           cudaStream_t s) {
+  const int ld = (n + 31) / 32 * 32;
+  split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, gh, gl);
+  return cudaGetLastError();
+}
+
 size_t sigma2_tc_smem_bytes(int n) {
   const int Np = (n + 15) / 16 * 16;
   const int ld = (n + 31) / 32 * 32;

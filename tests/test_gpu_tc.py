@@ -80,3 +80,55 @@ def test_solve_2b_tf32_he_small_energy(ctx):
     out = ctx.solve_2b(s.beta, s.u, s.p, s.mixing, s.tol, 100, precision=TF32)
     assert abs(out["E0"] - res["E0"]) < E0_TOL
     assert abs(out["N"] - res["N"]) < 1e-6
+
+
+@pytest.mark.parametrize("n,u,p,beta,seed", [(8, 2, 3, 10.0, 0), (37, 2, 3, 25.0, 1),
+                                             (130, 1, 3, 100.0, 2), (257, 1, 2, 100.0, 3)])
+def test_conv1_tf32_random(ctx, n, u, p, beta, seed):
+    rng = W.system_rng(98, seed)
+    M = 2 * u * p + 1
+    A = W.random_symmetric_stack(rng, M, n)
+    G = W.random_symmetric_stack(rng, M, n)
+    dHF = W.random_symmetric(rng, n, 0.1)
+    I1 = torch.empty((M, n, n), dtype=torch.float64, device="cuda")
+    ctx.conv_sigma_g(beta, u, p, _dev(dHF), _dev(A), _dev(G), I1, precision=TF32)
+    torch.cuda.synchronize()
+    mesh = O.power_mesh(beta, u, p)
+    ref = O.conv1(dHF, A, G, mesh, beta, O.lag_table(mesh["tau"], beta))
+    assert maxrel(I1.cpu().numpy(), ref) < SIGMA_TOL
+
+
+def test_conv1_tf32_he_small_full(ctx):
+    ref = oracle_system("he_small")
+    s, hf, mesh, G0 = ref["sys"], ref["hf"], ref["mesh"], ref["G0"]
+    A = O.sigma2(G0, ref["V"], 2.0)
+    dHF = O.hf_selfenergy(G0[-1], ref["V"], 2.0) - hf["Sigma0"]
+    I1 = torch.empty(G0.shape, dtype=torch.float64, device="cuda")
+    ctx.conv_sigma_g(s.beta, s.u, s.p, _dev(dHF), _dev(A), _dev(G0), I1, precision=TF32)
+    torch.cuda.synchronize()
+    want = O.conv1(dHF, A, G0, mesh, s.beta, O.lag_table(mesh["tau"], s.beta))
+    assert maxrel(I1.cpu().numpy(), want) < SIGMA_TOL
+
+
+def test_conv1_tf32_he_medium_sampled_rows(ctx):
+    ref = oracle_system("he_medium")
+    s, mesh, G0 = ref["sys"], ref["mesh"], ref["G0"]
+    M, n = G0.shape[0], G0.shape[1]
+    A = O.sigma2(G0[[0, M // 3, M - 1]], ref["V"], 2.0)  # realistic magnitudes
+    rng = W.system_rng(99, 0)
+    Afull = (np.max(np.abs(A)) * W.random_symmetric_stack(rng, M, n))
+    dHF = W.random_symmetric(rng, n, 1e-4)
+    I1 = torch.empty(G0.shape, dtype=torch.float64, device="cuda")
+    ctx.conv_sigma_g(s.beta, s.u, s.p, _dev(dHF), _dev(Afull), _dev(G0), I1, precision=TF32)
+    torch.cuda.synchronize()
+    got = I1.cpu().numpy()
+    rows = [0, M // 2, M - 1]
+    lag = {"k": np.zeros((M, M), np.int32), "t": np.zeros((M, M)), "s": np.zeros((M, M))}
+    for i in rows:
+        for j in range(M):
+            if i != j:
+                y, sg = O.lag_point(mesh["tau"], s.beta, i, j)
+                k, t = O.bracket(mesh["tau"], y)
+                lag["k"][i, j], lag["t"][i, j], lag["s"][i, j] = k, t, sg
+    want = O.conv1(dHF, Afull, G0, mesh, s.beta, lag, rows=rows)
+    assert maxrel(got[rows], want) < SIGMA_TOL
