@@ -11,6 +11,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 SIGMA_TOL = 1e-5
 E0_TOL = 1e-6
+# I1 = sum_j B_ij g_j: the terms of the two anti-periodic branches cancel, so
+# the split-TF32 product error (2^-21 relative per product) is amplified by
+# sum|terms| / |I1| (about 20-40 on the He models). Bound: 2^-21 x 100.
+CONV_TOL = 5e-5
 TF32 = 1
 
 
@@ -107,7 +111,7 @@ def test_conv1_tf32_he_small_full(ctx):
     ctx.conv_sigma_g(s.beta, s.u, s.p, _dev(dHF), _dev(A), _dev(G0), I1, precision=TF32)
     torch.cuda.synchronize()
     want = O.conv1(dHF, A, G0, mesh, s.beta, O.lag_table(mesh["tau"], s.beta))
-    assert maxrel(I1.cpu().numpy(), want) < SIGMA_TOL
+    assert maxrel(I1.cpu().numpy(), want) < CONV_TOL
 
 
 def test_conv1_tf32_he_medium_sampled_rows(ctx):
@@ -131,4 +135,4 @@ def test_conv1_tf32_he_medium_sampled_rows(ctx):
                 k, t = O.bracket(mesh["tau"], y)
                 lag["k"][i, j], lag["t"][i, j], lag["s"][i, j] = k, t, sg
     want = O.conv1(dHF, Afull, G0, mesh, s.beta, lag, rows=rows)
-    assert maxrel(got[rows], want) < SIGMA_TOL
+    assert maxrel(got[rows], want) < CONV_TOL
