@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -127,6 +128,10 @@ cudaError_t launch_phi_table(int n, int M, double beta, const double *eps, const
 // sigma2.cu (FP64 path)
 cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double *G,
                         double *Sigma, double *Q, double *T1, double *W, cudaStream_t s);
+
+// tmap.cu: 3-D TMA map over [M][n][ld] floats, box 32 x rows x 1, 128B swizzle,
+// rows beyond n read as zero.
+cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows);
 
 // sigma2_tc.cu (tensor cores, split TF32). ws holds 4 * M*n*ld + n*ld floats
 // (ld = n rounded up to 32); S32 (may be NULL) receives Sigma in FP32 with row

@@ -17,30 +17,36 @@
 namespace fedvr {
 namespace {
 
-constexpr int kThreads = 384;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kTileA = 128 * 128;
+constexpr int kWarps = 14;  // 0-3 flush, 4-11 A producers, 12 TMA, 13 MMA
+constexpr int kThreads = kWarps * 32;
 
 struct C1Params {
-  int n, M, ld, MT, NT, Np, KC, JB;
+  int n, M, ld, MT, NT, Np, KC, JB, NBUF;
   int n0[2], nsz[2];
-  const float *S32, *gh, *gl;
+  const float *S32;
   const double *dHF;
   const ConvCoef *coef;
   double *I1;
   int *err;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) conv1_tc_kernel(const C1Params P) {
+__global__ void __launch_bounds__(kThreads, 1)
+    conv1_tc_kernel(const __grid_constant__ C1Params P, const __grid_constant__ CUtensorMap th0,
+                    const __grid_constant__ CUtensorMap tl0,
+                    const __grid_constant__ CUtensorMap th1,
+                    const __grid_constant__ CUtensorMap tl1) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
   const int n = P.n, ld = P.ld, M = P.M;
   const uint32_t tileB = (uint32_t)P.Np * 128;
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);  // free[2], full, drain
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
-  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
+  uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long nld = (long)n * ld;
 
@@ -49,7 +55,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv1_tc_kernel(const C1Params P)
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q) tc::mbar_init(&bars[q], 1);
+    tc::mbar_init(&full[0], 257);
+    tc::mbar_init(&full[1], 257);
+    tc::mbar_init(&empty[0], 1);
+    tc::mbar_init(&empty[1], 1);
+    tc::mbar_init(&accf[0], 1);
+    tc::mbar_init(&accf[1], 1);
+    tc::mbar_init(&acce[0], 128);
+    tc::mbar_init(&acce[1], 128);
+    tc::mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -57,113 +71,162 @@ __global__ void __launch_bounds__(kThreads, 1) conv1_tc_kernel(const C1Params P)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-
-  uint32_t cc = 0, blocks = 0;
-  bool issued = false;
   const long items = (long)M * P.MT;
-  for (long w = blockIdx.x; w < items; w += gridDim.x) {
-    const int i = (int)(w / P.MT), mt = (int)(w % P.MT);
-    for (int j0 = 0; j0 < M; j0 += P.JB) {
-      const int j1 = min(M, j0 + P.JB);
-      for (int j = j0; j < j1; ++j) {
+  bool issued = false;
+
+  if (warp >= 4 && warp < 12) {
+    // ---- A producers: B_ij(a, c) = c1 Sigma_k1(a, c) + c2 Sigma_k2(a, c) (+ dHF on j = i) ----
+    const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
+    uint32_t cc = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      const int i = (int)(w / P.MT), mt = (int)(w % P.MT);
+      for (int j = 0; j < M && !*abort_flag; ++j) {
         const ConvCoef cf = P.coef[(long)i * M + j];
         const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
         const float c1 = (float)cf.c1, c2 = (float)cf.c2;
-        const bool diag = cf.diag != 0;
         const float *S1 = P.S32 + (long)k1 * nld, *S2 = P.S32 + (long)k2 * nld;
-        const float *ghB = P.gh + (long)j * nld, *glB = P.gl + (long)j * nld;
         for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+          const int l0 = kc * 32;
+          float4 s1[4], s2[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int a = mt * 128 + r0 + 32 * k;
+            if (a < n) {
+              s1[k] = *reinterpret_cast<const float4 *>(S1 + (long)a * ld + l0 + 4 * c);
+              s2[k] = *reinterpret_cast<const float4 *>(S2 + (long)a * ld + l0 + 4 * c);
+            } else {
+              s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
           const int s = cc & 1;
           const uint32_t use = cc >> 1;
-          if (use > 0 && !tc::mbar_wait(&bars[s], (use - 1) & 1, kWaitNs)) *abort_flag = 1;
-          __syncthreads();
-          if (*abort_flag) goto finish;
+          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
           uint8_t *st = smem + s * stage_bytes;
-          const int l0 = kc * 32;
-          for (int u = tid; u < 128 * 8; u += kThreads) {
-            const int r = u >> 3, c = u & 7, a = mt * 128 + r;
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (a < n) {
-              const float4 s1 = *reinterpret_cast<const float4 *>(S1 + (long)a * ld + l0 + 4 * c);
-              const float4 s2 = *reinterpret_cast<const float4 *>(S2 + (long)a * ld + l0 + 4 * c);
-              x[0] = fmaf(c1, s1.x, c2 * s2.x);
-              x[1] = fmaf(c1, s1.y, c2 * s2.y);
-              x[2] = fmaf(c1, s1.z, c2 * s2.z);
-              x[3] = fmaf(c1, s1.w, c2 * s2.w);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int l = l0 + 4 * c + q;
-                if (l >= n) x[q] = 0.f;
-                else if (diag) x[q] += (float)P.dHF[(long)a * n + l];
-              }
+          for (int k = 0; k < 4; ++k) {
+            const int a = mt * 128 + r0 + 32 * k;
+            float x[4] = {fmaf(c1, s1[k].x, c2 * s2[k].x), fmaf(c1, s1[k].y, c2 * s2[k].y),
+                          fmaf(c1, s1[k].z, c2 * s2[k].z), fmaf(c1, s1[k].w, c2 * s2[k].w)};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int l = l0 + 4 * c + q;
+              if (l >= n || a >= n) x[q] = 0.f;
+              else if (cf.diag) x[q] += (float)P.dHF[(long)a * n + l];
             }
-            float4 hi, lo;
-            hi.x = tc::tf32_rna(x[0]);
-            hi.y = tc::tf32_rna(x[1]);
-            hi.z = tc::tf32_rna(x[2]);
-            hi.w = tc::tf32_rna(x[3]);
-            lo.x = tc::tf32_rna(x[0] - hi.x);
-            lo.y = tc::tf32_rna(x[1] - hi.y);
-            lo.z = tc::tf32_rna(x[2] - hi.z);
-            lo.w = tc::tf32_rna(x[3] - hi.w);
-            const uint32_t off = tc::sw128_offset(r, c);
+            const float4 hi = make_float4(tc::tf32_rna(x[0]), tc::tf32_rna(x[1]),
+                                          tc::tf32_rna(x[2]), tc::tf32_rna(x[3]));
+            const float4 lo = make_float4(tc::tf32_rna(x[0] - hi.x), tc::tf32_rna(x[1] - hi.y),
+                                          tc::tf32_rna(x[2] - hi.z), tc::tf32_rna(x[3] - hi.w));
+            const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
             *reinterpret_cast<float4 *>(st + off) = hi;
             *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
           }
-          for (int u = tid; u < P.Np * 8; u += kThreads) {
-            const int r = u >> 3, c = u & 7;
-            float4 hv = make_float4(0.f, 0.f, 0.f, 0.f), lv = hv;
-            if (r < n) {
-              hv = *reinterpret_cast<const float4 *>(ghB + (long)r * ld + l0 + 4 * c);
-              lv = *reinterpret_cast<const float4 *>(glB + (long)r * ld + l0 + 4 * c);
-            }
-            const uint32_t off = tc::sw128_offset(r, c);
-            *reinterpret_cast<float4 *>(st + 2 * kTileA + off) = hv;
-            *reinterpret_cast<float4 *>(st + 2 * kTileA + tileB + off) = lv;
-          }
           tc::fence_smem_to_async();
-          __syncthreads();
-          if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(st);
-            const int ksteps = min(4, (n - l0 + 7) / 8);
-            const bool fresh = (j == j0 && kc == 0);
-            for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
-              const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-              for (int nt = 0; nt < P.NT; ++nt) {
-                const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
-                const uint64_t bh = tc::sdesc_k128(sa + boff);
-                const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-                const uint32_t d = tmem + (uint32_t)P.n0[nt];
-                const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
-                tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
-                tc::mma_tf32(d, ah, bl, idesc, 1u);
-                tc::mma_tf32(d, al, bh, idesc, 1u);
-              }
+          tc::mbar_arrive(&full[s]);
+        }
+      }
+    }
+  } else if (warp == 12) {
+    // ---- TMA: g_j rows 0..Np-1, 32 columns per chunk, hi and lo ----
+    if (lane == 0) {
+      uint32_t cc = 0;
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        for (int j = 0; j < M && !*abort_flag; ++j) {
+          for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
             }
-            tc::mma_commit(&bars[s]);
-            if (j == j1 - 1 && kc == P.KC - 1) tc::mma_commit(&bars[2]);
-            issued = true;
+            uint8_t *st = smem + s * stage_bytes;
+            tc::mbar_arrive_expect_tx(&full[s], 2 * tileB);
+            tc::tma_load_3d(st + 2 * kTileA + P.n0[0] * 128, &th0, kc * 32, P.n0[0], j, &full[s]);
+            tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[0] * 128, &tl0, kc * 32, P.n0[0], j,
+                            &full[s]);
+            if (P.NT > 1) {
+              tc::tma_load_3d(st + 2 * kTileA + P.n0[1] * 128, &th1, kc * 32, P.n0[1], j,
+                              &full[s]);
+              tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[1] * 128, &tl1, kc * 32, P.n0[1], j,
+                              &full[s]);
+            }
           }
         }
       }
-      // add this block of mesh points into the FP64 result
-      if (!tc::mbar_wait(&bars[2], blocks & 1, kWaitNs)) *abort_flag = 1;
-      ++blocks;
-      __syncthreads();
-      if (*abort_flag) goto finish;
-      tc::fence_after_sync();
-      {
-        const int wq = warp & 3, grp = warp >> 2;  // 3 warpgroups share the columns
-        const int a = mt * 128 + wq * 32 + lane;
-        const bool live = a < n;
-        double *row = P.I1 + ((long)i * n + (live ? a : 0)) * n;
-        int q = 0;
-        for (int c0 = 0; c0 < n; c0 += 16, ++q) {
-          if (q % 3 != grp) continue;
+    }
+  } else if (warp == 13) {
+    // ---- MMA issue: one accumulator block per JB mesh points ----
+    if (lane == 0) {
+      uint32_t cc = 0, tcount = 0;
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        for (int j0 = 0; j0 < M && !*abort_flag; j0 += P.JB, ++tcount) {
+          const int j1 = min(M, j0 + P.JB);
+          const int buf = tcount % P.NBUF;
+          const uint32_t tu = tcount / P.NBUF;
+          if (tu > 0 && !tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t dbase = tmem + (uint32_t)(buf * 256);
+          for (int j = j0; j < j1 && !*abort_flag; ++j) {
+            for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+              const int s = cc & 1;
+              const uint32_t use = cc >> 1;
+              if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+                *abort_flag = 1;
+                break;
+              }
+              tc::fence_after_sync();
+              const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
+              const int ksteps = min(4, (n - kc * 32 + 7) / 8);
+              const bool fresh = (j == j0 && kc == 0);
+              for (int kk = 0; kk < ksteps; ++kk) {
+                const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+                const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+                for (int nt = 0; nt < P.NT; ++nt) {
+                  const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
+                  const uint64_t bh = tc::sdesc_k128(sa + boff);
+                  const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+                  const uint32_t d = dbase + (uint32_t)P.n0[nt];
+                  const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
+                  tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
+                  tc::mma_tf32(d, ah, bl, idesc, 1u);
+                  tc::mma_tf32(d, al, bh, idesc, 1u);
+                }
+              }
+              tc::mma_commit(&empty[s]);
+              issued = true;
+            }
+          }
+          tc::mma_commit(&accf[buf]);
+        }
+      }
+    }
+  } else {
+    // ---- flush: add each FP32 block into the FP64 result ----
+    uint32_t tcount = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      const int i = (int)(w / P.MT), mt = (int)(w % P.MT);
+      const int a = mt * 128 + warp * 32 + lane;
+      const bool live = a < n;
+      double *row = P.I1 + ((long)i * n + (live ? a : 0)) * n;
+      for (int j0 = 0; j0 < M; j0 += P.JB, ++tcount) {
+        const int buf = tcount % P.NBUF;
+        const uint32_t tu = tcount / P.NBUF;
+        if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int c0 = 0; c0 < n; c0 += 16) {
           float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
+          tc::tmem_ld16(tmem + (uint32_t)(buf * 256) + ((uint32_t)(warp * 32) << 16) +
+                            (uint32_t)c0,
+                        v);
           if (live) {
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
@@ -172,19 +235,19 @@ __global__ void __launch_bounds__(kThreads, 1) conv1_tc_kernel(const C1Params P)
             }
           }
         }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&acce[buf]);
       }
-      tc::fence_before_sync();
-      __syncthreads();
     }
   }
-finish:
+
   __syncthreads();
   if (*abort_flag) {
-    if (tid == 0) {
-      if (issued) tc::mma_commit(&bars[3]);
+    if (warp == 13 && lane == 0) {
+      if (issued) tc::mma_commit(drain);
       atomicExch(P.err, 1);
+      if (issued) tc::mbar_wait(drain, 0, kWaitNs);
     }
-    if (issued) tc::mbar_wait(&bars[3], 0, kWaitNs);
     __syncthreads();
   }
   tc::fence_after_sync();
@@ -226,6 +289,8 @@ cudaError_t conv1_tc(int n, int M, const ConvCoef *coef, const double *dHF, cons
     P.NT = 1;
     P.n0[0] = 0;
     P.nsz[0] = P.Np;
+    P.n0[1] = 0;
+    P.nsz[1] = P.Np;
   } else {
     P.NT = 2;
     const int half = ((P.Np / 2) + 15) / 16 * 16;
@@ -234,20 +299,26 @@ cudaError_t conv1_tc(int n, int M, const ConvCoef *coef, const double *dHF, cons
     P.n0[1] = half;
     P.nsz[1] = P.Np - half;
   }
+  P.NBUF = (P.Np <= 256) ? 2 : 1;
   P.S32 = S32;
-  P.gh = gh;
-  P.gl = gl;
   P.dHF = dHF;
   P.coef = coef;
   P.I1 = I1;
   P.err = err;
-  const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)P.Np * 128) + 64;
-  cudaError_t e = cudaFuncSetAttribute(conv1_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  CUtensorMap th[2], tl[2];
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < 2; ++t) {
+    e = make_tmap_rows(&th[t], gh, n, M, P.ld, P.nsz[t]);
+    if (e == cudaSuccess) e = make_tmap_rows(&tl[t], gl, n, M, P.ld, P.nsz[t]);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)P.Np * 128) + 128;
+  e = cudaFuncSetAttribute(conv1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
   const long items = (long)M * P.MT;
   const int grid = (int)(items < num_sms ? items : num_sms);
-  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(P);
+  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(P, th[0], tl[0], th[1], tl[1]);
   return cudaGetLastError();
 }
 

@@ -19,7 +19,6 @@
 namespace fedvr {
 namespace {
 
-constexpr int kThreads = 384;                 // 12 warps produce; warps 0-3 also drain TMEM
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound on every mbarrier wait (2 s)
 constexpr uint32_t kTileA = 128 * 128;        // bytes of one 128-row x 32-col fp32 operand half
 
@@ -46,11 +45,12 @@ __global__ void split_kernel(int n, long rows, int ld, const double *__restrict_
   }
 }
 
-// QV[j] = (g32[j] o g32[M-1-j]) V32 in FP32, padded rows of ld (64x64 tiles).
-__global__ void __launch_bounds__(256) qv_kernel(int n, int M, int ld,
+// VQ[j] = V32 (g32[j] o g32[M-1-j]) in FP32: row b of VQ is column b of (g o gb) V
+// (V and g o gb are symmetric). Rows padded to ld (64x64 tiles).
+__global__ void __launch_bounds__(256) vq_kernel(int n, int M, int ld,
                                                  const float *__restrict__ g32,
                                                  const float *__restrict__ V32,
-                                                 float *__restrict__ QV) {
+                                                 float *__restrict__ VQ) {
   const int j = blockIdx.z;
   const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
   const float *g = g32 + (long)j * n * ld, *gb = g32 + (long)(M - 1 - j) * n * ld;
@@ -60,9 +60,9 @@ __global__ void __launch_bounds__(256) qv_kernel(int n, int M, int ld,
   for (int k0 = 0; k0 < n; k0 += 16) {
     for (int e = threadIdx.x; e < 1024; e += 256) {
       int kk = e % 16, rr = e / 16, r = r0 + rr, k = k0 + kk;
-      As[kk][rr] = (r < n && k < n) ? g[(long)r * ld + k] * gb[(long)r * ld + k] : 0.f;
+      As[kk][rr] = (r < n && k < n) ? V32[(long)r * ld + k] : 0.f;
       int cc = e % 64, k2 = e / 64, c = c0 + cc, kq = k0 + k2;
-      Bs[k2][cc] = (c < n && kq < n) ? V32[(long)kq * ld + c] : 0.f;
+      Bs[k2][cc] = (c < n && kq < n) ? g[(long)kq * ld + c] * gb[(long)kq * ld + c] : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -86,31 +86,43 @@ __global__ void __launch_bounds__(256) qv_kernel(int n, int M, int ld,
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int c = c0 + tx + 16 * q;
-      if (c < ld) QV[((long)j * n + r) * ld + c] = (c < n) ? acc[i][q] : 0.f;
+      if (c < ld) VQ[((long)j * n + r) * ld + c] = (c < n) ? acc[i][q] : 0.f;
     }
   }
 }
 
 struct XParams {
-  int n, M, ld, MT, NT, Np, KC;
+  int n, M, ld, MT, NT, Np, KC, NBUF;
   int n0[2], nsz[2];
   float spin;
-  const float *g32, *gh, *gl, *V32, *QV;
+  const float *g32, *V32, *VQ;
   double *Sigma;
   float *S32;
   int *err;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) exchange_tc_kernel(const XParams P) {
+// Warp roles: 0-3 epilogue (TMEM lanes 0-127), 4-11 A-operand producers,
+// 12 TMA loads of the gb operand, 13 MMA issue. Stages handed over with
+// mbarriers: full[s] (256 producer arrivals + TMA bytes), empty[s] (MMA
+// commit); accumulators double-buffered with accf/acce.
+constexpr int kWarps2 = 14;
+constexpr int kThreads2 = kWarps2 * 32;
+
+__global__ void __launch_bounds__(kThreads2, 1)
+    exchange_tc_kernel(const __grid_constant__ XParams P, const __grid_constant__ CUtensorMap th0,
+                       const __grid_constant__ CUtensorMap tl0,
+                       const __grid_constant__ CUtensorMap th1,
+                       const __grid_constant__ CUtensorMap tl1) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  const int n = P.n, ld = P.ld;
+  const int n = P.n, ld = P.ld, M = P.M;
   const uint32_t tileB = (uint32_t)P.Np * 128;
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);  // free[2], full, drain
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
-  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
+  uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   float *gcol = reinterpret_cast<float *>(tmem_slot + 4);
   float *qcol = gcol + ld;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -120,7 +132,15 @@ __global__ void __launch_bounds__(kThreads, 1) exchange_tc_kernel(const XParams 
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) tc::mbar_init(&bars[i], 1);
+    tc::mbar_init(&full[0], 257);
+    tc::mbar_init(&full[1], 257);
+    tc::mbar_init(&empty[0], 1);
+    tc::mbar_init(&empty[1], 1);
+    tc::mbar_init(&accf[0], 1);
+    tc::mbar_init(&accf[1], 1);
+    tc::mbar_init(&acce[0], 128);
+    tc::mbar_init(&acce[1], 128);
+    tc::mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -128,102 +148,168 @@ __global__ void __launch_bounds__(kThreads, 1) exchange_tc_kernel(const XParams 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-
-  uint32_t cc = 0, tiles = 0;
+  const long items = (long)M * n;
   bool issued = false;
-  const long items = (long)P.M * n;
-  for (long w = blockIdx.x; w < items; w += gridDim.x) {
-    const int j = (int)(w / n), b = (int)(w % n);
-    const float *gA = P.g32 + (long)j * n * ld;
-    const float *ghB = P.gh + (long)(P.M - 1 - j) * n * ld;
-    const float *glB = P.gl + (long)(P.M - 1 - j) * n * ld;
-    const float *Vb = P.V32 + (long)b * ld;
-    for (int k = tid; k < n; k += kThreads) {
-      gcol[k] = gA[(long)k * ld + b];
-      qcol[k] = P.QV[((long)j * n + k) * ld + b];
-    }
-    for (int mt = b >> 7; mt < P.MT; ++mt) {
-      for (int kc = 0; kc < P.KC; ++kc, ++cc) {
-        const int s = cc & 1;
-        const uint32_t use = cc >> 1;
-        if (use > 0 && !tc::mbar_wait(&bars[s], (use - 1) & 1, kWaitNs)) *abort_flag = 1;
-        __syncthreads();
-        if (*abort_flag) goto finish;
-        uint8_t *st = smem + s * stage_bytes;
-        const int l0 = kc * 32;
-        for (int u = tid; u < 128 * 8; u += kThreads) {
-          const int r = u >> 3, c = u & 7, a = mt * 128 + r;
-          float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
-          if (a < n) {
-            const float4 gv = *reinterpret_cast<const float4 *>(gA + (long)a * ld + l0 + 4 * c);
-            const float4 vv = *reinterpret_cast<const float4 *>(Vb + l0 + 4 * c);
-            const float x0 = gv.x * vv.x, x1 = gv.y * vv.y, x2 = gv.z * vv.z, x3 = gv.w * vv.w;
-            hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2), tc::tf32_rna(x3));
-            lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
-                             tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
+
+  if (warp >= 4 && warp < 12) {
+    // ---- A producers: A(a, l) = g_al * V_bl, split hi/lo, 4 rows per thread ----
+    const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
+    uint32_t cc = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      const int j = (int)(w / n), b = (int)(w % n);
+      const float *gA = P.g32 + (long)j * n * ld;
+      const float *Vb = P.V32 + (long)b * ld;
+      for (int mt = b >> 7; mt < P.MT && !*abort_flag; ++mt) {
+        for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+          const int l0 = kc * 32;
+          const float4 vv = *reinterpret_cast<const float4 *>(Vb + l0 + 4 * c);
+          float4 gv[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int a = mt * 128 + r0 + 32 * k;
+            gv[k] = (a < n) ? *reinterpret_cast<const float4 *>(gA + (long)a * ld + l0 + 4 * c)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          const uint32_t off = tc::sw128_offset(r, c);
-          *reinterpret_cast<float4 *>(st + off) = hi;
-          *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
-        }
-        for (int u = tid; u < P.Np * 8; u += kThreads) {
-          const int r = u >> 3, c = u & 7;
-          float4 hv = make_float4(0.f, 0.f, 0.f, 0.f), lv = hv;
-          if (r < n) {
-            hv = *reinterpret_cast<const float4 *>(ghB + (long)r * ld + l0 + 4 * c);
-            lv = *reinterpret_cast<const float4 *>(glB + (long)r * ld + l0 + 4 * c);
+          const int s = cc & 1;
+          const uint32_t use = cc >> 1;
+          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
           }
-          const uint32_t off = tc::sw128_offset(r, c);
-          *reinterpret_cast<float4 *>(st + 2 * kTileA + off) = hv;
-          *reinterpret_cast<float4 *>(st + 2 * kTileA + tileB + off) = lv;
-        }
-        tc::fence_smem_to_async();
-        __syncthreads();
-        if (tid == 0) {
-          tc::fence_after_sync();
-          const uint32_t sa = tc::smem_u32(st);
-          const int ksteps = min(4, (n - l0 + 7) / 8);
-          for (int kk = 0; kk < ksteps; ++kk) {
-            const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
-            const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-            for (int nt = 0; nt < P.NT; ++nt) {
-              const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
-              const uint64_t bh = tc::sdesc_k128(sa + boff);
-              const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-              const uint32_t d = tmem + (uint32_t)P.n0[nt];
-              const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
-              tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-              tc::mma_tf32(d, ah, bl, idesc, 1u);
-              tc::mma_tf32(d, al, bh, idesc, 1u);
-            }
+          uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float x0 = gv[k].x * vv.x, x1 = gv[k].y * vv.y, x2 = gv[k].z * vv.z,
+                        x3 = gv[k].w * vv.w;
+            const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
+                                          tc::tf32_rna(x3));
+            const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
+                                          tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
+            const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
+            *reinterpret_cast<float4 *>(st + off) = hi;
+            *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
           }
-          tc::mma_commit(&bars[s]);
-          if (kc == P.KC - 1) tc::mma_commit(&bars[2]);
-          issued = true;
+          tc::fence_smem_to_async();
+          tc::mbar_arrive(&full[s]);
         }
       }
-      if (!tc::mbar_wait(&bars[2], tiles & 1, kWaitNs)) *abort_flag = 1;
-      ++tiles;
-      __syncthreads();
-      if (*abort_flag) goto finish;
-      tc::fence_after_sync();
-      if (warp < 4) {
+    }
+  } else if (warp == 12) {
+    // ---- TMA: gb = G[M-1-j] rows 0..Np-1, 32 columns per chunk, hi and lo ----
+    if (lane == 0) {
+      uint32_t cc = 0;
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        const int j = (int)(w / n), b = (int)(w % n);
+        for (int mt = b >> 7; mt < P.MT && !*abort_flag; ++mt) {
+          for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            uint8_t *st = smem + s * stage_bytes;
+            tc::mbar_arrive_expect_tx(&full[s], 2 * tileB);
+            tc::tma_load_3d(st + 2 * kTileA + P.n0[0] * 128, &th0, kc * 32, P.n0[0], M - 1 - j,
+                            &full[s]);
+            tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[0] * 128, &tl0, kc * 32, P.n0[0],
+                            M - 1 - j, &full[s]);
+            if (P.NT > 1) {
+              tc::tma_load_3d(st + 2 * kTileA + P.n0[1] * 128, &th1, kc * 32, P.n0[1], M - 1 - j,
+                              &full[s]);
+              tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[1] * 128, &tl1, kc * 32, P.n0[1],
+                              M - 1 - j, &full[s]);
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 13) {
+    // ---- MMA issue ----
+    if (lane == 0) {
+      uint32_t cc = 0, tcount = 0;
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        const int b = (int)(w % n);
+        for (int mt = b >> 7; mt < P.MT && !*abort_flag; ++mt, ++tcount) {
+          const int buf = tcount % P.NBUF;
+          const uint32_t tu = tcount / P.NBUF;
+          if (tu > 0 && !tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t dbase = tmem + (uint32_t)(buf * 256);
+          for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
+            const int ksteps = min(4, (n - kc * 32 + 7) / 8);
+            for (int kk = 0; kk < ksteps; ++kk) {
+              const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+              const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+              for (int nt = 0; nt < P.NT; ++nt) {
+                const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
+                const uint64_t bh = tc::sdesc_k128(sa + boff);
+                const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+                const uint32_t d = dbase + (uint32_t)P.n0[nt];
+                const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
+                tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_tf32(d, ah, bl, idesc, 1u);
+                tc::mma_tf32(d, al, bh, idesc, 1u);
+              }
+            }
+            tc::mma_commit(&empty[s]);
+            issued = true;
+          }
+          tc::mma_commit(&accf[buf]);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: Sigma_ab = sum_k V_ak (sigma g_ab (QV)_kb - g_kb P_ak) ----
+    uint32_t tcount = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      const int j = (int)(w / n), b = (int)(w % n);
+      const float *gA = P.g32 + (long)j * n * ld;
+      tc::named_bar(1, 128);
+      for (int k = tid; k < n; k += 128) {
+        gcol[k] = gA[(long)b * ld + k];                  // g_kb = g_bk
+        qcol[k] = P.VQ[((long)j * n + b) * ld + k];      // (QV)_kb = (VQ)_bk
+      }
+      tc::named_bar(1, 128);
+      for (int mt = b >> 7; mt < P.MT; ++mt, ++tcount) {
+        const int buf = tcount % P.NBUF;
+        const uint32_t tu = tcount / P.NBUF;
+        if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc::fence_after_sync();
         const int a = mt * 128 + warp * 32 + lane;
         const bool live = a < n;
-        const float gab = live ? gA[(long)a * ld + b] : 0.f;
-        const float sg = P.spin * gab;
+        const float sg = live ? P.spin * gA[(long)a * ld + b] : 0.f;
         float acc = 0.f;
         for (int c0 = 0; c0 < n; c0 += 16) {
           float pv[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, pv);
+          tc::tmem_ld16(tmem + (uint32_t)(buf * 256) + ((uint32_t)(warp * 32) << 16) +
+                            (uint32_t)c0,
+                        pv);
           if (live) {
+            float vk[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int k = c0 + i;
-              if (k < n) acc = fmaf(P.V32[(long)k * ld + a], sg * qcol[k] - gcol[k] * pv[i], acc);
-            }
+            for (int i = 0; i < 16; ++i) vk[i] = (c0 + i < n) ? P.V32[(long)(c0 + i) * ld + a] : 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (c0 + i < n) acc = fmaf(vk[i], sg * qcol[c0 + i] - gcol[c0 + i] * pv[i], acc);
           }
         }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&acce[buf]);
         if (live && a >= b) {
           const long nn = (long)n * n;
           P.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
@@ -234,19 +320,17 @@ __global__ void __launch_bounds__(kThreads, 1) exchange_tc_kernel(const XParams 
           }
         }
       }
-      tc::fence_before_sync();
-      __syncthreads();
     }
   }
-finish:
+
   __syncthreads();
   if (*abort_flag) {
-    // let any MMAs still in flight finish (bounded) before the TMEM goes away
-    if (tid == 0) {
-      if (issued) tc::mma_commit(&bars[3]);
+    // let MMAs still in flight finish (bounded) before the TMEM goes away
+    if (warp == 13 && lane == 0) {
+      if (issued) tc::mma_commit(drain);
       atomicExch(P.err, 1);
+      if (issued) tc::mbar_wait(drain, 0, kWaitNs);
     }
-    if (issued) tc::mbar_wait(&bars[3], 0, kWaitNs);
     __syncthreads();
   }
   tc::fence_after_sync();
@@ -265,7 +349,7 @@ cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh,
 size_t sigma2_tc_smem_bytes(int n) {
   const int Np = (n + 15) / 16 * 16;
   const int ld = (n + 31) / 32 * 32;
-  return 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np * 128) + 64 + 2 * (size_t)ld * 4;
+  return 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np * 128) + 128 + 2 * (size_t)ld * 4;
 }
 
 int sigma2_tc_max_n() {
@@ -279,12 +363,12 @@ cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *
                       cudaStream_t s) {
   const int ld = (n + 31) / 32 * 32;
   const long stack = (long)M * n * ld;
-  float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *QV = ws + 3 * stack;
+  float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *VQ = ws + 3 * stack;
   float *V32 = ws + 4 * stack;
   split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, gh, gl);
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
   dim3 gq((ld + 63) / 64, (n + 63) / 64, M);
-  qv_kernel<<<gq, 256, 0, s>>>(n, M, ld, g32, V32, QV);
+  vq_kernel<<<gq, 256, 0, s>>>(n, M, ld, g32, V32, VQ);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   XParams P{};
@@ -298,7 +382,8 @@ cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *
     P.NT = 1;
     P.n0[0] = 0;
     P.nsz[0] = P.Np;
-    P.n0[1] = P.nsz[1] = 0;
+    P.n0[1] = 0;
+    P.nsz[1] = P.Np;
   } else {
     P.NT = 2;
     const int half = ((P.Np / 2) + 15) / 16 * 16;
@@ -307,22 +392,27 @@ cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *
     P.n0[1] = half;
     P.nsz[1] = P.Np - half;
   }
+  P.NBUF = (P.Np <= 256) ? 2 : 1;
   P.spin = (float)spin;
   P.g32 = g32;
-  P.gh = gh;
-  P.gl = gl;
   P.V32 = V32;
-  P.QV = QV;
+  P.VQ = VQ;
   P.Sigma = Sigma;
   P.S32 = S32;
   P.err = err;
+  CUtensorMap th[2], tl[2];
+  for (int t = 0; t < 2; ++t) {
+    e = make_tmap_rows(&th[t], gh, n, M, ld, P.nsz[t]);
+    if (e == cudaSuccess) e = make_tmap_rows(&tl[t], gl, n, M, ld, P.nsz[t]);
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = sigma2_tc_smem_bytes(n);
   e = cudaFuncSetAttribute(exchange_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
   long items = (long)M * n;
   int grid = (int)(items < num_sms ? items : num_sms);
-  exchange_tc_kernel<<<grid, kThreads, smem, s>>>(P);
+  exchange_tc_kernel<<<grid, kThreads2, smem, s>>>(P, th[0], tl[0], th[1], tl[1]);
   return cudaGetLastError();
 }
 
