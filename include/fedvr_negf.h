@@ -57,7 +57,9 @@ typedef enum {
   FEDVR_FP64 = 0,        /* every contraction in IEEE double */
   FEDVR_SPLIT_TF32 = 1,  /* Sigma^(2) and I^(1) contractions on tensor cores,
                             hi+lo TF32 operands, FP32 accumulation, FP64
-                            epilogues and cross-tile sums */
+                            cross-block sums; I^(2) eigenbasis products in
+                            FP32; tables, update, residual, N and E0 in FP64.
+                            Requires n_b <= 304. */
   FEDVR_SPLIT_BF16 = 2   /* as above with three-way BF16 splits */
 } fedvr_precision;
 

@@ -203,7 +203,8 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->b_J, &ctx->b_scal, &ctx->b_hf_tmp, &ctx->b_sigma_init, &ctx->w_tau,
                     &ctx->w_w, &ctx->w_wm, &ctx->w_wp, &ctx->w_coef, &ctx->w_K, &ctx->w_phi,
                     &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
-                    &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc};
+                    &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
+                    &ctx->w_K32};
   for (DevBuf *b : bufs) release(*b);
   for (int i = 0; i < 7; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -478,6 +479,10 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
                       P<double>(ctx->w_G0), n, nn, M, s));
   FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, tau, w, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
                                     eps, nullptr, ctx->mu, P<double>(ctx->w_K), s));
+  if (precision == FEDVR_SPLIT_TF32) {
+    ENSURE(ctx, w_K32, (size_t)n * M * M * sizeof(float));
+    FEDVR_CK(ctx, launch_to_f32((size_t)n * M * M, P<double>(ctx->w_K), P<float>(ctx->w_K32), s));
+  }
   FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->w_G0), P<double>(ctx->w_G), s));
   if (int r = sync(ctx)) return r;
   ctx->history.clear();
@@ -550,7 +555,12 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   }
   launches += 1;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[4], s));
-  FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, t1, t2, s));
+  if (ctx->precision == FEDVR_SPLIT_TF32) {
+    FEDVR_CK(ctx, conv2_apply_f32(n, M, P<float>(ctx->w_K32), C, I1, I2,
+                                  reinterpret_cast<float *>(t1), reinterpret_cast<float *>(t2), s));
+  } else {
+    FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, t1, t2, s));
+  }
   launches += 5;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[5], s));
   FEDVR_CK(ctx, cudaMemsetAsync(red + 2, 0, sizeof(double), s));

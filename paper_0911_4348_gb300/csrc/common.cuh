@@ -59,7 +59,7 @@ struct fedvr_ctx {
   fedvr::DevBuf b_sigma_init;
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
-      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc;
+      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32;
 };
 
 namespace fedvr {
@@ -161,6 +161,10 @@ cudaError_t launch_conv2_kernel(int n, int M, double beta, const double *tau, co
                                 const double *mu_dev, double mu_host, double *K, cudaStream_t s);
 cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const double *I1,
                         double *I2, double *t1, double *t2, cudaStream_t s);
+
+cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s);
+cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
+                            double *I2, float *t1, float *t2, cudaStream_t s);
 
 // update.cu
 cudaError_t launch_update(int n, int M, double mixing, const double *G0, const double *I2,

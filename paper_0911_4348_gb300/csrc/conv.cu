@@ -116,7 +116,101 @@ __global__ void conv2_kernel_table(int n, int M, double beta, const double *__re
   K[idx] = v;
 }
 
+// FP32 batched GEMM with mixed input/output types (64x64 tiles, 4x4 per thread):
+// C = op(A) op(B), operands converted to float on load, result stored as To.
+template <bool TA, bool TB, typename Ta, typename Tb, typename To>
+__global__ void __launch_bounds__(256) gemm32_kernel(int M, int N, int K,
+                                                     const Ta *__restrict__ A, long lda, long sA,
+                                                     const Tb *__restrict__ B, long ldb, long sB,
+                                                     To *__restrict__ C, long ldc, long sC) {
+  const long bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  __shared__ float As[16][65];
+  __shared__ float Bs[16][65];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int kk, mm;
+      if (TA) { mm = e % 64; kk = e / 64; } else { kk = e % 16; mm = e / 16; }
+      int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? (float)(TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk])
+                                      : 0.f;
+      int nn;
+      if (TB) { kk = e % 16; nn = e / 16; } else { nn = e % 64; kk = e / 64; }
+      int gn = n0 + nn;
+      gk = k0 + kk;
+      Bs[kk][nn] = (gn < N && gk < K) ? (float)(TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn])
+                                      : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int gm = m0 + ty + 16 * r;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int gn = n0 + tx + 16 * q;
+      if (gn < N) C[(long)gm * ldc + gn] = (To)acc[r][q];
+    }
+  }
+}
+
+__global__ void to_f32_kernel(size_t count, const double *__restrict__ x, float *__restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+template <bool TA, bool TB, typename Ta, typename Tb, typename To>
+cudaError_t gemm32(int M, int N, int K, const Ta *A, long lda, long sA, const Tb *B, long ldb,
+                   long sB, To *C, long ldc, long sC, int batch, cudaStream_t s) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  gemm32_kernel<TA, TB, Ta, Tb, To><<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s) {
+  to_f32_kernel<<<1024, 256, 0, s>>>(count, x, y);
+  return cudaGetLastError();
+}
+
+// FP32 variant of conv2_apply for the split-precision mode: the same five
+// products with float arithmetic (K32 is the eigen-kernel table in FP32,
+// t1/t2 float scratch of M*n*n), FP64 I1 in and FP64 I2 out.
+cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
+                            double *I2, float *t1, float *t2, cudaStream_t s) {
+  long nn = (long)n * n, MM = (long)M * M;
+  cudaError_t e;
+  e = gemm32<true, false>(n, n, n, C, n, 0, I1, n, nn, t1, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  e = gemm32<false, false>(n, n, n, (const float *)t1, n, nn, C, n, 0, t2, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  e = gemm32<false, false>(M, n, M, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
+  if (e != cudaSuccess) return e;
+  e = gemm32<false, false>(n, n, n, C, n, 0, (const float *)t1, n, nn, t2, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  return gemm32<false, true>(n, n, n, (const float *)t2, n, nn, C, n, 0, I2, n, nn, M, s);
+}
 
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
                        const double *G, double *I1, cudaStream_t s) {
