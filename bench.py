@@ -14,7 +14,7 @@ scaling); ranks only meet at the timing barrier.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|tf32|bf16] [--workload he_medium|he_small|h3p_large]
-                    [--time-to-e0]
+                    [--no-time-to-e0] [--no-fp64-compare] [--no-cpu-baseline]
 """
 
 from __future__ import annotations
@@ -208,9 +208,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="fp64")
+    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="tf32")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="he_medium")
-    ap.add_argument("--time-to-e0", action="store_true")
+    ap.add_argument("--no-time-to-e0", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -320,7 +321,7 @@ def main():
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
            "E_hf": E_hf}
 
-    if args.time_to_e0:
+    if not args.no_time_to_e0:
         ctx2 = Context(stream.cuda_stream)
         ctx2.build_fedvr(sys_.n_elem, sys_.order, sys_.xmin, sys_.xmax, sys_.grid_kind)
         ctx2.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
@@ -336,6 +337,26 @@ def main():
                              "iterations": int(k_ok + 1), "solve_seconds": time.perf_counter() - t0,
                              "solve_iterations": r["iters"], "E0": Ef, "status": r["status"]}
         ctx2.close()
+
+    if prec != 0 and not args.no_fp64_compare:
+        # the plain FP64 GPU path on the same system: one warm-up and one timed step
+        ctx3 = Context(stream.cuda_stream)
+        ctx3.build_fedvr(sys_.n_elem, sys_.order, sys_.xmin, sys_.xmax, sys_.grid_kind)
+        ctx3.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
+        ctx3.solve_hf(sys_.beta, tol=1e-12)
+        ctx3.prepare_2b(sys_.beta, sys_.u, sys_.p, 0)
+        ctx3.step_2b(sys_.mixing)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx3.step_2b(sys_.mixing)
+        e1.record(stream)
+        barrier()
+        fp64_ms = e0.elapsed_time(e1)
+        st3, _ = ctx3.stage_times()
+        out["fp64_path"] = {"ms_per_step": fp64_ms, "builds_per_s": 1000.0 / fp64_ms,
+                            "stage_ms": st3, "speedup_per_step": fp64_ms / (elapsed / args.steps)}
+        ctx3.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, _, _ = oracle_sample(sys_, 6, 3)

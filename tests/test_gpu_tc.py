@@ -136,3 +136,26 @@ def test_conv1_tf32_he_medium_sampled_rows(ctx):
                 lag["k"][i, j], lag["t"][i, j], lag["s"][i, j] = k, t, sg
     want = O.conv1(dHF, Afull, G0, mesh, s.beta, lag, rows=rows)
     assert maxrel(got[rows], want) < CONV_TOL
+
+
+def test_tf32_and_fp64_steps_agree_at_full_size():
+    # three iterations of the He n_b=199, M=513 workload in both precisions
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Context
+    s = W.he_medium()
+    out = {}
+    for prec in (0, TF32):
+        c = Context()
+        c.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+        c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+        c.solve_hf(s.beta, tol=1e-12)
+        c.prepare_2b(s.beta, s.u, s.p, prec)
+        Es = [c.step_2b(s.mixing)["E0"] for _ in range(3)]
+        G = np.empty((s.n_tau, s.n_b, s.n_b))
+        c.read_2b(G_out=G)
+        out[prec] = (Es, G)
+        c.close()
+    for e64, e32 in zip(out[0][0], out[TF32][0]):
+        assert abs(e64 - e32) < E0_TOL
+    assert maxrel(out[TF32][1], out[0][1]) < 1e-6
