@@ -245,6 +245,25 @@ class Context:
                                             _dev(I2, (M, n, n))))
 
 
+def solve_2b_batched(contexts, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
+                     precision=SPLIT_TF32, check=True):
+    """Second-Born self-consistency of several prepared contexts (HF solved)
+    advanced together: one tensor-core launch per kernel per iteration covers
+    every system (``solve_2b_batched``). Returns per-system E0, N, iterations."""
+    lib = _native.lib()
+    k = len(contexts)
+    handles = (C.c_void_p * k)(*[c.handle.value for c in contexts])
+    beta = np.ascontiguousarray(np.broadcast_to(beta, (k,)), dtype=np.float64)
+    u = np.ascontiguousarray(np.broadcast_to(u, (k,)), dtype=np.int32)
+    p = np.ascontiguousarray(np.broadcast_to(p, (k,)), dtype=np.int32)
+    E0, N, it = np.empty(k), np.empty(k), np.empty(k, dtype=np.int32)
+    code = lib.solve_2b_batched(handles, k, _dptr(beta), _iptr(u), _iptr(p), mixing, tol, max_iter,
+                                precision, _dptr(E0), _dptr(N), _iptr(it))
+    if check and code != 0:
+        raise FedvrError(code, contexts[0].last_error())
+    return dict(E0=E0, N=N, iters=it, status=code)
+
+
 def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
     """Allocation-free FP64 Sigma^(2) build (``fedvr_sigma2_noalloc``) for callers
     that cannot let the library allocate device memory. Limit M*n*n <= 2^19;
@@ -259,4 +278,4 @@ def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
         raise FedvrError(code, "fedvr_sigma2_noalloc failed")
 
 
-__all__ = ["sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]
+__all__ = ["solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]

@@ -3,12 +3,14 @@
 // second-Born Dyson iteration (Sec. 2.3). Every numerical step is a kernel of
 // this library; the host only sequences launches and reads scalars.
 #include "common.cuh"
+#include "tc_sys.cuh"
 
 #include <math.h>
 #include <string.h>
 
 #include <chrono>
 #include <new>
+#include <vector>
 
 namespace fedvr {
 
@@ -158,6 +160,119 @@ int check_precision(fedvr_ctx *ctx, int precision, int n) {
     return FEDVR_OK;
   }
   return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+}
+
+// Device tables of the tensor-core kernels for one system: XSys, C1Sys and
+// the two work-queue prefixes {0, items}, at 256-byte aligned offsets.
+constexpr size_t kTabX = 0;
+constexpr size_t kTabC = (sizeof(XSys) + 255) / 256 * 256;
+constexpr size_t kTabPX = kTabC + (sizeof(C1Sys) + 255) / 256 * 256;
+constexpr size_t kTabPC = kTabPX + 256;
+constexpr size_t kTabBytes = kTabPC + 256;
+
+int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *Sigma,
+                         float *S32, const double *dHF, const ConvCoef *coef, double *I1) {
+  ENSURE(ctx, w_tab, kTabBytes);
+  XSys x;
+  C1Sys c;
+  memset(&x, 0, sizeof(x));
+  memset(&c, 0, sizeof(c));
+  FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32));
+  FEDVR_CK(ctx, c1sys_fill(&c, n, M, ws, S32, dHF, coef, I1));
+  long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M)};
+  uint8_t *base = P<uint8_t>(ctx->w_tab);
+  FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabX, &x, sizeof(x), cudaMemcpyHostToDevice, ctx->stream));
+  FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabC, &c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream));
+  FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabPX, px, sizeof(px), cudaMemcpyHostToDevice, ctx->stream));
+  FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabPC, pc, sizeof(pc), cudaMemcpyHostToDevice, ctx->stream));
+  return sync(ctx);  // host descriptors go out of scope
+}
+
+// The pieces of one iteration for one system, enqueued on stream s.
+// (1) Sigma^(2): operand preparation (split path) or the whole FP64 build.
+int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches) {
+  const int n = ctx->n, M = ctx->M;
+  const size_t stack = (size_t)M * n * n;
+  double *G = P<double>(ctx->w_G), *S = P<double>(ctx->w_S);
+  const double *V = P<double>(ctx->b_V);
+  if (warm) {
+    FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->b_sigma_init), S, s));
+    *launches += 1;
+    if (ctx->precision == FEDVR_SPLIT_TF32) {  // operands for the tensor-core convolution
+      float *ws, *S32;
+      int *err;
+      if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+      const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
+      FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
+      FEDVR_CK(ctx, launch_sigma_to_f32(n, M, S, S32, s));
+      *launches += 2;
+    }
+  } else if (ctx->precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s));
+    *launches += 3;
+  } else {
+    FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
+                              P<double>(ctx->w_t3), s));
+    *launches += 4;
+  }
+  return FEDVR_OK;
+}
+
+// (2) HF self-energy change and the energy/particle number of (g_k, Sigma_k).
+int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
+  const int n = ctx->n, M = ctx->M;
+  const size_t nn = (size_t)n * n;
+  double *G = P<double>(ctx->w_G), *S = P<double>(ctx->w_S);
+  const double *V = P<double>(ctx->b_V);
+  FEDVR_CK(ctx, launch_hf_selfenergy(n, ctx->spin, G + (size_t)(M - 1) * nn, V, nullptr,
+                                     P<double>(ctx->b_Sigma0), P<double>(ctx->w_dHF), s));
+  FEDVR_CK(ctx, launch_energy(n, M, ctx->spin, P<double>(ctx->b_h), V, G, S, P<double>(ctx->w_w),
+                              P<double>(ctx->w_part), P<double>(ctx->w_red), s));
+  *launches += 3;
+  return FEDVR_OK;
+}
+
+// (3) FP64 first convolution (the split path launches its tensor-core kernel instead).
+int phase_conv1_fp64(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
+  FEDVR_CK(ctx, conv1_fp64(ctx->n, ctx->M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF),
+                           P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s));
+  *launches += 1;
+  return FEDVR_OK;
+}
+
+// (4) second convolution.
+int phase_conv2(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
+  const int n = ctx->n, M = ctx->M;
+  const double *C = P<double>(ctx->b_C);
+  double *I1 = P<double>(ctx->w_I1), *I2 = P<double>(ctx->w_I2);
+  if (ctx->precision == FEDVR_SPLIT_TF32) {
+    FEDVR_CK(ctx, conv2_apply_f32(n, M, P<float>(ctx->w_K32), C, I1, I2, P<float>(ctx->w_t1),
+                                  P<float>(ctx->w_t2), s));
+  } else {
+    FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, P<double>(ctx->w_t1),
+                              P<double>(ctx->w_t2), s));
+  }
+  *launches += 5;
+  return FEDVR_OK;
+}
+
+// (5) mixed update and residual.
+int phase_update(fedvr_ctx *ctx, double mixing, cudaStream_t s, int *launches) {
+  double *red = P<double>(ctx->w_red);
+  FEDVR_CK(ctx, cudaMemsetAsync(red + 2, 0, sizeof(double), s));
+  FEDVR_CK(ctx, launch_update(ctx->n, ctx->M, mixing, P<double>(ctx->w_G0), P<double>(ctx->w_I2),
+                              P<double>(ctx->w_G), reinterpret_cast<unsigned long long *>(red + 2),
+                              s));
+  *launches += 1;
+  return FEDVR_OK;
+}
+
+int tc_err_ptr(fedvr_ctx *ctx, int **err) {
+  float *ws, *S32;
+  return tc_workspace(ctx, ctx->n, ctx->M, &ws, &S32, err);
 }
 
 }  // namespace
@@ -482,6 +597,12 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   if (precision == FEDVR_SPLIT_TF32) {
     ENSURE(ctx, w_K32, (size_t)n * M * M * sizeof(float));
     FEDVR_CK(ctx, launch_to_f32((size_t)n * M * M, P<double>(ctx->w_K), P<float>(ctx->w_K32), s));
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    if (int r = upload_single_tables(ctx, n, M, ws, P<double>(ctx->w_S), S32, P<double>(ctx->w_dHF),
+                                     P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_I1)))
+      return r;
   }
   FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->w_G0), P<double>(ctx->w_G), s));
   if (int r = sync(ctx)) return r;
@@ -512,72 +633,49 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   const double *C = P<double>(ctx->b_C), *h = P<double>(ctx->b_h), *V = P<double>(ctx->b_V);
   auto t0 = std::chrono::steady_clock::now();
   int launches = 0;
+  const bool split = ctx->precision == FEDVR_SPLIT_TF32;
+  int *err = nullptr;
+  if (split) {
+    if (int r = tc_err_ptr(ctx, &err)) return r;
+  }
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[0], s));
   if (G_in)
     FEDVR_CK(ctx, cudaMemcpyAsync(G, G_in, dsz(stack),
                                   in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[1], s));
   const bool warm = ctx->step_k == 0 && ctx->sigma_init_M;
-  if (warm) {
-    FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->b_sigma_init), S, s));
+  if (int r = phase_sigma_pre(ctx, warm, s, &launches)) return r;
+  uint8_t *tab = P<uint8_t>(ctx->w_tab);
+  if (split && !warm) {
+    const TcGeom g = tc_geom(n, M);
+    FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
+                                     reinterpret_cast<const long *>(tab + kTabPX), 1,
+                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s));
     launches += 1;
-  } else if (ctx->precision == FEDVR_SPLIT_TF32) {
-    float *ws, *S32;
-    int *err;
-    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-    FEDVR_CK(ctx, sigma2_tc(n, M, spin, V, G, S, S32, ws, err, ctx->num_sms, s));
-    launches += 5;
-  } else {
-    FEDVR_CK(ctx, sigma2_fp64(n, M, spin, V, G, S, t1, t2, t3, s));
-    launches += 4;
   }
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[2], s));
-  FEDVR_CK(ctx, launch_hf_selfenergy(n, spin, G + (size_t)(M - 1) * nn, V, nullptr,
-                                     P<double>(ctx->b_Sigma0), P<double>(ctx->w_dHF), s));
-  FEDVR_CK(ctx, launch_energy(n, M, spin, h, V, G, S, P<double>(ctx->w_w), P<double>(ctx->w_part),
-                              red, s));
-  launches += 3;
+  if (int r = phase_mid(ctx, s, &launches)) return r;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[3], s));
-  if (ctx->precision == FEDVR_SPLIT_TF32) {
-    float *ws, *S32;
-    int *err;
-    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-    const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
-    if (warm) {  // the Sigma build was skipped: split g and convert Sigma here
-      FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
-      FEDVR_CK(ctx, launch_sigma_to_f32(n, M, S, S32, s));
-      launches += 2;
-    }
-    FEDVR_CK(ctx, conv1_tc(n, M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF), S32,
-                           ws + tstack, ws + 2 * tstack, I1, err, ctx->num_sms, s));
+  if (split) {
+    const TcGeom g = tc_geom(n, M);
+    FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
+                                  reinterpret_cast<const long *>(tab + kTabPC), 1,
+                                  conv1_items(n, M), g.Np, err, ctx->num_sms, s));
+    launches += 1;
   } else {
-    FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF), S, G, I1, s));
+    if (int r = phase_conv1_fp64(ctx, s, &launches)) return r;
   }
-  launches += 1;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[4], s));
-  if (ctx->precision == FEDVR_SPLIT_TF32) {
-    FEDVR_CK(ctx, conv2_apply_f32(n, M, P<float>(ctx->w_K32), C, I1, I2,
-                                  reinterpret_cast<float *>(t1), reinterpret_cast<float *>(t2), s));
-  } else {
-    FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, t1, t2, s));
-  }
-  launches += 5;
+  if (int r = phase_conv2(ctx, s, &launches)) return r;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[5], s));
-  FEDVR_CK(ctx, cudaMemsetAsync(red + 2, 0, sizeof(double), s));
-  FEDVR_CK(ctx, launch_update(n, M, mixing, G0, I2, G,
-                              reinterpret_cast<unsigned long long *>(red + 2), s));
-  launches += 1;
+  if (int r = phase_update(ctx, mixing, s, &launches)) return r;
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[6], s));
   ctx->step_launches = launches;
+  (void)G0; (void)I1; (void)I2; (void)t1; (void)t2; (void)t3; (void)C; (void)h; (void)V; (void)spin;
   double hr[3];
   int tc_err = 0;
   FEDVR_CK(ctx, cudaMemcpyAsync(hr, red, sizeof(hr), cudaMemcpyDeviceToHost, s));
-  if (ctx->precision == FEDVR_SPLIT_TF32) {
-    float *ws, *S32;
-    int *err;
-    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-    FEDVR_CK(ctx, cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  }
+  if (split) FEDVR_CK(ctx, cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (int r = sync(ctx)) return r;
   if (tc_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
   double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -663,9 +761,148 @@ int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len) {
 int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u, const int *p,
                      double mixing, double tol, int max_iter, int precision, double *E0,
                      double *N_out, int *iters) {
-  if (!ctxs || n_sys < 1 || !beta || !u || !p) return FEDVR_ERR_ARG;
-  if (ctxs[0]) fail(ctxs[0], FEDVR_ERR_ARG, "batched solve is not available in this build");
-  return FEDVR_ERR_ARG;
+  if (!ctxs || n_sys < 1 || n_sys > 4096 || !beta || !u || !p) return FEDVR_ERR_ARG;
+  for (int k = 0; k < n_sys; ++k) {
+    if (!ctxs[k]) return FEDVR_ERR_ARG;
+    if (ctxs[k]->failed) return FEDVR_ERR_STATE;
+  }
+  fedvr_ctx *lead = ctxs[0];
+  if (precision != FEDVR_SPLIT_TF32)
+    return fail(lead, FEDVR_ERR_ARG, "the batched solve runs the split-TF32 tensor-core path");
+  if (!(mixing > 0.0 && mixing <= 1.0) || !(tol > 0.0) || max_iter < 1)
+    return fail(lead, FEDVR_ERR_ARG, "need 0 < mixing <= 1, tol > 0, max_iter >= 1");
+  for (int k = 0; k < n_sys; ++k) {
+    if (ctxs[k]->device != lead->device)
+      return fail(lead, FEDVR_ERR_ARG, "all systems must be on one device");
+    for (int q = 0; q < k; ++q)
+      if (ctxs[q] == ctxs[k]) return fail(lead, FEDVR_ERR_ARG, "a context appears twice");
+  }
+  cudaStream_t s = lead->stream;
+  // per-system preparation (mesh, g^0, tables, workspace) on each context
+  int Np_max = 16, ld_max = 32;
+  for (int k = 0; k < n_sys; ++k) {
+    if (int r = fedvr_2b_prepare(ctxs[k], beta[k], u[k], p[k], precision)) {
+      fail(lead, r, "system %d: %s", k, ctxs[k]->err);
+      return r;
+    }
+    const TcGeom g = tc_geom(ctxs[k]->n, ctxs[k]->M);
+    Np_max = g.Np > Np_max ? g.Np : Np_max;
+    ld_max = g.ld > ld_max ? g.ld : ld_max;
+  }
+  // the batch tables: descriptors of every system, prefixes rebuilt per iteration
+  const size_t xs = (size_t)n_sys * sizeof(XSys), cs = (size_t)n_sys * sizeof(C1Sys);
+  const size_t off_c = (xs + 255) / 256 * 256, off_px = off_c + (cs + 255) / 256 * 256;
+  const size_t off_pc = off_px + ((size_t)(n_sys + 1) * sizeof(long) + 255) / 256 * 256;
+  const size_t off_err = off_pc + ((size_t)(n_sys + 1) * sizeof(long) + 255) / 256 * 256;
+  const size_t off_red = off_err + 256;
+  ENSURE(lead, w_btab, off_red + (size_t)n_sys * 3 * sizeof(double));
+  uint8_t *bt = P<uint8_t>(lead->w_btab);
+  {
+    std::vector<XSys> hx(n_sys);
+    std::vector<C1Sys> hc(n_sys);
+    for (int k = 0; k < n_sys; ++k) {
+      fedvr_ctx *c = ctxs[k];
+      float *ws, *S32;
+      int *err;
+      if (int r = tc_workspace(c, c->n, c->M, &ws, &S32, &err)) return r;
+      memset(&hx[k], 0, sizeof(XSys));
+      memset(&hc[k], 0, sizeof(C1Sys));
+      FEDVR_CK(lead, xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32));
+      FEDVR_CK(lead, c1sys_fill(&hc[k], c->n, c->M, ws, S32, P<double>(c->w_dHF),
+                                P<ConvCoef>(c->w_coef), P<double>(c->w_I1)));
+    }
+    FEDVR_CK(lead, cudaMemcpyAsync(bt, hx.data(), xs, cudaMemcpyHostToDevice, s));
+    FEDVR_CK(lead, cudaMemcpyAsync(bt + off_c, hc.data(), cs, cudaMemcpyHostToDevice, s));
+    FEDVR_CK(lead, cudaMemsetAsync(bt + off_err, 0, sizeof(int), s));
+    if (int r = sync(lead)) return r;
+  }
+  int *d_err = reinterpret_cast<int *>(bt + off_err);
+  std::vector<char> active(n_sys, 1);
+  std::vector<double> res(n_sys, INFINITY), best(n_sys, INFINITY), hred(3 * (size_t)n_sys);
+  std::vector<int> grow(n_sys, 0), done_it(n_sys, 0), status(n_sys, FEDVR_OK);
+  std::vector<long> px(n_sys + 1), pc(n_sys + 1);
+  int remaining = n_sys;
+  for (int it = 0; it < max_iter && remaining > 0; ++it) {
+    auto t0 = std::chrono::steady_clock::now();
+    px[0] = pc[0] = 0;
+    for (int k = 0; k < n_sys; ++k) {
+      const int n = ctxs[k]->n, M = ctxs[k]->M;
+      px[k + 1] = px[k] + (active[k] ? exchange_items(n, M) : 0);
+      pc[k + 1] = pc[k] + (active[k] ? conv1_items(n, M) : 0);
+    }
+    FEDVR_CK(lead, cudaMemcpyAsync(bt + off_px, px.data(), (n_sys + 1) * sizeof(long),
+                                   cudaMemcpyHostToDevice, s));
+    FEDVR_CK(lead, cudaMemcpyAsync(bt + off_pc, pc.data(), (n_sys + 1) * sizeof(long),
+                                   cudaMemcpyHostToDevice, s));
+    int launches = 0;
+    for (int k = 0; k < n_sys; ++k)
+      if (active[k]) {
+        if (int r = phase_sigma_pre(ctxs[k], false, s, &launches)) return r;
+      }
+    FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
+                                      reinterpret_cast<const long *>(bt + off_px), n_sys,
+                                      px[n_sys], Np_max, ld_max, d_err, lead->num_sms, s));
+    for (int k = 0; k < n_sys; ++k)
+      if (active[k]) {
+        if (int r = phase_mid(ctxs[k], s, &launches)) return r;
+      }
+    FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + off_c),
+                                   reinterpret_cast<const long *>(bt + off_pc), n_sys, pc[n_sys],
+                                   Np_max, d_err, lead->num_sms, s));
+    for (int k = 0; k < n_sys; ++k)
+      if (active[k]) {
+        if (int r = phase_conv2(ctxs[k], s, &launches)) return r;
+        if (int r = phase_update(ctxs[k], mixing, s, &launches)) return r;
+        FEDVR_CK(lead, cudaMemcpyAsync(bt + off_red + (size_t)k * 3 * sizeof(double),
+                                       ctxs[k]->w_red.ptr, 3 * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+      }
+    FEDVR_CK(lead, cudaMemcpyAsync(hred.data(), bt + off_red, hred.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+    int h_err = 0;
+    FEDVR_CK(lead, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (int r = sync(lead)) return r;
+    if (h_err) return fail(lead, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < n_sys; ++k) {
+      if (!active[k]) continue;
+      fedvr_ctx *c = ctxs[k];
+      const double E = hred[3 * k], Nel = hred[3 * k + 1], r = hred[3 * k + 2];
+      double rec[5] = {(double)c->step_k, r, E, Nel, ms};
+      c->history.insert(c->history.end(), rec, rec + 5);
+      c->step_k++;
+      done_it[k] = it + 1;
+      if (E0) E0[k] = E;
+      if (N_out) N_out[k] = Nel;
+      bool stop = false;
+      if (r != r || !is_fin(E)) {
+        status[k] = fail(c, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", it);
+        stop = true;
+      } else if (r < tol) {
+        stop = true;
+      } else if (r < best[k]) {
+        best[k] = r;
+        grow[k] = 0;
+      } else if (++grow[k] >= 8) {
+        status[k] = fail(c, FEDVR_ERR_DIVERGED, "residual grew for 8 iterations (at %d)", it);
+        stop = true;
+      }
+      if (stop) {
+        active[k] = 0;
+        --remaining;
+      }
+    }
+    lead->step_launches = launches + 2;
+  }
+  int worst = FEDVR_OK;
+  for (int k = 0; k < n_sys; ++k) {
+    if (active[k]) status[k] = fail(ctxs[k], FEDVR_ERR_NOCONV, "not converged after %d iterations",
+                                    max_iter);
+    if (iters) iters[k] = done_it[k];
+    if (status[k] < worst) worst = status[k];
+  }
+  return worst;
 }
 
 int fedvr_power_mesh(fedvr_ctx *ctx, double beta, int u, int p, double *tau, double *w,
@@ -674,6 +911,7 @@ int fedvr_power_mesh(fedvr_ctx *ctx, double beta, int u, int p, double *tau, dou
   if (int r = check_mesh_args(ctx, beta, u, p)) return r;
   if ((lag_k == nullptr) != (lag_t == nullptr))
     return fail(ctx, FEDVR_ERR_ARG, "lag_k and lag_t go together");
+  ctx->prepared = false;
   if (int r = build_mesh(ctx, beta, u, p, false)) return r;
   int M = 2 * u * p + 1;
   cudaStream_t s = ctx->stream;
@@ -694,14 +932,23 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, 1 <= M <= 4097 and device buffers");
   if (!is_fin(spin)) return fail(ctx, FEDVR_ERR_ARG, "spin factor must be finite");
   if (int r = check_precision(ctx, precision, n)) return r;
+  ctx->prepared = false;  // the workspace below is shared with a prepared run
   if (precision == FEDVR_SPLIT_TF32) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-    FEDVR_CK(ctx, sigma2_tc(n, M, spin, V, G, Sigma, nullptr, ws, err, ctx->num_sms, ctx->stream));
+    cudaStream_t s = ctx->stream;
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (int r = upload_single_tables(ctx, n, M, ws, Sigma, nullptr, nullptr, nullptr, nullptr))
+      return r;
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s));
+    const TcGeom g = tc_geom(n, M);
+    uint8_t *tab = P<uint8_t>(ctx->w_tab);
+    FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
+                                     reinterpret_cast<const long *>(tab + kTabPX), 1,
+                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s));
     int h_err = 0;
-    FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
     if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
     return FEDVR_OK;
@@ -722,6 +969,7 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
   if (n < 1 || n > 1024 || !dHF || !Sigma || !G || !I1)
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024 and device buffers");
   if (int r = check_precision(ctx, precision, n)) return r;
+  ctx->prepared = false;  // the workspace below is shared with a prepared run
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
   int M = 2 * u * p + 1;
   if (precision == FEDVR_SPLIT_TF32) {
@@ -731,10 +979,15 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
     cudaStream_t s = ctx->stream;
     FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (int r = upload_single_tables(ctx, n, M, ws, nullptr, S32, dHF, P<ConvCoef>(ctx->w_coef), I1))
+      return r;
     FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
     FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s));
-    FEDVR_CK(ctx, conv1_tc(n, M, P<ConvCoef>(ctx->w_coef), dHF, S32, ws + tstack, ws + 2 * tstack,
-                           I1, err, ctx->num_sms, s));
+    const TcGeom g = tc_geom(n, M);
+    uint8_t *tab = P<uint8_t>(ctx->w_tab);
+    FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
+                                  reinterpret_cast<const long *>(tab + kTabPC), 1,
+                                  conv1_items(n, M), g.Np, err, ctx->num_sms, s));
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
@@ -751,6 +1004,7 @@ int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double
   if (int r = check_mesh_args(ctx, beta, u, p)) return r;
   if (n < 1 || n > 1024 || !eps || !C || !I1 || !I2 || !is_fin(mu))
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, finite mu and device buffers");
+  ctx->prepared = false;
   if (int r = build_mesh(ctx, beta, u, p, false)) return r;
   int M = 2 * u * p + 1;
   size_t stack = (size_t)M * n * n;

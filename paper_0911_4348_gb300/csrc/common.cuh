@@ -59,7 +59,7 @@ struct fedvr_ctx {
   fedvr::DevBuf b_sigma_init;
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
-      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32;
+      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab;
 };
 
 namespace fedvr {
@@ -133,14 +133,10 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
 // rows beyond n read as zero.
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows);
 
-// sigma2_tc.cu (tensor cores, split TF32). ws holds 4 * M*n*ld + n*ld floats
-// (ld = n rounded up to 32); S32 (may be NULL) receives Sigma in FP32 with row
-// pitch ld; *err is set to 1 if a bounded device-side wait gave up.
+// sigma2_tc.cu (tensor cores, split TF32): the split workspace of a system
+// holds 4 * M*n*ld + n*ld floats (g32, gh, gl, VQ, V32; ld = n rounded up to 32).
 size_t sigma2_tc_smem_bytes(int n);
 int sigma2_tc_max_n();
-cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *G,
-                      double *Sigma, float *S32, float *ws, int *err, int num_sms,
-                      cudaStream_t s);
 
 // g32 = (float)G, gh/gl = TF32 hi/lo of G, rows padded to ld = n rounded up to 32.
 cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh, float *gl,
@@ -149,9 +145,6 @@ cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh,
 // conv_tc.cu (tensor cores, split TF32): S32 = Sigma in FP32 (pitch ld); gh/gl
 // are the split copies of G from launch_split_g / sigma2_tc.
 cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s);
-cudaError_t conv1_tc(int n, int M, const ConvCoef *coef, const double *dHF, const float *S32,
-                     const float *gh, const float *gl, double *I1, int *err, int num_sms,
-                     cudaStream_t s);
 
 // conv.cu
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,

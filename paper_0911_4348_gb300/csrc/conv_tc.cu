@@ -13,6 +13,7 @@
 // is then added into the FP64 result, so rounding does not grow with M.
 #include "common.cuh"
 #include "tc.cuh"
+#include "tc_sys.cuh"
 
 namespace fedvr {
 namespace {
@@ -22,33 +23,22 @@ constexpr uint32_t kTileA = 128 * 128;
 constexpr int kWarps = 14;  // 0-3 flush, 4-11 A producers, 12 TMA, 13 MMA
 constexpr int kThreads = kWarps * 32;
 
-struct C1Params {
-  int n, M, ld, MT, NT, Np, KC, JB, NBUF;
-  int n0[2], nsz[2];
-  const float *S32;
-  const double *dHF;
-  const ConvCoef *coef;
-  double *I1;
-  int *err;
-};
-
+// Work queue: the (i, M-tile) items of every system in the table, each a
+// sequence of accumulator blocks of JB mesh points j, each block a sequence
+// of 32-wide chunks c. Roles as in the exchange kernel.
 __global__ void __launch_bounds__(kThreads, 1)
-    conv1_tc_kernel(const __grid_constant__ C1Params P, const __grid_constant__ CUtensorMap th0,
-                    const __grid_constant__ CUtensorMap tl0,
-                    const __grid_constant__ CUtensorMap th1,
-                    const __grid_constant__ CUtensorMap tl1) {
+    conv1_tc_kernel(const C1Sys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
+                    long items, int Np_max, int nbuf, int *err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  const int n = P.n, ld = P.ld, M = P.M;
-  const uint32_t tileB = (uint32_t)P.Np * 128;
+  const uint32_t tileB = (uint32_t)Np_max * 128;
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
   uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long nld = (long)n * ld;
 
   if (warp == 0) {
     tc::tmem_alloc(tmem_slot, 512);
@@ -71,21 +61,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const long items = (long)M * P.MT;
   bool issued = false;
+  int cur = 0;
 
   if (warp >= 4 && warp < 12) {
     // ---- A producers: B_ij(a, c) = c1 Sigma_k1(a, c) + c2 Sigma_k2(a, c) (+ dHF on j = i) ----
     const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
     uint32_t cc = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      const int i = (int)(w / P.MT), mt = (int)(w % P.MT);
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const C1Sys &S = sys[cur];
+      const int n = S.g.n, ld = S.g.ld, M = S.g.M, MT = S.g.MT;
+      const long nld = (long)n * ld;
+      const long q = w - prefix[cur];
+      const int i = (int)(q / MT), mt = (int)(q % MT);
       for (int j = 0; j < M && !*abort_flag; ++j) {
-        const ConvCoef cf = P.coef[(long)i * M + j];
+        const ConvCoef cf = S.coef[(long)i * M + j];
         const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
         const float c1 = (float)cf.c1, c2 = (float)cf.c2;
-        const float *S1 = P.S32 + (long)k1 * nld, *S2 = P.S32 + (long)k2 * nld;
-        for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+        const float *S1 = S.S32 + (long)k1 * nld, *S2 = S.S32 + (long)k2 * nld;
+        for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
           const int l0 = kc * 32;
           float4 s1[4], s2[4];
 #pragma unroll
@@ -111,10 +106,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             float x[4] = {fmaf(c1, s1[k].x, c2 * s2[k].x), fmaf(c1, s1[k].y, c2 * s2[k].y),
                           fmaf(c1, s1[k].z, c2 * s2[k].z), fmaf(c1, s1[k].w, c2 * s2[k].w)};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int l = l0 + 4 * c + q;
-              if (l >= n || a >= n) x[q] = 0.f;
-              else if (cf.diag) x[q] += (float)P.dHF[(long)a * n + l];
+            for (int qq = 0; qq < 4; ++qq) {
+              const int l = l0 + 4 * c + qq;
+              if (l >= n || a >= n) x[qq] = 0.f;
+              else if (cf.diag) x[qq] += (float)S.dHF[(long)a * n + l];
             }
             const float4 hi = make_float4(tc::tf32_rna(x[0]), tc::tf32_rna(x[1]),
                                           tc::tf32_rna(x[2]), tc::tf32_rna(x[3]));
@@ -134,23 +129,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t cc = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        for (int j = 0; j < M && !*abort_flag; ++j) {
-          for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+        const C1Sys &S = sys[cur];
+        const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
+        for (int j = 0; j < S.g.M && !*abort_flag; ++j) {
+          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
             if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
               *abort_flag = 1;
               break;
             }
-            uint8_t *st = smem + s * stage_bytes;
-            tc::mbar_arrive_expect_tx(&full[s], 2 * tileB);
-            tc::tma_load_3d(st + 2 * kTileA + P.n0[0] * 128, &th0, kc * 32, P.n0[0], j, &full[s]);
-            tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[0] * 128, &tl0, kc * 32, P.n0[0], j,
-                            &full[s]);
-            if (P.NT > 1) {
-              tc::tma_load_3d(st + 2 * kTileA + P.n0[1] * 128, &th1, kc * 32, P.n0[1], j,
-                              &full[s]);
-              tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[1] * 128, &tl1, kc * 32, P.n0[1], j,
+            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+            tc::mbar_arrive_expect_tx(&full[s], bytes);
+            for (int nt = 0; nt < S.g.NT; ++nt) {
+              tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt], j, &full[s]);
+              tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt], j,
                               &full[s]);
             }
           }
@@ -162,18 +156,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t cc = 0, tcount = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        for (int j0 = 0; j0 < M && !*abort_flag; j0 += P.JB, ++tcount) {
-          const int j1 = min(M, j0 + P.JB);
-          const int buf = tcount % P.NBUF;
-          const uint32_t tu = tcount / P.NBUF;
-          if (tu > 0 && !tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs)) {
+        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+        const C1Sys &S = sys[cur];
+        const int n = S.g.n, M = S.g.M;
+        for (int j0 = 0; j0 < M && !*abort_flag; j0 += S.JB, ++tcount) {
+          const int j1 = min(M, j0 + S.JB);
+          const int buf = tcount & 1;
+          const uint32_t tu = tcount >> 1;
+          bool ok = true;
+          if (nbuf == 1 && tcount > 0)
+            ok = tc::mbar_wait(&acce[(tcount - 1) & 1], ((tcount - 1) >> 1) & 1, kWaitNs);
+          else if (nbuf == 2 && tu > 0)
+            ok = tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs);
+          if (!ok) {
             *abort_flag = 1;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t dbase = tmem + (uint32_t)(buf * 256);
+          const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
           for (int j = j0; j < j1 && !*abort_flag; ++j) {
-            for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+            for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
               const int s = cc & 1;
               const uint32_t use = cc >> 1;
               if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
@@ -187,12 +189,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int kk = 0; kk < ksteps; ++kk) {
                 const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
                 const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-                for (int nt = 0; nt < P.NT; ++nt) {
-                  const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
+                for (int nt = 0; nt < S.g.NT; ++nt) {
+                  const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
                   const uint64_t bh = tc::sdesc_k128(sa + boff);
                   const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-                  const uint32_t d = dbase + (uint32_t)P.n0[nt];
-                  const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
+                  const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
+                  const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
                   tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
                   tc::mma_tf32(d, ah, bl, idesc, 1u);
                   tc::mma_tf32(d, al, bh, idesc, 1u);
@@ -210,23 +212,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- flush: add each FP32 block into the FP64 result ----
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      const int i = (int)(w / P.MT), mt = (int)(w % P.MT);
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const C1Sys &S = sys[cur];
+      const int n = S.g.n, M = S.g.M, MT = S.g.MT;
+      const long q = w - prefix[cur];
+      const int i = (int)(q / MT), mt = (int)(q % MT);
       const int a = mt * 128 + warp * 32 + lane;
       const bool live = a < n;
-      double *row = P.I1 + ((long)i * n + (live ? a : 0)) * n;
-      for (int j0 = 0; j0 < M; j0 += P.JB, ++tcount) {
-        const int buf = tcount % P.NBUF;
-        const uint32_t tu = tcount / P.NBUF;
+      double *row = S.I1 + ((long)i * n + (live ? a : 0)) * n;
+      for (int j0 = 0; j0 < M; j0 += S.JB, ++tcount) {
+        const int buf = tcount & 1;
+        const uint32_t tu = tcount >> 1;
         if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
           *abort_flag = 1;
           break;
         }
         tc::fence_after_sync();
+        const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
         for (int c0 = 0; c0 < n; c0 += 16) {
           float v[16];
-          tc::tmem_ld16(tmem + (uint32_t)(buf * 256) + ((uint32_t)(warp * 32) << 16) +
-                            (uint32_t)c0,
-                        v);
+          tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
           if (live) {
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (*abort_flag) {
     if (warp == 13 && lane == 0) {
       if (issued) tc::mma_commit(drain);
-      atomicExch(P.err, 1);
+      atomicExch(err, 1);
       if (issued) tc::mbar_wait(drain, 0, kWaitNs);
     }
     __syncthreads();
@@ -274,51 +279,32 @@ cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t conv1_tc(int n, int M, const ConvCoef *coef, const double *dHF, const float *S32,
-                     const float *gh, const float *gl, double *I1, int *err, int num_sms,
-                     cudaStream_t s) {
-  C1Params P{};
-  P.n = n;
-  P.M = M;
-  P.ld = (n + 31) / 32 * 32;
-  P.MT = (n + 127) / 128;
-  P.Np = (n + 15) / 16 * 16;
-  P.KC = (n + 31) / 32;
-  P.JB = 4096 / n > 1 ? 4096 / n : 1;
-  if (P.Np <= 256) {
-    P.NT = 1;
-    P.n0[0] = 0;
-    P.nsz[0] = P.Np;
-    P.n0[1] = 0;
-    P.nsz[1] = P.Np;
-  } else {
-    P.NT = 2;
-    const int half = ((P.Np / 2) + 15) / 16 * 16;
-    P.n0[0] = 0;
-    P.nsz[0] = half;
-    P.n0[1] = half;
-    P.nsz[1] = P.Np - half;
-  }
-  P.NBUF = (P.Np <= 256) ? 2 : 1;
-  P.S32 = S32;
-  P.dHF = dHF;
-  P.coef = coef;
-  P.I1 = I1;
-  P.err = err;
-  CUtensorMap th[2], tl[2];
-  cudaError_t e = cudaSuccess;
+cudaError_t c1sys_fill(C1Sys *d, int n, int M, const float *ws, const float *S32,
+                       const double *dHF, const ConvCoef *coef, double *I1) {
+  d->g = tc_geom(n, M);
+  const long stack = (long)M * n * d->g.ld;
+  d->JB = 4096 / n > 1 ? 4096 / n : 1;
+  d->S32 = S32;
+  d->dHF = dHF;
+  d->coef = coef;
+  d->I1 = I1;
   for (int t = 0; t < 2; ++t) {
-    e = make_tmap_rows(&th[t], gh, n, M, P.ld, P.nsz[t]);
-    if (e == cudaSuccess) e = make_tmap_rows(&tl[t], gl, n, M, P.ld, P.nsz[t]);
+    cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t]);
+    if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)P.Np * 128) + 128;
-  e = cudaFuncSetAttribute(conv1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  return cudaSuccess;
+}
+
+cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
+                            int Np_max, int *err, int num_sms, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(Np_max, 0, false);
+  cudaError_t e = cudaFuncSetAttribute(conv1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  const long items = (long)M * P.MT;
   const int grid = (int)(items < num_sms ? items : num_sms);
-  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(P, th[0], tl[0], th[1], tl[1]);
+  const int nbuf = (Np_max <= 256) ? 2 : 1;
+  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
   return cudaGetLastError();
 }
 

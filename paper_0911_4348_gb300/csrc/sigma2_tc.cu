@@ -15,6 +15,7 @@
 // are formed; the symmetric result is mirrored.
 #include "common.cuh"
 #include "tc.cuh"
+#include "tc_sys.cuh"
 
 namespace fedvr {
 namespace {
@@ -91,40 +92,29 @@ __global__ void __launch_bounds__(256) vq_kernel(int n, int M, int ld,
   }
 }
 
-struct XParams {
-  int n, M, ld, MT, NT, Np, KC, NBUF;
-  int n0[2], nsz[2];
-  float spin;
-  const float *g32, *V32, *VQ;
-  double *Sigma;
-  float *S32;
-  int *err;
-};
-
 // Warp roles: 0-3 epilogue (TMEM lanes 0-127), 4-11 A-operand producers,
 // 12 TMA loads of the gb operand, 13 MMA issue. Stages handed over with
 // mbarriers: full[s] (256 producer arrivals + TMA bytes), empty[s] (MMA
-// commit); accumulators double-buffered with accf/acce.
+// commit); accumulators double-buffered with accf/acce. The work queue is the
+// concatenation of the (j, b) items of every system in the table; every role
+// walks it in the same order. The stage layout uses the table's largest N.
 constexpr int kWarps2 = 14;
 constexpr int kThreads2 = kWarps2 * 32;
 
 __global__ void __launch_bounds__(kThreads2, 1)
-    exchange_tc_kernel(const __grid_constant__ XParams P, const __grid_constant__ CUtensorMap th0,
-                       const __grid_constant__ CUtensorMap tl0,
-                       const __grid_constant__ CUtensorMap th1,
-                       const __grid_constant__ CUtensorMap tl1) {
+    exchange_tc_kernel(const XSys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
+                       long items, int Np_max, int ld_max, int nbuf, int *err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  const int n = P.n, ld = P.ld, M = P.M;
-  const uint32_t tileB = (uint32_t)P.Np * 128;
+  const uint32_t tileB = (uint32_t)Np_max * 128;
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
   uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   float *gcol = reinterpret_cast<float *>(tmem_slot + 4);
-  float *qcol = gcol + ld;
+  float *qcol = gcol + ld_max;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -148,19 +138,23 @@ __global__ void __launch_bounds__(kThreads2, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const long items = (long)M * n;
   bool issued = false;
+  int cur = 0;  // system of the current item (items ascend within a CTA)
 
   if (warp >= 4 && warp < 12) {
     // ---- A producers: A(a, l) = g_al * V_bl, split hi/lo, 4 rows per thread ----
     const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
     uint32_t cc = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      const int j = (int)(w / n), b = (int)(w % n);
-      const float *gA = P.g32 + (long)j * n * ld;
-      const float *Vb = P.V32 + (long)b * ld;
-      for (int mt = b >> 7; mt < P.MT && !*abort_flag; ++mt) {
-        for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const XSys &S = sys[cur];
+      const int n = S.g.n, ld = S.g.ld;
+      const long q = w - prefix[cur];
+      const int j = (int)(q / n), b = (int)(q % n);
+      const float *gA = S.g32 + (long)j * n * ld;
+      const float *Vb = S.V32 + (long)b * ld;
+      for (int mt = b >> 7; mt < S.g.MT && !*abort_flag; ++mt) {
+        for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
           const int l0 = kc * 32;
           const float4 vv = *reinterpret_cast<const float4 *>(Vb + l0 + 4 * c);
           float4 gv[4];
@@ -199,26 +193,27 @@ __global__ void __launch_bounds__(kThreads2, 1)
     if (lane == 0) {
       uint32_t cc = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        const int j = (int)(w / n), b = (int)(w % n);
-        for (int mt = b >> 7; mt < P.MT && !*abort_flag; ++mt) {
-          for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+        const XSys &S = sys[cur];
+        const int n = S.g.n;
+        const long q = w - prefix[cur];
+        const int j = (int)(q / n), b = (int)(q % n);
+        const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
+        for (int mt = b >> 7; mt < S.g.MT && !*abort_flag; ++mt) {
+          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
             if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
               *abort_flag = 1;
               break;
             }
-            uint8_t *st = smem + s * stage_bytes;
-            tc::mbar_arrive_expect_tx(&full[s], 2 * tileB);
-            tc::tma_load_3d(st + 2 * kTileA + P.n0[0] * 128, &th0, kc * 32, P.n0[0], M - 1 - j,
-                            &full[s]);
-            tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[0] * 128, &tl0, kc * 32, P.n0[0],
-                            M - 1 - j, &full[s]);
-            if (P.NT > 1) {
-              tc::tma_load_3d(st + 2 * kTileA + P.n0[1] * 128, &th1, kc * 32, P.n0[1], M - 1 - j,
-                              &full[s]);
-              tc::tma_load_3d(st + 2 * kTileA + tileB + P.n0[1] * 128, &tl1, kc * 32, P.n0[1],
-                              M - 1 - j, &full[s]);
+            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+            tc::mbar_arrive_expect_tx(&full[s], bytes);
+            for (int nt = 0; nt < S.g.NT; ++nt) {
+              tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt],
+                              S.g.M - 1 - j, &full[s]);
+              tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt],
+                              S.g.M - 1 - j, &full[s]);
             }
           }
         }
@@ -229,17 +224,26 @@ __global__ void __launch_bounds__(kThreads2, 1)
     if (lane == 0) {
       uint32_t cc = 0, tcount = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        const int b = (int)(w % n);
-        for (int mt = b >> 7; mt < P.MT && !*abort_flag; ++mt, ++tcount) {
-          const int buf = tcount % P.NBUF;
-          const uint32_t tu = tcount / P.NBUF;
-          if (tu > 0 && !tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs)) {
+        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+        const XSys &S = sys[cur];
+        const int n = S.g.n;
+        const int b = (int)((w - prefix[cur]) % n);
+        for (int mt = b >> 7; mt < S.g.MT && !*abort_flag; ++mt, ++tcount) {
+          const int buf = tcount & 1;
+          const uint32_t tu = tcount >> 1;
+          // one TMEM buffer: the previous tile must be drained; two: the one before it
+          bool ok = true;
+          if (nbuf == 1 && tcount > 0)
+            ok = tc::mbar_wait(&acce[(tcount - 1) & 1], ((tcount - 1) >> 1) & 1, kWaitNs);
+          else if (nbuf == 2 && tu > 0)
+            ok = tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs);
+          if (!ok) {
             *abort_flag = 1;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t dbase = tmem + (uint32_t)(buf * 256);
-          for (int kc = 0; kc < P.KC; ++kc, ++cc) {
+          const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
+          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
             if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
@@ -252,12 +256,12 @@ __global__ void __launch_bounds__(kThreads2, 1)
             for (int kk = 0; kk < ksteps; ++kk) {
               const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
               const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-              for (int nt = 0; nt < P.NT; ++nt) {
-                const uint32_t boff = 2 * kTileA + (uint32_t)P.n0[nt] * 128 + kk * 32;
+              for (int nt = 0; nt < S.g.NT; ++nt) {
+                const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
                 const uint64_t bh = tc::sdesc_k128(sa + boff);
                 const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-                const uint32_t d = dbase + (uint32_t)P.n0[nt];
-                const uint32_t idesc = tc::idesc_tf32(128, P.nsz[nt]);
+                const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
+                const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
                 tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                 tc::mma_tf32(d, ah, bl, idesc, 1u);
                 tc::mma_tf32(d, al, bh, idesc, 1u);
@@ -274,17 +278,21 @@ __global__ void __launch_bounds__(kThreads2, 1)
     // ---- epilogue: Sigma_ab = sum_k V_ak (sigma g_ab (QV)_kb - g_kb P_ak) ----
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      const int j = (int)(w / n), b = (int)(w % n);
-      const float *gA = P.g32 + (long)j * n * ld;
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const XSys &S = sys[cur];
+      const int n = S.g.n, ld = S.g.ld;
+      const long q = w - prefix[cur];
+      const int j = (int)(q / n), b = (int)(q % n);
+      const float *gA = S.g32 + (long)j * n * ld;
       tc::named_bar(1, 128);
       for (int k = tid; k < n; k += 128) {
         gcol[k] = gA[(long)b * ld + k];                  // g_kb = g_bk
-        qcol[k] = P.VQ[((long)j * n + b) * ld + k];      // (QV)_kb = (VQ)_bk
+        qcol[k] = S.VQ[((long)j * n + b) * ld + k];      // (QV)_kb = (VQ)_bk
       }
       tc::named_bar(1, 128);
-      for (int mt = b >> 7; mt < P.MT; ++mt, ++tcount) {
-        const int buf = tcount % P.NBUF;
-        const uint32_t tu = tcount / P.NBUF;
+      for (int mt = b >> 7; mt < S.g.MT; ++mt, ++tcount) {
+        const int buf = tcount & 1;
+        const uint32_t tu = tcount >> 1;
         if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
           *abort_flag = 1;
           break;
@@ -292,31 +300,37 @@ __global__ void __launch_bounds__(kThreads2, 1)
         tc::fence_after_sync();
         const int a = mt * 128 + warp * 32 + lane;
         const bool live = a < n;
-        const float sg = live ? P.spin * gA[(long)a * ld + b] : 0.f;
+        const float sg = live ? S.spin * gA[(long)a * ld + b] : 0.f;
+        const float *Va = S.V32 + (long)(live ? a : 0) * ld;  // V_ak = V_ka: row a
+        const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
         float acc = 0.f;
         for (int c0 = 0; c0 < n; c0 += 16) {
           float pv[16];
-          tc::tmem_ld16(tmem + (uint32_t)(buf * 256) + ((uint32_t)(warp * 32) << 16) +
-                            (uint32_t)c0,
-                        pv);
+          tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, pv);
           if (live) {
             float vk[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) vk[i] = (c0 + i < n) ? P.V32[(long)(c0 + i) * ld + a] : 0.f;
+            for (int t = 0; t < 4; ++t) {
+              const float4 v4 = *reinterpret_cast<const float4 *>(Va + c0 + 4 * t);
+              vk[4 * t] = v4.x;
+              vk[4 * t + 1] = v4.y;
+              vk[4 * t + 2] = v4.z;
+              vk[4 * t + 3] = v4.w;
+            }
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (c0 + i < n) acc = fmaf(vk[i], sg * qcol[c0 + i] - gcol[c0 + i] * pv[i], acc);
+            for (int t = 0; t < 16; ++t)
+              if (c0 + t < n) acc = fmaf(vk[t], sg * qcol[c0 + t] - gcol[c0 + t] * pv[t], acc);
           }
         }
         tc::fence_before_sync();
         tc::mbar_arrive(&acce[buf]);
         if (live && a >= b) {
           const long nn = (long)n * n;
-          P.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
-          P.Sigma[(long)j * nn + (long)b * n + a] = (double)acc;
-          if (P.S32) {
-            P.S32[((long)j * n + a) * ld + b] = acc;
-            P.S32[((long)j * n + b) * ld + a] = acc;
+          S.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
+          S.Sigma[(long)j * nn + (long)b * n + a] = (double)acc;
+          if (S.S32) {
+            S.S32[((long)j * n + a) * ld + b] = acc;
+            S.S32[((long)j * n + b) * ld + a] = acc;
           }
         }
       }
@@ -328,7 +342,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
     // let MMAs still in flight finish (bounded) before the TMEM goes away
     if (warp == 13 && lane == 0) {
       if (issued) tc::mma_commit(drain);
-      atomicExch(P.err, 1);
+      atomicExch(err, 1);
       if (issued) tc::mbar_wait(drain, 0, kWaitNs);
     }
     __syncthreads();
@@ -346,10 +360,41 @@ cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh,
   return cudaGetLastError();
 }
 
+TcGeom tc_geom(int n, int M) {
+  TcGeom g{};
+  g.n = n;
+  g.M = M;
+  g.ld = (n + 31) / 32 * 32;
+  g.MT = (n + 127) / 128;
+  g.Np = (n + 15) / 16 * 16;
+  g.KC = (n + 31) / 32;
+  if (g.Np <= 256) {
+    g.NT = 1;
+    g.n0[0] = 0;
+    g.nsz[0] = g.Np;
+    g.n0[1] = 0;
+    g.nsz[1] = g.Np;
+  } else {
+    g.NT = 2;
+    const int half = ((g.Np / 2) + 15) / 16 * 16;
+    g.n0[0] = 0;
+    g.nsz[0] = half;
+    g.n0[1] = half;
+    g.nsz[1] = g.Np - half;
+  }
+  g.NBUF = (g.Np <= 256) ? 2 : 1;
+  return g;
+}
+
+size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns) {
+  size_t b = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 128) + 128;
+  if (with_columns) b += 2 * (size_t)ld_max * 4;
+  return b;
+}
+
 size_t sigma2_tc_smem_bytes(int n) {
-  const int Np = (n + 15) / 16 * 16;
-  const int ld = (n + 31) / 32 * 32;
-  return 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np * 128) + 128 + 2 * (size_t)ld * 4;
+  const TcGeom g = tc_geom(n, 1);
+  return tc_smem_bytes(g.Np, g.ld, true);
 }
 
 int sigma2_tc_max_n() {
@@ -358,9 +403,8 @@ int sigma2_tc_max_n() {
   return n;
 }
 
-cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *G,
-                      double *Sigma, float *S32, float *ws, int *err, int num_sms,
-                      cudaStream_t s) {
+cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
+                          cudaStream_t s) {
   const int ld = (n + 31) / 32 * 32;
   const long stack = (long)M * n * ld;
   float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *VQ = ws + 3 * stack;
@@ -369,50 +413,37 @@ cudaError_t sigma2_tc(int n, int M, double spin, const double *V, const double *
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
   dim3 gq((ld + 63) / 64, (n + 63) / 64, M);
   vq_kernel<<<gq, 256, 0, s>>>(n, M, ld, g32, V32, VQ);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  XParams P{};
-  P.n = n;
-  P.M = M;
-  P.ld = ld;
-  P.MT = (n + 127) / 128;
-  P.Np = (n + 15) / 16 * 16;
-  P.KC = (n + 31) / 32;
-  if (P.Np <= 256) {
-    P.NT = 1;
-    P.n0[0] = 0;
-    P.nsz[0] = P.Np;
-    P.n0[1] = 0;
-    P.nsz[1] = P.Np;
-  } else {
-    P.NT = 2;
-    const int half = ((P.Np / 2) + 15) / 16 * 16;
-    P.n0[0] = 0;
-    P.nsz[0] = half;
-    P.n0[1] = half;
-    P.nsz[1] = P.Np - half;
-  }
-  P.NBUF = (P.Np <= 256) ? 2 : 1;
-  P.spin = (float)spin;
-  P.g32 = g32;
-  P.V32 = V32;
-  P.VQ = VQ;
-  P.Sigma = Sigma;
-  P.S32 = S32;
-  P.err = err;
-  CUtensorMap th[2], tl[2];
+  return cudaGetLastError();
+}
+
+cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
+                      float *S32) {
+  d->g = tc_geom(n, M);
+  const long stack = (long)M * n * d->g.ld;
+  d->spin = (float)spin;
+  d->g32 = ws;
+  d->VQ = ws + 3 * stack;
+  d->V32 = ws + 4 * stack;
+  d->Sigma = Sigma;
+  d->S32 = S32;
   for (int t = 0; t < 2; ++t) {
-    e = make_tmap_rows(&th[t], gh, n, M, ld, P.nsz[t]);
-    if (e == cudaSuccess) e = make_tmap_rows(&tl[t], gl, n, M, ld, P.nsz[t]);
+    cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t]);
+    if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = sigma2_tc_smem_bytes(n);
-  e = cudaFuncSetAttribute(exchange_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  return cudaSuccess;
+}
+
+cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
+                               int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(Np_max, ld_max, true);
+  cudaError_t e = cudaFuncSetAttribute(exchange_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  long items = (long)M * n;
-  int grid = (int)(items < num_sms ? items : num_sms);
-  exchange_tc_kernel<<<grid, kThreads2, smem, s>>>(P, th[0], tl[0], th[1], tl[1]);
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  const int nbuf = (Np_max <= 256) ? 2 : 1;
+  exchange_tc_kernel<<<grid, kThreads2, smem, s>>>(sys, prefix, n_sys, items, Np_max, ld_max,
+                                                   nbuf, err);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,69 @@
+// Per-system descriptors of the tensor-core kernels. One persistent launch
+// walks a work queue that concatenates the items of every system in a table
+// (a batch of systems with different n_b and mesh sizes); a single system is a
+// table of one. Descriptors live in device memory and are written before the
+// launch; each holds its own TMA maps (CUtensorMap carries its own alignment).
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace fedvr {
+
+// Shared tile geometry of one system for the split-TF32 kernels.
+struct TcGeom {
+  int n, M, ld;     // basis size, mesh points, padded row pitch (n rounded up to 32)
+  int MT, NT, Np;   // 128-row M tiles, N tiles (1 or 2), N rounded up to 16
+  int KC;           // 32-wide contraction chunks per matrix
+  int NBUF;         // TMEM accumulator buffers (2 if Np <= 256)
+  int n0[2], nsz[2];
+};
+
+// Sigma^(2) exchange kernel: one system.
+struct XSys {
+  CUtensorMap th[2], tl[2];   // gb = G[M-1-j] split, per N tile
+  TcGeom g;
+  float spin;
+  const float *g32, *V32, *VQ;
+  double *Sigma;
+  float *S32;
+};
+
+// First convolution kernel: one system.
+struct C1Sys {
+  CUtensorMap th[2], tl[2];   // g_j split, per N tile
+  TcGeom g;
+  int JB;                     // mesh points per FP32 accumulation block
+  const float *S32;
+  const double *dHF;
+  const ConvCoef *coef;
+  double *I1;
+};
+
+TcGeom tc_geom(int n, int M);
+// Largest tile footprint over a table (smem bytes of the shared stage layout).
+size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns);
+
+// Host-side descriptor fill (tensor maps included); the caller copies the
+// descriptors to device memory.
+cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
+                      float *S32);
+cudaError_t c1sys_fill(C1Sys *d, int n, int M, const float *ws, const float *S32,
+                       const double *dHF, const ConvCoef *coef, double *I1);
+
+// Per-system preparation of the exchange operands (splits of G and V, VQ).
+cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
+                          cudaStream_t s);
+// Persistent launches over a device table of n_sys systems; prefix[n_sys + 1]
+// (device) holds the cumulative work items; Np_max/ld_max size the stages.
+cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
+                               int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s);
+cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
+                            int Np_max, int *err, int num_sms, cudaStream_t s);
+
+// Work items per system: exchange (j, b) pairs; convolution (i, M-tile) pairs.
+inline long exchange_items(int n, int M) { return (long)M * n; }
+inline long conv1_items(int n, int M) { return (long)M * ((n + 127) / 128); }
+
+}  // namespace fedvr

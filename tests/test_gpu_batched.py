@@ -1,0 +1,83 @@
+"""Batched second Born: systems of different n_b and mesh size advanced
+together by one tensor-core launch per kernel per iteration give exactly what
+the same systems give one at a time, and match the FP64 oracle's energy."""
+import numpy as np
+import pytest
+
+from oracle import fedvr_oracle as O
+from paper_0911_4348_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TF32 = 1
+
+
+def _systems():
+    a = W.he_small()                                                   # n=15, M=129
+    b = W.System("He n=39", -20.0, 20.0, 10, 4, [2.0], [0.0], u=2, p=16)   # n=39, M=65
+    c = W.System("H3+ n=59", -30.0, 30.0, 10, 6, [1.0, 1.0, 1.0], [-1.6, 0.0, 1.6], u=3, p=16)
+    d = W.System("He n=139", -40.0, 40.0, 20, 7, [1.8], [0.0], u=2, p=12)  # two M tiles
+    return [a, b, c, d]
+
+
+def _ctx(s):
+    from paper_0911_4348_gb300 import Context
+    c = Context()
+    c.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+    c.solve_hf(s.beta, tol=1e-12)
+    return c
+
+
+def test_batched_equals_single_system_solves():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import solve_2b_batched
+    systems = _systems()
+    single = []
+    for s in systems:
+        c = _ctx(s)
+        single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=TF32))
+        c.close()
+    ctxs = [_ctx(s) for s in systems]
+    out = solve_2b_batched(ctxs, [s.beta for s in systems], [s.u for s in systems],
+                           [s.p for s in systems], 0.5, 1e-8, 150, TF32)
+    for k, s in enumerate(systems):
+        assert out["iters"][k] == single[k]["iters"], s.name
+        assert out["E0"][k] == single[k]["E0"], s.name
+        assert out["N"][k] == single[k]["N"], s.name
+        hist = ctxs[k].get_history()
+        assert hist.shape[0] == out["iters"][k] and hist[-1, 1] < 1e-8
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_energy_matches_oracle_he_small():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import solve_2b_batched
+    s = W.he_small()
+    b = O.fedvr_basis(s.n_elem, s.order, s.xmin, s.xmax, 0)
+    T, v = O.kinetic(b), O.potential(b["nodes"], s.Z, s.R, 1.0)
+    V = O.interaction(b["nodes"], 1.0)
+    h = T + np.diag(v)
+    hf = O.hf_scf(h, V, 2.0, 1, s.beta, tol=1e-13)
+    ref = O.solve_2b(h, V, 2.0, hf, s.beta, s.u, s.p, 0.5, 1e-8, 100)
+    ctxs = [_ctx(s), _ctx(W.System("He n=39", -20.0, 20.0, 10, 4, [2.0], [0.0], u=2, p=16))]
+    out = solve_2b_batched(ctxs, [s.beta, 100.0], [s.u, 2], [s.p, 16])
+    assert abs(out["E0"][0] - ref["E0"]) < 1e-6
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_rejects_fp64_and_duplicates():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import FedvrError, solve_2b_batched
+    s = W.he_small()
+    c = _ctx(s)
+    with pytest.raises(FedvrError):
+        solve_2b_batched([c], [s.beta], [s.u], [s.p], precision=0)
+    with pytest.raises(FedvrError):
+        solve_2b_batched([c, c], [s.beta] * 2, [s.u] * 2, [s.p] * 2)
+    c.close()
