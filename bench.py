@@ -38,7 +38,8 @@ from paper_0911_4348_gb300 import workloads as W  # noqa: E402
 METRIC = "Sigma^(2) builds/s (one build + its Dyson iteration per step)"
 UNIT = "builds/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2}
-WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large}
+WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large,
+             "batch64": None}
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
 
@@ -202,6 +203,70 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, dist, rank, world, local):
+    """64 uneven systems (32 He, 32 H3+; n_b 59-239, 257-513 mesh points)
+    advanced together; a step is one batched iteration of every system."""
+    import torch
+    from paper_0911_4348_gb300 import Batch, Context, solve_2b_batched
+    systems = W.batch_systems(64, config_id=4 + 100 * rank)
+    stream = torch.cuda.current_stream()
+
+    def make():
+        ctxs = []
+        for s_ in systems:
+            c = Context(stream.cuda_stream)
+            c.build_fedvr(s_.n_elem, s_.order, s_.xmin, s_.xmax, s_.grid_kind)
+            c.set_potential(s_.Z, s_.R, s_.soft_en, s_.soft_ee, s_.n_elec)
+            c.solve_hf(s_.beta, tol=1e-12)
+            ctxs.append(c)
+        return ctxs
+
+    ctxs = make()
+    betas = [s_.beta for s_ in systems]
+    us, ps = [s_.u for s_ in systems], [s_.p for s_ in systems]
+    batch = Batch(ctxs, betas, us, ps)
+    for _ in range(args.warmup):
+        batch.step(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batch.step(0.5)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    batch.close()
+    n_sys = len(systems)
+    value = world * n_sys * args.steps / (elapsed / 1000.0)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
+           "config": {"workload": "batch of 64: 32 He (Z~U[1.5,2.5]) + 32 H3+ (R~U[1.2,3.0])",
+                      "n_b": [s_.n_b for s_ in systems], "n_tau": [s_.n_tau for s_ in systems],
+                      "precision": "tf32", "parallelism": f"replicas x{world}"}}
+    if not args.no_time_to_e0:
+        ctxs2 = make()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = solve_2b_batched(ctxs2, betas, us, ps, 0.5, 1e-8, 200, check=False)
+        torch.cuda.synchronize()
+        out["time_to_converge_all"] = {"seconds": time.perf_counter() - t0,
+                                       "max_iterations": int(np.max(r["iters"])),
+                                       "status": r["status"]}
+        for c in ctxs2:
+            c.close()
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,6 +293,11 @@ def main():
     from paper_0911_4348_gb300 import Context
 
     torch.cuda.set_device(local)
+    if args.workload == "batch64":
+        run_batch(args, dist, rank, world, local)
+        if dist:
+            dist.destroy_process_group()
+        return
     sys_ = WORKLOADS[args.workload]()
     prec = PRECISIONS[args.precision]
     stream = torch.cuda.current_stream()

@@ -189,14 +189,31 @@ int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_
 int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len);
 
 /* Batched solve over n_sys independent prepared contexts (each has run
- * build_fedvr, set_potential and solve_hf). Arrays have n_sys entries; the
- * per-system result pointers follow solve_2b (host outputs; any entry may be
- * NULL). All systems advance together, one batched launch per kernel per
- * iteration, on the stream of ctxs[0]; each stops updating when it
- * converges. Returns the worst status over systems. */
+ * build_fedvr, set_potential and solve_hf at its beta). Arrays have n_sys
+ * entries; the per-system results E0, N_out (host doubles) and iters (host
+ * ints) may be NULL. All systems advance together on the stream of ctxs[0]:
+ * per iteration one tensor-core launch per contraction kernel covers every
+ * unconverged system of the batch (a work queue over all systems' tiles), and
+ * each system stops updating when its residual is below tol. Requires
+ * precision FEDVR_SPLIT_TF32 and distinct contexts on one device. Returns the
+ * worst per-system status; each context keeps its history and its last
+ * g and Sigma (fedvr_2b_read). */
 int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u,
                      const int *p, double mixing, double tol, int max_iter, int precision,
                      double *E0, double *N_out, int *iters);
+
+/* The batch behind solve_2b_batched, for callers that drive the iteration:
+ * fedvr_batch_create prepares every context (fedvr_2b_prepare) and the device
+ * work tables; fedvr_batch_step runs one iteration of every active system
+ * (active[k] != 0, host int array, updated in place: a system whose residual
+ * falls below tol > 0 becomes inactive) and writes per-system res, E0, N (host
+ * arrays, may be NULL). The contexts must outlive the batch. */
+typedef struct fedvr_batch fedvr_batch;
+int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const double *beta,
+                       const int *u, const int *p, int precision);
+int fedvr_batch_step(fedvr_batch *b, double mixing, double tol, int *active, double *res,
+                     double *E0, double *N_out);
+void fedvr_batch_destroy(fedvr_batch *b);
 
 /* ---------------------------------------------------------------------- */
 /* Stage-level calls on caller device buffers (the hot-path kernels)       */

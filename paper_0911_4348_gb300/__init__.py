@@ -264,6 +264,45 @@ def solve_2b_batched(contexts, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
     return dict(E0=E0, N=N, iters=it, status=code)
 
 
+class Batch:
+    """A batch of prepared contexts stepped together (``fedvr_batch_*``)."""
+
+    def __init__(self, contexts, beta, u, p, precision=SPLIT_TF32):
+        self._lib = _native.lib()
+        self.contexts = list(contexts)
+        k = len(self.contexts)
+        handles = (C.c_void_p * k)(*[c.handle.value for c in self.contexts])
+        beta = np.ascontiguousarray(np.broadcast_to(beta, (k,)), dtype=np.float64)
+        u = np.ascontiguousarray(np.broadcast_to(u, (k,)), dtype=np.int32)
+        p = np.ascontiguousarray(np.broadcast_to(p, (k,)), dtype=np.int32)
+        self._h = C.c_void_p()
+        code = self._lib.fedvr_batch_create(C.byref(self._h), handles, k, _dptr(beta), _iptr(u),
+                                            _iptr(p), precision)
+        if code != 0:
+            raise FedvrError(code, self.contexts[0].last_error())
+        self.active = np.ones(k, dtype=np.int32)
+
+    def step(self, mixing=0.5, tol=0.0):
+        k = len(self.contexts)
+        res, E0, N = np.empty(k), np.empty(k), np.empty(k)
+        code = self._lib.fedvr_batch_step(self._h, mixing, tol, _iptr(self.active), _dptr(res),
+                                          _dptr(E0), _dptr(N))
+        if code != 0:
+            raise FedvrError(code, self.contexts[0].last_error())
+        return dict(res=res, E0=E0, N=N)
+
+    def close(self):
+        if self._h:
+            self._lib.fedvr_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
     """Allocation-free FP64 Sigma^(2) build (``fedvr_sigma2_noalloc``) for callers
     that cannot let the library allocate device memory. Limit M*n*n <= 2^19;
@@ -278,4 +317,4 @@ def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
         raise FedvrError(code, "fedvr_sigma2_noalloc failed")
 
 
-__all__ = ["solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]
+__all__ = ["Batch", "solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]

@@ -37,6 +37,10 @@ SIGNATURES = {
     "fedvr_get_history": (C.c_int, [_vp, _dp, C.c_int, _ip]),
     "solve_2b_batched": (C.c_int, [C.POINTER(_vp), C.c_int, _dp, _ip, _ip, C.c_double, C.c_double,
                                    C.c_int, C.c_int, _dp, _dp, _ip]),
+    "fedvr_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _dp, _ip, _ip,
+                                     C.c_int]),
+    "fedvr_batch_step": (C.c_int, [_vp, C.c_double, C.c_double, _ip, _dp, _dp, _dp]),
+    "fedvr_batch_destroy": (None, [_vp]),
     "fedvr_power_mesh": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
                                    _vp]),
     "fedvr_sigma2": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int]),

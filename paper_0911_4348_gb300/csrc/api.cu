@@ -758,9 +758,24 @@ int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len) {
   return FEDVR_OK;
 }
 
-int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u, const int *p,
-                     double mixing, double tol, int max_iter, int precision, double *E0,
-                     double *N_out, int *iters) {
+}  // extern "C"
+
+struct fedvr_batch {
+  std::vector<fedvr_ctx *> ctxs;
+  int Np_max = 16, ld_max = 32;
+  size_t off_c = 0, off_px = 0, off_pc = 0, off_err = 0, off_red = 0;
+  std::vector<long> px, pc;
+  std::vector<double> hred;
+  std::vector<double> best;
+  std::vector<int> grow;
+};
+
+extern "C" {
+
+int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const double *beta,
+                       const int *u, const int *p, int precision) {
+  if (!out) return FEDVR_ERR_ARG;
+  *out = nullptr;
   if (!ctxs || n_sys < 1 || n_sys > 4096 || !beta || !u || !p) return FEDVR_ERR_ARG;
   for (int k = 0; k < n_sys; ++k) {
     if (!ctxs[k]) return FEDVR_ERR_ARG;
@@ -769,137 +784,207 @@ int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int 
   fedvr_ctx *lead = ctxs[0];
   if (precision != FEDVR_SPLIT_TF32)
     return fail(lead, FEDVR_ERR_ARG, "the batched solve runs the split-TF32 tensor-core path");
-  if (!(mixing > 0.0 && mixing <= 1.0) || !(tol > 0.0) || max_iter < 1)
-    return fail(lead, FEDVR_ERR_ARG, "need 0 < mixing <= 1, tol > 0, max_iter >= 1");
   for (int k = 0; k < n_sys; ++k) {
     if (ctxs[k]->device != lead->device)
       return fail(lead, FEDVR_ERR_ARG, "all systems must be on one device");
     for (int q = 0; q < k; ++q)
       if (ctxs[q] == ctxs[k]) return fail(lead, FEDVR_ERR_ARG, "a context appears twice");
   }
+  fedvr_batch *B = new (std::nothrow) fedvr_batch();
+  if (!B) return fail(lead, FEDVR_ERR_ARG, "out of host memory");
+  B->ctxs.assign(ctxs, ctxs + n_sys);
   cudaStream_t s = lead->stream;
-  // per-system preparation (mesh, g^0, tables, workspace) on each context
-  int Np_max = 16, ld_max = 32;
   for (int k = 0; k < n_sys; ++k) {
     if (int r = fedvr_2b_prepare(ctxs[k], beta[k], u[k], p[k], precision)) {
       fail(lead, r, "system %d: %s", k, ctxs[k]->err);
+      delete B;
       return r;
     }
     const TcGeom g = tc_geom(ctxs[k]->n, ctxs[k]->M);
-    Np_max = g.Np > Np_max ? g.Np : Np_max;
-    ld_max = g.ld > ld_max ? g.ld : ld_max;
+    B->Np_max = g.Np > B->Np_max ? g.Np : B->Np_max;
+    B->ld_max = g.ld > B->ld_max ? g.ld : B->ld_max;
   }
-  // the batch tables: descriptors of every system, prefixes rebuilt per iteration
+  if (tc_smem_bytes(B->Np_max, B->ld_max, true) > 232448) {
+    delete B;
+    return fail(lead, FEDVR_ERR_ARG, "batch too wide for one shared-memory stage layout");
+  }
   const size_t xs = (size_t)n_sys * sizeof(XSys), cs = (size_t)n_sys * sizeof(C1Sys);
-  const size_t off_c = (xs + 255) / 256 * 256, off_px = off_c + (cs + 255) / 256 * 256;
-  const size_t off_pc = off_px + ((size_t)(n_sys + 1) * sizeof(long) + 255) / 256 * 256;
-  const size_t off_err = off_pc + ((size_t)(n_sys + 1) * sizeof(long) + 255) / 256 * 256;
-  const size_t off_red = off_err + 256;
-  ENSURE(lead, w_btab, off_red + (size_t)n_sys * 3 * sizeof(double));
+  const size_t pfx = ((size_t)(n_sys + 1) * sizeof(long) + 255) / 256 * 256;
+  B->off_c = (xs + 255) / 256 * 256;
+  B->off_px = B->off_c + (cs + 255) / 256 * 256;
+  B->off_pc = B->off_px + pfx;
+  B->off_err = B->off_pc + pfx;
+  B->off_red = B->off_err + 256;
+  if (!ensure(lead, lead->w_btab, B->off_red + (size_t)n_sys * 3 * sizeof(double), "w_btab")) {
+    delete B;
+    return FEDVR_ERR_CUDA;
+  }
   uint8_t *bt = P<uint8_t>(lead->w_btab);
-  {
-    std::vector<XSys> hx(n_sys);
-    std::vector<C1Sys> hc(n_sys);
-    for (int k = 0; k < n_sys; ++k) {
-      fedvr_ctx *c = ctxs[k];
-      float *ws, *S32;
-      int *err;
-      if (int r = tc_workspace(c, c->n, c->M, &ws, &S32, &err)) return r;
-      memset(&hx[k], 0, sizeof(XSys));
-      memset(&hc[k], 0, sizeof(C1Sys));
-      FEDVR_CK(lead, xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32));
-      FEDVR_CK(lead, c1sys_fill(&hc[k], c->n, c->M, ws, S32, P<double>(c->w_dHF),
-                                P<ConvCoef>(c->w_coef), P<double>(c->w_I1)));
+  std::vector<XSys> hx(n_sys);
+  std::vector<C1Sys> hc(n_sys);
+  for (int k = 0; k < n_sys; ++k) {
+    fedvr_ctx *c = ctxs[k];
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(c, c->n, c->M, &ws, &S32, &err)) {
+      delete B;
+      return r;
     }
-    FEDVR_CK(lead, cudaMemcpyAsync(bt, hx.data(), xs, cudaMemcpyHostToDevice, s));
-    FEDVR_CK(lead, cudaMemcpyAsync(bt + off_c, hc.data(), cs, cudaMemcpyHostToDevice, s));
-    FEDVR_CK(lead, cudaMemsetAsync(bt + off_err, 0, sizeof(int), s));
-    if (int r = sync(lead)) return r;
+    memset(&hx[k], 0, sizeof(XSys));
+    memset(&hc[k], 0, sizeof(C1Sys));
+    cudaError_t e = xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32);
+    if (e == cudaSuccess)
+      e = c1sys_fill(&hc[k], c->n, c->M, ws, S32, P<double>(c->w_dHF), P<ConvCoef>(c->w_coef),
+                     P<double>(c->w_I1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bt + k * sizeof(XSys), &hx[k], sizeof(XSys),
+                                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bt + B->off_c + k * sizeof(C1Sys), &hc[k],
+                                              sizeof(C1Sys), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      delete B;
+      return cuda_fail(lead, e, "batch tables", __FILE__, __LINE__);
+    }
   }
-  int *d_err = reinterpret_cast<int *>(bt + off_err);
-  std::vector<char> active(n_sys, 1);
-  std::vector<double> res(n_sys, INFINITY), best(n_sys, INFINITY), hred(3 * (size_t)n_sys);
-  std::vector<int> grow(n_sys, 0), done_it(n_sys, 0), status(n_sys, FEDVR_OK);
-  std::vector<long> px(n_sys + 1), pc(n_sys + 1);
-  int remaining = n_sys;
-  for (int it = 0; it < max_iter && remaining > 0; ++it) {
-    auto t0 = std::chrono::steady_clock::now();
-    px[0] = pc[0] = 0;
-    for (int k = 0; k < n_sys; ++k) {
-      const int n = ctxs[k]->n, M = ctxs[k]->M;
-      px[k + 1] = px[k] + (active[k] ? exchange_items(n, M) : 0);
-      pc[k + 1] = pc[k] + (active[k] ? conv1_items(n, M) : 0);
-    }
-    FEDVR_CK(lead, cudaMemcpyAsync(bt + off_px, px.data(), (n_sys + 1) * sizeof(long),
-                                   cudaMemcpyHostToDevice, s));
-    FEDVR_CK(lead, cudaMemcpyAsync(bt + off_pc, pc.data(), (n_sys + 1) * sizeof(long),
-                                   cudaMemcpyHostToDevice, s));
-    int launches = 0;
-    for (int k = 0; k < n_sys; ++k)
-      if (active[k]) {
-        if (int r = phase_sigma_pre(ctxs[k], false, s, &launches)) return r;
-      }
-    FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
-                                      reinterpret_cast<const long *>(bt + off_px), n_sys,
-                                      px[n_sys], Np_max, ld_max, d_err, lead->num_sms, s));
-    for (int k = 0; k < n_sys; ++k)
-      if (active[k]) {
-        if (int r = phase_mid(ctxs[k], s, &launches)) return r;
-      }
-    FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + off_c),
-                                   reinterpret_cast<const long *>(bt + off_pc), n_sys, pc[n_sys],
-                                   Np_max, d_err, lead->num_sms, s));
-    for (int k = 0; k < n_sys; ++k)
-      if (active[k]) {
-        if (int r = phase_conv2(ctxs[k], s, &launches)) return r;
-        if (int r = phase_update(ctxs[k], mixing, s, &launches)) return r;
-        FEDVR_CK(lead, cudaMemcpyAsync(bt + off_red + (size_t)k * 3 * sizeof(double),
-                                       ctxs[k]->w_red.ptr, 3 * sizeof(double),
-                                       cudaMemcpyDeviceToDevice, s));
-      }
-    FEDVR_CK(lead, cudaMemcpyAsync(hred.data(), bt + off_red, hred.size() * sizeof(double),
-                                   cudaMemcpyDeviceToHost, s));
-    int h_err = 0;
-    FEDVR_CK(lead, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (int r = sync(lead)) return r;
-    if (h_err) return fail(lead, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
-    const double ms =
-        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    for (int k = 0; k < n_sys; ++k) {
-      if (!active[k]) continue;
-      fedvr_ctx *c = ctxs[k];
-      const double E = hred[3 * k], Nel = hred[3 * k + 1], r = hred[3 * k + 2];
-      double rec[5] = {(double)c->step_k, r, E, Nel, ms};
-      c->history.insert(c->history.end(), rec, rec + 5);
-      c->step_k++;
-      done_it[k] = it + 1;
-      if (E0) E0[k] = E;
-      if (N_out) N_out[k] = Nel;
-      bool stop = false;
-      if (r != r || !is_fin(E)) {
-        status[k] = fail(c, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", it);
-        stop = true;
-      } else if (r < tol) {
-        stop = true;
-      } else if (r < best[k]) {
-        best[k] = r;
-        grow[k] = 0;
-      } else if (++grow[k] >= 8) {
-        status[k] = fail(c, FEDVR_ERR_DIVERGED, "residual grew for 8 iterations (at %d)", it);
-        stop = true;
-      }
-      if (stop) {
-        active[k] = 0;
-        --remaining;
-      }
-    }
-    lead->step_launches = launches + 2;
+  if (cudaMemsetAsync(bt + B->off_err, 0, sizeof(int), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    delete B;
+    return cuda_fail(lead, cudaGetLastError(), "batch tables", __FILE__, __LINE__);
   }
+  B->px.assign(n_sys + 1, 0);
+  B->pc.assign(n_sys + 1, 0);
+  B->hred.assign(3 * (size_t)n_sys, 0.0);
+  B->best.assign(n_sys, INFINITY);
+  B->grow.assign(n_sys, 0);
+  *out = B;
+  return FEDVR_OK;
+}
+
+void fedvr_batch_destroy(fedvr_batch *b) { delete b; }
+
+int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, double *res_out,
+                     double *E0, double *N_out) {
+  if (!B || !active) return FEDVR_ERR_ARG;
+  fedvr_ctx *lead = B->ctxs[0];
+  CHECK_CTX(lead);
+  if (!(mixing > 0.0 && mixing <= 1.0)) return fail(lead, FEDVR_ERR_ARG, "need 0 < mixing <= 1");
+  const int n_sys = (int)B->ctxs.size();
+  cudaStream_t s = lead->stream;
+  uint8_t *bt = P<uint8_t>(lead->w_btab);
+  auto t0 = std::chrono::steady_clock::now();
+  B->px[0] = B->pc[0] = 0;
+  for (int k = 0; k < n_sys; ++k) {
+    const fedvr_ctx *c = B->ctxs[k];
+    if (!c->prepared) return fail(lead, FEDVR_ERR_STATE, "system %d is no longer prepared", k);
+    B->px[k + 1] = B->px[k] + (active[k] ? exchange_items(c->n, c->M) : 0);
+    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M) : 0);
+  }
+  if (B->px[n_sys] == 0) return FEDVR_OK;
+  FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_px, B->px.data(), (n_sys + 1) * sizeof(long),
+                                 cudaMemcpyHostToDevice, s));
+  FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_pc, B->pc.data(), (n_sys + 1) * sizeof(long),
+                                 cudaMemcpyHostToDevice, s));
+  int *d_err = reinterpret_cast<int *>(bt + B->off_err);
+  int launches = 0;
+  for (int k = 0; k < n_sys; ++k)
+    if (active[k]) {
+      if (int r = phase_sigma_pre(B->ctxs[k], false, s, &launches)) return r;
+    }
+  FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
+                                    reinterpret_cast<const long *>(bt + B->off_px), n_sys,
+                                    B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s));
+  for (int k = 0; k < n_sys; ++k)
+    if (active[k]) {
+      if (int r = phase_mid(B->ctxs[k], s, &launches)) return r;
+    }
+  FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + B->off_c),
+                                 reinterpret_cast<const long *>(bt + B->off_pc), n_sys,
+                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s));
+  for (int k = 0; k < n_sys; ++k)
+    if (active[k]) {
+      fedvr_ctx *c = B->ctxs[k];
+      if (int r = phase_conv2(c, s, &launches)) return r;
+      if (int r = phase_update(c, mixing, s, &launches)) return r;
+      FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_red + (size_t)k * 3 * sizeof(double),
+                                     c->w_red.ptr, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     s));
+    }
+  FEDVR_CK(lead, cudaMemcpyAsync(B->hred.data(), bt + B->off_red, B->hred.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+  int h_err = 0;
+  FEDVR_CK(lead, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (int r = sync(lead)) return r;
+  if (h_err) return fail(lead, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  lead->step_launches = launches + 2;
   int worst = FEDVR_OK;
   for (int k = 0; k < n_sys; ++k) {
-    if (active[k]) status[k] = fail(ctxs[k], FEDVR_ERR_NOCONV, "not converged after %d iterations",
-                                    max_iter);
-    if (iters) iters[k] = done_it[k];
+    if (!active[k]) continue;
+    fedvr_ctx *c = B->ctxs[k];
+    const double E = B->hred[3 * k], Nel = B->hred[3 * k + 1], r = B->hred[3 * k + 2];
+    double rec[5] = {(double)c->step_k, r, E, Nel, ms};
+    c->history.insert(c->history.end(), rec, rec + 5);
+    c->step_k++;
+    if (res_out) res_out[k] = r;
+    if (E0) E0[k] = E;
+    if (N_out) N_out[k] = Nel;
+    if (r != r || !is_fin(E)) {
+      worst = fail(c, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", c->step_k - 1);
+      active[k] = 0;
+    } else if (tol > 0.0 && r < tol) {
+      active[k] = 0;
+    }
+  }
+  return worst;
+}
+
+int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u, const int *p,
+                     double mixing, double tol, int max_iter, int precision, double *E0,
+                     double *N_out, int *iters) {
+  if (!ctxs || n_sys < 1) return FEDVR_ERR_ARG;
+  if (!(mixing > 0.0 && mixing <= 1.0) || !(tol > 0.0) || max_iter < 1)
+    return ctxs[0] ? fail(ctxs[0], FEDVR_ERR_ARG, "need 0 < mixing <= 1, tol > 0, max_iter >= 1")
+                   : FEDVR_ERR_ARG;
+  fedvr_batch *B = nullptr;
+  if (int r = fedvr_batch_create(&B, ctxs, n_sys, beta, u, p, precision)) return r;
+  std::vector<int> active(n_sys, 1), status(n_sys, FEDVR_OK), done(n_sys, 0);
+  std::vector<double> res(n_sys, INFINITY), best(n_sys, INFINITY), e(n_sys, 0.0), nn(n_sys, 0.0);
+  std::vector<int> grow(n_sys, 0);
+  for (int it = 0; it < max_iter; ++it) {
+    int remaining = 0;
+    for (int k = 0; k < n_sys; ++k) remaining += active[k] != 0;
+    if (!remaining) break;
+    std::vector<int> was(active);
+    int r = fedvr_batch_step(B, mixing, tol, active.data(), res.data(), e.data(), nn.data());
+    if (r != FEDVR_OK && r != FEDVR_ERR_NAN) {
+      fedvr_batch_destroy(B);
+      return r;
+    }
+    for (int k = 0; k < n_sys; ++k) {
+      if (!was[k]) continue;
+      done[k] = it + 1;
+      if (E0) E0[k] = e[k];
+      if (N_out) N_out[k] = nn[k];
+      if (res[k] != res[k]) {
+        status[k] = FEDVR_ERR_NAN;
+      } else if (active[k]) {  // still running: watch for a growing residual
+        if (res[k] < best[k]) {
+          best[k] = res[k];
+          grow[k] = 0;
+        } else if (++grow[k] >= 8) {
+          status[k] = fail(ctxs[k], FEDVR_ERR_DIVERGED, "residual grew for 8 iterations (at %d)",
+                           it);
+          active[k] = 0;
+        }
+      }
+    }
+  }
+  fedvr_batch_destroy(B);
+  int worst = FEDVR_OK;
+  for (int k = 0; k < n_sys; ++k) {
+    if (active[k])
+      status[k] = fail(ctxs[k], FEDVR_ERR_NOCONV, "not converged after %d iterations", max_iter);
+    if (iters) iters[k] = done[k];
     if (status[k] < worst) worst = status[k];
   }
   return worst;
