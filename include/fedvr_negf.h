@@ -178,10 +178,15 @@ int fedvr_2b_read(fedvr_ctx *ctx, int out_on_device, double *G_out, double *Sigm
  * number of kernels that step launched. ms is a host array of 6 doubles. */
 int fedvr_stage_times(const fedvr_ctx *ctx, double *ms, int *launches);
 
-/* Start the next solve_2b from this Sigma^corr in its first iteration instead
- * of Sigma^corr[g^0] (warm start). Sigma0 is [M][n_b][n_b] on host or device;
- * M must match the next solve's mesh. Pass NULL to clear. Copied at once. */
-int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_device);
+/* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
+ * [M][n_b][n_b] on host or device; M must match the next solve's mesh; copied
+ * at once; NULL clears. inner_steps = 0: the first iteration uses Sigma0
+ * instead of Sigma^corr[g^0]. inner_steps > 0: the first inner_steps
+ * iterations keep Sigma0 fixed and take the full Dyson step (no mixing), so g
+ * moves to the Green's function of Sigma0 before the regular iteration
+ * starts; no convergence test is made during them. */
+int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_device,
+                            int inner_steps);
 
 /* Per-iteration record of the last solve_2b: 5 doubles per iteration
  * (iteration, residual, E0, N, wall milliseconds). Copies min(cap, count)
@@ -214,6 +219,51 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
 int fedvr_batch_step(fedvr_batch *b, double mixing, double tol, int *active, double *res,
                      double *E0, double *N_out);
 void fedvr_batch_destroy(fedvr_batch *b);
+
+/* ---------------------------------------------------------------------- */
+/* Learned warm start (no counterpart in the paper)                        */
+/* ---------------------------------------------------------------------- */
+
+/* A per-(a, b)-pair network that predicts the converged self-energy of a new
+ * system from its one-shot Sigma^(2)[g^0]: input [S1_ab(tau)/s (M values),
+ * g^0_ab(tau) (M), V_ab, x_a/L, x_b/L] (s = max|S1|, L = box length), hidden
+ * ReLU layers of `hidden` units, output Delta_ab(tau)/s (M) with
+ * Sigma_pred = S1 + s * Delta. FP32 master weights (He-normal initialisation
+ * from `seed`), Adam training, BF16 inference; all on the GPU. M is fixed
+ * per network (the mesh size it serves); n_b may differ between systems. */
+typedef struct fedvr_mlp fedvr_mlp;
+int fedvr_mlp_create(fedvr_mlp **out, int M, int hidden, unsigned long long seed,
+                     void *cuda_stream);
+void fedvr_mlp_destroy(fedvr_mlp *m);
+const char *fedvr_mlp_last_error(const fedvr_mlp *m);
+/* Parameter vector: W1 [2M+3][hidden], b1, W2 [hidden][hidden], b2,
+ * W3 [hidden][M], b3, row-major, FP32, host buffers of *count floats. */
+int fedvr_mlp_num_params(const fedvr_mlp *m, long *count);
+int fedvr_mlp_get_params(fedvr_mlp *m, float *params, long count);
+int fedvr_mlp_set_params(fedvr_mlp *m, const float *params, long count);
+/* Loss sum (y-t)^2 / (2 rows M) and its gradient (host, num_params floats) for
+ * device rows X [rows][2M+3], T [rows][M], FP32 weights. */
+int fedvr_mlp_loss_grad(fedvr_mlp *m, const float *X, const float *T, int rows, float *grad,
+                        double *loss);
+/* y = net(X) for device rows; bf16 != 0 uses the BF16 weights (as updated by
+ * the last fedvr_mlp_train or fedvr_mlp_set_params). */
+int fedvr_mlp_forward(fedvr_mlp *m, const float *X, int rows, float *Y, int bf16);
+/* Run a plain split-TF32 solve_2b on ctx (HF solved, mesh with M points) and
+ * add the system's pairs (features, scaled converged correction) to the
+ * training set if it converged. *iters (may be NULL) = iterations used. */
+int fedvr_mlp_collect(fedvr_mlp *m, fedvr_ctx *ctx, double beta, int u, int p, double mixing,
+                      double tol, int max_iter, int *iters);
+/* Adam over the training set: `epochs` shuffled passes of `batch` rows at
+ * learning rate lr; *final_loss (may be NULL) = mean loss of the last pass;
+ * refreshes the BF16 weights. Training rows: fedvr_mlp_rows. */
+int fedvr_mlp_train(fedvr_mlp *m, int epochs, int batch, double lr, double *final_loss);
+int fedvr_mlp_rows(const fedvr_mlp *m, long *rows);
+/* Copy `count` collected training rows starting at `start` to host buffers
+ * X [count][2M+3] and T [count][M] (either may be NULL). */
+int fedvr_mlp_get_rows(fedvr_mlp *m, long start, long count, float *X, float *T);
+/* Predict Sigma for ctx's next solve_2b at (beta, u, p) with the BF16 weights
+ * and set it with fedvr_set_initial_sigma(..., inner_steps). */
+int fedvr_warm_start(fedvr_ctx *ctx, fedvr_mlp *m, double beta, int u, int p, int inner_steps);
 
 /* ---------------------------------------------------------------------- */
 /* Stage-level calls on caller device buffers (the hot-path kernels)       */

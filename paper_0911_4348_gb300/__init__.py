@@ -203,13 +203,21 @@ class Context:
         on_dev = 1 if kinds == {True} else 0
         self._check(self._lib.fedvr_2b_read(self._h, on_dev, outs[0][0], outs[1][0], outs[2][0]))
 
-    def set_initial_sigma(self, Sigma0, M=None):
+    def set_initial_sigma(self, Sigma0, M=None, inner_steps=0):
         if Sigma0 is None:
-            self._check(self._lib.fedvr_set_initial_sigma(self._h, None, 0, 0))
+            self._check(self._lib.fedvr_set_initial_sigma(self._h, None, 0, 0, 0))
             return
         ptr, dev = _host_or_dev(Sigma0)
         M = Sigma0.shape[0] if M is None else M
-        self._check(self._lib.fedvr_set_initial_sigma(self._h, ptr, M, 1 if dev else 0))
+        self._check(self._lib.fedvr_set_initial_sigma(self._h, ptr, M, 1 if dev else 0,
+                                                      inner_steps))
+
+    def warm_start(self, mlp, beta, u, p, inner_steps=4):
+        """Predict the converged Sigma with the network and set it as the warm
+        start of the next solve_2b (``fedvr_warm_start``)."""
+        code = self._lib.fedvr_warm_start(self._h, mlp.handle, beta, u, p, inner_steps)
+        if code != 0:
+            raise FedvrError(code, mlp.last_error() or self.last_error())
 
     def get_history(self) -> np.ndarray:
         ln = C.c_int()
@@ -303,6 +311,99 @@ class Batch:
             pass
 
 
+def _fptr(arr):
+    if arr is None:
+        return None
+    assert arr.dtype == np.float32 and arr.flags["C_CONTIGUOUS"]
+    return arr.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class WarmStartNet:
+    """The per-pair warm-start network (``fedvr_mlp_*``)."""
+
+    def __init__(self, M, hidden=512, seed=9114348, stream=None):
+        self._lib = _native.lib()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = C.c_void_p()
+        code = self._lib.fedvr_mlp_create(C.byref(self._h), M, hidden, seed, C.c_void_p(stream))
+        if code != 0:
+            raise FedvrError(code, "fedvr_mlp_create failed")
+        self.M, self.hidden = M, hidden
+
+    @property
+    def handle(self):
+        return self._h
+
+    def last_error(self):
+        return self._lib.fedvr_mlp_last_error(self._h).decode()
+
+    def _check(self, code):
+        if code != 0:
+            raise FedvrError(code, self.last_error())
+
+    def num_params(self):
+        n = C.c_long()
+        self._check(self._lib.fedvr_mlp_num_params(self._h, C.byref(n)))
+        return n.value
+
+    def get_params(self):
+        out = np.empty(self.num_params(), dtype=np.float32)
+        self._check(self._lib.fedvr_mlp_get_params(self._h, _fptr(out), out.size))
+        return out
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._lib.fedvr_mlp_set_params(self._h, _fptr(params), params.size))
+
+    def loss_grad(self, X, T):
+        """X, T: float32 CUDA tensors [rows][2M+3], [rows][M]."""
+        grad = np.empty(self.num_params(), dtype=np.float32)
+        loss = C.c_double()
+        self._check(self._lib.fedvr_mlp_loss_grad(self._h, C.c_void_p(X.data_ptr()),
+                                                  C.c_void_p(T.data_ptr()), X.shape[0],
+                                                  _fptr(grad), C.byref(loss)))
+        return loss.value, grad
+
+    def forward(self, X, Y, bf16=False):
+        self._check(self._lib.fedvr_mlp_forward(self._h, C.c_void_p(X.data_ptr()), X.shape[0],
+                                                C.c_void_p(Y.data_ptr()), 1 if bf16 else 0))
+
+    def collect(self, ctx, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200):
+        it = C.c_int()
+        self._check(self._lib.fedvr_mlp_collect(self._h, ctx.handle, beta, u, p, mixing, tol,
+                                                max_iter, C.byref(it)))
+        return it.value
+
+    def rows(self):
+        n = C.c_long()
+        self._check(self._lib.fedvr_mlp_rows(self._h, C.byref(n)))
+        return n.value
+
+    def get_rows(self, start, count):
+        X = np.empty((count, 2 * self.M + 3), dtype=np.float32)
+        T = np.empty((count, self.M), dtype=np.float32)
+        self._check(self._lib.fedvr_mlp_get_rows(self._h, start, count, _fptr(X), _fptr(T)))
+        return X, T
+
+    def train(self, epochs, batch=4096, lr=1e-3):
+        loss = C.c_double()
+        self._check(self._lib.fedvr_mlp_train(self._h, epochs, batch, lr, C.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self._h:
+            self._lib.fedvr_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
     """Allocation-free FP64 Sigma^(2) build (``fedvr_sigma2_noalloc``) for callers
     that cannot let the library allocate device memory. Limit M*n*n <= 2^19;
@@ -317,4 +418,4 @@ def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
         raise FedvrError(code, "fedvr_sigma2_noalloc failed")
 
 
-__all__ = ["Batch", "solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]
+__all__ = ["WarmStartNet", "Batch", "solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]

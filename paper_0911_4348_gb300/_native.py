@@ -33,7 +33,7 @@ SIGNATURES = {
     "fedvr_2b_step": (C.c_int, [_vp, C.c_double, _vp, C.c_int, _dp, _dp, _dp]),
     "fedvr_2b_read": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "fedvr_stage_times": (C.c_int, [_vp, _dp, _ip]),
-    "fedvr_set_initial_sigma": (C.c_int, [_vp, _vp, C.c_int, C.c_int]),
+    "fedvr_set_initial_sigma": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int]),
     "fedvr_get_history": (C.c_int, [_vp, _dp, C.c_int, _ip]),
     "solve_2b_batched": (C.c_int, [C.POINTER(_vp), C.c_int, _dp, _ip, _ip, C.c_double, C.c_double,
                                    C.c_int, C.c_int, _dp, _dp, _ip]),
@@ -41,6 +41,21 @@ SIGNATURES = {
                                      C.c_int]),
     "fedvr_batch_step": (C.c_int, [_vp, C.c_double, C.c_double, _ip, _dp, _dp, _dp]),
     "fedvr_batch_destroy": (None, [_vp]),
+    "fedvr_mlp_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, C.c_ulonglong, _vp]),
+    "fedvr_mlp_destroy": (None, [_vp]),
+    "fedvr_mlp_last_error": (C.c_char_p, [_vp]),
+    "fedvr_mlp_num_params": (C.c_int, [_vp, C.POINTER(C.c_long)]),
+    "fedvr_mlp_get_params": (C.c_int, [_vp, C.POINTER(C.c_float), C.c_long]),
+    "fedvr_mlp_set_params": (C.c_int, [_vp, C.POINTER(C.c_float), C.c_long]),
+    "fedvr_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_float), _dp]),
+    "fedvr_mlp_forward": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int]),
+    "fedvr_mlp_collect": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double,
+                                    C.c_int, _ip]),
+    "fedvr_mlp_train": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _dp]),
+    "fedvr_mlp_rows": (C.c_int, [_vp, C.POINTER(C.c_long)]),
+    "fedvr_mlp_get_rows": (C.c_int, [_vp, C.c_long, C.c_long, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float)]),
+    "fedvr_warm_start": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_int, C.c_int]),
     "fedvr_power_mesh": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
                                    _vp]),
     "fedvr_sigma2": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int]),

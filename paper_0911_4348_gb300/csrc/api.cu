@@ -277,6 +277,30 @@ int tc_err_ptr(fedvr_ctx *ctx, int **err) {
 
 }  // namespace
 
+int fedvr::sigma_of_current_g(fedvr_ctx *ctx) {
+  if (!ctx->prepared) return fail(ctx, FEDVR_ERR_STATE, "no prepared second-Born run");
+  cudaStream_t s = ctx->stream;
+  int launches = 0;
+  if (int r = phase_sigma_pre(ctx, false, s, &launches)) return r;
+  if (ctx->precision == FEDVR_SPLIT_TF32) {
+    int *err = nullptr;
+    if (int r = tc_err_ptr(ctx, &err)) return r;
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    const TcGeom g = tc_geom(ctx->n, ctx->M);
+    uint8_t *tab = P<uint8_t>(ctx->w_tab);
+    FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
+                                     reinterpret_cast<const long *>(tab + kTabPX), 1,
+                                     exchange_items(ctx->n, ctx->M), g.Np, g.ld, err,
+                                     ctx->num_sms, s));
+    int h_err = 0;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (int r = sync(ctx)) return r;
+    if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+    return FEDVR_OK;
+  }
+  return sync(ctx);
+}
+
 extern "C" {
 
 int fedvr_create(fedvr_ctx **out, void *cuda_stream) {
@@ -538,11 +562,17 @@ int fedvr_get_hf(const fedvr_ctx *cctx, double *eps, double *C, double *rho0, do
   return sync(ctx);
 }
 
-int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_device) {
+int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_device,
+                            int inner_steps) {
   CHECK_CTX(ctx);
   if (ctx->stage < 1) return fail(ctx, FEDVR_ERR_STATE, "no basis");
-  if (!Sigma0) { ctx->sigma_init_M = 0; return FEDVR_OK; }
+  if (!Sigma0) {
+    ctx->sigma_init_M = 0;
+    ctx->warm_inner = 0;
+    return FEDVR_OK;
+  }
   if (M < 3 || M > 4097) return fail(ctx, FEDVR_ERR_ARG, "M outside [3, 4097]");
+  if (inner_steps < 0 || inner_steps > 64) return fail(ctx, FEDVR_ERR_ARG, "inner_steps outside [0, 64]");
   size_t cnt = (size_t)M * ctx->n * ctx->n;
   ENSURE(ctx, b_sigma_init, dsz(cnt));
   FEDVR_CK(ctx, cudaMemcpyAsync(ctx->b_sigma_init.ptr, Sigma0, dsz(cnt),
@@ -550,6 +580,7 @@ int fedvr_set_initial_sigma(fedvr_ctx *ctx, const double *Sigma0, int M, int on_
                                 ctx->stream));
   if (int r = sync(ctx)) return r;
   ctx->sigma_init_M = M;
+  ctx->warm_inner = inner_steps;
   return FEDVR_OK;
 }
 
@@ -643,7 +674,9 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
     FEDVR_CK(ctx, cudaMemcpyAsync(G, G_in, dsz(stack),
                                   in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[1], s));
-  const bool warm = ctx->step_k == 0 && ctx->sigma_init_M;
+  const bool warm = ctx->sigma_init_M &&
+                    ctx->step_k < (ctx->warm_inner > 0 ? ctx->warm_inner : 1);
+  if (warm && ctx->warm_inner > 0) mixing = 1.0;  // full Dyson step at the fixed warm-start Sigma
   if (int r = phase_sigma_pre(ctx, warm, s, &launches)) return r;
   uint8_t *tab = P<uint8_t>(ctx->w_tab);
   if (split && !warm) {
@@ -712,10 +745,12 @@ int solve_2b(fedvr_ctx *ctx, double beta, int u, int p, double mixing, double to
   double E = 0, Nel = 0, res = INFINITY, best = INFINITY;
   int grow = 0, k = 0, status = FEDVR_OK;
   bool conv = false;
+  const int inner = ctx->sigma_init_M ? ctx->warm_inner : 0;
   for (k = 0; k < max_iter; ++k) {
     int r = fedvr_2b_step(ctx, mixing, nullptr, 0, &res, &E, &Nel);
     if (r == FEDVR_ERR_NAN) { status = r; break; }
     if (r) return r;
+    if (k < inner) continue;  // fixed-Sigma warm-start steps
     if (res < tol) { conv = true; break; }
     if (res < best) { best = res; grow = 0; } else if (++grow >= 8) {
       status = fail(ctx, FEDVR_ERR_DIVERGED, "residual grew for 8 iterations (at %d)", k);
@@ -727,6 +762,7 @@ int solve_2b(fedvr_ctx *ctx, double beta, int u, int p, double mixing, double to
     status = fail(ctx, FEDVR_ERR_NOCONV, "not converged after %d iterations (res %.3e)", max_iter, res);
   if (int r = fedvr_2b_read(ctx, out_on_device, G_out, Sigma_out, tau_out)) return r;
   ctx->sigma_init_M = 0;
+  ctx->warm_inner = 0;
   if (E0) *E0 = E;
   if (N_out) *N_out = Nel;
   if (iters) *iters = done;

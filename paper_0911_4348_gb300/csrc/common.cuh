@@ -40,6 +40,7 @@ struct fedvr_ctx {
   int hf_iters = 0;
   // warm start
   int sigma_init_M = 0;
+  int warm_inner = 0;
   // prepared second-Born run
   bool prepared = false;
   int u = 0, p = 0, M = 0, precision = 0, step_k = 0;
@@ -65,6 +66,9 @@ struct fedvr_ctx {
 namespace fedvr {
 
 int fail(fedvr_ctx *ctx, int code, const char *fmt, ...);
+// Sigma^corr[g] of the current iterate of a prepared context into its Sigma
+// workspace (split-TF32 or FP64 per the prepared precision); synchronous.
+int sigma_of_current_g(fedvr_ctx *ctx);
 int cuda_fail(fedvr_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
 // Ensure buf holds at least `bytes`; returns false (and records the error) on failure.
 bool ensure(fedvr_ctx *ctx, DevBuf &buf, size_t bytes, const char *name);

@@ -15,7 +15,7 @@
 
 #include <vector>
 
-#include "common.cuh"
+#include "mlp.cuh"
 
 namespace fedvr {
 namespace {
@@ -237,11 +237,6 @@ __global__ void scatter_kernel(int n, int M, const double *__restrict__ S1,
 }  // namespace
 
 // ---- host-side network ----
-struct MlpNet {
-  int din = 0, H = 0, dout = 0;
-  long o_W1 = 0, o_b1 = 0, o_W2 = 0, o_b2 = 0, o_W3 = 0, o_b3 = 0, nparam = 0;
-};
-
 MlpNet mlp_layout(int M, int H) {
   MlpNet L;
   L.din = 2 * M + 3;
