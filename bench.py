@@ -13,8 +13,10 @@ Every rank runs its own replica of the workload (independent systems, weak
 scaling); ranks only meet at the timing barrier.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp64|tf32|bf16] [--workload he_medium|he_small|h3p_large]
+                    [--precision fp64|tf32|bf16]
+                    [--workload he_medium|he_small|h3p_large|batch64|warmstart]
                     [--no-time-to-e0] [--no-fp64-compare] [--no-cpu-baseline]
+                    [--train-systems T] [--test-systems H] [--epochs E] [--hidden H]
 """
 
 from __future__ import annotations
@@ -39,7 +41,7 @@ METRIC = "Sigma^(2) builds/s (one build + its Dyson iteration per step)"
 UNIT = "builds/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2}
 WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large,
-             "batch64": None}
+             "batch64": None, "warmstart": None}
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
 
@@ -181,7 +183,11 @@ def run_reference(args, rank: int):
     """The reference arm: the CPU oracle as it stands, on this host's cores."""
     if rank != 0:
         return
-    sys_ = WORKLOADS[args.workload]()
+    make = WORKLOADS[args.workload]
+    if make is None:  # families: time the oracle on their first system
+        make = (lambda: W.warmstart_system(0)) if args.workload == "warmstart" else \
+            (lambda: W.batch_systems(64)[0])
+    sys_ = make()
     vals, prepared, spent = [], None, 0.0
     sample = ""
     for k in range(args.warmup + args.steps):
@@ -267,6 +273,109 @@ def run_batch(args, dist, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+def _context(stream, s_):
+    from paper_0911_4348_gb300 import Context
+    c = Context(stream.cuda_stream)
+    c.build_fedvr(s_.n_elem, s_.order, s_.xmin, s_.xmax, s_.grid_kind)
+    c.set_potential(s_.Z, s_.R, s_.soft_en, s_.soft_ee, s_.n_elec)
+    c.solve_hf(s_.beta, tol=1e-12)
+    return c
+
+
+def _to_e0(hist, E_ref, tol=1e-6):
+    """Iterations and summed step wall time until E0 stays within tol of E_ref."""
+    k = next((i for i in range(len(hist)) if np.all(np.abs(hist[i:, 2] - E_ref) <= tol)), None)
+    if k is None:
+        return None, None
+    return int(k + 1), float(np.sum(hist[: k + 1, 4]) / 1000.0)
+
+
+def run_warmstart(args, dist, rank, world, local):
+    """Learned warm start on the family of 20 x 7-point systems (n_b = 119,
+    257-point mesh): collect converged self-energies of T training systems,
+    train the per-pair network (FP32 master weights), then time H held-out
+    systems to a converged E0 (within 1e-6 Ha of their own converged E0) from
+    (a) the plain start g = g^0, (b) Sigma^(2)[g^0] with the same fixed-Sigma
+    inner steps (network output forced to zero) and (c) the network's
+    prediction (BF16 inference). A step is one iteration of one system."""
+    import torch
+    from paper_0911_4348_gb300 import WarmStartNet
+    stream = torch.cuda.current_stream()
+    base = 100000 * rank
+    train = [W.warmstart_system(base + k) for k in range(args.train_systems)]
+    test = [W.warmstart_system(base + 50000 + k) for k in range(args.test_systems)]
+    M = train[0].n_tau
+    net = WarmStartNet(M, args.hidden, seed=W.MASTER_SEED, stream=stream.cuda_stream)
+    zero = WarmStartNet(M, args.hidden, seed=1, stream=stream.cuda_stream)
+    zero.set_params(np.zeros(zero.num_params(), dtype=np.float32))
+    t0 = time.perf_counter()
+    collect_iters = []
+    for s_ in train:
+        c = _context(stream, s_)
+        collect_iters.append(net.collect(c, s_.beta, s_.u, s_.p))
+        c.close()
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = net.train(args.epochs, batch=4096, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    per = []
+    steps_total, step_ms = 0, 0.0
+    for s_ in test:
+        row = {"system": s_.name}
+        for mode, model in (("plain", None), ("sigma1", zero), ("network", net)):
+            c = _context(stream, s_)
+            torch.cuda.synchronize()
+            t_ws = 0.0
+            if model is not None:
+                t1 = time.perf_counter()
+                c.warm_start(model, s_.beta, s_.u, s_.p, inner_steps=4)
+                torch.cuda.synchronize()
+                t_ws = time.perf_counter() - t1
+            r = c.solve_2b(s_.beta, s_.u, s_.p, s_.mixing, s_.tol, 200, 1, check=False)
+            hist = c.get_history()
+            if mode == "plain":
+                E_ref = r["E0"]
+                steps_total += len(hist)
+                step_ms += float(np.sum(hist[:, 4]))
+            it, sec = _to_e0(hist, E_ref)
+            row[mode] = {"iterations": it, "seconds": None if sec is None else sec + t_ws,
+                         "predict_seconds": t_ws, "E0": r["E0"], "status": r["status"],
+                         "dE0_vs_plain": abs(r["E0"] - E_ref)}
+            c.close()
+        per.append(row)
+    net.close()
+    zero.close()
+
+    def total(mode, key):
+        v = [r[mode][key] for r in per]
+        return None if any(x is None for x in v) else float(np.sum(v))
+
+    value = world * steps_total / (step_ms / 1000.0)
+    s0 = train[0]
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": steps_total, "warmup": 0, "ms_per_step": step_ms / steps_total,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
+           "data": "synthetic",
+           "config": {"workload": "warm-start family: He (Z~U[1.5,2.5]) / H3+ (R~U[1.2,3.0]), "
+                                  f"20 x 7 points (n_b={s0.n_b}), M={M}",
+                      "train_systems": len(train), "test_systems": len(test),
+                      "hidden": args.hidden, "epochs": args.epochs, "precision": "tf32",
+                      "parallelism": f"replicas x{world}"},
+           "warm_start": {"collect_seconds": t_collect,
+                          "collect_iterations_mean": float(np.mean(collect_iters)),
+                          "train_seconds": t_train, "final_train_loss": loss,
+                          "rows": len(train) * s0.n_b * (s0.n_b + 1) // 2,
+                          "time_to_E0_seconds": {m: total(m, "seconds")
+                                                 for m in ("plain", "sigma1", "network")},
+                          "iterations_to_E0": {m: total(m, "iterations")
+                                               for m in ("plain", "sigma1", "network")},
+                          "max_dE0_network": max(r["network"]["dE0_vs_plain"] for r in per),
+                          "per_system": per}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,6 +387,12 @@ def main():
     ap.add_argument("--no-time-to-e0", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch each iteration's kernels eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--train-systems", type=int, default=48)
+    ap.add_argument("--test-systems", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--hidden", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -293,8 +408,8 @@ def main():
     from paper_0911_4348_gb300 import Context
 
     torch.cuda.set_device(local)
-    if args.workload == "batch64":
-        run_batch(args, dist, rank, world, local)
+    if args.workload in ("batch64", "warmstart"):
+        (run_batch if args.workload == "batch64" else run_warmstart)(args, dist, rank, world, local)
         if dist:
             dist.destroy_process_group()
         return
@@ -305,6 +420,7 @@ def main():
     ctx.build_fedvr(sys_.n_elem, sys_.order, sys_.xmin, sys_.xmax, sys_.grid_kind)
     ctx.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
     E_hf, _ = ctx.solve_hf(sys_.beta, tol=1e-12)
+    ctx.use_graphs(not args.no_graphs)
     ctx.prepare_2b(sys_.beta, sys_.u, sys_.p, prec)
     n, M = sys_.n_b, sys_.n_tau
 
@@ -387,6 +503,7 @@ def main():
            "data": "synthetic",
            "config": {"workload": sys_.name, "n_b": n, "n_tau": M, "beta": sys_.beta,
                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                      "graphs": ctx.use_graphs(),
                       "l2": "inputs larger than L2 (g stack %.0f MB)" % (M * n * n * 8 / 1e6)},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
            "E_hf": E_hf}

@@ -178,6 +178,17 @@ int fedvr_2b_read(fedvr_ctx *ctx, int out_on_device, double *G_out, double *Sigm
  * number of kernels that step launched. ms is a host array of 6 doubles. */
 int fedvr_stage_times(const fedvr_ctx *ctx, double *ms, int *launches);
 
+/* Graph replay of the iteration (the driver loop of Sec. 2.3 with its launch
+ * overhead removed; the paper has no counterpart). With graphs enabled (the
+ * default) the first regular fedvr_2b_step after fedvr_2b_prepare captures
+ * its kernels into a CUDA graph and later steps replay it; warm-start inner
+ * steps and a change of mixing are handled by re-capture or eager launch.
+ * Results are identical either way. enable: 1 on, 0 off, < 0 leave as is.
+ * *last_step_graph (may be NULL) receives 1 if the last step ran as a graph
+ * replay. If the driver refuses a capture, the context keeps running eagerly
+ * and reports 0 there; this is not an error. */
+int fedvr_use_graphs(fedvr_ctx *ctx, int enable, int *last_step_graph);
+
 /* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
  * [M][n_b][n_b] on host or device; M must match the next solve's mesh; copied
  * at once; NULL clears. inner_steps = 0: the first iteration uses Sigma0

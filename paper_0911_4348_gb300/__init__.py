@@ -187,6 +187,14 @@ class Context:
             self._check(code)
         return dict(res=res.value, E0=E0.value, N=N.value, status=code)
 
+    def use_graphs(self, enable=None) -> bool:
+        """Switch graph replay of the iteration on/off (None: leave it); returns
+        whether the last step ran as a graph replay."""
+        last = C.c_int()
+        self._check(self._lib.fedvr_use_graphs(self._h, -1 if enable is None else int(bool(enable)),
+                                               C.byref(last)))
+        return bool(last.value)
+
     def stage_times(self):
         """Device milliseconds of the last step's stages: sigma2, hf+energy,
         conv1, conv2, update, whole step; and its kernel launch count."""

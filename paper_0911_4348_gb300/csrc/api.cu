@@ -36,6 +36,7 @@ int cuda_fail(fedvr_ctx *ctx, cudaError_t e, const char *what, const char *file,
 bool ensure(fedvr_ctx *ctx, DevBuf &buf, size_t bytes, const char *name) {
   if (bytes == 0) bytes = 16;
   if (buf.bytes >= bytes) return true;
+  drop_graph(ctx);  // the captured iteration holds the old address
   if (buf.ptr) cudaFree(buf.ptr);
   buf.ptr = nullptr;
   buf.bytes = 0;
@@ -56,6 +57,13 @@ void release(DevBuf &buf) {
   if (buf.ptr) cudaFree(buf.ptr);
   buf.ptr = nullptr;
   buf.bytes = 0;
+}
+
+void drop_graph(fedvr_ctx *ctx) {
+  if (ctx && ctx->step_graph) {
+    cudaGraphExecDestroy(ctx->step_graph);
+    ctx->step_graph = nullptr;
+  }
 }
 
 }  // namespace fedvr
@@ -275,6 +283,86 @@ int tc_err_ptr(fedvr_ctx *ctx, int **err) {
   return tc_workspace(ctx, ctx->n, ctx->M, &ws, &S32, err);
 }
 
+// Enqueue one iteration on s without host synchronisation, recording the
+// stage events with evflags (cudaEventRecordExternal inside a capture).
+int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsigned evflags,
+                 int *launches) {
+  const int n = ctx->n, M = ctx->M;
+  const bool split = ctx->precision == FEDVR_SPLIT_TF32;
+  int *err = nullptr;
+  if (split) {
+    if (int r = tc_err_ptr(ctx, &err)) return r;
+  }
+  FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[1], s, evflags));
+  if (int r = phase_sigma_pre(ctx, warm, s, launches)) return r;
+  uint8_t *tab = P<uint8_t>(ctx->w_tab);
+  if (split && !warm) {
+    const TcGeom g = tc_geom(n, M);
+    FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
+                                     reinterpret_cast<const long *>(tab + kTabPX), 1,
+                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s));
+    *launches += 1;
+  }
+  FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[2], s, evflags));
+  if (int r = phase_mid(ctx, s, launches)) return r;
+  FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[3], s, evflags));
+  if (split) {
+    const TcGeom g = tc_geom(n, M);
+    FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
+                                  reinterpret_cast<const long *>(tab + kTabPC), 1,
+                                  conv1_items(n, M), g.Np, err, ctx->num_sms, s));
+    *launches += 1;
+  } else {
+    if (int r = phase_conv1_fp64(ctx, s, launches)) return r;
+  }
+  FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[4], s, evflags));
+  if (int r = phase_conv2(ctx, s, launches)) return r;
+  FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[5], s, evflags));
+  if (int r = phase_update(ctx, mixing, s, launches)) return r;
+  FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[6], s, evflags));
+  return FEDVR_OK;
+}
+
+// Capture one regular iteration into ctx->step_graph. Capture happens on a
+// private non-blocking stream (the context's stream may be the legacy default
+// stream, which cannot be captured). If the driver refuses the capture the
+// context carries on without graphs: the refusal is not an error of the run.
+int capture_step(fedvr_ctx *ctx, double mixing) {
+  if (!ctx->cap_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->cap_stream = nullptr;
+      ctx->use_graphs = false;
+      return FEDVR_OK;
+    }
+  }
+  cudaStream_t cs = ctx->cap_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->use_graphs = false;
+    return FEDVR_OK;
+  }
+  int launches = 0;
+  const int r = enqueue_step(ctx, false, mixing, cs, cudaEventRecordExternal, &launches);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (r == FEDVR_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (r != FEDVR_OK || e != cudaSuccess || !exec) {
+    // a launcher that cannot be captured: run this context eagerly from now on
+    cudaGetLastError();
+    ctx->failed = false;
+    ctx->err[0] = 0;
+    ctx->use_graphs = false;
+    return FEDVR_OK;
+  }
+  ctx->step_graph = exec;
+  ctx->graph_mixing = mixing;
+  ctx->graph_launches = launches;
+  return FEDVR_OK;
+}
+
 }  // namespace
 
 int fedvr::sigma_of_current_g(fedvr_ctx *ctx) {
@@ -343,7 +431,9 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_w, &ctx->w_wm, &ctx->w_wp, &ctx->w_coef, &ctx->w_K, &ctx->w_phi,
                     &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
                     &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
-                    &ctx->w_K32};
+                    &ctx->w_K32, &ctx->w_tab, &ctx->w_btab};
+  drop_graph(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
   for (int i = 0; i < 7; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -595,6 +685,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   if (ctx->sigma_init_M && ctx->sigma_init_M != M)
     return fail(ctx, FEDVR_ERR_ARG, "initial Sigma has M = %d, mesh has %d", ctx->sigma_init_M, M);
   ctx->prepared = false;
+  drop_graph(ctx);
   const size_t nn = (size_t)n * n, stack = (size_t)M * nn;
   cudaStream_t s = ctx->stream;
   ENSURE(ctx, w_K, dsz((size_t)n * M * M));
@@ -653,17 +744,9 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   CHECK_CTX(ctx);
   if (!ctx->prepared) return fail(ctx, FEDVR_ERR_STATE, "fedvr_2b_step before fedvr_2b_prepare");
   if (!(mixing > 0.0 && mixing <= 1.0)) return fail(ctx, FEDVR_ERR_ARG, "need 0 < mixing <= 1");
-  const int n = ctx->n, M = ctx->M;
-  const size_t nn = (size_t)n * n, stack = (size_t)M * nn;
-  const double spin = ctx->spin;
+  const size_t stack = (size_t)ctx->M * ctx->n * ctx->n;
   cudaStream_t s = ctx->stream;
-  double *G0 = P<double>(ctx->w_G0), *G = P<double>(ctx->w_G), *S = P<double>(ctx->w_S);
-  double *I1 = P<double>(ctx->w_I1), *I2 = P<double>(ctx->w_I2);
-  double *t1 = P<double>(ctx->w_t1), *t2 = P<double>(ctx->w_t2), *t3 = P<double>(ctx->w_t3);
-  double *red = P<double>(ctx->w_red);
-  const double *C = P<double>(ctx->b_C), *h = P<double>(ctx->b_h), *V = P<double>(ctx->b_V);
   auto t0 = std::chrono::steady_clock::now();
-  int launches = 0;
   const bool split = ctx->precision == FEDVR_SPLIT_TF32;
   int *err = nullptr;
   if (split) {
@@ -671,43 +754,30 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   }
   FEDVR_CK(ctx, cudaEventRecord(ctx->ev[0], s));
   if (G_in)
-    FEDVR_CK(ctx, cudaMemcpyAsync(G, G_in, dsz(stack),
+    FEDVR_CK(ctx, cudaMemcpyAsync(P<double>(ctx->w_G), G_in, dsz(stack),
                                   in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[1], s));
   const bool warm = ctx->sigma_init_M &&
                     ctx->step_k < (ctx->warm_inner > 0 ? ctx->warm_inner : 1);
   if (warm && ctx->warm_inner > 0) mixing = 1.0;  // full Dyson step at the fixed warm-start Sigma
-  if (int r = phase_sigma_pre(ctx, warm, s, &launches)) return r;
-  uint8_t *tab = P<uint8_t>(ctx->w_tab);
-  if (split && !warm) {
-    const TcGeom g = tc_geom(n, M);
-    FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
-                                     reinterpret_cast<const long *>(tab + kTabPX), 1,
-                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s));
-    launches += 1;
+  int launches = 0;
+  ctx->last_step_graph = false;
+  if (ctx->use_graphs && !warm) {
+    if (ctx->step_graph && ctx->graph_mixing != mixing) drop_graph(ctx);
+    if (!ctx->step_graph) {
+      if (int r = capture_step(ctx, mixing)) return r;
+    }
   }
-  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[2], s));
-  if (int r = phase_mid(ctx, s, &launches)) return r;
-  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[3], s));
-  if (split) {
-    const TcGeom g = tc_geom(n, M);
-    FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
-                                  reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                  conv1_items(n, M), g.Np, err, ctx->num_sms, s));
-    launches += 1;
+  if (ctx->step_graph && !warm) {
+    FEDVR_CK(ctx, cudaGraphLaunch(ctx->step_graph, s));
+    launches = ctx->graph_launches;
+    ctx->last_step_graph = true;
   } else {
-    if (int r = phase_conv1_fp64(ctx, s, &launches)) return r;
+    if (int r = enqueue_step(ctx, warm, mixing, s, cudaEventRecordDefault, &launches)) return r;
   }
-  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[4], s));
-  if (int r = phase_conv2(ctx, s, &launches)) return r;
-  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[5], s));
-  if (int r = phase_update(ctx, mixing, s, &launches)) return r;
-  FEDVR_CK(ctx, cudaEventRecord(ctx->ev[6], s));
   ctx->step_launches = launches;
-  (void)G0; (void)I1; (void)I2; (void)t1; (void)t2; (void)t3; (void)C; (void)h; (void)V; (void)spin;
   double hr[3];
   int tc_err = 0;
-  FEDVR_CK(ctx, cudaMemcpyAsync(hr, red, sizeof(hr), cudaMemcpyDeviceToHost, s));
+  FEDVR_CK(ctx, cudaMemcpyAsync(hr, P<double>(ctx->w_red), sizeof(hr), cudaMemcpyDeviceToHost, s));
   if (split) FEDVR_CK(ctx, cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (int r = sync(ctx)) return r;
   if (tc_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
@@ -720,6 +790,16 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   if (N_out) *N_out = hr[1];
   if (hr[2] != hr[2] || !is_fin(hr[0]))
     return fail(ctx, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", ctx->step_k - 1);
+  return FEDVR_OK;
+}
+
+int fedvr_use_graphs(fedvr_ctx *ctx, int enable, int *last_step_graph) {
+  CHECK_CTX(ctx);
+  if (last_step_graph) *last_step_graph = ctx->last_step_graph ? 1 : 0;
+  if (enable >= 0) {
+    ctx->use_graphs = enable != 0;
+    if (!ctx->use_graphs) drop_graph(ctx);
+  }
   return FEDVR_OK;
 }
 

@@ -49,6 +49,15 @@ struct fedvr_ctx {
   cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int step_launches = 0;
   int num_sms = 0;
+  // CUDA graph of one regular iteration: captured on a private stream at the
+  // first step after prepare, replayed on `stream`; dropped when the mixing
+  // changes or a workspace buffer moves.
+  bool use_graphs = true;
+  bool last_step_graph = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  double graph_mixing = 0;
+  int graph_launches = 0;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
 
@@ -73,6 +82,8 @@ int cuda_fail(fedvr_ctx *ctx, cudaError_t e, const char *what, const char *file,
 // Ensure buf holds at least `bytes`; returns false (and records the error) on failure.
 bool ensure(fedvr_ctx *ctx, DevBuf &buf, size_t bytes, const char *name);
 void release(DevBuf &buf);
+// Destroy the context's captured iteration graph (if any).
+void drop_graph(fedvr_ctx *ctx);
 
 template <typename T>
 inline T *P(DevBuf &b) { return reinterpret_cast<T *>(b.ptr); }
