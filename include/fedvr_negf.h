@@ -189,6 +189,16 @@ int fedvr_stage_times(const fedvr_ctx *ctx, double *ms, int *launches);
  * and reports 0 there; this is not an error. */
 int fedvr_use_graphs(fedvr_ctx *ctx, int enable, int *last_step_graph);
 
+/* Work split of the split-TF32 first convolution (Eq. deq; the paper has no
+ * counterpart): each 128-row tile of the stacked rows (i, a) may be cut into S
+ * ranges of mesh points j, computed by different CTAs into separate partial
+ * stacks and summed in a fixed order. request = 0 (default): fedvr_2b_prepare
+ * times the candidates S once per (device, n_b, M) in the process and keeps
+ * the fastest; request > 0: use the largest candidate <= request (1 = no
+ * split); request < 0: leave the setting. *in_use (may be NULL) receives S of
+ * the currently prepared run. Takes effect at the next prepare. */
+int fedvr_conv1_splits(fedvr_ctx *ctx, int request, int *in_use);
+
 /* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
  * [M][n_b][n_b] on host or device; M must match the next solve's mesh; copied
  * at once; NULL clears. inner_steps = 0: the first iteration uses Sigma0

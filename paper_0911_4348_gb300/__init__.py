@@ -195,6 +195,14 @@ class Context:
                                                C.byref(last)))
         return bool(last.value)
 
+    def conv1_splits(self, request=None) -> int:
+        """Request the first convolution's split count (0 = measured choice,
+        None = leave); returns the count of the prepared run."""
+        cur = C.c_int()
+        self._check(self._lib.fedvr_conv1_splits(self._h, -1 if request is None else int(request),
+                                                 C.byref(cur)))
+        return cur.value
+
     def stage_times(self):
         """Device milliseconds of the last step's stages: sigma2, hf+energy,
         conv1, conv2, update, whole step; and its kernel launch count."""

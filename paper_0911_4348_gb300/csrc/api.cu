@@ -9,7 +9,10 @@
 #include <string.h>
 
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 namespace fedvr {
@@ -179,21 +182,103 @@ constexpr size_t kTabPC = kTabPX + 256;
 constexpr size_t kTabBytes = kTabPC + 256;
 
 int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *Sigma,
-                         float *S32, const double *dHF, const ConvCoef *coef, double *I1) {
+                         float *S32, const double *dHF, const ConvCoef *coef, double *I1,
+                         int splits = 1, double *part = nullptr) {
   ENSURE(ctx, w_tab, kTabBytes);
   XSys x;
   C1Sys c;
   memset(&x, 0, sizeof(x));
   memset(&c, 0, sizeof(c));
   FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32));
-  FEDVR_CK(ctx, c1sys_fill(&c, n, M, ws, S32, dHF, coef, I1));
-  long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M)};
+  FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, coef, I1, part));
+  long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M, splits)};
   uint8_t *base = P<uint8_t>(ctx->w_tab);
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabX, &x, sizeof(x), cudaMemcpyHostToDevice, ctx->stream));
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabC, &c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream));
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabPX, px, sizeof(px), cudaMemcpyHostToDevice, ctx->stream));
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabPC, pc, sizeof(pc), cudaMemcpyHostToDevice, ctx->stream));
   return sync(ctx);  // host descriptors go out of scope
+}
+
+// First convolution of the prepared single system (tables at w_tab) with its
+// splits summed into I1.
+int launch_conv1_single(fedvr_ctx *ctx, int splits, int *err, cudaStream_t s, int *launches) {
+  const int n = ctx->n, M = ctx->M;
+  const TcGeom g = tc_geom(n, M);
+  uint8_t *tab = P<uint8_t>(ctx->w_tab);
+  FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
+                                reinterpret_cast<const long *>(tab + kTabPC), 1,
+                                conv1_items(n, M, splits), g.Np, err, ctx->num_sms, s));
+  *launches += 1;
+  if (splits > 1) {
+    FEDVR_CK(ctx, conv1_sum_splits((long)M * n * n, splits - 1, P<double>(ctx->w_c1p),
+                                   P<double>(ctx->w_I1), s));
+    *launches += 1;
+  }
+  return FEDVR_OK;
+}
+
+// Measured choice of the first convolution's splits, once per (device, n, M)
+// in this process: every candidate's persistent launch (and split sum) is
+// timed on the prepared buffers and the fastest kept. Candidates keep at
+// least 4 mesh points per split and at most 16 work items per SM.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_conv1_splits;
+
+int choose_conv1_splits(fedvr_ctx *ctx, float *ws, float *S32, int *err) {
+  const int n = ctx->n, M = ctx->M;
+  const size_t stack = (size_t)M * n * n;
+  const long RT = ((long)M * n + 127) / 128;
+  std::vector<int> cand;
+  for (int S : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+    if (S > 1 && (S > M / 4 || RT * S > 16L * ctx->num_sms || (S - 1) * stack * 8 > (2ull << 30)))
+      continue;
+    cand.push_back(S);
+  }
+  int best = 1;
+  if (ctx->c1_request > 0) {
+    best = 1;
+    for (int S : cand)
+      if (S <= ctx->c1_request) best = S;
+  } else {
+    const auto key = std::make_tuple(ctx->device, n, M);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_conv1_splits.find(key);
+      if (it != g_conv1_splits.end()) best = it->second;
+    }
+    if (cand.size() > 1 && best == 1 && !g_conv1_splits.count(key)) {
+      ENSURE(ctx, w_c1p, dsz((size_t)(cand.back() - 1) * stack));
+      float best_ms = 0.f;
+      cudaStream_t s = ctx->stream;
+      for (int S : cand) {
+        if (int r = upload_single_tables(ctx, n, M, ws, P<double>(ctx->w_S), S32,
+                                         P<double>(ctx->w_dHF), P<ConvCoef>(ctx->w_coef),
+                                         P<double>(ctx->w_I1), S, P<double>(ctx->w_c1p)))
+          return r;
+        int launches = 0;
+        if (int r = launch_conv1_single(ctx, S, err, s, &launches)) return r;  // warm-up
+        FEDVR_CK(ctx, cudaEventRecord(ctx->ev[0], s));
+        if (int r = launch_conv1_single(ctx, S, err, s, &launches)) return r;
+        FEDVR_CK(ctx, cudaEventRecord(ctx->ev[6], s));
+        int h_err = 0;
+        FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (int r = sync(ctx)) return r;
+        if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+        float ms = 0.f;
+        FEDVR_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[6]));
+        if (S == cand.front() || ms < 0.97f * best_ms) {  // more splits must win clearly
+          best = S;
+          best_ms = ms;
+        }
+      }
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_conv1_splits[key] = best;
+    }
+  }
+  if (best > 1) ENSURE(ctx, w_c1p, dsz((size_t)(best - 1) * stack));
+  ctx->c1_splits = best;
+  return FEDVR_OK;
 }
 
 // The pieces of one iteration for one system, enqueued on stream s.
@@ -307,11 +392,7 @@ int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsig
   if (int r = phase_mid(ctx, s, launches)) return r;
   FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[3], s, evflags));
   if (split) {
-    const TcGeom g = tc_geom(n, M);
-    FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
-                                  reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                  conv1_items(n, M), g.Np, err, ctx->num_sms, s));
-    *launches += 1;
+    if (int r = launch_conv1_single(ctx, ctx->c1_splits, err, s, launches)) return r;
   } else {
     if (int r = phase_conv1_fp64(ctx, s, launches)) return r;
   }
@@ -431,7 +512,7 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_w, &ctx->w_wm, &ctx->w_wp, &ctx->w_coef, &ctx->w_K, &ctx->w_phi,
                     &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
                     &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
-                    &ctx->w_K32, &ctx->w_tab, &ctx->w_btab};
+                    &ctx->w_K32, &ctx->w_tab, &ctx->w_btab, &ctx->w_c1p};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -722,9 +803,15 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    ctx->n = n;
+    ctx->M = M;
+    if (int r = choose_conv1_splits(ctx, ws, S32, err)) return r;
     if (int r = upload_single_tables(ctx, n, M, ws, P<double>(ctx->w_S), S32, P<double>(ctx->w_dHF),
-                                     P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_I1)))
+                                     P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_I1),
+                                     ctx->c1_splits, P<double>(ctx->w_c1p)))
       return r;
+  } else {
+    ctx->c1_splits = 1;
   }
   FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->w_G0), P<double>(ctx->w_G), s));
   if (int r = sync(ctx)) return r;
@@ -790,6 +877,14 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   if (N_out) *N_out = hr[1];
   if (hr[2] != hr[2] || !is_fin(hr[0]))
     return fail(ctx, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", ctx->step_k - 1);
+  return FEDVR_OK;
+}
+
+int fedvr_conv1_splits(fedvr_ctx *ctx, int request, int *in_use) {
+  CHECK_CTX(ctx);
+  if (request > 64) return fail(ctx, FEDVR_ERR_ARG, "at most 64 splits");
+  if (request >= 0) ctx->c1_request = request;
+  if (in_use) *in_use = ctx->c1_splits;
   return FEDVR_OK;
 }
 
@@ -950,8 +1045,8 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
     memset(&hc[k], 0, sizeof(C1Sys));
     cudaError_t e = xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32);
     if (e == cudaSuccess)
-      e = c1sys_fill(&hc[k], c->n, c->M, ws, S32, P<double>(c->w_dHF), P<ConvCoef>(c->w_coef),
-                     P<double>(c->w_I1));
+      e = c1sys_fill(&hc[k], c->n, c->M, 1, ws, S32, P<double>(c->w_dHF),
+                     P<ConvCoef>(c->w_coef), P<double>(c->w_I1), nullptr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt + k * sizeof(XSys), &hx[k], sizeof(XSys),
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt + B->off_c + k * sizeof(C1Sys), &hc[k],
@@ -992,7 +1087,7 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
     const fedvr_ctx *c = B->ctxs[k];
     if (!c->prepared) return fail(lead, FEDVR_ERR_STATE, "system %d is no longer prepared", k);
     B->px[k + 1] = B->px[k] + (active[k] ? exchange_items(c->n, c->M) : 0);
-    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M) : 0);
+    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M, 1) : 0);
   }
   if (B->px[n_sys] == 0) return FEDVR_OK;
   FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_px, B->px.data(), (n_sys + 1) * sizeof(long),
@@ -1188,7 +1283,7 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
                                   reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                  conv1_items(n, M), g.Np, err, ctx->num_sms, s));
+                                  conv1_items(n, M, 1), g.Np, err, ctx->num_sms, s));
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;

@@ -58,6 +58,10 @@ struct fedvr_ctx {
   cudaGraphExec_t step_graph = nullptr;
   double graph_mixing = 0;
   int graph_launches = 0;
+  // splits of the first convolution's mesh-point range (split-TF32 path):
+  // requested (0 = measured choice) and in use by the prepared run
+  int c1_request = 0;
+  int c1_splits = 1;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
 
@@ -69,7 +73,7 @@ struct fedvr_ctx {
   fedvr::DevBuf b_sigma_init;
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
-      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab;
+      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p;
 };
 
 namespace fedvr {

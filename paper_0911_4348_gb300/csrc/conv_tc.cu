@@ -4,13 +4,21 @@
 //                           B_ii = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1}
 //
 // with the lag bracket k and the trapezoid/interpolation weights c1, c2 of the
-// FP64 path (FP64 tables, applied here in FP32). One tile = one output mesh
-// point i and 128 rows a; all columns b sit in one or two N tiles. The
-// contraction runs over (j, c) in 32-wide chunks: the A operand B_ij(a, c) is
-// formed by the CUDA cores and split as hi + lo (TF32); B = g_j(b, c) comes
-// from the split copy of g. Products hi*hi + hi*lo + lo*hi accumulate in FP32 in
-// TMEM over a block of mesh points (about 4096 contraction terms) and each block
-// is then added into the FP64 result, so rounding does not grow with M.
+// FP64 path (FP64 tables, applied here in FP32). The rows (i, a) of all mesh
+// points are stacked into one M*n-row matrix, so a 128-row tile is full except
+// at the very end of the stack (no padding of n up to a multiple of 128); all
+// columns b sit in one or two N tiles. The contraction runs over (j, c) in
+// 32-wide chunks: the A operand B_ij(a, c) of each row is formed by the CUDA
+// cores and split as hi + lo (TF32); B = g_j(b, c) comes from the split copy of
+// g by TMA. Products hi*hi + hi*lo + lo*hi accumulate in FP32 in TMEM over a
+// block of JB mesh points (about 4096 contraction terms) and each block is
+// then added into the FP64 result, so rounding does not grow with M.
+//
+// A work item is (row tile, split s): split s covers the mesh points
+// j in [s M / S, (s + 1) M / S). Split 0 writes I1, split s > 0 its own
+// partial stack; a fixed-order sum then adds the partials into I1, so results
+// do not depend on the schedule. S > 1 only pays when there are too few row
+// tiles to fill the GPU (small systems) or to balance the last wave.
 #include "common.cuh"
 #include "tc.cuh"
 #include "tc_sys.cuh"
@@ -23,9 +31,21 @@ constexpr uint32_t kTileA = 128 * 128;
 constexpr int kWarps = 14;  // 0-3 flush, 4-11 A producers, 12 TMA, 13 MMA
 constexpr int kThreads = kWarps * 32;
 
-// Work queue: the (i, M-tile) items of every system in the table, each a
-// sequence of accumulator blocks of JB mesh points j, each block a sequence
-// of 32-wide chunks c. Roles as in the exchange kernel.
+struct C1Item {
+  int t, j_lo, j_hi;
+  double *out;  // I1 or the split's partial stack
+};
+
+__device__ __forceinline__ C1Item c1_item(const C1Sys &S, long q) {
+  C1Item it;
+  it.t = (int)(q / S.S);
+  const int s = (int)(q % S.S);
+  it.j_lo = (int)(((long)s * S.g.M) / S.S);
+  it.j_hi = (int)(((long)(s + 1) * S.g.M) / S.S);
+  it.out = (s == 0) ? S.I1 : S.part + (long)(s - 1) * S.g.M * S.g.n * S.g.n;
+  return it;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     conv1_tc_kernel(const C1Sys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
                     long items, int Np_max, int nbuf, int *err) {
@@ -65,30 +85,49 @@ __global__ void __launch_bounds__(kThreads, 1)
   int cur = 0;
 
   if (warp >= 4 && warp < 12) {
-    // ---- A producers: B_ij(a, c) = c1 Sigma_k1(a, c) + c2 Sigma_k2(a, c) (+ dHF on j = i) ----
+    // ---- A producers: rows r0 + 32 k of the tile, 16-byte chunk c of each 32-wide slice ----
     const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
+    uint32_t off[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) off[k] = tc::sw128_offset(r0 + 32 * k, c);
     uint32_t cc = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
-      const int n = S.g.n, ld = S.g.ld, M = S.g.M, MT = S.g.MT;
-      const long nld = (long)n * ld;
-      const long q = w - prefix[cur];
-      const int i = (int)(q / MT), mt = (int)(q % MT);
-      for (int j = 0; j < M && !*abort_flag; ++j) {
-        const ConvCoef cf = S.coef[(long)i * M + j];
-        const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
-        const float c1 = (float)cf.c1, c2 = (float)cf.c2;
-        const float *S1 = S.S32 + (long)k1 * nld, *S2 = S.S32 + (long)k2 * nld;
-        for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+      const int n = S.g.n, ld = S.g.ld, M = S.g.M, KC = S.g.KC;
+      const long R = (long)M * n;
+      const C1Item it = c1_item(S, w - prefix[cur]);
+      int ia[4], aa[4];
+      bool live[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long r = (long)it.t * 128 + r0 + 32 * k;
+        live[k] = r < R;
+        ia[k] = live[k] ? (int)(r / n) : 0;
+        aa[k] = live[k] ? (int)(r % n) : 0;
+      }
+      for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
+        uint32_t o1[4], o2[4];  // element offsets into S32 (M n ld < 2^31)
+        float c1[4], c2[4];
+        bool dg[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const ConvCoef cf = S.coef[(long)ia[k] * M + j];
+          const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
+          o1[k] = (uint32_t)((k1 * n + aa[k]) * ld + 4 * c);
+          o2[k] = (uint32_t)((k2 * n + aa[k]) * ld + 4 * c);
+          c1[k] = (float)cf.c1;
+          c2[k] = (float)cf.c2;
+          dg[k] = live[k] && cf.diag;
+        }
+        for (int kc = 0; kc < KC; ++kc, ++cc) {
           const int l0 = kc * 32;
           float4 s1[4], s2[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const int a = mt * 128 + r0 + 32 * k;
-            if (a < n) {
-              s1[k] = *reinterpret_cast<const float4 *>(S1 + (long)a * ld + l0 + 4 * c);
-              s2[k] = *reinterpret_cast<const float4 *>(S2 + (long)a * ld + l0 + 4 * c);
+            if (live[k]) {
+              s1[k] = *reinterpret_cast<const float4 *>(S.S32 + o1[k] + l0);
+              s2[k] = *reinterpret_cast<const float4 *>(S.S32 + o2[k] + l0);
             } else {
               s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -102,22 +141,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint8_t *st = smem + s * stage_bytes;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const int a = mt * 128 + r0 + 32 * k;
-            float x[4] = {fmaf(c1, s1[k].x, c2 * s2[k].x), fmaf(c1, s1[k].y, c2 * s2[k].y),
-                          fmaf(c1, s1[k].z, c2 * s2[k].z), fmaf(c1, s1[k].w, c2 * s2[k].w)};
+            // S32 rows are zero beyond n, so the padded columns come out zero
+            float x[4] = {fmaf(c1[k], s1[k].x, c2[k] * s2[k].x),
+                          fmaf(c1[k], s1[k].y, c2[k] * s2[k].y),
+                          fmaf(c1[k], s1[k].z, c2[k] * s2[k].z),
+                          fmaf(c1[k], s1[k].w, c2[k] * s2[k].w)};
+            if (dg[k]) {
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-              const int l = l0 + 4 * c + qq;
-              if (l >= n || a >= n) x[qq] = 0.f;
-              else if (cf.diag) x[qq] += (float)S.dHF[(long)a * n + l];
+              for (int qq = 0; qq < 4; ++qq) {
+                const int l = l0 + 4 * c + qq;
+                if (l < n) x[qq] += (float)S.dHF[(long)aa[k] * n + l];
+              }
             }
             const float4 hi = make_float4(tc::tf32_rna(x[0]), tc::tf32_rna(x[1]),
                                           tc::tf32_rna(x[2]), tc::tf32_rna(x[3]));
             const float4 lo = make_float4(tc::tf32_rna(x[0] - hi.x), tc::tf32_rna(x[1] - hi.y),
                                           tc::tf32_rna(x[2] - hi.z), tc::tf32_rna(x[3] - hi.w));
-            const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
-            *reinterpret_cast<float4 *>(st + off) = hi;
-            *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+            *reinterpret_cast<float4 *>(st + off[k]) = hi;
+            *reinterpret_cast<float4 *>(st + kTileA + off[k]) = lo;
           }
           tc::fence_smem_to_async();
           tc::mbar_arrive(&full[s]);
@@ -131,8 +172,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const C1Sys &S = sys[cur];
+        const C1Item it = c1_item(S, w - prefix[cur]);
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
-        for (int j = 0; j < S.g.M && !*abort_flag; ++j) {
+        for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
           for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
@@ -158,9 +200,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const C1Sys &S = sys[cur];
-        const int n = S.g.n, M = S.g.M;
-        for (int j0 = 0; j0 < M && !*abort_flag; j0 += S.JB, ++tcount) {
-          const int j1 = min(M, j0 + S.JB);
+        const C1Item it = c1_item(S, w - prefix[cur]);
+        const int n = S.g.n;
+        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += S.JB, ++tcount) {
+          const int j1 = min(it.j_hi, j0 + S.JB);
           const int buf = tcount & 1;
           const uint32_t tu = tcount >> 1;
           bool ok = true;
@@ -209,18 +252,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---- flush: add each FP32 block into the FP64 result ----
+    // ---- flush: add each FP32 block into the FP64 output rows ----
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
-      const int n = S.g.n, M = S.g.M, MT = S.g.MT;
-      const long q = w - prefix[cur];
-      const int i = (int)(q / MT), mt = (int)(q % MT);
-      const int a = mt * 128 + warp * 32 + lane;
-      const bool live = a < n;
-      double *row = S.I1 + ((long)i * n + (live ? a : 0)) * n;
-      for (int j0 = 0; j0 < M; j0 += S.JB, ++tcount) {
+      const int n = S.g.n;
+      const C1Item it = c1_item(S, w - prefix[cur]);
+      const long r = (long)it.t * 128 + warp * 32 + lane;
+      const bool live = r < (long)S.g.M * n;
+      double *row = it.out + (live ? r : 0) * n;
+      for (int j0 = it.j_lo; j0 < it.j_hi; j0 += S.JB, ++tcount) {
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
         if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
@@ -229,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::fence_after_sync();
         const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
+        const bool first = j0 == it.j_lo;
         for (int c0 = 0; c0 < n; c0 += 16) {
           float v[16];
           tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -236,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const int b = c0 + t;
-              if (b < n) row[b] = (j0 == 0) ? (double)v[t] : row[b] + (double)v[t];
+              if (b < n) row[b] = first ? (double)v[t] : row[b] + (double)v[t];
             }
           }
         }
@@ -259,6 +302,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// I1 += part[0] + part[1] + ... (fixed order).
+__global__ void conv1_sum_splits_kernel(long count, int nparts, const double *__restrict__ part,
+                                        double *__restrict__ I1) {
+  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < count;
+       x += (long)gridDim.x * blockDim.x) {
+    double v = I1[x];
+    for (int q = 0; q < nparts; ++q) v += part[(long)q * count + x];
+    I1[x] = v;
+  }
+}
+
 // S32 = (float)Sigma with rows padded to ld (zeros beyond n).
 __global__ void sigma_to_f32_kernel(int n, long rows, int ld, const double *__restrict__ S,
                                     float *__restrict__ S32) {
@@ -279,21 +333,31 @@ cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t c1sys_fill(C1Sys *d, int n, int M, const float *ws, const float *S32,
-                       const double *dHF, const ConvCoef *coef, double *I1) {
+cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
+                       const double *dHF, const ConvCoef *coef, double *I1, double *part) {
   d->g = tc_geom(n, M);
   const long stack = (long)M * n * d->g.ld;
   d->JB = 4096 / n > 1 ? 4096 / n : 1;
+  d->S = splits;
+  d->RT = (int)(((long)M * n + 127) / 128);
   d->S32 = S32;
   d->dHF = dHF;
   d->coef = coef;
   d->I1 = I1;
+  d->part = part;
   for (int t = 0; t < 2; ++t) {
     cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
+                             cudaStream_t s) {
+  if (nparts < 1) return cudaSuccess;
+  conv1_sum_splits_kernel<<<1024, 256, 0, s>>>(count, nparts, part, I1);
+  return cudaGetLastError();
 }
 
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,

@@ -35,10 +35,13 @@ struct C1Sys {
   CUtensorMap th[2], tl[2];   // g_j split, per N tile
   TcGeom g;
   int JB;                     // mesh points per FP32 accumulation block
+  int S;                      // splits of the mesh-point range per row tile
+  int RT;                     // 128-row tiles of the stacked (i, a) rows
   const float *S32;
   const double *dHF;
   const ConvCoef *coef;
-  double *I1;
+  double *I1;                 // output (split 0 and the final sum)
+  double *part;               // splits 1..S-1: [S-1][M][n][n]
 };
 
 TcGeom tc_geom(int n, int M);
@@ -49,8 +52,11 @@ size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns);
 // descriptors to device memory.
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
                       float *S32);
-cudaError_t c1sys_fill(C1Sys *d, int n, int M, const float *ws, const float *S32,
-                       const double *dHF, const ConvCoef *coef, double *I1);
+cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
+                       const double *dHF, const ConvCoef *coef, double *I1, double *part);
+// I1 += part[0] + ... + part[nparts-1] (count doubles each), fixed order.
+cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
+                             cudaStream_t s);
 
 // Per-system preparation of the exchange operands (splits of G and V, VQ).
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
@@ -62,8 +68,11 @@ cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, l
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
                             int Np_max, int *err, int num_sms, cudaStream_t s);
 
-// Work items per system: exchange (j, b) pairs; convolution (i, M-tile) pairs.
+// Work items per system: exchange (j, b) pairs; convolution (row tile, split)
+// pairs over the M*n stacked rows.
 inline long exchange_items(int n, int M) { return (long)M * n; }
-inline long conv1_items(int n, int M) { return (long)M * ((n + 127) / 128); }
+inline long conv1_items(int n, int M, int splits) {
+  return ((long)M * n + 127) / 128 * (long)splits;
+}
 
 }  // namespace fedvr

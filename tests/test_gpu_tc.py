@@ -159,3 +159,47 @@ def test_tf32_and_fp64_steps_agree_at_full_size():
     for e64, e32 in zip(out[0][0], out[TF32][0]):
         assert abs(e64 - e32) < E0_TOL
     assert maxrel(out[TF32][1], out[0][1]) < 1e-6
+
+
+@pytest.mark.parametrize("splits", [3, 8])
+def test_conv1_splits_agree(splits):
+    # the first convolution cut into mesh-point ranges (partial stacks summed in
+    # a fixed order) gives the unsplit result up to FP32 block rounding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Context
+    s = W.he_small()
+    out = {}
+    for S in (1, splits):
+        c = Context()
+        c.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+        c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+        c.solve_hf(s.beta, tol=1e-12)
+        c.conv1_splits(S)
+        c.prepare_2b(s.beta, s.u, s.p, TF32)
+        assert c.conv1_splits() == S
+        Es = [c.step_2b(s.mixing)["E0"] for _ in range(3)]
+        G = np.empty((s.n_tau, s.n_b, s.n_b))
+        c.read_2b(G_out=G)
+        out[S] = (Es, G)
+        c.close()
+    for e1, es in zip(out[1][0], out[splits][0]):
+        assert abs(e1 - es) < 1e-8
+    assert maxrel(out[splits][1], out[1][1]) < 1e-6
+
+
+def test_conv1_measured_split_choice_is_a_candidate():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Context
+    s = W.he_small()
+    c = Context()
+    c.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+    c.solve_hf(s.beta, tol=1e-12)
+    c.prepare_2b(s.beta, s.u, s.p, TF32)
+    S = c.conv1_splits()
+    assert S in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32) and S <= s.n_tau // 4
+    r = c.solve_2b(s.beta, s.u, s.p, s.mixing, s.tol, 100, precision=TF32)
+    assert r["status"] == 0
+    c.close()
