@@ -39,6 +39,7 @@ def test_batched_equals_single_system_solves():
     single = []
     for s in systems:
         c = _ctx(s)
+        c.conv1_splits(1)  # the batched queue runs unsplit convolution tiles
         single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=TF32, check=False))
         c.close()
     ctxs = [_ctx(s) for s in systems]
