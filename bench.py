@@ -503,7 +503,7 @@ def main():
            "data": "synthetic",
            "config": {"workload": sys_.name, "n_b": n, "n_tau": M, "beta": sys_.beta,
                       "precision": args.precision, "parallelism": f"replicas x{world}",
-                      "graphs": ctx.use_graphs(),
+                      "graphs": ctx.use_graphs(), "conv1_splits": ctx.conv1_splits(),
                       "l2": "inputs larger than L2 (g stack %.0f MB)" % (M * n * n * 8 / 1e6)},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
            "E_hf": E_hf}
