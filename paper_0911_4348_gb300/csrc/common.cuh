@@ -150,7 +150,8 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
 
 // tmap.cu: 3-D TMA map over [M][n][ld] floats, box 32 x rows x 1, 128B swizzle,
 // rows beyond n read as zero.
-cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows);
+cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows,
+                           int box_cols = 32);
 
 // sigma2_tc.cu (tensor cores, split TF32): the split workspace of a system
 // holds 4 * M*n*ld + n*ld floats (g32, gh, gl, VQ, V32; ld = n rounded up to 32).

@@ -1,6 +1,7 @@
 // TMA tensor maps for the split operand arrays: a 3-D map over [M][n][ld]
-// floats (ld = n rounded up to 32) whose box is 32 columns x `rows` rows x 1
-// matrix, 128-byte swizzled, rows beyond n zero-filled. The encoder comes from
+// floats (ld = n rounded up to 32) whose box is 32 columns (128-byte swizzle)
+// or 16 columns (64-byte swizzle) x `rows` rows x 1 matrix, rows beyond n
+// zero-filled. The encoder comes from
 // the driver through the runtime's entry-point lookup, so no link against
 // libcuda is needed.
 #include <cudaTypedefs.h>
@@ -28,18 +29,19 @@ void load_encoder() {
 }  // namespace
 
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld,
-                           int rows) {
+                           int rows, int box_cols) {
   std::call_once(g_encode_once, load_encoder);
   if (!g_encode) return cudaErrorNotSupported;
-  if (rows < 1 || rows > 256 || (ld % 32) != 0) return cudaErrorInvalidValue;
+  if (rows < 1 || rows > 256 || (ld % 32) != 0 || (box_cols != 32 && box_cols != 16))
+    return cudaErrorInvalidValue;
   const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)n, (cuuint64_t)M};
   const cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)n * (cuuint64_t)ld * 4};
-  const cuuint32_t box[3] = {32, (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
