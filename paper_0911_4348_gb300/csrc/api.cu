@@ -118,6 +118,8 @@ int build_mesh(fedvr_ctx *ctx, double beta, int u, int p, bool coef) {
     FEDVR_CK(ctx, launch_conv_coef(M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
                                    P<double>(ctx->w_wm), P<double>(ctx->w_wp),
                                    P<ConvCoef>(ctx->w_coef), ctx->stream));
+    ENSURE(ctx, w_coef32, (size_t)M * M * sizeof(int4));
+    FEDVR_CK(ctx, launch_coef32(M, P<ConvCoef>(ctx->w_coef), P<int4>(ctx->w_coef32), ctx->stream));
   }
   return FEDVR_OK;
 }
@@ -150,16 +152,17 @@ int eig(fedvr_ctx *ctx, double *A, const double *Vinit, double *eps, double *C) 
 }
 
 // Workspace of the tensor-core Sigma^(2) build: split operands, QV, V32, an
-// FP32 copy of Sigma (for the tensor-core convolution) and the error flag.
+// FP32 copy of Sigma followed by the diagonal operands B_ii of the first
+// convolution (both read by the tensor-core convolution) and the error flag.
 int tc_workspace(fedvr_ctx *ctx, int n, int M, float **ws, float **S32, int **err) {
   const size_t ld = (size_t)(n + 31) / 32 * 32;
   const size_t stack = (size_t)M * n * ld;
-  const size_t floats = 5 * stack + (size_t)n * ld + 64;
+  const size_t floats = 6 * stack + (size_t)n * ld + 64;
   ENSURE(ctx, w_tc, floats * sizeof(float));
   float *base = P<float>(ctx->w_tc);
   *ws = base;
-  *S32 = base + 4 * stack + (size_t)n * ld;
-  *err = reinterpret_cast<int *>(base + 5 * stack + (size_t)n * ld);
+  *S32 = base + 4 * stack + (size_t)n * ld;  // [2M][n][ld]: Sigma, then the diagonal operands
+  *err = reinterpret_cast<int *>(base + 6 * stack + (size_t)n * ld);
   return FEDVR_OK;
 }
 
@@ -190,7 +193,8 @@ int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *
   memset(&x, 0, sizeof(x));
   memset(&c, 0, sizeof(c));
   FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32));
-  FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, coef, I1, part));
+  (void)coef;
+  FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, P<int4>(ctx->w_coef32), I1, part));
   long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M, splits)};
   uint8_t *base = P<uint8_t>(ctx->w_tab);
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabX, &x, sizeof(x), cudaMemcpyHostToDevice, ctx->stream));
@@ -325,6 +329,14 @@ int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
   FEDVR_CK(ctx, launch_energy(n, M, ctx->spin, P<double>(ctx->b_h), V, G, S, P<double>(ctx->w_w),
                               P<double>(ctx->w_part), P<double>(ctx->w_red), s));
   *launches += 3;
+  if (ctx->precision == FEDVR_SPLIT_TF32) {
+    float *ws, *S32;
+    int *err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    FEDVR_CK(ctx, launch_diag_f32(n, M, P<double>(ctx->w_dHF), S, P<double>(ctx->w_wm),
+                                  P<double>(ctx->w_wp), S32, s));
+    *launches += 1;
+  }
   return FEDVR_OK;
 }
 
@@ -512,7 +524,8 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_w, &ctx->w_wm, &ctx->w_wp, &ctx->w_coef, &ctx->w_K, &ctx->w_phi,
                     &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
                     &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
-                    &ctx->w_K32, &ctx->w_tab, &ctx->w_btab, &ctx->w_c1p};
+                    &ctx->w_K32, &ctx->w_tab, &ctx->w_btab, &ctx->w_c1p,
+                    &ctx->w_coef32};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -1046,7 +1059,7 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
     cudaError_t e = xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32);
     if (e == cudaSuccess)
       e = c1sys_fill(&hc[k], c->n, c->M, 1, ws, S32, P<double>(c->w_dHF),
-                     P<ConvCoef>(c->w_coef), P<double>(c->w_I1), nullptr);
+                     P<int4>(c->w_coef32), P<double>(c->w_I1), nullptr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt + k * sizeof(XSys), &hx[k], sizeof(XSys),
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt + B->off_c + k * sizeof(C1Sys), &hc[k],
@@ -1279,6 +1292,8 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
       return r;
     FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
     FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s));
+    FEDVR_CK(ctx, launch_diag_f32(n, M, dHF, Sigma, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
+                                  S32, s));
     const TcGeom g = tc_geom(n, M);
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),

@@ -27,11 +27,9 @@ namespace fedvr {
 namespace {
 
 constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr uint32_t kTileA = 128 * 64;       // 128 rows x 16 floats (64-byte swizzled)
-constexpr int kRaw = 3;                      // raw source chunks in flight per producer
-constexpr uint32_t kRawSlot = 2 * 128 * 64;  // both bracket rows of 128 rows x 16 floats
+constexpr uint32_t kTileA = 128 * 64;  // 128 rows x 16 floats (64-byte swizzled)
 constexpr int kMaxStages = 6;
-constexpr int kWarps = 14;  // 0-3 flush, 4-11 A producers, 12 TMA, 13 MMA
+constexpr int kWarps = 14;  // 0-3 flush, 4-7 and 8-11 A producers (even / odd chunks), 12 TMA, 13 MMA
 constexpr int kThreads = kWarps * 32;
 
 // Item q of a system: split s = q / RT (split-major, so the CTAs running at
@@ -51,13 +49,14 @@ __device__ __forceinline__ C1Item c1_item(const C1Sys &S, long q) {
   return it;
 }
 
-// Walk over the (item, j, chunk) sequence of one CTA for the two rows r0 and
-// r0 + 64 of each tile that a producer thread owns.
+// Walk over the (item, j, chunk) sequence of one CTA for the four rows
+// r0 + 32 k of each tile that a producer thread owns.
 struct ProdCur {
   long w;
   int cur, n, M, ld, KC, j, j_hi, kc;
-  int i[2], a[2];
-  bool live[2], done;
+  int i[4], a[4];
+  unsigned live;  // bit k: row k exists
+  bool done;
 };
 
 __device__ __forceinline__ void pc_item(ProdCur &p, const C1Sys *sys, const long *prefix,
@@ -75,12 +74,14 @@ __device__ __forceinline__ void pc_item(ProdCur &p, const C1Sys *sys, const long
       p.j_hi = it.j_hi;
       p.kc = 0;
       const long R = (long)p.M * p.n;
+      p.live = 0;
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const long r = (long)it.t * 128 + r0 + 64 * k;
-        p.live[k] = r < R;
-        p.i[k] = p.live[k] ? (int)(r / p.n) : 0;
-        p.a[k] = p.live[k] ? (int)(r % p.n) : 0;
+      for (int k = 0; k < 4; ++k) {
+        const long r = (long)it.t * 128 + r0 + 32 * k;
+        const bool lv = r < R;
+        p.live |= (lv ? 1u : 0u) << k;
+        p.i[k] = lv ? (int)(r / p.n) : 0;
+        p.a[k] = lv ? (int)(r % p.n) : 0;
       }
       return;
     }
@@ -89,15 +90,49 @@ __device__ __forceinline__ void pc_item(ProdCur &p, const C1Sys *sys, const long
   p.done = true;
 }
 
-// Advance by one chunk; returns true when the mesh point (or item) changed.
-__device__ __forceinline__ bool pc_next(ProdCur &p, const C1Sys *sys, const long *prefix,
-                                        int n_sys, long items, int r0) {
-  if (++p.kc < p.KC) return false;
+// Advance by one chunk. Returns 0 (same mesh point), 1 (next mesh point of the
+// same item) or 2 (another item, or the end).
+__device__ __forceinline__ int pc_next(ProdCur &p, const C1Sys *sys, const long *prefix,
+                                       int n_sys, long items, int r0) {
+  if (++p.kc < p.KC) return 0;
   p.kc = 0;
-  if (++p.j < p.j_hi) return true;
+  if (++p.j < p.j_hi) return 1;
   p.w += gridDim.x;
   pc_item(p, sys, prefix, n_sys, items, r0);
-  return true;
+  return 2;
+}
+
+// Coefficients of the cursor's mesh point after it moved (how: 0 same mesh
+// point, 1 next mesh point, 2 new item). The loads are only issued here; they
+// are first used a whole group step later, when the next chunk's rows load.
+__device__ __forceinline__ void pc_coefs(const ProdCur &p, const C1Sys *sys, int4 (&cf)[4],
+                                         int how) {
+  if (p.done || how == 0) return;
+  const int4 *tab = sys[p.cur].coef32;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cf[k] = tab[(long)p.i[k] * p.M + p.j];
+}
+
+// Start the loads of the cursor's chunk: both source rows of the thread's
+// four rows (16-byte chunk c) and their weights.
+__device__ __forceinline__ void pc_load(const ProdCur &p, const C1Sys *sys, int c,
+                                        const int4 (&cf)[4], float4 (&s1)[4], float4 (&s2)[4],
+                                        float (&d1)[4], float (&d2)[4]) {
+  const float *S32 = sys[p.cur].S32;
+  const long nld = (long)p.n * p.ld;
+  const int l0 = p.kc * 16 + 4 * c;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d1[k] = __int_as_float(cf[k].z);
+    d2[k] = __int_as_float(cf[k].w);
+    if ((p.live >> k) & 1u) {
+      const long base = (long)p.a[k] * p.ld + l0;
+      s1[k] = *reinterpret_cast<const float4 *>(S32 + (long)cf[k].x * nld + base);
+      s2[k] = *reinterpret_cast<const float4 *>(S32 + (long)cf[k].y * nld + base);
+    } else {
+      s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -108,8 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                               ~uintptr_t(1023));
   const uint32_t tileB = (uint32_t)Np_max * 64;
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
-  uint8_t *raw = smem + nstage * stage_bytes;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(raw + kRaw * kRawSlot);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage * stage_bytes);
   uint64_t *full = bars, *empty = bars + kMaxStages, *accf = bars + 2 * kMaxStages,
            *acce = accf + 2, *drain = acce + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
@@ -122,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     for (int s = 0; s < nstage; ++s) {
-      tc::mbar_init(&full[s], 257);
+      tc::mbar_init(&full[s], 129);  // one producer group + the TMA thread
       tc::mbar_init(&empty[s], 1);
     }
     tc::mbar_init(&accf[0], 1);
@@ -141,122 +175,68 @@ __global__ void __launch_bounds__(kThreads, 1)
   int cur = 0;
 
   if (warp >= 4 && warp < 12) {
-    // ---- A producers: rows r0 and r0 + 64 of the tile, 16-byte chunk c of each
-    // 16-wide slice. The bracket rows Sigma_k1, Sigma_k2 of the next kRaw
-    // chunks stream into a per-thread ring by cp.async; each thread reads back
-    // only what it copied, so no barrier guards the ring. ----
-    const int pt = tid - 128, c = pt & 3, r0 = pt >> 2;
-    const uint32_t offA[2] = {tc::sw64_offset(r0, c), tc::sw64_offset(r0 + 64, c)};
-    uint32_t rofs[2][2];  // ring byte offsets: [bracket row][row k]
+    // ---- A producers. Group grp (warps 4-7 or 8-11) forms every other chunk
+    // (global chunk index q = grp, grp + 2, ...); a thread owns rows r0 + 32 k
+    // and 16-byte chunk c of the 16-wide slice. The two source rows of the
+    // group's next chunk are loaded into registers while the stage of the
+    // current one drains; a mesh point's coefficients are requested as soon as
+    // the cursor reaches it, one group step before their first use. Diagonal entries j = i read the precomputed B_ii
+    // (source row M + i), so every entry is c1 S_k1 + c2 S_k2. ----
+    const int grp = (warp - 4) >> 2;
+    const int gt = (tid - 128) & 127;
+    const int c = gt & 3, r0 = gt >> 2;
+    uint32_t offA[4];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      rofs[0][k] = (uint32_t)((r0 + 64 * k) * 64 + c * 16);
-      rofs[1][k] = (uint32_t)((128 + r0 + 64 * k) * 64 + c * 16);
-    }
-    ProdCur ip{}, cp{};
-    ip.w = cp.w = blockIdx.x;
-    ip.done = cp.done = false;
+    for (int k = 0; k < 4; ++k) offA[k] = tc::sw64_offset(r0 + 32 * k, c);
+    ProdCur ip{};
+    ip.w = blockIdx.x;
     pc_item(ip, sys, prefix, n_sys, items, r0);
-    pc_item(cp, sys, prefix, n_sys, items, r0);
-    uint32_t o1[2] = {0, 0}, o2[2] = {0, 0};  // issue side: element offsets into S32
-    float c1[2] = {0.f, 0.f}, c2[2] = {0.f, 0.f};
-    bool dg[2] = {false, false};
-    const float *iS32 = nullptr;
-    const double *dHF = nullptr;
-    auto issue_coefs = [&]() {
-      const C1Sys &S = sys[ip.cur];
-      iS32 = S.S32;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const ConvCoef cf = S.coef[(long)ip.i[k] * ip.M + ip.j];
-        const int k1 = cf.k, k2 = cf.diag ? (ip.M - 1) : (cf.k + 1);
-        o1[k] = (uint32_t)((k1 * ip.n + ip.a[k]) * ip.ld + 4 * c);
-        o2[k] = (uint32_t)((k2 * ip.n + ip.a[k]) * ip.ld + 4 * c);
-      }
-    };
-    auto consume_coefs = [&]() {
-      const C1Sys &S = sys[cp.cur];
-      dHF = S.dHF;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const ConvCoef cf = S.coef[(long)cp.i[k] * cp.M + cp.j];
-        c1[k] = (float)cf.c1;
-        c2[k] = (float)cf.c2;
-        dg[k] = cp.live[k] && cf.diag;
-      }
-    };
-    auto issue = [&](int slot) {
-      uint8_t *rs = raw + slot * kRawSlot;
-      const int l0 = ip.kc * 16;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const uint32_t b = ip.live[k] ? 16u : 0u;
-        tc::cp_async16(rs + rofs[0][k], iS32 + o1[k] + l0, b);
-        tc::cp_async16(rs + rofs[1][k], iS32 + o2[k] + l0, b);
-      }
-    };
-    if (!ip.done) issue_coefs();
-    if (!cp.done) consume_coefs();
-    for (int q = 0; q < kRaw; ++q) {
-      if (!ip.done) {
-        issue(q);
-        if (pc_next(ip, sys, prefix, n_sys, items, r0) && !ip.done) issue_coefs();
-      }
-      tc::cp_async_commit();
+    if (grp == 1 && !ip.done) pc_next(ip, sys, prefix, n_sys, items, r0);
+    int4 cf[4];  // {k1, k2, c1, c2} of ip's mesh point
+    if (!ip.done) pc_coefs(ip, sys, cf, 2);
+    float4 s1[4], s2[4];
+    float d1[4], d2[4];
+    bool have = !ip.done;
+    if (have) {
+      pc_load(ip, sys, c, cf, s1, s2, d1, d2);
+      for (int h = 0; h < 2 && !ip.done; ++h)
+        pc_coefs(ip, sys, cf, pc_next(ip, sys, prefix, n_sys, items, r0));
     }
-    int slot = 0, st = 0;
-    uint32_t u = 0;
-    while (!cp.done && !*abort_flag) {
-      tc::cp_async_wait<kRaw - 1>();
-      const uint8_t *rs = raw + slot * kRawSlot;
-      float x[2][4];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float4 s1 = *reinterpret_cast<const float4 *>(rs + rofs[0][k]);
-        const float4 s2 = *reinterpret_cast<const float4 *>(rs + rofs[1][k]);
-        x[k][0] = fmaf(c1[k], s1.x, c2[k] * s2.x);
-        x[k][1] = fmaf(c1[k], s1.y, c2[k] * s2.y);
-        x[k][2] = fmaf(c1[k], s1.z, c2[k] * s2.z);
-        x[k][3] = fmaf(c1[k], s1.w, c2[k] * s2.w);
-        if (dg[k]) {  // B_ii carries the HF self-energy change
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            const int l = cp.kc * 16 + 4 * c + qq;
-            if (l < cp.n) x[k][qq] += (float)dHF[(long)cp.a[k] * cp.n + l];
-          }
-        }
-      }
+    int st = grp % nstage;
+    uint32_t u = (uint32_t)(grp / nstage);
+    while (have && !*abort_flag) {
       if (u > 0 && !tc::mbar_wait(&empty[st], (u - 1) & 1, kWaitNs)) {
         *abort_flag = 1;
         break;
       }
       uint8_t *sa = smem + st * stage_bytes;
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float4 hi = make_float4(tc::tf32_rna(x[k][0]), tc::tf32_rna(x[k][1]),
-                                      tc::tf32_rna(x[k][2]), tc::tf32_rna(x[k][3]));
-        const float4 lo =
-            make_float4(tc::tf32_rna(x[k][0] - hi.x), tc::tf32_rna(x[k][1] - hi.y),
-                        tc::tf32_rna(x[k][2] - hi.z), tc::tf32_rna(x[k][3] - hi.w));
+      for (int k = 0; k < 4; ++k) {
+        const float x0 = fmaf(d1[k], s1[k].x, d2[k] * s2[k].x);
+        const float x1 = fmaf(d1[k], s1[k].y, d2[k] * s2[k].y);
+        const float x2 = fmaf(d1[k], s1[k].z, d2[k] * s2[k].z);
+        const float x3 = fmaf(d1[k], s1[k].w, d2[k] * s2[k].w);
+        const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
+                                      tc::tf32_rna(x3));
+        const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
+                                      tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
         *reinterpret_cast<float4 *>(sa + offA[k]) = hi;
         *reinterpret_cast<float4 *>(sa + kTileA + offA[k]) = lo;
       }
       tc::fence_smem_to_async();
       tc::mbar_arrive(&full[st]);
-      // refill the ring slot just read with the chunk kRaw ahead
-      if (!ip.done) {
-        issue(slot);
-        if (pc_next(ip, sys, prefix, n_sys, items, r0) && !ip.done) issue_coefs();
-      }
-      tc::cp_async_commit();
-      slot = (slot + 1 == kRaw) ? 0 : slot + 1;
-      if (++st == nstage) {
-        st = 0;
+      st += 2;
+      while (st >= nstage) {
+        st -= nstage;
         ++u;
       }
-      if (pc_next(cp, sys, prefix, n_sys, items, r0) && !cp.done) consume_coefs();
+      have = !ip.done;
+      if (have) {  // the group's next chunk: in flight while that stage drains
+        pc_load(ip, sys, c, cf, s1, s2, d1, d2);
+        for (int h = 0; h < 2 && !ip.done; ++h)
+          pc_coefs(ip, sys, cf, pc_next(ip, sys, prefix, n_sys, items, r0));
+      }
     }
-    tc::cp_async_wait<0>();
   } else if (warp == 12) {
     // ---- TMA: g_j rows 0..Np-1, 16 columns per chunk, hi and lo ----
     if (lane == 0) {
@@ -401,6 +381,40 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+__global__ void coef32_kernel(long mm, int M, const ConvCoef *__restrict__ coef,
+                              int4 *__restrict__ out) {
+  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < mm;
+       x += (long)gridDim.x * blockDim.x) {
+    const ConvCoef c = coef[x];
+    if (c.diag) {
+      const int i = (int)(x / M);
+      out[x] = make_int4(M + i, M + i, __float_as_int(1.f), __float_as_int(0.f));
+    } else {
+      out[x] = make_int4(c.k, c.k + 1, __float_as_int((float)c.c1), __float_as_int((float)c.c2));
+    }
+  }
+}
+
+// D_i = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} at rows M + i of S32 (zero padded to ld).
+__global__ void diag_f32_kernel(int n, int M, int ld, const double *__restrict__ dHF,
+                                const double *__restrict__ S, const double *__restrict__ wm,
+                                const double *__restrict__ wp, float *__restrict__ D) {
+  const long nn = (long)n * n, total = (long)M * n * ld;
+  const double *S0 = S, *S1 = S + (long)(M - 1) * nn;
+  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (long)gridDim.x * blockDim.x) {
+    const long row = x / ld;
+    const int c = (int)(x % ld);
+    const int i = (int)(row / n), a = (int)(row % n);
+    float v = 0.f;
+    if (c < n) {
+      const long e = (long)a * n + c;
+      v = (float)(dHF[e] - wm[i] * S0[e] + wp[i] * S1[e]);
+    }
+    D[x] = v;
+  }
+}
+
 // I1 += part[0] + part[1] + ... (fixed order).
 __global__ void conv1_sum_splits_kernel(long count, int nparts, const double *__restrict__ part,
                                         double *__restrict__ I1) {
@@ -433,7 +447,7 @@ cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaS
 }
 
 cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
-                       const double *dHF, const ConvCoef *coef, double *I1, double *part) {
+                       const double *dHF, const int4 *coef32, double *I1, double *part) {
   d->g = tc_geom(n, M);
   const long stack = (long)M * n * d->g.ld;
   d->JB = 4096 / n > 1 ? 4096 / n : 1;
@@ -441,7 +455,7 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
   d->RT = (int)(((long)M * n + 127) / 128);
   d->S32 = S32;
   d->dHF = dHF;
-  d->coef = coef;
+  d->coef32 = coef32;
   d->I1 = I1;
   d->part = part;
   for (int t = 0; t < 2; ++t) {
@@ -453,6 +467,19 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
   return cudaSuccess;
 }
 
+cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma,
+                            const double *wm, const double *wp, float *S32, cudaStream_t s) {
+  const int ld = (n + 31) / 32 * 32;
+  diag_f32_kernel<<<1024, 256, 0, s>>>(n, M, ld, dHF, Sigma, wm, wp,
+                                       S32 + (long)M * n * ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coef32(int M, const ConvCoef *coef, int4 *out, cudaStream_t s) {
+  coef32_kernel<<<512, 256, 0, s>>>((long)M * M, M, coef, out);
+  return cudaGetLastError();
+}
+
 cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
                              cudaStream_t s) {
   if (nparts < 1) return cudaSuccess;
@@ -461,17 +488,16 @@ cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double 
 }
 
 // Shared memory of the convolution kernel: operand stages (as many as fit,
-// at most kMaxStages), the raw-source ring and the barriers.
+// at most kMaxStages) and the barriers.
 static int conv1_stages(int Np_max) {
   const size_t stage = 2 * (size_t)kTileA + 2 * (size_t)Np_max * 64;
-  const size_t fixed = 1024 + (size_t)kRaw * kRawSlot + 256;
+  const size_t fixed = 1024 + 256;
   int ns = (int)((232448 - fixed) / stage);
   return ns > kMaxStages ? kMaxStages : ns;
 }
 
 static size_t conv1_smem_bytes(int Np_max, int nstage) {
-  return 1024 + (size_t)nstage * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 64) +
-         (size_t)kRaw * kRawSlot + 256;
+  return 1024 + (size_t)nstage * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 64) + 256;
 }
 
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,

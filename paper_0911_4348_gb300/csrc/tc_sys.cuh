@@ -39,7 +39,7 @@ struct C1Sys {
   int RT;                     // 128-row tiles of the stacked (i, a) rows
   const float *S32;
   const double *dHF;
-  const ConvCoef *coef;
+  const int4 *coef32;         // per (i, j): {k1, k2, c1, c2 (float bits)}
   double *I1;                 // output (split 0 and the final sum)
   double *part;               // splits 1..S-1: [S-1][M][n][n]
 };
@@ -53,7 +53,15 @@ size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns);
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
                       float *S32);
 cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
-                       const double *dHF, const ConvCoef *coef, double *I1, double *part);
+                       const double *dHF, const int4 *coef32, double *I1, double *part);
+// Compact FP32 convolution coefficients {k1, k2, (float)c1, (float)c2} per
+// (i, j) over the extended FP32 source stack [2M][n][ld]: rows k < M are
+// Sigma_k, row M + i is the diagonal operand B_ii, taken with weight 1.
+cudaError_t launch_coef32(int M, const ConvCoef *coef, int4 *out, cudaStream_t s);
+// Diagonal operands B_ii = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} (FP64 sum,
+// rounded to FP32) into rows M..2M-1 of the FP32 source stack S32.
+cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma,
+                            const double *wm, const double *wp, float *S32, cudaStream_t s);
 // I1 += part[0] + ... + part[nparts-1] (count doubles each), fixed order.
 cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
                              cudaStream_t s);
