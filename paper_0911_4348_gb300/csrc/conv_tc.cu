@@ -27,18 +27,17 @@ namespace fedvr {
 namespace {
 
 constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr uint32_t kTileA = 128 * 64;  // 128 rows x 16 floats (64-byte swizzled)
-constexpr int kMaxStages = 6;
-constexpr int kWarps = 14;  // 0-3 flush, 4-7 and 8-11 A producers (even / odd chunks), 12 TMA, 13 MMA
+constexpr uint32_t kTileA = 128 * 128;
+constexpr int kWarps = 14;  // 0-3 flush, 4-11 A producers, 12 TMA, 13 MMA
 constexpr int kThreads = kWarps * 32;
 
-// Item q of a system: split s = q / RT (split-major, so the CTAs running at
-// the same time walk the same mesh points and share g_j in L2), tile t.
 struct C1Item {
   int t, j_lo, j_hi;
   double *out;  // I1 or the split's partial stack
 };
 
+// Item q of a system: split s = q / RT (split-major, so that the CTAs running
+// at the same time walk the same mesh points and share g_j in L2), tile t.
 __device__ __forceinline__ C1Item c1_item(const C1Sys &S, long q) {
   C1Item it;
   const int s = (int)(q / S.RT);
@@ -49,104 +48,17 @@ __device__ __forceinline__ C1Item c1_item(const C1Sys &S, long q) {
   return it;
 }
 
-// Walk over the (item, j, chunk) sequence of one CTA for the four rows
-// r0 + 32 k of each tile that a producer thread owns.
-struct ProdCur {
-  long w;
-  int cur, n, M, ld, KC, j, j_hi, kc;
-  int i[4], a[4];
-  unsigned live;  // bit k: row k exists
-  bool done;
-};
-
-__device__ __forceinline__ void pc_item(ProdCur &p, const C1Sys *sys, const long *prefix,
-                                        int n_sys, long items, int r0) {
-  while (p.w < items) {
-    while (p.cur + 1 < n_sys && p.w >= prefix[p.cur + 1]) ++p.cur;
-    const C1Sys &S = sys[p.cur];
-    const C1Item it = c1_item(S, p.w - prefix[p.cur]);
-    if (it.j_lo < it.j_hi) {
-      p.n = S.g.n;
-      p.M = S.g.M;
-      p.ld = S.g.ld;
-      p.KC = (S.g.n + 15) / 16;
-      p.j = it.j_lo;
-      p.j_hi = it.j_hi;
-      p.kc = 0;
-      const long R = (long)p.M * p.n;
-      p.live = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const long r = (long)it.t * 128 + r0 + 32 * k;
-        const bool lv = r < R;
-        p.live |= (lv ? 1u : 0u) << k;
-        p.i[k] = lv ? (int)(r / p.n) : 0;
-        p.a[k] = lv ? (int)(r % p.n) : 0;
-      }
-      return;
-    }
-    p.w += gridDim.x;
-  }
-  p.done = true;
-}
-
-// Advance by one chunk. Returns 0 (same mesh point), 1 (next mesh point of the
-// same item) or 2 (another item, or the end).
-__device__ __forceinline__ int pc_next(ProdCur &p, const C1Sys *sys, const long *prefix,
-                                       int n_sys, long items, int r0) {
-  if (++p.kc < p.KC) return 0;
-  p.kc = 0;
-  if (++p.j < p.j_hi) return 1;
-  p.w += gridDim.x;
-  pc_item(p, sys, prefix, n_sys, items, r0);
-  return 2;
-}
-
-// Coefficients of the cursor's mesh point after it moved (how: 0 same mesh
-// point, 1 next mesh point, 2 new item). The loads are only issued here; they
-// are first used a whole group step later, when the next chunk's rows load.
-__device__ __forceinline__ void pc_coefs(const ProdCur &p, const C1Sys *sys, int4 (&cf)[4],
-                                         int how) {
-  if (p.done || how == 0) return;
-  const int4 *tab = sys[p.cur].coef32;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) cf[k] = tab[(long)p.i[k] * p.M + p.j];
-}
-
-// Start the loads of the cursor's chunk: both source rows of the thread's
-// four rows (16-byte chunk c) and their weights.
-__device__ __forceinline__ void pc_load(const ProdCur &p, const C1Sys *sys, int c,
-                                        const int4 (&cf)[4], float4 (&s1)[4], float4 (&s2)[4],
-                                        float (&d1)[4], float (&d2)[4]) {
-  const float *S32 = sys[p.cur].S32;
-  const long nld = (long)p.n * p.ld;
-  const int l0 = p.kc * 16 + 4 * c;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    d1[k] = __int_as_float(cf[k].z);
-    d2[k] = __int_as_float(cf[k].w);
-    if ((p.live >> k) & 1u) {
-      const long base = (long)p.a[k] * p.ld + l0;
-      s1[k] = *reinterpret_cast<const float4 *>(S32 + (long)cf[k].x * nld + base);
-      s2[k] = *reinterpret_cast<const float4 *>(S32 + (long)cf[k].y * nld + base);
-    } else {
-      s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     conv1_tc_kernel(const C1Sys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
-                    long items, int Np_max, int nstage, int nbuf, int *err) {
+                    long items, int Np_max, int nbuf, int *err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
-  const uint32_t tileB = (uint32_t)Np_max * 64;
+  const uint32_t tileB = (uint32_t)Np_max * 128;
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage * stage_bytes);
-  uint64_t *full = bars, *empty = bars + kMaxStages, *accf = bars + 2 * kMaxStages,
-           *acce = accf + 2, *drain = acce + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
+  uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -155,10 +67,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < nstage; ++s) {
-      tc::mbar_init(&full[s], 129);  // one producer group + the TMA thread
-      tc::mbar_init(&empty[s], 1);
-    }
+    tc::mbar_init(&full[0], 257);
+    tc::mbar_init(&full[1], 257);
+    tc::mbar_init(&empty[0], 1);
+    tc::mbar_init(&empty[1], 1);
     tc::mbar_init(&accf[0], 1);
     tc::mbar_init(&accf[1], 1);
     tc::mbar_init(&acce[0], 128);
@@ -175,95 +87,100 @@ __global__ void __launch_bounds__(kThreads, 1)
   int cur = 0;
 
   if (warp >= 4 && warp < 12) {
-    // ---- A producers. Group grp (warps 4-7 or 8-11) forms every other chunk
-    // (global chunk index q = grp, grp + 2, ...); a thread owns rows r0 + 32 k
-    // and 16-byte chunk c of the 16-wide slice. The two source rows of the
-    // group's next chunk are loaded into registers while the stage of the
-    // current one drains; a mesh point's coefficients are requested as soon as
-    // the cursor reaches it, one group step before their first use. Diagonal entries j = i read the precomputed B_ii
-    // (source row M + i), so every entry is c1 S_k1 + c2 S_k2. ----
-    const int grp = (warp - 4) >> 2;
-    const int gt = (tid - 128) & 127;
-    const int c = gt & 3, r0 = gt >> 2;
-    uint32_t offA[4];
+    // ---- A producers: rows r0 + 32 k of the tile, 16-byte chunk c of each 32-wide slice ----
+    const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
+    uint32_t off[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) offA[k] = tc::sw64_offset(r0 + 32 * k, c);
-    ProdCur ip{};
-    ip.w = blockIdx.x;
-    pc_item(ip, sys, prefix, n_sys, items, r0);
-    if (grp == 1 && !ip.done) pc_next(ip, sys, prefix, n_sys, items, r0);
-    int4 cf[4];  // {k1, k2, c1, c2} of ip's mesh point
-    if (!ip.done) pc_coefs(ip, sys, cf, 2);
-    float4 s1[4], s2[4];
-    float d1[4], d2[4];
-    bool have = !ip.done;
-    if (have) {
-      pc_load(ip, sys, c, cf, s1, s2, d1, d2);
-      for (int h = 0; h < 2 && !ip.done; ++h)
-        pc_coefs(ip, sys, cf, pc_next(ip, sys, prefix, n_sys, items, r0));
-    }
-    int st = grp % nstage;
-    uint32_t u = (uint32_t)(grp / nstage);
-    while (have && !*abort_flag) {
-      if (u > 0 && !tc::mbar_wait(&empty[st], (u - 1) & 1, kWaitNs)) {
-        *abort_flag = 1;
-        break;
-      }
-      uint8_t *sa = smem + st * stage_bytes;
+    for (int k = 0; k < 4; ++k) off[k] = tc::sw128_offset(r0 + 32 * k, c);
+    uint32_t cc = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const C1Sys &S = sys[cur];
+      const int n = S.g.n, ld = S.g.ld, M = S.g.M, KC = S.g.KC;
+      const long R = (long)M * n;
+      const C1Item it = c1_item(S, w - prefix[cur]);
+      int ia[4], aa[4];
+      bool live[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float x0 = fmaf(d1[k], s1[k].x, d2[k] * s2[k].x);
-        const float x1 = fmaf(d1[k], s1[k].y, d2[k] * s2[k].y);
-        const float x2 = fmaf(d1[k], s1[k].z, d2[k] * s2[k].z);
-        const float x3 = fmaf(d1[k], s1[k].w, d2[k] * s2[k].w);
-        const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
-                                      tc::tf32_rna(x3));
-        const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
-                                      tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
-        *reinterpret_cast<float4 *>(sa + offA[k]) = hi;
-        *reinterpret_cast<float4 *>(sa + kTileA + offA[k]) = lo;
+        const long r = (long)it.t * 128 + r0 + 32 * k;
+        live[k] = r < R;
+        ia[k] = live[k] ? (int)(r / n) : 0;
+        aa[k] = live[k] ? (int)(r % n) : 0;
       }
-      tc::fence_smem_to_async();
-      tc::mbar_arrive(&full[st]);
-      st += 2;
-      while (st >= nstage) {
-        st -= nstage;
-        ++u;
-      }
-      have = !ip.done;
-      if (have) {  // the group's next chunk: in flight while that stage drains
-        pc_load(ip, sys, c, cf, s1, s2, d1, d2);
-        for (int h = 0; h < 2 && !ip.done; ++h)
-          pc_coefs(ip, sys, cf, pc_next(ip, sys, prefix, n_sys, items, r0));
+      for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
+        uint32_t o1[4], o2[4];  // element offsets into S32 ([2M][n][ld] < 2^31)
+        float c1[4], c2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int4 cf = S.coef32[(long)ia[k] * M + j];
+          o1[k] = (uint32_t)((cf.x * n + aa[k]) * ld + 4 * c);
+          o2[k] = (uint32_t)((cf.y * n + aa[k]) * ld + 4 * c);
+          c1[k] = __int_as_float(cf.z);
+          c2[k] = __int_as_float(cf.w);
+        }
+        for (int kc = 0; kc < KC; ++kc, ++cc) {
+          const int l0 = kc * 32;
+          float4 s1[4], s2[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (live[k]) {
+              s1[k] = *reinterpret_cast<const float4 *>(S.S32 + o1[k] + l0);
+              s2[k] = *reinterpret_cast<const float4 *>(S.S32 + o2[k] + l0);
+            } else {
+              s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+          const int s = cc & 1;
+          const uint32_t use = cc >> 1;
+          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+          uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            // S32 rows are zero beyond n, so the padded columns come out zero;
+            // the diagonal entry j = i reads its precomputed B_ii (row M + i)
+            float x[4] = {fmaf(c1[k], s1[k].x, c2[k] * s2[k].x),
+                          fmaf(c1[k], s1[k].y, c2[k] * s2[k].y),
+                          fmaf(c1[k], s1[k].z, c2[k] * s2[k].z),
+                          fmaf(c1[k], s1[k].w, c2[k] * s2[k].w)};
+            const float4 hi = make_float4(tc::tf32_rna(x[0]), tc::tf32_rna(x[1]),
+                                          tc::tf32_rna(x[2]), tc::tf32_rna(x[3]));
+            const float4 lo = make_float4(tc::tf32_rna(x[0] - hi.x), tc::tf32_rna(x[1] - hi.y),
+                                          tc::tf32_rna(x[2] - hi.z), tc::tf32_rna(x[3] - hi.w));
+            *reinterpret_cast<float4 *>(st + off[k]) = hi;
+            *reinterpret_cast<float4 *>(st + kTileA + off[k]) = lo;
+          }
+          tc::fence_smem_to_async();
+          tc::mbar_arrive(&full[s]);
+        }
       }
     }
   } else if (warp == 12) {
-    // ---- TMA: g_j rows 0..Np-1, 16 columns per chunk, hi and lo ----
+    // ---- TMA: g_j rows 0..Np-1, 32 columns per chunk, hi and lo ----
     if (lane == 0) {
-      int st = 0;
-      uint32_t u = 0;
+      uint32_t cc = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const C1Sys &S = sys[cur];
         const C1Item it = c1_item(S, w - prefix[cur]);
-        const uint32_t bytes = 2u * (uint32_t)S.g.Np * 64u;
-        const int KC = (S.g.n + 15) / 16;
+        const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
         for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-          for (int kc = 0; kc < KC; ++kc) {
-            if (u > 0 && !tc::mbar_wait(&empty[st], (u - 1) & 1, kWaitNs)) {
+          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
               *abort_flag = 1;
               break;
             }
-            uint8_t *sb = smem + st * stage_bytes + 2 * kTileA;
-            tc::mbar_arrive_expect_tx(&full[st], bytes);
+            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+            tc::mbar_arrive_expect_tx(&full[s], bytes);
             for (int nt = 0; nt < S.g.NT; ++nt) {
-              tc::tma_load_3d(sb + S.g.n0[nt] * 64, &S.th[nt], kc * 16, S.g.n0[nt], j, &full[st]);
-              tc::tma_load_3d(sb + tileB + S.g.n0[nt] * 64, &S.tl[nt], kc * 16, S.g.n0[nt], j,
-                              &full[st]);
-            }
-            if (++st == nstage) {
-              st = 0;
-              ++u;
+              tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt], j, &full[s]);
+              tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt], j,
+                              &full[s]);
             }
           }
         }
@@ -272,13 +189,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 13) {
     // ---- MMA issue: one accumulator block per JB mesh points ----
     if (lane == 0) {
-      int st = 0;
-      uint32_t u = 0, tcount = 0;
+      uint32_t cc = 0, tcount = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const C1Sys &S = sys[cur];
         const C1Item it = c1_item(S, w - prefix[cur]);
-        const int n = S.g.n, KC = (n + 15) / 16;
+        const int n = S.g.n;
         for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += S.JB, ++tcount) {
           const int j1 = min(it.j_hi, j0 + S.JB);
           const int buf = tcount & 1;
@@ -295,22 +211,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::fence_after_sync();
           const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
           for (int j = j0; j < j1 && !*abort_flag; ++j) {
-            for (int kc = 0; kc < KC; ++kc) {
-              if (!tc::mbar_wait(&full[st], u & 1, kWaitNs)) {
+            for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+              const int s = cc & 1;
+              const uint32_t use = cc >> 1;
+              if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
                 *abort_flag = 1;
                 break;
               }
               tc::fence_after_sync();
-              const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
-              const int ksteps = min(2, (n - kc * 16 + 7) / 8);
+              const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
+              const int ksteps = min(4, (n - kc * 32 + 7) / 8);
               const bool fresh = (j == j0 && kc == 0);
               for (int kk = 0; kk < ksteps; ++kk) {
-                const uint64_t ah = tc::sdesc_k64(sa + kk * 32);
-                const uint64_t al = tc::sdesc_k64(sa + kTileA + kk * 32);
+                const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+                const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
                 for (int nt = 0; nt < S.g.NT; ++nt) {
-                  const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 64 + kk * 32;
-                  const uint64_t bh = tc::sdesc_k64(sa + boff);
-                  const uint64_t bl = tc::sdesc_k64(sa + boff + tileB);
+                  const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
+                  const uint64_t bh = tc::sdesc_k128(sa + boff);
+                  const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
                   const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
                   const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
                   tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
@@ -318,12 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   tc::mma_tf32(d, al, bh, idesc, 1u);
                 }
               }
-              tc::mma_commit(&empty[st]);
+              tc::mma_commit(&empty[s]);
               issued = true;
-              if (++st == nstage) {
-                st = 0;
-                ++u;
-              }
             }
           }
           tc::mma_commit(&accf[buf]);
@@ -459,9 +373,8 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
   d->I1 = I1;
   d->part = part;
   for (int t = 0; t < 2; ++t) {
-    cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t], 16);
-    if (e == cudaSuccess)
-      e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t], 16);
+    cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t]);
+    if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -487,31 +400,15 @@ cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double 
   return cudaGetLastError();
 }
 
-// Shared memory of the convolution kernel: operand stages (as many as fit,
-// at most kMaxStages) and the barriers.
-static int conv1_stages(int Np_max) {
-  const size_t stage = 2 * (size_t)kTileA + 2 * (size_t)Np_max * 64;
-  const size_t fixed = 1024 + 256;
-  int ns = (int)((232448 - fixed) / stage);
-  return ns > kMaxStages ? kMaxStages : ns;
-}
-
-static size_t conv1_smem_bytes(int Np_max, int nstage) {
-  return 1024 + (size_t)nstage * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 64) + 256;
-}
-
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
                             int Np_max, int *err, int num_sms, cudaStream_t s) {
-  const int nstage = conv1_stages(Np_max);
-  if (nstage < 2) return cudaErrorInvalidValue;
-  const size_t smem = conv1_smem_bytes(Np_max, nstage);
+  const size_t smem = tc_smem_bytes(Np_max, 0, false);
   cudaError_t e = cudaFuncSetAttribute(conv1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
-  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(sys, prefix, n_sys, items, Np_max, nstage, nbuf,
-                                               err);
+  conv1_tc_kernel<<<grid, kThreads, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
   return cudaGetLastError();
 }
 
