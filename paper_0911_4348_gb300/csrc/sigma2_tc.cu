@@ -6,13 +6,15 @@
 //
 // The first bracket term is the direct term sigma g o (V Q V), the second the
 // second-order exchange X. P^(b) is the only O(n^3)-per-column contraction
-// (O(n^4) per mesh point): it runs as tcgen05.mma kind::tf32 with 128 rows a
-// per tile, all k in one or two N tiles and the contraction over l in
-// 32-wide chunks, each operand split as x = hi + lo (TF32) and the product
-// taken as hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM. The A operand
-// g_al V_bl is formed by the CUDA cores while the previous chunk multiplies;
-// the epilogue reads P from TMEM and folds the k-sum in FP32. Only rows a >= b
-// are formed; the symmetric result is mirrored.
+// (O(n^4) per mesh point): it runs as tcgen05.mma kind::tf32 over the rows
+// (b, a), a >= b, of one mesh point stacked into n(n+1)/2 rows (128 per tile,
+// tiles full except the last), all k in one or two N tiles and the
+// contraction over l in 32-wide chunks, each operand split as x = hi + lo
+// (TF32) and the product taken as hi*hi + hi*lo + lo*hi with FP32
+// accumulation in TMEM. The A operand g_al V_bl of each row is formed by the
+// CUDA cores while the previous chunk multiplies; B = gb is the same for every
+// row of the mesh point. The epilogue reads row (b, a) of P^(b) from TMEM and
+// folds the k-sum in FP32; the symmetric result is mirrored.
 #include "common.cuh"
 #include "tc.cuh"
 #include "tc_sys.cuh"
@@ -92,18 +94,34 @@ __global__ void __launch_bounds__(256) vq_kernel(int n, int M, int ld,
   }
 }
 
+// Row r of the stacked lower triangle of one mesh point: rows ordered by b,
+// then a = b..n-1, so row b starts at off(b) = b n - b (b - 1) / 2.
+__device__ __forceinline__ long tri_off(int n, int b) { return (long)b * n - (long)b * (b - 1) / 2; }
+
+__device__ __forceinline__ void tri_row(int n, long r, int *b, int *a) {
+  const double h = 2.0 * n + 1.0;
+  int bb = (int)((h - sqrt(fmax(h * h - 8.0 * (double)r, 0.0))) * 0.5);
+  if (bb < 0) bb = 0;
+  if (bb > n - 1) bb = n - 1;
+  while (bb > 0 && tri_off(n, bb) > r) --bb;
+  while (bb + 1 < n && tri_off(n, bb + 1) <= r) ++bb;
+  *b = bb;
+  *a = bb + (int)(r - tri_off(n, bb));
+}
+
 // Warp roles: 0-3 epilogue (TMEM lanes 0-127), 4-11 A-operand producers,
 // 12 TMA loads of the gb operand, 13 MMA issue. Stages handed over with
 // mbarriers: full[s] (256 producer arrivals + TMA bytes), empty[s] (MMA
 // commit); accumulators double-buffered with accf/acce. The work queue is the
-// concatenation of the (j, b) items of every system in the table; every role
-// walks it in the same order. The stage layout uses the table's largest N.
+// concatenation of the (j, row tile) items of every system in the table
+// (mesh-point-major, so that concurrent CTAs share gb in L2); every role walks
+// it in the same order. The stage layout uses the table's largest N.
 constexpr int kWarps2 = 14;
 constexpr int kThreads2 = kWarps2 * 32;
 
 __global__ void __launch_bounds__(kThreads2, 1)
     exchange_tc_kernel(const XSys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
-                       long items, int Np_max, int ld_max, int nbuf, int *err) {
+                       long items, int Np_max, int nbuf, int *err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -113,8 +131,6 @@ __global__ void __launch_bounds__(kThreads2, 1)
   uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  float *gcol = reinterpret_cast<float *>(tmem_slot + 4);
-  float *qcol = gcol + ld_max;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -142,50 +158,62 @@ __global__ void __launch_bounds__(kThreads2, 1)
   int cur = 0;  // system of the current item (items ascend within a CTA)
 
   if (warp >= 4 && warp < 12) {
-    // ---- A producers: A(a, l) = g_al * V_bl, split hi/lo, 4 rows per thread ----
+    // ---- A producers: row (b, a): A(l) = g_al * V_bl, split hi/lo, 4 rows per thread ----
     const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
     uint32_t cc = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
       const int n = S.g.n, ld = S.g.ld;
+      const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
       const long q = w - prefix[cur];
-      const int j = (int)(q / n), b = (int)(q % n);
+      const int j = (int)(q / RT);
+      const long t = q % RT;
       const float *gA = S.g32 + (long)j * n * ld;
-      const float *Vb = S.V32 + (long)b * ld;
-      for (int mt = b >> 7; mt < S.g.MT && !*abort_flag; ++mt) {
-        for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
-          const int l0 = kc * 32;
-          const float4 vv = *reinterpret_cast<const float4 *>(Vb + l0 + 4 * c);
-          float4 gv[4];
+      uint32_t og[4], ov[4];  // element offsets of row a of g_j and row b of V
+      bool live[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int a = mt * 128 + r0 + 32 * k;
-            gv[k] = (a < n) ? *reinterpret_cast<const float4 *>(gA + (long)a * ld + l0 + 4 * c)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-          const int s = cc & 1;
-          const uint32_t use = cc >> 1;
-          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-            *abort_flag = 1;
-            break;
-          }
-          uint8_t *st = smem + s * stage_bytes;
+      for (int k = 0; k < 4; ++k) {
+        const long r = t * 128 + r0 + 32 * k;
+        live[k] = r < T;
+        int b = 0, a = 0;
+        if (live[k]) tri_row(n, r, &b, &a);
+        og[k] = (uint32_t)(a * ld + 4 * c);
+        ov[k] = (uint32_t)(b * ld + 4 * c);
+      }
+      for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+        const int l0 = kc * 32;
+        float4 gv[4], vv[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float x0 = gv[k].x * vv.x, x1 = gv[k].y * vv.y, x2 = gv[k].z * vv.z,
-                        x3 = gv[k].w * vv.w;
-            const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
-                                          tc::tf32_rna(x3));
-            const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
-                                          tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
-            const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
-            *reinterpret_cast<float4 *>(st + off) = hi;
-            *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+        for (int k = 0; k < 4; ++k) {
+          if (live[k]) {
+            gv[k] = *reinterpret_cast<const float4 *>(gA + og[k] + l0);
+            vv[k] = *reinterpret_cast<const float4 *>(S.V32 + ov[k] + l0);
+          } else {
+            gv[k] = vv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          tc::fence_smem_to_async();
-          tc::mbar_arrive(&full[s]);
         }
+        const int s = cc & 1;
+        const uint32_t use = cc >> 1;
+        if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float x0 = gv[k].x * vv[k].x, x1 = gv[k].y * vv[k].y, x2 = gv[k].z * vv[k].z,
+                      x3 = gv[k].w * vv[k].w;
+          const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
+                                        tc::tf32_rna(x3));
+          const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
+                                        tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
+          const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
+          *reinterpret_cast<float4 *>(st + off) = hi;
+          *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+        }
+        tc::fence_smem_to_async();
+        tc::mbar_arrive(&full[s]);
       }
     }
   } else if (warp == 12) {
@@ -196,142 +224,133 @@ __global__ void __launch_bounds__(kThreads2, 1)
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const XSys &S = sys[cur];
         const int n = S.g.n;
-        const long q = w - prefix[cur];
-        const int j = (int)(q / n), b = (int)(q % n);
+        const long RT = ((long)n * (n + 1) / 2 + 127) / 128;
+        const int j = (int)((w - prefix[cur]) / RT);
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
-        for (int mt = b >> 7; mt < S.g.MT && !*abort_flag; ++mt) {
-          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
-            const int s = cc & 1;
-            const uint32_t use = cc >> 1;
-            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-              *abort_flag = 1;
-              break;
-            }
-            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
-            tc::mbar_arrive_expect_tx(&full[s], bytes);
-            for (int nt = 0; nt < S.g.NT; ++nt) {
-              tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt],
-                              S.g.M - 1 - j, &full[s]);
-              tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt],
-                              S.g.M - 1 - j, &full[s]);
-            }
+        for (int kc = 0; kc < S.g.KC && !*abort_flag; ++kc, ++cc) {
+          const int s = cc & 1;
+          const uint32_t use = cc >> 1;
+          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+          uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+          tc::mbar_arrive_expect_tx(&full[s], bytes);
+          for (int nt = 0; nt < S.g.NT; ++nt) {
+            tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt], S.g.M - 1 - j,
+                            &full[s]);
+            tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt],
+                            S.g.M - 1 - j, &full[s]);
           }
         }
       }
     }
   } else if (warp == 13) {
-    // ---- MMA issue ----
+    // ---- MMA issue: one accumulator per row tile ----
     if (lane == 0) {
       uint32_t cc = 0, tcount = 0;
-      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const XSys &S = sys[cur];
         const int n = S.g.n;
-        const int b = (int)((w - prefix[cur]) % n);
-        for (int mt = b >> 7; mt < S.g.MT && !*abort_flag; ++mt, ++tcount) {
-          const int buf = tcount & 1;
-          const uint32_t tu = tcount >> 1;
-          // one TMEM buffer: the previous tile must be drained; two: the one before it
-          bool ok = true;
-          if (nbuf == 1 && tcount > 0)
-            ok = tc::mbar_wait(&acce[(tcount - 1) & 1], ((tcount - 1) >> 1) & 1, kWaitNs);
-          else if (nbuf == 2 && tu > 0)
-            ok = tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs);
-          if (!ok) {
-            *abort_flag = 1;
-            break;
-          }
-          tc::fence_after_sync();
-          const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
-            const int s = cc & 1;
-            const uint32_t use = cc >> 1;
-            if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
-              *abort_flag = 1;
-              break;
-            }
-            tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
-            const int ksteps = min(4, (n - kc * 32 + 7) / 8);
-            for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
-              const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-              for (int nt = 0; nt < S.g.NT; ++nt) {
-                const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
-                const uint64_t bh = tc::sdesc_k128(sa + boff);
-                const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-                const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
-                const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
-                tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                tc::mma_tf32(d, ah, bl, idesc, 1u);
-                tc::mma_tf32(d, al, bh, idesc, 1u);
-              }
-            }
-            tc::mma_commit(&empty[s]);
-            issued = true;
-          }
-          tc::mma_commit(&accf[buf]);
-        }
-      }
-    }
-  } else {
-    // ---- epilogue: Sigma_ab = sum_k V_ak (sigma g_ab (QV)_kb - g_kb P_ak) ----
-    uint32_t tcount = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
-      const XSys &S = sys[cur];
-      const int n = S.g.n, ld = S.g.ld;
-      const long q = w - prefix[cur];
-      const int j = (int)(q / n), b = (int)(q % n);
-      const float *gA = S.g32 + (long)j * n * ld;
-      tc::named_bar(1, 128);
-      for (int k = tid; k < n; k += 128) {
-        gcol[k] = gA[(long)b * ld + k];                  // g_kb = g_bk
-        qcol[k] = S.VQ[((long)j * n + b) * ld + k];      // (QV)_kb = (VQ)_bk
-      }
-      tc::named_bar(1, 128);
-      for (int mt = b >> 7; mt < S.g.MT; ++mt, ++tcount) {
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
-        if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+        // one TMEM buffer: the previous tile must be drained; two: the one before it
+        bool ok = true;
+        if (nbuf == 1 && tcount > 0)
+          ok = tc::mbar_wait(&acce[(tcount - 1) & 1], ((tcount - 1) >> 1) & 1, kWaitNs);
+        else if (nbuf == 2 && tu > 0)
+          ok = tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs);
+        if (!ok) {
           *abort_flag = 1;
           break;
         }
         tc::fence_after_sync();
-        const int a = mt * 128 + warp * 32 + lane;
-        const bool live = a < n;
-        const float sg = live ? S.spin * gA[(long)a * ld + b] : 0.f;
-        const float *Va = S.V32 + (long)(live ? a : 0) * ld;  // V_ak = V_ka: row a
-        const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-        float acc = 0.f;
-        for (int c0 = 0; c0 < n; c0 += 16) {
-          float pv[16];
-          tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, pv);
-          if (live) {
-            float vk[16];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              const float4 v4 = *reinterpret_cast<const float4 *>(Va + c0 + 4 * t);
-              vk[4 * t] = v4.x;
-              vk[4 * t + 1] = v4.y;
-              vk[4 * t + 2] = v4.z;
-              vk[4 * t + 3] = v4.w;
+        const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
+        for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+          const int s = cc & 1;
+          const uint32_t use = cc >> 1;
+          if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
+          const int ksteps = min(4, (n - kc * 32 + 7) / 8);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+            const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+            for (int nt = 0; nt < S.g.NT; ++nt) {
+              const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
+              const uint64_t bh = tc::sdesc_k128(sa + boff);
+              const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+              const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
+              const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
+              tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_tf32(d, ah, bl, idesc, 1u);
+              tc::mma_tf32(d, al, bh, idesc, 1u);
             }
+          }
+          tc::mma_commit(&empty[s]);
+          issued = true;
+        }
+        tc::mma_commit(&accf[buf]);
+      }
+    }
+  } else {
+    // ---- epilogue, row (b, a): Sigma_ab = sum_k V_ak (sigma g_ab (QV)_kb - g_kb P_ak) ----
+    uint32_t tcount = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const XSys &S = sys[cur];
+      const int n = S.g.n, ld = S.g.ld;
+      const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
+      const long q = w - prefix[cur];
+      const int j = (int)(q / RT);
+      const long r = (q % RT) * 128 + warp * 32 + lane;
+      const bool live = r < T;
+      int b = 0, a = 0;
+      if (live) tri_row(n, r, &b, &a);
+      const float *gA = S.g32 + (long)j * n * ld;
+      const float *Va = S.V32 + (long)a * ld;              // V_ak = V_ka: row a
+      const float *gb_row = gA + (long)b * ld;              // g_kb = g_bk: row b
+      const float *qb_row = S.VQ + ((long)j * n + b) * ld;  // (QV)_kb = (VQ)_bk
+      const float sg = live ? S.spin * gA[(long)a * ld + b] : 0.f;
+      const int buf = tcount & 1;
+      const uint32_t tu = tcount >> 1;
+      if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
+      float acc = 0.f;
+      for (int c0 = 0; c0 < n; c0 += 16) {
+        float pv[16];
+        tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, pv);
+        if (live) {
 #pragma unroll
-            for (int t = 0; t < 16; ++t)
-              if (c0 + t < n) acc = fmaf(vk[t], sg * qcol[c0 + t] - gcol[c0 + t] * pv[t], acc);
+          for (int t4 = 0; t4 < 4; ++t4) {
+            const float4 v4 = *reinterpret_cast<const float4 *>(Va + c0 + 4 * t4);
+            const float4 g4 = *reinterpret_cast<const float4 *>(gb_row + c0 + 4 * t4);
+            const float4 q4 = *reinterpret_cast<const float4 *>(qb_row + c0 + 4 * t4);
+            // rows are zero beyond n, so padded columns add nothing
+            acc = fmaf(v4.x, sg * q4.x - g4.x * pv[4 * t4], acc);
+            acc = fmaf(v4.y, sg * q4.y - g4.y * pv[4 * t4 + 1], acc);
+            acc = fmaf(v4.z, sg * q4.z - g4.z * pv[4 * t4 + 2], acc);
+            acc = fmaf(v4.w, sg * q4.w - g4.w * pv[4 * t4 + 3], acc);
           }
         }
-        tc::fence_before_sync();
-        tc::mbar_arrive(&acce[buf]);
-        if (live && a >= b) {
-          const long nn = (long)n * n;
-          S.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
-          S.Sigma[(long)j * nn + (long)b * n + a] = (double)acc;
-          if (S.S32) {
-            S.S32[((long)j * n + a) * ld + b] = acc;
-            S.S32[((long)j * n + b) * ld + a] = acc;
-          }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&acce[buf]);
+      if (live) {
+        const long nn = (long)n * n;
+        S.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
+        S.Sigma[(long)j * nn + (long)b * n + a] = (double)acc;
+        if (S.S32) {
+          S.S32[((long)j * n + a) * ld + b] = acc;
+          S.S32[((long)j * n + b) * ld + a] = acc;
         }
       }
     }
@@ -436,14 +455,14 @@ cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, doubl
 
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
                                int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s) {
-  const size_t smem = tc_smem_bytes(Np_max, ld_max, true);
+  (void)ld_max;
+  const size_t smem = tc_smem_bytes(Np_max, 0, false);
   cudaError_t e = cudaFuncSetAttribute(exchange_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
-  exchange_tc_kernel<<<grid, kThreads2, smem, s>>>(sys, prefix, n_sys, items, Np_max, ld_max,
-                                                   nbuf, err);
+  exchange_tc_kernel<<<grid, kThreads2, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
   return cudaGetLastError();
 }
 

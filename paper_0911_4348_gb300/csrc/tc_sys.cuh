@@ -76,9 +76,12 @@ cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, l
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
                             int Np_max, int *err, int num_sms, cudaStream_t s);
 
-// Work items per system: exchange (j, b) pairs; convolution (row tile, split)
+// Work items per system: exchange (j, row tile) pairs over the n(n+1)/2
+// stacked rows (b, a >= b) of each mesh point; convolution (row tile, split)
 // pairs over the M*n stacked rows.
-inline long exchange_items(int n, int M) { return (long)M * n; }
+inline long exchange_items(int n, int M) {
+  return (long)M * (((long)n * (n + 1) / 2 + 127) / 128);
+}
 inline long conv1_items(int n, int M, int splits) {
   return ((long)M * n + 127) / 128 * (long)splits;
 }
