@@ -195,7 +195,7 @@ int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *
   FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32));
   (void)coef;
   FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, P<int4>(ctx->w_coef32), I1, part));
-  long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M, splits, conv1_pairs(tc_geom(n, M).Np))};
+  long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M, splits)};
   uint8_t *base = P<uint8_t>(ctx->w_tab);
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabX, &x, sizeof(x), cudaMemcpyHostToDevice, ctx->stream));
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabC, &c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream));
@@ -212,7 +212,7 @@ int launch_conv1_single(fedvr_ctx *ctx, int splits, int *err, cudaStream_t s, in
   uint8_t *tab = P<uint8_t>(ctx->w_tab);
   FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
                                 reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                conv1_items(n, M, splits, conv1_pairs(tc_geom(n, M).Np)), g.Np, err, ctx->num_sms, s));
+                                conv1_items(n, M, splits), g.Np, err, ctx->num_sms, s));
   *launches += 1;
   if (splits > 1) {
     FEDVR_CK(ctx, conv1_sum_splits((long)M * n * n, splits - 1, P<double>(ctx->w_c1p),
@@ -1100,7 +1100,7 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
     const fedvr_ctx *c = B->ctxs[k];
     if (!c->prepared) return fail(lead, FEDVR_ERR_STATE, "system %d is no longer prepared", k);
     B->px[k + 1] = B->px[k] + (active[k] ? exchange_items(c->n, c->M) : 0);
-    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M, 1, conv1_pairs(B->Np_max)) : 0);
+    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M, 1) : 0);
   }
   if (B->px[n_sys] == 0) return FEDVR_OK;
   FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_px, B->px.data(), (n_sys + 1) * sizeof(long),
@@ -1298,7 +1298,7 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
                                   reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                  conv1_items(n, M, 1, conv1_pairs(tc_geom(n, M).Np)), g.Np, err, ctx->num_sms, s));
+                                  conv1_items(n, M, 1), g.Np, err, ctx->num_sms, s));
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;

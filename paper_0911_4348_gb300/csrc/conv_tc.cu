@@ -295,278 +295,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// ---------------------------------------------------------------------------
-// Paired-tile variant (all columns in one N tile, Np <= 256): an item is two
-// consecutive 128-row tiles that share every g_j chunk, so g streams through
-// shared memory once per 256 rows instead of once per 128. Chunks are 16
-// columns wide (64-byte swizzle) so that three or more stages of two A tiles
-// and one B tile fit; both accumulators (2 x Np columns) live in TMEM at once
-// and are flushed between blocks of JB mesh points.
-constexpr uint32_t kTileA16 = 128 * 64;  // 128 rows x 16 floats
-constexpr int kMaxStages = 6;
-
-struct C1Pair {
-  long r0;  // first stacked row of the pair
-  int j_lo, j_hi;
-  double *out;
-};
-
-__device__ __forceinline__ C1Pair c1_pair(const C1Sys &S, long q) {
-  const long RP = ((long)S.RT + 1) / 2;
-  C1Pair it;
-  const int s = (int)(q / RP);
-  it.r0 = (q % RP) * 256;
-  it.j_lo = (int)(((long)s * S.g.M) / S.S);
-  it.j_hi = (int)(((long)(s + 1) * S.g.M) / S.S);
-  it.out = (s == 0) ? S.I1 : S.part + (long)(s - 1) * S.g.M * S.g.n * S.g.n;
-  return it;
-}
-
-__global__ void __launch_bounds__(kThreads, 1)
-    conv1_pair_kernel(const C1Sys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
-                      long items, int Np_max, int nstage, int *err) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                              ~uintptr_t(1023));
-  const uint32_t tileB = (uint32_t)Np_max * 64;
-  const uint32_t stage_bytes = 4 * kTileA16 + 2 * tileB;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage * stage_bytes);
-  uint64_t *full = bars, *empty = bars + kMaxStages, *accf = bars + 2 * kMaxStages,
-           *acce = accf + 1, *drain = acce + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-  if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, 512);
-    tc::tmem_relinquish();
-  }
-  if (tid == 0) {
-    for (int s = 0; s < nstage; ++s) {
-      tc::mbar_init(&full[s], 257);
-      tc::mbar_init(&empty[s], 1);
-    }
-    tc::mbar_init(accf, 1);
-    tc::mbar_init(acce, 128);
-    tc::mbar_init(drain, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = *tmem_slot;
-  bool issued = false;
-  int cur = 0;
-
-  if (warp >= 4 && warp < 12) {
-    // ---- A producers: rows r0 + 64 k of the pair (k = 0, 1 in the first tile,
-    // 2, 3 in the second), 16-byte chunk c of each 16-wide slice ----
-    const int pt = tid - 128, c = pt & 3, r0 = pt >> 2;
-    uint32_t off[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      off[k] = (uint32_t)(k >> 1) * 2 * kTileA16 + tc::sw64_offset((r0 + 64 * k) & 127, c);
-    int st = 0;
-    uint32_t u = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
-      const C1Sys &S = sys[cur];
-      const int n = S.g.n, ld = S.g.ld, M = S.g.M, KC = (n + 15) / 16;
-      const long R = (long)M * n;
-      const C1Pair it = c1_pair(S, w - prefix[cur]);
-      int ia[4], aa[4];
-      bool live[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const long r = it.r0 + r0 + 64 * k;
-        live[k] = r < R;
-        ia[k] = live[k] ? (int)(r / n) : 0;
-        aa[k] = live[k] ? (int)(r % n) : 0;
-      }
-      for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-        uint32_t o1[4], o2[4];  // element offsets into S32 ([2M][n][ld] < 2^31)
-        float c1[4], c2[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int4 cf = S.coef32[(long)ia[k] * M + j];
-          o1[k] = (uint32_t)((cf.x * n + aa[k]) * ld + 4 * c);
-          o2[k] = (uint32_t)((cf.y * n + aa[k]) * ld + 4 * c);
-          c1[k] = __int_as_float(cf.z);
-          c2[k] = __int_as_float(cf.w);
-        }
-        for (int kc = 0; kc < KC; ++kc) {
-          const int l0 = kc * 16;
-          float4 s1[4], s2[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (live[k]) {
-              s1[k] = *reinterpret_cast<const float4 *>(S.S32 + o1[k] + l0);
-              s2[k] = *reinterpret_cast<const float4 *>(S.S32 + o2[k] + l0);
-            } else {
-              s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-          }
-          if (u > 0 && !tc::mbar_wait(&empty[st], (u - 1) & 1, kWaitNs)) {
-            *abort_flag = 1;
-            break;
-          }
-          uint8_t *sa = smem + st * stage_bytes;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float x0 = fmaf(c1[k], s1[k].x, c2[k] * s2[k].x);
-            const float x1 = fmaf(c1[k], s1[k].y, c2[k] * s2[k].y);
-            const float x2 = fmaf(c1[k], s1[k].z, c2[k] * s2[k].z);
-            const float x3 = fmaf(c1[k], s1[k].w, c2[k] * s2[k].w);
-            const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
-                                          tc::tf32_rna(x3));
-            const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
-                                          tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
-            *reinterpret_cast<float4 *>(sa + off[k]) = hi;
-            *reinterpret_cast<float4 *>(sa + kTileA16 + off[k]) = lo;
-          }
-          tc::fence_smem_to_async();
-          tc::mbar_arrive(&full[st]);
-          if (++st == nstage) {
-            st = 0;
-            ++u;
-          }
-        }
-      }
-    }
-  } else if (warp == 12) {
-    // ---- TMA: g_j rows 0..Np-1, 16 columns per chunk, hi and lo ----
-    if (lane == 0) {
-      int st = 0;
-      uint32_t u = 0;
-      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
-        const C1Sys &S = sys[cur];
-        const C1Pair it = c1_pair(S, w - prefix[cur]);
-        const uint32_t bytes = 2u * (uint32_t)S.g.Np * 64u;
-        const int KC = (S.g.n + 15) / 16;
-        for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-          for (int kc = 0; kc < KC; ++kc) {
-            if (u > 0 && !tc::mbar_wait(&empty[st], (u - 1) & 1, kWaitNs)) {
-              *abort_flag = 1;
-              break;
-            }
-            uint8_t *sb = smem + st * stage_bytes + 4 * kTileA16;
-            tc::mbar_arrive_expect_tx(&full[st], bytes);
-            tc::tma_load_3d(sb, &S.th16, kc * 16, 0, j, &full[st]);
-            tc::tma_load_3d(sb + tileB, &S.tl16, kc * 16, 0, j, &full[st]);
-            if (++st == nstage) {
-              st = 0;
-              ++u;
-            }
-          }
-        }
-      }
-    }
-  } else if (warp == 13) {
-    // ---- MMA issue: both tiles of the pair per chunk; one accumulator block per JB mesh points ----
-    if (lane == 0) {
-      int st = 0;
-      uint32_t u = 0, tcount = 0;
-      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
-        const C1Sys &S = sys[cur];
-        const C1Pair it = c1_pair(S, w - prefix[cur]);
-        const int n = S.g.n, KC = (n + 15) / 16;
-        const uint32_t idesc = tc::idesc_tf32(128, S.g.Np);
-        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += S.JB, ++tcount) {
-          const int j1 = min(it.j_hi, j0 + S.JB);
-          if (tcount > 0 && !tc::mbar_wait(acce, (tcount - 1) & 1, kWaitNs)) {
-            *abort_flag = 1;
-            break;
-          }
-          tc::fence_after_sync();
-          for (int j = j0; j < j1 && !*abort_flag; ++j) {
-            for (int kc = 0; kc < KC; ++kc) {
-              if (!tc::mbar_wait(&full[st], u & 1, kWaitNs)) {
-                *abort_flag = 1;
-                break;
-              }
-              tc::fence_after_sync();
-              const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
-              const int ksteps = min(2, (n - kc * 16 + 7) / 8);
-              const bool fresh = (j == j0 && kc == 0);
-              for (int kk = 0; kk < ksteps; ++kk) {
-                const uint64_t bh = tc::sdesc_k64(sa + 4 * kTileA16 + kk * 32);
-                const uint64_t bl = tc::sdesc_k64(sa + 4 * kTileA16 + tileB + kk * 32);
-#pragma unroll
-                for (int tt = 0; tt < 2; ++tt) {
-                  const uint64_t ah = tc::sdesc_k64(sa + tt * 2 * kTileA16 + kk * 32);
-                  const uint64_t al = tc::sdesc_k64(sa + tt * 2 * kTileA16 + kTileA16 + kk * 32);
-                  const uint32_t d = tmem + (uint32_t)(tt * Np_max);
-                  tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
-                  tc::mma_tf32(d, ah, bl, idesc, 1u);
-                  tc::mma_tf32(d, al, bh, idesc, 1u);
-                }
-              }
-              tc::mma_commit(&empty[st]);
-              issued = true;
-              if (++st == nstage) {
-                st = 0;
-                ++u;
-              }
-            }
-          }
-          tc::mma_commit(accf);
-        }
-      }
-    }
-  } else {
-    // ---- flush: add both FP32 blocks into the FP64 output rows ----
-    uint32_t tcount = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
-      const C1Sys &S = sys[cur];
-      const int n = S.g.n;
-      const long R = (long)S.g.M * n;
-      const C1Pair it = c1_pair(S, w - prefix[cur]);
-      for (int j0 = it.j_lo; j0 < it.j_hi; j0 += S.JB, ++tcount) {
-        if (!tc::mbar_wait(accf, tcount & 1, kWaitNs)) {
-          *abort_flag = 1;
-          break;
-        }
-        tc::fence_after_sync();
-        const bool first = j0 == it.j_lo;
-        for (int tt = 0; tt < 2; ++tt) {
-          const long r = it.r0 + tt * 128 + warp * 32 + lane;
-          const bool live = r < R;
-          double *row = it.out + (live ? r : 0) * n;
-          for (int c0 = 0; c0 < n; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tt * Np_max + c0), v);
-            if (live) {
-#pragma unroll
-              for (int t = 0; t < 16; ++t) {
-                const int b = c0 + t;
-                if (b < n) row[b] = first ? (double)v[t] : row[b] + (double)v[t];
-              }
-            }
-          }
-        }
-        tc::fence_before_sync();
-        tc::mbar_arrive(acce);
-      }
-    }
-  }
-
-  __syncthreads();
-  if (*abort_flag) {
-    if (warp == 13 && lane == 0) {
-      if (issued) tc::mma_commit(drain);
-      atomicExch(err, 1);
-      if (issued) tc::mbar_wait(drain, 0, kWaitNs);
-    }
-    __syncthreads();
-  }
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
-}
-
 __global__ void coef32_kernel(long mm, int M, const ConvCoef *__restrict__ coef,
                               int4 *__restrict__ out) {
   for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < mm;
@@ -649,11 +377,6 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
     if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
-  if (conv1_pairs(d->g.Np)) {
-    cudaError_t e = make_tmap_rows(&d->th16, ws + stack, n, M, d->g.ld, d->g.Np, 16);
-    if (e == cudaSuccess) e = make_tmap_rows(&d->tl16, ws + 2 * stack, n, M, d->g.ld, d->g.Np, 16);
-    if (e != cudaSuccess) return e;
-  }
   return cudaSuccess;
 }
 
@@ -679,23 +402,11 @@ cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double 
 
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
                             int Np_max, int *err, int num_sms, cudaStream_t s) {
-  const int grid = (int)(items < num_sms ? items : num_sms);
-  if (conv1_pairs(Np_max)) {
-    const size_t stage = 4 * (size_t)kTileA16 + 2 * (size_t)Np_max * 64;
-    int nstage = (int)((232448 - 1024 - 256) / stage);
-    nstage = nstage > kMaxStages ? kMaxStages : nstage;
-    if (nstage < 2) return cudaErrorInvalidValue;
-    const size_t smem = 1024 + (size_t)nstage * stage + 256;
-    cudaError_t e = cudaFuncSetAttribute(conv1_pair_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    conv1_pair_kernel<<<grid, kThreads, smem, s>>>(sys, prefix, n_sys, items, Np_max, nstage, err);
-    return cudaGetLastError();
-  }
   const size_t smem = tc_smem_bytes(Np_max, 0, false);
   cudaError_t e = cudaFuncSetAttribute(conv1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
   conv1_tc_kernel<<<grid, kThreads, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
   return cudaGetLastError();

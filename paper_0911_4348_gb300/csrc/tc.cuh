@@ -134,18 +134,6 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
   return d;
 }
 
-// The same for the 64-byte swizzle: 8-row atoms of 512 bytes, rows of 16
-// 32-bit elements.
-__device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(512 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)4 << 61;             // 64-byte swizzle
-  return d;
-}
-
 // Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -181,12 +169,6 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // Byte offset of 16-byte chunk c (0..7) of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-}
-
-// Byte offset of 16-byte chunk c (0..3) of row r in a 64B-swizzled K-major
-// tile (address bits 5:4 XOR bits 8:7).
-__device__ __forceinline__ uint32_t sw64_offset(int r, int c) {
-  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
 }  // namespace tc

@@ -32,8 +32,7 @@ struct XSys {
 
 // First convolution kernel: one system.
 struct C1Sys {
-  CUtensorMap th[2], tl[2];   // g_j split, per N tile, 32-column boxes (128-byte swizzle)
-  CUtensorMap th16, tl16;     // the same for one N tile, 16-column boxes (64-byte swizzle)
+  CUtensorMap th[2], tl[2];   // g_j split, per N tile
   TcGeom g;
   int JB;                     // mesh points per FP32 accumulation block
   int S;                      // splits of the mesh-point range per row tile
@@ -83,14 +82,8 @@ cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, lon
 inline long exchange_items(int n, int M) {
   return (long)M * (((long)n * (n + 1) / 2 + 127) / 128);
 }
-// With pairs, an item is two consecutive row tiles sharing each g_j chunk
-// (the kernel for N <= 256).
-inline long conv1_items(int n, int M, int splits, bool pairs) {
-  const long tiles = ((long)M * n + 127) / 128;
-  return (pairs ? (tiles + 1) / 2 : tiles) * (long)splits;
+inline long conv1_items(int n, int M, int splits) {
+  return ((long)M * n + 127) / 128 * (long)splits;
 }
-// Whether the convolution launch for a table whose widest system has Np_max
-// columns runs the paired-tile kernel.
-inline bool conv1_pairs(int Np_max) { return Np_max <= 256; }
 
 }  // namespace fedvr
