@@ -22,6 +22,7 @@ scaling); ranks only meet at the timing barrier.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -63,6 +64,22 @@ def load_peaks() -> dict:
             return json.load(fh)
     except OSError:
         return {}
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    if there is none for this workload or the kernel source changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            entry = json.load(fh).get(kernel)
+        if not entry or entry.get("workload") != workload:
+            return None
+        with open(os.path.join(ROOT, entry["source"]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != entry["source_sha256_16"]:
+                return None
+        return int(entry["dram_read_bytes"]) + int(entry["dram_write_bytes"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 class ClockSampler:
@@ -491,8 +508,10 @@ def main():
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) / 2.0
         bound, punit, psrc = "tensor", "TFLOP/s", "measured bf16 sustained x 1/2 (tf32 ratio)"
     achieved = algorithmic(dom, n, M) / (avg[dom] / 1000.0) / 1e12
+    kernel_name = {"conv1": "conv1_tc_kernel", "sigma2": "exchange_tc_kernel"}.get(dom)
+    traffic = measured_traffic(kernel_name, sys_.name) if (prec != 0 and kernel_name) else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
-            "frac": achieved / peak, "traffic": None, "kernel": dom,
+            "frac": achieved / peak, "traffic": traffic, "kernel": dom,
             "algorithmic_flops_per_launch": algorithmic(dom, n, M), "peak_source": psrc,
             "stage_ms": avg}
 
