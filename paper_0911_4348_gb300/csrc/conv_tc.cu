@@ -96,7 +96,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
+      // fields in registers: the asm statements below clobber memory, which would
+      // otherwise make the compiler reload them from the table every chunk
       const int n = S.g.n, ld = S.g.ld, M = S.g.M, KC = S.g.KC;
+      const float *const S32 = S.S32;
+      const int4 *const coef32 = S.coef32;
       const long R = (long)M * n;
       const C1Item it = c1_item(S, w - prefix[cur]);
       int ia[4], aa[4];
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float c1[4], c2[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int4 cf = S.coef32[(long)ia[k] * M + j];
+          const int4 cf = coef32[(long)ia[k] * M + j];
           o1[k] = (uint32_t)((cf.x * n + aa[k]) * ld + 4 * c);
           o2[k] = (uint32_t)((cf.y * n + aa[k]) * ld + 4 * c);
           c1[k] = __int_as_float(cf.z);
@@ -125,8 +129,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (live[k]) {
-              s1[k] = *reinterpret_cast<const float4 *>(S.S32 + o1[k] + l0);
-              s2[k] = *reinterpret_cast<const float4 *>(S.S32 + o2[k] + l0);
+              s1[k] = *reinterpret_cast<const float4 *>(S32 + o1[k] + l0);
+              s2[k] = *reinterpret_cast<const float4 *>(S32 + o2[k] + l0);
             } else {
               s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -167,8 +171,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const C1Sys &S = sys[cur];
         const C1Item it = c1_item(S, w - prefix[cur]);
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
+        const int NT = S.g.NT, KC = S.g.KC, n00 = S.g.n0[0], n01 = S.g.n0[1];
+        const CUtensorMap *th0 = &S.th[0], *th1 = &S.th[1], *tl0 = &S.tl[0], *tl1 = &S.tl[1];
         for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-          for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+          for (int kc = 0; kc < KC; ++kc, ++cc) {
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
             if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
@@ -177,10 +183,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
             tc::mbar_arrive_expect_tx(&full[s], bytes);
-            for (int nt = 0; nt < S.g.NT; ++nt) {
-              tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt], j, &full[s]);
-              tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt], j,
-                              &full[s]);
+            for (int nt = 0; nt < NT; ++nt) {
+              const int r = nt ? n01 : n00;
+              tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 32, r, j, &full[s]);
+              tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 32, r, j, &full[s]);
             }
           }
         }
@@ -194,9 +200,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const C1Sys &S = sys[cur];
         const C1Item it = c1_item(S, w - prefix[cur]);
-        const int n = S.g.n;
-        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += S.JB, ++tcount) {
-          const int j1 = min(it.j_hi, j0 + S.JB);
+        const int n = S.g.n, KC = S.g.KC, NT = S.g.NT, JB = S.JB;
+        const uint32_t n00 = (uint32_t)S.g.n0[0], n01 = (uint32_t)S.g.n0[1];
+        const uint32_t id0 = tc::idesc_tf32(128, S.g.nsz[0]), id1 = tc::idesc_tf32(128, S.g.nsz[1]);
+        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB, ++tcount) {
+          const int j1 = min(it.j_hi, j0 + JB);
           const int buf = tcount & 1;
           const uint32_t tu = tcount >> 1;
           bool ok = true;
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::fence_after_sync();
           const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
           for (int j = j0; j < j1 && !*abort_flag; ++j) {
-            for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+            for (int kc = 0; kc < KC; ++kc, ++cc) {
               const int s = cc & 1;
               const uint32_t use = cc >> 1;
               if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
@@ -225,12 +233,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int kk = 0; kk < ksteps; ++kk) {
                 const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
                 const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-                for (int nt = 0; nt < S.g.NT; ++nt) {
-                  const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
+                for (int nt = 0; nt < NT; ++nt) {
+                  const uint32_t r = nt ? n01 : n00;
+                  const uint32_t boff = 2 * kTileA + r * 128 + kk * 32;
                   const uint64_t bh = tc::sdesc_k128(sa + boff);
                   const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-                  const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
-                  const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
+                  const uint32_t d = dbase + r;
+                  const uint32_t idesc = nt ? id1 : id0;
                   tc::mma_tf32(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
                   tc::mma_tf32(d, ah, bl, idesc, 1u);
                   tc::mma_tf32(d, al, bh, idesc, 1u);

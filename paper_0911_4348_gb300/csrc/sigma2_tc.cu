@@ -164,12 +164,13 @@ __global__ void __launch_bounds__(kThreads2, 1)
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
-      const int n = S.g.n, ld = S.g.ld;
+      const int n = S.g.n, ld = S.g.ld, KC = S.g.KC;
       const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
       const long q = w - prefix[cur];
       const int j = (int)(q / RT);
       const long t = q % RT;
-      const float *gA = S.g32 + (long)j * n * ld;
+      const float *const gA = S.g32 + (long)j * n * ld;
+      const float *const V32 = S.V32;  // in a register across the memory-clobbering asm
       uint32_t og[4], ov[4];  // element offsets of row a of g_j and row b of V
       bool live[4];
 #pragma unroll
@@ -181,14 +182,14 @@ __global__ void __launch_bounds__(kThreads2, 1)
         og[k] = (uint32_t)(a * ld + 4 * c);
         ov[k] = (uint32_t)(b * ld + 4 * c);
       }
-      for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+      for (int kc = 0; kc < KC; ++kc, ++cc) {
         const int l0 = kc * 32;
         float4 gv[4], vv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (live[k]) {
             gv[k] = *reinterpret_cast<const float4 *>(gA + og[k] + l0);
-            vv[k] = *reinterpret_cast<const float4 *>(S.V32 + ov[k] + l0);
+            vv[k] = *reinterpret_cast<const float4 *>(V32 + ov[k] + l0);
           } else {
             gv[k] = vv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
           }
@@ -227,7 +228,9 @@ __global__ void __launch_bounds__(kThreads2, 1)
         const long RT = ((long)n * (n + 1) / 2 + 127) / 128;
         const int j = (int)((w - prefix[cur]) / RT);
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
-        for (int kc = 0; kc < S.g.KC && !*abort_flag; ++kc, ++cc) {
+        const int NT = S.g.NT, KC = S.g.KC, jb = S.g.M - 1 - j, n00 = S.g.n0[0], n01 = S.g.n0[1];
+        const CUtensorMap *th0 = &S.th[0], *th1 = &S.th[1], *tl0 = &S.tl[0], *tl1 = &S.tl[1];
+        for (int kc = 0; kc < KC && !*abort_flag; ++kc, ++cc) {
           const int s = cc & 1;
           const uint32_t use = cc >> 1;
           if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
@@ -236,11 +239,10 @@ __global__ void __launch_bounds__(kThreads2, 1)
           }
           uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
           tc::mbar_arrive_expect_tx(&full[s], bytes);
-          for (int nt = 0; nt < S.g.NT; ++nt) {
-            tc::tma_load_3d(st + S.g.n0[nt] * 128, &S.th[nt], kc * 32, S.g.n0[nt], S.g.M - 1 - j,
-                            &full[s]);
-            tc::tma_load_3d(st + tileB + S.g.n0[nt] * 128, &S.tl[nt], kc * 32, S.g.n0[nt],
-                            S.g.M - 1 - j, &full[s]);
+          for (int nt = 0; nt < NT; ++nt) {
+            const int r = nt ? n01 : n00;
+            tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 32, r, jb, &full[s]);
+            tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 32, r, jb, &full[s]);
           }
         }
       }
@@ -252,7 +254,9 @@ __global__ void __launch_bounds__(kThreads2, 1)
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const XSys &S = sys[cur];
-        const int n = S.g.n;
+        const int n = S.g.n, KC = S.g.KC, NT = S.g.NT;
+        const uint32_t n00 = (uint32_t)S.g.n0[0], n01 = (uint32_t)S.g.n0[1];
+        const uint32_t id0 = tc::idesc_tf32(128, S.g.nsz[0]), id1 = tc::idesc_tf32(128, S.g.nsz[1]);
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
         // one TMEM buffer: the previous tile must be drained; two: the one before it
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
         }
         tc::fence_after_sync();
         const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-        for (int kc = 0; kc < S.g.KC; ++kc, ++cc) {
+        for (int kc = 0; kc < KC; ++kc, ++cc) {
           const int s = cc & 1;
           const uint32_t use = cc >> 1;
           if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
@@ -280,12 +284,13 @@ __global__ void __launch_bounds__(kThreads2, 1)
           for (int kk = 0; kk < ksteps; ++kk) {
             const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
             const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-            for (int nt = 0; nt < S.g.NT; ++nt) {
-              const uint32_t boff = 2 * kTileA + (uint32_t)S.g.n0[nt] * 128 + kk * 32;
+            for (int nt = 0; nt < NT; ++nt) {
+              const uint32_t r = nt ? n01 : n00;
+              const uint32_t boff = 2 * kTileA + r * 128 + kk * 32;
               const uint64_t bh = tc::sdesc_k128(sa + boff);
               const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-              const uint32_t d = dbase + (uint32_t)S.g.n0[nt];
-              const uint32_t idesc = tc::idesc_tf32(128, S.g.nsz[nt]);
+              const uint32_t d = dbase + r;
+              const uint32_t idesc = nt ? id1 : id0;
               tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               tc::mma_tf32(d, ah, bl, idesc, 1u);
               tc::mma_tf32(d, al, bh, idesc, 1u);
