@@ -187,6 +187,101 @@ cudaError_t gemm32(int M, int N, int K, const Ta *A, long lda, long sA, const Tb
   return cudaGetLastError();
 }
 
+// FP32 GEMM with 128 x 128 tiles, 8 x 8 outputs per thread, 8-deep K slices
+// double-buffered in shared memory: Cm[m][q] = sum_k op(A)[m][k] op(B)[k][q],
+// operands converted to float on load, result stored as To. With nb > 0 the
+// columns q of B and C are stacked blocks of nb columns (q = blk * nb + col,
+// element blk * sB + k * ldb + col), which turns the per-mesh-point left
+// products C^T X_j of a [M][n][n] stack into one wide GEMM; blockIdx.z walks an
+// ordinary batch (strides sA/sB/sC) when nb = 0.
+template <bool TA, bool TB, typename Ta, typename Tb, typename To>
+__global__ void __launch_bounds__(256) sgemm128_kernel(int M, int N, int K, int nb,
+                                                       const Ta *__restrict__ A, long lda, long sA,
+                                                       const Tb *__restrict__ B, long ldb, long sB,
+                                                       To *__restrict__ C, long ldc, long sC) {
+  if (nb == 0) {
+    const long bz = blockIdx.z;
+    A += bz * sA;
+    B += bz * sB;
+    C += bz * sC;
+  }
+  __shared__ __align__(16) float As[2][8][128];
+  __shared__ __align__(16) float Bs[2][8][128];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * 128, q0 = blockIdx.x * 128;
+  // loader coordinates: 4 elements of each 8 x 128 slice per thread
+  const int lr = tid >> 5, lc = (tid & 31) * 4;  // slice row (k), first of 4 columns (m or q)
+  auto b_off = [&](int q) -> long {               // element offset of column q in B / C
+    if (nb > 0) return (long)(q / nb) * sB + (q % nb);
+    return q;
+  };
+  float ra[4], rb[4];
+  auto load = [&](int k0) {
+    const int k = k0 + lr;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int m = m0 + lc + t, q = q0 + lc + t;
+      ra[t] = (m < M && k < K) ? (float)(TA ? A[(long)k * lda + m] : A[(long)m * lda + k]) : 0.f;
+      rb[t] = (q < N && k < K) ? (float)(TB ? B[(long)q * ldb + k] : B[(long)k * ldb + b_off(q)])
+                               : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+    *reinterpret_cast<float4 *>(&As[buf][lr][lc]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    *reinterpret_cast<float4 *>(&Bs[buf][lr][lc]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+  };
+  // compute coordinates: rows ty*4 + {0..3, 64..67}, columns tx*4 + {0..3, 64..67}
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[8][8] = {};
+  load(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    const bool more = k0 + 8 < K;
+    if (more) load(k0 + 8);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+    }
+    if (more) {
+      stash(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int m = m0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
+    if (m >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int col = q0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
+      if (col >= N) continue;
+      const long off = nb > 0 ? (long)(col / nb) * sC + (col % nb) : col;
+      C[(long)m * ldc + off] = (To)acc[r][q];
+    }
+  }
+}
+
+template <bool TA, bool TB, typename Ta, typename Tb, typename To>
+cudaError_t sgemm128(int M, int N, int K, int nb, const Ta *A, long lda, long sA, const Tb *B,
+                     long ldb, long sB, To *C, long ldc, long sC, int batch, cudaStream_t s) {
+  dim3 grid((N + 127) / 128, (M + 127) / 128, nb > 0 ? 1 : batch);
+  sgemm128_kernel<TA, TB, Ta, Tb, To><<<grid, 256, 0, s>>>(M, N, K, nb, A, lda, sA, B, ldb, sB, C,
+                                                          ldc, sC);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s) {
@@ -199,17 +294,33 @@ cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t 
 // t1/t2 float scratch of M*n*n), FP64 I1 in and FP64 I2 out.
 cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
                             double *I2, float *t1, float *t2, cudaStream_t s) {
-  long nn = (long)n * n, MM = (long)M * M;
+  const long nn = (long)n * n, MM = (long)M * M;
+  const int Mn = M * n;
   cudaError_t e;
-  e = gemm32<true, false>(n, n, n, C, n, 0, I1, n, nn, t1, n, nn, M, s);
+  if (n < 96) {  // small matrices: 64 x 64 tiles, one GEMM per mesh point
+    e = gemm32<true, false>(n, n, n, C, n, 0, I1, n, nn, t1, n, nn, M, s);
+    if (e != cudaSuccess) return e;
+    e = gemm32<false, false>(n, n, n, (const float *)t1, n, nn, C, n, 0, t2, n, nn, M, s);
+    if (e != cudaSuccess) return e;
+    e = gemm32<false, false>(M, n, M, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
+    if (e != cudaSuccess) return e;
+    e = gemm32<false, false>(n, n, n, C, n, 0, (const float *)t1, n, nn, t2, n, nn, M, s);
+    if (e != cudaSuccess) return e;
+    return gemm32<false, true>(n, n, n, (const float *)t2, n, nn, C, n, 0, I2, n, nn, M, s);
+  }
+  // u_j = I1_j C for all j: one tall GEMM over the [M n][n] stack
+  e = sgemm128<false, false>(Mn, n, n, 0, I1, n, 0, C, n, 0, t1, n, 0, 1, s);
   if (e != cudaSuccess) return e;
-  e = gemm32<false, false>(n, n, n, (const float *)t1, n, nn, C, n, 0, t2, n, nn, M, s);
+  // I1~_j = C^T u_j: one wide GEMM over the stacked columns (j, b)
+  e = sgemm128<true, false>(n, Mn, n, n, C, n, 0, (const float *)t1, n, nn, t2, n, nn, 1, s);
   if (e != cudaSuccess) return e;
-  e = gemm32<false, false>(M, n, M, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
+  // t[i][a][:] = sum_j K_a[i][j] I1~[j][a][:], batched over a
+  e = sgemm128<false, false>(M, n, M, 0, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
   if (e != cudaSuccess) return e;
-  e = gemm32<false, false>(n, n, n, C, n, 0, (const float *)t1, n, nn, t2, n, nn, M, s);
+  // v_i = t_i C^T (tall), I2_i = C v_i (wide)
+  e = sgemm128<false, true>(Mn, n, n, 0, (const float *)t1, n, 0, C, n, 0, t2, n, 0, 1, s);
   if (e != cudaSuccess) return e;
-  return gemm32<false, true>(n, n, n, (const float *)t2, n, nn, C, n, 0, I2, n, nn, M, s);
+  return sgemm128<false, false>(n, Mn, n, n, C, n, 0, (const float *)t2, n, nn, I2, n, nn, 1, s);
 }
 
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
