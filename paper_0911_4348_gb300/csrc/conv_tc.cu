@@ -150,10 +150,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                           fmaf(c1[k], s1[k].y, c2[k] * s2[k].y),
                           fmaf(c1[k], s1[k].z, c2[k] * s2[k].z),
                           fmaf(c1[k], s1[k].w, c2[k] * s2[k].w)};
-            const float4 hi = make_float4(tc::tf32_rna(x[0]), tc::tf32_rna(x[1]),
-                                          tc::tf32_rna(x[2]), tc::tf32_rna(x[3]));
-            const float4 lo = make_float4(tc::tf32_rna(x[0] - hi.x), tc::tf32_rna(x[1] - hi.y),
-                                          tc::tf32_rna(x[2] - hi.z), tc::tf32_rna(x[3] - hi.w));
+            float4 hi, lo;
+            tc::tf32_split(x[0], hi.x, lo.x);
+            tc::tf32_split(x[1], hi.y, lo.y);
+            tc::tf32_split(x[2], hi.z, lo.z);
+            tc::tf32_split(x[3], hi.w, lo.w);
             *reinterpret_cast<float4 *>(st + off[k]) = hi;
             *reinterpret_cast<float4 *>(st + kTileA + off[k]) = lo;
           }

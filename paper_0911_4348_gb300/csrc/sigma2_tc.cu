@@ -205,10 +205,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
         for (int k = 0; k < 4; ++k) {
           const float x0 = gv[k].x * vv[k].x, x1 = gv[k].y * vv[k].y, x2 = gv[k].z * vv[k].z,
                       x3 = gv[k].w * vv[k].w;
-          const float4 hi = make_float4(tc::tf32_rna(x0), tc::tf32_rna(x1), tc::tf32_rna(x2),
-                                        tc::tf32_rna(x3));
-          const float4 lo = make_float4(tc::tf32_rna(x0 - hi.x), tc::tf32_rna(x1 - hi.y),
-                                        tc::tf32_rna(x2 - hi.z), tc::tf32_rna(x3 - hi.w));
+          float4 hi, lo;
+          tc::tf32_split(x0, hi.x, lo.x);
+          tc::tf32_split(x1, hi.y, lo.y);
+          tc::tf32_split(x2, hi.z, lo.z);
+          tc::tf32_split(x3, hi.w, lo.w);
           const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
           *reinterpret_cast<float4 *>(st + off) = hi;
           *reinterpret_cast<float4 *>(st + kTileA + off) = lo;

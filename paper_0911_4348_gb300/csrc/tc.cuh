@@ -166,6 +166,17 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// Split x = hi + lo for the 3-product TF32 scheme without the conversion
+// instruction: hi is x rounded to TF32 (10 explicit mantissa bits, ties away
+// from zero) by adding half a TF32 unit to the magnitude bits and clearing the
+// 13 low bits (sign-magnitude layout); lo = x - hi is exact in FP32 and goes to
+// the tensor core as is, which reads its leading 19 bits (relative error of
+// the split about 2^-22 of |x|).
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
 // Byte offset of 16-byte chunk c (0..7) of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
