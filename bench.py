@@ -133,13 +133,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist():
+def _dist(backend: str = "nccl"):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
+
+
+def max_over_ranks(dist, x: float, device: str = "cuda") -> float:
+    """The largest of the ranks' values of x (the whole job ends with its
+    slowest rank); x itself when running alone."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_config(config_id: int, rank: int) -> int:
+    """Seed stream of a rank's share of a family of independent systems: every
+    rank draws its own systems (weak scaling, no data exchanged)."""
+    return config_id + 100 * rank
 
 
 def _cpu_cores() -> int:
@@ -231,7 +248,7 @@ def run_batch(args, dist, rank, world, local):
     advanced together; a step is one batched iteration of every system."""
     import torch
     from paper_0911_4348_gb300 import Batch, Context, solve_2b_batched
-    systems = W.batch_systems(64, config_id=4 + 100 * rank)
+    systems = W.batch_systems(64, config_id=rank_config(4, rank))
     stream = torch.cuda.current_stream()
 
     def make():
@@ -260,10 +277,7 @@ def run_batch(args, dist, rank, world, local):
     ev1.record(stream)
     torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(dist, elapsed)
     batch.close()
     n_sys = len(systems)
     value = world * n_sys * args.steps / (elapsed / 1000.0)
@@ -318,9 +332,9 @@ def run_warmstart(args, dist, rank, world, local):
     import torch
     from paper_0911_4348_gb300 import WarmStartNet
     stream = torch.cuda.current_stream()
-    base = 100000 * rank
-    train = [W.warmstart_system(base + k) for k in range(args.train_systems)]
-    test = [W.warmstart_system(base + 50000 + k) for k in range(args.test_systems)]
+    cid = rank_config(5, rank)
+    train = [W.warmstart_system(k, cid) for k in range(args.train_systems)]
+    test = [W.warmstart_system(50000 + k, cid) for k in range(args.test_systems)]
     M = train[0].n_tau
     net = WarmStartNet(M, args.hidden, seed=W.MASTER_SEED, stream=stream.cuda_stream)
     zero = WarmStartNet(M, args.hidden, seed=1, stream=stream.cuda_stream)
@@ -473,10 +487,7 @@ def main():
     barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(dist, elapsed)
     value = world * args.steps / (elapsed / 1000.0)
 
     # end to end through the public API: each step takes its input g from
@@ -489,10 +500,7 @@ def main():
         ctx.step_2b(sys_.mixing, G_in=G_host.numpy())
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, e2e_s)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": M * n * n * 8, "d2h_bytes_per_step": 3 * 8}
 
