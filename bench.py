@@ -14,7 +14,7 @@ scaling); ranks only meet at the timing barrier.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|tf32|bf16]
-                    [--workload he_medium|he_small|h3p_large|batch64|warmstart]
+                    [--workload he_medium|he_small|h3p_large|he_paper|batch64|warmstart]
                     [--no-time-to-e0] [--no-fp64-compare] [--no-cpu-baseline]
                     [--train-systems T] [--test-systems H] [--epochs E] [--hidden H]
 """
@@ -42,7 +42,7 @@ METRIC = "Sigma^(2) builds/s (one build + its Dyson iteration per step)"
 UNIT = "builds/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2}
 WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large,
-             "batch64": None, "warmstart": None}
+             "he_paper": W.he_paper, "batch64": None, "warmstart": None}
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
 

@@ -79,6 +79,14 @@ def he_medium() -> System:
     return System("He n_b=199 M=513", -50.0, 50.0, 25, 8, [2.0], [0.0], u=16, p=16)
 
 
+def he_paper() -> System:
+    """The paper's second-Born He run (Sec. 3.1): graded (case II) grid of 29
+    elements of order 7 over 200 a.u. (n_b=202), beta=100, 1025-point mesh
+    (u=32, p=16)."""
+    return System("He case II n_b=202 M=1025", -100.0, 100.0, 29, 7, [2.0], [0.0], u=32, p=16,
+                  grid_kind=1)
+
+
 def h3p_large(system_id: int = 0) -> System:
     """Linear H3+: unit charges at (-R, 0, R), R = 1.8, each nucleus shifted by
     an independent U(-0.1, 0.1) jitter; box [-60,60], 30 elements x 11 GLL
