@@ -328,7 +328,7 @@ int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
                                      P<double>(ctx->b_Sigma0), P<double>(ctx->w_dHF), s));
   FEDVR_CK(ctx, launch_energy(n, M, ctx->spin, P<double>(ctx->b_h), V, G, S, P<double>(ctx->w_w),
                               P<double>(ctx->w_part), P<double>(ctx->w_red), s));
-  *launches += 3;
+  *launches += 4;
   if (ctx->precision == FEDVR_SPLIT_TF32) {
     float *ws, *S32;
     int *err;
@@ -793,13 +793,17 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ENSURE(ctx, w_t2, dsz(stack));
   ENSURE(ctx, w_t3, dsz(stack));
   ENSURE(ctx, w_dHF, dsz(nn));
-  ENSURE(ctx, w_part, dsz(M));
+  ENSURE(ctx, w_part, dsz((size_t)M + 3 * (size_t)n));
   ENSURE(ctx, w_red, dsz(8));
   if (precision == FEDVR_SPLIT_TF32) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
     FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    // the Sigma^(2) epilogue writes columns < n of the FP32 source stack only;
+    // its padding (read as zeros by the convolution) is cleared once here
+    FEDVR_CK(ctx, cudaMemsetAsync(S32, 0, 2 * (size_t)M * n * ((n + 31) / 32 * 32) * sizeof(float),
+                                  s));
   }
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
   double *tau = P<double>(ctx->w_tau), *w = P<double>(ctx->w_w);

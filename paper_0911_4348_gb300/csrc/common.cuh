@@ -150,6 +150,9 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
 
 // tmap.cu: 3-D TMA map over [M][n][ld] floats, box 32 x rows x 1, 128B swizzle,
 // rows beyond n read as zero.
+// VQ[j] = V32 (g32[j] o g32[M-1-j]) in FP32 for all j (rows padded to ld).
+cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, float *VQ,
+                      cudaStream_t s);
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows,
                            int box_cols = 32);
 

@@ -194,11 +194,16 @@ cudaError_t gemm32(int M, int N, int K, const Ta *A, long lda, long sA, const Tb
 // element blk * sB + k * ldb + col), which turns the per-mesh-point left
 // products C^T X_j of a [M][n][n] stack into one wide GEMM; blockIdx.z walks an
 // ordinary batch (strides sA/sB/sC) when nb = 0.
-template <bool TA, bool TB, typename Ta, typename Tb, typename To>
+//
+// With MUL2 (stacked columns only) the B element of block blk is the product
+// B[blk] o B2[nblk - 1 - blk] (used for V (g o gb) without forming g o gb).
+template <bool TA, bool TB, typename Ta, typename Tb, typename To, bool MUL2 = false>
 __global__ void __launch_bounds__(256) sgemm128_kernel(int M, int N, int K, int nb,
                                                        const Ta *__restrict__ A, long lda, long sA,
                                                        const Tb *__restrict__ B, long ldb, long sB,
-                                                       To *__restrict__ C, long ldc, long sC) {
+                                                       To *__restrict__ C, long ldc, long sC,
+                                                       const Tb *__restrict__ B2 = nullptr,
+                                                       int nblk = 0) {
   if (nb == 0) {
     const long bz = blockIdx.z;
     A += bz * sA;
@@ -222,8 +227,16 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(int M, int N, int K, int 
     for (int t = 0; t < 4; ++t) {
       const int m = m0 + lc + t, q = q0 + lc + t;
       ra[t] = (m < M && k < K) ? (float)(TA ? A[(long)k * lda + m] : A[(long)m * lda + k]) : 0.f;
-      rb[t] = (q < N && k < K) ? (float)(TB ? B[(long)q * ldb + k] : B[(long)k * ldb + b_off(q)])
-                               : 0.f;
+      if (MUL2) {
+        const int blk = q / nb;
+        const long o1 = (long)blk * sB + (long)k * ldb + (q % nb);
+        const long o2 = (long)(nblk - 1 - blk) * sB + (long)k * ldb + (q % nb);
+        rb[t] = (q < N && k < K) ? (float)B[o1] * (float)B2[o2] : 0.f;
+      } else {
+        rb[t] = (q < N && k < K)
+                    ? (float)(TB ? B[(long)q * ldb + k] : B[(long)k * ldb + b_off(q)])
+                    : 0.f;
+      }
     }
   };
   auto stash = [&](int buf) {
@@ -283,6 +296,17 @@ cudaError_t sgemm128(int M, int N, int K, int nb, const Ta *A, long lda, long sA
 }
 
 }  // namespace
+
+cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, float *VQ,
+                      cudaStream_t s) {
+  // VQ[j] = V (g_j o g_{M-1-j}) for all j: one wide GEMM over the stacked
+  // columns (j, c), c < ld (padded columns of g are zero, so are those of VQ)
+  const long nld = (long)n * ld;
+  dim3 grid((unsigned)(((long)M * ld + 127) / 128), (unsigned)((n + 127) / 128), 1);
+  sgemm128_kernel<false, false, float, float, float, true><<<grid, 256, 0, s>>>(
+      n, M * ld, n, ld, V32, ld, 0, g32, ld, nld, VQ, ld, nld, g32, M);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s) {
   to_f32_kernel<<<1024, 256, 0, s>>>(count, x, y);

@@ -332,23 +332,31 @@ __global__ void coef32_kernel(long mm, int M, const ConvCoef *__restrict__ coef,
   }
 }
 
-// D_i = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} at rows M + i of S32 (zero padded to ld).
+// D_i = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} at rows M + i of S32 (zero padded
+// to ld), in FP32 from the FP32 copy of Sigma (rows 0 and M-1 of S32): the
+// operand is split to TF32 anyway. A thread owns one element (a, c) and writes
+// it for every i, so the FP64 matrix dHF is converted once per element.
 __global__ void diag_f32_kernel(int n, int M, int ld, const double *__restrict__ dHF,
-                                const double *__restrict__ S, const double *__restrict__ wm,
-                                const double *__restrict__ wp, float *__restrict__ D) {
-  const long nn = (long)n * n, total = (long)M * n * ld;
-  const double *S0 = S, *S1 = S + (long)(M - 1) * nn;
-  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
-       x += (long)gridDim.x * blockDim.x) {
-    const long row = x / ld;
-    const int c = (int)(x % ld);
-    const int i = (int)(row / n), a = (int)(row % n);
-    float v = 0.f;
+                                const double *__restrict__ wm, const double *__restrict__ wp,
+                                float *__restrict__ S32) {
+  extern __shared__ float wf[];  // wm, wp in FP32: [2][M]
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    wf[i] = (float)wm[i];
+    wf[M + i] = (float)wp[i];
+  }
+  __syncthreads();
+  const long nld = (long)n * ld;
+  float *D = S32 + (long)M * nld;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nld;
+       e += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / ld), c = (int)(e % ld);
+    float h = 0.f, s0 = 0.f, s1 = 0.f;
     if (c < n) {
-      const long e = (long)a * n + c;
-      v = (float)(dHF[e] - wm[i] * S0[e] + wp[i] * S1[e]);
+      h = (float)dHF[(long)a * n + c];
+      s0 = S32[e];
+      s1 = S32[(long)(M - 1) * nld + e];
     }
-    D[x] = v;
+    for (int i = 0; i < M; ++i) D[(long)i * nld + e] = (h - wf[i] * s0) + wf[M + i] * s1;
   }
 }
 
@@ -405,9 +413,17 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
 
 cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma,
                             const double *wm, const double *wp, float *S32, cudaStream_t s) {
+  (void)Sigma;  // read through its FP32 copy in S32
   const int ld = (n + 31) / 32 * 32;
-  diag_f32_kernel<<<1024, 256, 0, s>>>(n, M, ld, dHF, Sigma, wm, wp,
-                                       S32 + (long)M * n * ld);
+  const long nld = (long)n * ld;
+  const int blocks = (int)((nld + 255) / 256);
+  const size_t shm = 2 * (size_t)M * sizeof(float);
+  if (shm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(diag_f32_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+  }
+  diag_f32_kernel<<<blocks, 256, shm, s>>>(n, M, ld, dHF, wm, wp, S32);
   return cudaGetLastError();
 }
 

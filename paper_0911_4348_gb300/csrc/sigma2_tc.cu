@@ -25,71 +25,37 @@ namespace {
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound on every mbarrier wait (2 s)
 constexpr uint32_t kTileA = 128 * 128;        // bytes of one 128-row x 32-col fp32 operand half
 
-// g32 = (float)g; gh, gl = TF32 split of g (hi = tf32(g), lo = tf32(g - hi));
-// rows padded to ld floats with zeros.
+// g32 = (float)g; gh, gl = TF32 split of g32 (hi = tf32(g32), lo = tf32(g32 - hi));
+// rows padded to ld floats with zeros. One warp per row: row-contiguous reads
+// of the FP64 source and writes of the FP32 rows.
 __global__ void split_kernel(int n, long rows, int ld, const double *__restrict__ G,
                              float *__restrict__ g32, float *__restrict__ gh,
                              float *__restrict__ gl) {
-  const long total = rows * ld;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long)gridDim.x * blockDim.x) {
-    const long row = idx / ld;
-    const int c = (int)(idx % ld);
-    float a = 0.f, h = 0.f, l = 0.f;
-    if (c < n) {
-      const double x = G[row * n + c];
-      a = (float)x;
-      h = tc::tf32_rna(a);
-      l = tc::tf32_rna((float)(x - (double)h));
-    }
-    if (g32) g32[idx] = a;
-    if (gh) gh[idx] = h;
-    if (gl) gl[idx] = l;
-  }
-}
-
-// VQ[j] = V32 (g32[j] o g32[M-1-j]) in FP32: row b of VQ is column b of (g o gb) V
-// (V and g o gb are symmetric). Rows padded to ld (64x64 tiles).
-__global__ void __launch_bounds__(256) vq_kernel(int n, int M, int ld,
-                                                 const float *__restrict__ g32,
-                                                 const float *__restrict__ V32,
-                                                 float *__restrict__ VQ) {
-  const int j = blockIdx.z;
-  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
-  const float *g = g32 + (long)j * n * ld, *gb = g32 + (long)(M - 1 - j) * n * ld;
-  __shared__ float As[16][65], Bs[16][65];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < n; k0 += 16) {
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      int kk = e % 16, rr = e / 16, r = r0 + rr, k = k0 + kk;
-      As[kk][rr] = (r < n && k < n) ? V32[(long)r * ld + k] : 0.f;
-      int cc = e % 64, k2 = e / 64, c = c0 + cc, kq = k0 + k2;
-      Bs[k2][cc] = (c < n && kq < n) ? g[(long)kq * ld + c] * gb[(long)kq * ld + c] : 0.f;
-    }
-    __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long wpb = blockDim.x >> 5, nw = (long)gridDim.x * wpb;
+  for (long row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += nw) {
+    const double *src = G + row * n;
+    const long o = row * ld;
+    for (int c0 = 0; c0 < ld; c0 += 128) {
+      double x[4];
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
+      for (int u = 0; u < 4; ++u) {  // all loads of the slice in flight before any store
+        const int c = c0 + 32 * u + lane;
+        x[u] = (c < n) ? src[c] : 0.0;
+      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx + 16 * q];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], b[q], acc[i][q]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int r = r0 + ty + 16 * i;
-    if (r >= n) continue;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int c = c0 + tx + 16 * q;
-      if (c < ld) VQ[((long)j * n + r) * ld + c] = (c < n) ? acc[i][q] : 0.f;
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u + lane;
+        if (c >= ld) break;
+        // one FP64 operation per element (the conversion): the low part is the
+        // exact FP32 residual a - hi, which carries all that survives the split
+        const float a = (float)x[u];
+        const float h = tc::tf32_rna(a);
+        const float l = tc::tf32_rna(a - h);
+        if (g32) g32[o + c] = a;
+        if (gh) gh[o + c] = h;
+        if (gl) gl[o + c] = l;
+      }
     }
   }
 }
@@ -436,9 +402,9 @@ cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float 
   float *V32 = ws + 4 * stack;
   split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, gh, gl);
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
-  dim3 gq((ld + 63) / 64, (n + 63) / 64, M);
-  vq_kernel<<<gq, 256, 0, s>>>(n, M, ld, g32, V32, VQ);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_vq(n, M, ld, V32, g32, VQ, s);
 }
 
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,

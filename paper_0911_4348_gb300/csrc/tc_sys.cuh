@@ -58,8 +58,8 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
 // (i, j) over the extended FP32 source stack [2M][n][ld]: rows k < M are
 // Sigma_k, row M + i is the diagonal operand B_ii, taken with weight 1.
 cudaError_t launch_coef32(int M, const ConvCoef *coef, int4 *out, cudaStream_t s);
-// Diagonal operands B_ii = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} (FP64 sum,
-// rounded to FP32) into rows M..2M-1 of the FP32 source stack S32.
+// Diagonal operands B_ii = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} (FP32, from
+// the FP32 copy of Sigma in rows 0..M-1 of S32) into rows M..2M-1 of S32.
 cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma,
                             const double *wm, const double *wp, float *S32, cudaStream_t s);
 // I1 += part[0] + ... + part[nparts-1] (count doubles each), fixed order.

@@ -7,28 +7,83 @@
 namespace fedvr {
 namespace {
 
-// g_new = g^0 + I2; s = 0.5 * (g_new_ab + g_new_ba); g' = (1 - a) * g + a * s;
+// g_new = g^0 + I2; g' = (1 - a) g + a (g_new_ab + g_new_ba) / 2;
 // res = max |g' - g| (bit pattern of a non-negative double; NaN propagates as
-// the largest pattern). Unfused IEEE operations in this order.
-__global__ void update_kernel(int n, int M, double mixing, const double *__restrict__ G0,
-                              const double *__restrict__ I2, double *__restrict__ G,
-                              unsigned long long *res_bits) {
-  long nn = (long)n * n;
+// the largest pattern). Each g_new is formed once per element (shared with its
+// mirror through shared memory) and the mix is one fused multiply-add, so an
+// element costs four FP64 operations: at GB300's FP64 rate that, not HBM,
+// bounds this kernel.
+//
+// One block per pair of 32 x 32 tiles (P, Q) = (rows ta, cols tb) and its
+// mirror (rows tb, cols ta), ta <= tb, of one mesh point: both tiles of g^0 and
+// I2 are read row-contiguously into shared memory, so the transposed partner
+// of every element comes from shared memory instead of a strided global read.
+constexpr int kUT = 32;
+
+__device__ __forceinline__ double upd_one(double gab, double gba, double old, double keep,
+                                          double half_mix, double &m, bool &bad) {
+  const double nw = fma(half_mix, gab + gba, keep * old);
+  const double d = fabs(nw - old);
+  if (d != d || d == INFINITY) bad = true; else m = fmax(m, d);
+  return nw;
+}
+
+__global__ void __launch_bounds__(256) update_kernel(int n, int M, int nt, double mixing,
+                                                     const double *__restrict__ G0,
+                                                     const double *__restrict__ I2,
+                                                     double *__restrict__ G,
+                                                     unsigned long long *res_bits) {
+  __shared__ double P[kUT][kUT + 1], Q[kUT][kUT + 1];
+  const long nn = (long)n * n;
+  const long pairs = (long)nt * (nt + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const double keep = 1.0 - mixing, half_mix = 0.5 * mixing;
   double m = 0.0;
   bool bad = false;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long)M * nn;
-       idx += (long)gridDim.x * blockDim.x) {
-    long j = idx / nn, e = idx % nn;
-    int a = (int)(e / n), b = (int)(e % n);
-    long t = j * nn + (long)b * n + a;
-    double gab = __dadd_rn(G0[idx], I2[idx]);
-    double gba = __dadd_rn(G0[t], I2[t]);
-    double sym = __dmul_rn(0.5, __dadd_rn(gab, gba));
-    double old = G[idx];
-    double nw = __dadd_rn(__dmul_rn(__dsub_rn(1.0, mixing), old), __dmul_rn(mixing, sym));
-    G[idx] = nw;
-    double d = fabs(nw - old);
-    if (d != d || d == INFINITY) bad = true; else m = fmax(m, d);
+  for (long w = blockIdx.x; w < (long)M * pairs; w += gridDim.x) {
+    const int j = (int)(w / pairs);
+    long p = w % pairs;
+    int ta = 0;  // pair p -> (ta, tb), ta <= tb, row-major over the upper triangle
+    while (p >= nt - ta) {
+      p -= nt - ta;
+      ++ta;
+    }
+    const int tb = ta + (int)p;
+    const long base = (long)j * nn;
+    // g_new of tile (ta, tb) into P and of tile (tb, ta) into Q; the old g of
+    // both tiles into registers in the same pass (one memory round trip)
+    double oP[4], oQ[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
+      const int a = ta * kUT + r, b = tb * kUT + tx;
+      oP[q] = oQ[q] = 0.0;
+      if (a < n && b < n) {
+        const long idx = base + (long)a * n + b;
+        P[r][tx] = __dadd_rn(G0[idx], I2[idx]);
+        oP[q] = G[idx];
+      }
+      const int a2 = tb * kUT + r, b2 = ta * kUT + tx;
+      if (a2 < n && b2 < n) {
+        const long idx = base + (long)a2 * n + b2;
+        Q[r][tx] = __dadd_rn(G0[idx], I2[idx]);
+        oQ[q] = G[idx];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
+      const int a = ta * kUT + r, b = tb * kUT + tx;
+      if (a < n && b < n)  // element (a, b) pairs with (b, a) = Q[tx][r]
+        G[base + (long)a * n + b] = upd_one(P[r][tx], Q[tx][r], oP[q], keep, half_mix, m, bad);
+      if (ta != tb) {
+        const int a2 = tb * kUT + r, b2 = ta * kUT + tx;
+        if (a2 < n && b2 < n)
+          G[base + (long)a2 * n + b2] = upd_one(Q[r][tx], P[tx][r], oQ[q], keep, half_mix, m, bad);
+      }
+    }
+    __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) {
     m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -65,27 +120,65 @@ __global__ void energy_part_kernel(int n, int M, const double *__restrict__ G,
   if (threadIdx.x == 0) part[j] = acc;
 }
 
+// Row partials of the one-body energy terms, one block per row a:
+// rows[a] = sum_b h_ab rho_ab, rows[n + a] = sum_b Sigma^HF_ab rho_ab with
+// Sigma^HF_ab = sigma delta_ab sum_k V_ak rho_kk - V_ab rho_ab, rows[2n + a] = rho_aa.
+__global__ void energy_rows_kernel(int n, int M, double spin, const double *__restrict__ h,
+                                   const double *__restrict__ V, const double *__restrict__ G,
+                                   double *__restrict__ rows) {
+  const int a = blockIdx.x;
+  const long nn = (long)n * n;
+  const double *rho = G + (long)(M - 1) * nn;
+  double e1 = 0.0, e2 = 0.0, hart = 0.0;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    const long e = (long)a * n + b;
+    const double r = rho[e];
+    e1 += h[e] * r;
+    e2 += (-V[e] * r) * r;
+    hart += V[e] * rho[(long)b * n + b];
+  }
+  e1 = block_sum256(e1);
+  e2 = block_sum256(e2);
+  hart = block_sum256(hart);
+  if (threadIdx.x == 0) {
+    const double raa = rho[(long)a * n + a];
+    rows[a] = e1;
+    rows[n + a] = e2 + spin * hart * raa;
+    rows[2 * n + a] = raa;
+  }
+}
+
 // out[0] = E0 = sigma Tr[h rho] + (sigma/2) Tr[Sigma^HF[rho] rho]
-//              - (sigma/2) sum_j w_j part[j];  out[1] = N = sigma Tr rho;  rho = G[M-1]
+//              - (sigma/2) sum_j w_j part[j];  out[1] = N = sigma Tr rho;  rho = G[M-1].
+// With rows (from energy_rows_kernel) the one-body sums are taken over its row
+// partials in a fixed order; without, directly (single-matrix use by the HF loop).
 __global__ void energy_final_kernel(int n, int M, double spin, const double *__restrict__ h,
                                     const double *__restrict__ V, const double *__restrict__ G,
                                     const double *__restrict__ w, const double *__restrict__ part,
-                                    double *out) {
+                                    const double *__restrict__ rows, double *out) {
   long nn = (long)n * n;
   const double *rho = G + (long)(M - 1) * nn;
   double e1 = 0.0, e2 = 0.0, tr = 0.0, ec = 0.0;
-  for (long e = threadIdx.x; e < nn; e += blockDim.x) {
-    int a = (int)(e / n), b = (int)(e % n);
-    double r = rho[e];
-    e1 += h[e] * r;
-    double shf = -V[e] * r;
-    if (a == b) {
-      double hart = 0.0;
-      for (int k = 0; k < n; ++k) hart += V[(long)a * n + k] * rho[(long)k * n + k];
-      shf += spin * hart;
-      tr += r;
+  if (rows) {
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+      e1 += rows[a];
+      e2 += rows[n + a];
+      tr += rows[2 * n + a];
     }
-    e2 += shf * r;
+  } else {
+    for (long e = threadIdx.x; e < nn; e += blockDim.x) {
+      int a = (int)(e / n), b = (int)(e % n);
+      double r = rho[e];
+      e1 += h[e] * r;
+      double shf = -V[e] * r;
+      if (a == b) {
+        double hart = 0.0;
+        for (int k = 0; k < n; ++k) hart += V[(long)a * n + k] * rho[(long)k * n + k];
+        shf += spin * hart;
+        tr += r;
+      }
+      e2 += shf * r;
+    }
   }
   if (part)
     for (int j = threadIdx.x; j < M; j += blockDim.x) ec += w[j] * part[j];
@@ -118,24 +211,26 @@ cudaError_t launch_axpby(size_t count, double a, const double *x, double b, cons
 cudaError_t launch_energy_hf(int n, double spin, const double *h, const double *V,
                              const double *rho, double *out, cudaStream_t s) {
   // a one-point "stack" whose only member is rho, with no correlation term
-  energy_final_kernel<<<1, 256, 0, s>>>(n, 1, spin, h, V, rho, nullptr, nullptr, out);
+  energy_final_kernel<<<1, 256, 0, s>>>(n, 1, spin, h, V, rho, nullptr, nullptr, nullptr, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(int n, int M, double mixing, const double *G0, const double *I2,
                           double *G, unsigned long long *res_bits, cudaStream_t s) {
-  long tot = (long)M * n * n;
-  long blocks = (tot + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  update_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, mixing, G0, I2, G, res_bits);
+  const int nt = (n + kUT - 1) / kUT;
+  const long work = (long)M * nt * (nt + 1) / 2;
+  const long blocks = work < 152 * 16 ? work : 152 * 16;
+  update_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, M, nt, mixing, G0, I2, G, res_bits);
   return cudaGetLastError();
 }
 
+// part holds M + 3 n doubles: the per-mesh-point correlation sums, then the row partials.
 cudaError_t launch_energy(int n, int M, double spin, const double *h, const double *V,
                           const double *G, const double *A, const double *w, double *part,
                           double *out, cudaStream_t s) {
   energy_part_kernel<<<M, 256, 0, s>>>(n, M, G, A, part);
-  energy_final_kernel<<<1, 256, 0, s>>>(n, M, spin, h, V, G, w, part, out);
+  energy_rows_kernel<<<n, 256, 0, s>>>(n, M, spin, h, V, G, part + M);
+  energy_final_kernel<<<1, 256, 0, s>>>(n, M, spin, h, V, G, w, part, part + M, out);
   return cudaGetLastError();
 }
 
