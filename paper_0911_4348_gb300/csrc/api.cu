@@ -840,6 +840,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ctx->precision = precision;
   ctx->step_k = 0;
   ctx->prepared = true;
+  ctx->prep_gen++;
   return FEDVR_OK;
 }
 
@@ -990,13 +991,99 @@ int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len) {
 
 struct fedvr_batch {
   std::vector<fedvr_ctx *> ctxs;
+  std::vector<unsigned long long> gens;  // each context's prepare generation at creation
   int Np_max = 16, ld_max = 32;
   size_t off_c = 0, off_px = 0, off_pc = 0, off_err = 0, off_red = 0;
   std::vector<long> px, pc;
   std::vector<double> hred;
   std::vector<double> best;
   std::vector<int> grow;
+  // CUDA graph of one batched iteration for the active set `g_active` and mixing `g_mix`
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int> g_active;
+  double g_mix = 0;
+  int g_launches = 0;
+  ~fedvr_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
 };
+
+
+namespace {
+
+// Enqueue one batched iteration of the active systems on s (no host sync).
+int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t s, int *launches) {
+  fedvr_ctx *lead = B->ctxs[0];
+  const int n_sys = (int)B->ctxs.size();
+  uint8_t *bt = P<uint8_t>(lead->w_btab);
+  int *d_err = reinterpret_cast<int *>(bt + B->off_err);
+  for (int k = 0; k < n_sys; ++k)
+    if (active[k]) {
+      if (int r = phase_sigma_pre(B->ctxs[k], false, s, launches)) return r;
+    }
+  FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
+                                    reinterpret_cast<const long *>(bt + B->off_px), n_sys,
+                                    B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s));
+  *launches += 1;
+  for (int k = 0; k < n_sys; ++k)
+    if (active[k]) {
+      if (int r = phase_mid(B->ctxs[k], s, launches)) return r;
+    }
+  FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + B->off_c),
+                                 reinterpret_cast<const long *>(bt + B->off_pc), n_sys,
+                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s));
+  *launches += 1;
+  for (int k = 0; k < n_sys; ++k)
+    if (active[k]) {
+      fedvr_ctx *c = B->ctxs[k];
+      if (int r = phase_conv2(c, s, launches)) return r;
+      if (int r = phase_update(c, mixing, s, launches)) return r;
+      FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_red + (size_t)k * 3 * sizeof(double),
+                                     c->w_red.ptr, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     s));
+    }
+  return FEDVR_OK;
+}
+
+// Capture enqueue_batch into B->graph on the lead context's private stream;
+// a refused capture leaves the batch running eagerly (not an error).
+int capture_batch(fedvr_batch *B, const int *active, double mixing) {
+  fedvr_ctx *lead = B->ctxs[0];
+  const int n_sys = (int)B->ctxs.size();
+  if (!lead->cap_stream &&
+      cudaStreamCreateWithFlags(&lead->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    lead->cap_stream = nullptr;
+    return FEDVR_OK;
+  }
+  cudaStream_t cs = lead->cap_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return FEDVR_OK;
+  }
+  int launches = 0;
+  const int r = enqueue_batch(B, active, mixing, cs, &launches);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (r == FEDVR_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (r != FEDVR_OK || e != cudaSuccess || !exec) {
+    cudaGetLastError();
+    for (fedvr_ctx *c : B->ctxs) {  // clear what the refused capture recorded
+      c->failed = false;
+      c->err[0] = 0;
+    }
+    return FEDVR_OK;
+  }
+  B->graph = exec;
+  B->g_active.assign(active, active + n_sys);
+  B->g_mix = mixing;
+  B->g_launches = launches;
+  return FEDVR_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1032,6 +1119,7 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
     B->Np_max = g.Np > B->Np_max ? g.Np : B->Np_max;
     B->ld_max = g.ld > B->ld_max ? g.ld : B->ld_max;
   }
+  for (int k = 0; k < n_sys; ++k) B->gens.push_back(ctxs[k]->prep_gen);
   if (tc_smem_bytes(B->Np_max, B->ld_max, true) > 232448) {
     delete B;
     return fail(lead, FEDVR_ERR_ARG, "batch too wide for one shared-memory stage layout");
@@ -1102,7 +1190,9 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
   B->px[0] = B->pc[0] = 0;
   for (int k = 0; k < n_sys; ++k) {
     const fedvr_ctx *c = B->ctxs[k];
-    if (!c->prepared) return fail(lead, FEDVR_ERR_STATE, "system %d is no longer prepared", k);
+    if (!c->prepared || c->prep_gen != B->gens[k])
+      return fail(lead, FEDVR_ERR_STATE, "system %d was re-prepared or released after the batch was made",
+                  k);
     B->px[k + 1] = B->px[k] + (active[k] ? exchange_items(c->n, c->M) : 0);
     B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M, 1) : 0);
   }
@@ -1113,29 +1203,24 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
                                  cudaMemcpyHostToDevice, s));
   int *d_err = reinterpret_cast<int *>(bt + B->off_err);
   int launches = 0;
-  for (int k = 0; k < n_sys; ++k)
-    if (active[k]) {
-      if (int r = phase_sigma_pre(B->ctxs[k], false, s, &launches)) return r;
+  // one iteration of the whole batch: replayed from a CUDA graph captured for
+  // this active set and mixing, or launched eagerly
+  const std::vector<int> act(active, active + n_sys);
+  if (lead->use_graphs && (!B->graph || B->g_active != act || B->g_mix != mixing)) {
+    if (B->graph) {
+      cudaGraphExecDestroy(B->graph);
+      B->graph = nullptr;
     }
-  FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
-                                    reinterpret_cast<const long *>(bt + B->off_px), n_sys,
-                                    B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s));
-  for (int k = 0; k < n_sys; ++k)
-    if (active[k]) {
-      if (int r = phase_mid(B->ctxs[k], s, &launches)) return r;
-    }
-  FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + B->off_c),
-                                 reinterpret_cast<const long *>(bt + B->off_pc), n_sys,
-                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s));
-  for (int k = 0; k < n_sys; ++k)
-    if (active[k]) {
-      fedvr_ctx *c = B->ctxs[k];
-      if (int r = phase_conv2(c, s, &launches)) return r;
-      if (int r = phase_update(c, mixing, s, &launches)) return r;
-      FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_red + (size_t)k * 3 * sizeof(double),
-                                     c->w_red.ptr, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
-                                     s));
-    }
+    if (int r = capture_batch(B, active, mixing)) return r;
+  }
+  if (B->graph && lead->use_graphs) {
+    FEDVR_CK(lead, cudaGraphLaunch(B->graph, s));
+    launches = B->g_launches;
+    lead->last_step_graph = true;
+  } else {
+    if (int r = enqueue_batch(B, active, mixing, s, &launches)) return r;
+    lead->last_step_graph = false;
+  }
   FEDVR_CK(lead, cudaMemcpyAsync(B->hred.data(), bt + B->off_red, B->hred.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, s));
   int h_err = 0;
@@ -1144,7 +1229,7 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
   if (h_err) return fail(lead, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
   const double ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  lead->step_launches = launches + 2;
+  lead->step_launches = launches;
   int worst = FEDVR_OK;
   for (int k = 0; k < n_sys; ++k) {
     if (!active[k]) continue;

@@ -62,6 +62,8 @@ struct fedvr_ctx {
   // requested (0 = measured choice) and in use by the prepared run
   int c1_request = 0;
   int c1_splits = 1;
+  // incremented by every fedvr_2b_prepare (batches check it before each step)
+  unsigned long long prep_gen = 0;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
 

@@ -87,3 +87,37 @@ def test_batched_rejects_fp64_and_duplicates():
     with pytest.raises(FedvrError):
         solve_2b_batched([c, c], [s.beta] * 2, [s.u] * 2, [s.p] * 2)
     c.close()
+
+
+def test_batched_graph_replay_is_bit_identical():
+    # the batched iteration replayed from CUDA graphs (re-captured when a system
+    # converges and leaves the active set) equals eager launches bit for bit
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Batch
+    systems = _systems()[:3]
+    runs = {}
+    for graphs in (False, True):
+        ctxs = [_ctx(s) for s in systems]
+        ctxs[0].use_graphs(graphs)
+        b = Batch(ctxs, [s.beta for s in systems], [s.u for s in systems], [s.p for s in systems])
+        rec, used = [], []
+        for it in range(40):
+            r = b.step(0.5, tol=1e-8)
+            rec.append((r["res"].copy(), r["E0"].copy(), b.active.copy()))
+            used.append(ctxs[0].use_graphs())
+            if not b.active.any():
+                break
+        runs[graphs] = (rec, used, [c.get_history() for c in ctxs])
+        b.close()
+        for c in ctxs:
+            c.close()
+    (e_rec, e_used, e_hist), (g_rec, g_used, g_hist) = runs[False], runs[True]
+    assert not any(e_used) and all(g_used)
+    assert len(e_rec) == len(g_rec)
+    for (er, ee, ea), (gr, ge, ga) in zip(e_rec, g_rec):
+        assert np.array_equal(ea, ga)
+        assert np.array_equal(er[ea == 1], gr[ga == 1]) or np.array_equal(er, gr)
+        assert np.array_equal(ee, ge)
+    for he, hg in zip(e_hist, g_hist):
+        assert np.array_equal(he[:, :4], hg[:, :4])
