@@ -60,7 +60,13 @@ typedef enum {
                             cross-block sums; I^(2) eigenbasis products in
                             FP32; tables, update, residual, N and E0 in FP64.
                             Requires n_b <= 304. */
-  FEDVR_SPLIT_BF16 = 2   /* as above with three-way BF16 splits */
+  FEDVR_SPLIT_BF16 = 2,  /* reserved (three-way BF16 splits); rejected */
+  FEDVR_SPLIT_F16 = 3    /* as FEDVR_SPLIT_TF32, with the I^(1) contraction on
+                            kind::f16 tensor cores: operands scaled by powers
+                            of two into FP16's normal range and split as
+                            hi + lo (22 significant bits, as the TF32 split),
+                            twice the TF32 rate. Requires |g| < 16 (g's
+                            eigenvalues lie in [0, 1]) and n_b <= 304. */
 } fedvr_precision;
 
 /* ---------------------------------------------------------------------- */

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native
 
-FP64, SPLIT_TF32, SPLIT_BF16 = 0, 1, 2
+FP64, SPLIT_TF32, SPLIT_BF16, SPLIT_F16 = 0, 1, 2, 3
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOCONV", -4: "ERR_DIVERGED",
           -5: "ERR_TIMEOUT", -6: "ERR_NAN", -7: "ERR_STATE"}
 
@@ -434,4 +434,5 @@ def sigma2_noalloc(V, G, Sigma, spin=2.0, stream=None):
         raise FedvrError(code, "fedvr_sigma2_noalloc failed")
 
 
-__all__ = ["WarmStartNet", "Batch", "solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16"]
+__all__ = ["WarmStartNet", "Batch", "solve_2b_batched", "sigma2_noalloc", "Context", "FedvrError", "FP64", "SPLIT_TF32", "SPLIT_BF16",
+           "SPLIT_F16"]

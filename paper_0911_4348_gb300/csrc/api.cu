@@ -166,14 +166,29 @@ int tc_workspace(fedvr_ctx *ctx, int n, int M, float **ws, float **S32, int **er
   return FEDVR_OK;
 }
 
+bool is_split(int precision) {
+  return precision == FEDVR_SPLIT_TF32 || precision == FEDVR_SPLIT_F16;
+}
+
 int check_precision(fedvr_ctx *ctx, int precision, int n) {
   if (precision == FEDVR_FP64) return FEDVR_OK;
-  if (precision == FEDVR_SPLIT_TF32) {
+  if (is_split(precision)) {
     if (n > sigma2_tc_max_n())
-      return fail(ctx, FEDVR_ERR_ARG, "split-TF32 path supports n_b <= %d", sigma2_tc_max_n());
+      return fail(ctx, FEDVR_ERR_ARG, "split precision supports n_b <= %d", sigma2_tc_max_n());
     return FEDVR_OK;
   }
   return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
+}
+
+// FP16-split workspace: the hi and lo FP16 stacks of g ([M][n][ld16] each),
+// then the operand scales. NULL pointers when the context is not in that mode.
+int f16_workspace(fedvr_ctx *ctx, int n, int M, void **h16, TcScale **scale) {
+  const size_t halves = 2 * (size_t)M * n * ld16_of(n);
+  const size_t off = (halves * 2 + 255) / 256 * 256;
+  ENSURE(ctx, w_h16, off + 256);
+  *h16 = ctx->w_h16.ptr;
+  *scale = reinterpret_cast<TcScale *>(P<uint8_t>(ctx->w_h16) + off);
+  return FEDVR_OK;
 }
 
 // Device tables of the tensor-core kernels for one system: XSys, C1Sys and
@@ -192,9 +207,16 @@ int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *
   C1Sys c;
   memset(&x, 0, sizeof(x));
   memset(&c, 0, sizeof(c));
-  FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32));
+  void *h16 = nullptr;
+  TcScale *scale = nullptr;
+  if (ctx->precision == FEDVR_SPLIT_F16) {
+    if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
+  }
+  FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32,
+                          scale ? &scale->maxS : nullptr));
   (void)coef;
-  FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, P<int4>(ctx->w_coef32), I1, part));
+  FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, P<int4>(ctx->w_coef32), I1, part, h16,
+                           scale));
   long px[2] = {0, exchange_items(n, M)}, pc[2] = {0, conv1_items(n, M, splits)};
   uint8_t *base = P<uint8_t>(ctx->w_tab);
   FEDVR_CK(ctx, cudaMemcpyAsync(base + kTabX, &x, sizeof(x), cudaMemcpyHostToDevice, ctx->stream));
@@ -212,7 +234,8 @@ int launch_conv1_single(fedvr_ctx *ctx, int splits, int *err, cudaStream_t s, in
   uint8_t *tab = P<uint8_t>(ctx->w_tab);
   FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
                                 reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                conv1_items(n, M, splits), g.Np, err, ctx->num_sms, s));
+                                conv1_items(n, M, splits), g.Np, err, ctx->num_sms, s,
+                                ctx->precision == FEDVR_SPLIT_F16));
   *launches += 1;
   if (splits > 1) {
     FEDVR_CK(ctx, conv1_sum_splits((long)M * n * n, splits - 1, P<double>(ctx->w_c1p),
@@ -292,19 +315,27 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches) {
   const size_t stack = (size_t)M * n * n;
   double *G = P<double>(ctx->w_G), *S = P<double>(ctx->w_S);
   const double *V = P<double>(ctx->b_V);
+  void *h16 = nullptr;
+  TcScale *scale = nullptr;
+  if (ctx->precision == FEDVR_SPLIT_F16) {  // FP16 operands of g; the Sigma bound restarts
+    if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
+    FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
+    FEDVR_CK(ctx, cudaMemsetAsync(&scale->maxS, 0, sizeof(unsigned), s));
+    *launches += 1;
+  }
   if (warm) {
     FEDVR_CK(ctx, launch_copy(stack, P<double>(ctx->b_sigma_init), S, s));
     *launches += 1;
-    if (ctx->precision == FEDVR_SPLIT_TF32) {  // operands for the tensor-core convolution
+    if (is_split(ctx->precision)) {  // operands for the tensor-core convolution
       float *ws, *S32;
       int *err;
       if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
       const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
       FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
-      FEDVR_CK(ctx, launch_sigma_to_f32(n, M, S, S32, s));
+      FEDVR_CK(ctx, launch_sigma_to_f32(n, M, S, S32, s, scale ? &scale->maxS : nullptr));
       *launches += 2;
     }
-  } else if (ctx->precision == FEDVR_SPLIT_TF32) {
+  } else if (is_split(ctx->precision)) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
@@ -329,12 +360,17 @@ int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
   FEDVR_CK(ctx, launch_energy(n, M, ctx->spin, P<double>(ctx->b_h), V, G, S, P<double>(ctx->w_w),
                               P<double>(ctx->w_part), P<double>(ctx->w_red), s));
   *launches += 4;
-  if (ctx->precision == FEDVR_SPLIT_TF32) {
+  if (is_split(ctx->precision)) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
+    void *h16 = nullptr;
+    TcScale *scale = nullptr;
+    if (ctx->precision == FEDVR_SPLIT_F16) {
+      if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
+    }
     FEDVR_CK(ctx, launch_diag_f32(n, M, P<double>(ctx->w_dHF), S, P<double>(ctx->w_wm),
-                                  P<double>(ctx->w_wp), S32, s));
+                                  P<double>(ctx->w_wp), S32, s, scale ? &scale->maxS : nullptr));
     *launches += 1;
   }
   return FEDVR_OK;
@@ -353,7 +389,7 @@ int phase_conv2(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
   const int n = ctx->n, M = ctx->M;
   const double *C = P<double>(ctx->b_C);
   double *I1 = P<double>(ctx->w_I1), *I2 = P<double>(ctx->w_I2);
-  if (ctx->precision == FEDVR_SPLIT_TF32) {
+  if (is_split(ctx->precision)) {
     FEDVR_CK(ctx, conv2_apply_f32(n, M, P<float>(ctx->w_K32), C, I1, I2, P<float>(ctx->w_t1),
                                   P<float>(ctx->w_t2), s));
   } else {
@@ -385,7 +421,7 @@ int tc_err_ptr(fedvr_ctx *ctx, int **err) {
 int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsigned evflags,
                  int *launches) {
   const int n = ctx->n, M = ctx->M;
-  const bool split = ctx->precision == FEDVR_SPLIT_TF32;
+  const bool split = is_split(ctx->precision);
   int *err = nullptr;
   if (split) {
     if (int r = tc_err_ptr(ctx, &err)) return r;
@@ -463,7 +499,7 @@ int fedvr::sigma_of_current_g(fedvr_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   int launches = 0;
   if (int r = phase_sigma_pre(ctx, false, s, &launches)) return r;
-  if (ctx->precision == FEDVR_SPLIT_TF32) {
+  if (is_split(ctx->precision)) {
     int *err = nullptr;
     if (int r = tc_err_ptr(ctx, &err)) return r;
     FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -795,7 +831,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ENSURE(ctx, w_dHF, dsz(nn));
   ENSURE(ctx, w_part, dsz((size_t)M + 3 * (size_t)n));
   ENSURE(ctx, w_red, dsz(8));
-  if (precision == FEDVR_SPLIT_TF32) {
+  if (is_split(precision)) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
@@ -814,7 +850,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
                       P<double>(ctx->w_G0), n, nn, M, s));
   FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, tau, w, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
                                     eps, nullptr, ctx->mu, P<double>(ctx->w_K), s));
-  if (precision == FEDVR_SPLIT_TF32) {
+  if (is_split(precision)) {
     ENSURE(ctx, w_K32, (size_t)n * M * M * sizeof(float));
     FEDVR_CK(ctx, launch_to_f32((size_t)n * M * M, P<double>(ctx->w_K), P<float>(ctx->w_K32), s));
     float *ws, *S32;
@@ -822,6 +858,13 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
     ctx->n = n;
     ctx->M = M;
+    ctx->precision = precision;  // the tables and the split timing below depend on it
+    if (precision == FEDVR_SPLIT_F16) {
+      void *h16;
+      TcScale *scale;
+      if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
+      FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), scale, s));
+    }
     if (int r = choose_conv1_splits(ctx, ws, S32, err)) return r;
     if (int r = upload_single_tables(ctx, n, M, ws, P<double>(ctx->w_S), S32, P<double>(ctx->w_dHF),
                                      P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_I1),
@@ -852,7 +895,7 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   const size_t stack = (size_t)ctx->M * ctx->n * ctx->n;
   cudaStream_t s = ctx->stream;
   auto t0 = std::chrono::steady_clock::now();
-  const bool split = ctx->precision == FEDVR_SPLIT_TF32;
+  const bool split = is_split(ctx->precision);
   int *err = nullptr;
   if (split) {
     if (int r = tc_err_ptr(ctx, &err)) return r;
@@ -1031,7 +1074,8 @@ int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t
     }
   FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + B->off_c),
                                  reinterpret_cast<const long *>(bt + B->off_pc), n_sys,
-                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s));
+                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s,
+                                 lead->precision == FEDVR_SPLIT_F16));
   *launches += 1;
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
@@ -1097,8 +1141,8 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
     if (ctxs[k]->failed) return FEDVR_ERR_STATE;
   }
   fedvr_ctx *lead = ctxs[0];
-  if (precision != FEDVR_SPLIT_TF32)
-    return fail(lead, FEDVR_ERR_ARG, "the batched solve runs the split-TF32 tensor-core path");
+  if (!is_split(precision))
+    return fail(lead, FEDVR_ERR_ARG, "the batched solve runs a split-precision tensor-core path");
   for (int k = 0; k < n_sys; ++k) {
     if (ctxs[k]->device != lead->device)
       return fail(lead, FEDVR_ERR_ARG, "all systems must be on one device");
@@ -1148,10 +1192,19 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
     }
     memset(&hx[k], 0, sizeof(XSys));
     memset(&hc[k], 0, sizeof(C1Sys));
-    cudaError_t e = xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32);
+    void *h16 = nullptr;
+    TcScale *scale = nullptr;
+    if (precision == FEDVR_SPLIT_F16) {
+      if (int r = f16_workspace(c, c->n, c->M, &h16, &scale)) {
+        delete B;
+        return r;
+      }
+    }
+    cudaError_t e = xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32,
+                              scale ? &scale->maxS : nullptr);
     if (e == cudaSuccess)
       e = c1sys_fill(&hc[k], c->n, c->M, 1, ws, S32, P<double>(c->w_dHF),
-                     P<int4>(c->w_coef32), P<double>(c->w_I1), nullptr);
+                     P<int4>(c->w_coef32), P<double>(c->w_I1), nullptr, h16, scale);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt + k * sizeof(XSys), &hx[k], sizeof(XSys),
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt + B->off_c + k * sizeof(C1Sys), &hc[k],
@@ -1331,7 +1384,8 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
   if (!is_fin(spin)) return fail(ctx, FEDVR_ERR_ARG, "spin factor must be finite");
   if (int r = check_precision(ctx, precision, n)) return r;
   ctx->prepared = false;  // the workspace below is shared with a prepared run
-  if (precision == FEDVR_SPLIT_TF32) {
+  if (is_split(precision)) {  // the exchange runs split TF32 in both split modes
+    ctx->precision = FEDVR_SPLIT_TF32;
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
@@ -1370,24 +1424,33 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
   ctx->prepared = false;  // the workspace below is shared with a prepared run
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
   int M = 2 * u * p + 1;
-  if (precision == FEDVR_SPLIT_TF32) {
+  if (is_split(precision)) {
+    ctx->precision = precision;
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
     const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
     cudaStream_t s = ctx->stream;
     FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    void *h16 = nullptr;
+    TcScale *scale = nullptr;
+    const bool f16 = precision == FEDVR_SPLIT_F16;
+    if (f16) {
+      if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
+      FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), scale, s));
+      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
+    }
     if (int r = upload_single_tables(ctx, n, M, ws, nullptr, S32, dHF, P<ConvCoef>(ctx->w_coef), I1))
       return r;
     FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
-    FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s));
+    FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s, f16 ? &scale->maxS : nullptr));
     FEDVR_CK(ctx, launch_diag_f32(n, M, dHF, Sigma, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
-                                  S32, s));
+                                  S32, s, f16 ? &scale->maxS : nullptr));
     const TcGeom g = tc_geom(n, M);
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
                                   reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                  conv1_items(n, M, 1), g.Np, err, ctx->num_sms, s));
+                                  conv1_items(n, M, 1), g.Np, err, ctx->num_sms, s, f16));
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;

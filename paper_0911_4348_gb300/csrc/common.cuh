@@ -75,7 +75,7 @@ struct fedvr_ctx {
   fedvr::DevBuf b_sigma_init;
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
-      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32;
+      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16;
 };
 
 namespace fedvr {
@@ -157,6 +157,7 @@ cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, 
                       cudaStream_t s);
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows,
                            int box_cols = 32);
+cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, int ld16, int rows);
 
 // sigma2_tc.cu (tensor cores, split TF32): the split workspace of a system
 // holds 4 * M*n*ld + n*ld floats (g32, gh, gl, VQ, V32; ld = n rounded up to 32).
@@ -169,7 +170,8 @@ cudaError_t launch_split_g(int n, int M, const double *G, float *g32, float *gh,
 
 // conv_tc.cu (tensor cores, split TF32): S32 = Sigma in FP32 (pitch ld); gh/gl
 // are the split copies of G from launch_split_g / sigma2_tc.
-cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s);
+cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s,
+                                unsigned *smax = nullptr);
 
 // conv.cu
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,

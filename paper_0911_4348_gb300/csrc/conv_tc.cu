@@ -338,7 +338,7 @@ __global__ void coef32_kernel(long mm, int M, const ConvCoef *__restrict__ coef,
 // it for every i, so the FP64 matrix dHF is converted once per element.
 __global__ void diag_f32_kernel(int n, int M, int ld, const double *__restrict__ dHF,
                                 const double *__restrict__ wm, const double *__restrict__ wp,
-                                float *__restrict__ S32) {
+                                float *__restrict__ S32, unsigned *smax) {
   extern __shared__ float wf[];  // wm, wp in FP32: [2][M]
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     wf[i] = (float)wm[i];
@@ -356,7 +356,16 @@ __global__ void diag_f32_kernel(int n, int M, int ld, const double *__restrict__
       s0 = S32[e];
       s1 = S32[(long)(M - 1) * nld + e];
     }
-    for (int i = 0; i < M; ++i) D[(long)i * nld + e] = (h - wf[i] * s0) + wf[M + i] * s1;
+    float m = 0.f;
+    for (int i = 0; i < M; ++i) {
+      const float v = (h - wf[i] * s0) + wf[M + i] * s1;
+      D[(long)i * nld + e] = v;
+      m = fmaxf(m, fabsf(v));
+    }
+    if (smax) {  // largest |B_ii| entry, for the FP16 operand scale
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(smax, __float_as_uint(m));
+    }
   }
 }
 
@@ -373,26 +382,359 @@ __global__ void conv1_sum_splits_kernel(long count, int nparts, const double *__
 
 // S32 = (float)Sigma with rows padded to ld (zeros beyond n).
 __global__ void sigma_to_f32_kernel(int n, long rows, int ld, const double *__restrict__ S,
-                                    float *__restrict__ S32) {
+                                    float *__restrict__ S32, unsigned *smax) {
   const long total = rows * ld;
+  float m = 0.f;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long)gridDim.x * blockDim.x) {
     const long row = idx / ld;
     const int c = (int)(idx % ld);
-    S32[idx] = (c < n) ? (float)S[row * n + c] : 0.f;
+    const float v = (c < n) ? (float)S[row * n + c] : 0.f;
+    S32[idx] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  if (smax) {
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(smax, __float_as_uint(m));
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// FP16-split variant (precision FEDVR_SPLIT_F16): the same contraction with
+// kind::f16 MMAs. A 128-byte operand row holds 64 FP16 values, so a chunk
+// covers 64 contraction terms for the same shared-memory stage size, and the
+// three products hi*hi + hi*lo + lo*hi run at twice the TF32 rate. Operands are
+// scaled by powers of two into FP16's normal range (g by 2^kScaleG, the
+// interpolated Sigma by 2^sA with sA from maxC * max|S32|), and the flush
+// multiplies the FP32 block sums by 2^-(sA + kScaleG) exactly. 16 producer
+// warps (two 16-byte units, i.e. 16 source floats, per thread and chunk).
+constexpr int kWarpsH = 22;  // 0-3 flush, 4-19 A producers, 20 TMA, 21 MMA
+constexpr int kThreadsH = kWarpsH * 32;
+
+__device__ __forceinline__ int a_scale_exp(const TcScale *sc) {
+  const float amax = __uint_as_float(sc->maxS) * sc->maxC;
+  if (!(amax > 0.f) || !(amax < 3.0e38f)) return 0;
+  int e;
+  frexpf(amax, &e);  // amax < 2^e
+  e = 14 - e;        // scaled maximum below 2^14
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+__global__ void __launch_bounds__(kThreadsH, 1)
+    conv1_f16_kernel(const C1Sys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
+                     long items, int Np_max, int nbuf, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+  const uint32_t tileB = (uint32_t)Np_max * 128;
+  const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
+  uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&full[0], 513);
+    tc::mbar_init(&full[1], 513);
+    tc::mbar_init(&empty[0], 1);
+    tc::mbar_init(&empty[1], 1);
+    tc::mbar_init(&accf[0], 1);
+    tc::mbar_init(&accf[1], 1);
+    tc::mbar_init(&acce[0], 128);
+    tc::mbar_init(&acce[1], 128);
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  bool issued = false;
+  int cur = 0;
+
+  if (warp >= 4 && warp < 20) {
+    // ---- A producers: rows r0 and r0 + 64 of the tile, 16-byte unit c (8 FP16
+    // values) of each 64-wide slice ----
+    const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
+    const uint32_t off[2] = {tc::sw128_offset(r0, c), tc::sw128_offset(r0 + 64, c)};
+    uint32_t cc = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const C1Sys &S = sys[cur];
+      const int n = S.g.n, ld = S.g.ld, M = S.g.M, KC = (n + 63) / 64;
+      const float *const S32 = S.S32;
+      const int4 *const coef32 = S.coef32;
+      const float fA = ldexpf(1.f, a_scale_exp(S.scale));
+      const long R = (long)M * n;
+      const C1Item it = c1_item(S, w - prefix[cur]);
+      int ia[2], aa[2];
+      bool live[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const long r = (long)it.t * 128 + r0 + 64 * k;
+        live[k] = r < R;
+        ia[k] = live[k] ? (int)(r / n) : 0;
+        aa[k] = live[k] ? (int)(r % n) : 0;
+      }
+      for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
+        uint32_t o1[2], o2[2];  // element offsets of the two bracket rows in S32
+        float c1[2], c2[2];     // weights times the operand scale 2^sA
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int4 cf = coef32[(long)ia[k] * M + j];
+          o1[k] = (uint32_t)((cf.x * n + aa[k]) * ld);
+          o2[k] = (uint32_t)((cf.y * n + aa[k]) * ld);
+          c1[k] = __int_as_float(cf.z) * fA;
+          c2[k] = __int_as_float(cf.w) * fA;
+        }
+        for (int kc = 0; kc < KC; ++kc, ++cc) {
+          const int l0 = kc * 64 + 8 * c;
+          const bool in = l0 < ld;  // ld is a multiple of 32: a unit is wholly in or out
+          float4 a1[2][2], a2[2][2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            if (live[k] && in) {
+              a1[k][0] = *reinterpret_cast<const float4 *>(S32 + o1[k] + l0);
+              a1[k][1] = *reinterpret_cast<const float4 *>(S32 + o1[k] + l0 + 4);
+              a2[k][0] = *reinterpret_cast<const float4 *>(S32 + o2[k] + l0);
+              a2[k][1] = *reinterpret_cast<const float4 *>(S32 + o2[k] + l0 + 4);
+            } else {
+              a1[k][0] = a1[k][1] = a2[k][0] = a2[k][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+          const int s = cc & 1;
+          const uint32_t use = cc >> 1;
+          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
+          }
+          uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const float y[8] = {fmaf(c1[k], a1[k][0].x, c2[k] * a2[k][0].x),
+                                fmaf(c1[k], a1[k][0].y, c2[k] * a2[k][0].y),
+                                fmaf(c1[k], a1[k][0].z, c2[k] * a2[k][0].z),
+                                fmaf(c1[k], a1[k][0].w, c2[k] * a2[k][0].w),
+                                fmaf(c1[k], a1[k][1].x, c2[k] * a2[k][1].x),
+                                fmaf(c1[k], a1[k][1].y, c2[k] * a2[k][1].y),
+                                fmaf(c1[k], a1[k][1].z, c2[k] * a2[k][1].z),
+                                fmaf(c1[k], a1[k][1].w, c2[k] * a2[k][1].w)};
+            uint4 hi, lo;
+            tc::f16_split2(y[0], y[1], hi.x, lo.x);
+            tc::f16_split2(y[2], y[3], hi.y, lo.y);
+            tc::f16_split2(y[4], y[5], hi.z, lo.z);
+            tc::f16_split2(y[6], y[7], hi.w, lo.w);
+            *reinterpret_cast<uint4 *>(st + off[k]) = hi;
+            *reinterpret_cast<uint4 *>(st + kTileA + off[k]) = lo;
+          }
+          tc::fence_smem_to_async();
+          tc::mbar_arrive(&full[s]);
+        }
+      }
+    }
+  } else if (warp == 20) {
+    // ---- TMA: g_j FP16 split rows 0..Np-1, 64 columns per chunk, hi and lo ----
+    if (lane == 0) {
+      uint32_t cc = 0;
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+        const C1Sys &S = sys[cur];
+        const C1Item it = c1_item(S, w - prefix[cur]);
+        const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
+        const int NT = S.g.NT, KC = (S.g.n + 63) / 64, n00 = S.g.n0[0], n01 = S.g.n0[1];
+        const CUtensorMap *th0 = &S.hh[0], *th1 = &S.hh[1], *tl0 = &S.hl[0], *tl1 = &S.hl[1];
+        for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
+          for (int kc = 0; kc < KC; ++kc, ++cc) {
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+            tc::mbar_arrive_expect_tx(&full[s], bytes);
+            for (int nt = 0; nt < NT; ++nt) {
+              const int r = nt ? n01 : n00;
+              tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 64, r, j, &full[s]);
+              tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 64, r, j, &full[s]);
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 21) {
+    // ---- MMA issue (kind::f16, K = 16 per instruction) ----
+    if (lane == 0) {
+      uint32_t cc = 0, tcount = 0;
+      for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+        const C1Sys &S = sys[cur];
+        const C1Item it = c1_item(S, w - prefix[cur]);
+        const int n = S.g.n, KC = (n + 63) / 64, NT = S.g.NT, JB = S.JB;
+        const uint32_t n00 = (uint32_t)S.g.n0[0], n01 = (uint32_t)S.g.n0[1];
+        const uint32_t id0 = tc::idesc_f16(128, S.g.nsz[0]), id1 = tc::idesc_f16(128, S.g.nsz[1]);
+        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB, ++tcount) {
+          const int j1 = min(it.j_hi, j0 + JB);
+          const int buf = tcount & 1;
+          const uint32_t tu = tcount >> 1;
+          bool ok = true;
+          if (nbuf == 1 && tcount > 0)
+            ok = tc::mbar_wait(&acce[(tcount - 1) & 1], ((tcount - 1) >> 1) & 1, kWaitNs);
+          else if (nbuf == 2 && tu > 0)
+            ok = tc::mbar_wait(&acce[buf], (tu - 1) & 1, kWaitNs);
+          if (!ok) {
+            *abort_flag = 1;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
+          for (int j = j0; j < j1 && !*abort_flag; ++j) {
+            for (int kc = 0; kc < KC; ++kc, ++cc) {
+              const int s = cc & 1;
+              const uint32_t use = cc >> 1;
+              if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+                *abort_flag = 1;
+                break;
+              }
+              tc::fence_after_sync();
+              const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
+              const int ksteps = min(4, (n - kc * 64 + 15) / 16);
+              const bool fresh = (j == j0 && kc == 0);
+              for (int kk = 0; kk < ksteps; ++kk) {
+                const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+                const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+                for (int nt = 0; nt < NT; ++nt) {
+                  const uint32_t r = nt ? n01 : n00;
+                  const uint32_t boff = 2 * kTileA + r * 128 + kk * 32;
+                  const uint64_t bh = tc::sdesc_k128(sa + boff);
+                  const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+                  const uint32_t d = dbase + r;
+                  const uint32_t idesc = nt ? id1 : id0;
+                  tc::mma_f16(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
+                  tc::mma_f16(d, ah, bl, idesc, 1u);
+                  tc::mma_f16(d, al, bh, idesc, 1u);
+                }
+              }
+              tc::mma_commit(&empty[s]);
+              issued = true;
+            }
+          }
+          tc::mma_commit(&accf[buf]);
+        }
+      }
+    }
+  } else if (warp < 4) {
+    // ---- flush: scale each FP32 block back and add it into the FP64 output rows ----
+    uint32_t tcount = 0;
+    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+      while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
+      const C1Sys &S = sys[cur];
+      const int n = S.g.n, JB = S.JB;
+      const double inv = ldexp(1.0, -(a_scale_exp(S.scale) + kScaleG));
+      const C1Item it = c1_item(S, w - prefix[cur]);
+      const long r = (long)it.t * 128 + warp * 32 + lane;
+      const bool live = r < (long)S.g.M * n;
+      double *row = it.out + (live ? r : 0) * n;
+      for (int j0 = it.j_lo; j0 < it.j_hi; j0 += JB, ++tcount) {
+        const int buf = tcount & 1;
+        const uint32_t tu = tcount >> 1;
+        if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
+        const bool first = j0 == it.j_lo;
+        for (int c0 = 0; c0 < n; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          if (live) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const int b = c0 + t;
+              if (b < n) row[b] = first ? (double)v[t] * inv : row[b] + (double)v[t] * inv;
+            }
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&acce[buf]);
+      }
+    }
+  }
+
+  __syncthreads();
+  if (*abort_flag) {
+    if (warp == 21 && lane == 0) {
+      if (issued) tc::mma_commit(drain);
+      atomicExch(err, 1);
+      if (issued) tc::mbar_wait(drain, 0, kWaitNs);
+    }
+    __syncthreads();
+  }
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// FP16 split of g scaled by 2^kScaleG; one warp per row, two columns per lane.
+__global__ void split_f16_kernel(int n, long rows, int ld16, const double *__restrict__ G,
+                                 uint32_t *__restrict__ hi, uint32_t *__restrict__ lo) {
+  const int lane = threadIdx.x & 31;
+  const long wpb = blockDim.x >> 5, nw = (long)gridDim.x * wpb;
+  const double sc = (double)(1 << kScaleG);
+  for (long row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += nw) {
+    const double *src = G + row * n;
+    const long o = row * (ld16 / 2);
+    for (int c0 = 0; c0 < ld16; c0 += 64) {
+      const int c = c0 + 2 * lane;
+      const float y0 = (c < n) ? (float)(src[c] * sc) : 0.f;
+      const float y1 = (c + 1 < n) ? (float)(src[c + 1] * sc) : 0.f;
+      uint32_t h, l;
+      tc::f16_split2(y0, y1, h, l);
+      hi[o + c / 2] = h;
+      lo[o + c / 2] = l;
+    }
+  }
+}
+
+// scale->maxC = max over (i, j) of |c1| + |c2|; scale->maxS = 0 (one block).
+__global__ void scale_init_kernel(long mm, const int4 *__restrict__ coef32, TcScale *scale) {
+  __shared__ float sh[256];
+  float m = 0.f;
+  for (long x = threadIdx.x; x < mm; x += blockDim.x) {
+    const int4 c = coef32[x];
+    m = fmaxf(m, fabsf(__int_as_float(c.z)) + fabsf(__int_as_float(c.w)));
+  }
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + st]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    scale->maxC = sh[0];
+    scale->maxS = 0u;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s) {
+cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaStream_t s,
+                                unsigned *smax) {
   const int ld = (n + 31) / 32 * 32;
-  sigma_to_f32_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, S, S32);
+  sigma_to_f32_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, S, S32, smax);
   return cudaGetLastError();
 }
 
 cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
-                       const double *dHF, const int4 *coef32, double *I1, double *part) {
+                       const double *dHF, const int4 *coef32, double *I1, double *part,
+                       const void *h16, const TcScale *scale) {
   d->g = tc_geom(n, M);
   const long stack = (long)M * n * d->g.ld;
   d->JB = 4096 / n > 1 ? 4096 / n : 1;
@@ -408,11 +750,36 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
     if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
+  d->scale = scale;
+  if (h16) {
+    const int ld16 = ld16_of(n);
+    const uint16_t *hh = reinterpret_cast<const uint16_t *>(h16);
+    const uint16_t *hl = hh + (size_t)M * n * ld16;
+    for (int t = 0; t < 2; ++t) {
+      cudaError_t e = make_tmap_rows16(&d->hh[t], hh, n, M, ld16, d->g.nsz[t]);
+      if (e == cudaSuccess) e = make_tmap_rows16(&d->hl[t], hl, n, M, ld16, d->g.nsz[t]);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return cudaSuccess;
 }
 
+cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s) {
+  const int ld16 = ld16_of(n);
+  uint32_t *hi = reinterpret_cast<uint32_t *>(h16);
+  uint32_t *lo = hi + (size_t)M * n * ld16 / 2;
+  split_f16_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld16, G, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_init(int M, const int4 *coef32, TcScale *scale, cudaStream_t s) {
+  scale_init_kernel<<<1, 256, 0, s>>>((long)M * M, coef32, scale);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma,
-                            const double *wm, const double *wp, float *S32, cudaStream_t s) {
+                            const double *wm, const double *wp, float *S32, cudaStream_t s,
+                            unsigned *smax) {
   (void)Sigma;  // read through its FP32 copy in S32
   const int ld = (n + 31) / 32 * 32;
   const long nld = (long)n * ld;
@@ -423,7 +790,7 @@ cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
   }
-  diag_f32_kernel<<<blocks, 256, shm, s>>>(n, M, ld, dHF, wm, wp, S32);
+  diag_f32_kernel<<<blocks, 256, shm, s>>>(n, M, ld, dHF, wm, wp, S32, smax);
   return cudaGetLastError();
 }
 
@@ -440,7 +807,7 @@ cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double 
 }
 
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
-                            int Np_max, int *err, int num_sms, cudaStream_t s) {
+                            int Np_max, int *err, int num_sms, cudaStream_t s, bool f16) {
   // stages + barriers (256 B) + four 32 x 17 float flush staging tiles
   const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 128) + 256 +
                       4 * 32 * 17 * sizeof(float);
@@ -449,6 +816,13 @@ cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, lon
   if (e != cudaSuccess) return e;
   const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
+  if (f16) {
+    e = cudaFuncSetAttribute(conv1_f16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    conv1_f16_kernel<<<grid, kThreadsH, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
+    return cudaGetLastError();
+  }
   conv1_tc_kernel<<<grid, kThreads, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
   return cudaGetLastError();
 }

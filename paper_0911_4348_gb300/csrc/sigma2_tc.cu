@@ -316,6 +316,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
       }
       tc::fence_before_sync();
       tc::mbar_arrive(&acce[buf]);
+      if (S.smax) {  // largest |Sigma| entry, for the FP16 operand scale of the convolution
+        float mx = live ? fabsf(acc) : 0.f;
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(S.smax, __float_as_uint(mx));
+      }
       if (live) {
         const long nn = (long)n * n;
         S.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
@@ -408,7 +413,7 @@ cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float 
 }
 
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
-                      float *S32) {
+                      float *S32, unsigned *smax) {
   d->g = tc_geom(n, M);
   const long stack = (long)M * n * d->g.ld;
   d->spin = (float)spin;
@@ -417,6 +422,7 @@ cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, doubl
   d->V32 = ws + 4 * stack;
   d->Sigma = Sigma;
   d->S32 = S32;
+  d->smax = smax;
   for (int t = 0; t < 2; ++t) {
     cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);

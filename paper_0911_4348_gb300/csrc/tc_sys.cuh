@@ -20,6 +20,17 @@ struct TcGeom {
   int n0[2], nsz[2];
 };
 
+// Operand scales of the FP16-split path, one per system (device memory).
+// Values of g and of g V enter FP16 as x * 2^kScaleG (|g| < 16 keeps them
+// below 65504); the convolution's interpolated Sigma enters as x * 2^sA with
+// sA from the bound maxC * max|Sigma| chosen per launch.
+constexpr int kScaleG = 12;
+struct TcScale {
+  unsigned maxS;  // bit pattern of max |x| over the FP32 source stack (Sigma and B_ii rows)
+  float maxC;     // max over (i, j) of |c1| + |c2|
+  unsigned pad[2];
+};
+
 // Sigma^(2) exchange kernel: one system.
 struct XSys {
   CUtensorMap th[2], tl[2];   // gb = G[M-1-j] split, per N tile
@@ -28,11 +39,14 @@ struct XSys {
   const float *g32, *V32, *VQ;
   double *Sigma;
   float *S32;
+  unsigned *smax;             // if set: atomic max of |Sigma| (FP32 bits)
 };
 
 // First convolution kernel: one system.
 struct C1Sys {
   CUtensorMap th[2], tl[2];   // g_j split, per N tile
+  CUtensorMap hh[2], hl[2];   // g_j FP16 split (scaled by 2^kScaleG), per N tile
+  const TcScale *scale;       // FP16 path: operand scales
   TcGeom g;
   int JB;                     // mesh points per FP32 accumulation block
   int S;                      // splits of the mesh-point range per row tile
@@ -51,9 +65,17 @@ size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns);
 // Host-side descriptor fill (tensor maps included); the caller copies the
 // descriptors to device memory.
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
-                      float *S32);
+                      float *S32, unsigned *smax = nullptr);
 cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
-                       const double *dHF, const int4 *coef32, double *I1, double *part);
+                       const double *dHF, const int4 *coef32, double *I1, double *part,
+                       const void *h16 = nullptr, const TcScale *scale = nullptr);
+// Pitch (elements) of the FP16 split rows: n rounded up to 64 (128-byte rows).
+inline int ld16_of(int n) { return (n + 63) / 64 * 64; }
+// FP16 split of g (scaled by 2^kScaleG) into h16 = [hi stack][lo stack],
+// [M][n][ld16] halves each, padding zero.
+cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s);
+// scale->maxC = max |c1| + |c2| over the coefficient table; scale->maxS = 0.
+cudaError_t launch_scale_init(int M, const int4 *coef32, TcScale *scale, cudaStream_t s);
 // Compact FP32 convolution coefficients {k1, k2, (float)c1, (float)c2} per
 // (i, j) over the extended FP32 source stack [2M][n][ld]: rows k < M are
 // Sigma_k, row M + i is the diagonal operand B_ii, taken with weight 1.
@@ -61,7 +83,8 @@ cudaError_t launch_coef32(int M, const ConvCoef *coef, int4 *out, cudaStream_t s
 // Diagonal operands B_ii = dHF - wm_i Sigma_0 + wp_i Sigma_{M-1} (FP32, from
 // the FP32 copy of Sigma in rows 0..M-1 of S32) into rows M..2M-1 of S32.
 cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma,
-                            const double *wm, const double *wp, float *S32, cudaStream_t s);
+                            const double *wm, const double *wp, float *S32, cudaStream_t s,
+                            unsigned *smax = nullptr);
 // I1 += part[0] + ... + part[nparts-1] (count doubles each), fixed order.
 cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
                              cudaStream_t s);
@@ -74,7 +97,7 @@ cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float 
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
                                int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s);
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
-                            int Np_max, int *err, int num_sms, cudaStream_t s);
+                            int Np_max, int *err, int num_sms, cudaStream_t s, bool f16 = false);
 
 // Work items per system: exchange (j, row tile) pairs over the n(n+1)/2
 // stacked rows (b, a >= b) of each mesh point; convolution (row tile, split)

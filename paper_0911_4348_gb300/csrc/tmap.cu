@@ -1,7 +1,8 @@
 // TMA tensor maps for the split operand arrays: a 3-D map over [M][n][ld]
 // floats (ld = n rounded up to 32) whose box is 32 columns (128-byte swizzle)
 // or 16 columns (64-byte swizzle) x `rows` rows x 1 matrix, rows beyond n
-// zero-filled. The encoder comes from
+// zero-filled. make_tmap_rows16 is the same over FP16 rows of ld16 halves
+// (a multiple of 64), box 64 halves (128 bytes) wide. The encoder comes from
 // the driver through the runtime's entry-point lookup, so no link against
 // libcuda is needed.
 #include <cudaTypedefs.h>
@@ -42,6 +43,22 @@ cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, in
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, int ld16,
+                             int rows) {
+  std::call_once(g_encode_once, load_encoder);
+  if (!g_encode) return cudaErrorNotSupported;
+  if (rows < 1 || rows > 256 || (ld16 % 64) != 0) return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {(cuuint64_t)ld16, (cuuint64_t)n, (cuuint64_t)M};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld16 * 2, (cuuint64_t)n * (cuuint64_t)ld16 * 2};
+  const cuuint32_t box[3] = {64, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

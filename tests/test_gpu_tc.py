@@ -203,3 +203,86 @@ def test_conv1_measured_split_choice_is_a_candidate():
     r = c.solve_2b(s.beta, s.u, s.p, s.mixing, s.tol, 100, precision=TF32)
     assert r["status"] == 0
     c.close()
+
+
+F16 = 3
+
+
+@pytest.mark.parametrize("n,u,p,beta,seed", [(8, 2, 3, 10.0, 0), (37, 2, 3, 25.0, 1),
+                                             (130, 1, 3, 100.0, 2), (257, 1, 2, 100.0, 3)])
+def test_conv1_f16_random(ctx, n, u, p, beta, seed):
+    # FP16-split operands scaled into FP16's range carry 22 significant bits,
+    # like the TF32 split: the same bound
+    rng = W.system_rng(98, seed)
+    M = 2 * u * p + 1
+    A = W.random_symmetric_stack(rng, M, n)
+    G = W.random_symmetric_stack(rng, M, n)
+    dHF = W.random_symmetric(rng, n, 0.1)
+    I1 = torch.empty((M, n, n), dtype=torch.float64, device="cuda")
+    ctx.conv_sigma_g(beta, u, p, _dev(dHF), _dev(A), _dev(G), I1, precision=F16)
+    torch.cuda.synchronize()
+    mesh = O.power_mesh(beta, u, p)
+    ref = O.conv1(dHF, A, G, mesh, beta, O.lag_table(mesh["tau"], beta))
+    assert maxrel(I1.cpu().numpy(), ref) < SIGMA_TOL
+
+
+def test_conv1_f16_small_magnitudes(ctx):
+    # Sigma five orders of magnitude below 1: the operand scale keeps FP16 normal
+    rng = W.system_rng(98, 7)
+    n, u, p, beta = 37, 2, 3, 25.0
+    M = 2 * u * p + 1
+    A = 1e-5 * W.random_symmetric_stack(rng, M, n)
+    G = W.random_symmetric_stack(rng, M, n)
+    dHF = W.random_symmetric(rng, n, 1e-6)
+    I1 = torch.empty((M, n, n), dtype=torch.float64, device="cuda")
+    ctx.conv_sigma_g(beta, u, p, _dev(dHF), _dev(A), _dev(G), I1, precision=F16)
+    torch.cuda.synchronize()
+    mesh = O.power_mesh(beta, u, p)
+    ref = O.conv1(dHF, A, G, mesh, beta, O.lag_table(mesh["tau"], beta))
+    assert maxrel(I1.cpu().numpy(), ref) < SIGMA_TOL
+
+
+def test_conv1_f16_he_small_full(ctx):
+    ref = oracle_system("he_small")
+    s, hf, mesh, G0 = ref["sys"], ref["hf"], ref["mesh"], ref["G0"]
+    A = O.sigma2(G0, ref["V"], 2.0)
+    dHF = O.hf_selfenergy(G0[-1], ref["V"], 2.0) - hf["Sigma0"]
+    I1 = torch.empty(G0.shape, dtype=torch.float64, device="cuda")
+    ctx.conv_sigma_g(s.beta, s.u, s.p, _dev(dHF), _dev(A), _dev(G0), I1, precision=F16)
+    torch.cuda.synchronize()
+    want = O.conv1(dHF, A, G0, mesh, s.beta, O.lag_table(mesh["tau"], s.beta))
+    assert maxrel(I1.cpu().numpy(), want) < CONV_TOL
+
+
+def test_solve_2b_f16_he_small_energy(ctx):
+    ref = oracle_system("he_small")
+    s = ref["sys"]
+    res = O.solve_2b(ref["h"], ref["V"], 2.0, ref["hf"], s.beta, s.u, s.p, s.mixing, s.tol, 100)
+    ctx.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    ctx.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+    ctx.solve_hf(s.beta, tol=1e-13)
+    out = ctx.solve_2b(s.beta, s.u, s.p, s.mixing, s.tol, 100, precision=F16)
+    assert abs(out["E0"] - res["E0"]) < E0_TOL
+    assert abs(out["N"] - res["N"]) < 1e-6
+
+
+def test_f16_and_fp64_steps_agree_at_full_size():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Context
+    s = W.he_medium()
+    out = {}
+    for prec in (0, F16):
+        c = Context()
+        c.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+        c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+        c.solve_hf(s.beta, tol=1e-12)
+        c.prepare_2b(s.beta, s.u, s.p, prec)
+        Es = [c.step_2b(s.mixing)["E0"] for _ in range(3)]
+        G = np.empty((s.n_tau, s.n_b, s.n_b))
+        c.read_2b(G_out=G)
+        out[prec] = (Es, G)
+        c.close()
+    for e64, e16 in zip(out[0][0], out[F16][0]):
+        assert abs(e64 - e16) < E0_TOL
+    assert maxrel(out[F16][1], out[0][1]) < 1e-6
