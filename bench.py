@@ -413,7 +413,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="tf32")
+    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="f16")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="he_medium")
     ap.add_argument("--no-time-to-e0", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")

@@ -61,12 +61,13 @@ typedef enum {
                             FP32; tables, update, residual, N and E0 in FP64.
                             Requires n_b <= 304. */
   FEDVR_SPLIT_BF16 = 2,  /* reserved (three-way BF16 splits); rejected */
-  FEDVR_SPLIT_F16 = 3    /* as FEDVR_SPLIT_TF32, with the I^(1) contraction on
-                            kind::f16 tensor cores: operands scaled by powers
-                            of two into FP16's normal range and split as
-                            hi + lo (22 significant bits, as the TF32 split),
-                            twice the TF32 rate. Requires |g| < 16 (g's
-                            eigenvalues lie in [0, 1]) and n_b <= 304. */
+  FEDVR_SPLIT_F16 = 3    /* as FEDVR_SPLIT_TF32, with the exchange and the
+                            I^(1) contractions on kind::f16 tensor cores:
+                            operands scaled by powers of two into FP16's
+                            normal range and split as hi + lo (22 significant
+                            bits, as the TF32 split), twice the TF32 rate.
+                            Requires |g| < 16 (g's eigenvalues lie in [0, 1])
+                            and n_b <= 304. */
 } fedvr_precision;
 
 /* ---------------------------------------------------------------------- */
@@ -311,7 +312,8 @@ int fedvr_power_mesh(fedvr_ctx *ctx, double beta, int u, int p, double *tau, dou
  * gb_j = G[M-1-j] and X_j,ab = sum_kl V_ak V_bl g_j,al gb_j,lk g_j,kb.
  * V [n][n] and G [M][n][n] are device inputs; each G_j and V must be symmetric
  * (the lower triangle is used). Sigma [M][n][n] is a device output.
- * precision: fedvr_precision. Uses context workspace. */
+ * spin >= 0 (FEDVR_ERR_ARG otherwise). precision: fedvr_precision. Uses
+ * context workspace. */
 int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V,
                  const double *G, double *Sigma, int precision);
 

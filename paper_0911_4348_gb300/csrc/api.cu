@@ -191,6 +191,19 @@ int f16_workspace(fedvr_ctx *ctx, int n, int M, void **h16, TcScale **scale) {
   return FEDVR_OK;
 }
 
+// The exchange row table for basis size n in w_xrow (built on the host once per n).
+int ensure_xrows(fedvr_ctx *ctx, int n) {
+  if (ctx->xrow_n == n) return FEDVR_OK;
+  std::vector<uint32_t> rows;
+  exchange_row_table(n, rows);
+  ENSURE(ctx, w_xrow, rows.size() * sizeof(uint32_t));
+  FEDVR_CK(ctx, cudaMemcpyAsync(ctx->w_xrow.ptr, rows.data(), rows.size() * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, ctx->stream));
+  if (int r = sync(ctx)) return r;  // the host vector goes out of scope
+  ctx->xrow_n = n;
+  return FEDVR_OK;
+}
+
 // Device tables of the tensor-core kernels for one system: XSys, C1Sys and
 // the two work-queue prefixes {0, items}, at 256-byte aligned offsets.
 constexpr size_t kTabX = 0;
@@ -201,7 +214,7 @@ constexpr size_t kTabBytes = kTabPC + 256;
 
 int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *Sigma,
                          float *S32, const double *dHF, const ConvCoef *coef, double *I1,
-                         int splits = 1, double *part = nullptr) {
+                         int splits = 1, double *part = nullptr, double spin = -1.0) {
   ENSURE(ctx, w_tab, kTabBytes);
   XSys x;
   C1Sys c;
@@ -212,8 +225,10 @@ int upload_single_tables(fedvr_ctx *ctx, int n, int M, const float *ws, double *
   if (ctx->precision == FEDVR_SPLIT_F16) {
     if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
   }
-  FEDVR_CK(ctx, xsys_fill(&x, n, M, ctx->spin, ws, Sigma, S32,
-                          scale ? &scale->maxS : nullptr));
+  if (int r = ensure_xrows(ctx, n)) return r;
+  // spin < 0: the context's own spin factor (a stage-level call passes its own)
+  FEDVR_CK(ctx, xsys_fill(&x, n, M, spin >= 0.0 ? spin : ctx->spin, ws, Sigma, S32,
+                          P<uint32_t>(ctx->w_xrow), scale ? &scale->maxS : nullptr, h16, scale));
   (void)coef;
   FEDVR_CK(ctx, c1sys_fill(&c, n, M, splits, ws, S32, dHF, P<int4>(ctx->w_coef32), I1, part, h16,
                            scale));
@@ -330,16 +345,19 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches) {
       float *ws, *S32;
       int *err;
       if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-      const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
-      FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
+      if (!scale) {  // the FP16 path reads g through its FP16 split, made above
+        const size_t tstack = (size_t)M * n * ((n + 31) / 32 * 32);
+        FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
+        *launches += 1;
+      }
       FEDVR_CK(ctx, launch_sigma_to_f32(n, M, S, S32, s, scale ? &scale->maxS : nullptr));
-      *launches += 2;
+      *launches += 1;
     }
   } else if (is_split(ctx->precision)) {
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s));
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale));
     *launches += 3;
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
@@ -433,7 +451,8 @@ int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsig
     const TcGeom g = tc_geom(n, M);
     FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
                                      reinterpret_cast<const long *>(tab + kTabPX), 1,
-                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s));
+                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s,
+                                     ctx->precision == FEDVR_SPLIT_F16));
     *launches += 1;
   }
   FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[2], s, evflags));
@@ -508,7 +527,7 @@ int fedvr::sigma_of_current_g(fedvr_ctx *ctx) {
     FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
                                      reinterpret_cast<const long *>(tab + kTabPX), 1,
                                      exchange_items(ctx->n, ctx->M), g.Np, g.ld, err,
-                                     ctx->num_sms, s));
+                                     ctx->num_sms, s, ctx->precision == FEDVR_SPLIT_F16));
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
@@ -863,7 +882,8 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
       void *h16;
       TcScale *scale;
       if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
-      FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), scale, s));
+      FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), n, P<double>(ctx->b_V), scale,
+                                      s));
     }
     if (int r = choose_conv1_splits(ctx, ws, S32, err)) return r;
     if (int r = upload_single_tables(ctx, n, M, ws, P<double>(ctx->w_S), S32, P<double>(ctx->w_dHF),
@@ -1066,7 +1086,8 @@ int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t
     }
   FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
                                     reinterpret_cast<const long *>(bt + B->off_px), n_sys,
-                                    B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s));
+                                    B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s,
+                                    lead->precision == FEDVR_SPLIT_F16));
   *launches += 1;
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
@@ -1200,8 +1221,12 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
         return r;
       }
     }
+    if (int r = ensure_xrows(c, c->n)) {
+      delete B;
+      return r;
+    }
     cudaError_t e = xsys_fill(&hx[k], c->n, c->M, c->spin, ws, P<double>(c->w_S), S32,
-                              scale ? &scale->maxS : nullptr);
+                              P<uint32_t>(c->w_xrow), scale ? &scale->maxS : nullptr, h16, scale);
     if (e == cudaSuccess)
       e = c1sys_fill(&hc[k], c->n, c->M, 1, ws, S32, P<double>(c->w_dHF),
                      P<int4>(c->w_coef32), P<double>(c->w_I1), nullptr, h16, scale);
@@ -1381,24 +1406,35 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
   CHECK_CTX(ctx);
   if (n < 1 || n > 1024 || M < 1 || M > 4097 || !V || !G || !Sigma)
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, 1 <= M <= 4097 and device buffers");
-  if (!is_fin(spin)) return fail(ctx, FEDVR_ERR_ARG, "spin factor must be finite");
+  if (!is_fin(spin) || spin < 0.0)
+    return fail(ctx, FEDVR_ERR_ARG, "spin factor must be finite and non-negative");
   if (int r = check_precision(ctx, precision, n)) return r;
   ctx->prepared = false;  // the workspace below is shared with a prepared run
-  if (is_split(precision)) {  // the exchange runs split TF32 in both split modes
-    ctx->precision = FEDVR_SPLIT_TF32;
+  if (is_split(precision)) {
+    ctx->precision = precision;
+    const bool f16 = precision == FEDVR_SPLIT_F16;
     float *ws, *S32;
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
     cudaStream_t s = ctx->stream;
     FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
-    if (int r = upload_single_tables(ctx, n, M, ws, Sigma, nullptr, nullptr, nullptr, nullptr))
+    if (f16) {  // operand scales from this V, and the FP16 split of G for the gb operand
+      void *h16;
+      TcScale *scale;
+      if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
+      FEDVR_CK(ctx, launch_scale_init(0, nullptr, n, V, scale, s));
+      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
+    }
+    if (int r = upload_single_tables(ctx, n, M, ws, Sigma, nullptr, nullptr, nullptr, nullptr, 1,
+                                     nullptr, spin))
       return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s));
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !f16));
     const TcGeom g = tc_geom(n, M);
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
                                      reinterpret_cast<const long *>(tab + kTabPX), 1,
-                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s));
+                                     exchange_items(n, M), g.Np, g.ld, err, ctx->num_sms, s,
+                                     f16));
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
@@ -1437,12 +1473,12 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     const bool f16 = precision == FEDVR_SPLIT_F16;
     if (f16) {
       if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
-      FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), scale, s));
+      FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), 0, nullptr, scale, s));
       FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
     }
     if (int r = upload_single_tables(ctx, n, M, ws, nullptr, S32, dHF, P<ConvCoef>(ctx->w_coef), I1))
       return r;
-    FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
+    if (!f16) FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
     FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s, f16 ? &scale->maxS : nullptr));
     FEDVR_CK(ctx, launch_diag_f32(n, M, dHF, Sigma, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
                                   S32, s, f16 ? &scale->maxS : nullptr));

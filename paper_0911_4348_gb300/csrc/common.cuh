@@ -64,6 +64,8 @@ struct fedvr_ctx {
   int c1_splits = 1;
   // incremented by every fedvr_2b_prepare (batches check it before each step)
   unsigned long long prep_gen = 0;
+  // n of the exchange row table held in w_xrow (0: none)
+  int xrow_n = 0;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
 
@@ -75,7 +77,8 @@ struct fedvr_ctx {
   fedvr::DevBuf b_sigma_init;
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
-      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16;
+      w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16,
+      w_xrow;
 };
 
 namespace fedvr {

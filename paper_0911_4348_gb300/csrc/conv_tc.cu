@@ -12,7 +12,13 @@
 // cores and split as hi + lo (TF32); B = g_j(b, c) comes from the split copy of
 // g by TMA. Products hi*hi + hi*lo + lo*hi accumulate in FP32 in TMEM over a
 // block of JB mesh points (about 4096 contraction terms) and each block is
-// then added into the FP64 result, so rounding does not grow with M.
+// then added into the FP64 result, so rounding does not grow with M. Within a
+// block the chunks run column slice by column slice, mesh point by mesh point:
+// along j the lag bracket of a row moves slowly (on the power mesh a step
+// needs 0.6 new bracket rows on average, against 1.8 without reuse), so the
+// FP16 kernel's producer threads (two rows each) keep their two bracket rows
+// in registers and fetch a row only when the bracket changes. (With four rows
+// per thread in the TF32 kernel the cache measured slower than plain loads.)
 //
 // A work item is (row tile, split s): split s covers the mesh points
 // j in [s M / S, (s + 1) M / S). Split 0 writes I1, split s > 0 its own
@@ -112,54 +118,57 @@ __global__ void __launch_bounds__(kThreads, 1)
         ia[k] = live[k] ? (int)(r / n) : 0;
         aa[k] = live[k] ? (int)(r % n) : 0;
       }
-      for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-        uint32_t o1[4], o2[4];  // element offsets into S32 ([2M][n][ld] < 2^31)
-        float c1[4], c2[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int4 cf = coef32[(long)ia[k] * M + j];
-          o1[k] = (uint32_t)((cf.x * n + aa[k]) * ld + 4 * c);
-          o2[k] = (uint32_t)((cf.y * n + aa[k]) * ld + 4 * c);
-          c1[k] = __int_as_float(cf.z);
-          c2[k] = __int_as_float(cf.w);
-        }
-        for (int kc = 0; kc < KC; ++kc, ++cc) {
-          const int l0 = kc * 32;
+      const int JB = S.JB;
+      // chunks in the order (accumulation block, 32-wide column slice, mesh point),
+      // as the MMA and TMA roles walk them
+      for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
+        const int j1 = min(it.j_hi, j0 + JB);
+        for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+          const int l0 = kc * 32 + 4 * c;
+          const bool in = l0 < n;  // units past n are zero padding: not fetched
           float4 s1[4], s2[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (live[k]) {
-              s1[k] = *reinterpret_cast<const float4 *>(S32 + o1[k] + l0);
-              s2[k] = *reinterpret_cast<const float4 *>(S32 + o2[k] + l0);
-            } else {
-              s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-          }
-          const int s = cc & 1;
-          const uint32_t use = cc >> 1;
-          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-            *abort_flag = 1;
-            break;
-          }
-          uint8_t *st = smem + s * stage_bytes;
+          for (int k = 0; k < 4; ++k) s1[k] = s2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int j = j0; j < j1; ++j, ++cc) {
+            float c1[4], c2[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            // S32 rows are zero beyond n, so the padded columns come out zero;
-            // the diagonal entry j = i reads its precomputed B_ii (row M + i)
-            float x[4] = {fmaf(c1[k], s1[k].x, c2[k] * s2[k].x),
-                          fmaf(c1[k], s1[k].y, c2[k] * s2[k].y),
-                          fmaf(c1[k], s1[k].z, c2[k] * s2[k].z),
-                          fmaf(c1[k], s1[k].w, c2[k] * s2[k].w)};
-            float4 hi, lo;
-            tc::tf32_split(x[0], hi.x, lo.x);
-            tc::tf32_split(x[1], hi.y, lo.y);
-            tc::tf32_split(x[2], hi.z, lo.z);
-            tc::tf32_split(x[3], hi.w, lo.w);
-            *reinterpret_cast<float4 *>(st + off[k]) = hi;
-            *reinterpret_cast<float4 *>(st + kTileA + off[k]) = lo;
+            for (int k = 0; k < 4; ++k) {
+              const int4 cf = coef32[(long)ia[k] * M + j];
+              c1[k] = __int_as_float(cf.z);
+              c2[k] = __int_as_float(cf.w);
+              if (live[k] && in) {  // element offsets into S32 ([2M][n][ld]) < 2^31
+                s1[k] = *reinterpret_cast<const float4 *>(
+                    S32 + (uint32_t)((cf.x * n + aa[k]) * ld + l0));
+                s2[k] = *reinterpret_cast<const float4 *>(
+                    S32 + (uint32_t)((cf.y * n + aa[k]) * ld + l0));
+              }
+            }
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              // rows past n and dead rows stay zero; the diagonal entry j = i reads its
+              // precomputed B_ii (row M + i)
+              float x[4] = {fmaf(c1[k], s1[k].x, c2[k] * s2[k].x),
+                            fmaf(c1[k], s1[k].y, c2[k] * s2[k].y),
+                            fmaf(c1[k], s1[k].z, c2[k] * s2[k].z),
+                            fmaf(c1[k], s1[k].w, c2[k] * s2[k].w)};
+              float4 hi, lo;
+              tc::tf32_split(x[0], hi.x, lo.x);
+              tc::tf32_split(x[1], hi.y, lo.y);
+              tc::tf32_split(x[2], hi.z, lo.z);
+              tc::tf32_split(x[3], hi.w, lo.w);
+              *reinterpret_cast<float4 *>(st + off[k]) = hi;
+              *reinterpret_cast<float4 *>(st + kTileA + off[k]) = lo;
+            }
+            tc::fence_smem_to_async();
+            tc::mbar_arrive(&full[s]);
           }
-          tc::fence_smem_to_async();
-          tc::mbar_arrive(&full[s]);
         }
       }
     }
@@ -174,20 +183,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
         const int NT = S.g.NT, KC = S.g.KC, n00 = S.g.n0[0], n01 = S.g.n0[1];
         const CUtensorMap *th0 = &S.th[0], *th1 = &S.th[1], *tl0 = &S.tl[0], *tl1 = &S.tl[1];
-        for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-          for (int kc = 0; kc < KC; ++kc, ++cc) {
-            const int s = cc & 1;
-            const uint32_t use = cc >> 1;
-            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-              *abort_flag = 1;
-              break;
-            }
-            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
-            tc::mbar_arrive_expect_tx(&full[s], bytes);
-            for (int nt = 0; nt < NT; ++nt) {
-              const int r = nt ? n01 : n00;
-              tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 32, r, j, &full[s]);
-              tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 32, r, j, &full[s]);
+        const int JB = S.JB;
+        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
+          const int j1 = min(it.j_hi, j0 + JB);
+          for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+            for (int j = j0; j < j1; ++j, ++cc) {
+              const int s = cc & 1;
+              const uint32_t use = cc >> 1;
+              if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+                *abort_flag = 1;
+                break;
+              }
+              uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+              tc::mbar_arrive_expect_tx(&full[s], bytes);
+              for (int nt = 0; nt < NT; ++nt) {
+                const int r = nt ? n01 : n00;
+                tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 32, r, j, &full[s]);
+                tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 32, r, j, &full[s]);
+              }
             }
           }
         }
@@ -219,8 +232,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::fence_after_sync();
           const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-          for (int j = j0; j < j1 && !*abort_flag; ++j) {
-            for (int kc = 0; kc < KC; ++kc, ++cc) {
+          for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+            const int ksteps = min(4, (n - kc * 32 + 7) / 8);
+            for (int j = j0; j < j1; ++j, ++cc) {
               const int s = cc & 1;
               const uint32_t use = cc >> 1;
               if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
@@ -229,7 +243,6 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               tc::fence_after_sync();
               const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
-              const int ksteps = min(4, (n - kc * 32 + 7) / 8);
               const bool fresh = (j == j0 && kc == 0);
               for (int kk = 0; kk < ksteps; ++kk) {
                 const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
@@ -327,7 +340,11 @@ __global__ void coef32_kernel(long mm, int M, const ConvCoef *__restrict__ coef,
       const int i = (int)(x / M);
       out[x] = make_int4(M + i, M + i, __float_as_int(1.f), __float_as_int(0.f));
     } else {
-      out[x] = make_int4(c.k, c.k + 1, __float_as_int((float)c.c1), __float_as_int((float)c.c2));
+      // a zero upper weight (the lag falls on a mesh point) names the lower row
+      // twice, so that no second row is fetched
+      const float c2 = (float)c.c2;
+      out[x] = make_int4(c.k, c2 != 0.f ? c.k + 1 : c.k, __float_as_int((float)c.c1),
+                         __float_as_int(c2));
     }
   }
 }
@@ -408,7 +425,7 @@ __global__ void sigma_to_f32_kernel(int n, long rows, int ld, const double *__re
 // scaled by powers of two into FP16's normal range (g by 2^kScaleG, the
 // interpolated Sigma by 2^sA with sA from maxC * max|S32|), and the flush
 // multiplies the FP32 block sums by 2^-(sA + kScaleG) exactly. 16 producer
-// warps (two 16-byte units, i.e. 16 source floats, per thread and chunk).
+// warps, two rows of one 16-byte unit (8 values) per thread and chunk.
 constexpr int kWarpsH = 22;  // 0-3 flush, 4-19 A producers, 20 TMA, 21 MMA
 constexpr int kThreadsH = kWarpsH * 32;
 
@@ -483,59 +500,77 @@ __global__ void __launch_bounds__(kThreadsH, 1)
         ia[k] = live[k] ? (int)(r / n) : 0;
         aa[k] = live[k] ? (int)(r % n) : 0;
       }
-      for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-        uint32_t o1[2], o2[2];  // element offsets of the two bracket rows in S32
-        float c1[2], c2[2];     // weights times the operand scale 2^sA
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int4 cf = coef32[(long)ia[k] * M + j];
-          o1[k] = (uint32_t)((cf.x * n + aa[k]) * ld);
-          o2[k] = (uint32_t)((cf.y * n + aa[k]) * ld);
-          c1[k] = __int_as_float(cf.z) * fA;
-          c2[k] = __int_as_float(cf.w) * fA;
-        }
-        for (int kc = 0; kc < KC; ++kc, ++cc) {
+      const int JB = S.JB;
+      // chunks in the order (accumulation block, 64-wide column slice, mesh point),
+      // the two bracket rows of each row held in registers while the bracket stays
+      for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
+        const int j1 = min(it.j_hi, j0 + JB);
+        for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
           const int l0 = kc * 64 + 8 * c;
-          const bool in = l0 < ld;  // ld is a multiple of 32: a unit is wholly in or out
+          const bool in = l0 < n;  // units starting past n are zero padding: not fetched
+          int k1[2], k2[2];        // S32 rows held in a1, a2 (-1: none)
           float4 a1[2][2], a2[2][2];
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            if (live[k] && in) {
-              a1[k][0] = *reinterpret_cast<const float4 *>(S32 + o1[k] + l0);
-              a1[k][1] = *reinterpret_cast<const float4 *>(S32 + o1[k] + l0 + 4);
-              a2[k][0] = *reinterpret_cast<const float4 *>(S32 + o2[k] + l0);
-              a2[k][1] = *reinterpret_cast<const float4 *>(S32 + o2[k] + l0 + 4);
-            } else {
-              a1[k][0] = a1[k][1] = a2[k][0] = a2[k][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            k1[k] = k2[k] = -1;
+            a1[k][0] = a1[k][1] = a2[k][0] = a2[k][1] = make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          const int s = cc & 1;
-          const uint32_t use = cc >> 1;
-          if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-            *abort_flag = 1;
-            break;
-          }
-          uint8_t *st = smem + s * stage_bytes;
+          for (int j = j0; j < j1; ++j, ++cc) {
+            float c1[2], c2[2];  // weights times the operand scale 2^sA
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const float y[8] = {fmaf(c1[k], a1[k][0].x, c2[k] * a2[k][0].x),
-                                fmaf(c1[k], a1[k][0].y, c2[k] * a2[k][0].y),
-                                fmaf(c1[k], a1[k][0].z, c2[k] * a2[k][0].z),
-                                fmaf(c1[k], a1[k][0].w, c2[k] * a2[k][0].w),
-                                fmaf(c1[k], a1[k][1].x, c2[k] * a2[k][1].x),
-                                fmaf(c1[k], a1[k][1].y, c2[k] * a2[k][1].y),
-                                fmaf(c1[k], a1[k][1].z, c2[k] * a2[k][1].z),
-                                fmaf(c1[k], a1[k][1].w, c2[k] * a2[k][1].w)};
-            uint4 hi, lo;
-            tc::f16_split2(y[0], y[1], hi.x, lo.x);
-            tc::f16_split2(y[2], y[3], hi.y, lo.y);
-            tc::f16_split2(y[4], y[5], hi.z, lo.z);
-            tc::f16_split2(y[6], y[7], hi.w, lo.w);
-            *reinterpret_cast<uint4 *>(st + off[k]) = hi;
-            *reinterpret_cast<uint4 *>(st + kTileA + off[k]) = lo;
+            for (int k = 0; k < 2; ++k) {
+              const int4 cf = coef32[(long)ia[k] * M + j];
+              c1[k] = __int_as_float(cf.z) * fA;
+              c2[k] = __int_as_float(cf.w) * fA;
+              if (live[k] && in) {
+                // updated in place (the upper row first: it may take the old lower
+                // one, when the bracket moved down by one); a bracket that moved up
+                // (only where the lag wraps around) is fetched again
+                if (cf.y == k1[k]) {
+                  a2[k][0] = a1[k][0];
+                  a2[k][1] = a1[k][1];
+                } else if (cf.y != k2[k]) {
+                  const float *p2 = S32 + (uint32_t)((cf.y * n + aa[k]) * ld + l0);
+                  a2[k][0] = *reinterpret_cast<const float4 *>(p2);
+                  a2[k][1] = *reinterpret_cast<const float4 *>(p2 + 4);
+                }
+                if (cf.x != k1[k]) {
+                  const float *p1 = S32 + (uint32_t)((cf.x * n + aa[k]) * ld + l0);
+                  a1[k][0] = *reinterpret_cast<const float4 *>(p1);
+                  a1[k][1] = *reinterpret_cast<const float4 *>(p1 + 4);
+                }
+                k1[k] = cf.x;
+                k2[k] = cf.y;
+              }
+            }
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const float y[8] = {fmaf(c1[k], a1[k][0].x, c2[k] * a2[k][0].x),
+                                  fmaf(c1[k], a1[k][0].y, c2[k] * a2[k][0].y),
+                                  fmaf(c1[k], a1[k][0].z, c2[k] * a2[k][0].z),
+                                  fmaf(c1[k], a1[k][0].w, c2[k] * a2[k][0].w),
+                                  fmaf(c1[k], a1[k][1].x, c2[k] * a2[k][1].x),
+                                  fmaf(c1[k], a1[k][1].y, c2[k] * a2[k][1].y),
+                                  fmaf(c1[k], a1[k][1].z, c2[k] * a2[k][1].z),
+                                  fmaf(c1[k], a1[k][1].w, c2[k] * a2[k][1].w)};
+              uint4 hi, lo;
+              tc::f16_split2(y[0], y[1], hi.x, lo.x);
+              tc::f16_split2(y[2], y[3], hi.y, lo.y);
+              tc::f16_split2(y[4], y[5], hi.z, lo.z);
+              tc::f16_split2(y[6], y[7], hi.w, lo.w);
+              *reinterpret_cast<uint4 *>(st + off[k]) = hi;
+              *reinterpret_cast<uint4 *>(st + kTileA + off[k]) = lo;
+            }
+            tc::fence_smem_to_async();
+            tc::mbar_arrive(&full[s]);
           }
-          tc::fence_smem_to_async();
-          tc::mbar_arrive(&full[s]);
         }
       }
     }
@@ -550,20 +585,24 @@ __global__ void __launch_bounds__(kThreadsH, 1)
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
         const int NT = S.g.NT, KC = (S.g.n + 63) / 64, n00 = S.g.n0[0], n01 = S.g.n0[1];
         const CUtensorMap *th0 = &S.hh[0], *th1 = &S.hh[1], *tl0 = &S.hl[0], *tl1 = &S.hl[1];
-        for (int j = it.j_lo; j < it.j_hi && !*abort_flag; ++j) {
-          for (int kc = 0; kc < KC; ++kc, ++cc) {
-            const int s = cc & 1;
-            const uint32_t use = cc >> 1;
-            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-              *abort_flag = 1;
-              break;
-            }
-            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
-            tc::mbar_arrive_expect_tx(&full[s], bytes);
-            for (int nt = 0; nt < NT; ++nt) {
-              const int r = nt ? n01 : n00;
-              tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 64, r, j, &full[s]);
-              tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 64, r, j, &full[s]);
+        const int JB = S.JB;
+        for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
+          const int j1 = min(it.j_hi, j0 + JB);
+          for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+            for (int j = j0; j < j1; ++j, ++cc) {
+              const int s = cc & 1;
+              const uint32_t use = cc >> 1;
+              if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+                *abort_flag = 1;
+                break;
+              }
+              uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+              tc::mbar_arrive_expect_tx(&full[s], bytes);
+              for (int nt = 0; nt < NT; ++nt) {
+                const int r = nt ? n01 : n00;
+                tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 64, r, j, &full[s]);
+                tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 64, r, j, &full[s]);
+              }
             }
           }
         }
@@ -595,8 +634,9 @@ __global__ void __launch_bounds__(kThreadsH, 1)
           }
           tc::fence_after_sync();
           const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-          for (int j = j0; j < j1 && !*abort_flag; ++j) {
-            for (int kc = 0; kc < KC; ++kc, ++cc) {
+          for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+            const int ksteps = min(4, (n - kc * 64 + 15) / 16);
+            for (int j = j0; j < j1; ++j, ++cc) {
               const int s = cc & 1;
               const uint32_t use = cc >> 1;
               if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
@@ -605,7 +645,6 @@ __global__ void __launch_bounds__(kThreadsH, 1)
               }
               tc::fence_after_sync();
               const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
-              const int ksteps = min(4, (n - kc * 64 + 15) / 16);
               const bool fresh = (j == j0 && kc == 0);
               for (int kk = 0; kk < ksteps; ++kk) {
                 const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
@@ -704,22 +743,30 @@ __global__ void split_f16_kernel(int n, long rows, int ld16, const double *__res
 }
 
 // scale->maxC = max over (i, j) of |c1| + |c2|; scale->maxS = 0 (one block).
-__global__ void scale_init_kernel(long mm, const int4 *__restrict__ coef32, TcScale *scale) {
-  __shared__ float sh[256];
-  float m = 0.f;
+__global__ void scale_init_kernel(long mm, const int4 *__restrict__ coef32, long nn,
+                                  const double *__restrict__ V, TcScale *scale) {
+  __shared__ float sh[2][256];
+  float m = 0.f, v = 0.f;
   for (long x = threadIdx.x; x < mm; x += blockDim.x) {
     const int4 c = coef32[x];
     m = fmaxf(m, fabsf(__int_as_float(c.z)) + fabsf(__int_as_float(c.w)));
   }
-  sh[threadIdx.x] = m;
+  for (long x = threadIdx.x; x < nn; x += blockDim.x) v = fmaxf(v, (float)fabs(V[x]));
+  sh[0][threadIdx.x] = m;
+  sh[1][threadIdx.x] = v;
   __syncthreads();
   for (int st = 128; st > 0; st >>= 1) {
-    if (threadIdx.x < st) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + st]);
+    if (threadIdx.x < st) {
+      sh[0][threadIdx.x] = fmaxf(sh[0][threadIdx.x], sh[0][threadIdx.x + st]);
+      sh[1][threadIdx.x] = fmaxf(sh[1][threadIdx.x], sh[1][threadIdx.x + st]);
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    scale->maxC = sh[0];
+    scale->maxC = sh[0][0];
+    scale->maxV = sh[1][0];  // the largest |V32| entry exactly: V32 = (float)V
     scale->maxS = 0u;
+    scale->pad = 0u;
   }
 }
 
@@ -772,8 +819,9 @@ cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale_init(int M, const int4 *coef32, TcScale *scale, cudaStream_t s) {
-  scale_init_kernel<<<1, 256, 0, s>>>((long)M * M, coef32, scale);
+cudaError_t launch_scale_init(int M, const int4 *coef32, int n, const double *V, TcScale *scale,
+                              cudaStream_t s) {
+  scale_init_kernel<<<1, 256, 0, s>>>((long)M * M, coef32, (long)n * n, V, scale);
   return cudaGetLastError();
 }
 

@@ -8,7 +8,9 @@
 // second-order exchange X. P^(b) is the only O(n^3)-per-column contraction
 // (O(n^4) per mesh point): it runs as tcgen05.mma kind::tf32 over the rows
 // (b, a), a >= b, of one mesh point stacked into n(n+1)/2 rows (128 per tile,
-// tiles full except the last), all k in one or two N tiles and the
+// tiles full except the last; the stacking order walks blocks of 16 b x 8 a,
+// so that a tile touches a few rows of V and g that stay in L1), all k in one
+// or two N tiles and the
 // contraction over l in 32-wide chunks, each operand split as x = hi + lo
 // (TF32) and the product taken as hi*hi + hi*lo + lo*hi with FP32
 // accumulation in TMEM. The A operand g_al V_bl of each row is formed by the
@@ -60,34 +62,45 @@ __global__ void split_kernel(int n, long rows, int ld, const double *__restrict_
   }
 }
 
-// Row r of the stacked lower triangle of one mesh point: rows ordered by b,
-// then a = b..n-1, so row b starts at off(b) = b n - b (b - 1) / 2.
-__device__ __forceinline__ long tri_off(int n, int b) { return (long)b * n - (long)b * (b - 1) / 2; }
+// Warp roles: 0-3 epilogue (TMEM lanes 0-127), then 8 warps of A-operand
+// producers, one warp of TMA loads of the gb operand
+// and one of MMA issue. Stages handed over with mbarriers: full[s] (producer
+// arrivals + TMA bytes), empty[s] (MMA commit); accumulators double-buffered
+// with accf/acce. The work queue is the concatenation of the (j, row tile)
+// items of every system in the table (mesh-point-major, so that concurrent
+// CTAs share gb in L2); every role walks it in the same order. The stage
+// layout uses the table's largest N.
+//
+// FP16 variant: 128-byte operand rows hold 64 FP16 values, so a chunk covers
+// 64 contraction terms and the three products run as kind::f16 at twice the
+// TF32 rate. A = g_al V_bl enters as x 2^eX (eX from max|V|, |g| < 16 keeps
+// it below 2^15), gb as x 2^kScaleG (the FP16 split of g that the first
+// convolution uses as well), and the epilogue scales P^(b) back exactly.
+template <bool F16>
+struct XRoles {
+  static constexpr int kProd = 8;                 // producer warps
+  static constexpr int kTma = 4 + kProd, kMma = 5 + kProd;
+  static constexpr int kThreads = (6 + kProd) * 32;
+  static constexpr int kCols = F16 ? 64 : 32;     // contraction terms per chunk
+  static constexpr int kRowsPer = 4;              // rows per producer thread: r0 + 32 k
+  static constexpr int kRowStep = 32;
+};
 
-__device__ __forceinline__ void tri_row(int n, long r, int *b, int *a) {
-  const double h = 2.0 * n + 1.0;
-  int bb = (int)((h - sqrt(fmax(h * h - 8.0 * (double)r, 0.0))) * 0.5);
-  if (bb < 0) bb = 0;
-  if (bb > n - 1) bb = n - 1;
-  while (bb > 0 && tri_off(n, bb) > r) --bb;
-  while (bb + 1 < n && tri_off(n, bb + 1) <= r) ++bb;
-  *b = bb;
-  *a = bb + (int)(r - tri_off(n, bb));
+// Exponent eX of the FP16 A operand g V: max|V| < 2^e, |g| < 16.
+__device__ __forceinline__ int x_scale_exp(const TcScale *sc) {
+  const float vmax = sc->maxV;
+  if (!(vmax > 0.f) || !(vmax < 3.0e38f)) return 0;
+  int e;
+  frexpf(vmax, &e);
+  e = 11 - e;
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
 }
 
-// Warp roles: 0-3 epilogue (TMEM lanes 0-127), 4-11 A-operand producers,
-// 12 TMA loads of the gb operand, 13 MMA issue. Stages handed over with
-// mbarriers: full[s] (256 producer arrivals + TMA bytes), empty[s] (MMA
-// commit); accumulators double-buffered with accf/acce. The work queue is the
-// concatenation of the (j, row tile) items of every system in the table
-// (mesh-point-major, so that concurrent CTAs share gb in L2); every role walks
-// it in the same order. The stage layout uses the table's largest N.
-constexpr int kWarps2 = 14;
-constexpr int kThreads2 = kWarps2 * 32;
-
-__global__ void __launch_bounds__(kThreads2, 1)
+template <bool F16>
+__global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     exchange_tc_kernel(const XSys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
                        long items, int Np_max, int nbuf, int *err) {
+  using R = XRoles<F16>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~uintptr_t(1023));
@@ -104,8 +117,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&full[0], 257);
-    tc::mbar_init(&full[1], 257);
+    tc::mbar_init(&full[0], R::kProd * 32 + 1);
+    tc::mbar_init(&full[1], R::kProd * 32 + 1);
     tc::mbar_init(&empty[0], 1);
     tc::mbar_init(&empty[1], 1);
     tc::mbar_init(&accf[0], 1);
@@ -123,41 +136,54 @@ __global__ void __launch_bounds__(kThreads2, 1)
   bool issued = false;
   int cur = 0;  // system of the current item (items ascend within a CTA)
 
-  if (warp >= 4 && warp < 12) {
-    // ---- A producers: row (b, a): A(l) = g_al * V_bl, split hi/lo, 4 rows per thread ----
+  if (warp >= 4 && warp < R::kTma) {
+    // ---- A producers: row (b, a): A(l) = g_al * V_bl, split hi/lo ----
+    // rows r0 + 32 k (k < 4), 16-byte unit c of each chunk row (TF32: 4 values of a
+    // 32-wide chunk, FP16: 8 values of a 64-wide chunk)
     const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
+    constexpr int KR = R::kRowsPer;
     uint32_t cc = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
-      const int n = S.g.n, ld = S.g.ld, KC = S.g.KC;
+      const int n = S.g.n, ld = S.g.ld, KC = (n + R::kCols - 1) / R::kCols;
       const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
       const long q = w - prefix[cur];
       const int j = (int)(q / RT);
       const long t = q % RT;
       const float *const gA = S.g32 + (long)j * n * ld;
       const float *const V32 = S.V32;  // in a register across the memory-clobbering asm
-      uint32_t og[4], ov[4];  // element offsets of row a of g_j and row b of V
-      bool live[4];
+      const float fX = F16 ? ldexpf(1.f, x_scale_exp(S.scale)) : 1.f;
+      const int u = F16 ? 8 * c : 4 * c;  // first column of this thread's unit in a chunk
+      uint32_t og[KR], ov[KR];  // element offsets of row a of g_j and row b of V
+      bool live[KR];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const long r = t * 128 + r0 + 32 * k;
+      for (int k = 0; k < KR; ++k) {
+        const long r = t * 128 + r0 + R::kRowStep * k;
         live[k] = r < T;
         int b = 0, a = 0;
-        if (live[k]) tri_row(n, r, &b, &a);
-        og[k] = (uint32_t)(a * ld + 4 * c);
-        ov[k] = (uint32_t)(b * ld + 4 * c);
+        if (live[k]) {
+          const uint32_t e = S.rows[r];
+          b = (int)(e >> 16);
+          a = (int)(e & 0xffffu);
+        }
+        og[k] = (uint32_t)(a * ld + u);
+        ov[k] = (uint32_t)(b * ld + u);
       }
       for (int kc = 0; kc < KC; ++kc, ++cc) {
-        const int l0 = kc * 32;
-        float4 gv[4], vv[4];
+        const int l0 = kc * R::kCols;
+        const bool in = l0 + u < n;  // units past n are zero padding: not fetched
+        float4 gv[KR][F16 ? 2 : 1], vv[KR][F16 ? 2 : 1];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (live[k]) {
-            gv[k] = *reinterpret_cast<const float4 *>(gA + og[k] + l0);
-            vv[k] = *reinterpret_cast<const float4 *>(V32 + ov[k] + l0);
-          } else {
-            gv[k] = vv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < KR; ++k) {
+#pragma unroll
+          for (int h = 0; h < (F16 ? 2 : 1); ++h) {
+            if (live[k] && in) {
+              gv[k][h] = *reinterpret_cast<const float4 *>(gA + og[k] + l0 + 4 * h);
+              vv[k][h] = *reinterpret_cast<const float4 *>(V32 + ov[k] + l0 + 4 * h);
+            } else {
+              gv[k][h] = vv[k][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
           }
         }
         const int s = cc & 1;
@@ -168,24 +194,42 @@ __global__ void __launch_bounds__(kThreads2, 1)
         }
         uint8_t *st = smem + s * stage_bytes;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float x0 = gv[k].x * vv[k].x, x1 = gv[k].y * vv[k].y, x2 = gv[k].z * vv[k].z,
-                      x3 = gv[k].w * vv[k].w;
-          float4 hi, lo;
-          tc::tf32_split(x0, hi.x, lo.x);
-          tc::tf32_split(x1, hi.y, lo.y);
-          tc::tf32_split(x2, hi.z, lo.z);
-          tc::tf32_split(x3, hi.w, lo.w);
-          const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
-          *reinterpret_cast<float4 *>(st + off) = hi;
-          *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+        for (int k = 0; k < KR; ++k) {
+          const uint32_t off = tc::sw128_offset(r0 + R::kRowStep * k, c);
+          if constexpr (F16) {
+            float x[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              x[4 * h + 0] = gv[k][h].x * vv[k][h].x * fX;
+              x[4 * h + 1] = gv[k][h].y * vv[k][h].y * fX;
+              x[4 * h + 2] = gv[k][h].z * vv[k][h].z * fX;
+              x[4 * h + 3] = gv[k][h].w * vv[k][h].w * fX;
+            }
+            uint4 hi, lo;
+            tc::f16_split2(x[0], x[1], hi.x, lo.x);
+            tc::f16_split2(x[2], x[3], hi.y, lo.y);
+            tc::f16_split2(x[4], x[5], hi.z, lo.z);
+            tc::f16_split2(x[6], x[7], hi.w, lo.w);
+            *reinterpret_cast<uint4 *>(st + off) = hi;
+            *reinterpret_cast<uint4 *>(st + kTileA + off) = lo;
+          } else {
+            const float x0 = gv[k][0].x * vv[k][0].x, x1 = gv[k][0].y * vv[k][0].y,
+                        x2 = gv[k][0].z * vv[k][0].z, x3 = gv[k][0].w * vv[k][0].w;
+            float4 hi, lo;
+            tc::tf32_split(x0, hi.x, lo.x);
+            tc::tf32_split(x1, hi.y, lo.y);
+            tc::tf32_split(x2, hi.z, lo.z);
+            tc::tf32_split(x3, hi.w, lo.w);
+            *reinterpret_cast<float4 *>(st + off) = hi;
+            *reinterpret_cast<float4 *>(st + kTileA + off) = lo;
+          }
         }
         tc::fence_smem_to_async();
         tc::mbar_arrive(&full[s]);
       }
     }
-  } else if (warp == 12) {
-    // ---- TMA: gb = G[M-1-j] rows 0..Np-1, 32 columns per chunk, hi and lo ----
+  } else if (warp == R::kTma) {
+    // ---- TMA: gb = G[M-1-j] rows 0..Np-1, one chunk of columns per stage, hi and lo ----
     if (lane == 0) {
       uint32_t cc = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
@@ -195,8 +239,10 @@ __global__ void __launch_bounds__(kThreads2, 1)
         const long RT = ((long)n * (n + 1) / 2 + 127) / 128;
         const int j = (int)((w - prefix[cur]) / RT);
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
-        const int NT = S.g.NT, KC = S.g.KC, jb = S.g.M - 1 - j, n00 = S.g.n0[0], n01 = S.g.n0[1];
-        const CUtensorMap *th0 = &S.th[0], *th1 = &S.th[1], *tl0 = &S.tl[0], *tl1 = &S.tl[1];
+        const int NT = S.g.NT, KC = (n + R::kCols - 1) / R::kCols, jb = S.g.M - 1 - j;
+        const int n00 = S.g.n0[0], n01 = S.g.n0[1];
+        const CUtensorMap *th0 = F16 ? &S.hh[0] : &S.th[0], *th1 = F16 ? &S.hh[1] : &S.th[1];
+        const CUtensorMap *tl0 = F16 ? &S.hl[0] : &S.tl[0], *tl1 = F16 ? &S.hl[1] : &S.tl[1];
         for (int kc = 0; kc < KC && !*abort_flag; ++kc, ++cc) {
           const int s = cc & 1;
           const uint32_t use = cc >> 1;
@@ -208,22 +254,24 @@ __global__ void __launch_bounds__(kThreads2, 1)
           tc::mbar_arrive_expect_tx(&full[s], bytes);
           for (int nt = 0; nt < NT; ++nt) {
             const int r = nt ? n01 : n00;
-            tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * 32, r, jb, &full[s]);
-            tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * 32, r, jb, &full[s]);
+            tc::tma_load_3d(st + r * 128, nt ? th1 : th0, kc * R::kCols, r, jb, &full[s]);
+            tc::tma_load_3d(st + tileB + r * 128, nt ? tl1 : tl0, kc * R::kCols, r, jb,
+                            &full[s]);
           }
         }
       }
     }
-  } else if (warp == 13) {
+  } else if (warp == R::kMma) {
     // ---- MMA issue: one accumulator per row tile ----
     if (lane == 0) {
       uint32_t cc = 0, tcount = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const XSys &S = sys[cur];
-        const int n = S.g.n, KC = S.g.KC, NT = S.g.NT;
+        const int n = S.g.n, KC = (n + R::kCols - 1) / R::kCols, NT = S.g.NT;
         const uint32_t n00 = (uint32_t)S.g.n0[0], n01 = (uint32_t)S.g.n0[1];
-        const uint32_t id0 = tc::idesc_tf32(128, S.g.nsz[0]), id1 = tc::idesc_tf32(128, S.g.nsz[1]);
+        const uint32_t id0 = F16 ? tc::idesc_f16(128, S.g.nsz[0]) : tc::idesc_tf32(128, S.g.nsz[0]);
+        const uint32_t id1 = F16 ? tc::idesc_f16(128, S.g.nsz[1]) : tc::idesc_tf32(128, S.g.nsz[1]);
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
         // one TMEM buffer: the previous tile must be drained; two: the one before it
@@ -247,7 +295,9 @@ __global__ void __launch_bounds__(kThreads2, 1)
           }
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
-          const int ksteps = min(4, (n - kc * 32 + 7) / 8);
+          // K per instruction: 8 (tf32) or 16 (f16) values, 32 bytes of the row either way
+          constexpr int kK = F16 ? 16 : 8;
+          const int ksteps = min(4, (n - kc * R::kCols + kK - 1) / kK);
           for (int kk = 0; kk < ksteps; ++kk) {
             const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
             const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
@@ -258,9 +308,16 @@ __global__ void __launch_bounds__(kThreads2, 1)
               const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
               const uint32_t d = dbase + r;
               const uint32_t idesc = nt ? id1 : id0;
-              tc::mma_tf32(d, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-              tc::mma_tf32(d, ah, bl, idesc, 1u);
-              tc::mma_tf32(d, al, bh, idesc, 1u);
+              const uint32_t acc0 = (kc > 0 || kk > 0) ? 1u : 0u;
+              if constexpr (F16) {
+                tc::mma_f16(d, ah, bh, idesc, acc0);
+                tc::mma_f16(d, ah, bl, idesc, 1u);
+                tc::mma_f16(d, al, bh, idesc, 1u);
+              } else {
+                tc::mma_tf32(d, ah, bh, idesc, acc0);
+                tc::mma_tf32(d, ah, bl, idesc, 1u);
+                tc::mma_tf32(d, al, bh, idesc, 1u);
+              }
             }
           }
           tc::mma_commit(&empty[s]);
@@ -269,7 +326,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
         tc::mma_commit(&accf[buf]);
       }
     }
-  } else {
+  } else if (warp < 4) {
     // ---- epilogue, row (b, a): Sigma_ab = sum_k V_ak (sigma g_ab (QV)_kb - g_kb P_ak) ----
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
@@ -282,12 +339,18 @@ __global__ void __launch_bounds__(kThreads2, 1)
       const long r = (q % RT) * 128 + warp * 32 + lane;
       const bool live = r < T;
       int b = 0, a = 0;
-      if (live) tri_row(n, r, &b, &a);
+      if (live) {
+        const uint32_t e = S.rows[r];
+        b = (int)(e >> 16);
+        a = (int)(e & 0xffffu);
+      }
       const float *gA = S.g32 + (long)j * n * ld;
       const float *Va = S.V32 + (long)a * ld;              // V_ak = V_ka: row a
       const float *gb_row = gA + (long)b * ld;              // g_kb = g_bk: row b
       const float *qb_row = S.VQ + ((long)j * n + b) * ld;  // (QV)_kb = (VQ)_bk
       const float sg = live ? S.spin * gA[(long)a * ld + b] : 0.f;
+      // FP16 operands carry 2^(eX + kScaleG); undo it on P (an exact power of two)
+      const float inv = F16 ? ldexpf(1.f, -(x_scale_exp(S.scale) + kScaleG)) : 1.f;
       const int buf = tcount & 1;
       const uint32_t tu = tcount >> 1;
       if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
@@ -307,10 +370,10 @@ __global__ void __launch_bounds__(kThreads2, 1)
             const float4 g4 = *reinterpret_cast<const float4 *>(gb_row + c0 + 4 * t4);
             const float4 q4 = *reinterpret_cast<const float4 *>(qb_row + c0 + 4 * t4);
             // rows are zero beyond n, so padded columns add nothing
-            acc = fmaf(v4.x, sg * q4.x - g4.x * pv[4 * t4], acc);
-            acc = fmaf(v4.y, sg * q4.y - g4.y * pv[4 * t4 + 1], acc);
-            acc = fmaf(v4.z, sg * q4.z - g4.z * pv[4 * t4 + 2], acc);
-            acc = fmaf(v4.w, sg * q4.w - g4.w * pv[4 * t4 + 3], acc);
+            acc = fmaf(v4.x, sg * q4.x - g4.x * (pv[4 * t4] * inv), acc);
+            acc = fmaf(v4.y, sg * q4.y - g4.y * (pv[4 * t4 + 1] * inv), acc);
+            acc = fmaf(v4.z, sg * q4.z - g4.z * (pv[4 * t4 + 2] * inv), acc);
+            acc = fmaf(v4.w, sg * q4.w - g4.w * (pv[4 * t4 + 3] * inv), acc);
           }
         }
       }
@@ -336,7 +399,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
   __syncthreads();
   if (*abort_flag) {
     // let MMAs still in flight finish (bounded) before the TMEM goes away
-    if (warp == 13 && lane == 0) {
+    if (warp == R::kMma && lane == 0) {
       if (issued) tc::mma_commit(drain);
       atomicExch(err, 1);
       if (issued) tc::mbar_wait(drain, 0, kWaitNs);
@@ -400,21 +463,36 @@ int sigma2_tc_max_n() {
 }
 
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool tf32_operands) {
   const int ld = (n + 31) / 32 * 32;
   const long stack = (long)M * n * ld;
   float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *VQ = ws + 3 * stack;
   float *V32 = ws + 4 * stack;
-  split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, gh, gl);
+  // the FP16 path takes gb from the FP16 split of g: only g32 is needed here
+  split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, tf32_operands ? gh : nullptr,
+                                    tf32_operands ? gl : nullptr);
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_vq(n, M, ld, V32, g32, VQ, s);
 }
 
+void exchange_row_table(int n, std::vector<uint32_t> &rows) {
+  rows.clear();
+  rows.reserve((size_t)n * (n + 1) / 2);
+  for (int b0 = 0; b0 < n; b0 += 16)
+    for (int a0 = b0; a0 < n; a0 += 8)  // b0 is a multiple of 8: the first a-block on the diagonal
+      for (int b = b0; b < b0 + 16 && b < n; ++b)
+        for (int a = a0 > b ? a0 : b; a < a0 + 8 && a < n; ++a)
+          rows.push_back((uint32_t)b << 16 | (uint32_t)a);
+}
+
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
-                      float *S32, unsigned *smax) {
+                      float *S32, const uint32_t *rows, unsigned *smax, const void *h16,
+                      const TcScale *scale) {
+  if (!rows) return cudaErrorInvalidValue;
   d->g = tc_geom(n, M);
+  d->rows = rows;
   const long stack = (long)M * n * d->g.ld;
   d->spin = (float)spin;
   d->g32 = ws;
@@ -423,24 +501,46 @@ cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, doubl
   d->Sigma = Sigma;
   d->S32 = S32;
   d->smax = smax;
+  d->scale = scale;
   for (int t = 0; t < 2; ++t) {
     cudaError_t e = make_tmap_rows(&d->th[t], ws + stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e == cudaSuccess) e = make_tmap_rows(&d->tl[t], ws + 2 * stack, n, M, d->g.ld, d->g.nsz[t]);
     if (e != cudaSuccess) return e;
   }
+  if (h16) {
+    const int ld16 = ld16_of(n);
+    const uint16_t *hh = reinterpret_cast<const uint16_t *>(h16);
+    const uint16_t *hl = hh + (size_t)M * n * ld16;
+    for (int t = 0; t < 2; ++t) {
+      cudaError_t e = make_tmap_rows16(&d->hh[t], hh, n, M, ld16, d->g.nsz[t]);
+      if (e == cudaSuccess) e = make_tmap_rows16(&d->hl[t], hl, n, M, ld16, d->g.nsz[t]);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return cudaSuccess;
 }
 
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
-                               int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s) {
+                               int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s,
+                               bool f16) {
   (void)ld_max;
   const size_t smem = tc_smem_bytes(Np_max, 0, false);
-  cudaError_t e = cudaFuncSetAttribute(exchange_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
-  exchange_tc_kernel<<<grid, kThreads2, smem, s>>>(sys, prefix, n_sys, items, Np_max, nbuf, err);
+  cudaError_t e;
+  if (f16) {
+    e = cudaFuncSetAttribute(exchange_tc_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    exchange_tc_kernel<true><<<grid, XRoles<true>::kThreads, smem, s>>>(sys, prefix, n_sys, items,
+                                                                        Np_max, nbuf, err);
+  } else {
+    e = cudaFuncSetAttribute(exchange_tc_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    exchange_tc_kernel<false><<<grid, XRoles<false>::kThreads, smem, s>>>(
+        sys, prefix, n_sys, items, Np_max, nbuf, err);
+  }
   return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 
 #include <cuda.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace fedvr {
@@ -21,19 +23,24 @@ struct TcGeom {
 };
 
 // Operand scales of the FP16-split path, one per system (device memory).
-// Values of g and of g V enter FP16 as x * 2^kScaleG (|g| < 16 keeps them
-// below 65504); the convolution's interpolated Sigma enters as x * 2^sA with
-// sA from the bound maxC * max|Sigma| chosen per launch.
+// Values of g enter FP16 as x * 2^kScaleG (|g| < 16 keeps them below 65504);
+// the convolution's interpolated Sigma enters as x * 2^sA with sA from the
+// bound maxC * max|Sigma| chosen per launch, the exchange's g V as x * 2^eX
+// with eX from max|V|.
 constexpr int kScaleG = 12;
 struct TcScale {
   unsigned maxS;  // bit pattern of max |x| over the FP32 source stack (Sigma and B_ii rows)
   float maxC;     // max over (i, j) of |c1| + |c2|
-  unsigned pad[2];
+  float maxV;     // max |V_ab| (the exchange's A operand g V enters as x 2^(11 - e), |V| < 2^e)
+  unsigned pad;
 };
 
 // Sigma^(2) exchange kernel: one system.
 struct XSys {
   CUtensorMap th[2], tl[2];   // gb = G[M-1-j] split, per N tile
+  CUtensorMap hh[2], hl[2];   // FP16 path: the FP16 split of g (scaled by 2^kScaleG), per N tile
+  const TcScale *scale;       // FP16 path: operand scales
+  const uint32_t *rows;       // stacked row r -> (b << 16) | a (exchange_row_table)
   TcGeom g;
   float spin;
   const float *g32, *V32, *VQ;
@@ -65,7 +72,13 @@ size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns);
 // Host-side descriptor fill (tensor maps included); the caller copies the
 // descriptors to device memory.
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
-                      float *S32, unsigned *smax = nullptr);
+                      float *S32, const uint32_t *rows, unsigned *smax = nullptr,
+                      const void *h16 = nullptr, const TcScale *scale = nullptr);
+// The exchange kernel's stacking of the rows (b, a >= b) of one mesh point:
+// blocks of 16 values of b x 8 values of a (block-major; b, then a inside a
+// block), packed densely, entry r = (b << 16) | a. Every pair appears once;
+// a 128-row tile then touches 8-24 rows of V and 16-48 rows of g.
+void exchange_row_table(int n, std::vector<uint32_t> &rows);
 cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
                        const double *dHF, const int4 *coef32, double *I1, double *part,
                        const void *h16 = nullptr, const TcScale *scale = nullptr);
@@ -74,8 +87,10 @@ inline int ld16_of(int n) { return (n + 63) / 64 * 64; }
 // FP16 split of g (scaled by 2^kScaleG) into h16 = [hi stack][lo stack],
 // [M][n][ld16] halves each, padding zero.
 cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s);
-// scale->maxC = max |c1| + |c2| over the coefficient table; scale->maxS = 0.
-cudaError_t launch_scale_init(int M, const int4 *coef32, TcScale *scale, cudaStream_t s);
+// scale->maxC = max |c1| + |c2| over the coefficient table, scale->maxV =
+// max |V| over the n x n interaction matrix, scale->maxS = 0.
+cudaError_t launch_scale_init(int M, const int4 *coef32, int n, const double *V, TcScale *scale,
+                              cudaStream_t s);
 // Compact FP32 convolution coefficients {k1, k2, (float)c1, (float)c2} per
 // (i, j) over the extended FP32 source stack [2M][n][ld]: rows k < M are
 // Sigma_k, row M + i is the diagonal operand B_ii, taken with weight 1.
@@ -89,13 +104,15 @@ cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma
 cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
                              cudaStream_t s);
 
-// Per-system preparation of the exchange operands (splits of G and V, VQ).
+// Per-system preparation of the exchange operands (FP32 copies of G and V,
+// VQ, and with tf32_operands the TF32 split of G for the gb operand).
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
-                          cudaStream_t s);
+                          cudaStream_t s, bool tf32_operands = true);
 // Persistent launches over a device table of n_sys systems; prefix[n_sys + 1]
 // (device) holds the cumulative work items; Np_max/ld_max size the stages.
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
-                               int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s);
+                               int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s,
+                               bool f16 = false);
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
                             int Np_max, int *err, int num_sms, cudaStream_t s, bool f16 = false);
 

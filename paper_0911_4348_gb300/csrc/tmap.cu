@@ -1,7 +1,8 @@
 // TMA tensor maps for the split operand arrays: a 3-D map over [M][n][ld]
 // floats (ld = n rounded up to 32) whose box is 32 columns (128-byte swizzle)
-// or 16 columns (64-byte swizzle) x `rows` rows x 1 matrix, rows beyond n
-// zero-filled. make_tmap_rows16 is the same over FP16 rows of ld16 halves
+// or 16 columns (64-byte swizzle) x `rows` rows x 1 matrix, rows and columns
+// beyond n zero-filled (the map's column extent is n, so the padding is not
+// fetched). make_tmap_rows16 is the same over FP16 rows of ld16 halves
 // (a multiple of 64), box 64 halves (128 bytes) wide. The encoder comes from
 // the driver through the runtime's entry-point lookup, so no link against
 // libcuda is needed.
@@ -35,7 +36,10 @@ cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, in
   if (!g_encode) return cudaErrorNotSupported;
   if (rows < 1 || rows > 256 || (ld % 32) != 0 || (box_cols != 32 && box_cols != 16))
     return cudaErrorInvalidValue;
-  const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)n, (cuuint64_t)M};
+  // columns past n lie outside the map and are zero-filled by the copy engine
+  // without being read (the arrays hold zeros there as well)
+  const cuuint64_t cols = n >= box_cols ? (cuuint64_t)n : (cuuint64_t)ld;
+  const cuuint64_t dims[3] = {cols, (cuuint64_t)n, (cuuint64_t)M};
   const cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)n * (cuuint64_t)ld * 4};
   const cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
@@ -51,7 +55,8 @@ cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, i
   std::call_once(g_encode_once, load_encoder);
   if (!g_encode) return cudaErrorNotSupported;
   if (rows < 1 || rows > 256 || (ld16 % 64) != 0) return cudaErrorInvalidValue;
-  const cuuint64_t dims[3] = {(cuuint64_t)ld16, (cuuint64_t)n, (cuuint64_t)M};
+  const cuuint64_t cols = n >= 64 ? (cuuint64_t)n : (cuuint64_t)ld16;
+  const cuuint64_t dims[3] = {cols, (cuuint64_t)n, (cuuint64_t)M};
   const cuuint64_t strides[2] = {(cuuint64_t)ld16 * 2, (cuuint64_t)n * (cuuint64_t)ld16 * 2};
   const cuuint32_t box[3] = {64, (cuuint32_t)rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};

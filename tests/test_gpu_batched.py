@@ -122,3 +122,26 @@ def test_batched_graph_replay_is_bit_identical():
         assert np.array_equal(er, gr) and np.array_equal(ee, ge)
     for he, hg in zip(e_hist, g_hist):
         assert np.array_equal(he[:, :4], hg[:, :4])
+
+
+def test_batched_f16_equals_single_system_solves():
+    # the FP16-split mode through the batched queue: same results as one system at a time
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import solve_2b_batched
+    F16 = 3
+    systems = _systems()[:3]
+    single = []
+    for s in systems:
+        c = _ctx(s)
+        c.conv1_splits(1)
+        single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=F16, check=False))
+        c.close()
+    ctxs = [_ctx(s) for s in systems]
+    out = solve_2b_batched(ctxs, [s.beta for s in systems], [s.u for s in systems],
+                           [s.p for s in systems], 0.5, 1e-8, 150, F16, check=False)
+    for k, s in enumerate(systems):
+        assert out["iters"][k] == single[k]["iters"], s.name
+        assert out["E0"][k] == single[k]["E0"], s.name
+    for c in ctxs:
+        c.close()
