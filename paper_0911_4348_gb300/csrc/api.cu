@@ -151,18 +151,16 @@ int eig(fedvr_ctx *ctx, double *A, const double *Vinit, double *eps, double *C) 
   return FEDVR_OK;
 }
 
-// Workspace of the tensor-core Sigma^(2) build: split operands, QV, V32, an
+// Workspace of the tensor-core Sigma^(2) build: split operands, VQ, V32, an
 // FP32 copy of Sigma followed by the diagonal operands B_ii of the first
-// convolution (both read by the tensor-core convolution) and the error flag.
+// convolution (both read by the tensor-core convolution), V Q V and the error
+// flag (offsets in tc_sys.cuh).
 int tc_workspace(fedvr_ctx *ctx, int n, int M, float **ws, float **S32, int **err) {
-  const size_t ld = (size_t)(n + 31) / 32 * 32;
-  const size_t stack = (size_t)M * n * ld;
-  const size_t floats = 6 * stack + (size_t)n * ld + 64;
-  ENSURE(ctx, w_tc, floats * sizeof(float));
+  ENSURE(ctx, w_tc, tc_ws_floats(n, M) * sizeof(float));
   float *base = P<float>(ctx->w_tc);
   *ws = base;
-  *S32 = base + 4 * stack + (size_t)n * ld;  // [2M][n][ld]: Sigma, then the diagonal operands
-  *err = reinterpret_cast<int *>(base + 6 * stack + (size_t)n * ld);
+  *S32 = base + tc_ws_s32(n, M);
+  *err = reinterpret_cast<int *>(base + tc_ws_w(n, M) + tc_ws_stack(n, M));
   return FEDVR_OK;
 }
 
@@ -358,7 +356,7 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches) {
     int *err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
     FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale));
-    *launches += 3;
+    *launches += 4;  // splits of g and V, VQ, W = (VQ) V
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
                               P<double>(ctx->w_t3), s));

@@ -158,6 +158,9 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
 // VQ[j] = V32 (g32[j] o g32[M-1-j]) in FP32 for all j (rows padded to ld).
 cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, float *VQ,
                       cudaStream_t s);
+// W[j] = VQ[j] V (rows of ld floats; columns past n not written).
+cudaError_t launch_vqv(int n, int M, int ld, const float *VQ, const float *V32, float *W,
+                       cudaStream_t s);
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows,
                            int box_cols = 32);
 cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, int ld16, int rows);

@@ -308,6 +308,13 @@ cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_vqv(int n, int M, int ld, const float *VQ, const float *V32, float *W,
+                       cudaStream_t s) {
+  // W[j] = VQ[j] V for all j: the stacked rows (j, b) of VQ times V, one tall GEMM
+  return sgemm128<false, false, float, float, float>(M * n, n, n, 0, VQ, ld, 0, V32, ld, 0, W, ld,
+                                                     0, 1, s);
+}
+
 cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s) {
   to_f32_kernel<<<1024, 256, 0, s>>>(count, x, y);
   return cudaGetLastError();

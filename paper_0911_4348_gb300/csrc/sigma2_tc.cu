@@ -15,8 +15,10 @@
 // (TF32) and the product taken as hi*hi + hi*lo + lo*hi with FP32
 // accumulation in TMEM. The A operand g_al V_bl of each row is formed by the
 // CUDA cores while the previous chunk multiplies; B = gb is the same for every
-// row of the mesh point. The epilogue reads row (b, a) of P^(b) from TMEM and
-// folds the k-sum in FP32; the symmetric result is mirrored.
+// row of the mesh point. The direct term's matrix W = V Q V comes from two
+// FP32 GEMMs beforehand, so the epilogue reads row (b, a) of P^(b) from TMEM
+// and folds sum_k V_ak g_kb P_ak in FP32 (two warps per row, one per half of
+// k); the symmetric result is mirrored.
 #include "common.cuh"
 #include "tc.cuh"
 #include "tc_sys.cuh"
@@ -62,14 +64,15 @@ __global__ void split_kernel(int n, long rows, int ld, const double *__restrict_
   }
 }
 
-// Warp roles: 0-3 epilogue (TMEM lanes 0-127), then 8 warps of A-operand
-// producers, one warp of TMA loads of the gb operand
-// and one of MMA issue. Stages handed over with mbarriers: full[s] (producer
-// arrivals + TMA bytes), empty[s] (MMA commit); accumulators double-buffered
-// with accf/acce. The work queue is the concatenation of the (j, row tile)
-// items of every system in the table (mesh-point-major, so that concurrent
-// CTAs share gb in L2); every role walks it in the same order. The stage
-// layout uses the table's largest N.
+// Warp roles: 0-7 epilogue (two warps per TMEM lane quarter, one per half of
+// the columns), 8-15 A-operand producers, 16 TMA loads of the gb operand, 17
+// MMA issue. Stages handed over with mbarriers: full[s] (producer arrivals +
+// TMA bytes), empty[s] (MMA commit); accumulators double-buffered with
+// accf/acce; the two column halves of a row meet through a small shared
+// buffer handed over with pfull/pempty. Every wait is bounded. The work queue
+// is the concatenation of the (j, row tile) items of every system in the table
+// (mesh-point-major, so that concurrent CTAs share gb in L2); every role walks
+// it in the same order. The stage layout uses the table's largest N.
 //
 // FP16 variant: 128-byte operand rows hold 64 FP16 values, so a chunk covers
 // 64 contraction terms and the three products run as kind::f16 at twice the
@@ -78,13 +81,14 @@ __global__ void split_kernel(int n, long rows, int ld, const double *__restrict_
 // convolution uses as well), and the epilogue scales P^(b) back exactly.
 template <bool F16>
 struct XRoles {
-  static constexpr int kProd = 8;                 // producer warps
-  static constexpr int kTma = 4 + kProd, kMma = 5 + kProd;
-  static constexpr int kThreads = (6 + kProd) * 32;
+  static constexpr int kEpi = 8, kProd = 8;       // epilogue and producer warps
+  static constexpr int kTma = kEpi + kProd, kMma = kTma + 1;
+  static constexpr int kThreads = (kMma + 1) * 32;
   static constexpr int kCols = F16 ? 64 : 32;     // contraction terms per chunk
-  static constexpr int kRowsPer = 4;              // rows per producer thread: r0 + 32 k
-  static constexpr int kRowStep = 32;
 };
+
+// Bytes after the stages: barriers (256) and the column-half buffer (2 x 128 floats).
+constexpr uint32_t kXBarBytes = 256, kXPartBytes = 2 * 128 * 4;
 
 // Exponent eX of the FP16 A operand g V: max|V| < 2^e, |g| < 16.
 __device__ __forceinline__ int x_scale_exp(const TcScale *sc) {
@@ -108,8 +112,10 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
   uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+  uint64_t *pfull = bars + 9, *pempty = bars + 11;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 13);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  float *part = reinterpret_cast<float *>(smem + 2 * stage_bytes + kXBarBytes);  // [2][128]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -123,9 +129,13 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     tc::mbar_init(&empty[1], 1);
     tc::mbar_init(&accf[0], 1);
     tc::mbar_init(&accf[1], 1);
-    tc::mbar_init(&acce[0], 128);
-    tc::mbar_init(&acce[1], 128);
+    tc::mbar_init(&acce[0], R::kEpi * 32);
+    tc::mbar_init(&acce[1], R::kEpi * 32);
     tc::mbar_init(drain, 1);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&pfull[q], 128);
+      tc::mbar_init(&pempty[q], 128);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -136,12 +146,11 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
   bool issued = false;
   int cur = 0;  // system of the current item (items ascend within a CTA)
 
-  if (warp >= 4 && warp < R::kTma) {
-    // ---- A producers: row (b, a): A(l) = g_al * V_bl, split hi/lo ----
-    // rows r0 + 32 k (k < 4), 16-byte unit c of each chunk row (TF32: 4 values of a
-    // 32-wide chunk, FP16: 8 values of a 64-wide chunk)
-    const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
-    constexpr int KR = R::kRowsPer;
+  if (warp >= R::kEpi && warp < R::kTma) {
+    // ---- A producers: row (b, a): A(l) = g_al * V_bl, split hi/lo; rows r0 + 32 k
+    // (k < 4), 16-byte unit c of each chunk row (TF32: 4 values of a 32-wide chunk,
+    // FP16: 8 values of a 64-wide chunk) ----
+    const int pt = tid - R::kEpi * 32, c = pt & 7, r0 = pt >> 3;
     uint32_t cc = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
@@ -155,11 +164,11 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       const float *const V32 = S.V32;  // in a register across the memory-clobbering asm
       const float fX = F16 ? ldexpf(1.f, x_scale_exp(S.scale)) : 1.f;
       const int u = F16 ? 8 * c : 4 * c;  // first column of this thread's unit in a chunk
-      uint32_t og[KR], ov[KR];  // element offsets of row a of g_j and row b of V
-      bool live[KR];
+      uint32_t og[4], ov[4];  // element offsets of row a of g_j and row b of V
+      bool live[4];
 #pragma unroll
-      for (int k = 0; k < KR; ++k) {
-        const long r = t * 128 + r0 + R::kRowStep * k;
+      for (int k = 0; k < 4; ++k) {
+        const long r = t * 128 + r0 + 32 * k;
         live[k] = r < T;
         int b = 0, a = 0;
         if (live[k]) {
@@ -173,9 +182,9 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       for (int kc = 0; kc < KC; ++kc, ++cc) {
         const int l0 = kc * R::kCols;
         const bool in = l0 + u < n;  // units past n are zero padding: not fetched
-        float4 gv[KR][F16 ? 2 : 1], vv[KR][F16 ? 2 : 1];
+        float4 gv[4][F16 ? 2 : 1], vv[4][F16 ? 2 : 1];
 #pragma unroll
-        for (int k = 0; k < KR; ++k) {
+        for (int k = 0; k < 4; ++k) {
 #pragma unroll
           for (int h = 0; h < (F16 ? 2 : 1); ++h) {
             if (live[k] && in) {
@@ -194,8 +203,8 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         }
         uint8_t *st = smem + s * stage_bytes;
 #pragma unroll
-        for (int k = 0; k < KR; ++k) {
-          const uint32_t off = tc::sw128_offset(r0 + R::kRowStep * k, c);
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
           if constexpr (F16) {
             float x[8];
 #pragma unroll
@@ -326,8 +335,11 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         tc::mma_commit(&accf[buf]);
       }
     }
-  } else if (warp < 4) {
-    // ---- epilogue, row (b, a): Sigma_ab = sum_k V_ak (sigma g_ab (QV)_kb - g_kb P_ak) ----
+  } else if (warp < R::kEpi) {
+    // ---- epilogue, row (b, a) = TMEM lane 32 (warp & 3) + lane; warps 0-3 take the
+    // first half of the columns k, warps 4-7 the second:
+    //   Sigma_ab = sigma g_ab W_ab - sum_k V_ak g_kb P_ak,  W = V Q V ----
+    const int quarter = warp & 3, half = warp >> 2, prow = quarter * 32 + lane;
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
@@ -336,7 +348,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
       const long q = w - prefix[cur];
       const int j = (int)(q / RT);
-      const long r = (q % RT) * 128 + warp * 32 + lane;
+      const long r = (q % RT) * 128 + prow;
       const bool live = r < T;
       int b = 0, a = 0;
       if (live) {
@@ -345,12 +357,12 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         a = (int)(e & 0xffffu);
       }
       const float *gA = S.g32 + (long)j * n * ld;
-      const float *Va = S.V32 + (long)a * ld;              // V_ak = V_ka: row a
-      const float *gb_row = gA + (long)b * ld;              // g_kb = g_bk: row b
-      const float *qb_row = S.VQ + ((long)j * n + b) * ld;  // (QV)_kb = (VQ)_bk
-      const float sg = live ? S.spin * gA[(long)a * ld + b] : 0.f;
+      const float *Va = S.V32 + (long)a * ld;  // V_ak = V_ka: row a
+      const float *gb_row = gA + (long)b * ld;  // g_kb = g_bk: row b
       // FP16 operands carry 2^(eX + kScaleG); undo it on P (an exact power of two)
       const float inv = F16 ? ldexpf(1.f, -(x_scale_exp(S.scale) + kScaleG)) : 1.f;
+      const int NC = (n + 15) / 16, hc = (NC + 1) / 2;
+      const int cb = half ? hc : 0, ce = half ? NC : hc;
       const int buf = tcount & 1;
       const uint32_t tu = tcount >> 1;
       if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
@@ -359,38 +371,64 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       }
       tc::fence_after_sync();
       const uint32_t tbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-      float acc = 0.f;
-      for (int c0 = 0; c0 < n; c0 += 16) {
-        float pv[16];
-        tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, pv);
-        if (live) {
+      float acc0 = 0.f, acc1 = 0.f;
+      for (int ch = cb; ch < ce; ++ch) {
+        // the chunk's operands are requested before the TMEM read, so the two
+        // latencies overlap
+        float4 vc[4], gc[4];
 #pragma unroll
-          for (int t4 = 0; t4 < 4; ++t4) {
-            const float4 v4 = *reinterpret_cast<const float4 *>(Va + c0 + 4 * t4);
-            const float4 g4 = *reinterpret_cast<const float4 *>(gb_row + c0 + 4 * t4);
-            const float4 q4 = *reinterpret_cast<const float4 *>(qb_row + c0 + 4 * t4);
-            // rows are zero beyond n, so padded columns add nothing
-            acc = fmaf(v4.x, sg * q4.x - g4.x * (pv[4 * t4] * inv), acc);
-            acc = fmaf(v4.y, sg * q4.y - g4.y * (pv[4 * t4 + 1] * inv), acc);
-            acc = fmaf(v4.z, sg * q4.z - g4.z * (pv[4 * t4 + 2] * inv), acc);
-            acc = fmaf(v4.w, sg * q4.w - g4.w * (pv[4 * t4 + 3] * inv), acc);
-          }
+        for (int t4 = 0; t4 < 4; ++t4) {
+          vc[t4] = live ? *reinterpret_cast<const float4 *>(Va + ch * 16 + 4 * t4)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          gc[t4] = live ? *reinterpret_cast<const float4 *>(gb_row + ch * 16 + 4 * t4)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float pv[16];
+        tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 16), pv);
+        // rows are zero beyond n, so padded columns add nothing
+#pragma unroll
+        for (int t4 = 0; t4 < 4; ++t4) {
+          acc0 = fmaf(vc[t4].x * gc[t4].x, pv[4 * t4], acc0);
+          acc1 = fmaf(vc[t4].y * gc[t4].y, pv[4 * t4 + 1], acc1);
+          acc0 = fmaf(vc[t4].z * gc[t4].z, pv[4 * t4 + 2], acc0);
+          acc1 = fmaf(vc[t4].w * gc[t4].w, pv[4 * t4 + 3], acc1);
         }
       }
       tc::fence_before_sync();
       tc::mbar_arrive(&acce[buf]);
+      const float xh = (acc0 + acc1) * inv;
+      float *pb = part + buf * 128;
+      if (half) {
+        // hand the second half's sum to warp (warp - 4) through the buffer of this
+        // tile's parity, once that warp has read the buffer's previous use
+        if (tu > 0 && !tc::mbar_wait(&pempty[buf], (tu - 1) & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        pb[prow] = xh;
+        tc::mbar_arrive(&pfull[buf]);
+        continue;
+      }
+      if (!tc::mbar_wait(&pfull[buf], tu & 1, kWaitNs)) {
+        *abort_flag = 1;
+        break;
+      }
+      const float X = xh + pb[prow];
+      tc::mbar_arrive(&pempty[buf]);
+      float sig = 0.f;
+      if (live) sig = S.spin * gA[(long)a * ld + b] * S.W[((long)j * n + b) * ld + a] - X;
       if (S.smax) {  // largest |Sigma| entry, for the FP16 operand scale of the convolution
-        float mx = live ? fabsf(acc) : 0.f;
+        float mx = fabsf(sig);
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) atomicMax(S.smax, __float_as_uint(mx));
       }
       if (live) {
         const long nn = (long)n * n;
-        S.Sigma[(long)j * nn + (long)a * n + b] = (double)acc;
-        S.Sigma[(long)j * nn + (long)b * n + a] = (double)acc;
+        S.Sigma[(long)j * nn + (long)a * n + b] = (double)sig;
+        S.Sigma[(long)j * nn + (long)b * n + a] = (double)sig;
         if (S.S32) {
-          S.S32[((long)j * n + a) * ld + b] = acc;
-          S.S32[((long)j * n + b) * ld + a] = acc;
+          S.S32[((long)j * n + a) * ld + b] = sig;
+          S.S32[((long)j * n + b) * ld + a] = sig;
         }
       }
     }
@@ -474,7 +512,9 @@ cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float 
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_vq(n, M, ld, V32, g32, VQ, s);
+  e = launch_vq(n, M, ld, V32, g32, VQ, s);
+  if (e != cudaSuccess) return e;
+  return launch_vqv(n, M, ld, VQ, V32, ws + tc_ws_w(n, M), s);
 }
 
 void exchange_row_table(int n, std::vector<uint32_t> &rows) {
@@ -496,8 +536,8 @@ cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, doubl
   const long stack = (long)M * n * d->g.ld;
   d->spin = (float)spin;
   d->g32 = ws;
-  d->VQ = ws + 3 * stack;
   d->V32 = ws + 4 * stack;
+  d->W = ws + tc_ws_w(n, M);
   d->Sigma = Sigma;
   d->S32 = S32;
   d->smax = smax;
@@ -524,7 +564,8 @@ cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, l
                                int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s,
                                bool f16) {
   (void)ld_max;
-  const size_t smem = tc_smem_bytes(Np_max, 0, false);
+  const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 128) + kXBarBytes +
+                      kXPartBytes;
   const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
   cudaError_t e;

@@ -43,7 +43,8 @@ struct XSys {
   const uint32_t *rows;       // stacked row r -> (b << 16) | a (exchange_row_table)
   TcGeom g;
   float spin;
-  const float *g32, *V32, *VQ;
+  const float *g32, *V32;
+  const float *W;             // V Q V per mesh point (the direct term's matrix), rows of ld
   double *Sigma;
   float *S32;
   unsigned *smax;             // if set: atomic max of |Sigma| (FP32 bits)
@@ -104,8 +105,19 @@ cudaError_t launch_diag_f32(int n, int M, const double *dHF, const double *Sigma
 cudaError_t conv1_sum_splits(long count, int nparts, const double *part, double *I1,
                              cudaStream_t s);
 
+// Float offsets in the tensor-core workspace of one system (ld = n rounded up
+// to 32, stack = M n ld): g32 | gh | gl | VQ | V32 (n x ld) | S32 (2 stacks:
+// Sigma, then the diagonal operands B_ii) | W | error flag.
+inline size_t tc_ws_stack(int n, int M) { return (size_t)M * n * ((n + 31) / 32 * 32); }
+inline size_t tc_ws_s32(int n, int M) {
+  return 4 * tc_ws_stack(n, M) + (size_t)n * ((n + 31) / 32 * 32);
+}
+inline size_t tc_ws_w(int n, int M) { return tc_ws_s32(n, M) + 2 * tc_ws_stack(n, M); }
+inline size_t tc_ws_floats(int n, int M) { return tc_ws_w(n, M) + tc_ws_stack(n, M) + 64; }
+
 // Per-system preparation of the exchange operands (FP32 copies of G and V,
-// VQ, and with tf32_operands the TF32 split of G for the gb operand).
+// VQ and W = (VQ) V, and with tf32_operands the TF32 split of G for the gb
+// operand).
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
                           cudaStream_t s, bool tf32_operands = true);
 // Persistent launches over a device table of n_sys systems; prefix[n_sys + 1]
