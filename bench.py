@@ -512,14 +512,17 @@ def main():
         peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
         bound, punit, psrc = "alu", "TFLOP/s", ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x "
                                                f"{sm_max:.0f} MHz (unit counts and clocks)")
-    elif args.precision == "f16" and dom == "conv1":
+    elif args.precision == "f16" and dom in ("conv1", "sigma2"):  # both run kind::f16
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         bound, punit, psrc = "tensor", "TFLOP/s", "measured bf16 sustained (fp16 dense rate = bf16)"
     else:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) / 2.0
         bound, punit, psrc = "tensor", "TFLOP/s", "measured bf16 sustained x 1/2 (tf32 ratio)"
     achieved = algorithmic(dom, n, M) / (avg[dom] / 1000.0) / 1e12
-    kernel_name = {"conv1": "conv1_tc_kernel", "sigma2": "exchange_tc_kernel"}.get(dom)
+    # keys of profiles/ncu_traffic.json: the kernel of the stage in this precision
+    kernel_name = {("conv1", "f16"): "conv1_f16_kernel", ("conv1", "tf32"): "conv1_tc_kernel",
+                   ("sigma2", "f16"): "exchange_tc_kernel<f16>",
+                   ("sigma2", "tf32"): "exchange_tc_kernel<tf32>"}.get((dom, args.precision))
     traffic = measured_traffic(kernel_name, sys_.name) if (prec != 0 and kernel_name) else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
             "frac": achieved / peak, "traffic": traffic, "kernel": dom,
