@@ -153,6 +153,14 @@ def max_over_ranks(dist, x: float, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def split_precision(args) -> int:
+    """The library code of a split precision (the batched and warm-start paths run
+    only on the tensor-core kernels)."""
+    if args.precision not in ("tf32", "f16"):
+        raise SystemExit(f"--precision {args.precision}: this workload runs split tf32 or f16")
+    return PRECISIONS[args.precision]
+
+
 def rank_config(config_id: int, rank: int) -> int:
     """Seed stream of a rank's share of a family of independent systems: every
     rank draws its own systems (weak scaling, no data exchanged)."""
@@ -264,7 +272,8 @@ def run_batch(args, dist, rank, world, local):
     ctxs = make()
     betas = [s_.beta for s_ in systems]
     us, ps = [s_.u for s_ in systems], [s_.p for s_ in systems]
-    batch = Batch(ctxs, betas, us, ps)
+    prec = split_precision(args)
+    batch = Batch(ctxs, betas, us, ps, prec)
     for _ in range(args.warmup):
         batch.step(0.5)
     if dist:
@@ -283,15 +292,15 @@ def run_batch(args, dist, rank, world, local):
     value = world * n_sys * args.steps / (elapsed / 1000.0)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
            "config": {"workload": "batch of 64: 32 He (Z~U[1.5,2.5]) + 32 H3+ (R~U[1.2,3.0])",
                       "n_b": [s_.n_b for s_ in systems], "n_tau": [s_.n_tau for s_ in systems],
-                      "precision": "tf32", "parallelism": f"replicas x{world}"}}
+                      "precision": args.precision, "parallelism": f"replicas x{world}"}}
     if not args.no_time_to_e0:
         ctxs2 = make()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = solve_2b_batched(ctxs2, betas, us, ps, 0.5, 1e-8, 200, check=False)
+        r = solve_2b_batched(ctxs2, betas, us, ps, 0.5, 1e-8, 200, prec, check=False)
         torch.cuda.synchronize()
         out["time_to_converge_all"] = {"seconds": time.perf_counter() - t0,
                                        "max_iterations": int(np.max(r["iters"])),
@@ -363,7 +372,8 @@ def run_warmstart(args, dist, rank, world, local):
                 c.warm_start(model, s_.beta, s_.u, s_.p, inner_steps=4)
                 torch.cuda.synchronize()
                 t_ws = time.perf_counter() - t1
-            r = c.solve_2b(s_.beta, s_.u, s_.p, s_.mixing, s_.tol, 200, 1, check=False)
+            r = c.solve_2b(s_.beta, s_.u, s_.p, s_.mixing, s_.tol, 200, split_precision(args),
+                           check=False)
             hist = c.get_history()
             if mode == "plain":
                 E_ref = r["E0"]
@@ -386,12 +396,12 @@ def run_warmstart(args, dist, rank, world, local):
     s0 = train[0]
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": steps_total, "warmup": 0, "ms_per_step": step_ms / steps_total,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
            "data": "synthetic",
            "config": {"workload": "warm-start family: He (Z~U[1.5,2.5]) / H3+ (R~U[1.2,3.0]), "
                                   f"20 x 7 points (n_b={s0.n_b}), M={M}",
                       "train_systems": len(train), "test_systems": len(test),
-                      "hidden": args.hidden, "epochs": args.epochs, "precision": "tf32",
+                      "hidden": args.hidden, "epochs": args.epochs, "precision": args.precision,
                       "parallelism": f"replicas x{world}"},
            "warm_start": {"collect_seconds": t_collect,
                           "collect_iterations_mean": float(np.mean(collect_iters)),
@@ -511,6 +521,11 @@ def main():
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
         bound, punit, psrc = "alu", "TFLOP/s", ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x "
+                                               f"{sm_max:.0f} MHz (unit counts and clocks)")
+    elif dom == "conv2":  # the second convolution's GEMMs run on the FP32 pipe
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = N_SM * 128 * 2 * sm_max * 1e6 / 1e12
+        bound, punit, psrc = "alu", "TFLOP/s", ("FP32 pipe: 152 SMs x 128 FMA/clk x 2 flop x "
                                                f"{sm_max:.0f} MHz (unit counts and clocks)")
     elif args.precision == "f16" and dom in ("conv1", "sigma2"):  # both run kind::f16
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))

@@ -541,6 +541,11 @@ __global__ void __launch_bounds__(kThreadsH, 1)
                 }
                 k1[k] = cf.x;
                 k2[k] = cf.y;
+                // the bracket usually moves down by one row: ask L1 for that row now
+                if (cf.x > 0) {
+                  const float *pn = S32 + (uint32_t)(((cf.x - 1) * n + aa[k]) * ld + l0);
+                  asm volatile("prefetch.global.L1 [%0];" ::"l"(pn));
+                }
               }
             }
             const int s = cc & 1;
