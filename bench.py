@@ -14,7 +14,7 @@ scaling); ranks only meet at the timing barrier.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|tf32|f16]
-                    [--workload he_medium|he_small|h3p_large|he_paper|batch64|warmstart]
+                    [--workload he_medium|he_small|h3p_large|he_paper|batch64|warmstart|h3p_curve]
                     [--no-time-to-e0] [--no-fp64-compare] [--no-cpu-baseline]
                     [--train-systems T] [--test-systems H] [--epochs E] [--hidden H]
 """
@@ -42,7 +42,7 @@ METRIC = "Sigma^(2) builds/s (one build + its Dyson iteration per step)"
 UNIT = "builds/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "f16": 3}
 WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large,
-             "he_paper": W.he_paper, "batch64": None, "warmstart": None}
+             "he_paper": W.he_paper, "batch64": None, "warmstart": None, "h3p_curve": None}
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
 
@@ -227,8 +227,9 @@ def run_reference(args, rank: int):
         return
     make = WORKLOADS[args.workload]
     if make is None:  # families: time the oracle on their first system
-        make = (lambda: W.warmstart_system(0)) if args.workload == "warmstart" else \
-            (lambda: W.batch_systems(64)[0])
+        make = {"warmstart": lambda: W.warmstart_system(0),
+                "h3p_curve": lambda: W.h3p_curve()[0]}.get(args.workload,
+                                                           lambda: W.batch_systems(64)[0])
     sys_ = make()
     vals, prepared, spent = [], None, 0.0
     sample = ""
@@ -251,21 +252,37 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def _parabola_min(x, y):
+    """Abscissa of the vertex of the parabola through the lowest sample and its
+    two neighbours (None at the ends of the sampled range)."""
+    k = int(np.argmin(y))
+    if k == 0 or k == len(y) - 1:
+        return None
+    h = x[k + 1] - x[k]
+    return float(x[k] + h * (y[k - 1] - y[k + 1]) / (2 * (y[k - 1] - 2 * y[k] + y[k + 1])))
+
+
 def run_batch(args, dist, rank, world, local):
-    """64 uneven systems (32 He, 32 H3+; n_b 59-239, 257-513 mesh points)
-    advanced together; a step is one batched iteration of every system."""
+    """Systems advanced together, a step being one batched iteration of every
+    system. batch64: 64 uneven systems (32 He, 32 H3+; n_b 59-239, 257-513
+    mesh points). h3p_curve: the paper's H3+ binding curve (Sec. 3.2), 11
+    bond lengths on its n_b = 142 grid with 1025 mesh points."""
     import torch
     from paper_0911_4348_gb300 import Batch, Context, solve_2b_batched
-    systems = W.batch_systems(64, config_id=rank_config(4, rank))
+    curve = args.workload == "h3p_curve"
+    systems = W.h3p_curve() if curve else W.batch_systems(64, config_id=rank_config(4, rank))
     stream = torch.cuda.current_stream()
+    e_hf, e_nn = [], []
 
     def make():
         ctxs = []
+        e_hf.clear()
+        e_nn.clear()
         for s_ in systems:
             c = Context(stream.cuda_stream)
             c.build_fedvr(s_.n_elem, s_.order, s_.xmin, s_.xmax, s_.grid_kind)
-            c.set_potential(s_.Z, s_.R, s_.soft_en, s_.soft_ee, s_.n_elec)
-            c.solve_hf(s_.beta, tol=1e-12)
+            e_nn.append(c.set_potential(s_.Z, s_.R, s_.soft_en, s_.soft_ee, s_.n_elec))
+            e_hf.append(c.solve_hf(s_.beta, tol=1e-12)[0])
             ctxs.append(c)
         return ctxs
 
@@ -293,7 +310,9 @@ def run_batch(args, dist, rank, world, local):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-           "config": {"workload": "batch of 64: 32 He (Z~U[1.5,2.5]) + 32 H3+ (R~U[1.2,3.0])",
+           "config": {"workload": ("H3+ binding curve: R = 1.6..3.6 step 0.2, 13 x 11 graded "
+                                   "(n_b=142), M=1025") if curve else
+                                  "batch of 64: 32 He (Z~U[1.5,2.5]) + 32 H3+ (R~U[1.2,3.0])",
                       "n_b": [s_.n_b for s_ in systems], "n_tau": [s_.n_tau for s_ in systems],
                       "precision": args.precision, "parallelism": f"replicas x{world}"}}
     if not args.no_time_to_e0:
@@ -305,6 +324,14 @@ def run_batch(args, dist, rank, world, local):
         out["time_to_converge_all"] = {"seconds": time.perf_counter() - t0,
                                        "max_iterations": int(np.max(r["iters"])),
                                        "status": r["status"]}
+        if curve:
+            d = np.array([2.0 * s_.R[2] for s_ in systems])
+            tot_hf = np.array(e_hf) + np.array(e_nn)
+            tot_2b = np.asarray(r["E0"]) + np.array(e_nn)
+            out["h3p_curve"] = {"d": d.tolist(), "E_hf_total": tot_hf.tolist(),
+                                "E_2b_total": tot_2b.tolist(), "N": np.asarray(r["N"]).tolist(),
+                                "d_b_hf": _parabola_min(d, tot_hf),
+                                "d_b_2b": _parabola_min(d, tot_2b)}
         for c in ctxs2:
             c.close()
     for c in ctxs:
@@ -449,8 +476,8 @@ def main():
     from paper_0911_4348_gb300 import Context
 
     torch.cuda.set_device(local)
-    if args.workload in ("batch64", "warmstart"):
-        (run_batch if args.workload == "batch64" else run_warmstart)(args, dist, rank, world, local)
+    if args.workload in ("batch64", "warmstart", "h3p_curve"):
+        (run_warmstart if args.workload == "warmstart" else run_batch)(args, dist, rank, world, local)
         if dist:
             dist.destroy_process_group()
         return

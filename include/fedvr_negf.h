@@ -144,6 +144,25 @@ int solve_hf(fedvr_ctx *ctx, double beta, double tol, int max_iter, double *E_hf
  * Sigma0 = F - h [n_b][n_b]. */
 int fedvr_get_hf(const fedvr_ctx *ctx, double *eps, double *C, double *rho0, double *Sigma0);
 
+/* Sources of fedvr_density. */
+typedef enum {
+  FEDVR_DENSITY_HF = 0, /* rho0 of the last solve_hf */
+  FEDVR_DENSITY_2B = 1  /* g(0^-) of the current second-Born iterate (after
+                           solve_2b: its final g; after fedvr_2b_prepare
+                           alone: g^0, the HF density) */
+} fedvr_density_source;
+
+/* One-electron density at the basis nodes (Sec. 2.3: n(x) sums the products
+ * chi chi of basis functions weighted by g(0^-)). A DVR function is
+ * 1/sqrt(W_a) at its own node and zero at every other node, so
+ * n_out[a] = spin * g_aa(0^-) / W_a, with g the Green's function of one spin
+ * (the density integrates to N: sum_a W_a n_out[a] = spin Tr g(0^-)).
+ * n_out: host buffer of n_b doubles. Computed on the device from the context's
+ * own g and weights; synchronises the context's stream.
+ * Errors: FEDVR_ERR_ARG (n_out NULL or unknown source), FEDVR_ERR_STATE (no HF
+ * solution, resp. no prepared second-Born run). */
+int fedvr_density(const fedvr_ctx *ctx, int source, double *n_out);
+
 /* ---------------------------------------------------------------------- */
 /* Second Born (Sec. 2.3 Eqs. sigma2ndb, deq; Sec. 3.1 mesh)               */
 /* ---------------------------------------------------------------------- */

@@ -20,8 +20,11 @@ representation in nonequilibrium Green's function calculations" (arXiv
 * Sec. 3.1 (uniform power mesh, 2up+1 points): ``power_mesh``, ``lag_table``.
 * Sec. 2.3 (total energy "as in" the cited references): ``energy``
   (Galitskii-Migdal form).
-* Pins only: ``mp2`` (closed-shell MP2) and ``exact_ground`` (exact
-  two-electron ground state on the same grid).
+* Sec. 2.3 and 3.2 observables: ``density`` (one-electron density from
+  g(0^-)) and ``nuclear_repulsion`` (the internuclear term of Eq. h3pv).
+* Pins only: ``mp2`` (closed-shell MP2), ``exact_ground`` /
+  ``exact_ground_state`` / ``exact_density`` (exact two-electron ground state
+  on the same grid).
 
 Where the paper is silent or garbled the oracle takes one stated reading; each
 is marked "Reading:" below. Every floating-point step of the basis, mesh and
@@ -828,3 +831,61 @@ def exact_ground(T: np.ndarray, v: np.ndarray, V: np.ndarray) -> float:
     H = sp.kron(Ts, I) + sp.kron(I, Ts) + sp.diags(diag)
     val = spl.eigsh(H.tocsr(), k=1, which="SA", tol=1e-12)[0]
     return float(val[0])
+
+
+def exact_ground_state(T: np.ndarray, v: np.ndarray, V: np.ndarray) -> tuple[float, np.ndarray]:
+    """Lowest eigenpair of the two-electron grid Hamiltonian of ``exact_ground``:
+    the energy and the eigenvector as DVR coefficients Psi[a, b] of the two
+    electrons at nodes x_a and x_b (sum |Psi|^2 = 1, Psi symmetric)."""
+    n = T.shape[0]
+    diag = (v[:, None] + v[None, :] + V).ravel()
+    if n <= 40:
+        I = np.eye(n)
+        H = np.kron(T, I) + np.kron(I, T) + np.diag(diag)
+        vals, vecs = np.linalg.eigh(H)
+        return float(vals[0]), vecs[:, 0].reshape(n, n)
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    Ts = sp.csr_matrix(T)
+    I = sp.identity(n, format="csr")
+    H = sp.kron(Ts, I) + sp.kron(I, Ts) + sp.diags(diag)
+    vals, vecs = spl.eigsh(H.tocsr(), k=1, which="SA", tol=1e-12)
+    return float(vals[0]), vecs[:, 0].reshape(n, n)
+
+
+def exact_density(psi: np.ndarray, weights: np.ndarray) -> np.ndarray:
+    """One-electron density of the two-electron ground state at the nodes:
+    n(x_a) = 2 sum_b Psi_ab^2 / W_a (each electron's marginal, the DVR
+    function of node a being 1/sqrt(W_a) there); sum_a W_a n(x_a) = 2."""
+    return 2.0 * np.sum(psi * psi, axis=1) / weights
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 and 3.2: observables
+# ---------------------------------------------------------------------------
+
+
+def density(g0m: np.ndarray, weights: np.ndarray, sigma: float) -> np.ndarray:
+    """One-electron density at the nodes from g(0^-) (Sec. 2.3: n(x) is the sum
+    over basis pairs of chi chi g(0^-)). A DVR function is 1/sqrt(W_a) at its own
+    node and zero at every other node, so only the diagonal survives there:
+    n(x_a) = sigma g_aa(0^-) / W_a.
+
+    Reading: g is the Green's function of one spin (sigma Tr g(0^-) = N, as in
+    the particle number), so the density carries sigma and integrates to N:
+    sum_a W_a n(x_a) = N."""
+    return sigma * np.diag(g0m) / weights
+
+
+def nuclear_repulsion(Z, R) -> float:
+    """E_nn = sum_{A<B} Z_A Z_B / |R_A - R_B| (bare Coulomb).
+
+    Reading (Eq. h3pv): the offset 5/d of the H3+ model collects the
+    internuclear energy; for unit charges at (-d/2, 0, d/2) it is exactly
+    1/(d/2) + 1/(d/2) + 1/d = 5/d. It is added once to the electronic energy
+    (not to the one-electron potential, which would count it per electron)."""
+    e = 0.0
+    for A in range(len(Z)):
+        for B in range(A + 1, len(Z)):
+            e += float(Z[A]) * float(Z[B]) / abs(float(R[A]) - float(R[B]))
+    return e

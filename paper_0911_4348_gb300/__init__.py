@@ -155,6 +155,15 @@ class Context:
         self._check(self._lib.fedvr_get_hf(self._h, _dptr(eps), _dptr(Cm), _dptr(rho), _dptr(S0)))
         return dict(eps=eps, C=Cm, rho0=rho, Sigma0=S0)
 
+    def density(self, source="2b"):
+        """One-electron density at the nodes, spin * g_aa(0^-) / W_a
+        (``fedvr_density``): source "hf" (last HF solution) or "2b" (current
+        second-Born iterate)."""
+        src = {"hf": 0, "2b": 1}[source]
+        out = np.empty(self.n_b)
+        self._check(self._lib.fedvr_density(self._h, src, _dptr(out)))
+        return out
+
     # -- second Born ------------------------------------------------------------
     def solve_2b(self, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200, precision=FP64,
                  G_out=None, Sigma_out=None, tau_out=None, check=True):

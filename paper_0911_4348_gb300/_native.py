@@ -27,6 +27,7 @@ SIGNATURES = {
     "fedvr_get_operators": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
     "solve_hf": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, _dp, _dp]),
     "fedvr_get_hf": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+    "fedvr_density": (C.c_int, [_vp, C.c_int, _dp]),
     "solve_2b": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                            C.c_int, C.c_int, _vp, _vp, _vp, _dp, _dp, _ip]),
     "fedvr_2b_prepare": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, C.c_int]),

@@ -578,7 +578,7 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
                     &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
                     &ctx->w_K32, &ctx->w_tab, &ctx->w_btab, &ctx->w_c1p,
-                    &ctx->w_coef32};
+                    &ctx->w_coef32, &ctx->w_h16, &ctx->w_xrow, &ctx->w_dens};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -796,6 +796,27 @@ int fedvr_get_hf(const fedvr_ctx *cctx, double *eps, double *C, double *rho0, do
   if (C) { if (int r = copy_out(ctx, C, ctx->b_C.ptr, dsz(nn), false)) return r; }
   if (rho0) { if (int r = copy_out(ctx, rho0, ctx->b_rho_new.ptr, dsz(nn), false)) return r; }
   if (Sigma0) { if (int r = copy_out(ctx, Sigma0, ctx->b_Sigma0.ptr, dsz(nn), false)) return r; }
+  return sync(ctx);
+}
+
+int fedvr_density(const fedvr_ctx *cctx, int source, double *n_out) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  CHECK_CTX(ctx);
+  if (!n_out) return fail(ctx, FEDVR_ERR_ARG, "n_out must not be NULL");
+  const double *g = nullptr;
+  if (source == FEDVR_DENSITY_HF) {
+    if (ctx->stage < 3) return fail(ctx, FEDVR_ERR_STATE, "no HF solution");
+    g = P<double>(ctx->b_rho_new);
+  } else if (source == FEDVR_DENSITY_2B) {
+    if (!ctx->prepared) return fail(ctx, FEDVR_ERR_STATE, "no prepared second-Born run");
+    g = P<double>(ctx->w_G) + (size_t)(ctx->M - 1) * ctx->n * ctx->n;  // g(0^-)
+  } else {
+    return fail(ctx, FEDVR_ERR_ARG, "source must be FEDVR_DENSITY_HF or FEDVR_DENSITY_2B");
+  }
+  ENSURE(ctx, w_dens, dsz(ctx->n));
+  FEDVR_CK(ctx, launch_density(ctx->n, g, P<double>(ctx->b_weights), ctx->spin,
+                               P<double>(ctx->w_dens), ctx->stream));
+  if (int r = copy_out(ctx, n_out, ctx->w_dens.ptr, dsz(ctx->n), false)) return r;
   return sync(ctx);
 }
 

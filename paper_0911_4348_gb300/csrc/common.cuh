@@ -78,7 +78,7 @@ struct fedvr_ctx {
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
       w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16,
-      w_xrow;
+      w_xrow, w_dens;
 };
 
 namespace fedvr {
@@ -193,6 +193,9 @@ cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, con
                             double *I2, float *t1, float *t2, cudaStream_t s);
 
 // update.cu
+// n_out[a] = spin g[a][a] / W[a] (density at the nodes from g(0^-)).
+cudaError_t launch_density(int n, const double *g, const double *W, double spin, double *n_out,
+                           cudaStream_t s);
 cudaError_t launch_update(int n, int M, double mixing, const double *G0, const double *I2,
                           double *G, unsigned long long *res_bits, cudaStream_t s);
 cudaError_t launch_axpby(size_t count, double a, const double *x, double b, const double *y,

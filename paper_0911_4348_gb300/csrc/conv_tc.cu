@@ -73,14 +73,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&full[0], 257);
-    tc::mbar_init(&full[1], 257);
+    tc::mbar_init(&full[0], 9);  // one arrival per producer warp + the TMA thread's
+    tc::mbar_init(&full[1], 9);
     tc::mbar_init(&empty[0], 1);
     tc::mbar_init(&empty[1], 1);
     tc::mbar_init(&accf[0], 1);
     tc::mbar_init(&accf[1], 1);
-    tc::mbar_init(&acce[0], 128);
-    tc::mbar_init(&acce[1], 128);
+    tc::mbar_init(&acce[0], 4);  // one arrival per flush warp
+    tc::mbar_init(&acce[1], 4);
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int k = 0; k < 4; ++k) off[k] = tc::sw128_offset(r0 + 32 * k, c);
     uint32_t cc = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+    for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
       // fields in registers: the asm statements below clobber memory, which would
@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int JB = S.JB;
       // chunks in the order (accumulation block, 32-wide column slice, mesh point),
       // as the MMA and TMA roles walk them
-      for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
+      for (int j0 = it.j_lo; j0 < it.j_hi && !tc::warp_flag(abort_flag); j0 += JB) {
         const int j1 = min(it.j_hi, j0 + JB);
-        for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+        for (int kc = 0; kc < KC && !tc::warp_flag(abort_flag); ++kc) {
           const int l0 = kc * 32 + 4 * c;
           const bool in = l0 < n;  // units past n are zero padding: not fetched
           float4 s1[4], s2[4];
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
-            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
               *abort_flag = 1;
               break;
             }
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               *reinterpret_cast<float4 *>(st + kTileA + off[k]) = lo;
             }
             tc::fence_smem_to_async();
-            tc::mbar_arrive(&full[s]);
+            tc::warp_arrive(&full[s]);
           }
         }
       }
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     float *stg = reinterpret_cast<float *>(smem + 2 * stage_bytes + 256) + warp * (32 * 17);
     const int cl = lane & 15, rh = lane >> 4;
     uint32_t tcount = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+    for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
       const int n = S.g.n, JB = S.JB;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j0 = it.j_lo; j0 < it.j_hi; j0 += JB, ++tcount) {
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
-        if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+        if (!tc::warp_wait(&accf[buf], tu & 1, kWaitNs)) {
           *abort_flag = 1;
           break;
         }
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
         }
         tc::fence_before_sync();
-        tc::mbar_arrive(&acce[buf]);
+        tc::warp_arrive(&acce[buf]);
       }
     }
   }
@@ -457,14 +457,14 @@ __global__ void __launch_bounds__(kThreadsH, 1)
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&full[0], 513);
-    tc::mbar_init(&full[1], 513);
+    tc::mbar_init(&full[0], 17);  // one arrival per producer warp + the TMA thread's
+    tc::mbar_init(&full[1], 17);
     tc::mbar_init(&empty[0], 1);
     tc::mbar_init(&empty[1], 1);
     tc::mbar_init(&accf[0], 1);
     tc::mbar_init(&accf[1], 1);
-    tc::mbar_init(&acce[0], 128);
-    tc::mbar_init(&acce[1], 128);
+    tc::mbar_init(&acce[0], 4);  // one arrival per flush warp
+    tc::mbar_init(&acce[1], 4);
     tc::mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kThreadsH, 1)
     const int pt = tid - 128, c = pt & 7, r0 = pt >> 3;
     const uint32_t off[2] = {tc::sw128_offset(r0, c), tc::sw128_offset(r0 + 64, c)};
     uint32_t cc = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+    for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
       const int n = S.g.n, ld = S.g.ld, M = S.g.M, KC = (n + 63) / 64;
@@ -503,9 +503,9 @@ __global__ void __launch_bounds__(kThreadsH, 1)
       const int JB = S.JB;
       // chunks in the order (accumulation block, 64-wide column slice, mesh point),
       // the two bracket rows of each row held in registers while the bracket stays
-      for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
+      for (int j0 = it.j_lo; j0 < it.j_hi && !tc::warp_flag(abort_flag); j0 += JB) {
         const int j1 = min(it.j_hi, j0 + JB);
-        for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+        for (int kc = 0; kc < KC && !tc::warp_flag(abort_flag); ++kc) {
           const int l0 = kc * 64 + 8 * c;
           const bool in = l0 < n;  // units starting past n are zero padding: not fetched
           int k1[2], k2[2];        // S32 rows held in a1, a2 (-1: none)
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(kThreadsH, 1)
             }
             const int s = cc & 1;
             const uint32_t use = cc >> 1;
-            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
               *abort_flag = 1;
               break;
             }
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kThreadsH, 1)
               *reinterpret_cast<uint4 *>(st + kTileA + off[k]) = lo;
             }
             tc::fence_smem_to_async();
-            tc::mbar_arrive(&full[s]);
+            tc::warp_arrive(&full[s]);
           }
         }
       }
@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(kThreadsH, 1)
   } else if (warp < 4) {
     // ---- flush: scale each FP32 block back and add it into the FP64 output rows ----
     uint32_t tcount = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+    for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
       const int n = S.g.n, JB = S.JB;
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(kThreadsH, 1)
       for (int j0 = it.j_lo; j0 < it.j_hi; j0 += JB, ++tcount) {
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
-        if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+        if (!tc::warp_wait(&accf[buf], tu & 1, kWaitNs)) {
           *abort_flag = 1;
           break;
         }
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(kThreadsH, 1)
           }
         }
         tc::fence_before_sync();
-        tc::mbar_arrive(&acce[buf]);
+        tc::warp_arrive(&acce[buf]);
       }
     }
   }

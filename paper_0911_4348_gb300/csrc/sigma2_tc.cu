@@ -123,18 +123,18 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&full[0], R::kProd * 32 + 1);
-    tc::mbar_init(&full[1], R::kProd * 32 + 1);
+    tc::mbar_init(&full[0], R::kProd + 1);  // one arrival per producer warp + the TMA's
+    tc::mbar_init(&full[1], R::kProd + 1);
     tc::mbar_init(&empty[0], 1);
     tc::mbar_init(&empty[1], 1);
     tc::mbar_init(&accf[0], 1);
     tc::mbar_init(&accf[1], 1);
-    tc::mbar_init(&acce[0], R::kEpi * 32);
-    tc::mbar_init(&acce[1], R::kEpi * 32);
+    tc::mbar_init(&acce[0], R::kEpi);  // one arrival per epilogue warp
+    tc::mbar_init(&acce[1], R::kEpi);
     tc::mbar_init(drain, 1);
     for (int q = 0; q < 2; ++q) {
-      tc::mbar_init(&pfull[q], 128);
-      tc::mbar_init(&pempty[q], 128);
+      tc::mbar_init(&pfull[q], 4);  // the four warps of one column half
+      tc::mbar_init(&pempty[q], 4);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     // FP16: 8 values of a 64-wide chunk) ----
     const int pt = tid - R::kEpi * 32, c = pt & 7, r0 = pt >> 3;
     uint32_t cc = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+    for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
       const int n = S.g.n, ld = S.g.ld, KC = (n + R::kCols - 1) / R::kCols;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         }
         const int s = cc & 1;
         const uint32_t use = cc >> 1;
-        if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+        if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
           *abort_flag = 1;
           break;
         }
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
           }
         }
         tc::fence_smem_to_async();
-        tc::mbar_arrive(&full[s]);
+        tc::warp_arrive(&full[s]);
       }
     }
   } else if (warp == R::kTma) {
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     //   Sigma_ab = sigma g_ab W_ab - sum_k V_ak g_kb P_ak,  W = V Q V ----
     const int quarter = warp & 3, half = warp >> 2, prow = quarter * 32 + lane;
     uint32_t tcount = 0;
-    for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
+    for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x, ++tcount) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
       const int n = S.g.n, ld = S.g.ld;
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       const int cb = half ? hc : 0, ce = half ? NC : hc;
       const int buf = tcount & 1;
       const uint32_t tu = tcount >> 1;
-      if (!tc::mbar_wait(&accf[buf], tu & 1, kWaitNs)) {
+      if (!tc::warp_wait(&accf[buf], tu & 1, kWaitNs)) {
         *abort_flag = 1;
         break;
       }
@@ -395,26 +395,26 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         }
       }
       tc::fence_before_sync();
-      tc::mbar_arrive(&acce[buf]);
+      tc::warp_arrive(&acce[buf]);
       const float xh = (acc0 + acc1) * inv;
       float *pb = part + buf * 128;
       if (half) {
         // hand the second half's sum to warp (warp - 4) through the buffer of this
         // tile's parity, once that warp has read the buffer's previous use
-        if (tu > 0 && !tc::mbar_wait(&pempty[buf], (tu - 1) & 1, kWaitNs)) {
+        if (tu > 0 && !tc::warp_wait(&pempty[buf], (tu - 1) & 1, kWaitNs)) {
           *abort_flag = 1;
           break;
         }
         pb[prow] = xh;
-        tc::mbar_arrive(&pfull[buf]);
+        tc::warp_arrive(&pfull[buf]);
         continue;
       }
-      if (!tc::mbar_wait(&pfull[buf], tu & 1, kWaitNs)) {
+      if (!tc::warp_wait(&pfull[buf], tu & 1, kWaitNs)) {
         *abort_flag = 1;
         break;
       }
       const float X = xh + pb[prow];
-      tc::mbar_arrive(&pempty[buf]);
+      tc::warp_arrive(&pempty[buf]);
       float sig = 0.f;
       if (live) sig = S.spin * gA[(long)a * ld + b] * S.W[((long)j * n + b) * ld + a] - X;
       if (S.smax) {  // largest |Sigma| entry, for the FP16 operand scale of the convolution

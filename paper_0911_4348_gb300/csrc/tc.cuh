@@ -58,6 +58,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Warp-collective forms, called by all 32 lanes of a converged warp. The wait
+// holds for the warp only if every lane's own (acquiring) wait succeeded, so a
+// timeout takes the whole warp out of its loop together; the arrival is one
+// per warp (the barrier counts warps), made by lane 0 after a warp barrier
+// that orders every lane's earlier shared-memory writes before it.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, limit_ns));
+}
+__device__ __forceinline__ void warp_arrive(uint64_t *bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+// A flag in shared memory read as one value for the whole warp.
+__device__ __forceinline__ bool warp_flag(const volatile int *f) {
+  return __any_sync(0xffffffffu, *f != 0);
+}
+
 // Arrive and announce tx_bytes of asynchronous copies that will complete on bar.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t tx_bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),

@@ -200,7 +200,22 @@ __global__ void axpby_kernel(size_t count, double a, const double *__restrict__ 
     out[i] = a * x[i] + b * y[i];
 }
 
+// One-electron density at the nodes (Sec. 2.3): n(x) sums chi chi g(0^-) over
+// basis pairs, and a DVR function is 1/sqrt(W_a) at its own node and zero at the
+// others, so n(x_a) = spin g_aa(0^-) / W_a (g per spin, N = spin Tr g(0^-)).
+__global__ void density_kernel(int n, const double *__restrict__ g, const double *__restrict__ W,
+                               double spin, double *__restrict__ out) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) out[a] = spin * g[(size_t)a * n + a] / W[a];
+}
+
 }  // namespace
+
+cudaError_t launch_density(int n, const double *g, const double *W, double spin, double *out,
+                           cudaStream_t s) {
+  density_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, g, W, spin, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_axpby(size_t count, double a, const double *x, double b, const double *y,
                          double *out, cudaStream_t s) {

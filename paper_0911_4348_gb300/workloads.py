@@ -97,6 +97,18 @@ def h3p_large(system_id: int = 0) -> System:
     return System("H3+ n_b=299 M=1025", -60.0, 60.0, 30, 10, [1.0, 1.0, 1.0], R, u=32, p=16)
 
 
+def h3p_curve(Rs=None) -> list[System]:
+    """The paper's H3+ binding-curve grid (Sec. 3.2): 13 graded (case II)
+    elements of order 11 over a 50 a.u. interval (n_b = 142), beta = 100,
+    1025-point mesh (u = 32, p = 16); symmetric unit nuclei at (-R, 0, R) for
+    each R (default 1.6, 1.8, ..., 3.6, i.e. outer distance d = 2R from 3.2 to
+    7.2)."""
+    if Rs is None:
+        Rs = [1.6 + 0.2 * k for k in range(11)]
+    return [System(f"H3+ R={R:.3f}", -25.0, 25.0, 13, 11, [1.0, 1.0, 1.0], [-R, 0.0, R], u=32,
+                   p=16, grid_kind=1) for R in Rs]
+
+
 def batch_systems(count: int = 64, config_id: int = 4) -> list[System]:
     """Uneven batch: half He (Z ~ U[1.5,2.5], box [-50,50]), half H3+
     (R ~ U[1.2,3.0], box [-60,60]); order ~ U{4..10},

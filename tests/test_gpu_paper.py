@@ -35,3 +35,54 @@ def test_he_case2_second_born_matches_paper():
     assert abs(r["N"] - 2.0) < 1e-5
     frac = (r["E0"] - E_hf) / (gold["he_exact_Ha"] - E_hf)
     assert abs(frac - gold["he_2b_corr_fraction"]) < 0.01
+
+
+FIG2A = [(1, 29, 7), (1, 13, 15), (1, 21, 10), (1, 41, 7), (1, 25, 12),
+         (0, 25, 8), (0, 40, 5), (0, 20, 10), (0, 30, 10)]
+
+
+def test_fig2a_hf_sweep_matches_oracle():
+    """Sec. 3.1, Fig. 2a: HF energies of He on the 200 a.u. interval for graded
+    (case II) and equal (case I) elements, n_b 194-299, from the GPU equal the
+    oracle's to 1e-10 Ha (the oracle test pins the sweep itself to the printed
+    HF limit)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import numpy as np
+    from oracle import fedvr_oracle as O
+    from paper_0911_4348_gb300 import Context
+    for kind, ne, ng in FIG2A:
+        c = Context()
+        c.build_fedvr(ne, ng, -100.0, 100.0, kind)
+        c.set_potential([2.0], [0.0], 1.0, 1.0, 2)
+        E_gpu, _ = c.solve_hf(100.0, tol=1e-12)
+        c.close()
+        b = O.fedvr_basis(ne, ng, -100.0, 100.0, kind)
+        v = O.potential(b["nodes"], [2.0], [0.0], 1.0)
+        V = O.interaction(b["nodes"], 1.0)
+        E_ref = O.hf_scf(O.kinetic(b) + np.diag(v), V, 2.0, 1, 100.0, tol=1e-12)["E_hf"]
+        assert abs(E_gpu - E_ref) < 1e-10, (kind, ne, ng)
+
+
+def test_fig2b_second_born_converges_with_the_mesh():
+    """Sec. 3.1, Fig. 2b: second-Born energy of He on the 29 x 7 case II grid
+    against the mesh size 2up + 1 (p = 16): the differences between successive
+    doublings of u shrink (the quadrature converges) and the 1025- and
+    2049-point meshes land within 2e-6 Ha of the printed value."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Context
+    gold = load_golden("paper_values.txt")
+    E = {}
+    for u in (8, 16, 32, 64):
+        c = Context()
+        c.build_fedvr(29, 7, -100.0, 100.0, 1)
+        c.set_potential([2.0], [0.0], 1.0, 1.0, 2)
+        c.solve_hf(100.0, tol=1e-12)
+        r = c.solve_2b(100.0, u, 16, 0.5, 1e-8, 300, precision=3)
+        c.close()
+        assert r["status"] == 0 and abs(r["N"] - 2.0) < 1e-5
+        E[u] = r["E0"]
+    d1, d2, d3 = abs(E[16] - E[8]), abs(E[32] - E[16]), abs(E[64] - E[32])
+    assert d2 < d1 and d3 < d2
+    assert abs(E[32] - gold["he_2b_Ha"]) < 2e-6 and abs(E[64] - gold["he_2b_Ha"]) < 2e-6

@@ -109,3 +109,29 @@ def test_paper_hf_limit_and_exact_energy_case2_grid():
     assert abs(Eex - PAPER["he_exact_Ha"]) < 2e-7
     # exact energy is below HF (correlation energy negative)
     assert Eex < hf["E_hf"]
+
+
+# Sec. 3.1, Fig. 2a: HF energy of He on the 200 a.u. interval against the basis
+# size. On the graded (case II) grid the energy is converged to the printed HF
+# limit at 200-300 basis functions; on equal (case I) elements it depends
+# strongly on (n_e, n_g) and stays orders of magnitude further away at the
+# same sizes.
+FIG2A_CASE2 = [(29, 7), (13, 15), (21, 10), (41, 7), (25, 12)]   # n_b 194-299
+FIG2A_CASE1 = [(25, 8), (40, 5), (20, 10), (30, 10)]             # n_b 199-299
+
+
+def _he_hf_200(n_elem, order, grid_kind):
+    b = O.fedvr_basis(n_elem, order, -100.0, 100.0, grid_kind)
+    v = O.potential(b["nodes"], [2.0], [0.0], 1.0)
+    V = O.interaction(b["nodes"], 1.0)
+    return O.hf_scf(O.kinetic(b) + np.diag(v), V, 2.0, 1, 100.0, tol=1e-12)["E_hf"]
+
+
+def test_fig2a_case2_converges_at_200_to_300_functions_case1_does_not():
+    lim = PAPER["he_hf_limit_Ha"]
+    err2 = [abs(_he_hf_200(ne, ng, 1) - lim) for ne, ng in FIG2A_CASE2]
+    err1 = [abs(_he_hf_200(ne, ng, 0) - lim) for ne, ng in FIG2A_CASE1]
+    # the limit is printed to 1e-7: every case II grid reaches it at that level
+    assert max(err2) < 2e-7
+    # case I at the same sizes: at least two orders of magnitude further away
+    assert min(err1) > 100 * max(err2)
