@@ -54,7 +54,7 @@ def algorithmic(stage: str, n: int, M: int) -> float:
     if stage == "sigma2":
         return M * (1.0 * n ** 4 + 4.0 * n ** 3)  # symmetric exchange half + direct term
     if stage == "conv2":
-        return 2.0 * M * M * n * n + 8.0 * M * n ** 3
+        return 2.0 * M * M * n * n + 4.0 * M * n ** 3  # left transform, eigen-kernel, back
     return 0.0
 
 

@@ -372,7 +372,9 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
 
 /* Second Dyson convolution (Eq. deq): I2_i = int g^0(tau_i - t) I1(t) dt with
  * g^0(x) = C diag(phi(x)) C^T evaluated exactly at every lag (Eq. hfgf), same
- * split trapezoid (g^0(0^+) = -g^0(-beta)); computed in the HF eigenbasis.
+ * split trapezoid (g^0(0^+) = -g^0(-beta)); computed as
+ * I2_i = C sum_j diag(w_ij phi(tau_i - tau_j)) C^T I1_j, i.e. with the left
+ * index in the HF eigenbasis (three products).
  * eps [n] (ascending not required), C [n][n], I1 [M][n][n] device inputs;
  * I2 [M][n][n] device output. */
 int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *eps,

@@ -320,7 +320,7 @@ cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t 
   return cudaGetLastError();
 }
 
-// FP32 variant of conv2_apply for the split-precision mode: the same five
+// FP32 variant of conv2_apply for the split-precision mode: the same three
 // products with float arithmetic (K32 is the eigen-kernel table in FP32,
 // t1/t2 float scratch of M*n*n), FP64 I1 in and FP64 I2 out.
 cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
@@ -329,29 +329,20 @@ cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, con
   const int Mn = M * n;
   cudaError_t e;
   if (n < 96) {  // small matrices: 64 x 64 tiles, one GEMM per mesh point
-    e = gemm32<true, false>(n, n, n, C, n, 0, I1, n, nn, t1, n, nn, M, s);
-    if (e != cudaSuccess) return e;
-    e = gemm32<false, false>(n, n, n, (const float *)t1, n, nn, C, n, 0, t2, n, nn, M, s);
+    e = gemm32<true, false>(n, n, n, C, n, 0, I1, n, nn, t2, n, nn, M, s);
     if (e != cudaSuccess) return e;
     e = gemm32<false, false>(M, n, M, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
     if (e != cudaSuccess) return e;
-    e = gemm32<false, false>(n, n, n, C, n, 0, (const float *)t1, n, nn, t2, n, nn, M, s);
-    if (e != cudaSuccess) return e;
-    return gemm32<false, true>(n, n, n, (const float *)t2, n, nn, C, n, 0, I2, n, nn, M, s);
+    return gemm32<false, false>(n, n, n, C, n, 0, (const float *)t1, n, nn, I2, n, nn, M, s);
   }
-  // u_j = I1_j C for all j: one tall GEMM over the [M n][n] stack
-  e = sgemm128<false, false>(Mn, n, n, 0, I1, n, 0, C, n, 0, t1, n, 0, 1, s);
-  if (e != cudaSuccess) return e;
-  // I1~_j = C^T u_j: one wide GEMM over the stacked columns (j, b)
-  e = sgemm128<true, false>(n, Mn, n, n, C, n, 0, (const float *)t1, n, nn, t2, n, nn, 1, s);
+  // I1~_j = C^T I1_j: one wide GEMM over the stacked columns (j, b)
+  e = sgemm128<true, false>(n, Mn, n, n, C, n, 0, I1, n, nn, t2, n, nn, 1, s);
   if (e != cudaSuccess) return e;
   // t[i][a][:] = sum_j K_a[i][j] I1~[j][a][:], batched over a
   e = sgemm128<false, false>(M, n, M, 0, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
   if (e != cudaSuccess) return e;
-  // v_i = t_i C^T (tall), I2_i = C v_i (wide)
-  e = sgemm128<false, true>(Mn, n, n, 0, (const float *)t1, n, 0, C, n, 0, t2, n, 0, 1, s);
-  if (e != cudaSuccess) return e;
-  return sgemm128<false, false>(n, Mn, n, n, C, n, 0, (const float *)t2, n, nn, I2, n, nn, 1, s);
+  // I2_i = C t_i: one wide GEMM
+  return sgemm128<false, false>(n, Mn, n, n, C, n, 0, (const float *)t1, n, nn, I2, n, nn, 1, s);
 }
 
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
@@ -374,18 +365,16 @@ cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const do
                         double *I2, double *t1, double *t2, cudaStream_t s) {
   long nn = (long)n * n, MM = (long)M * M;
   cudaError_t e;
-  // t1_j = C^T I1_j ; t2_j = t1_j C   (eigenbasis)
+  // g0(x) = C diag(phi(x)) C^T acts on I1 from the left only, so only the left
+  // index goes to the HF eigenbasis (the right-hand C C^T = 1 drops out):
+  // t1_j = C^T I1_j
   e = dgemm(true, false, n, n, n, 1.0, C, n, 0, I1, n, nn, nullptr, 0, 0.0, t1, n, nn, M, s);
   if (e != cudaSuccess) return e;
-  e = dgemm(false, false, n, n, n, 1.0, t1, n, nn, C, n, 0, nullptr, 0, 0.0, t2, n, nn, M, s);
+  // t2[i][a][:] = sum_j K_a[i][j] t1[j][a][:]   (batched over a)
+  e = dgemm(false, false, M, n, M, 1.0, K, M, MM, t1, nn, n, nullptr, 0, 0.0, t2, nn, n, n, s);
   if (e != cudaSuccess) return e;
-  // t1[i][a][:] = sum_j K_a[i][j] t2[j][a][:]   (batched over a)
-  e = dgemm(false, false, M, n, M, 1.0, K, M, MM, t2, nn, n, nullptr, 0, 0.0, t1, nn, n, n, s);
-  if (e != cudaSuccess) return e;
-  // I2_i = C t1_i C^T
-  e = dgemm(false, false, n, n, n, 1.0, C, n, 0, t1, n, nn, nullptr, 0, 0.0, t2, n, nn, M, s);
-  if (e != cudaSuccess) return e;
-  return dgemm(false, true, n, n, n, 1.0, t2, n, nn, C, n, 0, nullptr, 0, 0.0, I2, n, nn, M, s);
+  // I2_i = C t2_i
+  return dgemm(false, false, n, n, n, 1.0, C, n, 0, t2, n, nn, nullptr, 0, 0.0, I2, n, nn, M, s);
 }
 
 }  // namespace fedvr
