@@ -164,6 +164,11 @@ int tc_workspace(fedvr_ctx *ctx, int n, int M, float **ws, float **S32, int **er
   return FEDVR_OK;
 }
 
+int tc_err_ptr(fedvr_ctx *ctx, int **err) {
+  float *ws, *S32;
+  return tc_workspace(ctx, ctx->n, ctx->M, &ws, &S32, err);
+}
+
 bool is_split(int precision) {
   return precision == FEDVR_SPLIT_TF32 || precision == FEDVR_SPLIT_F16;
 }
@@ -323,7 +328,8 @@ int choose_conv1_splits(fedvr_ctx *ctx, float *ws, float *S32, int *err) {
 
 // The pieces of one iteration for one system, enqueued on stream s.
 // (1) Sigma^(2): operand preparation (split path) or the whole FP64 build.
-int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches) {
+// err: device flag that the split path's tensor-core kernels raise on a timeout.
+int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, int *err) {
   const int n = ctx->n, M = ctx->M;
   const size_t stack = (size_t)M * n * n;
   double *G = P<double>(ctx->w_G), *S = P<double>(ctx->w_S);
@@ -353,9 +359,9 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches) {
     }
   } else if (is_split(ctx->precision)) {
     float *ws, *S32;
-    int *err;
-    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &err)) return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale));
+    int *own_err;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &own_err)) return r;
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale, err ? err : own_err));
     *launches += 4;  // splits of g and V, VQ, W = (VQ) V
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
@@ -401,18 +407,21 @@ int phase_conv1_fp64(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
 }
 
 // (4) second convolution.
-int phase_conv2(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
+int phase_conv2(fedvr_ctx *ctx, cudaStream_t s, int *launches, int *err) {
   const int n = ctx->n, M = ctx->M;
   const double *C = P<double>(ctx->b_C);
   double *I1 = P<double>(ctx->w_I1), *I2 = P<double>(ctx->w_I2);
   if (is_split(ctx->precision)) {
+    if (!err) {
+      if (int r = tc_err_ptr(ctx, &err)) return r;
+    }
     FEDVR_CK(ctx, conv2_apply_f32(n, M, P<float>(ctx->w_K32), C, I1, I2, P<float>(ctx->w_t1),
-                                  P<float>(ctx->w_t2), s));
+                                  P<float>(ctx->w_t2), err, s));
   } else {
     FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, P<double>(ctx->w_t1),
                               P<double>(ctx->w_t2), s));
   }
-  *launches += 5;
+  *launches += 3;
   return FEDVR_OK;
 }
 
@@ -427,11 +436,6 @@ int phase_update(fedvr_ctx *ctx, double mixing, cudaStream_t s, int *launches) {
   return FEDVR_OK;
 }
 
-int tc_err_ptr(fedvr_ctx *ctx, int **err) {
-  float *ws, *S32;
-  return tc_workspace(ctx, ctx->n, ctx->M, &ws, &S32, err);
-}
-
 // Enqueue one iteration on s without host synchronisation, recording the
 // stage events with evflags (cudaEventRecordExternal inside a capture).
 int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsigned evflags,
@@ -443,7 +447,7 @@ int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsig
     if (int r = tc_err_ptr(ctx, &err)) return r;
   }
   FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[1], s, evflags));
-  if (int r = phase_sigma_pre(ctx, warm, s, launches)) return r;
+  if (int r = phase_sigma_pre(ctx, warm, s, launches, err)) return r;
   uint8_t *tab = P<uint8_t>(ctx->w_tab);
   if (split && !warm) {
     const TcGeom g = tc_geom(n, M);
@@ -462,7 +466,7 @@ int enqueue_step(fedvr_ctx *ctx, bool warm, double mixing, cudaStream_t s, unsig
     if (int r = phase_conv1_fp64(ctx, s, launches)) return r;
   }
   FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[4], s, evflags));
-  if (int r = phase_conv2(ctx, s, launches)) return r;
+  if (int r = phase_conv2(ctx, s, launches, err)) return r;
   FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[5], s, evflags));
   if (int r = phase_update(ctx, mixing, s, launches)) return r;
   FEDVR_CK(ctx, cudaEventRecordWithFlags(ctx->ev[6], s, evflags));
@@ -515,11 +519,13 @@ int fedvr::sigma_of_current_g(fedvr_ctx *ctx) {
   if (!ctx->prepared) return fail(ctx, FEDVR_ERR_STATE, "no prepared second-Born run");
   cudaStream_t s = ctx->stream;
   int launches = 0;
-  if (int r = phase_sigma_pre(ctx, false, s, &launches)) return r;
+  int *err = nullptr;
   if (is_split(ctx->precision)) {
-    int *err = nullptr;
     if (int r = tc_err_ptr(ctx, &err)) return r;
     FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+  }
+  if (int r = phase_sigma_pre(ctx, false, s, &launches, err)) return r;
+  if (is_split(ctx->precision)) {
     const TcGeom g = tc_geom(ctx->n, ctx->M);
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),
@@ -1101,7 +1107,7 @@ int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t
   int *d_err = reinterpret_cast<int *>(bt + B->off_err);
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
-      if (int r = phase_sigma_pre(B->ctxs[k], false, s, launches)) return r;
+      if (int r = phase_sigma_pre(B->ctxs[k], false, s, launches, d_err)) return r;
     }
   FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
                                     reinterpret_cast<const long *>(bt + B->off_px), n_sys,
@@ -1120,7 +1126,7 @@ int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
       fedvr_ctx *c = B->ctxs[k];
-      if (int r = phase_conv2(c, s, launches)) return r;
+      if (int r = phase_conv2(c, s, launches, d_err)) return r;
       if (int r = phase_update(c, mixing, s, launches)) return r;
       FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_red + (size_t)k * 3 * sizeof(double),
                                      c->w_red.ptr, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1447,7 +1453,7 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
     if (int r = upload_single_tables(ctx, n, M, ws, Sigma, nullptr, nullptr, nullptr, nullptr, 1,
                                      nullptr, spin))
       return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !f16));
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !f16, err));
     const TcGeom g = tc_geom(n, M);
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),

@@ -155,12 +155,6 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
 
 // tmap.cu: 3-D TMA map over [M][n][ld] floats, box 32 x rows x 1, 128B swizzle,
 // rows beyond n read as zero.
-// VQ[j] = V32 (g32[j] o g32[M-1-j]) in FP32 for all j (rows padded to ld).
-cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, float *VQ,
-                      cudaStream_t s);
-// W[j] = VQ[j] V (rows of ld floats; columns past n not written).
-cudaError_t launch_vqv(int n, int M, int ld, const float *VQ, const float *V32, float *W,
-                       cudaStream_t s);
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows,
                            int box_cols = 32);
 cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, int ld16, int rows);
@@ -190,7 +184,7 @@ cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const do
 
 cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s);
 cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
-                            double *I2, float *t1, float *t2, cudaStream_t s);
+                            double *I2, float *t1, float *t2, int *err, cudaStream_t s);
 
 // update.cu
 // n_out[a] = spin g[a][a] / W[a] (density at the nodes from g(0^-)).

@@ -6,10 +6,13 @@
 // folded into c1, c2) and B_ii = dHF - wm_i A_0 + wp_i A_{M-1} (split trapezoid
 // at the jump). One block owns a 64x64 tile of one I1_i and streams over j.
 //
-// I2 is evaluated in the HF eigenbasis, where g^0 is diagonal:
-// I2~_i,ab = sum_j K_a(i,j) I1~_j,ab with K_a(i,j) the exact g^0 eigen-factor at
-// the lag times the same split-trapezoid weights, I1~ = C^T I1 C, I2 = C I2~ C^T.
+// I2 is evaluated with its left index in the HF eigenbasis, where g^0 is
+// diagonal (g^0 multiplies I1 from the left, so the right index needs no
+// transform): I2~_i,ab = sum_j K_a(i,j) I1~_j,ab with K_a(i,j) the exact g^0
+// eigen-factor at the lag times the same split-trapezoid weights,
+// I1~ = C^T I1, I2 = C I2~.
 #include "common.cuh"
+#include "tc_sys.cuh"
 
 #include <math.h>
 
@@ -187,133 +190,7 @@ cudaError_t gemm32(int M, int N, int K, const Ta *A, long lda, long sA, const Tb
   return cudaGetLastError();
 }
 
-// FP32 GEMM with 128 x 128 tiles, 8 x 8 outputs per thread, 8-deep K slices
-// double-buffered in shared memory: Cm[m][q] = sum_k op(A)[m][k] op(B)[k][q],
-// operands converted to float on load, result stored as To. With nb > 0 the
-// columns q of B and C are stacked blocks of nb columns (q = blk * nb + col,
-// element blk * sB + k * ldb + col), which turns the per-mesh-point left
-// products C^T X_j of a [M][n][n] stack into one wide GEMM; blockIdx.z walks an
-// ordinary batch (strides sA/sB/sC) when nb = 0.
-//
-// With MUL2 (stacked columns only) the B element of block blk is the product
-// B[blk] o B2[nblk - 1 - blk] (used for V (g o gb) without forming g o gb).
-template <bool TA, bool TB, typename Ta, typename Tb, typename To, bool MUL2 = false>
-__global__ void __launch_bounds__(256) sgemm128_kernel(int M, int N, int K, int nb,
-                                                       const Ta *__restrict__ A, long lda, long sA,
-                                                       const Tb *__restrict__ B, long ldb, long sB,
-                                                       To *__restrict__ C, long ldc, long sC,
-                                                       const Tb *__restrict__ B2 = nullptr,
-                                                       int nblk = 0) {
-  if (nb == 0) {
-    const long bz = blockIdx.z;
-    A += bz * sA;
-    B += bz * sB;
-    C += bz * sC;
-  }
-  __shared__ __align__(16) float As[2][8][128];
-  __shared__ __align__(16) float Bs[2][8][128];
-  const int tid = threadIdx.x;
-  const int m0 = blockIdx.y * 128, q0 = blockIdx.x * 128;
-  // loader coordinates: 4 elements of each 8 x 128 slice per thread
-  const int lr = tid >> 5, lc = (tid & 31) * 4;  // slice row (k), first of 4 columns (m or q)
-  auto b_off = [&](int q) -> long {               // element offset of column q in B / C
-    if (nb > 0) return (long)(q / nb) * sB + (q % nb);
-    return q;
-  };
-  float ra[4], rb[4];
-  auto load = [&](int k0) {
-    const int k = k0 + lr;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int m = m0 + lc + t, q = q0 + lc + t;
-      ra[t] = (m < M && k < K) ? (float)(TA ? A[(long)k * lda + m] : A[(long)m * lda + k]) : 0.f;
-      if (MUL2) {
-        const int blk = q / nb;
-        const long o1 = (long)blk * sB + (long)k * ldb + (q % nb);
-        const long o2 = (long)(nblk - 1 - blk) * sB + (long)k * ldb + (q % nb);
-        rb[t] = (q < N && k < K) ? (float)B[o1] * (float)B2[o2] : 0.f;
-      } else {
-        rb[t] = (q < N && k < K)
-                    ? (float)(TB ? B[(long)q * ldb + k] : B[(long)k * ldb + b_off(q)])
-                    : 0.f;
-      }
-    }
-  };
-  auto stash = [&](int buf) {
-    *reinterpret_cast<float4 *>(&As[buf][lr][lc]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
-    *reinterpret_cast<float4 *>(&Bs[buf][lr][lc]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-  };
-  // compute coordinates: rows ty*4 + {0..3, 64..67}, columns tx*4 + {0..3, 64..67}
-  const int tx = tid & 15, ty = tid >> 4;
-  float acc[8][8] = {};
-  load(0);
-  stash(0);
-  __syncthreads();
-  int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += 8) {
-    const bool more = k0 + 8 < K;
-    if (more) load(k0 + 8);
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
-      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
-      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
-    }
-    if (more) {
-      stash(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int m = m0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
-    if (m >= M) continue;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int col = q0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
-      if (col >= N) continue;
-      const long off = nb > 0 ? (long)(col / nb) * sC + (col % nb) : col;
-      C[(long)m * ldc + off] = (To)acc[r][q];
-    }
-  }
-}
-
-template <bool TA, bool TB, typename Ta, typename Tb, typename To>
-cudaError_t sgemm128(int M, int N, int K, int nb, const Ta *A, long lda, long sA, const Tb *B,
-                     long ldb, long sB, To *C, long ldc, long sC, int batch, cudaStream_t s) {
-  dim3 grid((N + 127) / 128, (M + 127) / 128, nb > 0 ? 1 : batch);
-  sgemm128_kernel<TA, TB, Ta, Tb, To><<<grid, 256, 0, s>>>(M, N, K, nb, A, lda, sA, B, ldb, sB, C,
-                                                          ldc, sC);
-  return cudaGetLastError();
-}
-
 }  // namespace
-
-cudaError_t launch_vq(int n, int M, int ld, const float *V32, const float *g32, float *VQ,
-                      cudaStream_t s) {
-  // VQ[j] = V (g_j o g_{M-1-j}) for all j: one wide GEMM over the stacked
-  // columns (j, c), c < ld (padded columns of g are zero, so are those of VQ)
-  const long nld = (long)n * ld;
-  dim3 grid((unsigned)(((long)M * ld + 127) / 128), (unsigned)((n + 127) / 128), 1);
-  sgemm128_kernel<false, false, float, float, float, true><<<grid, 256, 0, s>>>(
-      n, M * ld, n, ld, V32, ld, 0, g32, ld, nld, VQ, ld, nld, g32, M);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_vqv(int n, int M, int ld, const float *VQ, const float *V32, float *W,
-                       cudaStream_t s) {
-  // W[j] = VQ[j] V for all j: the stacked rows (j, b) of VQ times V, one tall GEMM
-  return sgemm128<false, false, float, float, float>(M * n, n, n, 0, VQ, ld, 0, V32, ld, 0, W, ld,
-                                                     0, 1, s);
-}
 
 cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s) {
   to_f32_kernel<<<1024, 256, 0, s>>>(count, x, y);
@@ -321,12 +198,13 @@ cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t 
 }
 
 // FP32 variant of conv2_apply for the split-precision mode: the same three
-// products with float arithmetic (K32 is the eigen-kernel table in FP32,
-// t1/t2 float scratch of M*n*n), FP64 I1 in and FP64 I2 out.
+// products, split TF32 on the tensor cores for n >= 96 (conv2_tc) and FP32 on
+// the CUDA cores below (K32 is the eigen-kernel table in FP32, t1/t2 float
+// scratch of M*n*n), FP64 I1 in and FP64 I2 out; err is raised if a
+// tensor-core wait gives up.
 cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
-                            double *I2, float *t1, float *t2, cudaStream_t s) {
+                            double *I2, float *t1, float *t2, int *err, cudaStream_t s) {
   const long nn = (long)n * n, MM = (long)M * M;
-  const int Mn = M * n;
   cudaError_t e;
   if (n < 96) {  // small matrices: 64 x 64 tiles, one GEMM per mesh point
     e = gemm32<true, false>(n, n, n, C, n, 0, I1, n, nn, t2, n, nn, M, s);
@@ -335,14 +213,7 @@ cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, con
     if (e != cudaSuccess) return e;
     return gemm32<false, false>(n, n, n, C, n, 0, (const float *)t1, n, nn, I2, n, nn, M, s);
   }
-  // I1~_j = C^T I1_j: one wide GEMM over the stacked columns (j, b)
-  e = sgemm128<true, false>(n, Mn, n, n, C, n, 0, I1, n, nn, t2, n, nn, 1, s);
-  if (e != cudaSuccess) return e;
-  // t[i][a][:] = sum_j K_a[i][j] I1~[j][a][:], batched over a
-  e = sgemm128<false, false>(M, n, M, 0, K32, M, MM, (const float *)t2, nn, n, t1, nn, n, n, s);
-  if (e != cudaSuccess) return e;
-  // I2_i = C t_i: one wide GEMM
-  return sgemm128<false, false>(n, Mn, n, n, C, n, 0, (const float *)t1, n, nn, I2, n, nn, 1, s);
+  return conv2_tc(n, M, K32, C, I1, I2, t1, t2, err, s);
 }
 
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,

@@ -501,7 +501,7 @@ int sigma2_tc_max_n() {
 }
 
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
-                          cudaStream_t s, bool tf32_operands) {
+                          cudaStream_t s, bool tf32_operands, int *err) {
   const int ld = (n + 31) / 32 * 32;
   const long stack = (long)M * n * ld;
   float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *VQ = ws + 3 * stack;
@@ -512,9 +512,8 @@ cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float 
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_vq(n, M, ld, V32, g32, VQ, s);
-  if (e != cudaSuccess) return e;
-  return launch_vqv(n, M, ld, VQ, V32, ws + tc_ws_w(n, M), s);
+  // VQ_j = V (g_j o g_{M-1-j}) and W_j = VQ_j V on the tensor cores
+  return vqv_tc(n, M, ld, V32, g32, VQ, ws + tc_ws_w(n, M), err, s);
 }
 
 void exchange_row_table(int n, std::vector<uint32_t> &rows) {

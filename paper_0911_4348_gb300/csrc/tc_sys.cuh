@@ -117,9 +117,17 @@ inline size_t tc_ws_floats(int n, int M) { return tc_ws_w(n, M) + tc_ws_stack(n,
 
 // Per-system preparation of the exchange operands (FP32 copies of G and V,
 // VQ and W = (VQ) V, and with tf32_operands the TF32 split of G for the gb
-// operand).
+// operand); err is raised if a tensor-core wait gives up.
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
-                          cudaStream_t s, bool tf32_operands = true);
+                          cudaStream_t s, bool tf32_operands, int *err);
+// Split-TF32 tensor-core products (gemm_tc.cu). vqv_tc: VQ_j = V (g_j o
+// g_{M-1-j}) and W_j = VQ_j V for all j (FP32 stacks of row pitch ld).
+// conv2_tc: I2_i = C sum_j diag(K(i, j)) C^T I1_j as three products (K32 the
+// FP32 eigen-kernel table [n][M][M], t1/t2 FP32 scratch of M n n).
+cudaError_t vqv_tc(int n, int M, int ld, const float *V32, const float *g32, float *VQ, float *W,
+                   int *err, cudaStream_t s);
+cudaError_t conv2_tc(int n, int M, const float *K32, const double *C, const double *I1,
+                     double *I2, float *t1, float *t2, int *err, cudaStream_t s);
 // Persistent launches over a device table of n_sys systems; prefix[n_sys + 1]
 // (device) holds the cumulative work items; Np_max/ld_max size the stages.
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
