@@ -278,15 +278,10 @@ cudaError_t gemm_tf32x3(GemmArgs p, int batch, cudaStream_t s) {
   p.tcols = 32;
   while (p.tcols < p.Nt) p.tcols *= 2;
   const size_t smem = 2 * (2 * (size_t)kTileA + 2 * (size_t)p.Nt * 128) + 1024 + 128;
-  static bool configured = false;  // one attribute call per instantiation (max size)
-  if (!configured) {
-    const size_t max_smem = 2 * (2 * (size_t)kTileA + 2 * 256 * 128) + 1024 + 128;
-    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<TA, TB, TO, A_MC, B_MC, MUL2>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)max_smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // set on every call: the attribute belongs to the current device
+  cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<TA, TB, TO, A_MC, B_MC, MUL2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((p.R + 127) / 128), (unsigned)ntile, (unsigned)batch);
   gemm_tf32x3_kernel<TA, TB, TO, A_MC, B_MC, MUL2><<<grid, kThreads, smem, s>>>(p);
   return cudaGetLastError();
