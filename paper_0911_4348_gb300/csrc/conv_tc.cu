@@ -675,17 +675,22 @@ __global__ void __launch_bounds__(kThreadsH, 1)
       }
     }
   } else if (warp < 4) {
-    // ---- flush: scale each FP32 block back and add it into the FP64 output rows ----
+    // ---- flush: scale each FP32 block back and add it into the FP64 output rows.
+    // TMEM gives each thread one row; a warp-private 32 x 16 staging tile turns
+    // that into row-contiguous read-modify-writes (16 columns of two rows per
+    // instruction) ----
+    float *stg = reinterpret_cast<float *>(smem + 2 * stage_bytes + 256) + warp * (32 * 17);
+    const int cl = lane & 15, rh = lane >> 4;
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const C1Sys &S = sys[cur];
       const int n = S.g.n, JB = S.JB;
       const double inv = ldexp(1.0, -(a_scale_exp(S.scale) + kScaleG));
+      const long R = (long)S.g.M * n;
       const C1Item it = c1_item(S, w - prefix[cur]);
-      const long r = (long)it.t * 128 + warp * 32 + lane;
-      const bool live = r < (long)S.g.M * n;
-      double *row = it.out + (live ? r : 0) * n;
+      const long row0 = (long)it.t * 128 + warp * 32;
+      double *const out = it.out;
       for (int j0 = it.j_lo; j0 < it.j_hi; j0 += JB, ++tcount) {
         const int buf = tcount & 1;
         const uint32_t tu = tcount >> 1;
@@ -699,13 +704,21 @@ __global__ void __launch_bounds__(kThreadsH, 1)
         for (int c0 = 0; c0 < n; c0 += 16) {
           float v[16];
           tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-          if (live) {
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
-              const int b = c0 + t;
-              if (b < n) row[b] = first ? (double)v[t] * inv : row[b] + (double)v[t] * inv;
+          for (int t = 0; t < 16; ++t) stg[lane * 17 + t] = v[t];
+          __syncwarp();
+          const int b = c0 + cl;
+#pragma unroll 4
+          for (int i = 0; i < 16; ++i) {
+            const int rr = 2 * i + rh;
+            const long grow = row0 + rr;
+            if (grow < R && b < n) {
+              double *p = out + grow * n + b;
+              const double val = (double)stg[rr * 17 + cl] * inv;
+              *p = first ? val : *p + val;
             }
           }
+          __syncwarp();
         }
         tc::fence_before_sync();
         tc::warp_arrive(&acce[buf]);
