@@ -116,3 +116,20 @@ def test_exact_density_reduces_to_hf_density_without_interaction(grid):
     rho = np.outer(C[:, 0], C[:, 0])
     assert np.max(np.abs(O.exact_density(psi, W) - O.density(rho, W, 2.0))) < 1e-10
     assert float(np.sum(W * O.exact_density(psi, W))) == pytest.approx(2.0, abs=1e-12)
+
+
+def test_density_of_the_harmonic_ground_state_is_the_gaussian():
+    """Closed form: with v = x^2/2 and no interaction the occupied orbital is
+    pi^(-1/4) exp(-x^2/2), so the density of two electrons in it is
+    2 pi^(-1/2) exp(-x^2) at every node, reached with spectral convergence in
+    the element order (10 equal elements on [-10, 10])."""
+    errs = []
+    for order in (6, 8, 10, 12, 14):
+        b = O.fedvr_basis(10, order, -10.0, 10.0, 0)
+        x = b["nodes"]
+        T = O.kinetic(b)
+        r = O.hf_scf(T + np.diag(0.5 * x * x), np.zeros_like(T), 2.0, 1, BETA)
+        n = O.density(r["rho0"], b["weights"], 2.0)
+        errs.append(float(np.max(np.abs(n - 2.0 / math.sqrt(math.pi) * np.exp(-x * x)))))
+    assert errs[-1] < 1e-11
+    assert all(e1 < e0 / 20 for e0, e1 in zip(errs, errs[1:]))
