@@ -802,7 +802,10 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
                        const void *h16, const TcScale *scale) {
   d->g = tc_geom(n, M);
   const long stack = (long)M * n * d->g.ld;
-  d->JB = 4096 / n > 1 ? 4096 / n : 1;
+  // FP32 accumulation blocks of the same number of MMA steps in both modes:
+  // 4096 contraction terms in TF32 (K = 8 per MMA), 8192 in FP16 (K = 16)
+  const int terms = h16 ? 8192 : 4096;
+  d->JB = terms / n > 1 ? terms / n : 1;
   d->S = splits;
   d->RT = (int)(((long)M * n + 127) / 128);
   d->S32 = S32;
