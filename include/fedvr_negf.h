@@ -55,14 +55,16 @@ typedef enum {
 
 typedef enum {
   FEDVR_FP64 = 0,        /* every contraction in IEEE double */
-  FEDVR_SPLIT_TF32 = 1,  /* Sigma^(2) and I^(1) contractions on tensor cores,
+  FEDVR_SPLIT_TF32 = 1,  /* Sigma^(2) (exchange and V Q V), I^(1) and, for
+                            n_b >= 96, the I^(2) products on tensor cores:
                             hi+lo TF32 operands, FP32 accumulation, FP64
-                            cross-block sums; I^(2) eigenbasis products in
-                            FP32; tables, update, residual, N and E0 in FP64.
-                            Requires n_b <= 304. */
+                            cross-block sums (I^(2) below n_b = 96 in FP32 on
+                            the CUDA cores); tables, update, residual, N and
+                            E0 in FP64. Requires n_b <= 304. */
   FEDVR_SPLIT_BF16 = 2,  /* reserved (three-way BF16 splits); rejected */
   FEDVR_SPLIT_F16 = 3    /* as FEDVR_SPLIT_TF32, with the exchange and the
-                            I^(1) contractions on kind::f16 tensor cores:
+                            I^(1) contractions on kind::f16 tensor cores
+                            (V Q V and I^(2) stay split TF32):
                             operands scaled by powers of two into FP16's
                             normal range and split as hi + lo (22 significant
                             bits, as the TF32 split), twice the TF32 rate.
