@@ -465,7 +465,8 @@ def main():
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 
-    dist, rank, world, local = _dist()
+    # the reference arm is the CPU oracle: its ranks meet (if at all) over gloo
+    dist, rank, world, local = _dist("gloo" if args.impl == "reference" else "nccl")
     if args.impl == "reference":
         run_reference(args, rank)
         if dist:
