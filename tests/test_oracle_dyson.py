@@ -91,34 +91,126 @@ def test_conv1_with_interpolated_lag_matches_closed_form_at_second_order():
     assert errs[2] < 1e-3
 
 
-def test_static_perturbation_dyson_fixed_point():
-    # Sigma^corr = 0 and a static dHF = dh: the Dyson fixed point is the
-    # Green's function of F + dh at the same mu, up to O(h^2) quadrature error.
-    rng = np.random.default_rng(3)
-    n, beta = 3, 8.0
+def _conv_closed_form(tau, CA, yA, CB, yB, beta):
+    # int A(tau - s) B(s) ds for A(x) = CA diag(phi(x; yA)) CA^T and
+    # B(x) = CB diag(phi(x; yB)) CB^T (all levels distinct): the projector
+    # pairs times the scalar convolution _closed_form
+    out = np.zeros((CA.shape[0], CA.shape[0]))
+    for a in range(len(yA)):
+        Pa = np.outer(CA[:, a], CA[:, a])
+        for b in range(len(yB)):
+            out += (Pa @ np.outer(CB[:, b], CB[:, b])) * _closed_form(tau, yA[a], yB[b], beta)
+    return out
+
+
+def test_convolutions_of_noncommuting_matrices_match_closed_form():
+    # matrix-valued pins of both convolutions: A and B do not commute, so a
+    # transposed or swapped factor in conv1 (Sigma at the lag times g) or conv2
+    # (g^0 at the lag times I1) fails; second order in the mesh
+    rng = np.random.default_rng(17)
+    beta = 10.0
+    CA, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    CB, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    yA, yB = np.array([-0.35, 0.2, 0.9]), np.array([-0.5, 0.1, 0.7])
+    dHF = 0.1 * W.random_symmetric(rng, 3)
+    e1, e2 = [], []
+    for u in (4, 8, 16):
+        mesh = O.power_mesh(beta, u, 6)
+        tau = mesh["tau"]
+        A = O.g0_mesh(yA, CA, 0.0, tau, beta)
+        B = O.g0_mesh(yB, CB, 0.0, tau, beta)
+        ref = np.array([_conv_closed_form(t, CA, yA, CB, yB, beta) for t in tau])
+        I1 = O.conv1(dHF, A, B, mesh, beta, O.lag_table(tau, beta))
+        e1.append(float(np.max(np.abs(I1 - (dHF @ B + ref)))))
+        I2 = O.conv2(B, yA, CA, 0.0, mesh, beta)
+        e2.append(float(np.max(np.abs(I2 - ref))))
+    for e in (e1, e2):
+        assert e[0] > 3.5 * e[1] > 3.5 ** 2 * e[2], e
+        assert e[2] < 1e-3
+
+
+def _closed_form_diag(tau, y, beta):
+    # the y_b -> y_a limit of _closed_form (the diagonal of a first-order change)
+    f = 1.0 / (math.exp(beta * y) + 1.0)
+    return -tau * f * f * math.exp(-tau * y) - (1.0 - f) * f * math.exp(-tau * y) * (tau + beta)
+
+
+def test_closed_form_diag_is_the_limit():
+    beta, y = 8.0, 0.6
+    for t in (-7.5, -3.0, -0.25):
+        assert abs(_closed_form_diag(t, y, beta) - _closed_form(t, y, y + 1e-6, beta)) < 1e-6
+
+
+def _static_problem(rng, n=3):
     Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
     eps = np.array([-0.9, 0.6, 1.3])
     dh = 0.05 * W.random_symmetric(rng, n)
-    e2, C2 = np.linalg.eigh((Q * eps) @ Q.T + dh)
+    F = (Q * eps) @ Q.T
+    # V = 0 makes Sigma^corr[g] and Sigma^HF[g] vanish identically, and
+    # Sigma0 = -dh turns the HF change dHF = Sigma^HF[g(0^-)] - Sigma0 into the
+    # fixed perturbation dh: the oracle's own driver runs unmodified
+    hf = dict(eps=eps, C=Q, mu=0.0, Sigma0=-dh)
+    return F, np.zeros((n, n)), dh, hf
+
+
+def test_static_perturbation_first_step_is_first_order_change():
+    # from g = g^0 one step gives g_1 = (1 - a) g^0 + a sym(g^0 + I2), so
+    # (g_1 - g^0) / a is the first-order change of g under dh: in the eigenbasis
+    # of F, dh'_ab J(tau; y_a, y_b) (closed form), up to O(h^2) quadrature error.
+    # A wrong mixing weight, a dropped or transposed factor in either
+    # convolution, or a missing symmetrisation fails it.
+    rng = np.random.default_rng(3)
+    F, V, dh, hf = _static_problem(rng)
+    beta, a = 8.0, 0.3
+    y, Cm = hf["eps"], hf["C"]
+    dhp = Cm.T @ dh @ Cm
     errs = []
-    for u in (3, 6):
+    for u in (4, 8, 16):
         mesh = O.power_mesh(beta, u, 5)
         tau = mesh["tau"]
         lag = O.lag_table(tau, beta)
-        G0 = O.g0_mesh(eps, Q, 0.0, tau, beta)
-        G = G0.copy()
-        for _ in range(200):
-            I1 = O.conv1(dh, np.zeros_like(G), G, mesh, beta, lag)
-            I2 = O.conv2(I1, eps, Q, 0.0, mesh, beta)
-            Gn = 0.5 * G + 0.5 * (G0 + I2)
-            r = np.max(np.abs(Gn - G))
-            G = Gn
-            # jump invariant holds at every iteration
-            assert np.max(np.abs(G[-1] + G[0] - np.eye(n))) < 1e-13
-            if r < 1e-13:
-                break
-        ref = O.g0_mesh(e2, C2, 0.0, tau, beta)
-        errs.append(np.max(np.abs(G - ref)))
+        G0 = O.g0_mesh(y, Cm, 0.0, tau, beta)
+        step = O.dyson_iteration(F, V, 2.0, hf, mesh, lag, beta, G0, G0, a)
+        assert np.max(np.abs(step["Sigma"])) == 0.0
+        got = (step["G"] - G0) / a
+        want = []
+        for t in tau:
+            J = np.array([[_closed_form(t, y[i], y[k], beta) if i != k else
+                           _closed_form_diag(t, y[i], beta) for k in range(3)] for i in range(3)])
+            want.append(Cm @ (dhp * J) @ Cm.T)
+        errs.append(float(np.max(np.abs(got - np.array(want)))))
+        # the update is symmetric although the sequential integration is not
+        gn = G0 + step["I2"]
+        assert np.max(np.abs(gn - gn.transpose(0, 2, 1))) > 1e-6
+        assert np.max(np.abs(step["G"] - step["G"].transpose(0, 2, 1))) < 1e-15
+    assert errs[0] > 3.5 * errs[1] > 3.5 ** 2 * errs[2]
+    assert errs[2] < 1e-4
+
+
+@pytest.mark.parametrize("mixing", [0.3, 0.5])
+def test_static_perturbation_dyson_fixed_point(mixing):
+    # Sigma^corr = 0 and a static dHF = dh through the oracle's own driver
+    # (solve_2b -> dyson_iteration, symmetrised mixed update): the fixed point
+    # is the Green's function of F + dh at the same mu (closed form by
+    # diagonalisation) up to O(h^2) quadrature error; the residual contracts
+    # by (1 - mixing) per step up to O(mixing |dh| / gap); the jump invariant
+    # g(0^-) + g(-beta) = 1 holds.
+    rng = np.random.default_rng(3)
+    F, V, dh, hf = _static_problem(rng)
+    beta = 8.0
+    e2, C2 = np.linalg.eigh(F + dh)
+    errs = []
+    for u in (3, 6):
+        res = O.solve_2b(F, V, 2.0, hf, beta, u, 5, mixing=mixing, tol=1e-13, max_iter=400)
+        assert res["converged"]
+        G = res["G"]
+        assert np.max(np.abs(G[-1] + G[0] - np.eye(3))) < 1e-13
+        assert np.max(np.abs(G - G.transpose(0, 2, 1))) < 1e-15
+        ref = O.g0_mesh(e2, C2, 0.0, res["mesh"]["tau"], beta)
+        errs.append(float(np.max(np.abs(G - ref))))
+        r = np.array([h[1] for h in res["history"]])
+        ratio = r[6:16] / r[5:15]
+        assert np.all(np.abs(ratio - (1.0 - mixing)) < 0.08), ratio
     assert errs[1] < 2e-3 and errs[0] > 3.0 * errs[1]
 
 
