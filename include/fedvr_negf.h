@@ -15,8 +15,9 @@
  *    validated before any launch; an invalid one returns FEDVR_ERR_ARG and
  *    changes nothing. The library never aborts and never throws. The message
  *    of the last failure is kept per context (fedvr_last_error). A CUDA error
- *    inside a call returns FEDVR_ERR_CUDA and is sticky: later calls on that
- *    context return FEDVR_ERR_STATE.
+ *    inside a call returns FEDVR_ERR_CUDA, a device wait that gave up
+ *    FEDVR_ERR_TIMEOUT; both are sticky: later calls on that context return
+ *    FEDVR_ERR_STATE.
  *  - Matrices are dense, row-major, unpadded. A tau-stack of matrices is
  *    [M][n][n] with tau ascending from -beta (index 0) to 0 (index M-1), the
  *    paper's interval tau in [-beta, 0]. All floating point is IEEE double
@@ -48,7 +49,10 @@ typedef enum {
   FEDVR_ERR_CUDA = -2,     /* a CUDA call failed; the context is now unusable */
   FEDVR_ERR_NOCONV = -3,   /* max_iter reached before the tolerance */
   FEDVR_ERR_DIVERGED = -4, /* residual grew for 8 consecutive iterations */
-  FEDVR_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+  FEDVR_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up; the kernel
+                              returned with its work unfinished, so the
+                              context is now unusable (later calls return
+                              FEDVR_ERR_STATE) */
   FEDVR_ERR_NAN = -6,      /* a NaN or Inf reached the iterate */
   FEDVR_ERR_STATE = -7     /* call out of order, or context already failed */
 } fedvr_status;
@@ -68,8 +72,12 @@ typedef enum {
                             operands scaled by powers of two into FP16's
                             normal range and split as hi + lo (22 significant
                             bits, as the TF32 split), twice the TF32 rate.
-                            Requires |g| < 16 (g's eigenvalues lie in [0, 1])
-                            and n_b <= 304. */
+                            Requires |g| < 65504/4096 (just below 16; g's
+                            eigenvalues lie in [0, 1]), checked on the
+                            device: an entry beyond it (or not finite) makes
+                            the call return FEDVR_ERR_ARG (a step whose
+                            iterate is not finite returns FEDVR_ERR_NAN).
+                            Requires n_b <= 304. */
 } fedvr_precision;
 
 /* ---------------------------------------------------------------------- */
@@ -92,17 +100,20 @@ const char *fedvr_last_error(const fedvr_ctx *ctx);
 /* Basis and operators (Sec. 2.1-2.2)                                      */
 /* ---------------------------------------------------------------------- */
 
-/* FE-DVR basis on [xmin, xmax] with n_elem finite elements of polynomial order
- * `order` (order + 1 Gauss-Lobatto-Legendre points per element; Sec. 2.1,
- * Eqs. xim, wim, basis; the paper's n_g is this order). grid_kind 0: equal
- * elements (Sec. 3.1 case I); 1: a central element of width 1 and widths
- * growing linearly outward (case II). The basis excludes both box ends, so
- * *n_b_out = n_elem*order - 1 (Eq. basisdim). Nodes, weights, the index map
- * and the kinetic matrix T (Eq. tmat) are built on the device bit-identically
- * to a plain IEEE evaluation in a fixed order (no fused multiply-add).
- * Limits: 1 <= n_elem, 1 <= order <= 32, 2 <= n_b <= 1024, xmin < xmax.
- * Resets any potential/HF/2B state of the context. */
-int build_fedvr(fedvr_ctx *ctx, int n_elem, int order, double xmin, double xmax,
+/* FE-DVR basis on [xmin, xmax] with n_elem finite elements of pts_per_elem
+ * Gauss-Lobatto-Legendre points each (Sec. 2.1, Eqs. xim, wim, basis): the
+ * element polynomials have order n_g = pts_per_elem - 1, the paper's n_g in
+ * the root and weight formulas. grid_kind 0: equal elements (Sec. 3.1 case
+ * I); 1: a central element of width 1 and widths growing linearly outward
+ * (case II). The basis excludes both box ends, so
+ * *n_b_out = n_elem*(pts_per_elem - 1) - 1 (Eq. basisdim; the paper's
+ * n_e = 29, n_g = 7 run is pts_per_elem = 8, n_b = 202). Nodes, weights, the
+ * index map and the kinetic matrix T (Eq. tmat) are built on the device
+ * bit-identically to a plain IEEE evaluation in a fixed order (no fused
+ * multiply-add).
+ * Limits: 1 <= n_elem, 2 <= pts_per_elem <= 33, 2 <= n_b <= 1024,
+ * xmin < xmax. Resets any potential/HF/2B state of the context. */
+int build_fedvr(fedvr_ctx *ctx, int n_elem, int pts_per_elem, double xmin, double xmax,
                 int grid_kind, int *n_b_out);
 
 /* Nuclear potential and interaction (Sec. 2.2 Eqs. vmat, umat1; Sec. 3 model
@@ -117,11 +128,11 @@ int set_potential(fedvr_ctx *ctx, int n_nuc, const double *Z, const double *R,
 /* Copy the basis to host buffers of n_b entries each (any may be NULL):
  * node coordinates, quadrature weights W_a (bridge = sum of two element
  * weights), element index and local point index of each basis function (a
- * bridge reports the left element and local index `order`). */
+ * bridge reports the left element and local index pts_per_elem - 1). */
 int fedvr_get_basis(const fedvr_ctx *ctx, double *nodes, double *weights, int *elem,
                     int *local);
 
-/* Copy the GLL reference points and weights (order + 1 each) to host. */
+/* Copy the GLL reference points and weights (pts_per_elem each) to host. */
 int fedvr_get_gll(const fedvr_ctx *ctx, double *xi, double *omega);
 
 /* Copy operators to host [n_b][n_b] buffers (v: [n_b]); any may be NULL.
@@ -217,14 +228,19 @@ int fedvr_stage_times(const fedvr_ctx *ctx, double *ms, int *launches);
  * and reports 0 there; this is not an error. */
 int fedvr_use_graphs(fedvr_ctx *ctx, int enable, int *last_step_graph);
 
-/* Work split of the split-TF32 first convolution (Eq. deq; the paper has no
- * counterpart): each 128-row tile of the stacked rows (i, a) may be cut into S
- * ranges of mesh points j, computed by different CTAs into separate partial
- * stacks and summed in a fixed order. request = 0 (default): fedvr_2b_prepare
- * times the candidates S once per (device, n_b, M) in the process and keeps
- * the fastest; request > 0: use the largest candidate <= request (1 = no
- * split); request < 0: leave the setting. *in_use (may be NULL) receives S of
- * the currently prepared run. Takes effect at the next prepare. */
+/* Work split of the split-precision first convolution (Eq. deq; the paper
+ * has no counterpart): each 128-row tile of the stacked rows (i, a) may be cut
+ * into S ranges of mesh points j, computed by different CTAs into separate
+ * partial stacks and summed in a fixed order. Each range is a whole number of
+ * the fixed FP32 accumulation blocks (whose length depends on n_b and M
+ * only), so S changes only the order of the FP64 additions of the block sums.
+ * Candidates: {1, 2, 3, 4, 6, 8, 12, 16}, at most the number of blocks.
+ * request = 0 (default): fedvr_2b_prepare times the candidates once per
+ * (device, n_b, M) in the process and keeps the fastest; request > 0: use the
+ * largest candidate <= request (1 = no split; also read by
+ * fedvr_conv_sigma_g); request < 0: leave the setting. *in_use (may be NULL)
+ * receives S of the currently prepared run (or of the last stage-level
+ * convolution). Takes effect at the next prepare. */
 int fedvr_conv1_splits(fedvr_ctx *ctx, int request, int *in_use);
 
 /* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
@@ -248,8 +264,9 @@ int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len);
  * ints) may be NULL. All systems advance together on the stream of ctxs[0]:
  * per iteration one tensor-core launch per contraction kernel covers every
  * unconverged system of the batch (a work queue over all systems' tiles), and
- * each system stops updating when its residual is below tol. Requires
- * precision FEDVR_SPLIT_TF32 and distinct contexts on one device. Returns the
+ * each system stops updating when its residual is below tol. Requires a split
+ * precision (FEDVR_SPLIT_TF32 or FEDVR_SPLIT_F16; FEDVR_FP64 returns
+ * FEDVR_ERR_ARG) and distinct contexts on one device. Returns the
  * worst per-system status; each context keeps its history and its last
  * g and Sigma (fedvr_2b_read). */
 int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int *u,
@@ -368,7 +385,13 @@ int fedvr_sigma2_noalloc(int n, int M, double spin, const double *V, const doubl
  * on the power mesh (beta, u, p), split trapezoid at t = tau_i with
  * Sigma(0^+) = -Sigma_0, Sigma(0^-) = Sigma_{M-1}; Sigma at off-mesh lags by
  * linear interpolation, anti-periodic beyond 0. dHF [n][n], Sigma and G
- * [M][n][n] device inputs; I1 [M][n][n] device output. */
+ * [M][n][n] device inputs; I1 [M][n][n] device output. In the split
+ * precisions the FP32 accumulation blocks are fixed ranges of mesh points
+ * (their length depends on n and M only) and the call cuts the mesh-point
+ * range into the split count requested with fedvr_conv1_splits (largest
+ * candidate in {1, 2, 3, 4, 6, 8, 12, 16} not above it and not above the
+ * number of blocks; no request: 1); results of different split counts
+ * differ only in the order of the FP64 additions of the block sums. */
 int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *dHF,
                        const double *Sigma, const double *G, double *I1, int precision);
 
@@ -378,9 +401,23 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
  * I2_i = C sum_j diag(w_ij phi(tau_i - tau_j)) C^T I1_j, i.e. with the left
  * index in the HF eigenbasis (three products).
  * eps [n] (ascending not required), C [n][n], I1 [M][n][n] device inputs;
- * I2 [M][n][n] device output. */
+ * I2 [M][n][n] device output. precision FEDVR_FP64: all three products in
+ * FP64; a split precision: the kernel table K(i, j) rounded to FP32 and the
+ * products of the split iteration (split TF32 on tensor cores for n >= 96,
+ * FP32 on the CUDA cores below), FP64 I1 in and I2 out. */
 int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *eps,
-                  const double *C, double mu, const double *I1, double *I2);
+                  const double *C, double mu, const double *I1, double *I2, int precision);
+
+/* Self-test of the bounded device-side waits that every tensor-core kernel
+ * uses (no counterpart in the paper): one warp waits on a shared-memory
+ * mbarrier with the kernels' own wait helper, limited to limit_seconds
+ * (1e-6 to 1) of wall time. release != 0: the barrier is released before
+ * the wait, which succeeds (FEDVR_OK). release = 0: nothing releases it; the
+ * wait gives up at the limit, the kernel records the timeout in a device flag
+ * and returns, and the call returns FEDVR_ERR_TIMEOUT and leaves the context
+ * failed, as every timeout does (later calls: FEDVR_ERR_STATE). Nothing
+ * faults or hangs. Synchronises the context's stream. */
+int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds);
 
 #ifdef __cplusplus
 }

@@ -106,11 +106,14 @@ class Context:
         return self._lib.fedvr_last_error(self._h).decode()
 
     # -- basis and operators -------------------------------------------------
-    def build_fedvr(self, n_elem, order, xmin, xmax, grid_kind=0) -> int:
+    def build_fedvr(self, n_elem, pts_per_elem, xmin, xmax, grid_kind=0) -> int:
+        """FE-DVR basis with n_elem elements of pts_per_elem GLL points each
+        (polynomial order pts_per_elem - 1); returns n_b."""
         nb = C.c_int()
-        self._check(self._lib.build_fedvr(self._h, n_elem, order, xmin, xmax, grid_kind, C.byref(nb)))
+        self._check(self._lib.build_fedvr(self._h, n_elem, pts_per_elem, xmin, xmax, grid_kind,
+                                          C.byref(nb)))
         self.n_b = nb.value
-        self.order = order
+        self.order = pts_per_elem - 1
         return nb.value
 
     def set_potential(self, Z, R, soft_en=1.0, soft_ee=1.0, n_elec=2) -> float:
@@ -270,12 +273,18 @@ class Context:
                                                  _dev(Sigma, (M, n, n)), _dev(G, (M, n, n)),
                                                  _dev(I1, (M, n, n)), precision))
 
-    def conv_g0(self, beta, u, p, eps, Cmat, mu, I1, I2):
+    def conv_g0(self, beta, u, p, eps, Cmat, mu, I1, I2, precision=FP64):
         M, n = I1.shape[0], I1.shape[1]
         assert M == 2 * u * p + 1
         self._check(self._lib.fedvr_conv_g0(self._h, n, beta, u, p, _dev(eps, (n,)),
                                             _dev(Cmat, (n, n)), mu, _dev(I1, (M, n, n)),
-                                            _dev(I2, (M, n, n))))
+                                            _dev(I2, (M, n, n)), precision))
+
+    def selftest_wait(self, release, limit_seconds=1e-3):
+        """Run the bounded device-wait self-test (``fedvr_selftest_wait``):
+        release=True must return normally; release=False raises FedvrError
+        with code -5 (timeout) and leaves the context failed."""
+        self._check(self._lib.fedvr_selftest_wait(self._h, 1 if release else 0, limit_seconds))
 
 
 def solve_2b_batched(contexts, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,

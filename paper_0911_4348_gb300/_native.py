@@ -66,7 +66,8 @@ SIGNATURES = {
     "fedvr_conv_sigma_g": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp,
                                      _vp, C.c_int]),
     "fedvr_conv_g0": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, _vp, _vp, C.c_double,
-                                _vp, _vp]),
+                                _vp, _vp, C.c_int]),
+    "fedvr_selftest_wait": (C.c_int, [_vp, C.c_int, C.c_double]),
 }
 
 _lib = None

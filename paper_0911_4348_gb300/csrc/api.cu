@@ -169,6 +169,29 @@ int tc_err_ptr(fedvr_ctx *ctx, int **err) {
   return tc_workspace(ctx, ctx->n, ctx->M, &ws, &S32, err);
 }
 
+// Decode the tensor-core path's device error flag (read back after a
+// synchronisation). Bit 0 (value 1): a bounded mbarrier wait gave up; the
+// kernel left its work unfinished, so the workspace is undefined and the
+// context is marked failed (later calls return FEDVR_ERR_STATE). Bit 1
+// (value 2): an entry of g outside the FP16 split's range; nothing is
+// corrupted, the flag is cleared and the call reports FEDVR_ERR_ARG.
+int flag_status(fedvr_ctx *ctx, int h_err, int *dflag) {
+  if (h_err & 1) {
+    ctx->failed = true;
+    return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+  }
+  if (h_err & 2) {
+    if (dflag) {
+      FEDVR_CK(ctx, cudaMemsetAsync(dflag, 0, sizeof(int), ctx->stream));
+      FEDVR_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return fail(ctx, FEDVR_ERR_ARG,
+                "an entry of g has |g| >= 16 or is not finite: outside the FP16 split's range "
+                "(FEDVR_SPLIT_TF32 and FEDVR_FP64 have no such limit)");
+  }
+  return FEDVR_OK;
+}
+
 bool is_split(int precision) {
   return precision == FEDVR_SPLIT_TF32 || precision == FEDVR_SPLIT_F16;
 }
@@ -265,8 +288,10 @@ int launch_conv1_single(fedvr_ctx *ctx, int splits, int *err, cudaStream_t s, in
 
 // Measured choice of the first convolution's splits, once per (device, n, M)
 // in this process: every candidate's persistent launch (and split sum) is
-// timed on the prepared buffers and the fastest kept. Candidates keep at
-// least 4 mesh points per split and at most 16 work items per SM.
+// timed on the prepared buffers and the fastest kept. A candidate takes whole
+// accumulation blocks (S <= the block count), so every choice gives the same
+// block sums and the results differ only in the order in which the FP64
+// partial sums are added; candidates also keep at most 16 work items per SM.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_conv1_splits;
 
@@ -274,9 +299,10 @@ int choose_conv1_splits(fedvr_ctx *ctx, float *ws, float *S32, int *err) {
   const int n = ctx->n, M = ctx->M;
   const size_t stack = (size_t)M * n * n;
   const long RT = ((long)M * n + 127) / 128;
+  const int NB = conv1_blocks(n, M, ctx->precision == FEDVR_SPLIT_F16);
   std::vector<int> cand;
-  for (int S : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
-    if (S > 1 && (S > M / 4 || RT * S > 16L * ctx->num_sms || (S - 1) * stack * 8 > (2ull << 30)))
+  for (int S : {1, 2, 3, 4, 6, 8, 12, 16}) {
+    if (S > 1 && (S > NB || RT * S > 16L * ctx->num_sms || (S - 1) * stack * 8 > (2ull << 30)))
       continue;
     cand.push_back(S);
   }
@@ -309,7 +335,7 @@ int choose_conv1_splits(fedvr_ctx *ctx, float *ws, float *S32, int *err) {
         int h_err = 0;
         FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
         if (int r = sync(ctx)) return r;
-        if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+        if (int r = flag_status(ctx, h_err, err)) return r;
         float ms = 0.f;
         FEDVR_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[6]));
         if (S == cand.front() || ms < 0.97f * best_ms) {  // more splits must win clearly
@@ -336,9 +362,12 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, in
   const double *V = P<double>(ctx->b_V);
   void *h16 = nullptr;
   TcScale *scale = nullptr;
+  if (is_split(ctx->precision) && !err) {
+    if (int r = tc_err_ptr(ctx, &err)) return r;
+  }
   if (ctx->precision == FEDVR_SPLIT_F16) {  // FP16 operands of g; the Sigma bound restarts
     if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
-    FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
+    FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err));
     FEDVR_CK(ctx, cudaMemsetAsync(&scale->maxS, 0, sizeof(unsigned), s));
     *launches += 1;
   }
@@ -361,7 +390,7 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, in
     float *ws, *S32;
     int *own_err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &own_err)) return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale, err ? err : own_err));
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale, err));
     *launches += 4;  // splits of g and V, VQ, W = (VQ) V
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
@@ -535,8 +564,7 @@ int fedvr::sigma_of_current_g(fedvr_ctx *ctx) {
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
-    if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
-    return FEDVR_OK;
+    return flag_status(ctx, h_err, err);
   }
   return sync(ctx);
 }
@@ -595,11 +623,12 @@ void fedvr_destroy(fedvr_ctx *ctx) {
 
 const char *fedvr_last_error(const fedvr_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
-int build_fedvr(fedvr_ctx *ctx, int n_elem, int order, double xmin, double xmax, int grid_kind,
-                int *n_b_out) {
+int build_fedvr(fedvr_ctx *ctx, int n_elem, int pts_per_elem, double xmin, double xmax,
+                int grid_kind, int *n_b_out) {
   CHECK_CTX(ctx);
-  if (n_elem < 1 || order < 1 || order > 32)
-    return fail(ctx, FEDVR_ERR_ARG, "need n_elem >= 1 and 1 <= order <= 32");
+  if (n_elem < 1 || pts_per_elem < 2 || pts_per_elem > 33)
+    return fail(ctx, FEDVR_ERR_ARG, "need n_elem >= 1 and 2 <= pts_per_elem <= 33");
+  const int order = pts_per_elem - 1;  // polynomial order n_g of the Lobatto rule
   long n = (long)n_elem * order - 1;
   if (n < 2 || n > 1024) return fail(ctx, FEDVR_ERR_ARG, "n_b = %ld outside [2, 1024]", n);
   if (!is_fin(xmin) || !is_fin(xmax) || !(xmin < xmax))
@@ -973,7 +1002,11 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   FEDVR_CK(ctx, cudaMemcpyAsync(hr, P<double>(ctx->w_red), sizeof(hr), cudaMemcpyDeviceToHost, s));
   if (split) FEDVR_CK(ctx, cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (int r = sync(ctx)) return r;
-  if (tc_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+  if ((tc_err & 1) || ((tc_err & 2) && hr[2] == hr[2] && is_fin(hr[0])))
+    return flag_status(ctx, tc_err, err);
+  if (tc_err) {  // a non-finite iterate also trips the FP16 range check: reported as NaN below
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+  }
   double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   double rec[5] = {(double)ctx->step_k, hr[2], hr[0], hr[1], ms};
   ctx->history.insert(ctx->history.end(), rec, rec + 5);
@@ -1329,7 +1362,18 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
   int h_err = 0;
   FEDVR_CK(lead, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (int r = sync(lead)) return r;
-  if (h_err) return fail(lead, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+  if (h_err & 2) {  // a non-finite iterate also trips the FP16 range check
+    bool nonfinite = false;
+    for (int k = 0; k < n_sys; ++k) {
+      const double E = B->hred[3 * k], r = B->hred[3 * k + 2];
+      if (active[k] && (r != r || !is_fin(E))) nonfinite = true;
+    }
+    if (nonfinite && !(h_err & 1)) {
+      FEDVR_CK(lead, cudaMemsetAsync(d_err, 0, sizeof(int), s));
+      h_err = 0;
+    }
+  }
+  if (int r = flag_status(lead, h_err, d_err)) return r;
   const double ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   lead->step_launches = launches;
@@ -1448,7 +1492,7 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
       TcScale *scale;
       if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
       FEDVR_CK(ctx, launch_scale_init(0, nullptr, n, V, scale, s));
-      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
+      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err));
     }
     if (int r = upload_single_tables(ctx, n, M, ws, Sigma, nullptr, nullptr, nullptr, nullptr, 1,
                                      nullptr, spin))
@@ -1463,8 +1507,7 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
-    if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
-    return FEDVR_OK;
+    return flag_status(ctx, h_err, err);
   }
   size_t stack = (size_t)M * n * n;
   ENSURE(ctx, w_t1, dsz(stack));
@@ -1496,12 +1539,23 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     void *h16 = nullptr;
     TcScale *scale = nullptr;
     const bool f16 = precision == FEDVR_SPLIT_F16;
+    // work split of the mesh-point range: the request of fedvr_conv1_splits
+    // (largest candidate not above it, whole accumulation blocks), else none
+    int S = 1;
+    if (ctx->c1_request > 1) {
+      const int NB = conv1_blocks(n, M, f16);
+      for (int c : {2, 3, 4, 6, 8, 12, 16})
+        if (c <= ctx->c1_request && c <= NB) S = c;
+    }
+    const size_t stack = (size_t)M * n * n;
+    if (S > 1) ENSURE(ctx, w_c1p, dsz((size_t)(S - 1) * stack));
     if (f16) {
       if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
       FEDVR_CK(ctx, launch_scale_init(M, P<int4>(ctx->w_coef32), 0, nullptr, scale, s));
-      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s));
+      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err));
     }
-    if (int r = upload_single_tables(ctx, n, M, ws, nullptr, S32, dHF, P<ConvCoef>(ctx->w_coef), I1))
+    if (int r = upload_single_tables(ctx, n, M, ws, nullptr, S32, dHF, P<ConvCoef>(ctx->w_coef), I1,
+                                     S, S > 1 ? P<double>(ctx->w_c1p) : nullptr))
       return r;
     if (!f16) FEDVR_CK(ctx, launch_split_g(n, M, G, ws, ws + tstack, ws + 2 * tstack, s));
     FEDVR_CK(ctx, launch_sigma_to_f32(n, M, Sigma, S32, s, f16 ? &scale->maxS : nullptr));
@@ -1511,23 +1565,25 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, conv1_tc_launch(reinterpret_cast<const C1Sys *>(tab + kTabC),
                                   reinterpret_cast<const long *>(tab + kTabPC), 1,
-                                  conv1_items(n, M, 1), g.Np, err, ctx->num_sms, s, f16));
+                                  conv1_items(n, M, S), g.Np, err, ctx->num_sms, s, f16));
+    if (S > 1) FEDVR_CK(ctx, conv1_sum_splits((long)stack, S - 1, P<double>(ctx->w_c1p), I1, s));
+    ctx->c1_splits = S;
     int h_err = 0;
     FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (int r = sync(ctx)) return r;
-    if (h_err) return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
-    return FEDVR_OK;
+    return flag_status(ctx, h_err, err);
   }
   FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), dHF, Sigma, G, I1, ctx->stream));
   return FEDVR_OK;
 }
 
 int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double *eps,
-                  const double *C, double mu, const double *I1, double *I2) {
+                  const double *C, double mu, const double *I1, double *I2, int precision) {
   CHECK_CTX(ctx);
   if (int r = check_mesh_args(ctx, beta, u, p)) return r;
   if (n < 1 || n > 1024 || !eps || !C || !I1 || !I2 || !is_fin(mu))
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, finite mu and device buffers");
+  if (int r = check_precision(ctx, precision, n)) return r;
   ctx->prepared = false;
   if (int r = build_mesh(ctx, beta, u, p, false)) return r;
   int M = 2 * u * p + 1;
@@ -1539,9 +1595,37 @@ int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double
   FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
                                     P<double>(ctx->w_wm), P<double>(ctx->w_wp), eps, nullptr, mu,
                                     P<double>(ctx->w_K), s));
+  if (is_split(precision)) {  // the split path's products: FP32 table, split TF32 / FP32 GEMMs
+    ENSURE(ctx, w_K32, (size_t)n * M * M * sizeof(float));
+    ENSURE(ctx, w_red, dsz(8));
+    int *err = reinterpret_cast<int *>(P<double>(ctx->w_red) + 7);
+    FEDVR_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    FEDVR_CK(ctx, launch_to_f32((size_t)n * M * M, P<double>(ctx->w_K), P<float>(ctx->w_K32), s));
+    FEDVR_CK(ctx, conv2_apply_f32(n, M, P<float>(ctx->w_K32), C, I1, I2, P<float>(ctx->w_t1),
+                                  P<float>(ctx->w_t2), err, s));
+    int h_err = 0;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (int r = sync(ctx)) return r;
+    return flag_status(ctx, h_err, err);
+  }
   FEDVR_CK(ctx, conv2_apply(n, M, P<double>(ctx->w_K), C, I1, I2, P<double>(ctx->w_t1),
                             P<double>(ctx->w_t2), s));
   return FEDVR_OK;
+}
+
+int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds) {
+  CHECK_CTX(ctx);
+  if (!(limit_seconds >= 1e-6 && limit_seconds <= 1.0))
+    return fail(ctx, FEDVR_ERR_ARG, "limit_seconds must lie in [1e-6, 1]");
+  ENSURE(ctx, b_scal, dsz(16));
+  int *flag = reinterpret_cast<int *>(P<double>(ctx->b_scal) + 10);
+  cudaStream_t s = ctx->stream;
+  FEDVR_CK(ctx, cudaMemsetAsync(flag, 0, sizeof(int), s));
+  FEDVR_CK(ctx, launch_wait_probe(release != 0, (unsigned long long)(limit_seconds * 1e9), flag, s));
+  int h_err = 0;
+  FEDVR_CK(ctx, cudaMemcpyAsync(&h_err, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (int r = sync(ctx)) return r;
+  return flag_status(ctx, h_err, flag);
 }
 
 }  // extern "C"

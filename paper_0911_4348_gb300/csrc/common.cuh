@@ -26,7 +26,7 @@ struct fedvr_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   char err[640] = {0};
-  bool failed = false;  // sticky after a CUDA error
+  bool failed = false;  // sticky after a CUDA error or a timed-out device wait
   int stage = 0;        // 0 none, 1 basis, 2 potential, 3 hf
 
   // basis (Sec. 2.1)
@@ -185,6 +185,12 @@ cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const do
 cudaError_t launch_to_f32(size_t count, const double *x, float *y, cudaStream_t s);
 cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, const double *I1,
                             double *I2, float *t1, float *t2, int *err, cudaStream_t s);
+
+// selftest.cu: one warp waits (bounded by limit_ns, the tensor-core kernels'
+// wait helper) on an mbarrier that is released first (release) or never; a
+// wait that gives up sets *flag = 1.
+cudaError_t launch_wait_probe(bool release, unsigned long long limit_ns, int *flag,
+                              cudaStream_t s);
 
 // update.cu
 // n_out[a] = spin g[a][a] / W[a] (density at the nodes from g(0^-)).

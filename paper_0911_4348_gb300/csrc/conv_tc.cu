@@ -44,12 +44,18 @@ struct C1Item {
 
 // Item q of a system: split s = q / RT (split-major, so that the CTAs running
 // at the same time walk the same mesh points and share g_j in L2), tile t.
+// The FP32 accumulation blocks are the fixed mesh-point ranges
+// [b JB, (b + 1) JB) of the system (JB depends on n and M only); split s
+// takes the whole blocks [s NB / S, (s + 1) NB / S) of the NB blocks, so the
+// split count decides which CTA sums a block, never where a block starts or
+// ends (the host keeps S <= NB: no split is empty).
 __device__ __forceinline__ C1Item c1_item(const C1Sys &S, long q) {
   C1Item it;
   const int s = (int)(q / S.RT);
   it.t = (int)(q % S.RT);
-  it.j_lo = (int)(((long)s * S.g.M) / S.S);
-  it.j_hi = (int)(((long)(s + 1) * S.g.M) / S.S);
+  const int NB = (S.g.M + S.JB - 1) / S.JB;
+  it.j_lo = (int)(((long)s * NB) / S.S) * S.JB;
+  it.j_hi = min(S.g.M, (int)(((long)(s + 1) * NB) / S.S) * S.JB);
   it.out = (s == 0) ? S.I1 : S.part + (long)(s - 1) * S.g.M * S.g.n * S.g.n;
   return it;
 }
@@ -740,11 +746,16 @@ __global__ void __launch_bounds__(kThreadsH, 1)
 }
 
 // FP16 split of g scaled by 2^kScaleG; one warp per row, two columns per lane.
+// A scaled entry at or above FP16's largest finite value (|g| >= 65504 / 2^12,
+// just below 16) or not finite cannot be represented: the warp raises bit 1
+// (value 2) of *flag and the caller reports the input as out of range.
 __global__ void split_f16_kernel(int n, long rows, int ld16, const double *__restrict__ G,
-                                 uint32_t *__restrict__ hi, uint32_t *__restrict__ lo) {
+                                 uint32_t *__restrict__ hi, uint32_t *__restrict__ lo,
+                                 int *flag) {
   const int lane = threadIdx.x & 31;
   const long wpb = blockDim.x >> 5, nw = (long)gridDim.x * wpb;
   const double sc = (double)(1 << kScaleG);
+  bool bad = false;
   for (long row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += nw) {
     const double *src = G + row * n;
     const long o = row * (ld16 / 2);
@@ -752,12 +763,14 @@ __global__ void split_f16_kernel(int n, long rows, int ld16, const double *__res
       const int c = c0 + 2 * lane;
       const float y0 = (c < n) ? (float)(src[c] * sc) : 0.f;
       const float y1 = (c + 1 < n) ? (float)(src[c + 1] * sc) : 0.f;
+      bad |= !(fabsf(y0) < 65504.f) || !(fabsf(y1) < 65504.f);
       uint32_t h, l;
       tc::f16_split2(y0, y1, h, l);
       hi[o + c / 2] = h;
       lo[o + c / 2] = l;
     }
   }
+  if (__any_sync(0xffffffffu, bad) && lane == 0 && flag) atomicOr(flag, 2);
 }
 
 // scale->maxC = max over (i, j) of |c1| + |c2|; scale->maxS = 0 (one block).
@@ -802,10 +815,8 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
                        const void *h16, const TcScale *scale) {
   d->g = tc_geom(n, M);
   const long stack = (long)M * n * d->g.ld;
-  // FP32 accumulation blocks of the same number of MMA steps in both modes:
-  // 4096 contraction terms in TF32 (K = 8 per MMA), 8192 in FP16 (K = 16)
-  const int terms = h16 ? 8192 : 4096;
-  d->JB = terms / n > 1 ? terms / n : 1;
+  d->JB = conv1_block_points(n, M, h16 != nullptr);
+  if (splits < 1 || splits > conv1_blocks(n, M, h16 != nullptr)) return cudaErrorInvalidValue;
   d->S = splits;
   d->RT = (int)(((long)M * n + 127) / 128);
   d->S32 = S32;
@@ -832,11 +843,12 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
   return cudaSuccess;
 }
 
-cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s) {
+cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s,
+                             int *flag) {
   const int ld16 = ld16_of(n);
   uint32_t *hi = reinterpret_cast<uint32_t *>(h16);
   uint32_t *lo = hi + (size_t)M * n * ld16 / 2;
-  split_f16_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld16, G, hi, lo);
+  split_f16_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld16, G, hi, lo, flag);
   return cudaGetLastError();
 }
 

@@ -175,7 +175,8 @@ cudaError_t scratch_on_current_device(double **out) {
 
 extern "C" int fedvr_sigma2_noalloc(int n, int M, double spin, const double *V, const double *G,
                                     double *Sigma, void *cuda_stream) {
-  if (n < 1 || n > 1024 || M < 1 || M > 4097 || !V || !G || !Sigma || !isfinite(spin))
+  if (n < 1 || n > 1024 || M < 1 || M > 4097 || !V || !G || !Sigma || !isfinite(spin) ||
+      spin < 0.0)
     return FEDVR_ERR_ARG;
   if ((size_t)M * (size_t)n * (size_t)n > kNoAllocStack) return FEDVR_ERR_ARG;
   double *scratch = nullptr;

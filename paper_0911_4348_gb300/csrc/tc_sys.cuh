@@ -86,8 +86,11 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
 // Pitch (elements) of the FP16 split rows: n rounded up to 64 (128-byte rows).
 inline int ld16_of(int n) { return (n + 63) / 64 * 64; }
 // FP16 split of g (scaled by 2^kScaleG) into h16 = [hi stack][lo stack],
-// [M][n][ld16] halves each, padding zero.
-cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s);
+// [M][n][ld16] halves each, padding zero. An entry the split cannot hold
+// (|g| >= 65504 / 2^kScaleG or not finite) raises bit 1 (value 2) of *flag
+// (the tensor-core error flag; may be NULL).
+cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s,
+                             int *flag);
 // scale->maxC = max |c1| + |c2| over the coefficient table, scale->maxV =
 // max |V| over the n x n interaction matrix, scale->maxS = 0.
 cudaError_t launch_scale_init(int M, const int4 *coef32, int n, const double *V, TcScale *scale,
@@ -144,6 +147,27 @@ inline long exchange_items(int n, int M) {
 }
 inline long conv1_items(int n, int M, int splits) {
   return ((long)M * n + 127) / 128 * (long)splits;
+}
+
+// Mesh points JB per FP32 accumulation block of the first convolution, a
+// function of (n, M) and the mode only: blocks of 512 MMA steps (4096
+// contraction terms in TF32, K = 8 per MMA; 8192 in FP16, K = 16), shortened
+// when the M n / 128 row tiles are too few to give two work items per SM of a
+// 152-SM GPU, so that the mesh-point range can be split over up to 16 CTAs.
+inline int conv1_block_points(int n, int M, bool f16) {
+  const int terms = f16 ? 8192 : 4096;
+  const long RT = ((long)M * n + 127) / 128;
+  long smax = (304 + RT - 1) / RT;
+  smax = smax < 1 ? 1 : (smax > 16 ? 16 : smax);
+  int jb = terms / n;
+  const int cap = (int)((M + smax - 1) / smax);
+  if (jb > cap) jb = cap;
+  return jb > 1 ? jb : 1;
+}
+// Accumulation blocks of the mesh-point range: the largest split count.
+inline int conv1_blocks(int n, int M, bool f16) {
+  const int jb = conv1_block_points(n, M, f16);
+  return (M + jb - 1) / jb;
 }
 
 }  // namespace fedvr

@@ -58,6 +58,11 @@ class System:
     tol: float = 1e-8
 
     @property
+    def pts_per_elem(self) -> int:
+        """GLL points per element, order + 1 (the library's build_fedvr argument)."""
+        return self.order + 1
+
+    @property
     def n_b(self) -> int:
         """Matrix dimension n_e * order - 1 (both box ends clamped)."""
         return self.n_elem * self.order - 1

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
 
 def test_null_context_is_rejected_without_touching_the_gpu(lib):
     nb = C.c_int()
-    assert lib.build_fedvr(None, 4, 4, -1.0, 1.0, 0, C.byref(nb)) == -1
+    assert lib.build_fedvr(None, 4, 5, -1.0, 1.0, 0, C.byref(nb)) == -1
     assert lib.solve_hf(None, 100.0, 1e-12, 10, None, None) == -1
     assert lib.fedvr_sigma2(None, 4, 3, 2.0, None, None, None, 0) == -1
     assert lib.fedvr_create(None, None) == -1

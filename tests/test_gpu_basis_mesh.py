@@ -33,7 +33,7 @@ GRIDS = [
 
 @pytest.mark.parametrize("ne,order,xmin,xmax,kind", GRIDS)
 def test_basis_and_kinetic_bit_exact(ctx, ne, order, xmin, xmax, kind):
-    nb = ctx.build_fedvr(ne, order, xmin, xmax, kind)
+    nb = ctx.build_fedvr(ne, order + 1, xmin, xmax, kind)
     ref = O.fedvr_basis(ne, order, xmin, xmax, kind)
     assert nb == ref["n"] == ne * order - 1
     xi, om = ctx.get_gll()
@@ -49,7 +49,7 @@ def test_basis_and_kinetic_bit_exact(ctx, ne, order, xmin, xmax, kind):
 @pytest.mark.parametrize("maker", [W.he_small, W.he_medium, W.h3p_large])
 def test_potential_interaction_hamiltonian_bit_exact(ctx, maker):
     s = maker()
-    ctx.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    ctx.build_fedvr(s.n_elem, s.pts_per_elem, s.xmin, s.xmax, s.grid_kind)
     enn = ctx.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
     b = O.fedvr_basis(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
     T = O.kinetic(b)

@@ -116,7 +116,7 @@ def he_small_2b():
 def test_solve_2b_he_small_matches_oracle(ctx, he_small_2b):
     ref, res = he_small_2b
     s = ref["sys"]
-    ctx.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    ctx.build_fedvr(s.n_elem, s.pts_per_elem, s.xmin, s.xmax, s.grid_kind)
     ctx.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
     ctx.solve_hf(s.beta, tol=1e-13)
     M, n = s.n_tau, s.n_b
@@ -138,7 +138,7 @@ def test_solve_2b_he_small_matches_oracle(ctx, he_small_2b):
 def test_solve_2b_device_outputs_and_warm_start(ctx, he_small_2b):
     ref, res = he_small_2b
     s = ref["sys"]
-    ctx.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    ctx.build_fedvr(s.n_elem, s.pts_per_elem, s.xmin, s.xmax, s.grid_kind)
     ctx.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
     ctx.solve_hf(s.beta, tol=1e-13)
     M, n = s.n_tau, s.n_b
@@ -158,12 +158,12 @@ def test_error_paths(ctx):
         c.solve_hf(100.0)
     assert e.value.code == -7  # out of order
     with pytest.raises(FedvrError) as e:
-        c.build_fedvr(0, 4, -1.0, 1.0)
+        c.build_fedvr(0, 5, -1.0, 1.0)
     assert e.value.code == -1
     with pytest.raises(FedvrError) as e:
-        c.build_fedvr(4, 4, 1.0, -1.0)
+        c.build_fedvr(4, 5, 1.0, -1.0)
     assert e.value.code == -1
-    c.build_fedvr(4, 4, -10.0, 10.0)
+    c.build_fedvr(4, 5, -10.0, 10.0)
     with pytest.raises(FedvrError) as e:
         c.set_potential([2.0], [0.0], n_elec=3)
     assert e.value.code == -1

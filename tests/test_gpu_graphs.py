@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 def _ctx(s):
     from paper_0911_4348_gb300 import Context
     c = Context()
-    c.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    c.build_fedvr(s.n_elem, s.pts_per_elem, s.xmin, s.xmax, s.grid_kind)
     c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
     c.solve_hf(s.beta, tol=1e-12)
     return c

@@ -43,7 +43,7 @@ def _need_gpu():
 def _context(R, n_elem=N_ELEM, order=ORDER, half=HALF):
     from paper_0911_4348_gb300 import Context
     c = Context()
-    c.build_fedvr(n_elem, order, -half, half, 1)
+    c.build_fedvr(n_elem, order + 1, -half, half, 1)
     enn = c.set_potential([1.0, 1.0, 1.0], [-R, 0.0, R], 1.0, 1.0, 2)
     E_hf, _ = c.solve_hf(BETA, tol=1e-12)
     return c, E_hf, enn
@@ -158,7 +158,7 @@ def test_h3p_small_grid_second_born_density_and_energy_match_oracle():
     R, K = 1.8, 25
     from paper_0911_4348_gb300 import Context
     c = Context()
-    c.build_fedvr(5, 4, -10.0, 10.0, 0)
+    c.build_fedvr(5, 5, -10.0, 10.0, 0)
     c.set_potential([1.0, 1.0, 1.0], [-R, 0.0, R], 1.0, 1.0, 2)
     E_hf, _ = c.solve_hf(BETA, tol=1e-12)
     r = c.solve_2b(BETA, 4, 16, 0.5, 1e-14, K, precision=0, check=False)

@@ -30,7 +30,7 @@ def _dev(a):
 def test_hf_matches_oracle(ctx, name):
     ref = oracle_system(name)
     s = ref["sys"]
-    ctx.build_fedvr(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+    ctx.build_fedvr(s.n_elem, s.pts_per_elem, s.xmin, s.xmax, s.grid_kind)
     ctx.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
     E, mu = ctx.solve_hf(s.beta, tol=1e-13, max_iter=500)
     hf = ref["hf"]

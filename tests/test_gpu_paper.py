@@ -22,7 +22,7 @@ def test_he_case2_second_born_matches_paper():
     from paper_0911_4348_gb300 import Context
     gold = load_golden("paper_values.txt")
     c = Context()
-    n_b = c.build_fedvr(int(gold["he_case2_n_elem"]), int(gold["he_case2_order"]),
+    n_b = c.build_fedvr(int(gold["he_case2_n_elem"]), int(gold["he_case2_order"]) + 1,
                         -gold["box_length_he"] / 2, gold["box_length_he"] / 2, 1)
     assert n_b == gold["he_case2_n_b"]
     c.set_potential([2.0], [0.0], 1.0, 1.0, 2)
@@ -53,7 +53,7 @@ def test_fig2a_hf_sweep_matches_oracle():
     from paper_0911_4348_gb300 import Context
     for kind, ne, ng in FIG2A:
         c = Context()
-        c.build_fedvr(ne, ng, -100.0, 100.0, kind)
+        c.build_fedvr(ne, ng + 1, -100.0, 100.0, kind)
         c.set_potential([2.0], [0.0], 1.0, 1.0, 2)
         E_gpu, _ = c.solve_hf(100.0, tol=1e-12)
         c.close()
@@ -76,7 +76,7 @@ def test_fig2b_second_born_converges_with_the_mesh():
     E = {}
     for u in (8, 16, 32, 64):
         c = Context()
-        c.build_fedvr(29, 7, -100.0, 100.0, 1)
+        c.build_fedvr(29, 8, -100.0, 100.0, 1)
         c.set_potential([2.0], [0.0], 1.0, 1.0, 2)
         c.solve_hf(100.0, tol=1e-12)
         r = c.solve_2b(100.0, u, 16, 0.5, 1e-8, 300, precision=3)
