@@ -217,13 +217,13 @@ int f16_workspace(fedvr_ctx *ctx, int n, int M, void **h16, TcScale **scale) {
   return FEDVR_OK;
 }
 
-// The exchange row table for basis size n in w_xrow (built on the host once per n).
+// The exchange tile table for basis size n in w_xrow (built on the host once per n).
 int ensure_xrows(fedvr_ctx *ctx, int n) {
   if (ctx->xrow_n == n) return FEDVR_OK;
-  std::vector<uint32_t> rows;
-  exchange_row_table(n, rows);
-  ENSURE(ctx, w_xrow, rows.size() * sizeof(uint32_t));
-  FEDVR_CK(ctx, cudaMemcpyAsync(ctx->w_xrow.ptr, rows.data(), rows.size() * sizeof(uint32_t),
+  std::vector<uint32_t> tiles;
+  exchange_tile_table(n, tiles);
+  ENSURE(ctx, w_xrow, tiles.size() * sizeof(uint32_t));
+  FEDVR_CK(ctx, cudaMemcpyAsync(ctx->w_xrow.ptr, tiles.data(), tiles.size() * sizeof(uint32_t),
                                 cudaMemcpyHostToDevice, ctx->stream));
   if (int r = sync(ctx)) return r;  // the host vector goes out of scope
   ctx->xrow_n = n;

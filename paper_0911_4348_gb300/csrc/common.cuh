@@ -64,7 +64,7 @@ struct fedvr_ctx {
   int c1_splits = 1;
   // incremented by every fedvr_2b_prepare (batches check it before each step)
   unsigned long long prep_gen = 0;
-  // n of the exchange row table held in w_xrow (0: none)
+  // n of the exchange tile table held in w_xrow (0: none)
   int xrow_n = 0;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;

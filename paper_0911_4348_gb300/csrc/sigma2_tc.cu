@@ -7,10 +7,10 @@
 // The first bracket term is the direct term sigma g o (V Q V), the second the
 // second-order exchange X. P^(b) is the only O(n^3)-per-column contraction
 // (O(n^4) per mesh point): it runs as tcgen05.mma kind::tf32 over the rows
-// (b, a), a >= b, of one mesh point stacked into n(n+1)/2 rows (128 per tile,
-// tiles full except the last; the stacking order walks blocks of 16 b x 8 a,
-// so that a tile touches a few rows of V and g that stay in L1), all k in one
-// or two N tiles and the
+// (b, a), a >= b, of one mesh point, tiled in blocks of 16 values of b x 8
+// values of a (128 rows per tile; the rows a < b of the diagonal blocks are
+// computed and dropped, so that a tile touches exactly 8 rows of V and 16 rows
+// of g), all k in one or two N tiles and the
 // contraction over l in 32-wide chunks, each operand split as x = hi + lo
 // (TF32) and the product taken as hi*hi + hi*lo + lo*hi with FP32
 // accumulation in TMEM. The A operand g_al V_bl of each row is formed by the
@@ -18,7 +18,8 @@
 // row of the mesh point. The direct term's matrix W = V Q V comes from two
 // FP32 GEMMs beforehand, so the epilogue reads row (b, a) of P^(b) from TMEM
 // and folds sum_k V_ak g_kb P_ak in FP32 (two warps per row, one per half of
-// k); the symmetric result is mirrored.
+// k), with the tile's rows of V and g staged in shared memory; the symmetric
+// result is mirrored.
 #include "common.cuh"
 #include "tc.cuh"
 #include "tc_sys.cuh"
@@ -70,9 +71,20 @@ __global__ void split_kernel(int n, long rows, int ld, const double *__restrict_
 // TMA bytes), empty[s] (MMA commit); accumulators double-buffered with
 // accf/acce; the two column halves of a row meet through a small shared
 // buffer handed over with pfull/pempty. Every wait is bounded. The work queue
-// is the concatenation of the (j, row tile) items of every system in the table
+// is the concatenation of the (j, tile) items of every system in the table
 // (mesh-point-major, so that concurrent CTAs share gb in L2); every role walks
 // it in the same order. The stage layout uses the table's largest N.
+//
+// A tile is one block of 16 values of b x 8 values of a (row r of the tile:
+// b = b0 + r / 8, a = a0 + r % 8), every block that holds a pair a >= b; the
+// rows with a < b of the blocks on the diagonal are computed and dropped. The
+// epilogue needs row a of V and row b of g for each row: with `stg` > 0 the
+// epilogue warps first copy the tile's 8 rows of V and 16 rows of g into
+// shared memory (pitch stg floats, stg = 4 mod 32, so that the eight values
+// of a read by a quarter-warp fall into distinct banks and the values of b
+// are broadcasts), double-buffered by tile parity and handed over with the
+// bounded sfull barrier; with stg = 0 (shared memory too small for large n)
+// each lane reads its rows from global memory.
 //
 // FP16 variant: 128-byte operand rows hold 64 FP16 values, so a chunk covers
 // 64 contraction terms and the three products run as kind::f16 at twice the
@@ -100,10 +112,23 @@ __device__ __forceinline__ int x_scale_exp(const TcScale *sc) {
   return e < -100 ? -100 : (e > 100 ? 100 : e);
 }
 
+// Tile t of mesh point j of a system: (j, b0, a0); tiles ascend within a mesh point.
+struct XTile {
+  int j, b0, a0;
+};
+__device__ __forceinline__ XTile x_tile(const XSys &S, long q) {
+  XTile x;
+  x.j = (int)(q / S.tiles_per_j);
+  const uint32_t e = S.tiles[q % S.tiles_per_j];
+  x.b0 = (int)(e >> 16);
+  x.a0 = (int)(e & 0xffffu);
+  return x;
+}
+
 template <bool F16>
 __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     exchange_tc_kernel(const XSys *__restrict__ sys, const long *__restrict__ prefix, int n_sys,
-                       long items, int Np_max, int nbuf, int *err) {
+                       long items, int Np_max, int nbuf, int stg, int *err) {
   using R = XRoles<F16>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -112,10 +137,11 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
   const uint32_t stage_bytes = 2 * kTileA + 2 * tileB;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
   uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *acce = bars + 6, *drain = bars + 8;
-  uint64_t *pfull = bars + 9, *pempty = bars + 11;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 13);
+  uint64_t *pfull = bars + 9, *pempty = bars + 11, *sfull = bars + 13;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 15);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   float *part = reinterpret_cast<float *>(smem + 2 * stage_bytes + kXBarBytes);  // [2][128]
+  float *stage_rows = part + 2 * 128;  // [2][24][stg]: V rows a0.., then g rows b0..
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -135,6 +161,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
     for (int q = 0; q < 2; ++q) {
       tc::mbar_init(&pfull[q], 4);  // the four warps of one column half
       tc::mbar_init(&pempty[q], 4);
+      tc::mbar_init(&sfull[q], R::kEpi);  // every epilogue warp copied its staged rows
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -156,11 +183,8 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
       const int n = S.g.n, ld = S.g.ld, KC = (n + R::kCols - 1) / R::kCols;
-      const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
-      const long q = w - prefix[cur];
-      const int j = (int)(q / RT);
-      const long t = q % RT;
-      const float *const gA = S.g32 + (long)j * n * ld;
+      const XTile xt = x_tile(S, w - prefix[cur]);
+      const float *const gA = S.g32 + (long)xt.j * n * ld;
       const float *const V32 = S.V32;  // in a register across the memory-clobbering asm
       const float fX = F16 ? ldexpf(1.f, x_scale_exp(S.scale)) : 1.f;
       const int u = F16 ? 8 * c : 4 * c;  // first column of this thread's unit in a chunk
@@ -168,16 +192,11 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       bool live[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const long r = t * 128 + r0 + 32 * k;
-        live[k] = r < T;
-        int b = 0, a = 0;
-        if (live[k]) {
-          const uint32_t e = S.rows[r];
-          b = (int)(e >> 16);
-          a = (int)(e & 0xffffu);
-        }
-        og[k] = (uint32_t)(a * ld + u);
-        ov[k] = (uint32_t)(b * ld + u);
+        const int r = r0 + 32 * k;
+        const int b = xt.b0 + (r >> 3), a = xt.a0 + (r & 7);
+        live[k] = a < n && b <= a;  // rows a < b of a diagonal block: computed as zeros
+        og[k] = live[k] ? (uint32_t)(a * ld + u) : 0u;
+        ov[k] = live[k] ? (uint32_t)(b * ld + u) : 0u;
       }
       for (int kc = 0; kc < KC; ++kc, ++cc) {
         const int l0 = kc * R::kCols;
@@ -245,8 +264,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const XSys &S = sys[cur];
         const int n = S.g.n;
-        const long RT = ((long)n * (n + 1) / 2 + 127) / 128;
-        const int j = (int)((w - prefix[cur]) / RT);
+        const int j = (int)((w - prefix[cur]) / S.tiles_per_j);
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
         const int NT = S.g.NT, KC = (n + R::kCols - 1) / R::kCols, jb = S.g.M - 1 - j;
         const int n00 = S.g.n0[0], n01 = S.g.n0[1];
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       }
     }
   } else if (warp == R::kMma) {
-    // ---- MMA issue: one accumulator per row tile ----
+    // ---- MMA issue: one accumulator per tile ----
     if (lane == 0) {
       uint32_t cc = 0, tcount = 0;
       for (long w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++tcount) {
@@ -336,35 +354,51 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       }
     }
   } else if (warp < R::kEpi) {
-    // ---- epilogue, row (b, a) = TMEM lane 32 (warp & 3) + lane; warps 0-3 take the
-    // first half of the columns k, warps 4-7 the second:
+    // ---- epilogue, row (b, a) = TMEM lane 32 (warp & 3) + lane, b = b0 + 4 (warp & 3)
+    // + lane / 8, a = a0 + lane % 8; warps 0-3 take the first half of the columns k,
+    // warps 4-7 the second:
     //   Sigma_ab = sigma g_ab W_ab - sum_k V_ak g_kb P_ak,  W = V Q V ----
     const int quarter = warp & 3, half = warp >> 2, prow = quarter * 32 + lane;
+    const int bl = prow >> 3, al = prow & 7;
     uint32_t tcount = 0;
     for (long w = blockIdx.x; w < items && !tc::warp_flag(abort_flag); w += gridDim.x, ++tcount) {
       while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
       const XSys &S = sys[cur];
       const int n = S.g.n, ld = S.g.ld;
-      const long T = (long)n * (n + 1) / 2, RT = (T + 127) / 128;
-      const long q = w - prefix[cur];
-      const int j = (int)(q / RT);
-      const long r = (q % RT) * 128 + prow;
-      const bool live = r < T;
-      int b = 0, a = 0;
-      if (live) {
-        const uint32_t e = S.rows[r];
-        b = (int)(e >> 16);
-        a = (int)(e & 0xffffu);
-      }
-      const float *gA = S.g32 + (long)j * n * ld;
-      const float *Va = S.V32 + (long)a * ld;  // V_ak = V_ka: row a
-      const float *gb_row = gA + (long)b * ld;  // g_kb = g_bk: row b
+      const XTile xt = x_tile(S, w - prefix[cur]);
+      const int b = xt.b0 + bl, a = xt.a0 + al;
+      const bool live = a < n && b <= a;
+      const float *gA = S.g32 + (long)xt.j * n * ld;
       // FP16 operands carry 2^(eX + kScaleG); undo it on P (an exact power of two)
       const float inv = F16 ? ldexpf(1.f, -(x_scale_exp(S.scale) + kScaleG)) : 1.f;
       const int NC = (n + 15) / 16, hc = (NC + 1) / 2;
       const int cb = half ? hc : 0, ce = half ? NC : hc;
       const int buf = tcount & 1;
       const uint32_t tu = tcount >> 1;
+      // row a of V (V_ak = V_ka) and row b of g (g_kb = g_bk): staged or global
+      const float *Va, *gb_row;
+      if (stg > 0) {
+        float *sb = stage_rows + (size_t)buf * 24 * stg;
+        for (int rr = warp; rr < 24; rr += R::kEpi) {  // rows >= n copy as zeros
+          const int src_row = rr < 8 ? xt.a0 + rr : xt.b0 + rr - 8;
+          const float *src = rr < 8 ? S.V32 + (long)src_row * ld : gA + (long)src_row * ld;
+          for (int c4 = 4 * lane; c4 < ld; c4 += 128) {
+            const float4 v = src_row < n ? *reinterpret_cast<const float4 *>(src + c4)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(sb + rr * stg + c4) = v;
+          }
+        }
+        tc::warp_arrive(&sfull[buf]);
+        if (!tc::warp_wait(&sfull[buf], tu & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        Va = sb + al * stg;
+        gb_row = sb + (8 + bl) * stg;
+      } else {
+        Va = S.V32 + (long)(live ? a : 0) * ld;
+        gb_row = gA + (long)(live ? b : 0) * ld;
+      }
       if (!tc::warp_wait(&accf[buf], tu & 1, kWaitNs)) {
         *abort_flag = 1;
         break;
@@ -378,10 +412,10 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         float4 vc[4], gc[4];
 #pragma unroll
         for (int t4 = 0; t4 < 4; ++t4) {
-          vc[t4] = live ? *reinterpret_cast<const float4 *>(Va + ch * 16 + 4 * t4)
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
-          gc[t4] = live ? *reinterpret_cast<const float4 *>(gb_row + ch * 16 + 4 * t4)
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          vc[t4] = (live || stg > 0) ? *reinterpret_cast<const float4 *>(Va + ch * 16 + 4 * t4)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          gc[t4] = (live || stg > 0) ? *reinterpret_cast<const float4 *>(gb_row + ch * 16 + 4 * t4)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float pv[16];
         tc::tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 16), pv);
@@ -416,7 +450,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       const float X = xh + pb[prow];
       tc::warp_arrive(&pempty[buf]);
       float sig = 0.f;
-      if (live) sig = S.spin * gA[(long)a * ld + b] * S.W[((long)j * n + b) * ld + a] - X;
+      if (live) sig = S.spin * gA[(long)a * ld + b] * S.W[((long)xt.j * n + b) * ld + a] - X;
       if (S.smax) {  // largest |Sigma| entry, for the FP16 operand scale of the convolution
         float mx = fabsf(sig);
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -424,6 +458,7 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
       }
       if (live) {
         const long nn = (long)n * n;
+        const int j = xt.j;
         S.Sigma[(long)j * nn + (long)a * n + b] = (double)sig;
         S.Sigma[(long)j * nn + (long)b * n + a] = (double)sig;
         if (S.S32) {
@@ -516,22 +551,20 @@ cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float 
   return vqv_tc(n, M, ld, V32, g32, VQ, ws + tc_ws_w(n, M), err, s);
 }
 
-void exchange_row_table(int n, std::vector<uint32_t> &rows) {
-  rows.clear();
-  rows.reserve((size_t)n * (n + 1) / 2);
+void exchange_tile_table(int n, std::vector<uint32_t> &tiles) {
+  tiles.clear();
   for (int b0 = 0; b0 < n; b0 += 16)
     for (int a0 = b0; a0 < n; a0 += 8)  // b0 is a multiple of 8: the first a-block on the diagonal
-      for (int b = b0; b < b0 + 16 && b < n; ++b)
-        for (int a = a0 > b ? a0 : b; a < a0 + 8 && a < n; ++a)
-          rows.push_back((uint32_t)b << 16 | (uint32_t)a);
+      tiles.push_back((uint32_t)b0 << 16 | (uint32_t)a0);
 }
 
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
-                      float *S32, const uint32_t *rows, unsigned *smax, const void *h16,
+                      float *S32, const uint32_t *tiles, unsigned *smax, const void *h16,
                       const TcScale *scale) {
-  if (!rows) return cudaErrorInvalidValue;
+  if (!tiles) return cudaErrorInvalidValue;
   d->g = tc_geom(n, M);
-  d->rows = rows;
+  d->tiles = tiles;
+  d->tiles_per_j = (int)exchange_tiles(n);
   const long stack = (long)M * n * d->g.ld;
   d->spin = (float)spin;
   d->g32 = ws;
@@ -559,12 +592,18 @@ cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, doubl
   return cudaSuccess;
 }
 
+size_t exchange_stage_pitch(int ld_max) { return (size_t)ld_max + 4; }
+
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,
                                int Np_max, int ld_max, int *err, int num_sms, cudaStream_t s,
                                bool f16) {
-  (void)ld_max;
-  const size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 128) + kXBarBytes +
-                      kXPartBytes;
+  size_t smem = 1024 + 2 * (2 * (size_t)kTileA + 2 * (size_t)Np_max * 128) + kXBarBytes +
+                kXPartBytes;
+  // the epilogue's staged rows of V and g (two buffers of 24 rows), where they fit
+  const size_t stg = exchange_stage_pitch(ld_max);
+  const size_t staged = smem + 2 * 24 * stg * sizeof(float);
+  const int pitch = staged <= 232448 ? (int)stg : 0;
+  if (pitch) smem = staged;
   const int grid = (int)(items < num_sms ? items : num_sms);
   const int nbuf = (Np_max <= 256) ? 2 : 1;
   cudaError_t e;
@@ -573,13 +612,13 @@ cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, l
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     exchange_tc_kernel<true><<<grid, XRoles<true>::kThreads, smem, s>>>(sys, prefix, n_sys, items,
-                                                                        Np_max, nbuf, err);
+                                                                        Np_max, nbuf, pitch, err);
   } else {
     e = cudaFuncSetAttribute(exchange_tc_kernel<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     exchange_tc_kernel<false><<<grid, XRoles<false>::kThreads, smem, s>>>(
-        sys, prefix, n_sys, items, Np_max, nbuf, err);
+        sys, prefix, n_sys, items, Np_max, nbuf, pitch, err);
   }
   return cudaGetLastError();
 }

@@ -40,7 +40,8 @@ struct XSys {
   CUtensorMap th[2], tl[2];   // gb = G[M-1-j] split, per N tile
   CUtensorMap hh[2], hl[2];   // FP16 path: the FP16 split of g (scaled by 2^kScaleG), per N tile
   const TcScale *scale;       // FP16 path: operand scales
-  const uint32_t *rows;       // stacked row r -> (b << 16) | a (exchange_row_table)
+  const uint32_t *tiles;      // tile t of a mesh point -> (b0 << 16) | a0 (exchange_tile_table)
+  int tiles_per_j;
   TcGeom g;
   float spin;
   const float *g32, *V32;
@@ -73,13 +74,17 @@ size_t tc_smem_bytes(int Np_max, int ld_max, bool with_columns);
 // Host-side descriptor fill (tensor maps included); the caller copies the
 // descriptors to device memory.
 cudaError_t xsys_fill(XSys *d, int n, int M, double spin, const float *ws, double *Sigma,
-                      float *S32, const uint32_t *rows, unsigned *smax = nullptr,
+                      float *S32, const uint32_t *tiles, unsigned *smax = nullptr,
                       const void *h16 = nullptr, const TcScale *scale = nullptr);
-// The exchange kernel's stacking of the rows (b, a >= b) of one mesh point:
-// blocks of 16 values of b x 8 values of a (block-major; b, then a inside a
-// block), packed densely, entry r = (b << 16) | a. Every pair appears once;
-// a 128-row tile then touches 8-24 rows of V and 16-48 rows of g.
-void exchange_row_table(int n, std::vector<uint32_t> &rows);
+// The exchange kernel's tiles of one mesh point: every block of 16 values of b
+// (b0 a multiple of 16) x 8 values of a (a0 a multiple of 8, a0 >= b0) that
+// holds a pair a >= b, b-block-major; entry t = (b0 << 16) | a0.
+void exchange_tile_table(int n, std::vector<uint32_t> &tiles);
+inline long exchange_tiles(int n) {
+  long t = 0;
+  for (int b0 = 0; b0 < n; b0 += 16) t += (n - b0 + 7) / 8;
+  return t;
+}
 cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, const float *S32,
                        const double *dHF, const int4 *coef32, double *I1, double *part,
                        const void *h16 = nullptr, const TcScale *scale = nullptr);
@@ -139,12 +144,10 @@ cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, l
 cudaError_t conv1_tc_launch(const C1Sys *sys, const long *prefix, int n_sys, long items,
                             int Np_max, int *err, int num_sms, cudaStream_t s, bool f16 = false);
 
-// Work items per system: exchange (j, row tile) pairs over the n(n+1)/2
-// stacked rows (b, a >= b) of each mesh point; convolution (row tile, split)
-// pairs over the M*n stacked rows.
-inline long exchange_items(int n, int M) {
-  return (long)M * (((long)n * (n + 1) / 2 + 127) / 128);
-}
+// Work items per system: exchange (j, tile) pairs over the 16 x 8 blocks of
+// each mesh point; convolution (row tile, split) pairs over the M*n stacked
+// rows.
+inline long exchange_items(int n, int M) { return (long)M * exchange_tiles(n); }
 inline long conv1_items(int n, int M, int splits) {
   return ((long)M * n + 127) / 128 * (long)splits;
 }
