@@ -14,7 +14,8 @@ scaling); ranks only meet at the timing barrier.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|tf32|f16]
-                    [--workload he_medium|he_small|h3p_large|he_paper|batch64|warmstart|h3p_curve]
+                    [--workload he_medium|he_small|h3p_large|he_paper|batch64|warmstart|h3p_curve|
+                                combined]
                     [--no-time-to-e0] [--no-fp64-compare] [--no-cpu-baseline]
                     [--train-systems T] [--test-systems H] [--epochs E] [--hidden H]
 """
@@ -42,7 +43,8 @@ METRIC = "Sigma^(2) builds/s (one build + its Dyson iteration per step)"
 UNIT = "builds/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "f16": 3}
 WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large,
-             "he_paper": W.he_paper, "batch64": None, "warmstart": None, "h3p_curve": None}
+             "he_paper": W.he_paper, "batch64": None, "warmstart": None, "h3p_curve": None,
+             "combined": None}
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
 
@@ -275,6 +277,7 @@ def run_reference(args, rank: int):
     make = WORKLOADS[args.workload]
     if make is None:  # families: time the oracle on their first system
         make = {"warmstart": lambda: W.warmstart_system(0),
+                "combined": lambda: W.warmstart_system(0),
                 "h3p_curve": lambda: W.h3p_curve()[0]}.get(args.workload,
                                                            lambda: W.batch_systems(64)[0])
     sys_ = make()
@@ -551,6 +554,121 @@ def run_warmstart(args, dist, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+def run_combined(args, dist, rank, world, local):
+    """Time to a converged E0 (within 1e-6 Ha of each system's FP64 answer) on
+    held-out systems of the warm-start family (20 x 7 points, n_b = 119, 257
+    mesh points): (a) the plain FP64 GPU path, one system after another, run to
+    tol 1e-8 (its converged E0 is the system's E_ref; its own time to E0 is read
+    from its history); (b) the batched, warm-started (network trained on the
+    largest training set), split-precision solver on all held-out systems at
+    once. Also a learning curve: total iterations to E0 of the held-out systems
+    solved one at a time from the network's warm start, for each training-set
+    size. A step is one iteration of one system."""
+    import torch
+    from paper_0911_4348_gb300 import WarmStartNet, solve_2b_batched
+    stream = torch.cuda.current_stream()
+    cid = rank_config(5, rank)
+    sizes = sorted({int(x) for x in args.curve.split(",") if x.strip()})
+    test = [W.warmstart_system(50000 + k, cid) for k in range(args.test_systems)]
+    M = test[0].n_tau
+    prec = split_precision(args)
+    # (a) FP64 reference solves
+    e_ref, fp64 = [], []
+    for s_ in test:
+        c = _context(stream, s_)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = c.solve_2b(s_.beta, s_.u, s_.p, s_.mixing, s_.tol, 200, 0, check=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        hist = c.get_history()
+        e_ref.append(r["E0"])
+        it, sec = _to_e0(hist, r["E0"])
+        fp64.append({"system": s_.name, "E0": r["E0"], "iterations": r["iters"],
+                     "status": r["status"], "solve_seconds": wall,
+                     "iterations_to_E0": it,
+                     "seconds_to_E0": None if sec is None else sec + (wall - float(np.sum(hist[:, 4])) / 1000.0)})
+        c.close()
+    # learning curve: one network per training-set size (same seed, same epochs)
+    curve, net = [], None
+    for T in sizes:
+        if net is not None:
+            net.close()
+        net = WarmStartNet(M, args.hidden, seed=W.MASTER_SEED, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        for k in range(T):
+            s_ = W.warmstart_system(k, cid)
+            c = _context(stream, s_)
+            net.collect(c, s_.beta, s_.u, s_.p)
+            c.close()
+        t_collect = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        loss = net.train(args.epochs, batch=4096, lr=1e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        iters, worst = 0, 0.0
+        for s_, E in zip(test, e_ref):
+            c = _context(stream, s_)
+            c.warm_start(net, s_.beta, s_.u, s_.p, inner_steps=4)
+            r = c.solve_2b(s_.beta, s_.u, s_.p, s_.mixing, s_.tol, 200, prec, check=False)
+            it, _ = _to_e0(c.get_history(), E)
+            iters += it if it is not None else 10 ** 6
+            worst = max(worst, abs(r["E0"] - E))
+            c.close()
+        curve.append({"train_systems": T, "iterations_to_E0": iters, "max_dE0_vs_fp64": worst,
+                      "collect_seconds": t_collect, "train_seconds": t_train,
+                      "final_train_loss": loss})
+    # (b) the combined solver: warm starts from the last network, one batched solve
+    ctxs = [_context(stream, s_) for s_ in test]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, s_ in zip(ctxs, test):
+        c.warm_start(net, s_.beta, s_.u, s_.p, inner_steps=4)
+    torch.cuda.synchronize()
+    t_ws = time.perf_counter() - t0
+    r = solve_2b_batched(ctxs, [s_.beta for s_ in test], [s_.u for s_ in test],
+                         [s_.p for s_ in test], 0.5, 1e-8, 200, prec, check=False)
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    hists = [c.get_history() for c in ctxs]
+    n_it = max(h.shape[0] for h in hists)
+    step_s = np.zeros(n_it)  # wall time of each batched iteration (the same for every system)
+    for h in hists:
+        step_s[: h.shape[0]] = np.maximum(step_s[: h.shape[0]], h[:, 4] / 1000.0)
+    k_all = 0
+    for h, E in zip(hists, e_ref):
+        k, _ = _to_e0(h, E)
+        k_all = max(k_all, k if k is not None else 10 ** 6)
+    t_batch_e0 = t_ws + (t_all - t_ws - float(np.sum(step_s))) + float(np.sum(step_s[:k_all]))
+    net.close()
+    for c in ctxs:
+        c.close()
+    fp64_total = sum(x["seconds_to_E0"] or 0.0 for x in fp64)
+    steps = int(sum(h.shape[0] for h in hists))
+    value = world * steps / max(float(np.sum(step_s)), 1e-9)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+           "warmup": 0, "ms_per_step": 1000.0 * float(np.sum(step_s)) / max(steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.precision, "data": "synthetic",
+           "config": {"workload": "combined solver on held-out warm-start systems: He "
+                                  "(Z~U[1.5,2.5]) / H3+ (R~U[1.2,3.0]), 20 x 7 points "
+                                  f"(n_b={test[0].n_b}), M={M}",
+                      "test_systems": len(test), "train_sizes": sizes, "hidden": args.hidden,
+                      "epochs": args.epochs, "precision": args.precision,
+                      "parallelism": f"replicas x{world}"},
+           "time_to_E0": {"E_ref": "each system's FP64 GPU solve at tol 1e-8",
+                          "fp64_sequential_seconds": fp64_total,
+                          "combined_seconds": t_batch_e0,
+                          "combined_warm_start_seconds": t_ws,
+                          "combined_iterations_to_E0": k_all,
+                          "combined_solve_status": r["status"],
+                          "max_dE0_vs_fp64": float(max(abs(a - b) for a, b in zip(r["E0"], e_ref))),
+                          "speedup": fp64_total / t_batch_e0 if t_batch_e0 > 0 else None},
+           "fp64_per_system": fp64, "learning_curve": curve}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -568,6 +686,8 @@ def main():
     ap.add_argument("--test-systems", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--hidden", type=int, default=512)
+    ap.add_argument("--curve", default="12,48,192",
+                    help="training-set sizes of the combined workload's learning curve")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -584,8 +704,9 @@ def main():
     from paper_0911_4348_gb300 import Context
 
     torch.cuda.set_device(local)
-    if args.workload in ("batch64", "warmstart", "h3p_curve"):
-        (run_warmstart if args.workload == "warmstart" else run_batch)(args, dist, rank, world, local)
+    if args.workload in ("batch64", "warmstart", "h3p_curve", "combined"):
+        {"warmstart": run_warmstart, "combined": run_combined}.get(args.workload, run_batch)(
+            args, dist, rank, world, local)
         if dist:
             dist.destroy_process_group()
         return

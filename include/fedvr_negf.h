@@ -236,7 +236,7 @@ int fedvr_use_graphs(fedvr_ctx *ctx, int enable, int *last_step_graph);
  * only), so S changes only the order of the FP64 additions of the block sums.
  * Candidates: {1, 2, 3, 4, 6, 8, 12, 16}, at most the number of blocks.
  * request = 0 (default): fedvr_2b_prepare times the candidates once per
- * (device, n_b, M) in the process and keeps the fastest; request > 0: use the
+ * (device, n_b, M, precision) in the process and keeps the fastest; request > 0: use the
  * largest candidate <= request (1 = no split; also read by
  * fedvr_conv_sigma_g); request < 0: leave the setting. *in_use (may be NULL)
  * receives S of the currently prepared run (or of the last stage-level
@@ -264,8 +264,14 @@ int fedvr_get_history(const fedvr_ctx *ctx, double *buf, int cap, int *len);
  * ints) may be NULL. All systems advance together on the stream of ctxs[0]:
  * per iteration one tensor-core launch per contraction kernel covers every
  * unconverged system of the batch (a work queue over all systems' tiles), and
- * each system stops updating when its residual is below tol. Requires a split
- * precision (FEDVR_SPLIT_TF32 or FEDVR_SPLIT_F16; FEDVR_FP64 returns
+ * each system stops updating when its residual is below tol. A system with a
+ * warm start set (fedvr_set_initial_sigma, fedvr_warm_start) takes it as in
+ * solve_2b: its warm-start steps run inside the batched iterations (no
+ * exchange work for them; the fixed-Sigma inner steps use mixing 1 and no
+ * convergence test), and the warm start is cleared afterwards. The first
+ * convolution's split count is measured once per batch (fedvr_batch_create;
+ * results do not depend on it beyond the order of FP64 additions). Requires a
+ * split precision (FEDVR_SPLIT_TF32 or FEDVR_SPLIT_F16; FEDVR_FP64 returns
  * FEDVR_ERR_ARG) and distinct contexts on one device. Returns the
  * worst per-system status; each context keeps its history and its last
  * g and Sigma (fedvr_2b_read). */

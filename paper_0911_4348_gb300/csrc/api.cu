@@ -286,14 +286,14 @@ int launch_conv1_single(fedvr_ctx *ctx, int splits, int *err, cudaStream_t s, in
   return FEDVR_OK;
 }
 
-// Measured choice of the first convolution's splits, once per (device, n, M)
-// in this process: every candidate's persistent launch (and split sum) is
+// Measured choice of the first convolution's splits, once per (device, n, M,
+// precision) in this process: every candidate's persistent launch (and split sum) is
 // timed on the prepared buffers and the fastest kept. A candidate takes whole
 // accumulation blocks (S <= the block count), so every choice gives the same
 // block sums and the results differ only in the order in which the FP64
 // partial sums are added; candidates also keep at most 16 work items per SM.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_conv1_splits;
+std::map<std::tuple<int, int, int, int>, int> g_conv1_splits;
 
 int choose_conv1_splits(fedvr_ctx *ctx, float *ws, float *S32, int *err) {
   const int n = ctx->n, M = ctx->M;
@@ -312,7 +312,8 @@ int choose_conv1_splits(fedvr_ctx *ctx, float *ws, float *S32, int *err) {
     for (int S : cand)
       if (S <= ctx->c1_request) best = S;
   } else {
-    const auto key = std::make_tuple(ctx->device, n, M);
+    // the block count, hence the candidate set, depends on the precision
+    const auto key = std::make_tuple(ctx->device, n, M, ctx->precision);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_conv1_splits.find(key);
@@ -1116,12 +1117,14 @@ struct fedvr_batch {
   int Np_max = 16, ld_max = 32;
   size_t off_c = 0, off_px = 0, off_pc = 0, off_err = 0, off_red = 0;
   std::vector<long> px, pc;
+  std::vector<int> S;  // measured split count of each system's first convolution
   std::vector<double> hred;
   std::vector<double> best;
   std::vector<int> grow;
-  // CUDA graph of one batched iteration for the active set `g_active` and mixing `g_mix`
+  // CUDA graph of one batched iteration for the active set `g_active`, the
+  // systems taking a warm-start step `g_warm` and mixing `g_mix`
   cudaGraphExec_t graph = nullptr;
-  std::vector<int> g_active;
+  std::vector<int> g_active, g_warm;
   double g_mix = 0;
   int g_launches = 0;
   ~fedvr_batch() {
@@ -1132,35 +1135,53 @@ struct fedvr_batch {
 
 namespace {
 
+// The next step of a prepared context is a warm-start step: the first step
+// from an initial Sigma, or one of its fixed-Sigma inner steps.
+bool warm_step(const fedvr_ctx *c) {
+  return c->sigma_init_M && c->step_k < (c->warm_inner > 0 ? c->warm_inner : 1);
+}
+
 // Enqueue one batched iteration of the active systems on s (no host sync).
-int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t s, int *launches) {
+// Systems in a warm-start step take their Sigma from the initial one (no
+// exchange work items) and, in the fixed-Sigma inner steps, the full Dyson
+// step (mixing 1).
+int enqueue_batch(fedvr_batch *B, const int *active, const int *warm, double mixing,
+                  cudaStream_t s, int *launches) {
   fedvr_ctx *lead = B->ctxs[0];
   const int n_sys = (int)B->ctxs.size();
   uint8_t *bt = P<uint8_t>(lead->w_btab);
   int *d_err = reinterpret_cast<int *>(bt + B->off_err);
+  const bool f16 = lead->precision == FEDVR_SPLIT_F16;
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
-      if (int r = phase_sigma_pre(B->ctxs[k], false, s, launches, d_err)) return r;
+      if (int r = phase_sigma_pre(B->ctxs[k], warm[k] != 0, s, launches, d_err)) return r;
     }
-  FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
-                                    reinterpret_cast<const long *>(bt + B->off_px), n_sys,
-                                    B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s,
-                                    lead->precision == FEDVR_SPLIT_F16));
-  *launches += 1;
+  if (B->px[n_sys] > 0) {
+    FEDVR_CK(lead, exchange_tc_launch(reinterpret_cast<const XSys *>(bt),
+                                      reinterpret_cast<const long *>(bt + B->off_px), n_sys,
+                                      B->px[n_sys], B->Np_max, B->ld_max, d_err, lead->num_sms, s,
+                                      f16));
+    *launches += 1;
+  }
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
       if (int r = phase_mid(B->ctxs[k], s, launches)) return r;
     }
   FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + B->off_c),
                                  reinterpret_cast<const long *>(bt + B->off_pc), n_sys,
-                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s,
-                                 lead->precision == FEDVR_SPLIT_F16));
+                                 B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s, f16));
   *launches += 1;
   for (int k = 0; k < n_sys; ++k)
     if (active[k]) {
       fedvr_ctx *c = B->ctxs[k];
+      if (B->S[k] > 1) {  // this system's partial stacks into its I1, in a fixed order
+        FEDVR_CK(lead, conv1_sum_splits((long)c->M * c->n * c->n, B->S[k] - 1,
+                                        P<double>(c->w_c1p), P<double>(c->w_I1), s));
+        *launches += 1;
+      }
       if (int r = phase_conv2(c, s, launches, d_err)) return r;
-      if (int r = phase_update(c, mixing, s, launches)) return r;
+      const double mix = (warm[k] && c->warm_inner > 0) ? 1.0 : mixing;
+      if (int r = phase_update(c, mix, s, launches)) return r;
       FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_red + (size_t)k * 3 * sizeof(double),
                                      c->w_red.ptr, 3 * sizeof(double), cudaMemcpyDeviceToDevice,
                                      s));
@@ -1170,7 +1191,7 @@ int enqueue_batch(fedvr_batch *B, const int *active, double mixing, cudaStream_t
 
 // Capture enqueue_batch into B->graph on the lead context's private stream;
 // a refused capture leaves the batch running eagerly (not an error).
-int capture_batch(fedvr_batch *B, const int *active, double mixing) {
+int capture_batch(fedvr_batch *B, const int *active, const int *warm, double mixing) {
   fedvr_ctx *lead = B->ctxs[0];
   const int n_sys = (int)B->ctxs.size();
   if (!lead->cap_stream &&
@@ -1185,7 +1206,7 @@ int capture_batch(fedvr_batch *B, const int *active, double mixing) {
     return FEDVR_OK;
   }
   int launches = 0;
-  const int r = enqueue_batch(B, active, mixing, cs, &launches);
+  const int r = enqueue_batch(B, active, warm, mixing, cs, &launches);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   cudaGraphExec_t exec = nullptr;
@@ -1201,9 +1222,90 @@ int capture_batch(fedvr_batch *B, const int *active, double mixing) {
   }
   B->graph = exec;
   B->g_active.assign(active, active + n_sys);
+  B->g_warm.assign(warm, warm + n_sys);
   B->g_mix = mixing;
   B->g_launches = launches;
   return FEDVR_OK;
+}
+
+// Write each system's first-convolution descriptor with split count
+// min(S, its block count) (partial stacks in the context's w_c1p) and the
+// batch's conv1 work-queue prefix for all systems active.
+int batch_c1_tables(fedvr_batch *B, std::vector<C1Sys> &hc, int S) {
+  fedvr_ctx *lead = B->ctxs[0];
+  const int n_sys = (int)B->ctxs.size();
+  const bool f16 = lead->precision == FEDVR_SPLIT_F16;
+  uint8_t *bt = P<uint8_t>(lead->w_btab);
+  cudaStream_t s = lead->stream;
+  B->pc[0] = 0;
+  for (int k = 0; k < n_sys; ++k) {
+    fedvr_ctx *c = B->ctxs[k];
+    const int NB = conv1_blocks(c->n, c->M, f16);
+    const int Sk = S < NB ? S : NB;
+    const size_t stack = (size_t)c->M * c->n * c->n;
+    if (Sk > 1) ENSURE(c, w_c1p, dsz((size_t)(Sk - 1) * stack));
+    hc[k].S = Sk;
+    hc[k].part = Sk > 1 ? P<double>(c->w_c1p) : nullptr;
+    B->S[k] = Sk;
+    B->pc[k + 1] = B->pc[k] + conv1_items(c->n, c->M, Sk);
+  }
+  FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_c, hc.data(), n_sys * sizeof(C1Sys),
+                                 cudaMemcpyHostToDevice, s));
+  FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_pc, B->pc.data(), (n_sys + 1) * sizeof(long),
+                                 cudaMemcpyHostToDevice, s));
+  return sync(lead);  // the host tables may change right after
+}
+
+// Measured split count of the batch's first convolution: the batched launch
+// (and the split sums) timed on the prepared buffers for S in {1, 2, 3, 4}
+// (each system capped at its own block count; every choice gives the same
+// FP32 block sums, see fedvr_conv1_splits), keeping the fastest (a larger S
+// must win by 3 %). A batch whose work queue already fills the GPU several
+// times over keeps S = 1 without timing; a split request on the lead context
+// (fedvr_conv1_splits) is taken as is.
+int tune_batch_splits(fedvr_batch *B, std::vector<C1Sys> &hc) {
+  fedvr_ctx *lead = B->ctxs[0];
+  const int n_sys = (int)B->ctxs.size();
+  const bool f16 = lead->precision == FEDVR_SPLIT_F16;
+  long items1 = 0;
+  for (fedvr_ctx *c : B->ctxs) items1 += conv1_items(c->n, c->M, 1);
+  int best = 1;
+  if (lead->c1_request > 0) {  // an explicit request on the lead context: no timing
+    for (int S : {1, 2, 3, 4})
+      if (S <= lead->c1_request) best = S;
+  } else if (items1 < 4L * lead->num_sms) {
+    uint8_t *bt = P<uint8_t>(lead->w_btab);
+    int *d_err = reinterpret_cast<int *>(bt + B->off_err);
+    cudaStream_t s = lead->stream;
+    float best_ms = 0.f;
+    for (int S : {1, 2, 3, 4}) {
+      if (int r = batch_c1_tables(B, hc, S)) return r;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // a warm-up launch, then the timed one
+        FEDVR_CK(lead, cudaEventRecord(lead->ev[0], s));
+        FEDVR_CK(lead, conv1_tc_launch(reinterpret_cast<const C1Sys *>(bt + B->off_c),
+                                       reinterpret_cast<const long *>(bt + B->off_pc), n_sys,
+                                       B->pc[n_sys], B->Np_max, d_err, lead->num_sms, s, f16));
+        for (int k = 0; k < n_sys; ++k) {
+          fedvr_ctx *c = B->ctxs[k];
+          if (B->S[k] > 1)
+            FEDVR_CK(lead, conv1_sum_splits((long)c->M * c->n * c->n, B->S[k] - 1,
+                                            P<double>(c->w_c1p), P<double>(c->w_I1), s));
+        }
+        FEDVR_CK(lead, cudaEventRecord(lead->ev[6], s));
+        int h_err = 0;
+        FEDVR_CK(lead, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (int r = sync(lead)) return r;
+        if (int r = flag_status(lead, h_err, d_err)) return r;
+        FEDVR_CK(lead, cudaEventElapsedTime(&ms, lead->ev[0], lead->ev[6]));
+      }
+      if (S == 1 || ms < 0.97f * best_ms) {
+        best = S;
+        best_ms = ms;
+      }
+    }
+  }
+  return batch_c1_tables(B, hc, best);
 }
 
 }  // namespace
@@ -1304,9 +1406,14 @@ int fedvr_batch_create(fedvr_batch **out, fedvr_ctx **ctxs, int n_sys, const dou
   }
   B->px.assign(n_sys + 1, 0);
   B->pc.assign(n_sys + 1, 0);
+  B->S.assign(n_sys, 1);
   B->hred.assign(3 * (size_t)n_sys, 0.0);
   B->best.assign(n_sys, INFINITY);
   B->grow.assign(n_sys, 0);
+  if (int r = tune_batch_splits(B, hc)) {
+    delete B;
+    return r;
+  }
   *out = B;
   return FEDVR_OK;
 }
@@ -1324,15 +1431,17 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
   uint8_t *bt = P<uint8_t>(lead->w_btab);
   auto t0 = std::chrono::steady_clock::now();
   B->px[0] = B->pc[0] = 0;
+  std::vector<int> warm(n_sys, 0);
   for (int k = 0; k < n_sys; ++k) {
     const fedvr_ctx *c = B->ctxs[k];
     if (!c->prepared || c->prep_gen != B->gens[k])
       return fail(lead, FEDVR_ERR_STATE, "system %d was re-prepared or released after the batch was made",
                   k);
-    B->px[k + 1] = B->px[k] + (active[k] ? exchange_items(c->n, c->M) : 0);
-    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M, 1) : 0);
+    warm[k] = active[k] && warm_step(c);
+    B->px[k + 1] = B->px[k] + ((active[k] && !warm[k]) ? exchange_items(c->n, c->M) : 0);
+    B->pc[k + 1] = B->pc[k] + (active[k] ? conv1_items(c->n, c->M, B->S[k]) : 0);
   }
-  if (B->px[n_sys] == 0) return FEDVR_OK;
+  if (B->pc[n_sys] == 0) return FEDVR_OK;
   FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_px, B->px.data(), (n_sys + 1) * sizeof(long),
                                  cudaMemcpyHostToDevice, s));
   FEDVR_CK(lead, cudaMemcpyAsync(bt + B->off_pc, B->pc.data(), (n_sys + 1) * sizeof(long),
@@ -1342,19 +1451,20 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
   // one iteration of the whole batch: replayed from a CUDA graph captured for
   // this active set and mixing, or launched eagerly
   const std::vector<int> act(active, active + n_sys);
-  if (lead->use_graphs && (!B->graph || B->g_active != act || B->g_mix != mixing)) {
+  if (lead->use_graphs &&
+      (!B->graph || B->g_active != act || B->g_warm != warm || B->g_mix != mixing)) {
     if (B->graph) {
       cudaGraphExecDestroy(B->graph);
       B->graph = nullptr;
     }
-    if (int r = capture_batch(B, active, mixing)) return r;
+    if (int r = capture_batch(B, active, warm.data(), mixing)) return r;
   }
   if (B->graph && lead->use_graphs) {
     FEDVR_CK(lead, cudaGraphLaunch(B->graph, s));
     launches = B->g_launches;
     lead->last_step_graph = true;
   } else {
-    if (int r = enqueue_batch(B, active, mixing, s, &launches)) return r;
+    if (int r = enqueue_batch(B, active, warm.data(), mixing, s, &launches)) return r;
     lead->last_step_graph = false;
   }
   FEDVR_CK(lead, cudaMemcpyAsync(B->hred.data(), bt + B->off_red, B->hred.size() * sizeof(double),
@@ -1391,8 +1501,8 @@ int fedvr_batch_step(fedvr_batch *B, double mixing, double tol, int *active, dou
     if (r != r || !is_fin(E)) {
       worst = fail(c, FEDVR_ERR_NAN, "NaN/Inf at iteration %d", c->step_k - 1);
       active[k] = 0;
-    } else if (tol > 0.0 && r < tol) {
-      active[k] = 0;
+    } else if (tol > 0.0 && r < tol && !(warm[k] && c->warm_inner > 0)) {
+      active[k] = 0;  // no convergence test in the fixed-Sigma warm-start steps
     }
   }
   return worst;
@@ -1414,7 +1524,10 @@ int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int 
     int remaining = 0;
     for (int k = 0; k < n_sys; ++k) remaining += active[k] != 0;
     if (!remaining) break;
-    std::vector<int> was(active);
+    std::vector<int> was(active), inner(n_sys, 0);
+    for (int k = 0; k < n_sys; ++k)  // fixed-Sigma warm-start steps: no divergence watch
+      inner[k] = ctxs[k]->sigma_init_M && ctxs[k]->warm_inner > 0 &&
+                 ctxs[k]->step_k < ctxs[k]->warm_inner;
     int r = fedvr_batch_step(B, mixing, tol, active.data(), res.data(), e.data(), nn.data());
     if (r != FEDVR_OK && r != FEDVR_ERR_NAN) {
       fedvr_batch_destroy(B);
@@ -1427,7 +1540,7 @@ int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int 
       if (N_out) N_out[k] = nn[k];
       if (res[k] != res[k]) {
         status[k] = FEDVR_ERR_NAN;
-      } else if (active[k]) {  // still running: watch for a growing residual
+      } else if (active[k] && !inner[k]) {  // still running: watch for a growing residual
         if (res[k] < best[k]) {
           best[k] = res[k];
           grow[k] = 0;
@@ -1442,6 +1555,8 @@ int solve_2b_batched(fedvr_ctx **ctxs, int n_sys, const double *beta, const int 
   fedvr_batch_destroy(B);
   int worst = FEDVR_OK;
   for (int k = 0; k < n_sys; ++k) {
+    ctxs[k]->sigma_init_M = 0;  // a warm start serves one solve, as in solve_2b
+    ctxs[k]->warm_inner = 0;
     if (active[k])
       status[k] = fail(ctxs[k], FEDVR_ERR_NOCONV, "not converged after %d iterations", max_iter);
     if (iters) iters[k] = done[k];

@@ -43,6 +43,7 @@ def test_batched_equals_single_system_solves():
         single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=TF32, check=False))
         c.close()
     ctxs = [_ctx(s) for s in systems]
+    ctxs[0].conv1_splits(1)  # the batch's own split count, as the single solves'
     out = solve_2b_batched(ctxs, [s.beta for s in systems], [s.u for s in systems],
                            [s.p for s in systems], 0.5, 1e-8, 150, TF32, check=False)
     assert out["status"] == min(r["status"] for r in single)
@@ -100,6 +101,7 @@ def test_batched_graph_replay_is_bit_identical():
     for graphs in (False, True):
         ctxs = [_ctx(s) for s in systems]
         ctxs[0].use_graphs(graphs)
+        ctxs[0].conv1_splits(2)  # one split count for both runs (not a timed choice)
         b = Batch(ctxs, [s.beta for s in systems], [s.u for s in systems], [s.p for s in systems])
         rec, used = [], []
         for it in range(40):
@@ -138,10 +140,52 @@ def test_batched_f16_equals_single_system_solves():
         single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=F16, check=False))
         c.close()
     ctxs = [_ctx(s) for s in systems]
+    ctxs[0].conv1_splits(1)
     out = solve_2b_batched(ctxs, [s.beta for s in systems], [s.u for s in systems],
                            [s.p for s in systems], 0.5, 1e-8, 150, F16, check=False)
     for k, s in enumerate(systems):
         assert out["iters"][k] == single[k]["iters"], s.name
         assert out["E0"][k] == single[k]["E0"], s.name
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("inner", [0, 3])
+def test_batched_warm_start_equals_single_warm_starts(inner):
+    # warm starts (an initial Sigma, optionally held fixed for `inner` full Dyson
+    # steps) inside the batched iteration give what solve_2b gives one system at
+    # a time; the initial Sigma is the oracle's Sigma^(2)[g^0] scaled by 0.9
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import solve_2b_batched
+    F16 = 3
+    systems = _systems()[:3]
+    sig0 = []
+    for s in systems:
+        b = O.fedvr_basis(s.n_elem, s.order, s.xmin, s.xmax, s.grid_kind)
+        T, v = O.kinetic(b), O.potential(b["nodes"], s.Z, s.R, s.soft_en)
+        V = O.interaction(b["nodes"], s.soft_ee)
+        hf = O.hf_scf(T + np.diag(v), V, 2.0, s.n_elec // 2, s.beta, tol=1e-12)
+        mesh = O.power_mesh(s.beta, s.u, s.p)
+        G0 = O.g0_mesh(hf["eps"], hf["C"], hf["mu"], mesh["tau"], s.beta)
+        sig0.append(np.ascontiguousarray(0.9 * O.sigma2(G0, V, 2.0)))
+    single = []
+    for s, S0 in zip(systems, sig0):
+        c = _ctx(s)
+        c.conv1_splits(1)
+        c.set_initial_sigma(S0, inner_steps=inner)
+        single.append(c.solve_2b(s.beta, s.u, s.p, 0.5, 1e-8, 150, precision=F16, check=False))
+        c.close()
+    ctxs = [_ctx(s) for s in systems]
+    ctxs[0].conv1_splits(1)
+    for c, S0 in zip(ctxs, sig0):
+        c.set_initial_sigma(S0, inner_steps=inner)
+    out = solve_2b_batched(ctxs, [s.beta for s in systems], [s.u for s in systems],
+                           [s.p for s in systems], 0.5, 1e-8, 150, F16, check=False)
+    for k, s in enumerate(systems):
+        assert single[k]["status"] == 0, s.name
+        assert out["iters"][k] == single[k]["iters"], s.name
+        assert out["E0"][k] == single[k]["E0"], s.name
+        assert out["N"][k] == single[k]["N"], s.name
     for c in ctxs:
         c.close()

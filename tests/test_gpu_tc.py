@@ -462,3 +462,22 @@ def test_bounded_wait_gives_up_and_fails_the_context():
     c2 = Context()
     c2.selftest_wait(True, 1e-3)
     c2.close()
+
+
+def test_measured_split_counts_are_kept_per_precision():
+    # the two split precisions have different accumulation blocks, hence
+    # different candidate split counts: preparing one after the other on the
+    # same (n_b, M) must measure each in its own right
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0911_4348_gb300 import Context
+    s = W.warmstart_system(0)
+    c = Context()
+    c.build_fedvr(s.n_elem, s.pts_per_elem, s.xmin, s.xmax, s.grid_kind)
+    c.set_potential(s.Z, s.R, s.soft_en, s.soft_ee, s.n_elec)
+    c.solve_hf(s.beta, tol=1e-12)
+    for prec in (TF32, F16, TF32):
+        c.prepare_2b(s.beta, s.u, s.p, prec)
+        assert c.conv1_splits() in (1, 2, 3, 4, 6, 8, 12, 16)
+        assert c.step_2b(s.mixing)["status"] == 0
+    c.close()
