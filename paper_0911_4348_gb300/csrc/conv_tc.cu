@@ -563,19 +563,18 @@ __global__ void __launch_bounds__(kThreadsH, 1)
             uint8_t *st = smem + s * stage_bytes;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-              const float y[8] = {fmaf(c1[k], a1[k][0].x, c2[k] * a2[k][0].x),
-                                  fmaf(c1[k], a1[k][0].y, c2[k] * a2[k][0].y),
-                                  fmaf(c1[k], a1[k][0].z, c2[k] * a2[k][0].z),
-                                  fmaf(c1[k], a1[k][0].w, c2[k] * a2[k][0].w),
-                                  fmaf(c1[k], a1[k][1].x, c2[k] * a2[k][1].x),
-                                  fmaf(c1[k], a1[k][1].y, c2[k] * a2[k][1].y),
-                                  fmaf(c1[k], a1[k][1].z, c2[k] * a2[k][1].z),
-                                  fmaf(c1[k], a1[k][1].w, c2[k] * a2[k][1].w)};
+              // c1 Sigma_k1 + c2 Sigma_k2 on pairs of values (packed FP32 pairs:
+              // the same rounding as the scalar multiply and fused multiply-add)
+              const uint64_t C1 = tc::f2_pack(c1[k], c1[k]), C2 = tc::f2_pack(c2[k], c2[k]);
+              const ulonglong2 p1a = *reinterpret_cast<const ulonglong2 *>(&a1[k][0]);
+              const ulonglong2 p1b = *reinterpret_cast<const ulonglong2 *>(&a1[k][1]);
+              const ulonglong2 p2a = *reinterpret_cast<const ulonglong2 *>(&a2[k][0]);
+              const ulonglong2 p2b = *reinterpret_cast<const ulonglong2 *>(&a2[k][1]);
               uint4 hi, lo;
-              tc::f16_split2(y[0], y[1], hi.x, lo.x);
-              tc::f16_split2(y[2], y[3], hi.y, lo.y);
-              tc::f16_split2(y[4], y[5], hi.z, lo.z);
-              tc::f16_split2(y[6], y[7], hi.w, lo.w);
+              tc::f16_split2p(tc::f2_fma(C1, p1a.x, tc::f2_mul(C2, p2a.x)), hi.x, lo.x);
+              tc::f16_split2p(tc::f2_fma(C1, p1a.y, tc::f2_mul(C2, p2a.y)), hi.y, lo.y);
+              tc::f16_split2p(tc::f2_fma(C1, p1b.x, tc::f2_mul(C2, p2b.x)), hi.z, lo.z);
+              tc::f16_split2p(tc::f2_fma(C1, p1b.y, tc::f2_mul(C2, p2b.y)), hi.w, lo.w);
               *reinterpret_cast<uint4 *>(st + off[k]) = hi;
               *reinterpret_cast<uint4 *>(st + kTileA + off[k]) = lo;
             }

@@ -225,19 +225,18 @@ __global__ void __launch_bounds__(XRoles<F16>::kThreads, 1)
         for (int k = 0; k < 4; ++k) {
           const uint32_t off = tc::sw128_offset(r0 + 32 * k, c);
           if constexpr (F16) {
-            float x[8];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              x[4 * h + 0] = gv[k][h].x * vv[k][h].x * fX;
-              x[4 * h + 1] = gv[k][h].y * vv[k][h].y * fX;
-              x[4 * h + 2] = gv[k][h].z * vv[k][h].z * fX;
-              x[4 * h + 3] = gv[k][h].w * vv[k][h].w * fX;
-            }
+            // (g_al V_bl) 2^eX on pairs of values (packed FP32 pairs, the rounding
+            // of the scalar products)
+            const uint64_t FX = tc::f2_pack(fX, fX);
+            const ulonglong2 ga = *reinterpret_cast<const ulonglong2 *>(&gv[k][0]);
+            const ulonglong2 gb = *reinterpret_cast<const ulonglong2 *>(&gv[k][1]);
+            const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(&vv[k][0]);
+            const ulonglong2 vb = *reinterpret_cast<const ulonglong2 *>(&vv[k][1]);
             uint4 hi, lo;
-            tc::f16_split2(x[0], x[1], hi.x, lo.x);
-            tc::f16_split2(x[2], x[3], hi.y, lo.y);
-            tc::f16_split2(x[4], x[5], hi.z, lo.z);
-            tc::f16_split2(x[6], x[7], hi.w, lo.w);
+            tc::f16_split2p(tc::f2_mul(tc::f2_mul(ga.x, va.x), FX), hi.x, lo.x);
+            tc::f16_split2p(tc::f2_mul(tc::f2_mul(ga.y, va.y), FX), hi.y, lo.y);
+            tc::f16_split2p(tc::f2_mul(tc::f2_mul(gb.x, vb.x), FX), hi.z, lo.z);
+            tc::f16_split2p(tc::f2_mul(tc::f2_mul(gb.y, vb.y), FX), hi.w, lo.w);
             *reinterpret_cast<uint4 *>(st + off) = hi;
             *reinterpret_cast<uint4 *>(st + kTileA + off) = lo;
           } else {

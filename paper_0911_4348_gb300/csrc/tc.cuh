@@ -223,6 +223,40 @@ __device__ __forceinline__ void f16_split2(float y0, float y1, uint32_t &hi, uin
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// ---- packed FP32 pairs (sm_100 family: one instruction for two FP32 lanes) ----
+// Two FP32 values in one 64-bit register pair, the first in the low half.
+__device__ __forceinline__ uint64_t f2_pack(float x, float y) {
+  return (uint64_t)__float_as_uint(x) | ((uint64_t)__float_as_uint(y) << 32);
+}
+__device__ __forceinline__ float f2_lo(uint64_t p) { return __uint_as_float((uint32_t)p); }
+__device__ __forceinline__ float f2_hi(uint64_t p) { return __uint_as_float((uint32_t)(p >> 32)); }
+// a * b + c, a * b and a - b on both halves, each rounded to nearest like the
+// scalar FP32 instruction.
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// f16_split2 of a packed pair: the residual y - hi on both halves at once.
+__device__ __forceinline__ void f16_split2p(uint64_t y, uint32_t &hi, uint32_t &lo) {
+  const __half2 h = __floats2half2_rn(f2_lo(y), f2_hi(y));
+  const float2 hf = __half22float2(h);
+  const uint64_t r = f2_sub(y, f2_pack(hf.x, hf.y));
+  const __half2 l = __floats2half2_rn(f2_lo(r), f2_hi(r));
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 // Byte offset of 16-byte chunk c (0..7) of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
