@@ -20,6 +20,10 @@ representation in nonequilibrium Green's function calculations" (arXiv
 * Sec. 3.1 (uniform power mesh, 2up+1 points): ``power_mesh``, ``lag_table``.
 * Sec. 2.3 (total energy "as in" the cited references): ``energy``
   (Galitskii-Migdal form).
+* A fourth-order variant of the "direct integration" of Eq. (deq) (the
+  paper gives no quadrature; the trapezoid with linear lag interpolation is
+  the default reading): ``quad4_weights``, ``cubic_lag``, ``quad="cubic4"``
+  in ``conv1``, ``conv2``, ``energy``, ``solve_2b``.
 * Sec. 2.3 and 3.2 observables: ``density`` (one-electron density from
   g(0^-)) and ``nuclear_repulsion`` (the internuclear term of Eq. h3pv).
 * Pins only: ``mp2`` (closed-shell MP2), ``exact_ground`` /
@@ -659,8 +663,55 @@ def sigma2_bruteforce(g: np.ndarray, gb: np.ndarray, eri: np.ndarray, sigma: flo
 # ---------------------------------------------------------------------------
 
 
+def _lagrange(xs, x: float) -> list:
+    """Values at x of the Lagrange basis polynomials of the nodes xs."""
+    out = []
+    for p in range(len(xs)):
+        v = 1.0
+        for q in range(len(xs)):
+            if q != p:
+                v *= (x - float(xs[q])) / (float(xs[p]) - float(xs[q]))
+        out.append(v)
+    return out
+
+
+def quad4_weights(x: np.ndarray) -> np.ndarray:
+    """Weights of a fourth-order rule for the integral of f over [x_0, x_m] on
+    the points x (any spacing): on each interval [x_q, x_q+1], f is replaced by
+    its cubic through the four points x_s0 .. x_s0+3 with s0 = q - 1 clamped to
+    [0, m - 3] (the stencil is shifted inward at the ends), and the cubic is
+    integrated exactly with the two-point Gauss-Legendre rule (exact for
+    cubics). With fewer than four points the interpolant through all of them
+    is used. Error O(h^4) for smooth f.
+
+    Variant (the paper's "direct integration" gives no rule; the trapezoid is
+    the default reading): it serves the fourth-order Dyson integrals below."""
+    x = np.asarray(x, dtype=np.float64)
+    m = len(x) - 1
+    w = np.zeros(m + 1)
+    g = 1.0 / math.sqrt(3.0)
+    for q in range(m):
+        s0 = 0 if m < 3 else min(max(q - 1, 0), m - 3)
+        st = list(range(s0, min(s0 + 4, m + 1)))
+        h = float(x[q + 1]) - float(x[q])
+        mid = 0.5 * (float(x[q]) + float(x[q + 1]))
+        for node in (mid - 0.5 * h * g, mid + 0.5 * h * g):
+            for p, l in zip(st, _lagrange(x[st], node)):
+                w[p] += 0.5 * h * l
+    return w
+
+
+def cubic_lag(tau: np.ndarray, y: float) -> tuple[int, list]:
+    """Cubic interpolation at y in [-beta, 0] on the mesh: the stencil start s0
+    (the bracket k of y, minus one, clamped to [0, M - 4]) and the Lagrange
+    coefficients of the four mesh points tau_s0 .. tau_s0+3."""
+    k, _ = bracket(tau, y)
+    s0 = min(max(k - 1, 0), len(tau) - 4)
+    return s0, _lagrange(tau[s0:s0 + 4], y)
+
+
 def conv1(dHF: np.ndarray, A: np.ndarray, G: np.ndarray, mesh: dict, beta: float,
-          lag: dict, rows=None) -> np.ndarray:
+          lag: dict, rows=None, quad: str = "trap") -> np.ndarray:
     """I^(1)(tau_i) = (Sigma^HF - Sigma^0) g(tau_i) + int Sigma^corr(tau_i - t) g(t) dt.
 
     Eq. (deq), second line. Reading (the quadrature of the "direct
@@ -670,13 +721,32 @@ def conv1(dHF: np.ndarray, A: np.ndarray, G: np.ndarray, mesh: dict, beta: float
     j = i the left half-interval uses Sigma^corr(0^+) = -A_0 with weight wm_i
     and the right one Sigma^corr(0^-) = A_{M-1} with weight wp_i.
     ``rows`` restricts the output to a subset of i (sampled checks).
+
+    quad="cubic4" (fourth-order variant): each side of the split, [-beta, tau_i]
+    and [tau_i, 0], is integrated with ``quad4_weights`` on its own mesh points,
+    and Sigma^corr at the lags is interpolated by ``cubic_lag`` (``lag`` is then
+    not used).
     """
     M = G.shape[0]
     w, wm, wp = mesh["w"], mesh["wm"], mesh["wp"]
+    tau = mesh["tau"]
     rows = range(M) if rows is None else rows
     out = []
     for i in rows:
         acc = dHF @ G[i]
+        if quad == "cubic4":
+            wl, wr = quad4_weights(tau[:i + 1]), quad4_weights(tau[i:])
+            acc = acc + (-wl[i] * A[0] + wr[0] * A[M - 1]) @ G[i]
+            for j in range(M):
+                if j == i:
+                    continue
+                y, s = lag_point(tau, beta, i, j)
+                s0, cl = cubic_lag(tau, y)
+                wj = wl[j] if j < i else wr[j - i]
+                B = (s * wj) * sum(c * A[s0 + q] for q, c in enumerate(cl))
+                acc = acc + B @ G[j]
+            out.append(acc)
+            continue
         acc = acc + (-wm[i] * A[0] + wp[i] * A[M - 1]) @ G[i]
         for j in range(M):
             if j == i:
@@ -689,13 +759,14 @@ def conv1(dHF: np.ndarray, A: np.ndarray, G: np.ndarray, mesh: dict, beta: float
 
 
 def conv2(I1: np.ndarray, eps: np.ndarray, C: np.ndarray, mu: float, mesh: dict,
-          beta: float, rows=None) -> np.ndarray:
+          beta: float, rows=None, quad: str = "trap") -> np.ndarray:
     """I^(2)(tau_i) = int g^0(tau_i - t) I^(1)(t) dt (Eq. deq, first integral).
 
     Same split trapezoid as ``conv1``; g^0 at every lag is evaluated from
     Eq. (hfgf) (no interpolation): lag < 0 gives C phi(lag) C^T, lag > 0 gives
     -C phi(lag - beta) C^T; at j = i the halves use g^0(0^+) = -g^0(-beta) and
-    g^0(0^-). Plain O(M^2 n^3) loop.
+    g^0(0^-). Plain O(M^2 n^3) loop. quad="cubic4": the two sides of the split
+    with ``quad4_weights`` (g^0 stays exact at every lag).
     """
     tau, w, wm, wp = mesh["tau"], mesh["w"], mesh["wm"], mesh["wp"]
     M = len(tau)
@@ -705,13 +776,19 @@ def conv2(I1: np.ndarray, eps: np.ndarray, C: np.ndarray, mu: float, mesh: dict,
     rows = range(M) if rows is None else rows
     out = []
     for i in rows:
-        acc = (wm[i] * g0_0p + wp[i] * g0_0m) @ I1[i]
+        if quad == "cubic4":
+            wl, wr = quad4_weights(tau[:i + 1]), quad4_weights(tau[i:])
+            wj_of = lambda j, wl=wl, wr=wr, i=i: wl[j] if j < i else wr[j - i]
+            acc = (wl[i] * g0_0p + wr[0] * g0_0m) @ I1[i]
+        else:
+            wj_of = lambda j: w[j]
+            acc = (wm[i] * g0_0p + wp[i] * g0_0m) @ I1[i]
         for j in range(M):
             if j == i:
                 continue
             yl, sg = lag_point(tau, beta, i, j)
             gl = sg * ((C * phi(yl, y, beta)) @ C.T)
-            acc = acc + (w[j] * gl) @ I1[j]
+            acc = acc + (wj_of(j) * gl) @ I1[j]
         out.append(acc)
     return np.stack(out)
 
@@ -742,7 +819,8 @@ def energy(h: np.ndarray, V: np.ndarray, sigma: float, G: np.ndarray, A: np.ndar
     return e - 0.5 * sigma * ec
 
 
-def dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=None) -> dict:
+def dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=None,
+                    quad: str = "trap") -> dict:
     """One step of the second-Born self-consistency (Eq. deq):
     A = Sigma^corr[g] (unless given), dHF = Sigma^HF[g(0^-)] - Sigma^0,
     I1 = conv1, I2 = conv2, g_new = g^0 + I2, g' = (1 - a) g + a sym(g_new),
@@ -752,15 +830,19 @@ def dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=None) -> 
     sequential direct integration g^0 * (Sigma * g) breaks that at the level
     of the quadrature error, so the update takes the symmetric part
     sym(X)_ab = 0.5 (X_ab + X_ba) of g_new. The jump invariant
-    g(0^-) + g(-beta) = 1 is unaffected."""
+    g(0^-) + g(-beta) = 1 is unaffected.
+
+    quad="cubic4": the fourth-order variant of both integrals and of the
+    energy's tau integral (``quad4_weights`` over the whole mesh)."""
     M = G.shape[0]
     if A is None:
         A = sigma2(G, V, sigma)
     dHF = hf_selfenergy(G[M - 1], V, sigma) - hf["Sigma0"]
-    E = energy(h, V, sigma, G, A, mesh["w"])
+    wE = quad4_weights(mesh["tau"]) if quad == "cubic4" else mesh["w"]
+    E = energy(h, V, sigma, G, A, wE)
     Nel = sigma * float(np.trace(G[M - 1]))
-    I1 = conv1(dHF, A, G, mesh, beta, lag)
-    I2 = conv2(I1, hf["eps"], hf["C"], hf["mu"], mesh, beta)
+    I1 = conv1(dHF, A, G, mesh, beta, lag, quad=quad)
+    I2 = conv2(I1, hf["eps"], hf["C"], hf["mu"], mesh, beta, quad=quad)
     Gnew = G0 + I2
     Gnew = 0.5 * (Gnew + Gnew.transpose(0, 2, 1))
     Gnext = (1.0 - mixing) * G + mixing * Gnew
@@ -769,7 +851,7 @@ def dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=None) -> 
 
 
 def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
-             sigma_init=None) -> dict:
+             sigma_init=None, quad: str = "trap") -> dict:
     """Second-Born Matsubara self-consistency (Sec. 2.3 and 3.1).
 
     Reading (the iteration scheme is not given): start from g = g^0; linear
@@ -787,7 +869,8 @@ def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
     converged = False
     for it in range(max_iter):
         step = dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing,
-                               A=sigma_init if (it == 0 and sigma_init is not None) else None)
+                               A=sigma_init if (it == 0 and sigma_init is not None) else None,
+                               quad=quad)
         hist.append((it, step["res"], step["E0"], step["N"]))
         G = step["G"]
         if step["res"] < tol:
