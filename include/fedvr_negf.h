@@ -152,6 +152,15 @@ int fedvr_get_operators(const fedvr_ctx *ctx, double *T, double *v, double *V, d
  * and mu. Returns FEDVR_ERR_NOCONV after max_iter steps. */
 int solve_hf(fedvr_ctx *ctx, double beta, double tol, int max_iter, double *E_hf, double *mu);
 
+/* Chemical potential of the second-Born run (Sec. 2.3: mu enters g^0 through
+ * the Fermi factors of Eq. hfgf; the paper fixes it by the HF normalisation
+ * and keeps it during the iteration). Replaces the HF value for the next
+ * fedvr_2b_prepare / solve_2b until the next solve_hf; drops a prepared run.
+ * Lets a caller re-fix mu between solves (e.g. so that N = n_elec) or show
+ * that N does not depend on mu inside the gap. Errors: FEDVR_ERR_STATE before
+ * solve_hf, FEDVR_ERR_ARG for a non-finite mu. */
+int fedvr_set_mu(fedvr_ctx *ctx, double mu);
+
 /* Copy the HF solution to host (any may be NULL): eps [n_b] ascending, C
  * [n_b][n_b] (column a = orbital a), rho0 = g^0(0^-) [n_b][n_b] and
  * Sigma0 = F - h [n_b][n_b]. */
@@ -242,6 +251,20 @@ int fedvr_use_graphs(fedvr_ctx *ctx, int enable, int *last_step_graph);
  * receives S of the currently prepared run (or of the last stage-level
  * convolution). Takes effect at the next prepare. */
 int fedvr_conv1_splits(fedvr_ctx *ctx, int request, int *in_use);
+
+/* Quadrature of the two Dyson integrals (Eq. deq; the paper's "direct
+ * integration" names no rule). order 2 (default): the split trapezoid with
+ * Sigma^corr linearly interpolated at off-mesh lags, second order in the mesh
+ * spacing. order 4: each side of the split at tau_i integrated with the
+ * exactly integrated cubic of each interval (through the interval's four
+ * nearest mesh points of that side), Sigma^corr interpolated by the cubic
+ * through four mesh points, and the energy's tau integral with the same
+ * rule; fourth order. Order 4 runs on the FP64 path only (a split precision
+ * returns FEDVR_ERR_ARG) and needs M >= 4. Applies to the next
+ * fedvr_2b_prepare / solve_2b and to the stage-level fedvr_conv_sigma_g and
+ * fedvr_conv_g0; drops a prepared run. Errors: FEDVR_ERR_ARG for another
+ * order. */
+int fedvr_set_quadrature(fedvr_ctx *ctx, int order);
 
 /* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
  * [M][n_b][n_b] on host or device; M must match the next solve's mesh; copied

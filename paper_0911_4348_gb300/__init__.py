@@ -215,6 +215,16 @@ class Context:
                                                  C.byref(cur)))
         return cur.value
 
+    def set_mu(self, mu):
+        """Chemical potential of the next second-Born run (``fedvr_set_mu``)."""
+        self._check(self._lib.fedvr_set_mu(self._h, float(mu)))
+
+    def set_quadrature(self, order):
+        """Quadrature of the Dyson integrals (``fedvr_set_quadrature``): 2 = split
+        trapezoid with linear lag interpolation, 4 = the fourth-order variant
+        (FP64 path)."""
+        self._check(self._lib.fedvr_set_quadrature(self._h, int(order)))
+
     def stage_times(self):
         """Device milliseconds of the last step's stages: sigma2, hf+energy,
         conv1, conv2, update, whole step; and its kernel launch count."""

@@ -36,6 +36,8 @@ SIGNATURES = {
     "fedvr_stage_times": (C.c_int, [_vp, _dp, _ip]),
     "fedvr_use_graphs": (C.c_int, [_vp, C.c_int, _ip]),
     "fedvr_conv1_splits": (C.c_int, [_vp, C.c_int, _ip]),
+    "fedvr_set_quadrature": (C.c_int, [_vp, C.c_int]),
+    "fedvr_set_mu": (C.c_int, [_vp, C.c_double]),
     "fedvr_set_initial_sigma": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int]),
     "fedvr_get_history": (C.c_int, [_vp, _dp, C.c_int, _ip]),
     "solve_2b_batched": (C.c_int, [C.POINTER(_vp), C.c_int, _dp, _ip, _ip, C.c_double, C.c_double,

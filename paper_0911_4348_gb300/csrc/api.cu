@@ -124,6 +124,37 @@ int build_mesh(fedvr_ctx *ctx, double beta, int u, int p, bool coef) {
   return FEDVR_OK;
 }
 
+// Tables of the fourth-order variant for the mesh in w_tau (M points).
+int build_quad4(fedvr_ctx *ctx, int M, double beta) {
+  ENSURE(ctx, w_q4coef, (size_t)M * M * sizeof(ConvCoef4));
+  ENSURE(ctx, w_q4W, dsz((size_t)M * M));
+  ENSURE(ctx, w_q4w, dsz(3 * (size_t)M));
+  double *q = P<double>(ctx->w_q4w);
+  FEDVR_CK(ctx, launch_quad4_tables(M, beta, P<double>(ctx->w_tau), P<ConvCoef4>(ctx->w_q4coef),
+                                    P<double>(ctx->w_q4W), q, q + M, q + 2 * M, ctx->stream));
+  return FEDVR_OK;
+}
+
+// The per-i end weights and the energy weights in use: the split trapezoid's
+// (wm, wp, w) or the fourth-order variant's (wL, wR, wE).
+const double *end_weight_left(fedvr_ctx *ctx) {
+  return ctx->quad_order == 4 ? P<double>(ctx->w_q4w) : P<double>(ctx->w_wm);
+}
+const double *end_weight_right(fedvr_ctx *ctx) {
+  return ctx->quad_order == 4 ? P<double>(ctx->w_q4w) + ctx->M : P<double>(ctx->w_wp);
+}
+const double *energy_weights(fedvr_ctx *ctx) {
+  return ctx->quad_order == 4 ? P<double>(ctx->w_q4w) + 2 * ctx->M : P<double>(ctx->w_w);
+}
+
+int check_quad(fedvr_ctx *ctx, int precision, int M) {
+  if (ctx->quad_order != 4) return FEDVR_OK;
+  if (precision != FEDVR_FP64)
+    return fail(ctx, FEDVR_ERR_ARG, "the fourth-order quadrature runs on the FP64 path only");
+  if (M < 4) return fail(ctx, FEDVR_ERR_ARG, "the fourth-order quadrature needs M >= 4");
+  return FEDVR_OK;
+}
+
 int check_mesh_args(fedvr_ctx *ctx, double beta, int u, int p) {
   if (!(beta > 0.0) || !is_fin(beta)) return fail(ctx, FEDVR_ERR_ARG, "beta must be > 0");
   if (u < 1 || p < 1 || p > 60) return fail(ctx, FEDVR_ERR_ARG, "need u >= 1, 1 <= p <= 60");
@@ -409,7 +440,7 @@ int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
   const double *V = P<double>(ctx->b_V);
   FEDVR_CK(ctx, launch_hf_selfenergy(n, ctx->spin, G + (size_t)(M - 1) * nn, V, nullptr,
                                      P<double>(ctx->b_Sigma0), P<double>(ctx->w_dHF), s));
-  FEDVR_CK(ctx, launch_energy(n, M, ctx->spin, P<double>(ctx->b_h), V, G, S, P<double>(ctx->w_w),
+  FEDVR_CK(ctx, launch_energy(n, M, ctx->spin, P<double>(ctx->b_h), V, G, S, energy_weights(ctx),
                               P<double>(ctx->w_part), P<double>(ctx->w_red), s));
   *launches += 4;
   if (is_split(ctx->precision)) {
@@ -430,6 +461,12 @@ int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
 
 // (3) FP64 first convolution (the split path launches its tensor-core kernel instead).
 int phase_conv1_fp64(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
+  if (ctx->quad_order == 4) {
+    FEDVR_CK(ctx, conv1_fp64_q4(ctx->n, ctx->M, P<ConvCoef4>(ctx->w_q4coef), P<double>(ctx->w_dHF),
+                                P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s));
+    *launches += 1;
+    return FEDVR_OK;
+  }
   FEDVR_CK(ctx, conv1_fp64(ctx->n, ctx->M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF),
                            P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s));
   *launches += 1;
@@ -613,7 +650,8 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_G0, &ctx->w_G, &ctx->w_S, &ctx->w_I1, &ctx->w_I2, &ctx->w_t1,
                     &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
                     &ctx->w_K32, &ctx->w_tab, &ctx->w_btab, &ctx->w_c1p,
-                    &ctx->w_coef32, &ctx->w_h16, &ctx->w_xrow, &ctx->w_dens};
+                    &ctx->w_coef32, &ctx->w_h16, &ctx->w_xrow, &ctx->w_dens,
+                    &ctx->w_q4coef, &ctx->w_q4W, &ctx->w_q4w};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -886,6 +924,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
     return fail(ctx, FEDVR_ERR_ARG, "beta differs from the HF solution's beta");
   if (int r = check_precision(ctx, precision, ctx->n)) return r;
   const int n = ctx->n, M = 2 * u * p + 1;
+  if (int r = check_quad(ctx, precision, M)) return r;
   if (ctx->sigma_init_M && ctx->sigma_init_M != M)
     return fail(ctx, FEDVR_ERR_ARG, "initial Sigma has M = %d, mesh has %d", ctx->sigma_init_M, M);
   ctx->prepared = false;
@@ -916,14 +955,19 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
                                   s));
   }
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
+  ctx->M = M;  // the weight accessors below read it
+  if (ctx->quad_order == 4) {
+    if (int r = build_quad4(ctx, M, beta)) return r;
+  }
   double *tau = P<double>(ctx->w_tau), *w = P<double>(ctx->w_w);
   const double *eps = P<double>(ctx->b_eps), *C = P<double>(ctx->b_C);
   // g^0 on the mesh (Eq. hfgf) and the conv2 eigen-kernel, fixed for the run
   FEDVR_CK(ctx, launch_phi_table(n, M, beta, eps, nullptr, ctx->mu, tau, P<double>(ctx->w_phi), s));
   FEDVR_CK(ctx, dgemm(false, true, n, n, n, 1.0, C, n, 0, C, n, 0, P<double>(ctx->w_phi), n, 0.0,
                       P<double>(ctx->w_G0), n, nn, M, s));
-  FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, tau, w, P<double>(ctx->w_wm), P<double>(ctx->w_wp),
-                                    eps, nullptr, ctx->mu, P<double>(ctx->w_K), s));
+  FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, tau, w, end_weight_left(ctx), end_weight_right(ctx),
+                                    eps, nullptr, ctx->mu, P<double>(ctx->w_K), s,
+                                    ctx->quad_order == 4 ? P<double>(ctx->w_q4W) : nullptr));
   if (is_split(precision)) {
     ENSURE(ctx, w_K32, (size_t)n * M * M * sizeof(float));
     FEDVR_CK(ctx, launch_to_f32((size_t)n * M * M, P<double>(ctx->w_K), P<float>(ctx->w_K32), s));
@@ -1025,6 +1069,25 @@ int fedvr_conv1_splits(fedvr_ctx *ctx, int request, int *in_use) {
   if (request > 64) return fail(ctx, FEDVR_ERR_ARG, "at most 64 splits");
   if (request >= 0) ctx->c1_request = request;
   if (in_use) *in_use = ctx->c1_splits;
+  return FEDVR_OK;
+}
+
+int fedvr_set_mu(fedvr_ctx *ctx, double mu) {
+  CHECK_CTX(ctx);
+  if (ctx->stage < 3) return fail(ctx, FEDVR_ERR_STATE, "fedvr_set_mu before solve_hf");
+  if (!is_fin(mu)) return fail(ctx, FEDVR_ERR_ARG, "mu must be finite");
+  ctx->mu = mu;
+  ctx->prepared = false;  // g^0 and the second convolution's table depend on mu
+  drop_graph(ctx);
+  return FEDVR_OK;
+}
+
+int fedvr_set_quadrature(fedvr_ctx *ctx, int order) {
+  CHECK_CTX(ctx);
+  if (order != 2 && order != 4) return fail(ctx, FEDVR_ERR_ARG, "quadrature order must be 2 or 4");
+  ctx->quad_order = order;
+  ctx->prepared = false;  // the tables of a prepared run belong to the old rule
+  drop_graph(ctx);
   return FEDVR_OK;
 }
 
@@ -1640,6 +1703,7 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
   if (n < 1 || n > 1024 || !dHF || !Sigma || !G || !I1)
     return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024 and device buffers");
   if (int r = check_precision(ctx, precision, n)) return r;
+  if (int r = check_quad(ctx, precision, 2 * u * p + 1)) return r;
   ctx->prepared = false;  // the workspace below is shared with a prepared run
   if (int r = build_mesh(ctx, beta, u, p, true)) return r;
   int M = 2 * u * p + 1;
@@ -1688,6 +1752,12 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
     if (int r = sync(ctx)) return r;
     return flag_status(ctx, h_err, err);
   }
+  if (ctx->quad_order == 4) {
+    if (int r = check_quad(ctx, precision, M)) return r;
+    if (int r = build_quad4(ctx, M, beta)) return r;
+    FEDVR_CK(ctx, conv1_fp64_q4(n, M, P<ConvCoef4>(ctx->w_q4coef), dHF, Sigma, G, I1, ctx->stream));
+    return FEDVR_OK;
+  }
   FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), dHF, Sigma, G, I1, ctx->stream));
   return FEDVR_OK;
 }
@@ -1707,9 +1777,16 @@ int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double
   ENSURE(ctx, w_t1, dsz(stack));
   ENSURE(ctx, w_t2, dsz(stack));
   cudaStream_t s = ctx->stream;
+  if (int r = check_quad(ctx, precision, M)) return r;
+  const bool q4 = ctx->quad_order == 4;
+  if (q4) {
+    if (int r = build_quad4(ctx, M, beta)) return r;
+  }
+  const double *qw = q4 ? P<double>(ctx->w_q4w) : nullptr;
   FEDVR_CK(ctx, launch_conv2_kernel(n, M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
-                                    P<double>(ctx->w_wm), P<double>(ctx->w_wp), eps, nullptr, mu,
-                                    P<double>(ctx->w_K), s));
+                                    q4 ? qw : P<double>(ctx->w_wm), q4 ? qw + M : P<double>(ctx->w_wp),
+                                    eps, nullptr, mu, P<double>(ctx->w_K), s,
+                                    q4 ? P<double>(ctx->w_q4W) : nullptr));
   if (is_split(precision)) {  // the split path's products: FP32 table, split TF32 / FP32 GEMMs
     ENSURE(ctx, w_K32, (size_t)n * M * M * sizeof(float));
     ENSURE(ctx, w_red, dsz(8));

@@ -66,6 +66,9 @@ struct fedvr_ctx {
   unsigned long long prep_gen = 0;
   // n of the exchange tile table held in w_xrow (0: none)
   int xrow_n = 0;
+  // quadrature of the Dyson integrals: 2 = split trapezoid with linear lag
+  // interpolation (default), 4 = the fourth-order variant (FP64 path)
+  int quad_order = 2;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
 
@@ -78,7 +81,7 @@ struct fedvr_ctx {
   // solve_2b / stage workspace
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
       w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16,
-      w_xrow, w_dens;
+      w_xrow, w_dens, w_q4coef, w_q4W, w_q4w;
 };
 
 namespace fedvr {
@@ -120,6 +123,18 @@ struct ConvCoef {
 };
 cudaError_t launch_conv_coef(int M, double beta, const double *tau, const double *w,
                              const double *wm, const double *wp, ConvCoef *coef, cudaStream_t s);
+// Fourth-order variant of the Dyson integrals (conv.cu): per (i, j) the rows
+// k0 .. k0 + 3 and weights c[] of the cubic lag interpolation times the side
+// weight (diagonal: c[0] for Sigma_0, c[1] for Sigma_{M-1}).
+struct ConvCoef4 {
+  int k0;
+  int diag;
+  double c[4];
+};
+// coef [M][M]; W [M][M] side weights (0 on the diagonal); wL, wR [M] the end
+// weights of the two sides of the split at tau_i; wE [M] whole-mesh weights.
+cudaError_t launch_quad4_tables(int M, double beta, const double *tau, ConvCoef4 *coef,
+                                double *W, double *wL, double *wR, double *wE, cudaStream_t s);
 
 // linalg.cu
 // C[b] = alpha * op(A[b]) diag(sk[b]) op(B[b]) + beta * C[b]  (row-major, FP64)
@@ -176,9 +191,14 @@ cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaS
 // conv.cu
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
                        const double *G, double *I1, cudaStream_t s);
+cudaError_t conv1_fp64_q4(int n, int M, const ConvCoef4 *coef, const double *dHF,
+                          const double *A, const double *G, double *I1, cudaStream_t s);
+// W (may be NULL): per-(i, j) weights replacing w_j (fourth-order variant;
+// wm, wp are then its end weights wL, wR).
 cudaError_t launch_conv2_kernel(int n, int M, double beta, const double *tau, const double *w,
                                 const double *wm, const double *wp, const double *eps,
-                                const double *mu_dev, double mu_host, double *K, cudaStream_t s);
+                                const double *mu_dev, double mu_host, double *K, cudaStream_t s,
+                                const double *W = nullptr);
 cudaError_t conv2_apply(int n, int M, const double *K, const double *C, const double *I1,
                         double *I2, double *t1, double *t2, cudaStream_t s);
 

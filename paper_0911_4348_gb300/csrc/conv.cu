@@ -21,8 +21,44 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// Rows and weights of the Sigma^corr combination B_ij of one (i, j) entry:
+// linear interpolation (ConvCoef: rows k, k + 1) or the cubic of the
+// fourth-order variant (ConvCoef4: rows k0 .. k0 + 3); the diagonal entry
+// names rows 0 and M - 1 (the jump values) and adds dHF.
+struct CoefView {
+  int r[4];
+  double c[4];
+  int np;
+  bool diag;
+};
+__device__ __forceinline__ CoefView coef_view(const ConvCoef &cf, int M) {
+  CoefView v;
+  v.diag = cf.diag != 0;
+  v.np = 2;
+  v.r[0] = cf.k;
+  v.r[1] = cf.diag ? (M - 1) : (cf.k + 1);
+  v.c[0] = cf.c1;
+  v.c[1] = cf.c2;
+  return v;
+}
+__device__ __forceinline__ CoefView coef_view(const ConvCoef4 &cf, int M) {
+  CoefView v;
+  v.diag = cf.diag != 0;
+  v.np = cf.diag ? 2 : 4;
+  for (int p = 0; p < 4; ++p) {
+    v.r[p] = cf.k0 + p;
+    v.c[p] = cf.c[p];
+  }
+  if (cf.diag) {
+    v.r[0] = 0;
+    v.r[1] = M - 1;
+  }
+  return v;
+}
+
+template <typename Coef>
 __global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M,
-                                                         const ConvCoef *__restrict__ coef,
+                                                         const Coef *__restrict__ coef,
                                                          const double *__restrict__ dHF,
                                                          const double *__restrict__ A,
                                                          const double *__restrict__ G,
@@ -39,9 +75,7 @@ __global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M,
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
   for (int j = 0; j < M; ++j) {
-    const ConvCoef cf = coef[(long)i * M + j];
-    const int k1 = cf.k, k2 = cf.diag ? (M - 1) : (cf.k + 1);
-    const double *A1 = A + (long)k1 * nn, *A2 = A + (long)k2 * nn;
+    const CoefView cv = coef_view(coef[(long)i * M + j], M);
     const double *g = G + (long)j * nn;
     for (int c0 = 0; c0 < n; c0 += BK) {
       for (int e = threadIdx.x; e < BM * BK; e += 256) {
@@ -50,8 +84,10 @@ __global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M,
         double v = 0.0;
         if (a < n && c < n) {
           long off = (long)a * n + c;
-          v = cf.c1 * A1[off] + cf.c2 * A2[off];
-          if (cf.diag) v += dHF[off];
+          v = cv.c[0] * A[(long)cv.r[0] * nn + off] + cv.c[1] * A[(long)cv.r[1] * nn + off];
+          if (cv.np == 4)
+            v += cv.c[2] * A[(long)cv.r[2] * nn + off] + cv.c[3] * A[(long)cv.r[3] * nn + off];
+          if (cv.diag) v += dHF[off];
         }
         As[cc][aa] = v;
       }
@@ -95,9 +131,12 @@ __device__ __forceinline__ double phi_eig(double x, double y, double beta) {
 
 // K[a][i][j]: j != i: sign * w_j * phi_a(y) with y the lag of tau_i - tau_j in
 // [-beta, 0]; j == i: wm_i * (-phi_a(-beta)) + wp_i * phi_a(0).
+// W (fourth-order variant, may be NULL): per-(i, j) weights [M][M] replacing
+// w_j, with wm, wp then the per-i end weights of the two sides of the split.
 __global__ void conv2_kernel_table(int n, int M, double beta, const double *__restrict__ tau,
                                    const double *__restrict__ w, const double *__restrict__ wm,
-                                   const double *__restrict__ wp, const double *__restrict__ eps,
+                                   const double *__restrict__ wp, const double *__restrict__ W,
+                                   const double *__restrict__ eps,
                                    const double *mu_dev, double mu_host, double *__restrict__ K) {
   long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long MM = (long)M * M;
@@ -114,9 +153,86 @@ __global__ void conv2_kernel_table(int n, int M, double beta, const double *__re
     double x = tau[i] - tau[j];
     double sg = 1.0;
     if (j < i) { x = x - beta; sg = -1.0; }
-    v = sg * w[j] * phi_eig(x, y, beta);
+    v = sg * (W ? W[(long)i * M + j] : w[j]) * phi_eig(x, y, beta);
   }
   K[idx] = v;
+}
+
+// ---- fourth-order variant of the integrals (the paper names no quadrature) ----
+
+// Weight of local point jl in the rule for the integral over x[0] .. x[m]: on
+// each interval the cubic through x[s0] .. x[s0 + 3] (s0 = q - 1 clamped to
+// [0, m - 3]; all points when m < 3), integrated by two-point Gauss.
+__device__ double q4_side_weight(const double *x, int m, int jl) {
+  if (m <= 0) return 0.0;
+  const double g = 1.0 / sqrt(3.0);
+  const int ns = m < 3 ? m + 1 : 4;
+  const int qlo = m < 3 ? 0 : max(0, jl - 3), qhi = m < 3 ? m - 1 : min(m - 1, jl + 2);
+  double w = 0.0;
+  for (int q = qlo; q <= qhi; ++q) {
+    const int s0 = m < 3 ? 0 : min(max(q - 1, 0), m - 3);
+    if (jl < s0 || jl >= s0 + ns) continue;
+    const double h = x[q + 1] - x[q], mid = 0.5 * (x[q] + x[q + 1]);
+    for (int e = 0; e < 2; ++e) {
+      const double node = e ? mid + 0.5 * h * g : mid - 0.5 * h * g;
+      double l = 1.0;
+      for (int r = s0; r < s0 + ns; ++r)
+        if (r != jl) l *= (node - x[r]) / (x[jl] - x[r]);
+      w += 0.5 * h * l;
+    }
+  }
+  return w;
+}
+
+// One thread per (i, j): the fourth-order coefficient entry (side weight of j
+// times the cubic's Lagrange coefficients at the lag, anti-periodic sign), the
+// side weight alone (W, for the second convolution's table), and on the
+// diagonal the end weights wL_i, wR_i; row 0 also writes the whole-mesh
+// weights wE (the energy's tau integral).
+__global__ void quad4_tables_kernel(int M, double beta, const double *__restrict__ tau,
+                                    ConvCoef4 *__restrict__ coef, double *__restrict__ W,
+                                    double *__restrict__ wL, double *__restrict__ wR,
+                                    double *__restrict__ wE) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)M * M) return;
+  const int i = (int)(idx / M), j = (int)(idx % M);
+  if (i == 0) wE[j] = q4_side_weight(tau, M - 1, j);
+  ConvCoef4 c;
+  if (i == j) {
+    const double l = q4_side_weight(tau, i, i), r = q4_side_weight(tau + i, M - 1 - i, 0);
+    wL[i] = l;
+    wR[i] = r;
+    W[idx] = 0.0;
+    c.k0 = 0;
+    c.diag = 1;
+    c.c[0] = -l;  // Sigma(0^+) = -Sigma_0
+    c.c[1] = r;   // Sigma(0^-) = Sigma_{M-1}
+    c.c[2] = c.c[3] = 0.0;
+    coef[idx] = c;
+    return;
+  }
+  double y = tau[i] - tau[j], sg = 1.0;
+  if (j < i) {
+    y -= beta;
+    sg = -1.0;
+  }
+  const double wij = j < i ? q4_side_weight(tau, i, j) : q4_side_weight(tau + i, M - 1 - i, j - i);
+  W[idx] = wij;
+  int lo = 0, hi = M - 1;  // bracket: the largest k in [0, M - 2] with tau_k <= y
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (tau[mid] <= y) lo = mid; else hi = mid;
+  }
+  const int s0 = min(max(lo - 1, 0), M - 4);
+  c.k0 = s0;
+  c.diag = 0;
+  for (int p = 0; p < 4; ++p) {
+    double l = 1.0;
+    for (int r = 0; r < 4; ++r)
+      if (r != p) l *= (y - tau[s0 + r]) / (tau[s0 + p] - tau[s0 + r]);
+    c.c[p] = sg * wij * l;
+  }
+  coef[idx] = c;
 }
 
 // FP32 batched GEMM with mixed input/output types (64x64 tiles, 4x4 per thread):
@@ -219,16 +335,34 @@ cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, con
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
                        const double *G, double *I1, cudaStream_t s) {
   dim3 grid((n + BN - 1) / BN, (n + BM - 1) / BM, M);
-  conv1_fp64_kernel<<<grid, 256, 0, s>>>(n, M, coef, dHF, A, G, I1);
+  conv1_fp64_kernel<ConvCoef><<<grid, 256, 0, s>>>(n, M, coef, dHF, A, G, I1);
+  return cudaGetLastError();
+}
+
+cudaError_t conv1_fp64_q4(int n, int M, const ConvCoef4 *coef, const double *dHF,
+                          const double *A, const double *G, double *I1, cudaStream_t s) {
+  if (M < 4) return cudaErrorInvalidValue;
+  dim3 grid((n + BN - 1) / BN, (n + BM - 1) / BM, M);
+  conv1_fp64_kernel<ConvCoef4><<<grid, 256, 0, s>>>(n, M, coef, dHF, A, G, I1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad4_tables(int M, double beta, const double *tau, ConvCoef4 *coef,
+                                double *W, double *wL, double *wR, double *wE, cudaStream_t s) {
+  if (M < 4) return cudaErrorInvalidValue;
+  const long mm = (long)M * M;
+  quad4_tables_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(M, beta, tau, coef, W, wL, wR,
+                                                                  wE);
   return cudaGetLastError();
 }
 
 cudaError_t launch_conv2_kernel(int n, int M, double beta, const double *tau, const double *w,
                                 const double *wm, const double *wp, const double *eps,
-                                const double *mu_dev, double mu_host, double *K, cudaStream_t s) {
+                                const double *mu_dev, double mu_host, double *K, cudaStream_t s,
+                                const double *W) {
   long cnt = (long)n * M * M;
-  conv2_kernel_table<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(n, M, beta, tau, w, wm, wp, eps,
-                                                                  mu_dev, mu_host, K);
+  conv2_kernel_table<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(n, M, beta, tau, w, wm, wp, W,
+                                                                  eps, mu_dev, mu_host, K);
   return cudaGetLastError();
 }
 
