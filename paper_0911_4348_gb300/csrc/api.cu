@@ -399,7 +399,11 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, in
   }
   if (ctx->precision == FEDVR_SPLIT_F16) {  // FP16 operands of g; the Sigma bound restarts
     if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
-    FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err));
+    float *ws, *S32;
+    int *own;
+    if (int r = tc_workspace(ctx, n, M, &ws, &S32, &own)) return r;
+    // with the FP32 copy of g for the exchange's producers and V Q V (ws offset 0)
+    FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err, warm ? nullptr : ws));
     FEDVR_CK(ctx, cudaMemsetAsync(&scale->maxS, 0, sizeof(unsigned), s));
     *launches += 1;
   }
@@ -422,8 +426,8 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, in
     float *ws, *S32;
     int *own_err;
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &own_err)) return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale, err));
-    *launches += 4;  // splits of g and V, VQ, W = (VQ) V
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale, err, scale != nullptr));
+    *launches += scale ? 3 : 4;  // splits of g (TF32 path) and V, VQ, W = (VQ) V
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
                               P<double>(ctx->w_t3), s));
@@ -942,7 +946,7 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ENSURE(ctx, w_t2, dsz(stack));
   ENSURE(ctx, w_t3, dsz(stack));
   ENSURE(ctx, w_dHF, dsz(nn));
-  ENSURE(ctx, w_part, dsz((size_t)M + 3 * (size_t)n));
+  ENSURE(ctx, w_part, dsz(4 * (size_t)M + 3 * (size_t)n));  // launch_energy's partials
   ENSURE(ctx, w_red, dsz(8));
   if (is_split(precision)) {
     float *ws, *S32;
@@ -1670,12 +1674,12 @@ int fedvr_sigma2(fedvr_ctx *ctx, int n, int M, double spin, const double *V, con
       TcScale *scale;
       if (int r = f16_workspace(ctx, n, M, &h16, &scale)) return r;
       FEDVR_CK(ctx, launch_scale_init(0, nullptr, n, V, scale, s));
-      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err));
+      FEDVR_CK(ctx, launch_split_f16(n, M, G, h16, s, err, ws));
     }
     if (int r = upload_single_tables(ctx, n, M, ws, Sigma, nullptr, nullptr, nullptr, nullptr, 1,
                                      nullptr, spin))
       return r;
-    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !f16, err));
+    FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !f16, err, f16));
     const TcGeom g = tc_geom(n, M);
     uint8_t *tab = P<uint8_t>(ctx->w_tab);
     FEDVR_CK(ctx, exchange_tc_launch(reinterpret_cast<const XSys *>(tab + kTabX),

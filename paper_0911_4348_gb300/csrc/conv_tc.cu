@@ -747,21 +747,28 @@ __global__ void __launch_bounds__(kThreadsH, 1)
 // FP16 split of g scaled by 2^kScaleG; one warp per row, two columns per lane.
 // A scaled entry at or above FP16's largest finite value (|g| >= 65504 / 2^12,
 // just below 16) or not finite cannot be represented: the warp raises bit 1
-// (value 2) of *flag and the caller reports the input as out of range.
+// (value 2) of *flag and the caller reports the input as out of range. With
+// g32 the same pass also writes the FP32 copy of g (pitch ld32, zero padded):
+// one read of g and one FP64-to-FP32 conversion per entry serve both, the
+// scaling then being an exact FP32 multiplication by 2^kScaleG.
 __global__ void split_f16_kernel(int n, long rows, int ld16, const double *__restrict__ G,
                                  uint32_t *__restrict__ hi, uint32_t *__restrict__ lo,
-                                 int *flag) {
+                                 int *flag, float *__restrict__ g32, int ld32) {
   const int lane = threadIdx.x & 31;
   const long wpb = blockDim.x >> 5, nw = (long)gridDim.x * wpb;
-  const double sc = (double)(1 << kScaleG);
+  const float sc = (float)(1 << kScaleG);
   bool bad = false;
   for (long row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += nw) {
     const double *src = G + row * n;
     const long o = row * (ld16 / 2);
     for (int c0 = 0; c0 < ld16; c0 += 64) {
       const int c = c0 + 2 * lane;
-      const float y0 = (c < n) ? (float)(src[c] * sc) : 0.f;
-      const float y1 = (c + 1 < n) ? (float)(src[c + 1] * sc) : 0.f;
+      const float x0 = (c < n) ? (float)src[c] : 0.f;
+      const float x1 = (c + 1 < n) ? (float)src[c + 1] : 0.f;
+      if (g32 && c < ld32) {  // ld32 is even: the pair lies inside the row
+        *reinterpret_cast<float2 *>(g32 + row * ld32 + c) = make_float2(x0, x1);
+      }
+      const float y0 = x0 * sc, y1 = x1 * sc;
       bad |= !(fabsf(y0) < 65504.f) || !(fabsf(y1) < 65504.f);
       uint32_t h, l;
       tc::f16_split2(y0, y1, h, l);
@@ -843,11 +850,12 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
 }
 
 cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s,
-                             int *flag) {
+                             int *flag, float *g32) {
   const int ld16 = ld16_of(n);
   uint32_t *hi = reinterpret_cast<uint32_t *>(h16);
   uint32_t *lo = hi + (size_t)M * n * ld16 / 2;
-  split_f16_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld16, G, hi, lo, flag);
+  split_f16_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld16, G, hi, lo, flag, g32,
+                                        (n + 31) / 32 * 32);
   return cudaGetLastError();
 }
 

@@ -535,14 +535,15 @@ int sigma2_tc_max_n() {
 }
 
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
-                          cudaStream_t s, bool tf32_operands, int *err) {
+                          cudaStream_t s, bool tf32_operands, int *err, bool g32_ready) {
   const int ld = (n + 31) / 32 * 32;
   const long stack = (long)M * n * ld;
   float *g32 = ws, *gh = ws + stack, *gl = ws + 2 * stack, *VQ = ws + 3 * stack;
   float *V32 = ws + 4 * stack;
-  // the FP16 path takes gb from the FP16 split of g: only g32 is needed here
-  split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, tf32_operands ? gh : nullptr,
-                                    tf32_operands ? gl : nullptr);
+  // the FP16 path takes gb from the FP16 split of g, which also made g32
+  if (tf32_operands || !g32_ready)
+    split_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld, G, g32, tf32_operands ? gh : nullptr,
+                                      tf32_operands ? gl : nullptr);
   split_kernel<<<64, 256, 0, s>>>(n, (long)n, ld, V, V32, nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

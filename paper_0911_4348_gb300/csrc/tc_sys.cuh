@@ -93,9 +93,10 @@ inline int ld16_of(int n) { return (n + 63) / 64 * 64; }
 // FP16 split of g (scaled by 2^kScaleG) into h16 = [hi stack][lo stack],
 // [M][n][ld16] halves each, padding zero. An entry the split cannot hold
 // (|g| >= 65504 / 2^kScaleG or not finite) raises bit 1 (value 2) of *flag
-// (the tensor-core error flag; may be NULL).
+// (the tensor-core error flag; may be NULL). With g32 (may be NULL) the same
+// pass writes the FP32 copy of g ([M][n][ld], ld = n rounded up to 32).
 cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s,
-                             int *flag);
+                             int *flag, float *g32 = nullptr);
 // scale->maxC = max |c1| + |c2| over the coefficient table, scale->maxV =
 // max |V| over the n x n interaction matrix, scale->maxS = 0.
 cudaError_t launch_scale_init(int M, const int4 *coef32, int n, const double *V, TcScale *scale,
@@ -125,9 +126,10 @@ inline size_t tc_ws_floats(int n, int M) { return tc_ws_w(n, M) + tc_ws_stack(n,
 
 // Per-system preparation of the exchange operands (FP32 copies of G and V,
 // VQ and W = (VQ) V, and with tf32_operands the TF32 split of G for the gb
-// operand); err is raised if a tensor-core wait gives up.
+// operand); g32_ready: the FP32 copy of G is already in ws (made by the FP16
+// split). err is raised if a tensor-core wait gives up.
 cudaError_t sigma2_tc_pre(int n, int M, const double *V, const double *G, float *ws,
-                          cudaStream_t s, bool tf32_operands, int *err);
+                          cudaStream_t s, bool tf32_operands, int *err, bool g32_ready = false);
 // Split-TF32 tensor-core products (gemm_tc.cu). vqv_tc: VQ_j = V (g_j o
 // g_{M-1-j}) and W_j = VQ_j V for all j (FP32 stacks of row pitch ld).
 // conv2_tc: I2_i = C sum_j diag(K(i, j)) C^T I1_j as three products (K32 the

@@ -7,11 +7,14 @@
 namespace fedvr {
 namespace {
 
-// g_new = g^0 + I2; g' = (1 - a) g + a (g_new_ab + g_new_ba) / 2;
-// res = max |g' - g| (bit pattern of a non-negative double; NaN propagates as
-// the largest pattern). Each g_new is formed once per element (shared with its
-// mirror through shared memory) and the mix is one fused multiply-add, so an
-// element costs four FP64 operations: at GB300's FP64 rate that, not HBM,
+// g_new = g^0 + I2; g' = (1 - a) g + a (g_new_ab + g_new_ba) / 2, evaluated as
+// t = (g_new_ab + g_new_ba) / 2 - g (one add per pair, one fused multiply-add
+// per element), g' = g + a t (fused), d = g' - g; res = max |d|, kept as the
+// integer maximum of |d|'s bit pattern (the sign bit cleared), which orders
+// non-negative doubles like their values and puts Inf and NaN above every
+// finite value, so the comparison costs no FP64 instruction. An element then
+// costs 4.5 FP64 instructions (the g_new add, half the pair add, two fused
+// multiply-adds, the difference): at GB300's FP64 issue rate that, not HBM,
 // bounds this kernel.
 //
 // One block per pair of 32 x 32 tiles (P, Q) = (rows ta, cols tb) and its
@@ -20,11 +23,12 @@ namespace {
 // of every element comes from shared memory instead of a strided global read.
 constexpr int kUT = 32;
 
-__device__ __forceinline__ double upd_one(double gab, double gba, double old, double keep,
-                                          double half_mix, double &m, bool &bad) {
-  const double nw = fma(half_mix, gab + gba, keep * old);
-  const double d = fabs(nw - old);
-  if (d != d || d == INFINITY) bad = true; else m = fmax(m, d);
+__device__ __forceinline__ double upd_one(double s, double old, double mixing,
+                                          unsigned long long &m) {
+  const double nw = fma(mixing, fma(0.5, s, -old), old);
+  const unsigned long long d =
+      (unsigned long long)__double_as_longlong(nw - old) & 0x7fffffffffffffffull;
+  m = d > m ? d : m;
   return nw;
 }
 
@@ -37,9 +41,7 @@ __global__ void __launch_bounds__(256) update_kernel(int n, int M, int nt, doubl
   const long nn = (long)n * n;
   const long pairs = (long)nt * (nt + 1) / 2;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  const double keep = 1.0 - mixing, half_mix = 0.5 * mixing;
-  double m = 0.0;
-  bool bad = false;
+  unsigned long long m = 0ull;
   for (long w = blockIdx.x; w < (long)M * pairs; w += gridDim.x) {
     const int j = (int)(w / pairs);
     long p = w % pairs;
@@ -75,22 +77,22 @@ __global__ void __launch_bounds__(256) update_kernel(int n, int M, int nt, doubl
     for (int q = 0; q < 4; ++q) {
       const int r = ty + 8 * q;
       const int a = ta * kUT + r, b = tb * kUT + tx;
-      if (a < n && b < n)  // element (a, b) pairs with (b, a) = Q[tx][r]
-        G[base + (long)a * n + b] = upd_one(P[r][tx], Q[tx][r], oP[q], keep, half_mix, m, bad);
+      // element (a, b) pairs with (b, a) = Q[tx][r]; the pair's sum serves both
+      const double sab = P[r][tx] + Q[tx][r];
+      if (a < n && b < n) G[base + (long)a * n + b] = upd_one(sab, oP[q], mixing, m);
       if (ta != tb) {
         const int a2 = tb * kUT + r, b2 = ta * kUT + tx;
         if (a2 < n && b2 < n)
-          G[base + (long)a2 * n + b2] = upd_one(Q[r][tx], P[tx][r], oQ[q], keep, half_mix, m, bad);
+          G[base + (long)a2 * n + b2] = upd_one(Q[r][tx] + P[tx][r], oQ[q], mixing, m);
       }
     }
     __syncthreads();
   }
   for (int o = 16; o > 0; o >>= 1) {
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    bad = __shfl_xor_sync(0xffffffffu, (int)bad, o) || bad;
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
   }
-  if (bad) m = __longlong_as_double(0x7ff8000000000000LL);  // NaN: the largest pattern here
-  if ((threadIdx.x & 31) == 0) atomicMax(res_bits, (unsigned long long)__double_as_longlong(m));
+  if ((threadIdx.x & 31) == 0) atomicMax(res_bits, m);
 }
 
 // Fixed-order block sum (blockDim.x = 256).
@@ -107,17 +109,26 @@ __device__ double block_sum256(double v) {
   return r;
 }
 
-// part[j] = sum_ab A[M-1-j]_ab G[j]_ab  (one block per j)
+// part[j kE + c] = sum over chunk c of the n^2 entries of A[M-1-j] o G[j]
+// (kE blocks per mesh point, so that the M kE blocks fill the GPU; the chunks
+// are added in a fixed order by energy_final_kernel).
+constexpr int kE = 4;
 __global__ void energy_part_kernel(int n, int M, const double *__restrict__ G,
                                    const double *__restrict__ A, double *__restrict__ part) {
-  int j = blockIdx.x;
-  long nn = (long)n * n;
+  const int j = blockIdx.x / kE, c = blockIdx.x % kE;
+  const long nn = (long)n * n;
+  const long lo = nn * c / kE, hi = nn * (c + 1) / kE;
   const double *g = G + (long)j * nn;
   const double *s = A + (long)(M - 1 - j) * nn;
-  double acc = 0.0;
-  for (long e = threadIdx.x; e < nn; e += blockDim.x) acc += s[e] * g[e];
-  acc = block_sum256(acc);
-  if (threadIdx.x == 0) part[j] = acc;
+  double acc0 = 0.0, acc1 = 0.0;
+  long e = lo + threadIdx.x;
+  for (; e + 256 < hi; e += 512) {  // two independent loads in flight per thread
+    acc0 = fma(s[e], g[e], acc0);
+    acc1 = fma(s[e + 256], g[e + 256], acc1);
+  }
+  if (e < hi) acc0 = fma(s[e], g[e], acc0);
+  const double acc = block_sum256(acc0 + acc1);
+  if (threadIdx.x == 0) part[(long)j * kE + c] = acc;
 }
 
 // Row partials of the one-body energy terms, one block per row a:
@@ -181,7 +192,11 @@ __global__ void energy_final_kernel(int n, int M, double spin, const double *__r
     }
   }
   if (part)
-    for (int j = threadIdx.x; j < M; j += blockDim.x) ec += w[j] * part[j];
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+      double pj = 0.0;
+      for (int c = 0; c < kE; ++c) pj += part[(long)j * kE + c];
+      ec += w[j] * pj;
+    }
   e1 = block_sum256(e1);
   e2 = block_sum256(e2);
   tr = block_sum256(tr);
@@ -239,13 +254,14 @@ cudaError_t launch_update(int n, int M, double mixing, const double *G0, const d
   return cudaGetLastError();
 }
 
-// part holds M + 3 n doubles: the per-mesh-point correlation sums, then the row partials.
+// part holds kE M + 3 n doubles: the per-mesh-point correlation sums in kE
+// chunks, then the row partials.
 cudaError_t launch_energy(int n, int M, double spin, const double *h, const double *V,
                           const double *G, const double *A, const double *w, double *part,
                           double *out, cudaStream_t s) {
-  energy_part_kernel<<<M, 256, 0, s>>>(n, M, G, A, part);
-  energy_rows_kernel<<<n, 256, 0, s>>>(n, M, spin, h, V, G, part + M);
-  energy_final_kernel<<<1, 256, 0, s>>>(n, M, spin, h, V, G, w, part, part + M, out);
+  energy_part_kernel<<<M * kE, 256, 0, s>>>(n, M, G, A, part);
+  energy_rows_kernel<<<n, 256, 0, s>>>(n, M, spin, h, V, G, part + (long)kE * M);
+  energy_final_kernel<<<1, 256, 0, s>>>(n, M, spin, h, V, G, w, part, part + (long)kE * M, out);
   return cudaGetLastError();
 }
 
