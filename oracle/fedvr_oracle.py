@@ -26,6 +26,11 @@ representation in nonequilibrium Green's function calculations" (arXiv
   in ``conv1``, ``conv2``, ``energy``, ``solve_2b``.
 * Sec. 2.3 and 3.2 observables: ``density`` (one-electron density from
   g(0^-)) and ``nuclear_repulsion`` (the internuclear term of Eq. h3pv).
+* Sec. 2, Eqs. (kbe), (skkbe), (skkbesigma) with (sigmahf), (sigma2ndb) on the
+  Keldysh components: ``kbe_propagate`` (real-time two-time Kadanoff-Baym
+  propagation from an uncorrelated initial state) and its self-energy
+  ``sigma2_realtime``; pin only: ``exact_dynamics`` (two-electron
+  Schroedinger evolution on the same grid).
 * Pins only: ``mp2`` (closed-shell MP2), ``exact_ground`` /
   ``exact_ground_state`` / ``exact_density`` (exact two-electron ground state
   on the same grid).
@@ -878,6 +883,162 @@ def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
             break
     return dict(G=G, Sigma=step["Sigma"], E0=step["E0"], N=step["N"], iters=len(hist),
                 converged=converged, history=hist, mesh=mesh, G0=G0)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2, Eqs. (kbe), (skkbe), (skkbesigma): real-time Kadanoff-Baym equations
+# ---------------------------------------------------------------------------
+
+
+def sigma2_realtime(g: np.ndarray, gb: np.ndarray, V: np.ndarray, sigma: float) -> np.ndarray:
+    """Second-Born self-energy of Eq. (sigma2ndb) for complex two-time
+    matrices: g = the Green's function at (t, t'), gb = minus the other
+    Keldysh component at (t', t) (indices kept: gb_lk is line l -> k from t'
+    back to t), in the convention L = -i G^< (so L(t, t) = rho) and
+    Gt = -i G^>:
+
+      -i Sigma^<(t, t') = S(L(t, t'), -Gt(t', t)),
+      -i Sigma^>(t, t') = S(Gt(t, t'), -L(t', t)),
+      S(g, gb) = sigma g o (V (g o gb^T) V) - X,  X_ab = sum_kl V_ak V_bl g_al gb_lk g_kb.
+
+    The polarisation bubble pairs g_kl(t, t') with the reversed line
+    gb_lk(t', t), hence the transpose; for the real symmetric Matsubara
+    functions of ``sigma2_tau`` (g(tau) and gb = g(-beta - tau)) the two forms
+    coincide. Reading (as for the Matsubara form): the time-consistent pairing
+    u_13 u_24 of Eq. (sigma2ndb)."""
+    Q = g * gb.T
+    D = sigma * g * (V @ Q @ V)
+    n = g.shape[0]
+    X = np.empty_like(g)
+    for b in range(n):
+        P = g @ (V[b][:, None] * gb)      # P_ak = sum_l g_al V_bl gb_lk
+        X[:, b] = (V * P) @ g[:, b]       # X_ab = sum_k V_ak P_ak g_kb
+    return D - X
+
+
+def kbe_propagate(h: np.ndarray, V: np.ndarray, sigma: float, rho0: np.ndarray, dt: float,
+                  n_steps: int, dv: np.ndarray = None, second_born: bool = True) -> dict:
+    """Two-time Kadanoff-Baym propagation (Eqs. kbe, skkbe with the self-energy
+    of Eq. skkbesigma: the time-local HF part of Eq. sigmahf plus second Born)
+    on the uniform grid t_k = k dt, k = 0 .. n_steps.
+
+    Reading (the paper states the equations, with initial correlations by the
+    mixed Green's function, and runs only the equilibrium problem): the
+    initial state is uncorrelated, L(0, 0) = rho0 (the one-particle density
+    matrix per spin of a Slater determinant or thermal HF state), so the
+    contour reduces to the real-time branches and the collision integrals start
+    at t = 0. With L = -i G^< and Gt = -i G^> (L(t, t) = rho(t),
+    Gt(t, t) = rho(t) - 1, L(t', t) = L(t, t')^H, Gt likewise) the equation for
+    the first time argument reads
+
+      d/dt F(t, t') = -i h_HF(t) F(t, t') + K_F(t, t'),   F = L or Gt,
+      K_L = int_0^t [s^> - s^<](t, s) L(s, t') ds + int_0^t' s^<(t, s) [L - Gt](s, t') ds,
+      K_G = int_0^t [s^> - s^<](t, s) Gt(s, t') ds + int_0^t' s^>(t, s) [L - Gt](s, t') ds,
+
+    s^x = -i Sigma^x (``sigma2_realtime``), h_HF(t) = h + diag(dv(t)) +
+    Sigma^HF[rho(t)]; the equal-time density follows
+    d rho/dt = X + X^H with X = -i h_HF rho + K_L(t, t) (the adjoint equation
+    gives the second argument). The integrals use the trapezoid on the grid and
+    each step is Heun's predictor-corrector (second order in dt): the new time
+    row F(t_N+1, t_j) and rho(t_N+1) from the right-hand sides at t_N, then
+    again with those at the predicted t_N+1.
+
+    Returns rho [n_steps+1][n][n] (complex), L, Gt [T][T][n][n], the energy
+    E(t) = sigma Tr[h rho] + (sigma/2) Tr[Sigma^HF rho] + (sigma/2) Re Tr[i K_L(t, t)]
+    (the one-body part with h(t), the HF interaction and the correlation
+    energy from the collision integral; conserved without dv) and
+    N(t) = sigma Tr rho. ``second_born`` False: time-dependent HF."""
+    n = h.shape[0]
+    T = n_steps + 1
+    L = np.zeros((T, T, n, n), complex)
+    G = np.zeros((T, T, n, n), complex)
+    sL = np.zeros((T, T, n, n), complex)
+    sG = np.zeros((T, T, n, n), complex)
+    hHF = np.zeros((T, n, n), complex)
+    ident = np.eye(n)
+    L[0, 0] = rho0
+    G[0, 0] = rho0 - ident
+
+    def h_at(i):
+        return h + (np.diag(dv[i]) if dv is not None else 0.0)
+
+    def self_energies(i):
+        hHF[i] = h_at(i) + hf_selfenergy(L[i, i], V, sigma)
+        if second_born:
+            for k in range(i + 1):
+                sL[i, k] = sigma2_realtime(L[i, k], -G[i, k].conj().T, V, sigma)
+                sG[i, k] = sigma2_realtime(G[i, k], -L[i, k].conj().T, V, sigma)
+
+    def weights(m):
+        w = np.full(m + 1, dt)
+        w[0] = w[-1] = 0.5 * dt
+        return w * (m > 0)
+
+    def rhs(i, j):
+        wi, wj = weights(i), weights(j)
+        A = sG[i, :i + 1] - sL[i, :i + 1]
+        D = L[:j + 1, j] - G[:j + 1, j]
+        KL = (np.einsum("s,sab,sbc->ac", wi, A, L[:i + 1, j])
+              + np.einsum("s,sab,sbc->ac", wj, sL[i, :j + 1], D))
+        KG = (np.einsum("s,sab,sbc->ac", wi, A, G[:i + 1, j])
+              + np.einsum("s,sab,sbc->ac", wj, sG[i, :j + 1], D))
+        return -1j * hHF[i] @ L[i, j] + KL, -1j * hHF[i] @ G[i, j] + KG, KL
+
+    def observe(i):
+        rho = L[i, i]
+        KL = rhs(i, i)[2]
+        e = sigma * np.trace(h_at(i) @ rho).real
+        e += 0.5 * sigma * np.trace(hf_selfenergy(rho, V, sigma) @ rho).real
+        e += 0.5 * sigma * (1j * np.trace(KL)).real
+        return e, sigma * np.trace(rho).real
+
+    def mirror(i):
+        for j in range(i):
+            L[j, i] = L[i, j].conj().T
+            G[j, i] = G[i, j].conj().T
+
+    self_energies(0)
+    obs = [observe(0)]
+    for N in range(n_steps):
+        r0 = [rhs(N, j) for j in range(N + 1)]
+        d0 = r0[N][0] + r0[N][0].conj().T
+        for j in range(N + 1):   # predictor
+            L[N + 1, j] = L[N, j] + dt * r0[j][0]
+            G[N + 1, j] = G[N, j] + dt * r0[j][1]
+        L[N + 1, N + 1] = L[N, N] + dt * d0
+        G[N + 1, N + 1] = L[N + 1, N + 1] - ident
+        mirror(N + 1)
+        self_energies(N + 1)
+        r1 = [rhs(N + 1, j) for j in range(N + 2)]
+        d1 = r1[N + 1][0] + r1[N + 1][0].conj().T
+        for j in range(N + 1):   # corrector
+            L[N + 1, j] = L[N, j] + 0.5 * dt * (r0[j][0] + r1[j][0])
+            G[N + 1, j] = G[N, j] + 0.5 * dt * (r0[j][1] + r1[j][1])
+        L[N + 1, N + 1] = L[N, N] + 0.5 * dt * (d0 + d1)
+        G[N + 1, N + 1] = L[N + 1, N + 1] - ident
+        mirror(N + 1)
+        self_energies(N + 1)
+        obs.append(observe(N + 1))
+    rho = np.array([L[i, i] for i in range(T)])
+    return dict(rho=rho, L=L, Gt=G, E=np.array([o[0] for o in obs]),
+                N=np.array([o[1] for o in obs]))
+
+
+def exact_dynamics(h: np.ndarray, V: np.ndarray, phi0: np.ndarray, times) -> np.ndarray:
+    """Pin only: the two-electron singlet evolved exactly on the grid, from the
+    doubly occupied orbital phi0 (spatial wave function Psi_ab = phi0_a phi0_b)
+    under H = h (x) 1 + 1 (x) h + diag(V_ab); returns the density matrix per
+    spin rho_ab(t) = sum_c Psi_ac(t) Psi_bc(t)^* for each time."""
+    import scipy.linalg as sla
+    n = h.shape[0]
+    ident = np.eye(n)
+    H2 = np.kron(h, ident) + np.kron(ident, h) + np.diag(np.asarray(V).ravel())
+    psi0 = np.outer(phi0, phi0).ravel().astype(complex)
+    out = []
+    for t in times:
+        psi = (sla.expm(-1j * H2 * float(t)) @ psi0).reshape(n, n)
+        out.append(psi @ psi.conj().T)
+    return np.array(out)
 
 
 # ---------------------------------------------------------------------------
