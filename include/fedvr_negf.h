@@ -448,6 +448,57 @@ int fedvr_conv_g0(fedvr_ctx *ctx, int n, double beta, int u, int p, const double
  * faults or hangs. Synchronises the context's stream. */
 int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds);
 
+/* Real-time two-time Kadanoff-Baym propagation (Sec. 2, Eqs. kbe, skkbe and
+ * skkbesigma; the self-energy is the time-local HF part of Eq. sigmahf plus,
+ * with second_born != 0, the second-Born part of Eq. sigma2ndb on the Keldysh
+ * components; second_born = 0 gives time-dependent HF). The paper states the
+ * equations and runs only their equilibrium (Matsubara) problem; this entry
+ * starts from an uncorrelated state rho0 at t = 0, so the collision integrals
+ * run over [0, t] only.
+ *
+ * Functions: L(t, t') = -i G^<(t, t') (L(t, t) = rho(t), the density matrix
+ * per spin) and Gt = -i G^> (Gt(t, t) = rho(t) - 1) on the grid t_k = k dt,
+ * k = 0 .. n_steps, advanced by Heun's predictor-corrector with trapezoid
+ * collision integrals (second order in dt), in complex FP64 on the device.
+ * Heun's step is explicit: a mode of energy e grows by
+ * sqrt(1 + (e dt)^4 / 4) per step, so dt must stay well below 1 / max|e| of
+ * h_HF (max|e| grows with the grid's highest kinetic energy, about 27 Ha at
+ * n_b = 74 on [-20, 20]); an unstable choice ends in Inf/NaN outputs, not an
+ * error code.
+ * The Hamiltonian is the context's h (after set_potential) plus
+ * diag(dv(t_k)) (a time-dependent potential at the nodes, e.g. x_a E(t_k)).
+ *
+ * rho0: host [n_b][n_b] complex (interleaved re, im; 16 bytes per entry), or
+ * NULL for the real HF density rho0 of the last solve_hf. dv: host
+ * [n_steps+1][n_b] or NULL. Outputs (host, any may be NULL): rho_out
+ * [n_steps+1][n_b][n_b] complex interleaved; E_out [n_steps+1], the total
+ * energy sigma Tr[h(t) rho] + sigma/2 Tr[Sigma^HF rho] + sigma/2 Re Tr[i K_L(t, t)]
+ * (one-body, HF and correlation parts; E_nn excluded; constant without dv);
+ * N_out [n_steps+1] = sigma Tr rho.
+ *
+ * Device memory: the two-time L and Gt are held whole, 2 (T n_b)^2 x 16 bytes
+ * with T = n_steps + 1 (about 1.2 GB at n_b = 15, T = 401), kept after the
+ * call for fedvr_kbe_get_block until the next call or fedvr_destroy.
+ * Errors: FEDVR_ERR_STATE before set_potential (or before solve_hf with
+ * rho0 = NULL); FEDVR_ERR_ARG for dt <= 0, n_steps outside [0, 32766],
+ * n_b > 80 or storage beyond the free device memory. Synchronises the stream. */
+int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
+                        const double *rho0, const double *dv, double *rho_out, double *E_out,
+                        double *N_out);
+
+/* Copy block (i, j) (time indices of the last fedvr_kbe_propagate) of
+ * which = 0: L = -i G^<, 1: Gt = -i G^> to host out [n_b][n_b] complex
+ * interleaved. Errors: FEDVR_ERR_STATE without a completed propagation,
+ * FEDVR_ERR_ARG for indices outside it. */
+int fedvr_kbe_get_block(const fedvr_ctx *ctx, int which, int i, int j, double *out);
+
+/* Timing of the last fedvr_kbe_propagate (CUDA events on the context's
+ * stream): out[0] total ms, out[1] ms in the collision-integral kernels,
+ * out[2] ms in the self-energy kernels, out[3] their algorithmic flops
+ * (8 per complex multiply-add of the collision integrals), out[4] the
+ * self-energy's, out[5] kernel launches. */
+int fedvr_kbe_stats(const fedvr_ctx *ctx, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -296,6 +296,46 @@ class Context:
         with code -5 (timeout) and leaves the context failed."""
         self._check(self._lib.fedvr_selftest_wait(self._h, 1 if release else 0, limit_seconds))
 
+    def kbe_propagate(self, dt, n_steps, second_born=True, rho0=None, dv=None, want_rho=True):
+        """Real-time two-time Kadanoff-Baym propagation (``fedvr_kbe_propagate``)
+        from rho0 (complex [n][n]; None: the HF density of the last solve_hf)
+        under h + diag(dv[k]) (dv: [n_steps+1][n] or None). Returns a dict with
+        rho [n_steps+1][n][n] complex (if want_rho), E and N [n_steps+1]."""
+        n = self.n_b
+        T = n_steps + 1
+        r0 = None
+        if rho0 is not None:
+            r0 = np.ascontiguousarray(np.asarray(rho0, dtype=np.complex128)).view(np.float64)
+            assert r0.shape == (n, 2 * n)
+        d = None
+        if dv is not None:
+            d = np.ascontiguousarray(dv, dtype=np.float64)
+            assert d.shape == (T, n)
+        rho = np.empty((T, n, n), dtype=np.complex128) if want_rho else None
+        E = np.empty(T)
+        N = np.empty(T)
+        self._check(self._lib.fedvr_kbe_propagate(
+            self._h, float(dt), int(n_steps), 1 if second_born else 0, _dptr(r0), _dptr(d),
+            _dptr(rho.view(np.float64)) if want_rho else None, _dptr(E), _dptr(N)))
+        return {"rho": rho, "E": E, "N": N}
+
+    def kbe_block(self, which, i, j):
+        """Block (i, j) of L = -i G^< (which 0 or "L") or Gt = -i G^> (1 or "G")
+        of the last propagation, complex [n][n]."""
+        w = {"L": 0, "G": 1}.get(which, which)
+        out = np.empty((self.n_b, self.n_b), dtype=np.complex128)
+        self._check(self._lib.fedvr_kbe_get_block(self._h, int(w), int(i), int(j),
+                                                  _dptr(out.view(np.float64))))
+        return out
+
+    def kbe_stats(self):
+        """Timing of the last propagation: total, collision and self-energy ms,
+        their algorithmic flops, and the kernel launches."""
+        out = np.zeros(6)
+        self._check(self._lib.fedvr_kbe_stats(self._h, _dptr(out)))
+        return {"ms": out[0], "collision_ms": out[1], "sigma_ms": out[2],
+                "collision_flops": out[3], "sigma_flops": out[4], "launches": int(out[5])}
+
 
 def solve_2b_batched(contexts, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
                      precision=SPLIT_TF32, check=True):

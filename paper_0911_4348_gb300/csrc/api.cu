@@ -655,12 +655,14 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_t2, &ctx->w_t3, &ctx->w_dHF, &ctx->w_part, &ctx->w_red, &ctx->w_tc,
                     &ctx->w_K32, &ctx->w_tab, &ctx->w_btab, &ctx->w_c1p,
                     &ctx->w_coef32, &ctx->w_h16, &ctx->w_xrow, &ctx->w_dens,
-                    &ctx->w_q4coef, &ctx->w_q4W, &ctx->w_q4w};
+                    &ctx->w_q4coef, &ctx->w_q4W, &ctx->w_q4w, &ctx->k_L, &ctx->k_G,
+                    &ctx->k_S, &ctx->k_T1, &ctx->k_R, &ctx->k_aux, &ctx->k_out};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
   for (int i = 0; i < 7; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (cudaEvent_t e : ctx->kbe_events) cudaEventDestroy(e);
   delete ctx;
 }
 

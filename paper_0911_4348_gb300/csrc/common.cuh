@@ -71,6 +71,12 @@ struct fedvr_ctx {
   int quad_order = 2;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
+  // last real-time propagation: time points and n (0: none), stage times and
+  // algorithmic flops (total ms, collision ms, self-energy ms, collision
+  // flops, self-energy flops, launches), events reused across calls
+  int kbe_T = 0, kbe_n = 0;
+  double kbe_stats[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> kbe_events;
 
   // named device buffers
   fedvr::DevBuf b_xi, b_om, b_edges, b_nodes, b_weights, b_elem, b_local, b_tt;
@@ -82,6 +88,8 @@ struct fedvr_ctx {
   fedvr::DevBuf w_tau, w_w, w_wm, w_wp, w_coef, w_K, w_phi, w_G0, w_G, w_S, w_I1, w_I2,
       w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16,
       w_xrow, w_dens, w_q4coef, w_q4W, w_q4w;
+  // real-time propagation: two-time L and Gt, self-energy row, scratch, outputs
+  fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out;
 };
 
 namespace fedvr {

@@ -1,0 +1,710 @@
+// Real-time two-time Kadanoff-Baym propagation (Sec. 2, Eqs. kbe, skkbe,
+// skkbesigma with the HF part of Eq. sigmahf and the second-Born part of Eq.
+// sigma2ndb), from an uncorrelated initial state, in complex FP64.
+//
+// Functions and layout. L = -i G^< and Gt = -i G^> (so L(t, t) = rho(t),
+// Gt(t, t) = rho(t) - 1, F(t', t) = F(t, t')^H) on the uniform grid
+// t_k = k dt, k = 0 .. T-1, stored as two full square matrices of T x T
+// blocks: block (s, j) of F is n x n at F + (s n) ld + j n with ld = T n
+// complex elements (interleaved double2). Both triangles are kept (the upper
+// one written as the mirror of each new time row), so every contraction reads
+// whole blocks along rows. Self-energies are needed only on the current time
+// row: S[w][k] (w = 0: s^< = -i Sigma^<, w = 1: s^> = -i Sigma^>) at
+// S + (w T + k) n n.
+//
+// One step N -> N+1 (Heun predictor-corrector, trapezoid collision integrals):
+//   R0 = rhs(N, j = 0..N); predictor row N+1; HF and self-energy row N+1;
+//   R1 = rhs(N+1, j = 0..N+1); corrector row N+1; HF and self-energy row N+1;
+//   observables at N+1 (K_L(t, t) from one more collision block).
+// with rhs(i, j) = -i h_HF(t_i) F(i, j) + K_F(i, j),
+//   K_L = sum_{s<=i} w^i_s [s^> - s^<](i, s) L(s, j) + sum_{s<=j} w^j_s s^<(i, s) [L - Gt](s, j),
+//   K_G = sum_{s<=i} w^i_s [s^> - s^<](i, s) Gt(s, j) + sum_{s<=j} w^j_s s^>(i, s) [L - Gt](s, j),
+// w^m_s the trapezoid weights on [0, t_m] (dt, halved at both ends; zero for m = 0).
+//
+// Every kernel here is bound by GB300's FP64 pipe (2 DFMA per clock per SM):
+// operands come from shared memory or L1, and the work per launch is counted
+// in complex multiply-adds (4 DFMA each).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fedvr {
+namespace {
+
+constexpr int kKbeMaxN = 80;  // exchange operands (2 n^2 complex) fit one CTA's shared memory
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cmla(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ double2 conjz(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 addz(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 subz(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ double2 scalez(double s, double2 a) {
+  return make_double2(s * a.x, s * a.y);
+}
+__host__ __device__ __forceinline__ long blk(int s, int j, int n, long ld) {
+  return (long)s * n * ld + (long)j * n;
+}
+// trapezoid weight of point s on [0, t_m]
+__device__ __forceinline__ double trap_w(int s, int m, double dt) {
+  if (m == 0) return 0.0;
+  return (s == 0 || s == m) ? 0.5 * dt : dt;
+}
+
+// Block (0, 0): L = rho0 (complex, already in place), Gt = L - 1.
+__global__ void g_from_l_kernel(int n, long ld, long off, const double2 *L, double2 *G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int b = idx / n, c = idx % n;
+  double2 v = L[off + b * ld + c];
+  if (b == c) v.x -= 1.0;
+  G[off + b * ld + c] = v;
+}
+
+// Real n x n density -> complex block of L (imaginary part zero).
+__global__ void rho_real_kernel(int n, long ld, const double *rho, double2 *L) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int b = idx / n, c = idx % n;
+  L[b * ld + c] = make_double2(rho[idx], 0.0);
+}
+
+// h_HF = h + diag(dv) + Sigma^HF[rho], Sigma^HF = spin diag(V diag rho) - V o rho
+// (Eq. sigmahf with rho = L(t, t)).
+__global__ void hf_kernel(int n, double spin, const double *h, const double *dv, const double *V,
+                          const double2 *L, long off, long ld, double2 *out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int a = idx / n, b = idx % n;
+  const double2 r = L[off + a * ld + b];
+  const double vab = V[idx];
+  double2 s = make_double2(-vab * r.x, -vab * r.y);
+  if (a == b) {
+    double2 H = make_double2(0.0, 0.0);
+    for (int c = 0; c < n; ++c) {
+      const double2 rc = L[off + (long)c * ld + c];
+      H.x = fma(V[a * n + c], rc.x, H.x);
+      H.y = fma(V[a * n + c], rc.y, H.y);
+    }
+    s.x = spin * H.x + s.x;
+    s.y = spin * H.y + s.y;
+  }
+  const double hd = h[idx] + ((a == b && dv) ? dv[a] : 0.0);
+  out[idx] = make_double2(hd + s.x, s.y);
+}
+
+// Second-Born self-energy of row i, entry e = 2k + w (w = 0: s^< from
+// g = L(i, k), H = Gt(i, k); w = 1: s^> from g = Gt(i, k), H = L(i, k)), with
+// the reversed line gb = -H^H:
+//   S = spin g o (V Q V) - X,  Q_kl = g_kl gb_lk = -g_kl conj(H_kl),
+//   X_ab = sum_kl V_ak V_bl g_al gb_lk g_kb.
+// First V Q into T1 [e][n][n].
+__global__ void vq_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                          const double *V, double2 *T1) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const int a = idx / n, l = idx % n;
+  const long off = blk(i, kt, n, ld);
+  const double2 *g = (w ? G : L) + off, *H = (w ? L : G) + off;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double2 q = cmul(g[k * ld + l], conjz(H[k * ld + l]));  // -Q_kl
+    const double v = V[a * n + k];
+    acc.x = fma(-v, q.x, acc.x);
+    acc.y = fma(-v, q.y, acc.y);
+  }
+  T1[(long)e * n * n + idx] = acc;
+}
+
+// Direct term S_e = spin g o (T1 V), written to the row's S[w][k].
+__global__ void direct_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                              const double *V, const double2 *T1, double spin, int Tcap,
+                              double2 *S) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const int a = idx / n, b = idx % n;
+  const double2 *t1 = T1 + (long)e * n * n + (long)a * n;
+  double2 W = make_double2(0.0, 0.0);
+  for (int l = 0; l < n; ++l) {
+    const double v = V[l * n + b];
+    W.x = fma(t1[l].x, v, W.x);
+    W.y = fma(t1[l].y, v, W.y);
+  }
+  const double2 g = (w ? G : L)[blk(i, kt, n, ld) + a * ld + b];
+  S[((long)w * Tcap + kt) * n * n + idx] = cmul(scalez(spin, g), W);
+}
+
+// Exchange term, one CTA per (column b, entry e): with g and
+// Hb_lk = V_bl gb_lk in shared memory, P_ak = sum_l g_al Hb_lk and
+// X_ab = sum_k V_ak P_ak g_kb (a warp per row a, lanes over k); S_ab -= X_ab.
+__global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, const double2 *L,
+                                                       const double2 *G, const double *V,
+                                                       int Tcap, double2 *S) {
+  extern __shared__ double2 xs[];
+  double2 *gs = xs, *hb = xs + n * n;
+  const int b = blockIdx.x, e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const long off = blk(i, kt, n, ld);
+  const double2 *g = (w ? G : L) + off, *H = (w ? L : G) + off;
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+    const int r = q / n, c = q % n;
+    gs[q] = g[r * ld + c];
+    // H_rc enters as gb_cr = -conj(H_rc), so Hb[c][r] = -V_bc conj(H_rc)
+    const double2 h = H[r * ld + c];
+    const double v = V[b * n + c];
+    hb[c * n + r] = make_double2(-v * h.x, v * h.y);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double2 *Sout = S + ((long)w * Tcap + kt) * n * n;
+  for (int a = warp; a < n; a += 8) {
+    double2 part = make_double2(0.0, 0.0);
+    for (int k = lane; k < n; k += 32) {
+      double2 P = make_double2(0.0, 0.0);
+      for (int l = 0; l < n; ++l) cmla(P, gs[a * n + l], hb[l * n + k]);
+      cmla(part, scalez(V[a * n + k], P), gs[k * n + b]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+    }
+    if (lane == 0) {
+      double2 v = Sout[a * n + b];
+      Sout[a * n + b] = subz(v, part);
+    }
+  }
+}
+
+struct CollArgs {
+  int n, i, j0, Tcap;
+  long ld;
+  double dt;
+  const double2 *L, *G, *S, *hHF;
+  double2 *RL, *RG;
+  int mode;  // 0: rhs of L and Gt for columns j0 + blockIdx.x; 1: K_L(i, j0) only
+  int corr;  // 0: no collision integrals (time-dependent HF)
+};
+
+// Collision integrals (and with mode 0 the -i h_HF F term) for one time row i.
+// CTA: column block j, a TT x TT output tile (TT = 16 R); thread (ty, tx) owns
+// rows a0 + ty + 16 r and columns c0 + tx + 16 q. Each term stages a 16-wide
+// slice of the contraction index: X tiles [TT][16] (left factors), Y tiles
+// [16][TT] (right factors).
+template <int R>
+__global__ void __launch_bounds__(256) collision_kernel(CollArgs p) {
+  constexpr int TT = 16 * R;
+  extern __shared__ double2 cs[];
+  double2 *X0 = cs, *X1 = cs + TT * 16, *Y0 = cs + 2 * TT * 16, *Y1 = cs + 3 * TT * 16;
+  const int n = p.n, i = p.i, j = p.j0 + blockIdx.x;
+  const long ld = p.ld, nn = (long)n * n;
+  const int a0 = blockIdx.y * TT, c0 = blockIdx.z * TT;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const double2 *SL = p.S, *SG = p.S + (long)p.Tcap * nn;
+  double2 accL[R][R], accG[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int q = 0; q < R; ++q) accL[r][q] = accG[r][q] = make_double2(0.0, 0.0);
+
+  // term kinds: 0 = -i h_HF(i) x [L(i,j), G(i,j)]; 1 = w (s^> - s^<)(i,s) x [L(s,j), G(s,j)];
+  // 2 = [w s^<(i,s), w s^>(i,s)] x (L - G)(s,j)
+  const int n0 = p.mode == 0 ? 1 : 0;
+  const int n1 = (p.corr && i > 0) ? i + 1 : 0;
+  const int n2 = (p.corr && j > 0) ? j + 1 : 0;
+  const int nterm = n0 + n1 + n2;
+  for (int t = 0; t < nterm; ++t) {
+    const int kind = t < n0 ? 0 : (t < n0 + n1 ? 1 : 2);
+    const int s = kind == 0 ? i : (kind == 1 ? t - n0 : t - n0 - n1);
+    const double w = kind == 1 ? trap_w(s, i, p.dt) : (kind == 2 ? trap_w(s, j, p.dt) : 0.0);
+    const long fb = blk(s, j, n, ld);
+    for (int bc = 0; bc < n; bc += 16) {
+      for (int q = tid; q < TT * 16; q += 256) {
+        const int r = q >> 4, bb = q & 15, a = a0 + r, b = bc + bb;
+        double2 x0 = make_double2(0.0, 0.0), x1 = x0;
+        if (a < n && b < n) {
+          if (kind == 0) {
+            const double2 hv = p.hHF[a * n + b];
+            x0 = make_double2(hv.y, -hv.x);  // -i h
+          } else {
+            const double2 sl = SL[(long)s * nn + a * n + b], sg = SG[(long)s * nn + a * n + b];
+            if (kind == 1) {
+              x0 = scalez(w, subz(sg, sl));
+            } else {
+              x0 = scalez(w, sl);
+              x1 = scalez(w, sg);
+            }
+          }
+        }
+        X0[q] = x0;
+        X1[q] = x1;
+      }
+      for (int q = tid; q < 16 * TT; q += 256) {
+        const int bb = q / TT, cc = q % TT, b = bc + bb, c = c0 + cc;
+        double2 y0 = make_double2(0.0, 0.0), y1 = y0;
+        if (b < n && c < n) {
+          const double2 l = p.L[fb + b * ld + c], g = p.G[fb + b * ld + c];
+          if (kind == 2) {
+            y0 = subz(l, g);
+          } else {
+            y0 = l;
+            y1 = g;
+          }
+        }
+        Y0[q] = y0;
+        Y1[q] = y1;
+      }
+      __syncthreads();
+      if (kind == 2) {
+#pragma unroll 4
+        for (int bb = 0; bb < 16; ++bb) {
+          double2 xl[R], xg[R], yd[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            xl[r] = X0[(ty + 16 * r) * 16 + bb];
+            xg[r] = X1[(ty + 16 * r) * 16 + bb];
+          }
+#pragma unroll
+          for (int q = 0; q < R; ++q) yd[q] = Y0[bb * TT + tx + 16 * q];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+              cmla(accL[r][q], xl[r], yd[q]);
+              cmla(accG[r][q], xg[r], yd[q]);
+            }
+        }
+      } else {
+#pragma unroll 4
+        for (int bb = 0; bb < 16; ++bb) {
+          double2 xa[R], yl[R], yg[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) xa[r] = X0[(ty + 16 * r) * 16 + bb];
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            yl[q] = Y0[bb * TT + tx + 16 * q];
+            yg[q] = Y1[bb * TT + tx + 16 * q];
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+              cmla(accL[r][q], xa[r], yl[q]);
+              cmla(accG[r][q], xa[r], yg[q]);
+            }
+        }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int a = a0 + ty + 16 * r, c = c0 + tx + 16 * q;
+      if (a < n && c < n) {
+        if (p.mode == 0) {
+          p.RL[(long)j * nn + a * n + c] = accL[r][q];
+          p.RG[(long)j * nn + a * n + c] = accG[r][q];
+        } else {
+          p.RL[a * n + c] = accL[r][q];
+        }
+      }
+    }
+}
+
+// Predictor (R1 == nullptr) or corrector of time row N+1 and its mirror column.
+__global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, const double2 *R0L,
+                               const double2 *R0G, const double2 *R1L, const double2 *R1G,
+                               double dt) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int j = blockIdx.y, b = idx / n, c = idx % n;
+  const long nn = (long)n * n;
+  if (j <= N) {
+    double2 dl = R0L[(long)j * nn + idx], dg = R0G[(long)j * nn + idx];
+    double f = dt;
+    if (R1L) {
+      dl = addz(dl, R1L[(long)j * nn + idx]);
+      dg = addz(dg, R1G[(long)j * nn + idx]);
+      f = 0.5 * dt;
+    }
+    const double2 vl = addz(L[blk(N, j, n, ld) + b * ld + c], scalez(f, dl));
+    const double2 vg = addz(G[blk(N, j, n, ld) + b * ld + c], scalez(f, dg));
+    L[blk(N + 1, j, n, ld) + b * ld + c] = vl;
+    G[blk(N + 1, j, n, ld) + b * ld + c] = vg;
+    L[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vl);
+    G[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vg);
+  } else {
+    // equal times: d rho/dt = X + X^H with X = rhs_L(t, t)
+    double2 d = addz(R0L[(long)N * nn + b * n + c], conjz(R0L[(long)N * nn + c * n + b]));
+    double f = dt;
+    if (R1L) {
+      const double2 d1 =
+          addz(R1L[(long)(N + 1) * nn + b * n + c], conjz(R1L[(long)(N + 1) * nn + c * n + b]));
+      d = addz(d, d1);
+      f = 0.5 * dt;
+    }
+    const double2 v = addz(L[blk(N, N, n, ld) + b * ld + c], scalez(f, d));
+    L[blk(N + 1, N + 1, n, ld) + b * ld + c] = v;
+    G[blk(N + 1, N + 1, n, ld) + b * ld + c] = make_double2(v.x - (b == c ? 1.0 : 0.0), v.y);
+  }
+}
+
+// E(t) = spin Tr[h(t) rho] + spin/2 Tr[Sigma^HF rho] + spin/2 Re Tr[i K_L(t, t)]
+// and N(t) = spin Tr rho; one CTA, fixed-order reduction.
+__global__ void observe_kernel(int n, double spin, const double *h, const double *dv,
+                               const double *V, const double2 *L, long off, long ld,
+                               const double2 *K, double *E_out, double *N_out) {
+  __shared__ double red[4][256];
+  const int tid = threadIdx.x;
+  double e1 = 0.0, e2 = 0.0, ek = 0.0, nn_ = 0.0;
+  for (int idx = tid; idx < n * n; idx += 256) {
+    const int a = idx / n, b = idx % n;
+    const double2 rab = L[off + a * ld + b], rba = L[off + b * ld + a];
+    e1 += h[idx] * rba.x;                         // Re h_ab rho_ba (h real)
+    e2 -= V[idx] * cmul(rab, rba).x;              // exchange: -V_ab rho_ab rho_ba
+    if (a == b) {
+      const double2 raa = rab;
+      double2 H = make_double2(0.0, 0.0);
+      for (int c = 0; c < n; ++c) {
+        const double2 rc = L[off + (long)c * ld + c];
+        H.x = fma(V[a * n + c], rc.x, H.x);
+        H.y = fma(V[a * n + c], rc.y, H.y);
+      }
+      e2 += spin * cmul(H, raa).x;                // Hartree
+      if (dv) e1 += dv[a] * raa.x;
+      ek -= K[idx].y;                             // Re(i K_aa)
+      nn_ += raa.x;
+    }
+  }
+  red[0][tid] = e1;
+  red[1][tid] = e2;
+  red[2][tid] = ek;
+  red[3][tid] = nn_;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st)
+      for (int q = 0; q < 4; ++q) red[q][tid] += red[q][tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *E_out = spin * red[0][0] + 0.5 * spin * red[1][0] + 0.5 * spin * red[2][0];
+    *N_out = spin * red[3][0];
+  }
+}
+
+__global__ void gather_diag_kernel(int n, long ld, const double2 *L, double2 *out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int t = blockIdx.y, b = idx / n, c = idx % n;
+  out[(long)t * n * n + idx] = L[blk(t, t, n, ld) + b * ld + c];
+}
+
+int coll_R(int n) { return n <= 16 ? 1 : (n <= 32 ? 2 : 3); }
+size_t coll_smem(int R) { return (size_t)4 * 16 * R * 16 * sizeof(double2); }
+
+cudaError_t launch_collision(const CollArgs &a, int ncols, cudaStream_t s) {
+  const int R = coll_R(a.n), TT = 16 * R;
+  const unsigned tiles = (unsigned)((a.n + TT - 1) / TT);
+  dim3 grid((unsigned)ncols, tiles, tiles);
+  const size_t sm = coll_smem(R);
+  cudaError_t e;
+  switch (R) {
+    case 1:
+      collision_kernel<1><<<grid, 256, sm, s>>>(a);
+      break;
+    case 2:
+      collision_kernel<2><<<grid, 256, sm, s>>>(a);
+      break;
+    default:
+      e = cudaFuncSetAttribute(collision_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+      if (e != cudaSuccess) return e;
+      collision_kernel<3><<<grid, 256, sm, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+#define KBE_CK(ctx, call)                                                   \
+  do {                                                                      \
+    cudaError_t e__ = (call);                                               \
+    if (e__ != cudaSuccess) return cuda_fail((ctx), e__, #call, __FILE__, __LINE__); \
+  } while (0)
+#define KBE_ENSURE(ctx, buf, bytes)                                         \
+  do {                                                                      \
+    if (!ensure((ctx), (ctx)->buf, (bytes), #buf)) return FEDVR_ERR_CUDA;   \
+  } while (0)
+
+// Algorithmic complex multiply-adds of one rhs call on row i (columns j0 ..
+// j0 + ncols - 1; mode 1: K_L only).
+double coll_cmacs(int n, int i, int j0, int ncols, int mode, bool corr) {
+  const double n3 = (double)n * n * n;
+  double c = 0;
+  for (int j = j0; j < j0 + ncols; ++j) {
+    const double f = mode == 0 ? 2.0 : 1.0;
+    if (mode == 0) c += f * n3;
+    if (corr && i > 0) c += f * (i + 1) * n3;
+    if (corr && j > 0) c += f * (j + 1) * n3;
+  }
+  return c;
+}
+
+struct KbeRun {
+  fedvr_ctx *ctx;
+  int n, Tcap;
+  long ld;
+  double dt, spin;
+  bool corr;
+  double2 *L, *G, *S, *T1, *R0L, *R0G, *R1L, *R1G, *hHF, *K;
+  const double *h, *V, *dv;
+  double *E, *Nn;
+  cudaStream_t s;
+  std::vector<cudaEvent_t> *ev;
+  size_t ev_used = 0;
+  double cmac_coll = 0, cmac_sigma = 0;
+  long launches = 0;
+  std::vector<std::pair<size_t, int>> marks;  // (event index, stage: 0 collision, 1 sigma)
+
+  cudaError_t mark(int stage_open) {
+    if (ev_used >= ev->size()) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev->push_back(e);
+    }
+    if (stage_open >= 0) marks.push_back({ev_used, stage_open});
+    return cudaEventRecord((*ev)[ev_used++], s);
+  }
+  const double *dv_at(int t) const { return dv ? dv + (long)t * n : nullptr; }
+
+  int hf(int t) {
+    const int nn = n * n;
+    hf_kernel<<<(nn + 255) / 256, 256, 0, s>>>(n, spin, h, dv_at(t), V, L, blk(t, t, n, ld), ld,
+                                               hHF);
+    KBE_CK(ctx, cudaGetLastError());
+    ++launches;
+    return FEDVR_OK;
+  }
+  int sigma(int i) {
+    if (!corr) return FEDVR_OK;
+    const int nn = n * n, ne = 2 * (i + 1);
+    KBE_CK(ctx, mark(1));
+    vq_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1);
+    KBE_CK(ctx, cudaGetLastError());
+    direct_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1, spin, Tcap,
+                                                             S);
+    KBE_CK(ctx, cudaGetLastError());
+    const size_t sm = (size_t)2 * nn * sizeof(double2);
+    exchange_kernel<<<dim3(n, ne), 256, sm, s>>>(n, i, ld, L, G, V, Tcap, S);
+    KBE_CK(ctx, cudaGetLastError());
+    KBE_CK(ctx, mark(-1));
+    const double n3 = (double)n * n * n;
+    cmac_sigma += ne * (n3 * n + 2.0 * n3);  // exchange n^4 + n^3, V Q V two half-real n^3
+    launches += 3;
+    return FEDVR_OK;
+  }
+  int rhs(int i, double2 *RL, double2 *RG) {
+    CollArgs a{n, i, 0, Tcap, ld, dt, L, G, S, hHF, RL, RG, 0, corr ? 1 : 0};
+    KBE_CK(ctx, mark(0));
+    KBE_CK(ctx, launch_collision(a, i + 1, s));
+    KBE_CK(ctx, mark(-1));
+    cmac_coll += coll_cmacs(n, i, 0, i + 1, 0, corr);
+    ++launches;
+    return FEDVR_OK;
+  }
+  int observe(int t) {
+    CollArgs a{n, t, t, Tcap, ld, dt, L, G, S, hHF, K, nullptr, 1, corr ? 1 : 0};
+    KBE_CK(ctx, mark(0));
+    KBE_CK(ctx, launch_collision(a, 1, s));
+    KBE_CK(ctx, mark(-1));
+    cmac_coll += coll_cmacs(n, t, t, 1, 1, corr);
+    observe_kernel<<<1, 256, 0, s>>>(n, spin, h, dv_at(t), V, L, blk(t, t, n, ld), ld, K, E + t,
+                                     Nn + t);
+    KBE_CK(ctx, cudaGetLastError());
+    launches += 2;
+    return FEDVR_OK;
+  }
+  int advance(int N, bool corrector) {
+    const int nn = n * n;
+    advance_kernel<<<dim3((nn + 255) / 256, N + 2), 256, 0, s>>>(
+        n, N, ld, L, G, R0L, R0G, corrector ? R1L : nullptr, corrector ? R1G : nullptr, dt);
+    KBE_CK(ctx, cudaGetLastError());
+    ++launches;
+    return FEDVR_OK;
+  }
+};
+
+}  // namespace
+}  // namespace fedvr
+
+using namespace fedvr;
+
+int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
+                        const double *rho0, const double *dv, double *rho_out, double *E_out,
+                        double *N_out) {
+  if (!ctx) return FEDVR_ERR_ARG;
+  if (ctx->failed) return FEDVR_ERR_STATE;
+  if (ctx->stage < 2) return fail(ctx, FEDVR_ERR_STATE, "fedvr_kbe_propagate before set_potential");
+  if (!rho0 && ctx->stage < 3)
+    return fail(ctx, FEDVR_ERR_STATE, "no initial density: pass rho0 or call solve_hf first");
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(ctx, FEDVR_ERR_ARG, "dt must be finite and > 0");
+  // 2 T self-energy entries index one grid dimension (at most 65535)
+  if (n_steps < 0 || n_steps > 32766) return fail(ctx, FEDVR_ERR_ARG, "n_steps must be in [0, 32766]");
+  const int n = ctx->n;
+  if (n > kKbeMaxN)
+    return fail(ctx, FEDVR_ERR_ARG, "fedvr_kbe_propagate supports n_b <= %d (got %d)", kKbeMaxN, n);
+  const int T = n_steps + 1;
+  const long ld = (long)T * n;
+  const size_t nn = (size_t)n * n, cz = sizeof(double2);
+  const size_t two = (size_t)ld * (size_t)ld * cz;
+  {
+    size_t fre = 0, tot = 0;
+    KBE_CK(ctx, cudaMemGetInfo(&fre, &tot));
+    const size_t held = ctx->k_L.bytes + ctx->k_G.bytes;
+    if (2 * two + (size_t)(16 * T + 8) * nn * cz > fre + held)
+      return fail(ctx, FEDVR_ERR_ARG,
+                  "two-time storage of %.2f GB (T = %d, n_b = %d) exceeds free device memory",
+                  2.0 * two / 1e9, T, n);
+  }
+  cudaStream_t s = ctx->stream;
+  ctx->kbe_T = 0;
+  KBE_ENSURE(ctx, k_L, two);
+  KBE_ENSURE(ctx, k_G, two);
+  KBE_ENSURE(ctx, k_S, 2 * (size_t)T * nn * cz);
+  KBE_ENSURE(ctx, k_T1, 2 * (size_t)T * nn * cz);
+  KBE_ENSURE(ctx, k_R, 4 * (size_t)T * nn * cz);
+  KBE_ENSURE(ctx, k_aux, (2 * nn + 2 * (size_t)T) * cz);
+  KBE_ENSURE(ctx, k_out, (size_t)T * nn * cz + (size_t)T * n * sizeof(double));
+  double2 *L = P<double2>(ctx->k_L), *G = P<double2>(ctx->k_G);
+  double2 *R = P<double2>(ctx->k_R);
+  double2 *aux = P<double2>(ctx->k_aux);
+  double *obs = reinterpret_cast<double *>(aux + 2 * nn);
+  double2 *rho_all = P<double2>(ctx->k_out);
+  double *dv_d = reinterpret_cast<double *>(rho_all + (size_t)T * nn);
+  KBE_CK(ctx, cudaMemsetAsync(L, 0, two, s));
+  KBE_CK(ctx, cudaMemsetAsync(G, 0, two, s));
+  KBE_CK(ctx, cudaMemsetAsync(ctx->k_S.ptr, 0, 2 * (size_t)T * nn * cz, s));
+  if (dv)
+    KBE_CK(ctx, cudaMemcpyAsync(dv_d, dv, (size_t)T * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (rho0) {
+    KBE_CK(ctx, cudaMemcpy2DAsync(L, (size_t)ld * cz, rho0, (size_t)n * cz, (size_t)n * cz, n,
+                                  cudaMemcpyHostToDevice, s));
+  } else {
+    rho_real_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, ld, CP<double>(ctx->b_rho_new), L);
+    KBE_CK(ctx, cudaGetLastError());
+  }
+  g_from_l_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, ld, 0, L, G);
+  KBE_CK(ctx, cudaGetLastError());
+
+  KbeRun run;
+  run.ctx = ctx;
+  run.n = n;
+  run.Tcap = T;
+  run.ld = ld;
+  run.dt = dt;
+  run.spin = ctx->spin;
+  run.corr = second_born != 0;
+  run.L = L;
+  run.G = G;
+  run.S = P<double2>(ctx->k_S);
+  run.T1 = P<double2>(ctx->k_T1);
+  run.R0L = R;
+  run.R0G = R + (size_t)T * nn;
+  run.R1L = R + 2 * (size_t)T * nn;
+  run.R1G = R + 3 * (size_t)T * nn;
+  run.hHF = aux;
+  run.K = aux + nn;
+  run.h = CP<double>(ctx->b_h);
+  run.V = CP<double>(ctx->b_V);
+  run.dv = dv ? dv_d : nullptr;
+  run.E = obs;
+  run.Nn = obs + T;
+  run.s = s;
+  run.ev = &ctx->kbe_events;
+  {
+    const size_t sm = 2 * nn * cz;
+    KBE_CK(ctx, cudaFuncSetAttribute(exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+  }
+  KBE_CK(ctx, run.mark(-1));
+  if (int r = run.hf(0)) return r;
+  if (int r = run.sigma(0)) return r;
+  if (int r = run.observe(0)) return r;
+  for (int N = 0; N < n_steps; ++N) {
+    if (int r = run.rhs(N, run.R0L, run.R0G)) return r;
+    if (int r = run.advance(N, false)) return r;
+    if (int r = run.hf(N + 1)) return r;
+    if (int r = run.sigma(N + 1)) return r;
+    if (int r = run.rhs(N + 1, run.R1L, run.R1G)) return r;
+    if (int r = run.advance(N, true)) return r;
+    if (int r = run.hf(N + 1)) return r;
+    if (int r = run.sigma(N + 1)) return r;
+    if (int r = run.observe(N + 1)) return r;
+  }
+  KBE_CK(ctx, run.mark(-1));
+  if (rho_out) {
+    gather_diag_kernel<<<dim3((unsigned)((nn + 255) / 256), T), 256, 0, s>>>(n, ld, L, rho_all);
+    KBE_CK(ctx, cudaGetLastError());
+    KBE_CK(ctx, cudaMemcpyAsync(rho_out, rho_all, (size_t)T * nn * cz, cudaMemcpyDeviceToHost, s));
+  }
+  if (E_out) KBE_CK(ctx, cudaMemcpyAsync(E_out, obs, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (N_out)
+    KBE_CK(ctx, cudaMemcpyAsync(N_out, obs + T, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+  KBE_CK(ctx, cudaStreamSynchronize(s));
+  // stage times from the recorded events
+  double ms[2] = {0, 0};
+  for (auto &m : run.marks) {
+    float f = 0.f;
+    KBE_CK(ctx, cudaEventElapsedTime(&f, (*run.ev)[m.first], (*run.ev)[m.first + 1]));
+    ms[m.second] += f;
+  }
+  float tot = 0.f;
+  KBE_CK(ctx, cudaEventElapsedTime(&tot, (*run.ev)[0], (*run.ev)[run.ev_used - 1]));
+  ctx->kbe_stats[0] = tot;
+  ctx->kbe_stats[1] = ms[0];
+  ctx->kbe_stats[2] = ms[1];
+  ctx->kbe_stats[3] = 8.0 * run.cmac_coll;
+  ctx->kbe_stats[4] = 8.0 * run.cmac_sigma;
+  ctx->kbe_stats[5] = (double)run.launches;
+  ctx->kbe_T = T;
+  ctx->kbe_n = n;
+  return FEDVR_OK;
+}
+
+int fedvr_kbe_get_block(const fedvr_ctx *cctx, int which, int i, int j, double *out) {
+  fedvr_ctx *ctx = const_cast<fedvr_ctx *>(cctx);
+  if (!ctx) return FEDVR_ERR_ARG;
+  if (ctx->failed) return FEDVR_ERR_STATE;
+  if (ctx->kbe_T == 0) return fail(ctx, FEDVR_ERR_STATE, "no completed fedvr_kbe_propagate");
+  if (which != 0 && which != 1) return fail(ctx, FEDVR_ERR_ARG, "which must be 0 (L) or 1 (Gt)");
+  const int T = ctx->kbe_T, n = ctx->kbe_n;
+  if (i < 0 || j < 0 || i >= T || j >= T || !out)
+    return fail(ctx, FEDVR_ERR_ARG, "block (%d, %d) outside the %d time points", i, j, T);
+  const long ld = (long)T * n;
+  const double2 *F = CP<double2>(which ? ctx->k_G : ctx->k_L);
+  KBE_CK(ctx, cudaMemcpy2DAsync(out, (size_t)n * sizeof(double2), F + blk(i, j, n, ld),
+                                (size_t)ld * sizeof(double2), (size_t)n * sizeof(double2), n,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  KBE_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return FEDVR_OK;
+}
+
+int fedvr_kbe_stats(const fedvr_ctx *cctx, double *out) {
+  if (!cctx || !out) return FEDVR_ERR_ARG;
+  if (cctx->kbe_T == 0)
+    return fail(const_cast<fedvr_ctx *>(cctx), FEDVR_ERR_STATE, "no completed fedvr_kbe_propagate");
+  for (int q = 0; q < 6; ++q) out[q] = cctx->kbe_stats[q];
+  return FEDVR_OK;
+}

@@ -1,0 +1,140 @@
+"""Real-time Kadanoff-Baym propagation on the GPU (Sec. 2, Eqs. kbe, skkbe,
+skkbesigma) against the oracle's ``kbe_propagate``: density matrices, energy,
+particle number and two-time blocks on the same seeded inputs, for each
+collision-kernel tile shape (n_b <= 16, <= 32, <= 48 and two 48-wide tiles)."""
+import numpy as np
+import pytest
+
+from oracle import fedvr_oracle as O
+from paper_0911_4348_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-11  # complex FP64 on both sides; differences are summation order only
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _setup(n_elem, order, half_width, Z=2.0):
+    from paper_0911_4348_gb300 import Context
+    ctx = Context()
+    ctx.build_fedvr(n_elem, order + 1, -half_width, half_width, 0)
+    ctx.set_potential([Z], [0.0], 1.0, 1.0, 2)
+    b = O.fedvr_basis(n_elem, order, -half_width, half_width, 0)
+    T, v = O.kinetic(b), O.potential(b["nodes"], [Z], [0.0], 1.0)
+    V = O.interaction(b["nodes"], 1.0)
+    h = T + np.diag(v)
+    ops = ctx.get_operators()
+    assert np.array_equal(ops["h"], h) and np.array_equal(ops["V"], V)
+    return ctx, h, V, b["nodes"]
+
+
+def _kicked_rho(h, x, kick=0.3):
+    # a doubly occupied orbital displaced by a static field, released at t = 0
+    e, C = np.linalg.eigh(h + kick * np.diag(x))
+    return np.outer(C[:, 0], C[:, 0]).astype(np.complex128)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _compare(ctx, ref, got, pairs):
+    assert _rel(got["rho"], ref["rho"]) < TOL
+    assert np.max(np.abs(got["E"] - ref["E"])) < TOL * np.max(np.abs(ref["E"]))
+    assert np.max(np.abs(got["N"] - ref["N"])) < 1e-12
+    for (i, j) in pairs:
+        assert _rel(ctx.kbe_block("L", i, j), ref["L"][i, j]) < TOL, (i, j)
+        assert _rel(ctx.kbe_block("G", i, j), ref["Gt"][i, j]) < TOL, (i, j)
+
+
+@pytest.mark.parametrize("n_elem,order,half_width,steps", [
+    (4, 4, 10.0, 24),    # n_b = 15: 16-wide tiles
+    (10, 3, 12.0, 12),   # n_b = 29: 32-wide tiles
+    (10, 4, 15.0, 8),    # n_b = 39: 48-wide tiles
+    (15, 5, 20.0, 4),    # n_b = 74: two 48-wide tiles per side
+])
+def test_second_born_matches_oracle(n_elem, order, half_width, steps):
+    _need_gpu()
+    ctx, h, V, x = _setup(n_elem, order, half_width)
+    rho0 = _kicked_rho(h, x)
+    dt = 0.05
+    ref = O.kbe_propagate(h, V, 2.0, rho0, dt, steps)
+    got = ctx.kbe_propagate(dt, steps, True, rho0=rho0)
+    T = steps + 1
+    _compare(ctx, ref, got, [(T - 1, j) for j in range(T)] + [(j, T - 1) for j in range(T)]
+             + [(T // 2, 1), (1, T // 2)])
+    st = ctx.kbe_stats()
+    assert st["collision_flops"] > 0 and st["ms"] > 0 and st["launches"] > 0
+    ctx.close()
+
+
+def test_field_driven_tdhf_and_second_born_match_oracle():
+    # HF ground state driven by a dipole field dv_a(t) = x_a E sin(w t)
+    _need_gpu()
+    ctx, h, V, x = _setup(4, 4, 10.0)
+    s = W.he_small()
+    ctx.solve_hf(s.beta, tol=1e-13)
+    rho_hf = ctx.get_hf()["rho0"].astype(np.complex128)
+    dt, steps = 0.04, 30
+    t = np.arange(steps + 1) * dt
+    dv = np.outer(0.2 * np.sin(1.3 * t), x)
+    for sb in (False, True):
+        ref = O.kbe_propagate(h, V, 2.0, rho_hf, dt, steps, dv=dv, second_born=sb)
+        got = ctx.kbe_propagate(dt, steps, sb, rho0=None, dv=dv)
+        _compare(ctx, ref, got, [(steps, 0), (steps, steps), (steps // 2, steps)])
+    ctx.close()
+
+
+def test_tdhf_keeps_the_hf_ground_state_stationary():
+    # the converged HF density is a fixed point of time-dependent HF: rho and
+    # E stay at their t = 0 values, and E(0) is the HF energy
+    _need_gpu()
+    ctx, h, V, x = _setup(4, 4, 10.0)
+    s = W.he_small()
+    E_hf, _ = ctx.solve_hf(s.beta, tol=1e-13)
+    got = ctx.kbe_propagate(0.1, 40, False)
+    assert np.max(np.abs(got["rho"] - got["rho"][0])) < 1e-9
+    assert abs(got["E"][0] - E_hf) < 1e-10
+    assert np.max(np.abs(got["E"] - got["E"][0])) < 1e-9
+    ctx.close()
+
+
+def test_argument_and_state_errors():
+    _need_gpu()
+    from paper_0911_4348_gb300 import Context, FedvrError
+    ctx = Context()
+    ctx.build_fedvr(4, 5, -10.0, 10.0, 0)
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_propagate(0.1, 3, True)          # before set_potential
+    assert e.value.code == -7
+    ctx.set_potential([2.0], [0.0], 1.0, 1.0, 2)
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_propagate(0.1, 3, True)          # no HF density and no rho0
+    assert e.value.code == -7
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_block("L", 0, 0)                 # nothing propagated yet
+    assert e.value.code == -7
+    rho0 = np.eye(ctx.n_b, dtype=np.complex128) * 0.0
+    rho0[0, 0] = 1.0
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_propagate(-0.1, 3, True, rho0=rho0)
+    assert e.value.code == -1
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_propagate(0.1, 40000, True, rho0=rho0)
+    assert e.value.code == -1
+    ctx.kbe_propagate(0.1, 2, True, rho0=rho0)
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_block("L", 3, 0)
+    assert e.value.code == -1
+    ctx.close()
+    big = Context()
+    big.build_fedvr(20, 6, -30.0, 30.0, 0)     # order 5: n_b = 99 > 80
+    big.set_potential([2.0], [0.0], 1.0, 1.0, 2)
+    with pytest.raises(FedvrError) as e:
+        big.kbe_propagate(0.1, 2, True, rho0=np.zeros((big.n_b, big.n_b), np.complex128))
+    assert e.value.code == -1
+    big.close()
