@@ -15,7 +15,7 @@ scaling); ranks only meet at the timing barrier.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|tf32|f16]
                     [--workload he_medium|he_small|h3p_large|he_paper|batch64|warmstart|h3p_curve|
-                                combined]
+                                combined|kbe] [--kbe-steps T]
                     [--no-time-to-e0] [--no-fp64-compare] [--no-cpu-baseline]
                     [--train-systems T] [--test-systems H] [--epochs E] [--hidden H]
 """
@@ -44,7 +44,7 @@ UNIT = "builds/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "f16": 3}
 WORKLOADS = {"he_medium": W.he_medium, "he_small": W.he_small, "h3p_large": W.h3p_large,
              "he_paper": W.he_paper, "batch64": None, "warmstart": None, "h3p_curve": None,
-             "combined": None}
+             "combined": None, "kbe": None}
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA per clock per SM -> 1.26 TFLOP/s at 2070 MHz
 
@@ -669,6 +669,93 @@ def run_combined(args, dist, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+def run_kbe(args, dist, rank, world, local):
+    """Real-time two-time Kadanoff-Baym propagation (second Born, complex FP64):
+    one step of this workload is one whole propagation of T time steps from
+    the HF ground state under a dipole field; the metric is time steps per
+    second. Each rank propagates its own replica (no exchange)."""
+    import torch
+    run = W.kbe_he(args.kbe_steps)
+    s_ = run.system
+    stream = torch.cuda.current_stream()
+    ctx = _context(stream, s_)
+    x = ctx.get_basis()["nodes"]
+    dv = np.ascontiguousarray(np.outer(run.field(), x))
+    T = run.n_steps + 1
+    for _ in range(args.warmup):
+        ctx.kbe_propagate(run.dt, run.n_steps, True, dv=dv, want_rho=False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0] or None)
+    clocks.start()
+    dev_ms, coll_ms, sig_ms, launches, walls = 0.0, 0.0, 0.0, 0, []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ctx.kbe_propagate(run.dt, run.n_steps, True, dv=dv)
+        walls.append(time.perf_counter() - t0)
+        st = ctx.kbe_stats()
+        dev_ms += st["ms"]
+        coll_ms += st["collision_ms"]
+        sig_ms += st["sigma_ms"]
+        launches += st["launches"]
+    ck = clocks.stop()
+    dev_s = max_over_ranks(dist, dev_ms / 1000.0)
+    wall_s = max_over_ranks(dist, float(sum(walls)))
+    steps_total = world * args.steps * run.n_steps
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * 2070e6
+    achieved = st["collision_flops"] / (coll_ms / args.steps / 1000.0)
+    n = ctx.n_b
+    line = {"metric": "real-time KBE time steps/s (second Born, two-time, complex FP64)",
+            "value": steps_total / dev_s, "unit": "time steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"{s_.name}: T={T} time points, dt={run.dt}, dipole field "
+                                   f"{run.amp} a.u. at omega={run.omega}, HF initial state",
+                       "two_time_bytes": 2 * (T * n) ** 2 * 16,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "two-time matrices larger than L2 beyond T = 145 at n_b = 39"},
+            "roofline": {"bound": "alu", "kernel": "collision_kernel (FP64 pipe)",
+                         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"},
+            "stage_ms_per_step": {"collision": coll_ms / args.steps,
+                                  "self_energy": sig_ms / args.steps,
+                                  "other": (dev_ms - coll_ms - sig_ms) / args.steps},
+            "e2e": {"value": steps_total / wall_s, "unit": "time steps/s",
+                    "h2d_bytes_per_step": int(dv.nbytes),
+                    "d2h_bytes_per_step": int(T * n * n * 16 + 2 * T * 8)},
+            "gpu_launches": launches,
+            "observables": {"E_first": float(out["E"][0]), "E_last": float(out["E"][-1]),
+                            "N_last": float(out["N"][-1])},
+            "clocks": ck}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = kbe_cpu_baseline(ctx, run, dv)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def kbe_cpu_baseline(ctx, run, dv):
+    """The oracle's propagation of the first steps of the same run (its cost
+    per step grows as the square of the step index, like the GPU's), timed on
+    the host cores."""
+    from oracle import fedvr_oracle as O
+    s_ = run.system
+    b = O.fedvr_basis(s_.n_elem, s_.order, s_.xmin, s_.xmax, s_.grid_kind)
+    h = O.kinetic(b) + np.diag(O.potential(b["nodes"], s_.Z, s_.R, s_.soft_en))
+    V = O.interaction(b["nodes"], s_.soft_ee)
+    rho0 = ctx.get_hf()["rho0"].astype(np.complex128)
+    ns = min(run.n_steps, 24)
+    t0 = time.perf_counter()
+    O.kbe_propagate(h, V, 2.0, rho0, run.dt, ns, dv=dv[: ns + 1])
+    sec = time.perf_counter() - t0
+    return {"value": ns / sec, "unit": "time steps/s", "cores": _cpu_cores(), "kind": "oracle",
+            "sample": f"first {ns} of {run.n_steps} time steps of the same run"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -688,6 +775,8 @@ def main():
     ap.add_argument("--hidden", type=int, default=512)
     ap.add_argument("--curve", default="12,48,192",
                     help="training-set sizes of the combined workload's learning curve")
+    ap.add_argument("--kbe-steps", type=int, default=100,
+                    help="time steps of one propagation of the kbe workload")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -704,8 +793,9 @@ def main():
     from paper_0911_4348_gb300 import Context
 
     torch.cuda.set_device(local)
-    if args.workload in ("batch64", "warmstart", "h3p_curve", "combined"):
-        {"warmstart": run_warmstart, "combined": run_combined}.get(args.workload, run_batch)(
+    if args.workload in ("batch64", "warmstart", "h3p_curve", "combined", "kbe"):
+        {"warmstart": run_warmstart, "combined": run_combined,
+         "kbe": run_kbe}.get(args.workload, run_batch)(
             args, dist, rank, world, local)
         if dist:
             dist.destroy_process_group()

@@ -193,135 +193,153 @@ struct CollArgs {
   double dt;
   const double2 *L, *G, *S, *hHF;
   double2 *RL, *RG;
-  int mode;  // 0: rhs of L and Gt for columns j0 + blockIdx.x; 1: K_L(i, j0) only
-  int corr;  // 0: no collision integrals (time-dependent HF)
+  int mode;    // 0: rhs of L and Gt for columns j0 .. j0 + ncols - 1; 1: K_L(i, j0) only
+  int corr;    // 0: no collision integrals (time-dependent HF)
+  int ncols;   // output column blocks j
+  int splits;  // CTAs sharing one column's contraction (partial sums in part)
+  int rows;    // output rows a per CTA (rows * n <= 256 * kCollQ)
+  double2 *part;  // [splits][ncols][2][n n] partial sums (splits > 1)
 };
 
-// Collision integrals (and with mode 0 the -i h_HF F term) for one time row i.
-// CTA: column block j, a TT x TT output tile (TT = 16 R); thread (ty, tx) owns
-// rows a0 + ty + 16 r and columns c0 + tx + 16 q. Each term stages a 16-wide
-// slice of the contraction index: X tiles [TT][16] (left factors), Y tiles
-// [16][TT] (right factors).
-template <int R>
-__global__ void __launch_bounds__(256) collision_kernel(CollArgs p) {
-  constexpr int TT = 16 * R;
-  extern __shared__ double2 cs[];
-  double2 *X0 = cs, *X1 = cs + TT * 16, *Y0 = cs + 2 * TT * 16, *Y1 = cs + 3 * TT * 16;
-  const int n = p.n, i = p.i, j = p.j0 + blockIdx.x;
-  const long ld = p.ld, nn = (long)n * n;
-  const int a0 = blockIdx.y * TT, c0 = blockIdx.z * TT;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const double2 *SL = p.S, *SG = p.S + (long)p.Tcap * nn;
-  double2 accL[R][R], accG[R][R];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int q = 0; q < R; ++q) accL[r][q] = accG[r][q] = make_double2(0.0, 0.0);
+constexpr int kCollQ = 8;   // outputs per thread
+constexpr int kCollKC = 16; // contraction index b per staged slice
 
-  // term kinds: 0 = -i h_HF(i) x [L(i,j), G(i,j)]; 1 = w (s^> - s^<)(i,s) x [L(s,j), G(s,j)];
-  // 2 = [w s^<(i,s), w s^>(i,s)] x (L - G)(s,j)
+// Collision integrals (and with mode 0 the -i h_HF F term) for one time row i.
+// CTA (column j, split, row tile): its rows x n outputs of block j are spread
+// over the 256 threads (output o = tid + 256 q, q < kCollQ), so no output is
+// padded. The terms of column j,
+//   kind 0: -i h_HF(i) x [L(i, j), Gt(i, j)]                       (mode 0)
+//   kind 1: w^i_s (s^> - s^<)(i, s) x [L(s, j), Gt(s, j)],  s = 0..i
+//   kind 2: [w^j_s s^<(i, s), w^j_s s^>(i, s)] x (L - Gt)(s, j), s = 0..j
+// times the 16-wide slices of b form a list of units; split k of S takes
+// units [U k / S, U (k+1) / S). Each unit stages its left factors X [rows][16]
+// and right factors Y [16][n] in shared memory.
+__global__ void __launch_bounds__(256, 2) collision_kernel(CollArgs p) {
+  extern __shared__ double2 cs[];
+  const int n = p.n, i = p.i, rows = p.rows;
+  double2 *X0 = cs, *X1 = X0 + rows * kCollKC, *Y0 = X1 + rows * kCollKC, *Y1 = Y0 + kCollKC * n;
+  const int split = blockIdx.x % p.splits, jj = blockIdx.x / p.splits, j = p.j0 + jj;
+  const long ld = p.ld, nn = (long)n * n;
+  const int a0 = blockIdx.y * rows, nr = min(rows, n - a0), nout = nr * n;
+  const int tid = threadIdx.x;
+  const double2 *SL = p.S, *SG = p.S + (long)p.Tcap * nn;
+  double2 accL[kCollQ], accG[kCollQ];
+  int xo[kCollQ], yo[kCollQ];
+  int nq = 0;
+#pragma unroll
+  for (int q = 0; q < kCollQ; ++q) {
+    accL[q] = accG[q] = make_double2(0.0, 0.0);
+    const int o = tid + 256 * q;
+    xo[q] = (o < nout) ? (o / n) * kCollKC : 0;
+    yo[q] = (o < nout) ? o % n : 0;
+    nq += (o < nout) ? 1 : 0;
+  }
   const int n0 = p.mode == 0 ? 1 : 0;
   const int n1 = (p.corr && i > 0) ? i + 1 : 0;
   const int n2 = (p.corr && j > 0) ? j + 1 : 0;
-  const int nterm = n0 + n1 + n2;
-  for (int t = 0; t < nterm; ++t) {
+  const int nch = (n + kCollKC - 1) / kCollKC;
+  const long units = (long)(n0 + n1 + n2) * nch;
+  const long u0 = units * split / p.splits, u1 = units * (split + 1) / p.splits;
+  for (long u = u0; u < u1; ++u) {
+    const int t = (int)(u / nch), bc = (int)(u % nch) * kCollKC;
     const int kind = t < n0 ? 0 : (t < n0 + n1 ? 1 : 2);
     const int s = kind == 0 ? i : (kind == 1 ? t - n0 : t - n0 - n1);
     const double w = kind == 1 ? trap_w(s, i, p.dt) : (kind == 2 ? trap_w(s, j, p.dt) : 0.0);
     const long fb = blk(s, j, n, ld);
-    for (int bc = 0; bc < n; bc += 16) {
-      for (int q = tid; q < TT * 16; q += 256) {
-        const int r = q >> 4, bb = q & 15, a = a0 + r, b = bc + bb;
-        double2 x0 = make_double2(0.0, 0.0), x1 = x0;
-        if (a < n && b < n) {
-          if (kind == 0) {
-            const double2 hv = p.hHF[a * n + b];
-            x0 = make_double2(hv.y, -hv.x);  // -i h
+    const int nb = min(kCollKC, n - bc);
+    for (int q = tid; q < nr * kCollKC; q += 256) {
+      const int r = q / kCollKC, bb = q % kCollKC, a = a0 + r, b = bc + bb;
+      double2 x0 = make_double2(0.0, 0.0), x1 = x0;
+      if (bb < nb) {
+        if (kind == 0) {
+          const double2 hv = p.hHF[a * n + b];
+          x0 = make_double2(hv.y, -hv.x);  // -i h
+        } else {
+          const double2 sl = SL[(long)s * nn + a * n + b], sg = SG[(long)s * nn + a * n + b];
+          if (kind == 1) {
+            x0 = scalez(w, subz(sg, sl));
           } else {
-            const double2 sl = SL[(long)s * nn + a * n + b], sg = SG[(long)s * nn + a * n + b];
-            if (kind == 1) {
-              x0 = scalez(w, subz(sg, sl));
-            } else {
-              x0 = scalez(w, sl);
-              x1 = scalez(w, sg);
-            }
+            x0 = scalez(w, sl);
+            x1 = scalez(w, sg);
           }
-        }
-        X0[q] = x0;
-        X1[q] = x1;
-      }
-      for (int q = tid; q < 16 * TT; q += 256) {
-        const int bb = q / TT, cc = q % TT, b = bc + bb, c = c0 + cc;
-        double2 y0 = make_double2(0.0, 0.0), y1 = y0;
-        if (b < n && c < n) {
-          const double2 l = p.L[fb + b * ld + c], g = p.G[fb + b * ld + c];
-          if (kind == 2) {
-            y0 = subz(l, g);
-          } else {
-            y0 = l;
-            y1 = g;
-          }
-        }
-        Y0[q] = y0;
-        Y1[q] = y1;
-      }
-      __syncthreads();
-      if (kind == 2) {
-#pragma unroll 4
-        for (int bb = 0; bb < 16; ++bb) {
-          double2 xl[R], xg[R], yd[R];
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            xl[r] = X0[(ty + 16 * r) * 16 + bb];
-            xg[r] = X1[(ty + 16 * r) * 16 + bb];
-          }
-#pragma unroll
-          for (int q = 0; q < R; ++q) yd[q] = Y0[bb * TT + tx + 16 * q];
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-              cmla(accL[r][q], xl[r], yd[q]);
-              cmla(accG[r][q], xg[r], yd[q]);
-            }
-        }
-      } else {
-#pragma unroll 4
-        for (int bb = 0; bb < 16; ++bb) {
-          double2 xa[R], yl[R], yg[R];
-#pragma unroll
-          for (int r = 0; r < R; ++r) xa[r] = X0[(ty + 16 * r) * 16 + bb];
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            yl[q] = Y0[bb * TT + tx + 16 * q];
-            yg[q] = Y1[bb * TT + tx + 16 * q];
-          }
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-              cmla(accL[r][q], xa[r], yl[q]);
-              cmla(accG[r][q], xa[r], yg[q]);
-            }
         }
       }
-      __syncthreads();
+      X0[q] = x0;
+      X1[q] = x1;
     }
+    for (int q = tid; q < nb * n; q += 256) {
+      const int bb = q / n, c = q % n, b = bc + bb;
+      const double2 l = p.L[fb + b * ld + c], g = p.G[fb + b * ld + c];
+      if (kind == 2) {
+        Y0[q] = subz(l, g);
+      } else {
+        Y0[q] = l;
+        Y1[q] = g;
+      }
+    }
+    __syncthreads();
+    if (kind == 2) {
+#pragma unroll 2
+      for (int bb = 0; bb < nb; ++bb) {
+#pragma unroll
+        for (int q = 0; q < kCollQ; ++q)
+          if (q < nq) {
+            const double2 yd = Y0[bb * n + yo[q]];
+            cmla(accL[q], X0[xo[q] + bb], yd);
+            cmla(accG[q], X1[xo[q] + bb], yd);
+          }
+      }
+    } else {
+#pragma unroll 2
+      for (int bb = 0; bb < nb; ++bb) {
+#pragma unroll
+        for (int q = 0; q < kCollQ; ++q)
+          if (q < nq) {
+            const double2 xa = X0[xo[q] + bb];
+            cmla(accL[q], xa, Y0[bb * n + yo[q]]);
+            cmla(accG[q], xa, Y1[bb * n + yo[q]]);
+          }
+      }
+    }
+    __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int a = a0 + ty + 16 * r, c = c0 + tx + 16 * q;
-      if (a < n && c < n) {
-        if (p.mode == 0) {
-          p.RL[(long)j * nn + a * n + c] = accL[r][q];
-          p.RG[(long)j * nn + a * n + c] = accG[r][q];
-        } else {
-          p.RL[a * n + c] = accL[r][q];
-        }
-      }
+  for (int q = 0; q < kCollQ; ++q) {
+    if (q >= nq) break;
+    const int o = tid + 256 * q, a = a0 + o / n, c = o % n;
+    const long e = (long)a * n + c;
+    if (p.splits > 1) {
+      double2 *P = p.part + ((long)(split * p.ncols + jj) * 2) * nn;
+      P[e] = accL[q];
+      P[nn + e] = accG[q];
+    } else if (p.mode == 0) {
+      p.RL[(long)j * nn + e] = accL[q];
+      p.RG[(long)j * nn + e] = accG[q];
+    } else {
+      p.RL[e] = accL[q];
     }
+  }
+}
+
+// Sum of the splits' partial results in split order (deterministic).
+__global__ void coll_reduce_kernel(int n, int j0, int ncols, int splits, int mode,
+                                   const double2 *part, double2 *RL, double2 *RG) {
+  const long nn = (long)n * n;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int jj = blockIdx.y;
+  double2 sl = make_double2(0.0, 0.0), sg = sl;
+  for (int k = 0; k < splits; ++k) {
+    const double2 *P = part + ((long)(k * ncols + jj) * 2) * nn;
+    sl = addz(sl, P[e]);
+    sg = addz(sg, P[nn + e]);
+  }
+  if (mode == 0) {
+    RL[(long)(j0 + jj) * nn + e] = sl;
+    RG[(long)(j0 + jj) * nn + e] = sg;
+  } else {
+    RL[e] = sl;
+  }
 }
 
 // Predictor (R1 == nullptr) or corrector of time row N+1 and its mirror column.
@@ -412,28 +430,29 @@ __global__ void gather_diag_kernel(int n, long ld, const double2 *L, double2 *ou
   out[(long)t * n * n + idx] = L[blk(t, t, n, ld) + b * ld + c];
 }
 
-int coll_R(int n) { return n <= 16 ? 1 : (n <= 32 ? 2 : 3); }
-size_t coll_smem(int R) { return (size_t)4 * 16 * R * 16 * sizeof(double2); }
+// Output rows per CTA and the CTAs' shared memory for n.
+int coll_rows(int n) { return std::min(n, 256 * kCollQ / n); }
+size_t coll_smem(int n) {
+  return (size_t)(2 * coll_rows(n) * kCollKC + 2 * kCollKC * n) * sizeof(double2);
+}
+// Partial-sum slots (splits x columns) a launch may use: the split count is
+// chosen so that a launch has about 4 CTAs per SM of a 152-SM GPU, at most 16.
+constexpr int kCollTargetCtas = 608;
+inline long coll_part_slots(int T) { return (long)kCollTargetCtas + T; }
 
-cudaError_t launch_collision(const CollArgs &a, int ncols, cudaStream_t s) {
-  const int R = coll_R(a.n), TT = 16 * R;
-  const unsigned tiles = (unsigned)((a.n + TT - 1) / TT);
-  dim3 grid((unsigned)ncols, tiles, tiles);
-  const size_t sm = coll_smem(R);
-  cudaError_t e;
-  switch (R) {
-    case 1:
-      collision_kernel<1><<<grid, 256, sm, s>>>(a);
-      break;
-    case 2:
-      collision_kernel<2><<<grid, 256, sm, s>>>(a);
-      break;
-    default:
-      e = cudaFuncSetAttribute(collision_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm);
-      if (e != cudaSuccess) return e;
-      collision_kernel<3><<<grid, 256, sm, s>>>(a);
-  }
+cudaError_t launch_collision(CollArgs a, cudaStream_t s, long *launches) {
+  a.rows = coll_rows(a.n);
+  const int tiles = (a.n + a.rows - 1) / a.rows;
+  const long ctas = (long)a.ncols * tiles;
+  a.splits = (int)std::max(1L, std::min(16L, (kCollTargetCtas + ctas - 1) / ctas));
+  dim3 grid((unsigned)(a.ncols * a.splits), (unsigned)tiles);
+  collision_kernel<<<grid, 256, coll_smem(a.n), s>>>(a);
+  ++*launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.splits == 1) return e;
+  ++*launches;
+  dim3 rg((unsigned)(((long)a.n * a.n + 255) / 256), (unsigned)a.ncols);
+  coll_reduce_kernel<<<rg, 256, 0, s>>>(a.n, a.j0, a.ncols, a.splits, a.mode, a.part, a.RL, a.RG);
   return cudaGetLastError();
 }
 
@@ -467,7 +486,7 @@ struct KbeRun {
   long ld;
   double dt, spin;
   bool corr;
-  double2 *L, *G, *S, *T1, *R0L, *R0G, *R1L, *R1G, *hHF, *K;
+  double2 *L, *G, *S, *T1, *R0L, *R0G, *R1L, *R1G, *hHF, *K, *part;
   const double *h, *V, *dv;
   double *E, *Nn;
   cudaStream_t s;
@@ -516,24 +535,23 @@ struct KbeRun {
     return FEDVR_OK;
   }
   int rhs(int i, double2 *RL, double2 *RG) {
-    CollArgs a{n, i, 0, Tcap, ld, dt, L, G, S, hHF, RL, RG, 0, corr ? 1 : 0};
+    CollArgs a{n, i, 0, Tcap, ld, dt, L, G, S, hHF, RL, RG, 0, corr ? 1 : 0, i + 1, 1, 0, part};
     KBE_CK(ctx, mark(0));
-    KBE_CK(ctx, launch_collision(a, i + 1, s));
+    KBE_CK(ctx, launch_collision(a, s, &launches));
     KBE_CK(ctx, mark(-1));
     cmac_coll += coll_cmacs(n, i, 0, i + 1, 0, corr);
-    ++launches;
     return FEDVR_OK;
   }
   int observe(int t) {
-    CollArgs a{n, t, t, Tcap, ld, dt, L, G, S, hHF, K, nullptr, 1, corr ? 1 : 0};
+    CollArgs a{n, t, t, Tcap, ld, dt, L, G, S, hHF, K, nullptr, 1, corr ? 1 : 0, 1, 1, 0, part};
     KBE_CK(ctx, mark(0));
-    KBE_CK(ctx, launch_collision(a, 1, s));
+    KBE_CK(ctx, launch_collision(a, s, &launches));
     KBE_CK(ctx, mark(-1));
     cmac_coll += coll_cmacs(n, t, t, 1, 1, corr);
     observe_kernel<<<1, 256, 0, s>>>(n, spin, h, dv_at(t), V, L, blk(t, t, n, ld), ld, K, E + t,
                                      Nn + t);
     KBE_CK(ctx, cudaGetLastError());
-    launches += 2;
+    ++launches;
     return FEDVR_OK;
   }
   int advance(int N, bool corrector) {
@@ -587,6 +605,7 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   KBE_ENSURE(ctx, k_R, 4 * (size_t)T * nn * cz);
   KBE_ENSURE(ctx, k_aux, (2 * nn + 2 * (size_t)T) * cz);
   KBE_ENSURE(ctx, k_out, (size_t)T * nn * cz + (size_t)T * n * sizeof(double));
+  KBE_ENSURE(ctx, k_part, (size_t)coll_part_slots(T) * 2 * nn * cz);
   double2 *L = P<double2>(ctx->k_L), *G = P<double2>(ctx->k_G);
   double2 *R = P<double2>(ctx->k_R);
   double2 *aux = P<double2>(ctx->k_aux);
@@ -626,6 +645,7 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   run.R1G = R + 3 * (size_t)T * nn;
   run.hHF = aux;
   run.K = aux + nn;
+  run.part = P<double2>(ctx->k_part);
   run.h = CP<double>(ctx->b_h);
   run.V = CP<double>(ctx->b_V);
   run.dv = dv ? dv_d : nullptr;
@@ -637,6 +657,8 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
     const size_t sm = 2 * nn * cz;
     KBE_CK(ctx, cudaFuncSetAttribute(exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sm));
+    KBE_CK(ctx, cudaFuncSetAttribute(collision_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)coll_smem(n)));
   }
   KBE_CK(ctx, run.mark(-1));
   if (int r = run.hf(0)) return r;

@@ -148,6 +148,33 @@ def warmstart_system(system_id: int, config_id: int = 5) -> System:
                   u=8, p=16)
 
 
+@dataclass
+class KbeRun:
+    """A real-time propagation: the system (its HF ground state is the
+    uncorrelated initial state), the time step, the number of steps and a
+    dipole field E(t) = amp sin(omega t) sin^2(pi t / t_end) applied as the
+    potential x_a E(t) at the nodes."""
+    system: System
+    dt: float
+    n_steps: int
+    amp: float
+    omega: float
+
+    def field(self) -> np.ndarray:
+        """E(t_k) for k = 0 .. n_steps."""
+        t = np.arange(self.n_steps + 1) * self.dt
+        t_end = self.n_steps * self.dt
+        return self.amp * np.sin(self.omega * t) * np.sin(np.pi * t / t_end) ** 2
+
+
+def kbe_he(n_steps: int = 100) -> KbeRun:
+    """1D He, Z=2, box [-15,15], 10 elements of order 4 (n_b = 39), driven from
+    its HF ground state by a 0.1 a.u. field at omega = 0.9 Ha; dt = 0.04 keeps
+    Heun's step stable (max|e| of h about 10 Ha)."""
+    s = System("He n_b=39 (real time)", -15.0, 15.0, 10, 4, [2.0], [0.0])
+    return KbeRun(s, 0.04, n_steps, 0.1, 0.9)
+
+
 def random_symmetric(rng: np.random.Generator, n: int, scale: float = 1.0) -> np.ndarray:
     """Random symmetric n x n matrix with U(-scale, scale) entries."""
     a = rng.uniform(-scale, scale, size=(n, n))
