@@ -31,7 +31,7 @@
 namespace fedvr {
 namespace {
 
-constexpr int kKbeMaxN = 80;  // exchange operands (2 n^2 complex) fit one CTA's shared memory
+constexpr int kKbeMaxN = 80;  // exchange operands (2 n^2 + 1024 complex) fit one CTA's shared memory
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -146,12 +146,17 @@ __global__ void direct_kernel(int n, int i, long ld, const double2 *L, const dou
   S[((long)w * Tcap + kt) * n * n + idx] = cmul(scalez(spin, g), W);
 }
 
-// Exchange term, one CTA per (column b, entry e): with g and
-// Hb_lk = V_bl gb_lk in shared memory, P_ak = sum_l g_al Hb_lk and
-// X_ab = sum_k V_ak P_ak g_kb (a warp per row a, lanes over k); S_ab -= X_ab.
-__global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, const double2 *L,
-                                                       const double2 *G, const double *V,
-                                                       int Tcap, double2 *S) {
+// Exchange term (n > 16), one CTA per (column b, entry e): with g and
+// Hb_lk = V_bl gb_lk in shared memory, the (a, k) pairs of a chunk of rows
+// are spread over the threads (four per thread), each computing
+// P_ak = sum_l g_al Hb_lk and v_ak = V_ak P_ak g_kb into shared memory; then
+// one thread per row adds X_ab = sum_k v_ak in k order and S_ab -= X_ab.
+// Small n (<= 16): one warp per row a, lanes over k, warp-shuffle sum over k
+// (fewer FP64 instructions in the k-sum than the pair layout below).
+__global__ void __launch_bounds__(256) exchange_rows_kernel(int n, int i, long ld,
+                                                            const double2 *L, const double2 *G,
+                                                            const double *V, int Tcap,
+                                                            double2 *S) {
   extern __shared__ double2 xs[];
   double2 *gs = xs, *hb = xs + n * n;
   const int b = blockIdx.x, e = blockIdx.y, kt = e >> 1, w = e & 1;
@@ -160,7 +165,6 @@ __global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, co
   for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
     const int r = q / n, c = q % n;
     gs[q] = g[r * ld + c];
-    // H_rc enters as gb_cr = -conj(H_rc), so Hb[c][r] = -V_bc conj(H_rc)
     const double2 h = H[r * ld + c];
     const double v = V[b * n + c];
     hb[c * n + r] = make_double2(-v * h.x, v * h.y);
@@ -180,10 +184,65 @@ __global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, co
       part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
       part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
     }
-    if (lane == 0) {
-      double2 v = Sout[a * n + b];
-      Sout[a * n + b] = subz(v, part);
+    if (lane == 0) Sout[a * n + b] = subz(Sout[a * n + b], part);
+  }
+}
+
+constexpr int kXPairs = 4;  // (a, k) pairs per thread and chunk
+inline int xchg_rows(int n) { return n < 256 * kXPairs / n ? n : 256 * kXPairs / n; }
+
+__global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, const double2 *L,
+                                                       const double2 *G, const double *V,
+                                                       int Tcap, double2 *S) {
+  extern __shared__ double2 xs[];
+  const int rows = n < 256 * kXPairs / n ? n : 256 * kXPairs / n;
+  double2 *gs = xs, *hb = xs + n * n, *vs = xs + 2 * n * n;
+  const int b = blockIdx.x, e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const long off = blk(i, kt, n, ld);
+  const double2 *g = (w ? G : L) + off, *H = (w ? L : G) + off;
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+    const int r = q / n, c = q % n;
+    gs[q] = g[r * ld + c];
+    // H_rc enters as gb_cr = -conj(H_rc), so Hb[c][r] = -V_bc conj(H_rc)
+    const double2 h = H[r * ld + c];
+    const double v = V[b * n + c];
+    hb[c * n + r] = make_double2(-v * h.x, v * h.y);
+  }
+  __syncthreads();
+  double2 *Sout = S + ((long)w * Tcap + kt) * n * n;
+  for (int a0 = 0; a0 < n; a0 += rows) {
+    const int nr = min(rows, n - a0), np = nr * n;
+    int pa[kXPairs], pk[kXPairs];
+    double2 P[kXPairs];
+#pragma unroll
+    for (int q = 0; q < kXPairs; ++q) {
+      const int pp = threadIdx.x + 256 * q;
+      pa[q] = pp < np ? a0 + pp / n : a0;
+      pk[q] = pp < np ? pp % n : 0;
+      P[q] = make_double2(0.0, 0.0);
     }
+    for (int l = 0; l < n; ++l) {
+#pragma unroll
+      for (int q = 0; q < kXPairs; ++q) cmla(P[q], gs[pa[q] * n + l], hb[l * n + pk[q]]);
+    }
+#pragma unroll
+    for (int q = 0; q < kXPairs; ++q) {
+      const int pp = threadIdx.x + 256 * q;
+      if (pp < np) {
+        double2 v = make_double2(0.0, 0.0);
+        cmla(v, scalez(V[pa[q] * n + pk[q]], P[q]), gs[pk[q] * n + b]);
+        vs[pp] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      double2 x = make_double2(0.0, 0.0);
+      const double2 *vr = vs + threadIdx.x * n;
+      for (int k = 0; k < n; ++k) x = addz(x, vr[k]);
+      const int a = a0 + threadIdx.x;
+      Sout[a * n + b] = subz(Sout[a * n + b], x);
+    }
+    __syncthreads();
   }
 }
 
@@ -525,8 +584,13 @@ struct KbeRun {
     direct_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1, spin, Tcap,
                                                              S);
     KBE_CK(ctx, cudaGetLastError());
-    const size_t sm = (size_t)2 * nn * sizeof(double2);
-    exchange_kernel<<<dim3(n, ne), 256, sm, s>>>(n, i, ld, L, G, V, Tcap, S);
+    if (n <= 16) {
+      exchange_rows_kernel<<<dim3(n, ne), 256, (size_t)2 * nn * sizeof(double2), s>>>(
+          n, i, ld, L, G, V, Tcap, S);
+    } else {
+      const size_t sm = (size_t)(2 * nn + xchg_rows(n) * n) * sizeof(double2);
+      exchange_kernel<<<dim3(n, ne), 256, sm, s>>>(n, i, ld, L, G, V, Tcap, S);
+    }
     KBE_CK(ctx, cudaGetLastError());
     KBE_CK(ctx, mark(-1));
     const double n3 = (double)n * n * n;
@@ -654,7 +718,7 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   run.s = s;
   run.ev = &ctx->kbe_events;
   {
-    const size_t sm = 2 * nn * cz;
+    const size_t sm = (2 * nn + (size_t)xchg_rows(n) * n) * cz;
     KBE_CK(ctx, cudaFuncSetAttribute(exchange_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sm));
     KBE_CK(ctx, cudaFuncSetAttribute(collision_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
