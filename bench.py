@@ -682,8 +682,9 @@ def run_kbe(args, dist, rank, world, local):
     x = ctx.get_basis()["nodes"]
     dv = np.ascontiguousarray(np.outer(run.field(), x))
     T = run.n_steps + 1
+    prec = PRECISIONS[args.kbe_precision]
     for _ in range(args.warmup):
-        ctx.kbe_propagate(run.dt, run.n_steps, True, dv=dv, want_rho=False)
+        ctx.kbe_propagate(run.dt, run.n_steps, True, dv=dv, want_rho=False, precision=prec)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -693,7 +694,7 @@ def run_kbe(args, dist, rank, world, local):
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = ctx.kbe_propagate(run.dt, run.n_steps, True, dv=dv)
+        out = ctx.kbe_propagate(run.dt, run.n_steps, True, dv=dv, precision=prec)
         walls.append(time.perf_counter() - t0)
         st = ctx.kbe_stats()
         dev_ms += st["ms"]
@@ -704,23 +705,33 @@ def run_kbe(args, dist, rank, world, local):
     dev_s = max_over_ranks(dist, dev_ms / 1000.0)
     wall_s = max_over_ranks(dist, float(sum(walls)))
     steps_total = world * args.steps * run.n_steps
-    peak = N_SM * FP64_FLOP_PER_CLK_SM * 2070e6
     achieved = st["collision_flops"] / (coll_ms / args.steps / 1000.0)
     n = ctx.n_b
-    line = {"metric": "real-time KBE time steps/s (second Born, two-time, complex FP64)",
+    if prec == 0:
+        roof = {"bound": "alu", "kernel": "collision_kernel (FP64 pipe)",
+                "peak": N_SM * FP64_FLOP_PER_CLK_SM * 2070e6 / 1e12,
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
+    else:
+        # three TF32 products per algorithmic product on the tensor pipe (TF32 = half the BF16 rate)
+        pk = load_peaks().get("bf16_tflops")
+        roof = {"bound": "tensor", "kernel": "collision products (gemm_tf32x3_kernel, split TF32)",
+                "peak": (pk / 2.0) if pk else None,
+                "peak_source": "measured bf16 burst x 1/2 (tf32 dense rate), of measured"}
+    roof.update({"achieved": achieved / 1e12, "unit": "TFLOP/s", "traffic": None})
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    line = {"metric": "real-time KBE time steps/s (second Born, two-time)",
             "value": steps_total / dev_s, "unit": "time steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128" if prec == 0 else "c128 (collision integrals split tf32)",
+            "data": "synthetic",
             "config": {"workload": f"{s_.name}: T={T} time points, dt={run.dt}, dipole field "
                                    f"{run.amp} a.u. at omega={run.omega}, HF initial state",
                        "two_time_bytes": 2 * (T * n) ** 2 * 16,
                        "parallelism": f"replicas x{world}",
                        "l2": "two-time matrices larger than L2 beyond T = 145 at n_b = 39"},
-            "roofline": {"bound": "alu", "kernel": "collision_kernel (FP64 pipe)",
-                         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"},
+            "roofline": roof,
             "stage_ms_per_step": {"collision": coll_ms / args.steps,
                                   "self_energy": sig_ms / args.steps,
                                   "other": (dev_ms - coll_ms - sig_ms) / args.steps},
@@ -777,6 +788,8 @@ def main():
                     help="training-set sizes of the combined workload's learning curve")
     ap.add_argument("--kbe-steps", type=int, default=100,
                     help="time steps of one propagation of the kbe workload")
+    ap.add_argument("--kbe-precision", choices=("fp64", "tf32"), default="fp64",
+                    help="kbe workload: collision integrals in FP64 or as split-TF32 products")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -468,6 +468,14 @@ int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds);
  * The Hamiltonian is the context's h (after set_potential) plus
  * diag(dv(t_k)) (a time-dependent potential at the nodes, e.g. x_a E(t_k)).
  *
+ * precision: FEDVR_FP64 (everything in complex FP64), or FEDVR_SPLIT_TF32
+ * (second Born only): the two collision integrals of each time row run as
+ * split-TF32 tensor-core products (three TF32 products per product, FP32
+ * accumulation, about 2^-21 relative per product) over FP32 copies of L, Gt
+ * and the weighted L - Gt kept beside the FP64 matrices (3 x 8 (T n_b)^2
+ * more bytes; needs T n_b <= 32767); the -i h_HF F term, the energy, the
+ * self-energy and the stepping stay FP64.
+ *
  * rho0: host [n_b][n_b] complex (interleaved re, im; 16 bytes per entry), or
  * NULL for the real HF density rho0 of the last solve_hf. dv: host
  * [n_steps+1][n_b] or NULL. Outputs (host, any may be NULL): rho_out
@@ -481,8 +489,10 @@ int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds);
  * call for fedvr_kbe_get_block until the next call or fedvr_destroy.
  * Errors: FEDVR_ERR_STATE before set_potential (or before solve_hf with
  * rho0 = NULL); FEDVR_ERR_ARG for dt <= 0, n_steps outside [0, 32766],
- * n_b > 80 or storage beyond the free device memory. Synchronises the stream. */
-int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
+ * n_b > 80, another precision or storage beyond the free device memory;
+ * FEDVR_ERR_TIMEOUT if a tensor-core wait gave up (the context is then
+ * failed). Synchronises the stream. */
+int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born, int precision,
                         const double *rho0, const double *dv, double *rho_out, double *E_out,
                         double *N_out);
 

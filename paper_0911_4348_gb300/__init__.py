@@ -296,11 +296,13 @@ class Context:
         with code -5 (timeout) and leaves the context failed."""
         self._check(self._lib.fedvr_selftest_wait(self._h, 1 if release else 0, limit_seconds))
 
-    def kbe_propagate(self, dt, n_steps, second_born=True, rho0=None, dv=None, want_rho=True):
+    def kbe_propagate(self, dt, n_steps, second_born=True, rho0=None, dv=None, want_rho=True,
+                      precision=FP64):
         """Real-time two-time Kadanoff-Baym propagation (``fedvr_kbe_propagate``)
         from rho0 (complex [n][n]; None: the HF density of the last solve_hf)
-        under h + diag(dv[k]) (dv: [n_steps+1][n] or None). Returns a dict with
-        rho [n_steps+1][n][n] complex (if want_rho), E and N [n_steps+1]."""
+        under h + diag(dv[k]) (dv: [n_steps+1][n] or None); precision FP64 or
+        SPLIT_TF32 (collision integrals on the tensor cores). Returns a dict
+        with rho [n_steps+1][n][n] complex (if want_rho), E and N [n_steps+1]."""
         n = self.n_b
         T = n_steps + 1
         r0 = None
@@ -315,7 +317,8 @@ class Context:
         E = np.empty(T)
         N = np.empty(T)
         self._check(self._lib.fedvr_kbe_propagate(
-            self._h, float(dt), int(n_steps), 1 if second_born else 0, _dptr(r0), _dptr(d),
+            self._h, float(dt), int(n_steps), 1 if second_born else 0, int(precision), _dptr(r0),
+            _dptr(d),
             _dptr(rho.view(np.float64)) if want_rho else None, _dptr(E), _dptr(N)))
         return {"rho": rho, "E": E, "N": N}
 

@@ -70,7 +70,8 @@ SIGNATURES = {
     "fedvr_conv_g0": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, _vp, _vp, C.c_double,
                                 _vp, _vp, C.c_int]),
     "fedvr_selftest_wait": (C.c_int, [_vp, C.c_int, C.c_double]),
-    "fedvr_kbe_propagate": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]),
+    "fedvr_kbe_propagate": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp,
+                                      _dp, _dp]),
     "fedvr_kbe_get_block": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp]),
     "fedvr_kbe_stats": (C.c_int, [_vp, _dp]),
 }

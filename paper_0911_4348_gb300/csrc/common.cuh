@@ -89,7 +89,7 @@ struct fedvr_ctx {
       w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16,
       w_xrow, w_dens, w_q4coef, w_q4W, w_q4w;
   // real-time propagation: two-time L and Gt, self-energy row, scratch, outputs
-  fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part;
+  fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part, k_sh, k_aop, k_o, k_flag;
 };
 
 namespace fedvr {

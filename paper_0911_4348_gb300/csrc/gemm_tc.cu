@@ -19,6 +19,13 @@
 // index (blockIdx.z) adds a_sz, b_sz and o_sz. Element offsets fit in 32 bits
 // (checked on the host).
 //
+// Optional contraction slices: with nkz > 1 the K range is cut into slices of
+// kz values (a multiple of 32), blockIdx.z = batch * nkz + slice, and slice k
+// writes its partial product at O + k o_kz (the caller adds the slices). With
+// k_tri > 0 a tile stops its contraction at (g_max + 1) k_tri, g_max the
+// largest group among its rows (a block-triangular B: the rows of group g need
+// k < (g + 1) k_tri); a tile whose slice lies beyond that writes zeros.
+//
 // One CTA per 128 x Nt output tile (Nt <= 256, a multiple of 16): warps 0-3
 // drain TMEM, warps 4-11 load, convert, split and store both operands of a
 // 32-wide k chunk into the K-major 128-byte-swizzled stage layout, warp 12
@@ -46,6 +53,8 @@ struct GemmArgs {
   void *O;
   int o_sg, o_sc, o_sz;
   int *err;
+  int kz, nkz, k_tri;  // contraction slices and block-triangular limit (see above)
+  long o_kz;
 };
 
 // Split x and store the pair at element (r, k) of a 128B-swizzled K-major tile
@@ -84,8 +93,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 6);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row0 = blockIdx.x * 128, col0 = blockIdx.y * Nt, z = blockIdx.z;
-  const int KC = (p.K + 31) / 32;
+  const int row0 = blockIdx.x * 128, col0 = blockIdx.y * Nt;
+  const int z = blockIdx.z / p.nkz, zk = blockIdx.z % p.nkz;
+  const int kbeg = zk * p.kz;
+  int kend = min(p.K, kbeg + p.kz);
+  if (p.k_tri > 0) kend = min(kend, (min(p.R - 1, row0 + 127) / p.G + 1) * p.k_tri);
+  const int KC = kend > kbeg ? (kend - kbeg + 31) / 32 : 0;
 
   if (warp == 0) {
     tc::tmem_alloc(tmem_slot, (uint32_t)p.tcols);
@@ -142,14 +155,14 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
     // KC one local column
     const int cb = B_MC ? (pt >> 5) * 32 : pt;
     for (int kc = 0; kc < KC; ++kc) {
-      const int k0 = kc * 32;
+      const int k0 = kbeg + kc * 32;
       float av[16], bv[32];
       if (A_MC) {
         const int k = k0 + lane;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           float x = 0.f;
-          if (alive[i] && k < p.K) {
+          if (alive[i] && k < kend) {
             x = (float)A[aoff[i] + k * p.a_sk];
             if (MUL2) x *= (float)A2[aoff2[i] + k * p.a_sk];
           }
@@ -159,21 +172,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
         const int kb = k0 + (pt & 1) * 16;
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          av[i] = (alive[0] && kb + i < p.K) ? (float)A[aoff[0] + kb + i] : 0.f;
+          av[i] = (alive[0] && kb + i < kend) ? (float)A[aoff[0] + kb + i] : 0.f;
       }
       if (B_MC) {
         const int k = k0 + lane;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int c = col0 + cb + i;
-          bv[i] = (cb + i < Nt && c < p.N && k < p.K) ? (float)B[k * p.b_s + c] : 0.f;
+          bv[i] = (cb + i < Nt && c < p.N && k < kend) ? (float)B[k * p.b_s + c] : 0.f;
         }
       } else {
         const int c = col0 + cb;
         const bool ok = cb < Nt && c < p.N;
 #pragma unroll
         for (int i = 0; i < 32; ++i)
-          bv[i] = (ok && k0 + i < p.K) ? (float)B[c * p.b_s + k0 + i] : 0.f;
+          bv[i] = (ok && k0 + i < kend) ? (float)B[c * p.b_s + k0 + i] : 0.f;
       }
       const int s = kc & 1;
       const uint32_t use = kc >> 1;
@@ -214,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
         }
         tc::fence_after_sync();
         const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
-        const int ksteps = min(4, (p.K - kc * 32 + 7) / 8);
+        const int ksteps = min(4, (kend - kbeg - kc * 32 + 7) / 8);
         for (int kk = 0; kk < ksteps; ++kk) {
           const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
           const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
@@ -231,12 +244,20 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
     }
   } else {
     // ---- epilogue: TMEM lane = tile row, 16 columns per load ----
-    if (tc::warp_wait(accf, 0, kWaitNs)) {
+    if (KC == 0) {
+      // empty contraction slice: zeros, no MMA to wait for
+      const int r = row0 + warp * 32 + lane;
+      if (r < p.R) {
+        const long ooff = (long)zk * p.o_kz + (long)z * p.o_sz + (long)(r / p.G) * p.o_sg + (r % p.G);
+        TO *O = reinterpret_cast<TO *>(p.O);
+        for (int c = 0; c < Nt && col0 + c < p.N; ++c) O[ooff + (long)(col0 + c) * p.o_sc] = (TO)0;
+      }
+    } else if (tc::warp_wait(accf, 0, kWaitNs)) {
       tc::fence_after_sync();
       const int r = row0 + warp * 32 + lane;
       const bool live = r < p.R;
       const long ooff =
-          live ? (long)z * p.o_sz + (long)(r / p.G) * p.o_sg + (r % p.G) : 0;
+          live ? (long)zk * p.o_kz + (long)z * p.o_sz + (long)(r / p.G) * p.o_sg + (r % p.G) : 0;
       TO *O = reinterpret_cast<TO *>(p.O);
       for (int c0 = 0; c0 < Nt; c0 += 16) {
         float v[16];
@@ -273,6 +294,12 @@ template <typename TA, typename TB, typename TO, bool A_MC, bool B_MC, bool MUL2
 cudaError_t gemm_tf32x3(GemmArgs p, int batch, cudaStream_t s) {
   if (p.R <= 0 || p.N <= 0 || p.K <= 0) return cudaSuccess;
   if (p.N > 4096 || p.G <= 0) return cudaErrorInvalidValue;
+  if (p.nkz <= 1) {
+    p.nkz = 1;
+    p.kz = p.K;
+  } else if (p.kz <= 0 || p.kz % 32 != 0) {
+    return cudaErrorInvalidValue;
+  }
   const int ntile = (p.N + 255) / 256;
   p.Nt = ((p.N + ntile - 1) / ntile + 15) / 16 * 16;
   p.tcols = 32;
@@ -282,7 +309,7 @@ cudaError_t gemm_tf32x3(GemmArgs p, int batch, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<TA, TB, TO, A_MC, B_MC, MUL2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((p.R + 127) / 128), (unsigned)ntile, (unsigned)batch);
+  dim3 grid((unsigned)((p.R + 127) / 128), (unsigned)ntile, (unsigned)(batch * p.nkz));
   gemm_tf32x3_kernel<TA, TB, TO, A_MC, B_MC, MUL2><<<grid, kThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -295,6 +322,7 @@ GemmArgs args0(int R, int N, int K, int *err) {
   p.G = R;
   p.nG = 1;
   p.err = err;
+  p.nkz = 1;
   return p;
 }
 
@@ -336,6 +364,38 @@ cudaError_t vqv_tc(int n, int M, int ld, const float *V32, const float *g32, flo
   q.o_sg = n * ld;
   q.o_sc = ld;
   return gemm_tf32x3<float, float, float, false, false, false>(q, 1, s);
+}
+
+cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long sh_z,
+                        const float *Aop, int lda, long a_z, int nkz, bool tri, double *O,
+                        long o_z, long o_kz, int *err, cudaStream_t s) {
+  if (!fits32(2L * Tn * Tn) || !fits32(sh_z) || !fits32(a_z) || !fits32(o_z) ||
+      !fits32((long)2 * n * lda))
+    return cudaErrorInvalidValue;
+  // O[slice][z][j][p][a][c] = sum_k Sh_z[k][j n + c] Aop_z[p n + a][k]: rows (j, c) grouped by
+  // j, columns (p, a); batch z = 0, 1
+  GemmArgs g = args0(ncols * n, 2 * n, K, err);
+  g.G = n;
+  g.nG = ncols;
+  g.A = Sh;
+  g.a_sg = n;
+  g.a_sk = Tn;
+  g.a_sz = (int)sh_z;
+  g.B = Aop;
+  g.b_s = lda;
+  g.b_sz = (int)a_z;
+  g.O = O;
+  g.o_sg = 2 * n * n;
+  g.o_sc = n;
+  g.o_sz = (int)o_z;
+  g.o_kz = o_kz;
+  if (nkz > 1) {
+    g.nkz = nkz;
+    g.kz = ((K + nkz - 1) / nkz + 31) / 32 * 32;
+    g.nkz = (K + g.kz - 1) / g.kz;
+  }
+  g.k_tri = tri ? 2 * n : 0;
+  return gemm_tf32x3<float, float, double, true, false, false>(g, 2, s);
 }
 
 cudaError_t conv2_tc(int n, int M, const float *K32, const double *C, const double *I1,

@@ -21,12 +21,25 @@
 //   K_G = sum_{s<=i} w^i_s [s^> - s^<](i, s) Gt(s, j) + sum_{s<=j} w^j_s s^>(i, s) [L - Gt](s, j),
 // w^m_s the trapezoid weights on [0, t_m] (dt, halved at both ends; zero for m = 0).
 //
-// Every kernel here is bound by GB300's FP64 pipe (2 DFMA per clock per SM):
-// operands come from shared memory or L1, and the work per launch is counted
-// in complex multiply-adds (4 DFMA each).
+// Every FP64 kernel here is bound by GB300's FP64 pipe (2 DFMA per clock per
+// SM): operands come from shared memory or L1, and the work per launch is
+// counted in complex multiply-adds (4 DFMA each).
+//
+// Split-TF32 mode (precision 1): the two collision integrals of a time row run
+// as split-TF32 tensor-core products (gemm_tc.cu) over FP32 planar shadows of
+// L, Gt and the trapezoid-weighted L - Gt, written beside the FP64 matrices by
+// every advance: shadow w (0 L, 1 Gt, 2 Dw) holds row (2 s + p) n + b, column
+// j n + c = part p (re, im) of F(s, j)[b][c], and Dw(s, j) = w^j_s (L - Gt)(s, j)
+// for s <= j, zero below (so the second integral is a plain product over
+// s <= j, block-triangular in (s, j)). The left factors of both integrals are
+// laid out as real [2n][2 T n] matrices (rows re/im of the output, columns
+// (s, p, b)) that turn each complex product into one real product. The
+// -i h_HF F term, the energy's K_L(t, t), the self-energy and the stepping stay
+// in FP64.
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_sys.cuh"
 
 namespace fedvr {
 namespace {
@@ -404,7 +417,7 @@ __global__ void coll_reduce_kernel(int n, int j0, int ncols, int splits, int mod
 // Predictor (R1 == nullptr) or corrector of time row N+1 and its mirror column.
 __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, const double2 *R0L,
                                const double2 *R0G, const double2 *R1L, const double2 *R1G,
-                               double dt) {
+                               double dt, float *sh, long shz, long Tn) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int j = blockIdx.y, b = idx / n, c = idx % n;
@@ -423,6 +436,23 @@ __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, co
     G[blk(N + 1, j, n, ld) + b * ld + c] = vg;
     L[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vl);
     G[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vg);
+    if (sh) {
+      const long pim = (long)n * Tn;  // from part re to part im
+      const long r0 = ((long)2 * (N + 1) * n + b) * Tn + (long)j * n + c;  // (N+1, j)[b][c]
+      const long m0 = ((long)2 * j * n + c) * Tn + (long)(N + 1) * n + b;  // (j, N+1)[c][b]
+      sh[r0] = (float)vl.x;
+      sh[r0 + pim] = (float)vl.y;
+      sh[shz + r0] = (float)vg.x;
+      sh[shz + r0 + pim] = (float)vg.y;
+      sh[m0] = (float)vl.x;
+      sh[m0 + pim] = (float)(-vl.y);
+      sh[shz + m0] = (float)vg.x;
+      sh[shz + m0 + pim] = (float)(-vg.y);
+      // Dw(j, N+1) = w^{N+1}_j (L - Gt)(j, N+1), the conjugate transpose of row N+1's
+      const double wt = j == 0 ? 0.5 * dt : dt;
+      sh[2 * shz + m0] = (float)(wt * (vl.x - vg.x));
+      sh[2 * shz + m0 + pim] = (float)(-(wt * (vl.y - vg.y)));
+    }
   } else {
     // equal times: d rho/dt = X + X^H with X = rhs_L(t, t)
     double2 d = addz(R0L[(long)N * nn + b * n + c], conjz(R0L[(long)N * nn + c * n + b]));
@@ -434,8 +464,19 @@ __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, co
       f = 0.5 * dt;
     }
     const double2 v = addz(L[blk(N, N, n, ld) + b * ld + c], scalez(f, d));
+    const double2 vg = make_double2(v.x - (b == c ? 1.0 : 0.0), v.y);
     L[blk(N + 1, N + 1, n, ld) + b * ld + c] = v;
-    G[blk(N + 1, N + 1, n, ld) + b * ld + c] = make_double2(v.x - (b == c ? 1.0 : 0.0), v.y);
+    G[blk(N + 1, N + 1, n, ld) + b * ld + c] = vg;
+    if (sh) {
+      const long pim = (long)n * Tn;
+      const long r0 = ((long)2 * (N + 1) * n + b) * Tn + (long)(N + 1) * n + c;
+      sh[r0] = (float)v.x;
+      sh[r0 + pim] = (float)v.y;
+      sh[shz + r0] = (float)vg.x;
+      sh[shz + r0 + pim] = (float)vg.y;
+      sh[2 * shz + r0] = (float)(0.5 * dt * (v.x - vg.x));
+      sh[2 * shz + r0 + pim] = (float)(0.5 * dt * (v.y - vg.y));
+    }
   }
 }
 
@@ -480,6 +521,74 @@ __global__ void observe_kernel(int n, double spin, const double *h, const double
     *E_out = spin * red[0][0] + 0.5 * spin * red[1][0] + 0.5 * spin * red[2][0];
     *N_out = spin * red[3][0];
   }
+}
+
+// Shadows of block (0, 0) (Dw(0, 0) = w^0_0 (L - Gt) = 0 stays zero).
+__global__ void shadow00_kernel(int n, long ld, const double2 *L, const double2 *G, float *sh,
+                                long shz, long Tn) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int b = idx / n, c = idx % n;
+  const double2 l = L[b * ld + c], g = G[b * ld + c];
+  const long r0 = (long)b * Tn + c, pim = (long)n * Tn;
+  sh[r0] = (float)l.x;
+  sh[r0 + pim] = (float)l.y;
+  sh[shz + r0] = (float)g.x;
+  sh[shz + r0 + pim] = (float)g.y;
+}
+
+// Left factors of row i as real [2n][lda] matrices (column (2 s + p) n + b):
+// A1 from w^i_s (s^> - s^<)(i, s), A2 from s^<(i, s) and A2 + a_z from
+// s^>(i, s); row a holds the real part of the product (x.re, -x.im), row n + a
+// the imaginary part (x.im, x.re).
+__device__ __forceinline__ void put_cplx(float *A, int n, int lda, int a, long k0, double2 x) {
+  A[(long)a * lda + k0] = (float)x.x;
+  A[(long)a * lda + k0 + n] = (float)(-x.y);
+  A[(long)(n + a) * lda + k0] = (float)x.y;
+  A[(long)(n + a) * lda + k0 + n] = (float)x.x;
+}
+__global__ void aop_kernel(int n, int i, int Tcap, double dt, const double2 *S, int lda, float *A1,
+                           float *A2, long a_z) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int s = blockIdx.y, a = idx / n, b = idx % n;
+  const long nn = (long)n * n;
+  const double2 sl = S[(long)s * nn + idx], sg = S[((long)Tcap + s) * nn + idx];
+  const long k0 = (long)2 * s * n + b;
+  put_cplx(A1, n, lda, a, k0, scalez(trap_w(s, i, dt), subz(sg, sl)));
+  put_cplx(A2, n, lda, a, k0, sl);
+  put_cplx(A2 + a_z, n, lda, a, k0, sg);
+}
+
+// rhs of row i from the product slices: R_F(i, j) = -i h_HF F(i, j) + (sum of the
+// slices of both integrals), F = L (z = 0) and Gt (z = 1); O[k][z][j][p][a][c].
+__global__ void rhs_finish_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                                  const double2 *hHF, const double *O1, int ns1, const double *O2,
+                                  int ns2, int Tcap, double2 *RL, double2 *RG) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int j = blockIdx.y, a = idx / n, c = idx % n;
+  const long nn = (long)n * n, fb = blk(i, j, n, ld);
+  double2 hl = make_double2(0.0, 0.0), hg = hl;
+  for (int b = 0; b < n; ++b) {
+    const double2 hv = hHF[a * n + b];
+    cmla(hl, hv, L[fb + b * ld + c]);
+    cmla(hg, hv, G[fb + b * ld + c]);
+  }
+  const long zst = (long)Tcap * 2 * nn, kst = 2 * zst, e = (long)j * 2 * nn + idx;
+  double kr[2] = {0.0, 0.0}, ki[2] = {0.0, 0.0};
+  for (int z = 0; z < 2; ++z) {
+    for (int k = 0; k < ns1; ++k) {
+      kr[z] += O1[k * kst + z * zst + e];
+      ki[z] += O1[k * kst + z * zst + e + nn];
+    }
+    for (int k = 0; k < ns2; ++k) {
+      kr[z] += O2[k * kst + z * zst + e];
+      ki[z] += O2[k * kst + z * zst + e + nn];
+    }
+  }
+  RL[(long)j * nn + idx] = make_double2(hl.y + kr[0], -hl.x + ki[0]);
+  RG[(long)j * nn + idx] = make_double2(hg.y + kr[1], -hg.x + ki[1]);
 }
 
 __global__ void gather_diag_kernel(int n, long ld, const double2 *L, double2 *out) {
@@ -546,6 +655,12 @@ struct KbeRun {
   double dt, spin;
   bool corr;
   double2 *L, *G, *S, *T1, *R0L, *R0G, *R1L, *R1G, *hHF, *K, *part;
+  // split-TF32 collision integrals: shadows (null in FP64 mode), left factors, product slices
+  float *sh = nullptr, *aop = nullptr;
+  double *o1 = nullptr, *o2 = nullptr;
+  long shz = 0, Tn = 0, a_z = 0;
+  int lda = 0;
+  int *err = nullptr;
   const double *h, *V, *dv;
   double *E, *Nn;
   cudaStream_t s;
@@ -598,7 +713,32 @@ struct KbeRun {
     launches += 3;
     return FEDVR_OK;
   }
+  int rhs_tc(int i, double2 *RL, double2 *RG) {
+    const int nn = n * n, K = 2 * (i + 1) * n;
+    KBE_CK(ctx, mark(0));
+    float *A1 = aop, *A2 = aop + a_z;
+    aop_kernel<<<dim3((nn + 255) / 256, i + 1), 256, 0, s>>>(n, i, Tcap, dt, S, lda, A1, A2, a_z);
+    KBE_CK(ctx, cudaGetLastError());
+    // contraction slices: about two CTAs per SM, slices of at least 256 values
+    const long rt = ((long)(i + 1) * n + 127) / 128;
+    int nkz = (int)std::min(16L, std::max(1L, (304 + 2 * rt - 1) / (2 * rt)));
+    nkz = std::max(1, std::min(nkz, K / 256));
+    const int kz = ((K + nkz - 1) / nkz + 31) / 32 * 32, ns = (K + kz - 1) / kz;
+    const long oz = (long)Tcap * 2 * nn, okz = 2 * oz;
+    KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, sh, shz, A1, lda, 0, nkz, false, o1, oz, okz,
+                            err, s));
+    KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, sh + 2 * shz, 0, A2, lda, a_z, nkz, true, o2,
+                            oz, okz, err, s));
+    rhs_finish_kernel<<<dim3((nn + 255) / 256, i + 1), 256, 0, s>>>(n, i, ld, L, G, hHF, o1, ns,
+                                                                   o2, ns, Tcap, RL, RG);
+    KBE_CK(ctx, cudaGetLastError());
+    KBE_CK(ctx, mark(-1));
+    launches += 4;
+    cmac_coll += coll_cmacs(n, i, 0, i + 1, 0, corr);
+    return FEDVR_OK;
+  }
   int rhs(int i, double2 *RL, double2 *RG) {
+    if (sh && corr) return rhs_tc(i, RL, RG);
     CollArgs a{n, i, 0, Tcap, ld, dt, L, G, S, hHF, RL, RG, 0, corr ? 1 : 0, i + 1, 1, 0, part};
     KBE_CK(ctx, mark(0));
     KBE_CK(ctx, launch_collision(a, s, &launches));
@@ -621,7 +761,8 @@ struct KbeRun {
   int advance(int N, bool corrector) {
     const int nn = n * n;
     advance_kernel<<<dim3((nn + 255) / 256, N + 2), 256, 0, s>>>(
-        n, N, ld, L, G, R0L, R0G, corrector ? R1L : nullptr, corrector ? R1G : nullptr, dt);
+        n, N, ld, L, G, R0L, R0G, corrector ? R1L : nullptr, corrector ? R1G : nullptr, dt, sh,
+        shz, Tn);
     KBE_CK(ctx, cudaGetLastError());
     ++launches;
     return FEDVR_OK;
@@ -633,7 +774,7 @@ struct KbeRun {
 
 using namespace fedvr;
 
-int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
+int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born, int precision,
                         const double *rho0, const double *dv, double *rho_out, double *E_out,
                         double *N_out) {
   if (!ctx) return FEDVR_ERR_ARG;
@@ -647,18 +788,29 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   const int n = ctx->n;
   if (n > kKbeMaxN)
     return fail(ctx, FEDVR_ERR_ARG, "fedvr_kbe_propagate supports n_b <= %d (got %d)", kKbeMaxN, n);
+  if (precision != FEDVR_FP64 && precision != FEDVR_SPLIT_TF32)
+    return fail(ctx, FEDVR_ERR_ARG, "precision must be FEDVR_FP64 or FEDVR_SPLIT_TF32");
+  const bool split = precision == FEDVR_SPLIT_TF32 && second_born != 0;
   const int T = n_steps + 1;
   const long ld = (long)T * n;
+  if (split && 2 * ld * ld >= (1L << 31))
+    return fail(ctx, FEDVR_ERR_ARG, "split-TF32 propagation needs T n_b <= 32767 (got %ld)", ld);
   const size_t nn = (size_t)n * n, cz = sizeof(double2);
   const size_t two = (size_t)ld * (size_t)ld * cz;
+  const size_t shz = split ? 2 * (size_t)ld * (size_t)ld : 0;  // floats per shadow
+  const int lda = 2 * (int)ld;
+  const size_t aop_floats = split ? 3 * (size_t)2 * n * lda : 0;
+  const size_t o_doubles = split ? (size_t)16 * 2 * T * 2 * nn : 0;
   {
     size_t fre = 0, tot = 0;
     KBE_CK(ctx, cudaMemGetInfo(&fre, &tot));
-    const size_t held = ctx->k_L.bytes + ctx->k_G.bytes;
-    if (2 * two + (size_t)(16 * T + 8) * nn * cz > fre + held)
+    const size_t held = ctx->k_L.bytes + ctx->k_G.bytes + ctx->k_sh.bytes;
+    const size_t need = 2 * two + 3 * shz * sizeof(float) + aop_floats * sizeof(float) +
+                        2 * o_doubles * sizeof(double) + (size_t)(16 * T + 8) * nn * cz;
+    if (need > fre + held)
       return fail(ctx, FEDVR_ERR_ARG,
                   "two-time storage of %.2f GB (T = %d, n_b = %d) exceeds free device memory",
-                  2.0 * two / 1e9, T, n);
+                  need / 1e9, T, n);
   }
   cudaStream_t s = ctx->stream;
   ctx->kbe_T = 0;
@@ -670,6 +822,12 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   KBE_ENSURE(ctx, k_aux, (2 * nn + 2 * (size_t)T) * cz);
   KBE_ENSURE(ctx, k_out, (size_t)T * nn * cz + (size_t)T * n * sizeof(double));
   KBE_ENSURE(ctx, k_part, (size_t)coll_part_slots(T) * 2 * nn * cz);
+  if (split) {
+    KBE_ENSURE(ctx, k_sh, 3 * shz * sizeof(float));
+    KBE_ENSURE(ctx, k_aop, aop_floats * sizeof(float));
+    KBE_ENSURE(ctx, k_o, 2 * o_doubles * sizeof(double));
+    KBE_ENSURE(ctx, k_flag, sizeof(int));
+  }
   double2 *L = P<double2>(ctx->k_L), *G = P<double2>(ctx->k_G);
   double2 *R = P<double2>(ctx->k_R);
   double2 *aux = P<double2>(ctx->k_aux);
@@ -679,6 +837,11 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   KBE_CK(ctx, cudaMemsetAsync(L, 0, two, s));
   KBE_CK(ctx, cudaMemsetAsync(G, 0, two, s));
   KBE_CK(ctx, cudaMemsetAsync(ctx->k_S.ptr, 0, 2 * (size_t)T * nn * cz, s));
+  if (split) {
+    KBE_CK(ctx, cudaMemsetAsync(ctx->k_sh.ptr, 0, 3 * shz * sizeof(float), s));
+    KBE_CK(ctx, cudaMemsetAsync(ctx->k_aop.ptr, 0, aop_floats * sizeof(float), s));
+    KBE_CK(ctx, cudaMemsetAsync(ctx->k_flag.ptr, 0, sizeof(int), s));
+  }
   if (dv)
     KBE_CK(ctx, cudaMemcpyAsync(dv_d, dv, (size_t)T * n * sizeof(double), cudaMemcpyHostToDevice, s));
   if (rho0) {
@@ -690,6 +853,11 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   }
   g_from_l_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, ld, 0, L, G);
   KBE_CK(ctx, cudaGetLastError());
+  if (split) {
+    shadow00_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, ld, L, G, P<float>(ctx->k_sh),
+                                                                 (long)shz, ld);
+    KBE_CK(ctx, cudaGetLastError());
+  }
 
   KbeRun run;
   run.ctx = ctx;
@@ -710,6 +878,17 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   run.hHF = aux;
   run.K = aux + nn;
   run.part = P<double2>(ctx->k_part);
+  if (split) {
+    run.sh = P<float>(ctx->k_sh);
+    run.shz = (long)shz;
+    run.Tn = ld;
+    run.lda = lda;
+    run.aop = P<float>(ctx->k_aop);
+    run.a_z = (long)2 * n * lda;
+    run.o1 = P<double>(ctx->k_o);
+    run.o2 = run.o1 + o_doubles;
+    run.err = P<int>(ctx->k_flag);
+  }
   run.h = CP<double>(ctx->b_h);
   run.V = CP<double>(ctx->b_V);
   run.dv = dv ? dv_d : nullptr;
@@ -749,6 +928,14 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   if (N_out)
     KBE_CK(ctx, cudaMemcpyAsync(N_out, obs + T, T * sizeof(double), cudaMemcpyDeviceToHost, s));
   KBE_CK(ctx, cudaStreamSynchronize(s));
+  if (split) {
+    int flag = 0;
+    KBE_CK(ctx, cudaMemcpy(&flag, ctx->k_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      ctx->failed = true;
+      return fail(ctx, FEDVR_ERR_TIMEOUT, "a tensor-core wait of the collision products timed out");
+    }
+  }
   // stage times from the recorded events
   double ms[2] = {0, 0};
   for (auto &m : run.marks) {

@@ -138,6 +138,16 @@ cudaError_t vqv_tc(int n, int M, int ld, const float *V32, const float *g32, flo
                    int *err, cudaStream_t s);
 cudaError_t conv2_tc(int n, int M, const float *K32, const double *C, const double *I1,
                      double *I2, float *t1, float *t2, int *err, cudaStream_t s);
+// Real-time collision integrals of one time row (kbe.cu), two batched products
+// (z = 0, 1): O[k][z][j][p][a][c] = sum over the contraction slice k of
+// Sh_z[k'][j n + c] Aop_z[p n + a][k'] for j < ncols, k' < K; Sh_z at
+// Sh + z sh_z ([2T n][T n] FP32 planar two-time shadow, Tn = T n), Aop_z at
+// Aop + z a_z ([2n][lda]); tri: block-triangular shadow (rows of column j
+// need k' < 2n (j + 1)). The number of slices actually used is
+// ceil(K / kz) with kz = ceil(K / nkz) rounded up to 32.
+cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long sh_z,
+                        const float *Aop, int lda, long a_z, int nkz, bool tri, double *O,
+                        long o_z, long o_kz, int *err, cudaStream_t s);
 // Persistent launches over a device table of n_sys systems; prefix[n_sys + 1]
 // (device) holds the cumulative work items; Np_max/ld_max size the stages.
 cudaError_t exchange_tc_launch(const XSys *sys, const long *prefix, int n_sys, long items,

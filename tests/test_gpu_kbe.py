@@ -138,3 +138,51 @@ def test_argument_and_state_errors():
         big.kbe_propagate(0.1, 2, True, rho0=np.zeros((big.n_b, big.n_b), np.complex128))
     assert e.value.code == -1
     big.close()
+
+
+# Split-TF32 collision integrals: each product carries about 2^-21 of its
+# magnitude and a block of k FP32 accumulation steps up to k 2^-24 of the
+# partial sums (k = K / 8 MMA steps, K = 2 (i + 1) n_b <= 1.2e3 here: up to
+# 1e-5 of sum|terms|); K enters rho through dt per step, so over t <= 1.2 the
+# error in rho stays below about 1e-5 x |K| (~0.1) x t, relative to |rho| ~ 0.5
+# below 1e-5. N = sigma Tr rho is conserved only as far as Tr K_L(t, t) is
+# anti-Hermitian, i.e. to the same relative error.
+SPLIT_TOL = 1e-5
+
+
+@pytest.mark.parametrize("n_elem,order,half_width,steps", [
+    (4, 4, 10.0, 24),    # n_b = 15
+    (10, 4, 15.0, 12),   # n_b = 39
+    (15, 5, 20.0, 4),    # n_b = 74
+])
+def test_split_tf32_collisions_match_oracle(n_elem, order, half_width, steps):
+    _need_gpu()
+    from paper_0911_4348_gb300 import SPLIT_TF32
+    ctx, h, V, x = _setup(n_elem, order, half_width)
+    rho0 = _kicked_rho(h, x)
+    dt = 0.05
+    ref = O.kbe_propagate(h, V, 2.0, rho0, dt, steps)
+    got = ctx.kbe_propagate(dt, steps, True, rho0=rho0, precision=SPLIT_TF32)
+    err_rho = _rel(got["rho"], ref["rho"])
+    err_E = float(np.max(np.abs(got["E"] - ref["E"])))
+    print(f"split n_b={ctx.n_b}: rho {err_rho:.2e}, E {err_E:.2e}")
+    assert err_rho < SPLIT_TOL and err_E < SPLIT_TOL
+    assert np.max(np.abs(got["N"] - 2.0)) < 2.0 * SPLIT_TOL
+    T = steps + 1
+    for (i, j) in [(T - 1, 0), (T - 1, T - 1), (T // 2, T - 1)]:
+        assert _rel(ctx.kbe_block("L", i, j), ref["L"][i, j]) < SPLIT_TOL, (i, j)
+    ctx.close()
+
+
+def test_split_tf32_rejects_oversized_and_bad_precision():
+    _need_gpu()
+    from paper_0911_4348_gb300 import FedvrError, SPLIT_TF32
+    ctx, h, V, x = _setup(4, 4, 10.0)
+    rho0 = _kicked_rho(h, x)
+    with pytest.raises(FedvrError) as e:
+        ctx.kbe_propagate(0.05, 3, True, rho0=rho0, precision=3)
+    assert e.value.code == -1
+    with pytest.raises(FedvrError) as e:   # T n_b = 2201 * 15 > 32767
+        ctx.kbe_propagate(0.05, 2200, True, rho0=rho0, precision=SPLIT_TF32)
+    assert e.value.code == -1
+    ctx.close()
