@@ -690,7 +690,7 @@ def run_kbe(args, dist, rank, world, local):
         dist.barrier()
     clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0] or None)
     clocks.start()
-    dev_ms, coll_ms, sig_ms, launches, walls = 0.0, 0.0, 0.0, 0, []
+    dev_ms, coll_ms, sig_ms, prod_ms, launches, walls = 0.0, 0.0, 0.0, 0.0, 0, []
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -700,6 +700,7 @@ def run_kbe(args, dist, rank, world, local):
         dev_ms += st["ms"]
         coll_ms += st["collision_ms"]
         sig_ms += st["sigma_ms"]
+        prod_ms += st["products_ms"]
         launches += st["launches"]
     ck = clocks.stop()
     dev_s = max_over_ranks(dist, dev_ms / 1000.0)
@@ -712,12 +713,17 @@ def run_kbe(args, dist, rank, world, local):
                 "peak": N_SM * FP64_FLOP_PER_CLK_SM * 2070e6 / 1e12,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
     else:
-        # three TF32 products per algorithmic product on the tensor pipe (TF32 = half the BF16 rate)
-        pk = load_peaks().get("bf16_tflops")
-        roof = {"bound": "tensor", "kernel": "collision products (gemm_tf32x3_kernel, split TF32)",
-                "peak": (pk / 2.0) if pk else None,
-                "peak_source": "measured bf16 burst x 1/2 (tf32 dense rate), of measured"}
-    roof.update({"achieved": achieved / 1e12, "unit": "TFLOP/s", "traffic": None})
+        # the split products stream the FP32 shadows of the two-time matrices: HBM roofline
+        # on the bytes they read once, over the products' own CUDA-event time
+        hbm = load_peaks().get("hbm_gbs")
+        roof = {"bound": "hbm", "kernel": "collision products (gemm_tf32x3_kernel, split TF32)",
+                "achieved": st["products_bytes"] / (prod_ms / args.steps / 1000.0) / 1e9,
+                "peak": hbm, "unit": "GB/s", "peak_source": "measured copy bandwidth, of measured",
+                "products_ms_per_step": prod_ms / args.steps,
+                "collision_tflops_algorithmic": achieved / 1e12}
+    if prec == 0:
+        roof.update({"achieved": achieved / 1e12, "unit": "TFLOP/s"})
+    roof["traffic"] = None
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
     line = {"metric": "real-time KBE time steps/s (second Born, two-time)",
             "value": steps_total / dev_s, "unit": "time steps/s", "n_gpus": world,

@@ -503,10 +503,13 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
 int fedvr_kbe_get_block(const fedvr_ctx *ctx, int which, int i, int j, double *out);
 
 /* Timing of the last fedvr_kbe_propagate (CUDA events on the context's
- * stream): out[0] total ms, out[1] ms in the collision-integral kernels,
- * out[2] ms in the self-energy kernels, out[3] their algorithmic flops
- * (8 per complex multiply-add of the collision integrals), out[4] the
- * self-energy's, out[5] kernel launches. */
+ * stream), out[8]: out[0] total ms, out[1] ms in the collision-integral
+ * kernels, out[2] ms in the self-energy kernels, out[3] their algorithmic
+ * flops (8 per complex multiply-add of the collision integrals), out[4] the
+ * self-energy's, out[5] kernel launches, out[6] ms in the split-TF32
+ * collision products alone (0 in FP64 mode), out[7] the shadow bytes those
+ * products read once (L and Gt over the row's contraction, the triangle of
+ * the weighted L - Gt). */
 int fedvr_kbe_stats(const fedvr_ctx *ctx, double *out);
 
 #ifdef __cplusplus

@@ -334,10 +334,11 @@ class Context:
     def kbe_stats(self):
         """Timing of the last propagation: total, collision and self-energy ms,
         their algorithmic flops, and the kernel launches."""
-        out = np.zeros(6)
+        out = np.zeros(8)
         self._check(self._lib.fedvr_kbe_stats(self._h, _dptr(out)))
         return {"ms": out[0], "collision_ms": out[1], "sigma_ms": out[2],
-                "collision_flops": out[3], "sigma_flops": out[4], "launches": int(out[5])}
+                "collision_flops": out[3], "sigma_flops": out[4], "launches": int(out[5]),
+                "products_ms": out[6], "products_bytes": out[7]}
 
 
 def solve_2b_batched(contexts, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,

@@ -657,7 +657,7 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_coef32, &ctx->w_h16, &ctx->w_xrow, &ctx->w_dens,
                     &ctx->w_q4coef, &ctx->w_q4W, &ctx->w_q4w, &ctx->k_L, &ctx->k_G,
                     &ctx->k_S, &ctx->k_T1, &ctx->k_R, &ctx->k_aux, &ctx->k_out,
-                    &ctx->k_part, &ctx->k_sh, &ctx->k_aop, &ctx->k_o, &ctx->k_flag};
+                    &ctx->k_part, &ctx->k_sh, &ctx->k_aop, &ctx->k_o, &ctx->k_flag, &ctx->k_x};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);

@@ -72,10 +72,11 @@ struct fedvr_ctx {
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
   // last real-time propagation: time points and n (0: none), stage times and
-  // algorithmic flops (total ms, collision ms, self-energy ms, collision
-  // flops, self-energy flops, launches), events reused across calls
+  // algorithmic work (total ms, collision ms, self-energy ms, collision
+  // flops, self-energy flops, launches, ms and shadow bytes of the split
+  // collision products), events reused across calls
   int kbe_T = 0, kbe_n = 0;
-  double kbe_stats[6] = {0, 0, 0, 0, 0, 0};
+  double kbe_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> kbe_events;
 
   // named device buffers
@@ -89,7 +90,7 @@ struct fedvr_ctx {
       w_t1, w_t2, w_t3, w_dHF, w_part, w_red, w_tc, w_K32, w_tab, w_btab, w_c1p, w_coef32, w_h16,
       w_xrow, w_dens, w_q4coef, w_q4W, w_q4w;
   // real-time propagation: two-time L and Gt, self-energy row, scratch, outputs
-  fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part, k_sh, k_aop, k_o, k_flag;
+  fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part, k_sh, k_aop, k_o, k_flag, k_x;
 };
 
 namespace fedvr {

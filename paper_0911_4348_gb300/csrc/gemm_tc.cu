@@ -369,17 +369,17 @@ cudaError_t vqv_tc(int n, int M, int ld, const float *V32, const float *g32, flo
 cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long sh_z,
                         const float *Aop, int lda, long a_z, int nkz, bool tri, double *O,
                         long o_z, long o_kz, int *err, cudaStream_t s) {
-  if (!fits32(2L * Tn * Tn) || !fits32(sh_z) || !fits32(a_z) || !fits32(o_z) ||
+  if (!fits32(2L * Tn * Tn + 2L * Tn) || !fits32(sh_z) || !fits32(a_z) || !fits32(o_z) ||
       !fits32((long)2 * n * lda))
     return cudaErrorInvalidValue;
-  // O[slice][z][j][p][a][c] = sum_k Sh_z[k][j n + c] Aop_z[p n + a][k]: rows (j, c) grouped by
-  // j, columns (p, a); batch z = 0, 1
+  // O[slice][z][j][p][a][c] = sum_k Sh_z[j n + c][k] Aop_z[p n + a][k]: rows (j, c) grouped by
+  // j, columns (p, a); both operands read along k; batch z = 0, 1
   GemmArgs g = args0(ncols * n, 2 * n, K, err);
   g.G = n;
   g.nG = ncols;
   g.A = Sh;
-  g.a_sg = n;
-  g.a_sk = Tn;
+  g.a_sg = 2 * n * Tn;
+  g.a_sw = 2 * Tn;
   g.a_sz = (int)sh_z;
   g.B = Aop;
   g.b_s = lda;
@@ -395,7 +395,25 @@ cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long s
     g.nkz = (K + g.kz - 1) / g.kz;
   }
   g.k_tri = tri ? 2 * n : 0;
-  return gemm_tf32x3<float, float, double, true, false, false>(g, 2, s);
+  return gemm_tf32x3<float, float, double, false, false, false>(g, 2, s);
+}
+
+cudaError_t kbe_exchange_tc(int n, int ne, const float *Ap, const float *Bp, float *P, int *err,
+                            cudaStream_t s) {
+  const long n2 = (long)n * n;
+  if (2 * n > 128 || n2 > 4096 || !fits32(2 * n2 * n) || !fits32(4 * n2)) return cudaErrorInvalidValue;
+  // P_e[(b, k)][(p, a)] = sum_{(q, l)} Ap_e[(p, a)][(q, l)] Bp_e[(b, k)][(q, l)]
+  GemmArgs g = args0(2 * n, (int)n2, 2 * n, err);
+  g.A = Ap;
+  g.a_sw = 2 * n;
+  g.a_sz = (int)(4 * n2);
+  g.B = Bp;
+  g.b_s = 2 * n;
+  g.b_sz = (int)(2 * n2 * n);
+  g.O = P;
+  g.o_sc = 2 * n;
+  g.o_sz = (int)(2 * n2 * n);
+  return gemm_tf32x3<float, float, float, false, false, false>(g, ne, s);
 }
 
 cudaError_t conv2_tc(int n, int M, const float *K32, const double *C, const double *I1,

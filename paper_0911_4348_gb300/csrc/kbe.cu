@@ -28,14 +28,17 @@
 // Split-TF32 mode (precision 1): the two collision integrals of a time row run
 // as split-TF32 tensor-core products (gemm_tc.cu) over FP32 planar shadows of
 // L, Gt and the trapezoid-weighted L - Gt, written beside the FP64 matrices by
-// every advance: shadow w (0 L, 1 Gt, 2 Dw) holds row (2 s + p) n + b, column
-// j n + c = part p (re, im) of F(s, j)[b][c], and Dw(s, j) = w^j_s (L - Gt)(s, j)
+// every advance: shadow w (0 L, 1 Gt, 2 Dw) holds at row j n + c, column
+// (2 s + p) n + b (row length 2 T n, so the contraction index is contiguous)
+// part p (re, im) of F(s, j)[b][c], and Dw(s, j) = w^j_s (L - Gt)(s, j)
 // for s <= j, zero below (so the second integral is a plain product over
 // s <= j, block-triangular in (s, j)). The left factors of both integrals are
 // laid out as real [2n][2 T n] matrices (rows re/im of the output, columns
 // (s, p, b)) that turn each complex product into one real product. The
 // -i h_HF F term, the energy's K_L(t, t), the self-energy and the stepping stay
-// in FP64.
+// in FP64. In the same mode the exchange term's products
+// P^(b)_ak = sum_l g_al V_bl gb_lk of all entries of a row run as one batched
+// split-TF32 product (n_b <= 64) and only its k-sum stays in FP64.
 #include <algorithm>
 
 #include "common.cuh"
@@ -67,6 +70,10 @@ __device__ __forceinline__ double2 scalez(double s, double2 a) {
 }
 __host__ __device__ __forceinline__ long blk(int s, int j, int n, long ld) {
   return (long)s * n * ld + (long)j * n;
+}
+// element (s, j)[b][c], part p, of a planar two-time shadow (row j n + c, column (2 s + p) n + b)
+__device__ __forceinline__ long shi(int s, int j, int b, int c, int p, int n, long Tn) {
+  return ((long)j * n + c) * 2 * Tn + ((long)2 * s + p) * n + b;
 }
 // trapezoid weight of point s on [0, t_m]
 __device__ __forceinline__ double trap_w(int s, int m, double dt) {
@@ -259,6 +266,54 @@ __global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, co
   }
 }
 
+// Operands of the batched exchange product of row i, entry e = 2k + w:
+// Ap_e[(p, a)][(q, l)] the real form of g (rows re/im of the output, columns
+// re/im parts of the contraction), Bp_e[(b, k)][(q, l)] = part q of
+// V_bl gb_lk = -V_bl conj(H_kl).
+__global__ void xop_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                           const double *V, float *Ap, float *Bp) {
+  const int e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const long off = blk(i, kt, n, ld), n2 = (long)n * n;
+  const double2 *g = (w ? G : L) + off, *H = (w ? L : G) + off;
+  float *A = Ap + (long)e * 4 * n2, *B = Bp + (long)e * 2 * n2 * n;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n2 * n; q += (long)gridDim.x * blockDim.x) {
+    const int b = (int)(q / n2), k = (int)((q / n) % n), l = (int)(q % n);
+    const double2 h = H[k * ld + l];
+    const double v = V[b * n + l];
+    float *row = B + ((long)b * n + k) * 2 * n;
+    row[l] = (float)(-v * h.x);
+    row[n + l] = (float)(v * h.y);
+    if (q < n2) {  // Ap from g: element (a, l) = (k, l) here
+      const int a = (int)(q / n), ll = (int)(q % n);
+      const double2 x = g[a * ld + ll];
+      A[(long)a * 2 * n + ll] = (float)x.x;
+      A[(long)a * 2 * n + n + ll] = (float)(-x.y);
+      A[(long)(n + a) * 2 * n + ll] = (float)x.y;
+      A[(long)(n + a) * 2 * n + n + ll] = (float)x.x;
+    }
+  }
+}
+
+// k-sum of the exchange from the product: S_e[a][b] -= sum_k V_ak P_ak g_kb with
+// P_ak = P_e[(b, k)][(0, a)] + i P_e[(b, k)][(1, a)]; thread per (a, b).
+__global__ void xsum_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                            const double *V, const float *P, int Tcap, double2 *S) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int e = blockIdx.y, kt = e >> 1, w = e & 1, a = idx % n, b = idx / n;
+  const long off = blk(i, kt, n, ld), n2 = (long)n * n;
+  const double2 *g = (w ? G : L) + off;
+  const float *Pe = P + (long)e * 2 * n2 * n;
+  double2 x = make_double2(0.0, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const float *pr = Pe + ((long)b * n + k) * 2 * n;
+    const double2 pk = make_double2((double)pr[a], (double)pr[n + a]);
+    cmla(x, scalez(V[a * n + k], pk), g[k * ld + b]);
+  }
+  double2 *Se = S + ((long)w * Tcap + kt) * n2;
+  Se[a * n + b] = subz(Se[a * n + b], x);
+}
+
 struct CollArgs {
   int n, i, j0, Tcap;
   long ld;
@@ -284,7 +339,7 @@ constexpr int kCollKC = 16; // contraction index b per staged slice
 //   kind 1: w^i_s (s^> - s^<)(i, s) x [L(s, j), Gt(s, j)],  s = 0..i
 //   kind 2: [w^j_s s^<(i, s), w^j_s s^>(i, s)] x (L - Gt)(s, j), s = 0..j
 // times the 16-wide slices of b form a list of units; split k of S takes
-// units [U k / S, U (k+1) / S). Each unit stages its left factors X [rows][16]
+// units [U k / S, U (k+1) / S) (an empty range writes zeros). Each unit stages its left factors X [rows][16]
 // and right factors Y [16][n] in shared memory.
 __global__ void __launch_bounds__(256, 2) collision_kernel(CollArgs p) {
   extern __shared__ double2 cs[];
@@ -437,9 +492,9 @@ __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, co
     L[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vl);
     G[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vg);
     if (sh) {
-      const long pim = (long)n * Tn;  // from part re to part im
-      const long r0 = ((long)2 * (N + 1) * n + b) * Tn + (long)j * n + c;  // (N+1, j)[b][c]
-      const long m0 = ((long)2 * j * n + c) * Tn + (long)(N + 1) * n + b;  // (j, N+1)[c][b]
+      const long pim = n;  // from part re to part im
+      const long r0 = shi(N + 1, j, b, c, 0, n, Tn);  // (N+1, j)[b][c]
+      const long m0 = shi(j, N + 1, c, b, 0, n, Tn);  // (j, N+1)[c][b]
       sh[r0] = (float)vl.x;
       sh[r0 + pim] = (float)vl.y;
       sh[shz + r0] = (float)vg.x;
@@ -468,8 +523,8 @@ __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, co
     L[blk(N + 1, N + 1, n, ld) + b * ld + c] = v;
     G[blk(N + 1, N + 1, n, ld) + b * ld + c] = vg;
     if (sh) {
-      const long pim = (long)n * Tn;
-      const long r0 = ((long)2 * (N + 1) * n + b) * Tn + (long)(N + 1) * n + c;
+      const long pim = n;
+      const long r0 = shi(N + 1, N + 1, b, c, 0, n, Tn);
       sh[r0] = (float)v.x;
       sh[r0 + pim] = (float)v.y;
       sh[shz + r0] = (float)vg.x;
@@ -530,7 +585,7 @@ __global__ void shadow00_kernel(int n, long ld, const double2 *L, const double2 
   if (idx >= n * n) return;
   const int b = idx / n, c = idx % n;
   const double2 l = L[b * ld + c], g = G[b * ld + c];
-  const long r0 = (long)b * Tn + c, pim = (long)n * Tn;
+  const long r0 = shi(0, 0, b, c, 0, n, Tn), pim = n;
   sh[r0] = (float)l.x;
   sh[r0 + pim] = (float)l.y;
   sh[shz + r0] = (float)g.x;
@@ -604,7 +659,8 @@ size_t coll_smem(int n) {
   return (size_t)(2 * coll_rows(n) * kCollKC + 2 * kCollKC * n) * sizeof(double2);
 }
 // Partial-sum slots (splits x columns) a launch may use: the split count is
-// chosen so that a launch has about 4 CTAs per SM of a 152-SM GPU, at most 16.
+// chosen so that a launch has about 4 CTAs per SM of a 152-SM GPU, at most 128
+// (a single column, the energy's K_L(t, t), then still spreads over 128 CTAs).
 constexpr int kCollTargetCtas = 608;
 inline long coll_part_slots(int T) { return (long)kCollTargetCtas + T; }
 
@@ -612,7 +668,7 @@ cudaError_t launch_collision(CollArgs a, cudaStream_t s, long *launches) {
   a.rows = coll_rows(a.n);
   const int tiles = (a.n + a.rows - 1) / a.rows;
   const long ctas = (long)a.ncols * tiles;
-  a.splits = (int)std::max(1L, std::min(16L, (kCollTargetCtas + ctas - 1) / ctas));
+  a.splits = (int)std::max(1L, std::min(128L, (kCollTargetCtas + ctas - 1) / ctas));
   dim3 grid((unsigned)(a.ncols * a.splits), (unsigned)tiles);
   collision_kernel<<<grid, 256, coll_smem(a.n), s>>>(a);
   ++*launches;
@@ -657,6 +713,8 @@ struct KbeRun {
   double2 *L, *G, *S, *T1, *R0L, *R0G, *R1L, *R1G, *hHF, *K, *part;
   // split-TF32 collision integrals: shadows (null in FP64 mode), left factors, product slices
   float *sh = nullptr, *aop = nullptr;
+  // split-TF32 exchange products (null: FP64 exchange kernel)
+  float *xa = nullptr, *xb = nullptr, *xp = nullptr;
   double *o1 = nullptr, *o2 = nullptr;
   long shz = 0, Tn = 0, a_z = 0;
   int lda = 0;
@@ -666,7 +724,7 @@ struct KbeRun {
   cudaStream_t s;
   std::vector<cudaEvent_t> *ev;
   size_t ev_used = 0;
-  double cmac_coll = 0, cmac_sigma = 0;
+  double cmac_coll = 0, cmac_sigma = 0, bytes_tc = 0;
   long launches = 0;
   std::vector<std::pair<size_t, int>> marks;  // (event index, stage: 0 collision, 1 sigma)
 
@@ -699,7 +757,15 @@ struct KbeRun {
     direct_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1, spin, Tcap,
                                                              S);
     KBE_CK(ctx, cudaGetLastError());
-    if (n <= 16) {
+    if (xp) {
+      const long work = (long)nn * n;
+      const unsigned gx = (unsigned)std::min(64L, (work + 255) / 256);
+      xop_kernel<<<dim3(gx, ne), 256, 0, s>>>(n, i, ld, L, G, V, xa, xb);
+      KBE_CK(ctx, cudaGetLastError());
+      KBE_CK(ctx, kbe_exchange_tc(n, ne, xa, xb, xp, err, s));
+      xsum_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, xp, Tcap, S);
+      launches += 2;
+    } else if (n <= 16) {
       exchange_rows_kernel<<<dim3(n, ne), 256, (size_t)2 * nn * sizeof(double2), s>>>(
           n, i, ld, L, G, V, Tcap, S);
     } else {
@@ -725,10 +791,16 @@ struct KbeRun {
     nkz = std::max(1, std::min(nkz, K / 256));
     const int kz = ((K + nkz - 1) / nkz + 31) / 32 * 32, ns = (K + kz - 1) / kz;
     const long oz = (long)Tcap * 2 * nn, okz = 2 * oz;
+    KBE_CK(ctx, mark(2));
     KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, sh, shz, A1, lda, 0, nkz, false, o1, oz, okz,
                             err, s));
     KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, sh + 2 * shz, 0, A2, lda, a_z, nkz, true, o2,
                             oz, okz, err, s));
+    KBE_CK(ctx, mark(0));
+    // shadow bytes the two products read once: L and Gt rows j <= i over k < K, and the
+    // triangle s <= j of Dw
+    const double rows = (double)(i + 1) * n;
+    bytes_tc += 4.0 * (2.0 * rows * K + 0.5 * rows * K);
     rhs_finish_kernel<<<dim3((nn + 255) / 256, i + 1), 256, 0, s>>>(n, i, ld, L, G, hHF, o1, ns,
                                                                    o2, ns, Tcap, RL, RG);
     KBE_CK(ctx, cudaGetLastError());
@@ -801,12 +873,15 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   const int lda = 2 * (int)ld;
   const size_t aop_floats = split ? 3 * (size_t)2 * n * lda : 0;
   const size_t o_doubles = split ? (size_t)16 * 2 * T * 2 * nn : 0;
+  const bool split_x = split && n <= 64;  // exchange products on the tensor cores
+  const size_t x_floats = split_x ? (size_t)2 * T * (4 * nn + 4 * nn * n) : 0;
   {
     size_t fre = 0, tot = 0;
     KBE_CK(ctx, cudaMemGetInfo(&fre, &tot));
     const size_t held = ctx->k_L.bytes + ctx->k_G.bytes + ctx->k_sh.bytes;
     const size_t need = 2 * two + 3 * shz * sizeof(float) + aop_floats * sizeof(float) +
-                        2 * o_doubles * sizeof(double) + (size_t)(16 * T + 8) * nn * cz;
+                        2 * o_doubles * sizeof(double) + x_floats * sizeof(float) +
+                        (size_t)(16 * T + 8) * nn * cz;
     if (need > fre + held)
       return fail(ctx, FEDVR_ERR_ARG,
                   "two-time storage of %.2f GB (T = %d, n_b = %d) exceeds free device memory",
@@ -827,6 +902,7 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
     KBE_ENSURE(ctx, k_aop, aop_floats * sizeof(float));
     KBE_ENSURE(ctx, k_o, 2 * o_doubles * sizeof(double));
     KBE_ENSURE(ctx, k_flag, sizeof(int));
+    if (split_x) KBE_ENSURE(ctx, k_x, x_floats * sizeof(float));
   }
   double2 *L = P<double2>(ctx->k_L), *G = P<double2>(ctx->k_G);
   double2 *R = P<double2>(ctx->k_R);
@@ -888,6 +964,11 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
     run.o1 = P<double>(ctx->k_o);
     run.o2 = run.o1 + o_doubles;
     run.err = P<int>(ctx->k_flag);
+    if (split_x) {
+      run.xa = P<float>(ctx->k_x);
+      run.xb = run.xa + (size_t)2 * T * 4 * nn;
+      run.xp = run.xb + (size_t)2 * T * 2 * nn * n;
+    }
   }
   run.h = CP<double>(ctx->b_h);
   run.V = CP<double>(ctx->b_V);
@@ -937,7 +1018,7 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
     }
   }
   // stage times from the recorded events
-  double ms[2] = {0, 0};
+  double ms[3] = {0, 0, 0};
   for (auto &m : run.marks) {
     float f = 0.f;
     KBE_CK(ctx, cudaEventElapsedTime(&f, (*run.ev)[m.first], (*run.ev)[m.first + 1]));
@@ -946,8 +1027,10 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   float tot = 0.f;
   KBE_CK(ctx, cudaEventElapsedTime(&tot, (*run.ev)[0], (*run.ev)[run.ev_used - 1]));
   ctx->kbe_stats[0] = tot;
-  ctx->kbe_stats[1] = ms[0];
+  ctx->kbe_stats[1] = ms[0] + ms[2];
   ctx->kbe_stats[2] = ms[1];
+  ctx->kbe_stats[6] = ms[2];
+  ctx->kbe_stats[7] = run.bytes_tc;
   ctx->kbe_stats[3] = 8.0 * run.cmac_coll;
   ctx->kbe_stats[4] = 8.0 * run.cmac_sigma;
   ctx->kbe_stats[5] = (double)run.launches;
@@ -978,6 +1061,6 @@ int fedvr_kbe_stats(const fedvr_ctx *cctx, double *out) {
   if (!cctx || !out) return FEDVR_ERR_ARG;
   if (cctx->kbe_T == 0)
     return fail(const_cast<fedvr_ctx *>(cctx), FEDVR_ERR_STATE, "no completed fedvr_kbe_propagate");
-  for (int q = 0; q < 6; ++q) out[q] = cctx->kbe_stats[q];
+  for (int q = 0; q < 8; ++q) out[q] = cctx->kbe_stats[q];
   return FEDVR_OK;
 }
