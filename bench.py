@@ -691,6 +691,7 @@ def run_kbe(args, dist, rank, world, local):
     clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0] or None)
     clocks.start()
     dev_ms, coll_ms, sig_ms, prod_ms, launches, walls = 0.0, 0.0, 0.0, 0.0, 0, []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -702,6 +703,7 @@ def run_kbe(args, dist, rank, world, local):
         sig_ms += st["sigma_ms"]
         prod_ms += st["products_ms"]
         launches += st["launches"]
+    torch.cuda.nvtx.range_pop()
     ck = clocks.stop()
     dev_s = max_over_ranks(dist, dev_ms / 1000.0)
     wall_s = max_over_ranks(dist, float(sum(walls)))
