@@ -4,7 +4,7 @@
 // I1_i = sum_j B_ij g_j with B_ij = c1 A_k + c2 A_{k+1} (linear interpolation of
 // Sigma^corr at the lag tau_i - tau_j, anti-periodic beyond 0, trapezoid weight
 // folded into c1, c2) and B_ii = dHF - wm_i A_0 + wp_i A_{M-1} (split trapezoid
-// at the jump). One block owns a 64x64 tile of one I1_i and streams over j.
+// at the jump). One block owns a tile of whole rows of one I1_i and streams over j.
 //
 // I2 is evaluated with its left index in the HF eigenbasis, where g^0 is
 // diagonal (g^0 multiplies I1 from the left, so the right index needs no
@@ -19,7 +19,6 @@
 namespace fedvr {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
 
 // Rows and weights of the Sigma^corr combination B_ij of one (i, j) entry:
 // linear interpolation (ConvCoef: rows k, k + 1) or the cubic of the
@@ -56,72 +55,87 @@ __device__ __forceinline__ CoefView coef_view(const ConvCoef4 &cf, int M) {
   return v;
 }
 
+// First convolution, FP64. CTA (row tile, i): its rows x n outputs of I1_i are
+// spread over the 256 threads at up to kC1Q per thread (output o = tid + 256 q,
+// row a0 + o / n, column o % n), so no output is padded; for each j and each
+// 16-wide slice of c it stages B_ij[a][c] (the interpolated Sigma^corr, built
+// from up to four rows) [rows][16] and g_j[c][b] [16][n] in shared memory. Each
+// output adds its terms in the order j, c.
+constexpr int kC1Q = 8, kC1K = 16;
 template <typename Coef>
-__global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M,
+__global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M, int rows,
                                                          const Coef *__restrict__ coef,
                                                          const double *__restrict__ dHF,
                                                          const double *__restrict__ A,
                                                          const double *__restrict__ G,
                                                          double *__restrict__ I1) {
-  const int i = blockIdx.z;
-  const int a0 = blockIdx.y * BM, b0 = blockIdx.x * BN;
+  extern __shared__ double c1s[];
+  double *Xs = c1s, *Ys = c1s + rows * kC1K;
+  const int i = blockIdx.y, a0 = blockIdx.x * rows;
+  const int nr = min(rows, n - a0), nout = nr * n;
   const long nn = (long)n * n;
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  const int tid = threadIdx.x;
+  double acc[kC1Q];
+  int xo[kC1Q], yo[kC1Q];
+  int nq = 0;
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+  for (int q = 0; q < kC1Q; ++q) {
+    const int o = tid + 256 * q;
+    acc[q] = 0.0;
+    xo[q] = o < nout ? (o / n) * kC1K : 0;
+    yo[q] = o < nout ? o % n : 0;
+    nq += o < nout ? 1 : 0;
+  }
   for (int j = 0; j < M; ++j) {
     const CoefView cv = coef_view(coef[(long)i * M + j], M);
     const double *g = G + (long)j * nn;
-    for (int c0 = 0; c0 < n; c0 += BK) {
-      for (int e = threadIdx.x; e < BM * BK; e += 256) {
-        int cc = e % BK, aa = e / BK;
-        int a = a0 + aa, c = c0 + cc;
+    for (int c0 = 0; c0 < n; c0 += kC1K) {
+      const int nc = min(kC1K, n - c0);
+      for (int e = tid; e < nr * kC1K; e += 256) {
+        const int aa = e / kC1K, cc = e % kC1K;
         double v = 0.0;
-        if (a < n && c < n) {
-          long off = (long)a * n + c;
+        if (cc < nc) {
+          const long off = (long)(a0 + aa) * n + c0 + cc;
           v = cv.c[0] * A[(long)cv.r[0] * nn + off] + cv.c[1] * A[(long)cv.r[1] * nn + off];
           if (cv.np == 4)
             v += cv.c[2] * A[(long)cv.r[2] * nn + off] + cv.c[3] * A[(long)cv.r[3] * nn + off];
           if (cv.diag) v += dHF[off];
         }
-        As[cc][aa] = v;
+        Xs[e] = v;
       }
-      for (int e = threadIdx.x; e < BN * BK; e += 256) {
-        int bb = e % BN, cc = e / BN;
-        int b = b0 + bb, c = c0 + cc;
-        Bs[cc][bb] = (b < n && c < n) ? g[(long)c * n + b] : 0.0;
-      }
+      for (int e = tid; e < nc * n; e += 256) Ys[e] = g[(long)c0 * n + e];
       __syncthreads();
+#pragma unroll 2
+      for (int cc = 0; cc < nc; ++cc) {
 #pragma unroll
-      for (int cc = 0; cc < BK; ++cc) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) av[r] = As[cc][ty + 16 * r];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bv[q] = Bs[cc][tx + 16 * q];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+        for (int q = 0; q < kC1Q; ++q)
+          if (q < nq) acc[q] = fma(Xs[xo[q] + cc], Ys[cc * n + yo[q]], acc[q]);
       }
       __syncthreads();
     }
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    int a = a0 + ty + 16 * r;
-    if (a >= n) continue;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int b = b0 + tx + 16 * q;
-      if (b < n) I1[(long)i * nn + (long)a * n + b] = acc[r][q];
-    }
+  for (int q = 0; q < kC1Q; ++q) {
+    if (q >= nq) break;
+    const int o = tid + 256 * q;
+    I1[(long)i * nn + (long)(a0 + o / n) * n + o % n] = acc[q];
   }
+}
+
+inline int c1_rows(int n) { return n < 256 * kC1Q / n ? n : 256 * kC1Q / n; }
+
+template <typename Coef>
+cudaError_t launch_conv1_fp64(int n, int M, const Coef *coef, const double *dHF, const double *A,
+                              const double *G, double *I1, cudaStream_t s) {
+  const int rows = c1_rows(n);
+  if (rows < 1) return cudaErrorInvalidValue;
+  const size_t sm = (size_t)(rows * kC1K + kC1K * n) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(conv1_fp64_kernel<Coef>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((n + rows - 1) / rows), (unsigned)M);
+  conv1_fp64_kernel<Coef><<<grid, 256, sm, s>>>(n, M, rows, coef, dHF, A, G, I1);
+  return cudaGetLastError();
 }
 
 __device__ __forceinline__ double phi_eig(double x, double y, double beta) {
@@ -334,17 +348,13 @@ cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, con
 
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
                        const double *G, double *I1, cudaStream_t s) {
-  dim3 grid((n + BN - 1) / BN, (n + BM - 1) / BM, M);
-  conv1_fp64_kernel<ConvCoef><<<grid, 256, 0, s>>>(n, M, coef, dHF, A, G, I1);
-  return cudaGetLastError();
+  return launch_conv1_fp64<ConvCoef>(n, M, coef, dHF, A, G, I1, s);
 }
 
 cudaError_t conv1_fp64_q4(int n, int M, const ConvCoef4 *coef, const double *dHF,
                           const double *A, const double *G, double *I1, cudaStream_t s) {
   if (M < 4) return cudaErrorInvalidValue;
-  dim3 grid((n + BN - 1) / BN, (n + BM - 1) / BM, M);
-  conv1_fp64_kernel<ConvCoef4><<<grid, 256, 0, s>>>(n, M, coef, dHF, A, G, I1);
-  return cudaGetLastError();
+  return launch_conv1_fp64<ConvCoef4>(n, M, coef, dHF, A, G, I1, s);
 }
 
 cudaError_t launch_quad4_tables(int M, double beta, const double *tau, ConvCoef4 *coef,

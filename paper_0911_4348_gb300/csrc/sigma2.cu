@@ -23,90 +23,80 @@ __global__ void polarisation_kernel(int n, int M, const double *__restrict__ G,
   Q[idx] = G[idx] * G[(M - 1 - j) * nn + e];
 }
 
-constexpr int TA = 64, TK = 64, TL = 16;
+// One CTA per (mesh point j, column b, tile of rows a >= b): the tile's
+// (a, k) pairs (rows x n) are spread over the 256 threads at up to kXQ per
+// thread (pair o = tid + 256 q: row a0 + o / n, column o % n), so neither rows
+// nor columns are padded. P_ak = sum_l (g_al V_bl) gb_lk accumulates over
+// 16-wide slices of l staged in shared memory ([rows][16] and [16][n]); then
+// v_ak = V_ak g_kb P_ak is written to shared memory and summed over k in k
+// order (segments of k, then the segments in order).
+constexpr int kXQ = 8, kXL = 16;
+inline int xrows(int n) { return n < 256 * kXQ / n ? n : 256 * kXQ / n; }
 
-// One block: mesh point j, column b, 64 rows a. Loops over 64-wide k blocks;
-// P tile (a x k) accumulates over l with A = g(a, l) * V(b, l) and B = gb(l, k);
-// the epilogue folds sum_k V_ak g_kb P_ak into per-row partial sums.
-__global__ void __launch_bounds__(256) exchange_fp64_kernel(int n, int M, double spin,
+__global__ void __launch_bounds__(256) exchange_fp64_kernel(int n, int M, int rows, double spin,
                                                             const double *__restrict__ V,
                                                             const double *__restrict__ G,
                                                             const double *__restrict__ W,
                                                             double *__restrict__ Sigma) {
-  const int j = blockIdx.z, b = blockIdx.y;
-  const int a0 = blockIdx.x * TA;
-  if (a0 + TA <= b) return;  // whole block above the diagonal
+  extern __shared__ double xsm[];
+  double *Xs = xsm, *Ys = Xs + rows * kXL, *Vs = Ys + kXL * n, *Ps = Vs + rows * n;
+  const int j = blockIdx.z, b = blockIdx.y, a0 = b + blockIdx.x * rows;
+  if (a0 >= n) return;  // past the last row of this column
+  const int nr = min(rows, n - a0), nout = nr * n, tid = threadIdx.x;
   const long nn = (long)n * n;
   const double *g = G + (long)j * nn;
   const double *gb = G + (long)(M - 1 - j) * nn;
-  __shared__ double As[TL][TA + 1];
-  __shared__ double Bs[TL][TK + 1];
-  __shared__ double Vb[TL];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double xacc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int k0 = 0; k0 < n; k0 += TK) {
-    double acc[4][4];
+  double acc[kXQ];
+  int xo[kXQ], yo[kXQ];
+  int nq = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
-    for (int l0 = 0; l0 < n; l0 += TL) {
-      if (threadIdx.x < TL) {
-        int l = l0 + threadIdx.x;
-        Vb[threadIdx.x] = (l < n) ? V[(long)b * n + l] : 0.0;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < TA * TL; e += 256) {
-        int ll = e % TL, aa = e / TL;
-        int a = a0 + aa, l = l0 + ll;
-        As[ll][aa] = (a < n && l < n) ? g[(long)a * n + l] * Vb[ll] : 0.0;
-      }
-      for (int e = threadIdx.x; e < TK * TL; e += 256) {
-        int kk = e % TK, ll = e / TK;
-        int k = k0 + kk, l = l0 + ll;
-        Bs[ll][kk] = (k < n && l < n) ? gb[(long)l * n + k] : 0.0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int ll = 0; ll < TL; ++ll) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[ll][ty + 16 * i];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bv[q] = Bs[ll][tx + 16 * q];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[i][q] = fma(av[i], bv[q], acc[i][q]);
-      }
-      __syncthreads();
-    }
-    // epilogue for this k block: s_i = sum_q V[a_i][k_q] g[k_q][b] P[a_i][k_q]
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int a = a0 + ty + 16 * i;
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int k = k0 + tx + 16 * q;
-        if (a < n && k < n) s = fma(V[(long)a * n + k] * g[(long)k * n + b], acc[i][q], s);
-      }
-      // reduce over the 16 lanes (tx) that share row a
-      for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      xacc[i] += s;
-    }
+  for (int q = 0; q < kXQ; ++q) {
+    const int o = tid + 256 * q;
+    acc[q] = 0.0;
+    xo[q] = o < nout ? (o / n) * kXL : 0;
+    yo[q] = o < nout ? o % n : 0;
+    nq += o < nout ? 1 : 0;
   }
-  if (tx == 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int a = a0 + ty + 16 * i;
-      if (a < n && a >= b) {
-        long ab = (long)a * n + b;
-        double v = spin * g[ab] * W[(long)j * nn + ab] - xacc[i];
-        Sigma[(long)j * nn + ab] = v;
-        Sigma[(long)j * nn + (long)b * n + a] = v;
-      }
+  for (int l0 = 0; l0 < n; l0 += kXL) {
+    const int nl = min(kXL, n - l0);
+    for (int e = tid; e < nr * kXL; e += 256) {
+      const int r = e / kXL, ll = e % kXL;
+      Xs[e] = ll < nl ? g[(long)(a0 + r) * n + l0 + ll] * V[(long)b * n + l0 + ll] : 0.0;
     }
+    for (int e = tid; e < nl * n; e += 256) Ys[e] = gb[(long)l0 * n + e];
+    __syncthreads();
+#pragma unroll 2
+    for (int ll = 0; ll < nl; ++ll) {
+#pragma unroll
+      for (int q = 0; q < kXQ; ++q)
+        if (q < nq) acc[q] = fma(Xs[xo[q] + ll], Ys[ll * n + yo[q]], acc[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kXQ; ++q) {
+    if (q >= nq) break;
+    const int o = tid + 256 * q, a = a0 + o / n, k = o % n;
+    Vs[o] = V[(long)a * n + k] * g[(long)k * n + b] * acc[q];
+  }
+  __syncthreads();
+  // row sums over k: segments of seg values by nseg threads per row, then the segments
+  const int nseg = min(n, 256 / nr), seg = (n + nseg - 1) / nseg;
+  if (tid < nr * nseg) {
+    const int r = tid / nseg, sgi = tid % nseg, k1 = min(n, (sgi + 1) * seg);
+    double p = 0.0;
+    for (int k = sgi * seg; k < k1; ++k) p += Vs[r * n + k];
+    Ps[tid] = p;
+  }
+  __syncthreads();
+  if (tid < nr) {
+    double x = 0.0;
+    for (int sgi = 0; sgi < nseg; ++sgi) x += Ps[tid * nseg + sgi];
+    const int a = a0 + tid;
+    const long ab = (long)a * n + b;
+    const double v = spin * g[ab] * W[(long)j * nn + ab] - x;
+    Sigma[(long)j * nn + ab] = v;
+    Sigma[(long)j * nn + (long)b * n + a] = v;
   }
 }
 
@@ -124,8 +114,14 @@ cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double
   if (e != cudaSuccess) return e;
   e = dgemm(false, false, n, n, n, 1.0, V, n, 0, T1, n, nn, nullptr, 0, 0.0, W, n, nn, M, s);
   if (e != cudaSuccess) return e;
-  dim3 grid((n + TA - 1) / TA, n, M);
-  exchange_fp64_kernel<<<grid, 256, 0, s>>>(n, M, spin, V, G, W, Sigma);
+  const int rows = xrows(n);
+  if (rows < 1) return cudaErrorInvalidValue;
+  const size_t sm = (size_t)(rows * kXL + kXL * n + rows * n + 256) * sizeof(double);
+  e = cudaFuncSetAttribute(exchange_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((n + rows - 1) / rows), (unsigned)n, (unsigned)M);
+  exchange_fp64_kernel<<<grid, 256, sm, s>>>(n, M, rows, spin, V, G, W, Sigma);
   return cudaGetLastError();
 }
 
