@@ -473,7 +473,7 @@ int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds);
  * split-TF32 tensor-core products (three TF32 products per product, FP32
  * accumulation, about 2^-21 relative per product) over FP32 copies of L, Gt
  * and the weighted L - Gt kept beside the FP64 matrices (3 x 8 (T n_b)^2
- * more bytes; needs T n_b <= 32767); the -i h_HF F term, the energy, the
+ * more bytes; needs T n_b <= 32750); the -i h_HF F term, the energy, the
  * self-energy and the stepping stay FP64.
  *
  * rho0: host [n_b][n_b] complex (interleaved re, im; 16 bytes per entry), or

@@ -32,6 +32,8 @@
 // issues the MMAs. Two stages handed over with mbarriers (full: one arrival per
 // producer warp; empty: MMA commit); every wait is bounded and a timeout sets
 // the error flag.
+#include <type_traits>
+
 #include "common.cuh"
 #include "tc.cuh"
 #include "tc_sys.cuh"
@@ -55,6 +57,7 @@ struct GemmArgs {
   int *err;
   int kz, nkz, k_tri;  // contraction slices and block-triangular limit (see above)
   long o_kz;
+  int vec;  // FP32 operands read along k with 16-byte loads (alignment checked on the host)
 };
 
 // Split x and store the pair at element (r, k) of a 128B-swizzled K-major tile
@@ -65,6 +68,19 @@ __device__ __forceinline__ void put1(uint8_t *t, uint32_t lo_off, int r, int k, 
   const uint32_t off = tc::sw128_offset(r, k >> 2) + (uint32_t)(k & 3) * 4u;
   *reinterpret_cast<float *>(t + off) = hi;
   *reinterpret_cast<float *>(t + lo_off + off) = lo;
+}
+
+// Four consecutive k values from row offset off of an FP32 operand (zeros
+// beyond kend or for a dead row); 16-byte load when all four lie before kend.
+__device__ __forceinline__ float4 ld4(const float *X, long off, int k, int kend, bool live) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!live) return v;
+  if (k + 4 <= kend) return *reinterpret_cast<const float4 *>(X + off + k);
+  if (k < kend) v.x = X[off + k];
+  if (k + 1 < kend) v.y = X[off + k + 1];
+  if (k + 2 < kend) v.z = X[off + k + 2];
+  if (k + 3 < kend) v.w = X[off + k + 3];
+  return v;
 }
 
 // Split four consecutive k values (k0 a multiple of 4) of row r and store them
@@ -121,98 +137,153 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
   bool issued = false;
 
   if (warp >= 4 && warp < 12) {
-    // ---- producers ----
-    const int pt = tid - 128;
-    const TA *A = reinterpret_cast<const TA *>(p.A) + (long)z * p.a_sz;
-    const TA *A2 = reinterpret_cast<const TA *>(p.A2);
-    const TB *B = reinterpret_cast<const TB *>(p.B) + (long)z * p.b_sz;
-    // A rows of this thread: MC 16 consecutive rows (one k per lane), KC one row
-    const int ra = A_MC ? (pt >> 5) * 16 : (pt >> 1);
-    const int nra = A_MC ? 16 : 1;
-    int aoff[16], aoff2[16];
-    bool alive[16];
-    {
-      int r = row0 + ra;
-      int g = r / p.G, w = r % p.G;
+    bool vec_done = false;
+    if constexpr (!A_MC && !B_MC && std::is_same<TA, float>::value &&
+                  std::is_same<TB, float>::value) {
+      if (p.vec) {
+        // ---- producers, FP32 operands along k: a 32-value chunk row is 8 float4, eight
+        // lanes cover one 128-byte row segment (A: 4 float4 per thread, B: up to 8) ----
+        vec_done = true;
+        const int pt = tid - 128;
+        const float *A = reinterpret_cast<const float *>(p.A) + (long)z * p.a_sz;
+        const float *B = reinterpret_cast<const float *>(p.B) + (long)z * p.b_sz;
+        long aoff4[4], boff4[8];
+        bool alive4[4], blive4[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (i < nra) {
-          alive[i] = r < p.R;
-          aoff[i] = alive[i] ? g * p.a_sg + w * (A_MC ? 1 : p.a_sw) : 0;
-          aoff2[i] = (MUL2 && alive[i]) ? (p.nG - 1 - g) * p.a_sg + w : 0;
-          ++r;
-          if (++w == p.G) {
-            w = 0;
-            ++g;
+        for (int q = 0; q < 4; ++q) {
+          const int r = row0 + ((pt + 256 * q) >> 3);
+          alive4[q] = r < p.R;
+          aoff4[q] = alive4[q] ? (long)(r / p.G) * p.a_sg + (long)(r % p.G) * p.a_sw : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = (pt + 256 * q) >> 3;
+          blive4[q] = c < Nt && col0 + c < p.N;
+          boff4[q] = blive4[q] ? (long)(col0 + c) * p.b_s : 0;
+        }
+        const int c4 = (pt & 7) * 4;
+        for (int kc = 0; kc < KC; ++kc) {
+          const int k = kbeg + kc * 32 + c4;
+          float4 av[4], bv[8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) av[q] = ld4(A, aoff4[q], k, kend, alive4[q]);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) bv[q] = ld4(B, boff4[q], k, kend, blive4[q]);
+          const int s = kc & 1;
+          const uint32_t use = kc >> 1;
+          if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+            *abort_flag = 1;
+            break;
           }
-        } else {
-          alive[i] = false;
-          aoff[i] = aoff2[i] = 0;
+          uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            put4(st, kTileA, (pt + 256 * q) >> 3, c4, reinterpret_cast<const float *>(&av[q]));
+          uint8_t *sb = st + 2 * kTileA;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int c = (pt + 256 * q) >> 3;
+            if (c < Nt) put4(sb, tileB, c, c4, reinterpret_cast<const float *>(&bv[q]));
+          }
+          tc::fence_smem_to_async();
+          tc::warp_arrive(&full[s]);
         }
       }
     }
-    // B columns of this thread: MC 32 consecutive local columns (one k per lane),
-    // KC one local column
-    const int cb = B_MC ? (pt >> 5) * 32 : pt;
-    for (int kc = 0; kc < KC; ++kc) {
-      const int k0 = kbeg + kc * 32;
-      float av[16], bv[32];
-      if (A_MC) {
-        const int k = k0 + lane;
+    if (!vec_done) {
+      // ---- producers ----
+      const int pt = tid - 128;
+      const TA *A = reinterpret_cast<const TA *>(p.A) + (long)z * p.a_sz;
+      const TA *A2 = reinterpret_cast<const TA *>(p.A2);
+      const TB *B = reinterpret_cast<const TB *>(p.B) + (long)z * p.b_sz;
+      // A rows of this thread: MC 16 consecutive rows (one k per lane), KC one row
+      const int ra = A_MC ? (pt >> 5) * 16 : (pt >> 1);
+      const int nra = A_MC ? 16 : 1;
+      int aoff[16], aoff2[16];
+      bool alive[16];
+      {
+        int r = row0 + ra;
+        int g = r / p.G, w = r % p.G;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          float x = 0.f;
-          if (alive[i] && k < kend) {
-            x = (float)A[aoff[i] + k * p.a_sk];
-            if (MUL2) x *= (float)A2[aoff2[i] + k * p.a_sk];
+          if (i < nra) {
+            alive[i] = r < p.R;
+            aoff[i] = alive[i] ? g * p.a_sg + w * (A_MC ? 1 : p.a_sw) : 0;
+            aoff2[i] = (MUL2 && alive[i]) ? (p.nG - 1 - g) * p.a_sg + w : 0;
+            ++r;
+            if (++w == p.G) {
+              w = 0;
+              ++g;
+            }
+          } else {
+            alive[i] = false;
+            aoff[i] = aoff2[i] = 0;
           }
-          av[i] = x;
         }
-      } else {
-        const int kb = k0 + (pt & 1) * 16;
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          av[i] = (alive[0] && kb + i < kend) ? (float)A[aoff[0] + kb + i] : 0.f;
       }
-      if (B_MC) {
-        const int k = k0 + lane;
+      // B columns of this thread: MC 32 consecutive local columns (one k per lane),
+      // KC one local column
+      const int cb = B_MC ? (pt >> 5) * 32 : pt;
+      for (int kc = 0; kc < KC; ++kc) {
+        const int k0 = kbeg + kc * 32;
+        float av[16], bv[32];
+        if (A_MC) {
+          const int k = k0 + lane;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int c = col0 + cb + i;
-          bv[i] = (cb + i < Nt && c < p.N && k < kend) ? (float)B[k * p.b_s + c] : 0.f;
+          for (int i = 0; i < 16; ++i) {
+            float x = 0.f;
+            if (alive[i] && k < kend) {
+              x = (float)A[aoff[i] + k * p.a_sk];
+              if (MUL2) x *= (float)A2[aoff2[i] + k * p.a_sk];
+            }
+            av[i] = x;
+          }
+        } else {
+          const int kb = k0 + (pt & 1) * 16;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            av[i] = (alive[0] && kb + i < kend) ? (float)A[aoff[0] + kb + i] : 0.f;
         }
-      } else {
-        const int c = col0 + cb;
-        const bool ok = cb < Nt && c < p.N;
+        if (B_MC) {
+          const int k = k0 + lane;
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          bv[i] = (ok && k0 + i < kend) ? (float)B[c * p.b_s + k0 + i] : 0.f;
+          for (int i = 0; i < 32; ++i) {
+            const int c = col0 + cb + i;
+            bv[i] = (cb + i < Nt && c < p.N && k < kend) ? (float)B[k * p.b_s + c] : 0.f;
+          }
+        } else {
+          const int c = col0 + cb;
+          const bool ok = cb < Nt && c < p.N;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            bv[i] = (ok && k0 + i < kend) ? (float)B[c * p.b_s + k0 + i] : 0.f;
+        }
+        const int s = kc & 1;
+        const uint32_t use = kc >> 1;
+        if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+          *abort_flag = 1;
+          break;
+        }
+        uint8_t *st = smem + s * stage_bytes;
+        if (A_MC) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) put1(st, kTileA, ra + i, lane, av[i]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) put4(st, kTileA, ra, (pt & 1) * 16 + 4 * q, av + 4 * q);
+        }
+        uint8_t *sb = st + 2 * kTileA;
+        if (B_MC) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (cb + i < Nt) put1(sb, tileB, cb + i, lane, bv[i]);
+        } else if (cb < Nt) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) put4(sb, tileB, cb, 4 * q, bv + 4 * q);
+        }
+        tc::fence_smem_to_async();
+        tc::warp_arrive(&full[s]);
       }
-      const int s = kc & 1;
-      const uint32_t use = kc >> 1;
-      if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
-        *abort_flag = 1;
-        break;
-      }
-      uint8_t *st = smem + s * stage_bytes;
-      if (A_MC) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) put1(st, kTileA, ra + i, lane, av[i]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) put4(st, kTileA, ra, (pt & 1) * 16 + 4 * q, av + 4 * q);
-      }
-      uint8_t *sb = st + 2 * kTileA;
-      if (B_MC) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (cb + i < Nt) put1(sb, tileB, cb + i, lane, bv[i]);
-      } else if (cb < Nt) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) put4(sb, tileB, cb, 4 * q, bv + 4 * q);
-      }
-      tc::fence_smem_to_async();
-      tc::warp_arrive(&full[s]);
     }
   } else if (warp == 12) {
     // ---- MMA issue (kind::tf32, K = 8 per instruction) ----
@@ -302,6 +373,14 @@ cudaError_t gemm_tf32x3(GemmArgs p, int batch, cudaStream_t s) {
   }
   const int ntile = (p.N + 255) / 256;
   p.Nt = ((p.N + ntile - 1) / ntile + 15) / 16 * 16;
+  p.vec = 0;
+  if (!A_MC && !B_MC && std::is_same<TA, float>::value && std::is_same<TB, float>::value) {
+    const bool al = reinterpret_cast<uintptr_t>(p.A) % 16 == 0 &&
+                    reinterpret_cast<uintptr_t>(p.B) % 16 == 0;
+    const bool st = p.a_sg % 4 == 0 && p.a_sw % 4 == 0 && p.a_sz % 4 == 0 && p.b_s % 4 == 0 &&
+                    p.b_sz % 4 == 0 && (p.nkz == 1 || p.kz % 4 == 0);
+    p.vec = (al && st) ? 1 : 0;
+  }
   p.tcols = 32;
   while (p.tcols < p.Nt) p.tcols *= 2;
   const size_t smem = 2 * (2 * (size_t)kTileA + 2 * (size_t)p.Nt * 128) + 1024 + 128;
@@ -366,10 +445,10 @@ cudaError_t vqv_tc(int n, int M, int ld, const float *V32, const float *g32, flo
   return gemm_tf32x3<float, float, float, false, false, false>(q, 1, s);
 }
 
-cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long sh_z,
+cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, int sh_ld, const float *Sh, long sh_z,
                         const float *Aop, int lda, long a_z, int nkz, bool tri, double *O,
                         long o_z, long o_kz, int *err, cudaStream_t s) {
-  if (!fits32(2L * Tn * Tn + 2L * Tn) || !fits32(sh_z) || !fits32(a_z) || !fits32(o_z) ||
+  if (!fits32((long)Tn * sh_ld + sh_ld) || !fits32(sh_z) || !fits32(a_z) || !fits32(o_z) ||
       !fits32((long)2 * n * lda))
     return cudaErrorInvalidValue;
   // O[slice][z][j][p][a][c] = sum_k Sh_z[j n + c][k] Aop_z[p n + a][k]: rows (j, c) grouped by
@@ -378,8 +457,8 @@ cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long s
   g.G = n;
   g.nG = ncols;
   g.A = Sh;
-  g.a_sg = 2 * n * Tn;
-  g.a_sw = 2 * Tn;
+  g.a_sg = n * sh_ld;
+  g.a_sw = sh_ld;
   g.a_sz = (int)sh_z;
   g.B = Aop;
   g.b_s = lda;
@@ -398,18 +477,20 @@ cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long s
   return gemm_tf32x3<float, float, double, false, false, false>(g, 2, s);
 }
 
-cudaError_t kbe_exchange_tc(int n, int ne, const float *Ap, const float *Bp, float *P, int *err,
-                            cudaStream_t s) {
+cudaError_t kbe_exchange_tc(int n, int ne, int xld, const float *Ap, const float *Bp, float *P,
+                            int *err, cudaStream_t s) {
   const long n2 = (long)n * n;
-  if (2 * n > 128 || n2 > 4096 || !fits32(2 * n2 * n) || !fits32(4 * n2)) return cudaErrorInvalidValue;
-  // P_e[(b, k)][(p, a)] = sum_{(q, l)} Ap_e[(p, a)][(q, l)] Bp_e[(b, k)][(q, l)]
+  if (2 * n > 128 || n2 > 4096 || xld < 2 * n || !fits32(2 * n2 * n) || !fits32(n2 * xld))
+    return cudaErrorInvalidValue;
+  // P_e[(b, k)][(p, a)] = sum_{(q, l)} Ap_e[(p, a)][(q, l)] Bp_e[(b, k)][(q, l)]; operand rows
+  // of pitch xld
   GemmArgs g = args0(2 * n, (int)n2, 2 * n, err);
   g.A = Ap;
-  g.a_sw = 2 * n;
-  g.a_sz = (int)(4 * n2);
+  g.a_sw = xld;
+  g.a_sz = (int)(2 * n * xld);
   g.B = Bp;
-  g.b_s = 2 * n;
-  g.b_sz = (int)(2 * n2 * n);
+  g.b_s = xld;
+  g.b_sz = (int)(n2 * xld);
   g.O = P;
   g.o_sc = 2 * n;
   g.o_sz = (int)(2 * n2 * n);

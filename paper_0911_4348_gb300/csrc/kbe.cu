@@ -29,7 +29,8 @@
 // as split-TF32 tensor-core products (gemm_tc.cu) over FP32 planar shadows of
 // L, Gt and the trapezoid-weighted L - Gt, written beside the FP64 matrices by
 // every advance: shadow w (0 L, 1 Gt, 2 Dw) holds at row j n + c, column
-// (2 s + p) n + b (row length 2 T n, so the contraction index is contiguous)
+// (2 s + p) n + b (rows of 2 T n values padded to a multiple of 32, so the
+// contraction index is contiguous and every row starts 128-byte aligned)
 // part p (re, im) of F(s, j)[b][c], and Dw(s, j) = w^j_s (L - Gt)(s, j)
 // for s <= j, zero below (so the second integral is a plain product over
 // s <= j, block-triangular in (s, j)). The left factors of both integrals are
@@ -71,9 +72,10 @@ __device__ __forceinline__ double2 scalez(double s, double2 a) {
 __host__ __device__ __forceinline__ long blk(int s, int j, int n, long ld) {
   return (long)s * n * ld + (long)j * n;
 }
-// element (s, j)[b][c], part p, of a planar two-time shadow (row j n + c, column (2 s + p) n + b)
-__device__ __forceinline__ long shi(int s, int j, int b, int c, int p, int n, long Tn) {
-  return ((long)j * n + c) * 2 * Tn + ((long)2 * s + p) * n + b;
+// element (s, j)[b][c], part p, of a planar two-time shadow (row j n + c of pitch
+// shld, column (2 s + p) n + b)
+__device__ __forceinline__ long shi(int s, int j, int b, int c, int p, int n, long shld) {
+  return ((long)j * n + c) * shld + ((long)2 * s + p) * n + b;
 }
 // trapezoid weight of point s on [0, t_m]
 __device__ __forceinline__ double trap_w(int s, int m, double dt) {
@@ -271,25 +273,25 @@ __global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, co
 // re/im parts of the contraction), Bp_e[(b, k)][(q, l)] = part q of
 // V_bl gb_lk = -V_bl conj(H_kl).
 __global__ void xop_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
-                           const double *V, float *Ap, float *Bp) {
+                           const double *V, int xld, float *Ap, float *Bp) {
   const int e = blockIdx.y, kt = e >> 1, w = e & 1;
   const long off = blk(i, kt, n, ld), n2 = (long)n * n;
   const double2 *g = (w ? G : L) + off, *H = (w ? L : G) + off;
-  float *A = Ap + (long)e * 4 * n2, *B = Bp + (long)e * 2 * n2 * n;
+  float *A = Ap + (long)e * 2 * n * xld, *B = Bp + (long)e * n2 * xld;
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n2 * n; q += (long)gridDim.x * blockDim.x) {
     const int b = (int)(q / n2), k = (int)((q / n) % n), l = (int)(q % n);
     const double2 h = H[k * ld + l];
     const double v = V[b * n + l];
-    float *row = B + ((long)b * n + k) * 2 * n;
+    float *row = B + ((long)b * n + k) * xld;
     row[l] = (float)(-v * h.x);
     row[n + l] = (float)(v * h.y);
     if (q < n2) {  // Ap from g: element (a, l) = (k, l) here
       const int a = (int)(q / n), ll = (int)(q % n);
       const double2 x = g[a * ld + ll];
-      A[(long)a * 2 * n + ll] = (float)x.x;
-      A[(long)a * 2 * n + n + ll] = (float)(-x.y);
-      A[(long)(n + a) * 2 * n + ll] = (float)x.y;
-      A[(long)(n + a) * 2 * n + n + ll] = (float)x.x;
+      A[(long)a * xld + ll] = (float)x.x;
+      A[(long)a * xld + n + ll] = (float)(-x.y);
+      A[(long)(n + a) * xld + ll] = (float)x.y;
+      A[(long)(n + a) * xld + n + ll] = (float)x.x;
     }
   }
 }
@@ -472,7 +474,7 @@ __global__ void coll_reduce_kernel(int n, int j0, int ncols, int splits, int mod
 // Predictor (R1 == nullptr) or corrector of time row N+1 and its mirror column.
 __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, const double2 *R0L,
                                const double2 *R0G, const double2 *R1L, const double2 *R1G,
-                               double dt, float *sh, long shz, long Tn) {
+                               double dt, float *sh, long shz, long shld) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int j = blockIdx.y, b = idx / n, c = idx % n;
@@ -493,8 +495,8 @@ __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, co
     G[blk(j, N + 1, n, ld) + c * ld + b] = conjz(vg);
     if (sh) {
       const long pim = n;  // from part re to part im
-      const long r0 = shi(N + 1, j, b, c, 0, n, Tn);  // (N+1, j)[b][c]
-      const long m0 = shi(j, N + 1, c, b, 0, n, Tn);  // (j, N+1)[c][b]
+      const long r0 = shi(N + 1, j, b, c, 0, n, shld);  // (N+1, j)[b][c]
+      const long m0 = shi(j, N + 1, c, b, 0, n, shld);  // (j, N+1)[c][b]
       sh[r0] = (float)vl.x;
       sh[r0 + pim] = (float)vl.y;
       sh[shz + r0] = (float)vg.x;
@@ -524,7 +526,7 @@ __global__ void advance_kernel(int n, int N, long ld, double2 *L, double2 *G, co
     G[blk(N + 1, N + 1, n, ld) + b * ld + c] = vg;
     if (sh) {
       const long pim = n;
-      const long r0 = shi(N + 1, N + 1, b, c, 0, n, Tn);
+      const long r0 = shi(N + 1, N + 1, b, c, 0, n, shld);
       sh[r0] = (float)v.x;
       sh[r0 + pim] = (float)v.y;
       sh[shz + r0] = (float)vg.x;
@@ -580,12 +582,12 @@ __global__ void observe_kernel(int n, double spin, const double *h, const double
 
 // Shadows of block (0, 0) (Dw(0, 0) = w^0_0 (L - Gt) = 0 stays zero).
 __global__ void shadow00_kernel(int n, long ld, const double2 *L, const double2 *G, float *sh,
-                                long shz, long Tn) {
+                                long shz, long shld) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int b = idx / n, c = idx % n;
   const double2 l = L[b * ld + c], g = G[b * ld + c];
-  const long r0 = shi(0, 0, b, c, 0, n, Tn), pim = n;
+  const long r0 = shi(0, 0, b, c, 0, n, shld), pim = n;
   sh[r0] = (float)l.x;
   sh[r0 + pim] = (float)l.y;
   sh[shz + r0] = (float)g.x;
@@ -716,8 +718,8 @@ struct KbeRun {
   // split-TF32 exchange products (null: FP64 exchange kernel)
   float *xa = nullptr, *xb = nullptr, *xp = nullptr;
   double *o1 = nullptr, *o2 = nullptr;
-  long shz = 0, Tn = 0, a_z = 0;
-  int lda = 0;
+  long shz = 0, Tn = 0, shld = 0, a_z = 0;
+  int lda = 0, xld = 0;
   int *err = nullptr;
   const double *h, *V, *dv;
   double *E, *Nn;
@@ -760,9 +762,9 @@ struct KbeRun {
     if (xp) {
       const long work = (long)nn * n;
       const unsigned gx = (unsigned)std::min(64L, (work + 255) / 256);
-      xop_kernel<<<dim3(gx, ne), 256, 0, s>>>(n, i, ld, L, G, V, xa, xb);
+      xop_kernel<<<dim3(gx, ne), 256, 0, s>>>(n, i, ld, L, G, V, xld, xa, xb);
       KBE_CK(ctx, cudaGetLastError());
-      KBE_CK(ctx, kbe_exchange_tc(n, ne, xa, xb, xp, err, s));
+      KBE_CK(ctx, kbe_exchange_tc(n, ne, xld, xa, xb, xp, err, s));
       xsum_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, xp, Tcap, S);
       launches += 2;
     } else if (n <= 16) {
@@ -792,10 +794,10 @@ struct KbeRun {
     const int kz = ((K + nkz - 1) / nkz + 31) / 32 * 32, ns = (K + kz - 1) / kz;
     const long oz = (long)Tcap * 2 * nn, okz = 2 * oz;
     KBE_CK(ctx, mark(2));
-    KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, sh, shz, A1, lda, 0, nkz, false, o1, oz, okz,
-                            err, s));
-    KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, sh + 2 * shz, 0, A2, lda, a_z, nkz, true, o2,
+    KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, (int)shld, sh, shz, A1, lda, 0, nkz, false, o1,
                             oz, okz, err, s));
+    KBE_CK(ctx, kbe_rows_tc(n, i + 1, K, (int)Tn, (int)shld, sh + 2 * shz, 0, A2, lda, a_z, nkz,
+                            true, o2, oz, okz, err, s));
     KBE_CK(ctx, mark(0));
     // shadow bytes the two products read once: L and Gt rows j <= i over k < K, and the
     // triangle s <= j of Dw
@@ -834,7 +836,7 @@ struct KbeRun {
     const int nn = n * n;
     advance_kernel<<<dim3((nn + 255) / 256, N + 2), 256, 0, s>>>(
         n, N, ld, L, G, R0L, R0G, corrector ? R1L : nullptr, corrector ? R1G : nullptr, dt, sh,
-        shz, Tn);
+        shz, shld);
     KBE_CK(ctx, cudaGetLastError());
     ++launches;
     return FEDVR_OK;
@@ -865,16 +867,19 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   const bool split = precision == FEDVR_SPLIT_TF32 && second_born != 0;
   const int T = n_steps + 1;
   const long ld = (long)T * n;
-  if (split && 2 * ld * ld >= (1L << 31))
-    return fail(ctx, FEDVR_ERR_ARG, "split-TF32 propagation needs T n_b <= 32767 (got %ld)", ld);
+  const long shld = (2 * ld + 31) / 32 * 32;  // shadow row pitch (floats)
+  if (split && ld * shld + shld >= (1L << 31))
+    return fail(ctx, FEDVR_ERR_ARG, "split-TF32 propagation needs T n_b <= 32750 (got %ld)", ld);
   const size_t nn = (size_t)n * n, cz = sizeof(double2);
   const size_t two = (size_t)ld * (size_t)ld * cz;
-  const size_t shz = split ? 2 * (size_t)ld * (size_t)ld : 0;  // floats per shadow
-  const int lda = 2 * (int)ld;
+  const size_t shz = split ? (size_t)ld * (size_t)shld : 0;  // floats per shadow
+  const int lda = (int)shld;
+  const int xld = (2 * n + 3) / 4 * 4;  // exchange operand row pitch (floats)
   const size_t aop_floats = split ? 3 * (size_t)2 * n * lda : 0;
   const size_t o_doubles = split ? (size_t)16 * 2 * T * 2 * nn : 0;
   const bool split_x = split && n <= 64;  // exchange products on the tensor cores
-  const size_t x_floats = split_x ? (size_t)2 * T * (4 * nn + 4 * nn * n) : 0;
+  const size_t x_floats =
+      split_x ? (size_t)2 * T * ((size_t)2 * n * xld + nn * xld + 2 * nn * n) : 0;
   {
     size_t fre = 0, tot = 0;
     KBE_CK(ctx, cudaMemGetInfo(&fre, &tot));
@@ -931,7 +936,7 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
   KBE_CK(ctx, cudaGetLastError());
   if (split) {
     shadow00_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, ld, L, G, P<float>(ctx->k_sh),
-                                                                 (long)shz, ld);
+                                                                 (long)shz, shld);
     KBE_CK(ctx, cudaGetLastError());
   }
 
@@ -958,7 +963,9 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
     run.sh = P<float>(ctx->k_sh);
     run.shz = (long)shz;
     run.Tn = ld;
+    run.shld = shld;
     run.lda = lda;
+    run.xld = xld;
     run.aop = P<float>(ctx->k_aop);
     run.a_z = (long)2 * n * lda;
     run.o1 = P<double>(ctx->k_o);
@@ -966,8 +973,8 @@ int fedvr_kbe_propagate(fedvr_ctx *ctx, double dt, int n_steps, int second_born,
     run.err = P<int>(ctx->k_flag);
     if (split_x) {
       run.xa = P<float>(ctx->k_x);
-      run.xb = run.xa + (size_t)2 * T * 4 * nn;
-      run.xp = run.xb + (size_t)2 * T * 2 * nn * n;
+      run.xb = run.xa + (size_t)2 * T * 2 * n * xld;
+      run.xp = run.xb + (size_t)2 * T * nn * xld;
     }
   }
   run.h = CP<double>(ctx->b_h);

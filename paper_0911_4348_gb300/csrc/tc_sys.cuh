@@ -141,17 +141,18 @@ cudaError_t conv2_tc(int n, int M, const float *K32, const double *C, const doub
 // Real-time collision integrals of one time row (kbe.cu), two batched products
 // (z = 0, 1): O[k][z][j][p][a][c] = sum over the contraction slice k of
 // Sh_z[j n + c][k'] Aop_z[p n + a][k'] for j < ncols, k' < K; Sh_z at
-// Sh + z sh_z ([T n][2 T n] FP32 planar two-time shadow, Tn = T n), Aop_z at
+// Sh + z sh_z ([T n][sh_ld] FP32 planar two-time shadow, Tn = T n, row pitch
+// sh_ld >= 2 T n), Aop_z at
 // Aop + z a_z ([2n][lda]); tri: block-triangular shadow (rows of column j
 // need k' < 2n (j + 1)). The number of slices actually used is
 // ceil(K / kz) with kz = ceil(K / nkz) rounded up to 32.
 // Real-time exchange products of ne self-energy entries (kbe.cu), one batch
 // entry each: P_e[(b, k)][(p, a)] = sum over (q, l) of Ap_e[(p, a)][(q, l)]
-// Bp_e[(b, k)][(q, l)], Ap_e [2n][2n], Bp_e [n n][2n], P_e [n n][2n] (FP32);
-// needs 2n <= 128.
-cudaError_t kbe_exchange_tc(int n, int ne, const float *Ap, const float *Bp, float *P, int *err,
-                            cudaStream_t s);
-cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, const float *Sh, long sh_z,
+// Bp_e[(b, k)][(q, l)], Ap_e [2n][xld], Bp_e [n n][xld] (rows of pitch
+// xld >= 2n), P_e [n n][2n] (FP32); needs 2n <= 128.
+cudaError_t kbe_exchange_tc(int n, int ne, int xld, const float *Ap, const float *Bp, float *P,
+                            int *err, cudaStream_t s);
+cudaError_t kbe_rows_tc(int n, int ncols, int K, int Tn, int sh_ld, const float *Sh, long sh_z,
                         const float *Aop, int lda, long a_z, int nkz, bool tri, double *O,
                         long o_z, long o_kz, int *err, cudaStream_t s);
 // Persistent launches over a device table of n_sys systems; prefix[n_sys + 1]

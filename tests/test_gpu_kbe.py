@@ -186,3 +186,55 @@ def test_split_tf32_rejects_oversized_and_bad_precision():
         ctx.kbe_propagate(0.05, 2200, True, rho0=rho0, precision=SPLIT_TF32)
     assert e.value.code == -1
     ctx.close()
+
+
+def test_split_tf32_field_driven_matches_oracle():
+    # the HF ground state under a dipole field, collision integrals and exchange
+    # products on the tensor cores (n_b = 39 <= 64)
+    _need_gpu()
+    from paper_0911_4348_gb300 import SPLIT_TF32
+    ctx, h, V, x = _setup(10, 4, 15.0)
+    s = W.he_small()
+    ctx.solve_hf(s.beta, tol=1e-13)
+    rho_hf = ctx.get_hf()["rho0"].astype(np.complex128)
+    dt, steps = 0.04, 16
+    t = np.arange(steps + 1) * dt
+    dv = np.outer(0.2 * np.sin(1.3 * t), x)
+    ref = O.kbe_propagate(h, V, 2.0, rho_hf, dt, steps, dv=dv)
+    got = ctx.kbe_propagate(dt, steps, True, dv=dv, precision=SPLIT_TF32)
+    assert _rel(got["rho"], ref["rho"]) < SPLIT_TOL
+    assert float(np.max(np.abs(got["E"] - ref["E"]))) < SPLIT_TOL
+    ctx.close()
+
+
+def test_repeated_propagation_reuses_buffers_exactly():
+    # a longer propagation first, then a shorter one on the same context: the
+    # second equals the same call on a fresh context bit for bit (every buffer
+    # that outlives a call is cleared or rewritten), in both modes
+    _need_gpu()
+    from paper_0911_4348_gb300 import SPLIT_TF32
+    for prec in (0, SPLIT_TF32):
+        ctx, h, V, x = _setup(4, 4, 10.0)
+        rho0 = _kicked_rho(h, x)
+        ctx.kbe_propagate(0.05, 30, True, rho0=rho0, precision=prec)
+        a = ctx.kbe_propagate(0.05, 12, True, rho0=rho0, precision=prec)
+        La = ctx.kbe_block("L", 12, 3)
+        ctx.close()
+        fresh, _, _, _ = _setup(4, 4, 10.0)
+        b = fresh.kbe_propagate(0.05, 12, True, rho0=rho0, precision=prec)
+        assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["E"], b["E"])
+        assert np.array_equal(La, fresh.kbe_block("L", 12, 3))
+        fresh.close()
+
+
+def test_split_flag_leaves_tdhf_unchanged():
+    # without collision integrals there is nothing to split: TDHF with the split
+    # flag equals FP64 TDHF bit for bit
+    _need_gpu()
+    from paper_0911_4348_gb300 import SPLIT_TF32
+    ctx, h, V, x = _setup(4, 4, 10.0)
+    rho0 = _kicked_rho(h, x)
+    a = ctx.kbe_propagate(0.05, 20, False, rho0=rho0)
+    b = ctx.kbe_propagate(0.05, 20, False, rho0=rho0, precision=SPLIT_TF32)
+    assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["E"], b["E"])
+    ctx.close()
