@@ -37,9 +37,10 @@
 // laid out as real [2n][2 T n] matrices (rows re/im of the output, columns
 // (s, p, b)) that turn each complex product into one real product. The
 // -i h_HF F term, the energy's K_L(t, t), the self-energy and the stepping stay
-// in FP64. In the same mode the exchange term's products
+// in FP64. In the same mode (n_b <= 64) the exchange term's products
 // P^(b)_ak = sum_l g_al V_bl gb_lk of all entries of a row run as one batched
-// split-TF32 product (n_b <= 64) and only its k-sum stays in FP64.
+// split-TF32 product, and the exchange's k-sum and the direct term V Q V run in
+// FP32 on the CUDA cores (their inputs carry the products' precision).
 #include <algorithm>
 
 #include "common.cuh"
@@ -268,6 +269,45 @@ __global__ void __launch_bounds__(256) exchange_kernel(int n, int i, long ld, co
   }
 }
 
+// Split mode's direct term and exchange k-sum in FP32 (their inputs carry the
+// split products' precision): T1 = V Q as float2, then S = spin g o (T1 V).
+__global__ void vq32_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                            const double *V, float2 *T1) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const int a = idx / n, l = idx % n;
+  const long off = blk(i, kt, n, ld);
+  const double2 *g = (w ? G : L) + off, *H = (w ? L : G) + off;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int k = 0; k < n; ++k) {
+    const double2 gg = g[k * ld + l], hh = H[k * ld + l];
+    const float gr = (float)gg.x, gi = (float)gg.y, hr = (float)hh.x, hi = (float)hh.y;
+    const float qr = gr * hr + gi * hi, qi = gi * hr - gr * hi;  // g conj(H) = -Q_kl
+    const float v = (float)V[a * n + k];
+    acc.x = fmaf(-v, qr, acc.x);
+    acc.y = fmaf(-v, qi, acc.y);
+  }
+  T1[(long)e * n * n + idx] = acc;
+}
+__global__ void direct32_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
+                                const double *V, const float2 *T1, double spin, int Tcap,
+                                double2 *S) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int e = blockIdx.y, kt = e >> 1, w = e & 1;
+  const int a = idx / n, b = idx % n;
+  const float2 *t1 = T1 + (long)e * n * n + (long)a * n;
+  float2 W = make_float2(0.f, 0.f);
+  for (int l = 0; l < n; ++l) {
+    const float v = (float)V[l * n + b];
+    W.x = fmaf(t1[l].x, v, W.x);
+    W.y = fmaf(t1[l].y, v, W.y);
+  }
+  const double2 g = (w ? G : L)[blk(i, kt, n, ld) + a * ld + b];
+  S[((long)w * Tcap + kt) * n * n + idx] = cmul(scalez(spin, g), make_double2(W.x, W.y));
+}
+
 // Operands of the batched exchange product of row i, entry e = 2k + w:
 // Ap_e[(p, a)][(q, l)] the real form of g (rows re/im of the output, columns
 // re/im parts of the contraction), Bp_e[(b, k)][(q, l)] = part q of
@@ -296,8 +336,9 @@ __global__ void xop_kernel(int n, int i, long ld, const double2 *L, const double
   }
 }
 
-// k-sum of the exchange from the product: S_e[a][b] -= sum_k V_ak P_ak g_kb with
-// P_ak = P_e[(b, k)][(0, a)] + i P_e[(b, k)][(1, a)]; thread per (a, b).
+// k-sum of the exchange from the product (FP32, like the product): S_e[a][b] -=
+// sum_k V_ak P_ak g_kb with P_ak = P_e[(b, k)][(0, a)] + i P_e[(b, k)][(1, a)];
+// thread per (a, b).
 __global__ void xsum_kernel(int n, int i, long ld, const double2 *L, const double2 *G,
                             const double *V, const float *P, int Tcap, double2 *S) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -306,14 +347,19 @@ __global__ void xsum_kernel(int n, int i, long ld, const double2 *L, const doubl
   const long off = blk(i, kt, n, ld), n2 = (long)n * n;
   const double2 *g = (w ? G : L) + off;
   const float *Pe = P + (long)e * 2 * n2 * n;
-  double2 x = make_double2(0.0, 0.0);
+  float xr = 0.f, xi = 0.f;
   for (int k = 0; k < n; ++k) {
     const float *pr = Pe + ((long)b * n + k) * 2 * n;
-    const double2 pk = make_double2((double)pr[a], (double)pr[n + a]);
-    cmla(x, scalez(V[a * n + k], pk), g[k * ld + b]);
+    const double2 gk = g[k * ld + b];
+    const float v = (float)V[a * n + k], pre = v * pr[a], pim = v * pr[n + a];
+    const float gr = (float)gk.x, gi = (float)gk.y;
+    xr = fmaf(pre, gr, xr);
+    xr = fmaf(-pim, gi, xr);
+    xi = fmaf(pre, gi, xi);
+    xi = fmaf(pim, gr, xi);
   }
   double2 *Se = S + ((long)w * Tcap + kt) * n2;
-  Se[a * n + b] = subz(Se[a * n + b], x);
+  Se[a * n + b] = subz(Se[a * n + b], make_double2(xr, xi));
 }
 
 struct CollArgs {
@@ -754,10 +800,18 @@ struct KbeRun {
     if (!corr) return FEDVR_OK;
     const int nn = n * n, ne = 2 * (i + 1);
     KBE_CK(ctx, mark(1));
-    vq_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1);
-    KBE_CK(ctx, cudaGetLastError());
-    direct_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1, spin, Tcap,
-                                                             S);
+    if (xp) {
+      float2 *T132 = reinterpret_cast<float2 *>(T1);
+      vq32_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T132);
+      KBE_CK(ctx, cudaGetLastError());
+      direct32_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T132, spin,
+                                                                 Tcap, S);
+    } else {
+      vq_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1);
+      KBE_CK(ctx, cudaGetLastError());
+      direct_kernel<<<dim3((nn + 255) / 256, ne), 256, 0, s>>>(n, i, ld, L, G, V, T1, spin, Tcap,
+                                                               S);
+    }
     KBE_CK(ctx, cudaGetLastError());
     if (xp) {
       const long work = (long)nn * n;

@@ -238,3 +238,28 @@ def test_split_flag_leaves_tdhf_unchanged():
     b = ctx.kbe_propagate(0.05, 20, False, rho0=rho0, precision=SPLIT_TF32)
     assert np.array_equal(a["rho"], b["rho"]) and np.array_equal(a["E"], b["E"])
     ctx.close()
+
+
+def test_bench_size_propagation_properties():
+    # the bench's system (n_b = 39, box [-15, 15]) released from a kicked
+    # determinant without a field, 200 steps: FP64 keeps N = 2 and rho Hermitian
+    # to rounding; the split mode agrees with FP64 within its bound; the energy
+    # of the (conserving) scheme drifts by less than 1e-4 Ha and the drift at
+    # least halves with dt (the grid's highest modes have e dt ~ 0.4 at
+    # dt = 0.04, short of the asymptotic 4x that the oracle's pin checks on a
+    # small model)
+    _need_gpu()
+    from paper_0911_4348_gb300 import SPLIT_TF32
+    ctx, h, V, x = _setup(10, 4, 15.0)
+    rho0 = _kicked_rho(h, x)
+    a = ctx.kbe_propagate(0.04, 200, True, rho0=rho0)
+    assert np.max(np.abs(a["N"] - 2.0)) < 1e-12
+    assert np.max(np.abs(a["rho"] - a["rho"].conj().transpose(0, 2, 1))) < 1e-14
+    b = ctx.kbe_propagate(0.04, 200, True, rho0=rho0, precision=SPLIT_TF32)
+    assert _rel(b["rho"], a["rho"]) < SPLIT_TOL
+    assert float(np.max(np.abs(b["E"] - a["E"]))) < SPLIT_TOL
+    c = ctx.kbe_propagate(0.02, 400, True, rho0=rho0, precision=SPLIT_TF32)
+    drift = [float(np.max(r["E"]) - np.min(r["E"])) for r in (a, c)]
+    print(f"E drift dt=0.04: {drift[0]:.3e}, dt=0.02: {drift[1]:.3e}")
+    assert drift[0] < 1e-4 and drift[0] > 2.0 * drift[1]
+    ctx.close()
