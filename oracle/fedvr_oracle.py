@@ -26,6 +26,11 @@ representation in nonequilibrium Green's function calculations" (arXiv
   in ``conv1``, ``conv2``, ``energy``, ``solve_2b``.
 * Sec. 2.3 and 3.2 observables: ``density`` (one-electron density from
   g(0^-)) and ``nuclear_repulsion`` (the internuclear term of Eq. h3pv).
+* Sec. 4 (GW named as a further approximation the FE-DVR form simplifies):
+  ``bose_lag_table``, ``conv_bose``, ``screened_w``, ``sigma_gw`` and
+  ``solve_2b(..., self_energy="gw")`` (the screened interaction of the
+  two-index bubble series on the same mesh; its lowest order is the direct
+  term of Eq. sigma2ndb).
 * Sec. 2, Eqs. (kbe), (skkbe), (skkbesigma) with (sigmahf), (sigma2ndb) on the
   Keldysh components: ``kbe_propagate`` (real-time two-time Kadanoff-Baym
   propagation from an uncorrelated initial state) and its self-energy
@@ -855,8 +860,88 @@ def dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=None,
     return dict(G=Gnext, Sigma=A, E0=E, N=Nel, res=r, I1=I1, I2=I2)
 
 
+def bose_lag_table(tau: np.ndarray, beta: float) -> dict:
+    """(k, t) of the lag tau_i - tau_j for every (i, j), functions extended
+    periodically, F(x) = F(x - beta) for x in (0, beta] (bosonic: the bubble
+    and the screened interaction). j >= i: y = tau_i - tau_j (y = 0 at i = j,
+    the last mesh point); j < i: y = tau_i - tau_j - beta."""
+    M = len(tau)
+    K = np.zeros((M, M), dtype=np.int32)
+    T = np.zeros((M, M))
+    for i in range(M):
+        for j in range(M):
+            x = float(tau[i]) - float(tau[j])
+            y = x if j >= i else x - beta
+            K[i, j], T[i, j] = bracket(tau, y)
+    return dict(k=K, t=T)
+
+
+def conv_bose(A: np.ndarray, B: np.ndarray, mesh: dict, blag: dict) -> np.ndarray:
+    """(A * B)(tau_i) = int over one period of A(tau_i - s) B(s) ds for
+    periodic A: trapezoid on the mesh (weights w_j), A at the lag linearly
+    interpolated (``bose_lag_table``); a periodic A has no jump at lag 0, so
+    the trapezoid is not split there."""
+    M = A.shape[0]
+    w = mesh["w"]
+    out = []
+    for i in range(M):
+        # A at the lags tau_i - tau_j for every j, each times w_j, then the sum over j of
+        # those matrices times B_j
+        k = blag["k"][i]
+        t = blag["t"][i][:, None, None]
+        Al = w[:, None, None] * ((1.0 - t) * A[k] + t * A[k + 1])
+        out.append(np.einsum("jab,jbc->ac", Al, B))
+    return np.stack(out)
+
+
+def screened_w(G: np.ndarray, V: np.ndarray, sigma: float, mesh: dict, blag: dict, w0=None,
+               mixing: float = 0.3, tol: float = 1e-12, max_iter: int = 500) -> dict:
+    """Correlated screened interaction of the two-index bubble series.
+
+    In the FE-DVR form the interaction is two-index (V_ab between the nodes a
+    and b), so the polarisation bubble is too: with this code's g > 0 on
+    [-beta, 0] it is -sigma Q with Q_j = g_j o gb_j (gb_j = g(-beta - tau_j)),
+    and the correlated part of the screened interaction, W^c = V P V + V P * W^c,
+    becomes -sigma w with
+
+        w = V Q V - sigma V (Q * w),        Sigma^GW = sigma g o w,
+
+    whose lowest order w = V Q V gives the direct term of Eq. sigma2ndb.
+    Reading (the paper names GW without equations): the linear equation is
+    solved by the damped fixed-point iteration w <- (1 - a) w + a w_new from w0
+    (default V Q V) until max|w_new - w| < tol; the operator
+    w -> sigma V (Q * w) has real non-negative eigenvalues here (bounded by
+    about 5 on the He models at beta = 100), so a = 0.3 contracts where the
+    plain series diverges. Returns w, the iterations and the last residual."""
+    M = G.shape[0]
+    Q = np.stack([G[j] * G[M - 1 - j] for j in range(M)])
+    VQV = np.stack([V @ Q[j] @ V for j in range(M)])
+    w = VQV.copy() if w0 is None else np.array(w0, dtype=np.float64)
+    r = np.inf
+    it = 0
+    for it in range(1, max_iter + 1):
+        C = conv_bose(Q, w, mesh, blag)
+        new = VQV - sigma * np.stack([V @ C[j] for j in range(M)])
+        r = float(np.max(np.abs(new - w)))
+        w = (1.0 - mixing) * w + mixing * new
+        if r < tol:
+            break
+    return dict(w=w, iters=it, res=r, Q=Q, VQV=VQV)
+
+
+def sigma_gw(G: np.ndarray, V: np.ndarray, sigma: float, mesh: dict, blag: dict, w0=None,
+             mixing: float = 0.3, tol: float = 1e-12, max_iter: int = 500) -> dict:
+    """GW correlation self-energy Sigma^GW_j = sigma g_j o w_j (``screened_w``);
+    no exchange term (GW sums the bubbles, second Born adds the second-order
+    exchange)."""
+    sw = screened_w(G, V, sigma, mesh, blag, w0, mixing, tol, max_iter)
+    sw["Sigma"] = sigma * G * sw["w"]
+    return sw
+
+
 def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
-             sigma_init=None, quad: str = "trap") -> dict:
+             sigma_init=None, quad: str = "trap", self_energy: str = "2b",
+             gw_mixing: float = 0.3, gw_tol: float = 1e-12, gw_max_iter: int = 500) -> dict:
     """Second-Born Matsubara self-consistency (Sec. 2.3 and 3.1).
 
     Reading (the iteration scheme is not given): start from g = g^0; linear
@@ -864,25 +949,35 @@ def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
     ``sigma_init`` replaces Sigma^corr[g^0] in the first iteration only (warm
     start). Returns the final g_{k+1}, Sigma_k = Sigma^corr[g_k], and E0 and N
     evaluated on (g_k, Sigma_k).
+
+    self_energy="gw": Sigma^corr = ``sigma_gw`` instead of second Born; the
+    inner iteration for w starts from the previous outer iteration's w (V Q V
+    at the first) and ``gw_inner`` lists its iterations per outer step.
     """
     mesh = power_mesh(beta, u, p)
     lag = lag_table(mesh["tau"], beta)
+    blag = bose_lag_table(mesh["tau"], beta) if self_energy == "gw" else None
     G0 = g0_mesh(hf["eps"], hf["C"], hf["mu"], mesh["tau"], beta)
     G = G0.copy()
     hist = []
     step = None
     converged = False
+    w_state = None
+    gw_inner = []
     for it in range(max_iter):
-        step = dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing,
-                               A=sigma_init if (it == 0 and sigma_init is not None) else None,
-                               quad=quad)
+        A = sigma_init if (it == 0 and sigma_init is not None) else None
+        if A is None and self_energy == "gw":
+            sg = sigma_gw(G, V, sigma, mesh, blag, w_state, gw_mixing, gw_tol, gw_max_iter)
+            A, w_state = sg["Sigma"], sg["w"]
+            gw_inner.append(sg["iters"])
+        step = dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=A, quad=quad)
         hist.append((it, step["res"], step["E0"], step["N"]))
         G = step["G"]
         if step["res"] < tol:
             converged = True
             break
     return dict(G=G, Sigma=step["Sigma"], E0=step["E0"], N=step["N"], iters=len(hist),
-                converged=converged, history=hist, mesh=mesh, G0=G0)
+                converged=converged, history=hist, mesh=mesh, G0=G0, gw_inner=gw_inner)
 
 
 # ---------------------------------------------------------------------------
