@@ -266,6 +266,42 @@ int fedvr_conv1_splits(fedvr_ctx *ctx, int request, int *in_use);
  * order. */
 int fedvr_set_quadrature(fedvr_ctx *ctx, int order);
 
+/* Correlation self-energy of the next fedvr_2b_prepare / solve_2b:
+ * kind 0 = second Born (Sec. 2.3, Eq. sigma2ndb; default), kind 1 = GW, the
+ * approximation Sec. 4 names as the next one the FE-DVR form simplifies. In
+ * this basis the interaction is two-index, so the bubble is too: with
+ * Q_j = g_j o g_{M-1-j} the correlated screened interaction solves
+ *   w = V Q V - sigma V (Q * w)   (Q * w the periodic tau-convolution on the
+ *                                  mesh, trapezoid with Q interpolated at the lag),
+ * and Sigma^GW = sigma g o w (its lowest order w = V Q V is the direct term of
+ * Eq. sigma2ndb; GW has no second-order exchange). Each outer iteration solves
+ * for w by the damped fixed-point iteration w <- (1 - w_mixing) w +
+ * w_mixing (V Q V - sigma V (Q * w)) until max|w_new - w| < w_tol, starting
+ * from the previous outer iteration's w (V Q V at the first). GW runs on the
+ * FP64 path with the trapezoid rule (other precisions or quadratures:
+ * FEDVR_ERR_ARG at prepare) and eagerly (one host readback per inner
+ * iteration, no graph replay). An inner iteration that has not converged in
+ * w_max_iter steps ends the step with FEDVR_ERR_NOCONV. Drops a prepared run.
+ * Errors: FEDVR_ERR_ARG for another kind or for w_mixing outside (0, 1],
+ * w_tol <= 0 or w_max_iter < 1 (kind 1). */
+int fedvr_set_self_energy(fedvr_ctx *ctx, int kind, double w_mixing, double w_tol,
+                          int w_max_iter);
+
+/* Inner iterations of the last GW screened-interaction solve of the context. */
+int fedvr_gw_last_inner(const fedvr_ctx *ctx, int *iters);
+
+/* Stage-level GW on caller device buffers (the context's stream): Sigma^GW
+ * [M][n][n] of G [M][n][n] on the power mesh (beta, u, p), V [n][n], spin
+ * factor spin. w_io (device [M][n][n] or NULL): with w_valid != 0 the inner
+ * iteration starts from it (else from V Q V); the converged w is written back
+ * when given. iters (host, may be NULL): inner iterations. Synchronises the
+ * stream. Errors: FEDVR_ERR_ARG for invalid sizes, mesh or iteration
+ * parameters; FEDVR_ERR_NOCONV if w does not converge in w_max_iter steps;
+ * FEDVR_ERR_NAN if it diverges. */
+int fedvr_sigma_gw(fedvr_ctx *ctx, int n, double beta, int u, int p, double spin, const double *V,
+                   const double *G, double *Sigma, double *w_io, int w_valid, double w_mixing,
+                   double w_tol, int w_max_iter, int *iters);
+
 /* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
  * [M][n_b][n_b] on host or device; M must match the next solve's mesh; copied
  * at once; NULL clears. inner_steps = 0: the first iteration uses Sigma0

@@ -219,6 +219,31 @@ class Context:
         """Chemical potential of the next second-Born run (``fedvr_set_mu``)."""
         self._check(self._lib.fedvr_set_mu(self._h, float(mu)))
 
+    def set_self_energy(self, kind, w_mixing=0.3, w_tol=1e-12, w_max_iter=500):
+        """Correlation self-energy of the next prepare/solve: "2b" (second Born)
+        or "gw" (``fedvr_set_self_energy``)."""
+        k = {"2b": 0, "gw": 1}.get(kind, kind)
+        self._check(self._lib.fedvr_set_self_energy(self._h, int(k), float(w_mixing),
+                                                    float(w_tol), int(w_max_iter)))
+
+    def gw_last_inner(self) -> int:
+        it = C.c_int()
+        self._check(self._lib.fedvr_gw_last_inner(self._h, C.byref(it)))
+        return it.value
+
+    def sigma_gw(self, beta, u, p, V, G, Sigma, spin=2.0, w=None, w_valid=False, w_mixing=0.3,
+                 w_tol=1e-12, w_max_iter=500):
+        """Stage-level GW self-energy of the CUDA stack G into Sigma
+        (``fedvr_sigma_gw``); returns the inner iterations."""
+        M, n = G.shape[0], G.shape[1]
+        assert M == 2 * u * p + 1
+        it = C.c_int()
+        self._check(self._lib.fedvr_sigma_gw(
+            self._h, n, float(beta), int(u), int(p), float(spin), _dev(V, (n, n)),
+            _dev(G, (M, n, n)), _dev(Sigma, (M, n, n)), _dev(w, (M, n, n)) if w is not None else None,
+            1 if w_valid else 0, float(w_mixing), float(w_tol), int(w_max_iter), C.byref(it)))
+        return it.value
+
     def set_quadrature(self, order):
         """Quadrature of the Dyson integrals (``fedvr_set_quadrature``): 2 = split
         trapezoid with linear lag interpolation, 4 = the fourth-order variant

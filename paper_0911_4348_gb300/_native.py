@@ -74,6 +74,10 @@ SIGNATURES = {
                                       _dp, _dp]),
     "fedvr_kbe_get_block": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp]),
     "fedvr_kbe_stats": (C.c_int, [_vp, _dp]),
+    "fedvr_set_self_energy": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, C.c_int]),
+    "fedvr_gw_last_inner": (C.c_int, [_vp, _ip]),
+    "fedvr_sigma_gw": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double, _vp, _vp,
+                                 _vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _ip]),
 }
 
 _lib = None

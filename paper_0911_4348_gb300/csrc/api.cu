@@ -124,6 +124,60 @@ int build_mesh(fedvr_ctx *ctx, double beta, int u, int p, bool coef) {
   return FEDVR_OK;
 }
 
+// GW screened interaction of g and Sigma^GW = spin g o w: the damped fixed-point
+// iteration w <- (1 - a) w + a (V Q V - spin V (Q * w)) from w (V Q V when
+// !w_valid) until max|w_new - w| < tol, with Q * w the periodic convolution of
+// the table coef (conv1_fp64 with no diagonal entries; dummy is never read).
+// One host readback of the residual per inner iteration. Workspace: Q, T1,
+// VQV, C, Nw stacks and an 8-byte residual word.
+int gw_solve(fedvr_ctx *ctx, int n, int M, const double *V, const double *G, double *Sigma,
+             const ConvCoef *coef, double *w, bool w_valid, double *Q, double *T1, double *VQV,
+             double *C, double *Nw, unsigned long long *res_d, const double *dummy,
+             double mixing, double tol, int max_iter, int *iters) {
+  cudaStream_t s = ctx->stream;
+  const size_t stack = (size_t)M * n * n;
+  const long nn = (long)n * n;
+  FEDVR_CK(ctx, gw_bubble(n, M, V, G, Q, T1, VQV, s));
+  if (!w_valid) FEDVR_CK(ctx, launch_copy(stack, VQV, w, s));
+  double r = 0.0;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    FEDVR_CK(ctx, conv1_fp64(n, M, coef, dummy, Q, w, C, s));
+    FEDVR_CK(ctx, launch_copy(stack, VQV, Nw, s));
+    FEDVR_CK(ctx, dgemm(false, false, n, n, n, -ctx->spin, V, n, 0, C, n, nn, nullptr, 0, 1.0, Nw,
+                        n, nn, M, s));
+    FEDVR_CK(ctx, cudaMemsetAsync(res_d, 0, sizeof(unsigned long long), s));
+    FEDVR_CK(ctx, launch_max_abs_diff(stack, Nw, w, res_d, s));
+    FEDVR_CK(ctx, launch_axpby(stack, 1.0 - mixing, w, mixing, Nw, w, s));
+    unsigned long long bits = 0;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&bits, res_d, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    if (int rr = sync(ctx)) return rr;
+    memcpy(&r, &bits, sizeof(r));
+    if (!is_fin(r)) return fail(ctx, FEDVR_ERR_NAN, "GW screened interaction is not finite");
+    if (r < tol) break;
+  }
+  if (it > max_iter)
+    return fail(ctx, FEDVR_ERR_NOCONV,
+                "GW screened interaction not converged in %d iterations (residual %.3e)",
+                max_iter, r);
+  FEDVR_CK(ctx, launch_gw_sigma((long)stack, ctx->spin, G, w, Sigma, s));
+  *iters = it;
+  return FEDVR_OK;
+}
+
+int gw_workspace(fedvr_ctx *ctx, int n, int M) {
+  const size_t stack = (size_t)M * n * n;
+  ENSURE(ctx, g_w, dsz(stack));
+  ENSURE(ctx, g_vqv, dsz(stack));
+  ENSURE(ctx, g_c, dsz(stack));
+  ENSURE(ctx, g_new, dsz(stack));
+  ENSURE(ctx, g_coef, (size_t)M * M * sizeof(ConvCoef));
+  ENSURE(ctx, g_res, 16);
+  ENSURE(ctx, w_t1, dsz(stack));
+  ENSURE(ctx, w_t2, dsz(stack));
+  return FEDVR_OK;
+}
+
 // Tables of the fourth-order variant for the mesh in w_tau (M points).
 int build_quad4(fedvr_ctx *ctx, int M, double beta) {
   ENSURE(ctx, w_q4coef, (size_t)M * M * sizeof(ConvCoef4));
@@ -428,6 +482,17 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, in
     if (int r = tc_workspace(ctx, n, M, &ws, &S32, &own_err)) return r;
     FEDVR_CK(ctx, sigma2_tc_pre(n, M, V, G, ws, s, !scale, err, scale != nullptr));
     *launches += scale ? 3 : 4;  // splits of g (TF32 path) and V, VQ, W = (VQ) V
+  } else if (ctx->self_energy == 1) {
+    int it = 0;
+    if (int r = gw_solve(ctx, n, M, V, G, S, P<ConvCoef>(ctx->g_coef), P<double>(ctx->g_w),
+                         ctx->gw_w_valid, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
+                         P<double>(ctx->g_vqv), P<double>(ctx->g_c), P<double>(ctx->g_new),
+                         P<unsigned long long>(ctx->g_res), P<double>(ctx->w_dHF), ctx->gw_mixing,
+                         ctx->gw_tol, ctx->gw_max_iter, &it))
+      return r;
+    ctx->gw_w_valid = true;
+    ctx->gw_last_inner = it;
+    *launches += 3 + 6 * it;
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
                               P<double>(ctx->w_t3), s));
@@ -657,7 +722,8 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_coef32, &ctx->w_h16, &ctx->w_xrow, &ctx->w_dens,
                     &ctx->w_q4coef, &ctx->w_q4W, &ctx->w_q4w, &ctx->k_L, &ctx->k_G,
                     &ctx->k_S, &ctx->k_T1, &ctx->k_R, &ctx->k_aux, &ctx->k_out,
-                    &ctx->k_part, &ctx->k_sh, &ctx->k_aop, &ctx->k_o, &ctx->k_flag, &ctx->k_x};
+                    &ctx->k_part, &ctx->k_sh, &ctx->k_aop, &ctx->k_o, &ctx->k_flag, &ctx->k_x,
+                    &ctx->g_w, &ctx->g_vqv, &ctx->g_c, &ctx->g_new, &ctx->g_coef, &ctx->g_res};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -934,6 +1000,8 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   if (int r = check_quad(ctx, precision, M)) return r;
   if (ctx->sigma_init_M && ctx->sigma_init_M != M)
     return fail(ctx, FEDVR_ERR_ARG, "initial Sigma has M = %d, mesh has %d", ctx->sigma_init_M, M);
+  if (ctx->self_energy == 1 && (precision != FEDVR_FP64 || ctx->quad_order != 2))
+    return fail(ctx, FEDVR_ERR_ARG, "GW runs on the FP64 path with the trapezoid rule");
   ctx->prepared = false;
   drop_graph(ctx);
   const size_t nn = (size_t)n * n, stack = (size_t)M * nn;
@@ -965,6 +1033,12 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ctx->M = M;  // the weight accessors below read it
   if (ctx->quad_order == 4) {
     if (int r = build_quad4(ctx, M, beta)) return r;
+  }
+  if (ctx->self_energy == 1) {
+    if (int r = gw_workspace(ctx, n, M)) return r;
+    FEDVR_CK(ctx, launch_conv_coef_bose(M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                                        P<ConvCoef>(ctx->g_coef), s));
+    ctx->gw_w_valid = false;  // the first outer step starts the inner iteration from V Q V
   }
   double *tau = P<double>(ctx->w_tau), *w = P<double>(ctx->w_w);
   const double *eps = P<double>(ctx->b_eps), *C = P<double>(ctx->b_C);
@@ -1035,13 +1109,14 @@ int fedvr_2b_step(fedvr_ctx *ctx, double mixing, const double *G_in, int in_on_d
   if (warm && ctx->warm_inner > 0) mixing = 1.0;  // full Dyson step at the fixed warm-start Sigma
   int launches = 0;
   ctx->last_step_graph = false;
-  if (ctx->use_graphs && !warm) {
+  // the GW inner iteration reads its residual on the host: no graph capture
+  if (ctx->use_graphs && !warm && ctx->self_energy == 0) {
     if (ctx->step_graph && ctx->graph_mixing != mixing) drop_graph(ctx);
     if (!ctx->step_graph) {
       if (int r = capture_step(ctx, mixing)) return r;
     }
   }
-  if (ctx->step_graph && !warm) {
+  if (ctx->step_graph && !warm && ctx->self_energy == 0) {
     FEDVR_CK(ctx, cudaGraphLaunch(ctx->step_graph, s));
     launches = ctx->graph_launches;
     ctx->last_step_graph = true;
@@ -1087,6 +1162,66 @@ int fedvr_set_mu(fedvr_ctx *ctx, double mu) {
   ctx->prepared = false;  // g^0 and the second convolution's table depend on mu
   drop_graph(ctx);
   return FEDVR_OK;
+}
+
+int fedvr_set_self_energy(fedvr_ctx *ctx, int kind, double w_mixing, double w_tol,
+                          int w_max_iter) {
+  CHECK_CTX(ctx);
+  if (kind != 0 && kind != 1) return fail(ctx, FEDVR_ERR_ARG, "self-energy kind must be 0 or 1");
+  if (kind == 1 && (!(w_mixing > 0.0 && w_mixing <= 1.0) || !(w_tol > 0.0) || !is_fin(w_tol) ||
+                    w_max_iter < 1))
+    return fail(ctx, FEDVR_ERR_ARG, "GW needs 0 < w_mixing <= 1, w_tol > 0, w_max_iter >= 1");
+  ctx->self_energy = kind;
+  if (kind == 1) {
+    ctx->gw_mixing = w_mixing;
+    ctx->gw_tol = w_tol;
+    ctx->gw_max_iter = w_max_iter;
+  }
+  ctx->prepared = false;  // a prepared run's tables belong to the old self-energy
+  drop_graph(ctx);
+  return FEDVR_OK;
+}
+
+int fedvr_gw_last_inner(const fedvr_ctx *ctx, int *iters) {
+  if (!ctx || !iters) return FEDVR_ERR_ARG;
+  *iters = ctx->gw_last_inner;
+  return FEDVR_OK;
+}
+
+int fedvr_sigma_gw(fedvr_ctx *ctx, int n, double beta, int u, int p, double spin, const double *V,
+                   const double *G, double *Sigma, double *w_io, int w_valid, double w_mixing,
+                   double w_tol, int w_max_iter, int *iters) {
+  CHECK_CTX(ctx);
+  if (int r = check_mesh_args(ctx, beta, u, p)) return r;
+  if (n < 1 || n > 1024 || !V || !G || !Sigma || !is_fin(spin) || spin < 0.0)
+    return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 1024, spin >= 0 and device buffers");
+  if (!(w_mixing > 0.0 && w_mixing <= 1.0) || !(w_tol > 0.0) || w_max_iter < 1 ||
+      (w_valid && !w_io))
+    return fail(ctx, FEDVR_ERR_ARG, "GW needs 0 < w_mixing <= 1, w_tol > 0, w_max_iter >= 1");
+  ctx->prepared = false;  // the workspace below is shared with a prepared run
+  drop_graph(ctx);
+  if (int r = build_mesh(ctx, beta, u, p, false)) return r;
+  const int M = 2 * u * p + 1;
+  const size_t stack = (size_t)M * n * n;
+  if (int r = gw_workspace(ctx, n, M)) return r;
+  ENSURE(ctx, w_dHF, dsz((size_t)n * n));
+  cudaStream_t s = ctx->stream;
+  FEDVR_CK(ctx, launch_conv_coef_bose(M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                                      P<ConvCoef>(ctx->g_coef), s));
+  double *w = P<double>(ctx->g_w);
+  if (w_valid) FEDVR_CK(ctx, cudaMemcpyAsync(w, w_io, dsz(stack), cudaMemcpyDeviceToDevice, s));
+  const double spin0 = ctx->spin;
+  ctx->spin = spin;
+  int it = 0;
+  int r = gw_solve(ctx, n, M, V, G, Sigma, P<ConvCoef>(ctx->g_coef), w, w_valid != 0,
+                   P<double>(ctx->w_t1), P<double>(ctx->w_t2), P<double>(ctx->g_vqv),
+                   P<double>(ctx->g_c), P<double>(ctx->g_new), P<unsigned long long>(ctx->g_res),
+                   P<double>(ctx->w_dHF), w_mixing, w_tol, w_max_iter, &it);
+  ctx->spin = spin0;
+  if (r) return r;
+  if (w_io) FEDVR_CK(ctx, cudaMemcpyAsync(w_io, w, dsz(stack), cudaMemcpyDeviceToDevice, s));
+  if (iters) *iters = it;
+  return sync(ctx);
 }
 
 int fedvr_set_quadrature(fedvr_ctx *ctx, int order) {

@@ -333,7 +333,36 @@ __global__ void coef_kernel(int M, double beta, const double *tau, const double 
   coef[idx] = c;
 }
 
+// Periodic (bosonic) convolution coefficients for every (i, j), the lag
+// tau_i - tau_j taken as is for j >= i (lag 0 at i = j: the last mesh point)
+// and shifted by -beta for j < i; c1 = w_j (1 - t), c2 = w_j t, no diagonal
+// special case (a periodic function has no jump at lag 0).
+__global__ void coef_bose_kernel(int M, double beta, const double *tau, const double *w,
+                                 ConvCoef *coef) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)M * M) return;
+  int i = (int)(idx / M), j = (int)(idx % M);
+  double x = sub(tau[i], tau[j]);
+  double y = (j >= i) ? x : sub(x, beta);
+  int lo = 0, hi = M - 1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (tau[mid] <= y) lo = mid; else hi = mid;
+  }
+  double t = dv(sub(y, tau[lo]), sub(tau[lo + 1], tau[lo]));
+  ConvCoef c;
+  c.k = lo; c.diag = 0; c.c1 = mul(w[j], sub(1.0, t)); c.c2 = mul(w[j], t);
+  coef[idx] = c;
+}
+
 }  // namespace
+
+cudaError_t launch_conv_coef_bose(int M, double beta, const double *tau, const double *w,
+                                  ConvCoef *coef, cudaStream_t s) {
+  long mm = (long)M * M;
+  coef_bose_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(M, beta, tau, w, coef);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gll(int order, double *xi, double *om, int *status, cudaStream_t s) {
   gll_kernel<<<1, 256, 0, s>>>(order, xi, om, status);

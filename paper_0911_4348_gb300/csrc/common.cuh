@@ -69,6 +69,12 @@ struct fedvr_ctx {
   // quadrature of the Dyson integrals: 2 = split trapezoid with linear lag
   // interpolation (default), 4 = the fourth-order variant (FP64 path)
   int quad_order = 2;
+  // correlation self-energy: 0 second Born, 1 GW (FP64 path); the screened
+  // interaction's damped inner iteration and its state across outer steps
+  int self_energy = 0;
+  double gw_mixing = 0.3, gw_tol = 1e-12;
+  int gw_max_iter = 500, gw_last_inner = 0;
+  bool gw_w_valid = false;
   // history of the last solve_2b: iter, res, E0, N, ms
   std::vector<double> history;
   // last real-time propagation: time points and n (0: none), stage times and
@@ -91,6 +97,8 @@ struct fedvr_ctx {
       w_xrow, w_dens, w_q4coef, w_q4W, w_q4w;
   // real-time propagation: two-time L and Gt, self-energy row, scratch, outputs
   fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part, k_sh, k_aop, k_o, k_flag, k_x;
+  // GW: screened interaction w, V Q V, convolution and update scratch, periodic table, flag
+  fedvr::DevBuf g_w, g_vqv, g_c, g_new, g_coef, g_res;
 };
 
 namespace fedvr {
@@ -176,6 +184,14 @@ cudaError_t launch_phi_table(int n, int M, double beta, const double *eps, const
 // sigma2.cu (FP64 path)
 cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double *G,
                         double *Sigma, double *Q, double *T1, double *W, cudaStream_t s);
+// GW pieces: the bubble Q_j = g_j o g_{M-1-j} and V Q_j V; Sigma = spin g o w.
+cudaError_t gw_bubble(int n, int M, const double *V, const double *G, double *Q, double *T1,
+                      double *VQV, cudaStream_t s);
+cudaError_t launch_gw_sigma(long count, double spin, const double *G, const double *w,
+                            double *Sigma, cudaStream_t s);
+// basis.cu: periodic convolution coefficients (every (i, j), no diagonal case)
+cudaError_t launch_conv_coef_bose(int M, double beta, const double *tau, const double *w,
+                                  ConvCoef *coef, cudaStream_t s);
 
 // tmap.cu: 3-D TMA map over [M][n][ld] floats, box 32 x rows x 1, 128B swizzle,
 // rows beyond n read as zero.

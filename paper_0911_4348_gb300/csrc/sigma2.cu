@@ -100,7 +100,34 @@ __global__ void __launch_bounds__(256) exchange_fp64_kernel(int n, int M, int ro
   }
 }
 
+// Sigma^GW = spin g o w (elementwise over the stack).
+__global__ void gw_sigma_kernel(long count, double spin, const double *__restrict__ G,
+                                const double *__restrict__ w, double *__restrict__ Sigma) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  Sigma[idx] = spin * G[idx] * w[idx];
+}
+
 }  // namespace
+
+cudaError_t gw_bubble(int n, int M, const double *V, const double *G, double *Q, double *T1,
+                      double *VQV, cudaStream_t s) {
+  long nn = (long)n * n;
+  long tot = (long)M * nn;
+  polarisation_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, M, G, Q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // T1_j = Q_j V ; VQV_j = V T1_j
+  e = dgemm(false, false, n, n, n, 1.0, Q, n, nn, V, n, 0, nullptr, 0, 0.0, T1, n, nn, M, s);
+  if (e != cudaSuccess) return e;
+  return dgemm(false, false, n, n, n, 1.0, V, n, 0, T1, n, nn, nullptr, 0, 0.0, VQV, n, nn, M, s);
+}
+
+cudaError_t launch_gw_sigma(long count, double spin, const double *G, const double *w,
+                            double *Sigma, cudaStream_t s) {
+  gw_sigma_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, spin, G, w, Sigma);
+  return cudaGetLastError();
+}
 
 cudaError_t sigma2_fp64(int n, int M, double spin, const double *V, const double *G,
                         double *Sigma, double *Q, double *T1, double *W, cudaStream_t s) {
