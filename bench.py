@@ -798,6 +798,8 @@ def main():
                     help="time steps of one propagation of the kbe workload")
     ap.add_argument("--kbe-precision", choices=("fp64", "tf32"), default="fp64",
                     help="kbe workload: collision integrals in FP64 or as split-TF32 products")
+    ap.add_argument("--self-energy", choices=("2b", "gw"), default="2b",
+                    help="correlation self-energy of the Matsubara iteration (gw: FP64 path)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -829,8 +831,16 @@ def main():
     ctx.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
     E_hf, _ = ctx.solve_hf(sys_.beta, tol=1e-12)
     ctx.use_graphs(not args.no_graphs)
+    gw = args.self_energy == "gw"
+    if gw:
+        if prec != 0:
+            raise SystemExit("--self-energy gw runs on the FP64 path: add --precision fp64")
+        ctx.set_self_energy("gw")
+        args.no_fp64_compare = True   # the FP64 path is the one timed
+        args.no_cpu_baseline = True   # the oracle sample below is second Born's
     ctx.prepare_2b(sys_.beta, sys_.u, sys_.p, prec)
     n, M = sys_.n_b, sys_.n_tau
+    inner = []
 
     for _ in range(args.warmup):
         ctx.step_2b(sys_.mixing)
@@ -857,6 +867,8 @@ def main():
         ctx.step_2b(sys_.mixing)
         st, nl = ctx.stage_times()
         launches += nl
+        if gw:
+            inner.append(ctx.gw_last_inner())
         for k, v in st.items():
             stage_ms.setdefault(k, []).append(v)
     ev1.record(stream)
@@ -883,6 +895,8 @@ def main():
 
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     dom = max(("sigma2", "conv1", "conv2"), key=lambda k: avg.get(k, 0.0))
+    if gw:
+        dom = "sigma2"  # the screened interaction's periodic convolutions
     peaks = load_peaks()
     if prec == 0:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -907,7 +921,10 @@ def main():
         else:
             peak = base / 2.0
             bound, punit, psrc = "tensor", "TFLOP/s", f"measured bf16 {kind} x 1/2 (tf32 ratio)"
-    achieved = algorithmic(dom, n, M) / (avg[dom] / 1000.0) / 1e12
+    dom_flops = algorithmic(dom, n, M)
+    if gw:  # one periodic convolution (2 M^2 n^3) per inner iteration
+        dom_flops = float(np.mean(inner)) * algorithmic("conv1", n, M)
+    achieved = dom_flops / (avg[dom] / 1000.0) / 1e12
     # keys of profiles/ncu_traffic.json: the kernel of the stage in this precision
     kernel_name = {("conv1", "f16"): "conv1_f16_kernel", ("conv1", "tf32"): "conv1_tc_kernel",
                    ("sigma2", "f16"): "exchange_tc_kernel<f16>",
@@ -915,8 +932,11 @@ def main():
     traffic = measured_traffic(kernel_name, sys_.name) if (prec != 0 and kernel_name) else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
             "frac": achieved / peak, "traffic": traffic, "kernel": dom,
-            "algorithmic_flops_per_launch": algorithmic(dom, n, M), "peak_source": psrc,
+            "algorithmic_flops_per_launch": dom_flops, "peak_source": psrc,
             "stage_ms": avg}
+    if gw:
+        roof["kernel"] = "GW screened interaction (conv1_fp64_kernel, periodic table)"
+        roof["gw_inner_iterations_mean"] = float(np.mean(inner))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
@@ -925,17 +945,20 @@ def main():
            "data": "synthetic",
            "config": {"workload": sys_.name, "n_b": n, "n_tau": M, "beta": sys_.beta,
                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                      "self_energy": args.self_energy,
                       "graphs": ctx.use_graphs(), "conv1_splits": ctx.conv1_splits(),
                       "l2": "inputs larger than L2 (g stack %.0f MB)" % (M * n * n * 8 / 1e6)},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
            "E_hf": E_hf, "precision_by_stage": PRECISION_BY_STAGE[args.precision if prec else "fp64"]}
 
-    E_ref = golden_E_ref(sys_.name)
+    E_ref = None if gw else golden_E_ref(sys_.name)
     if not args.no_time_to_e0:
         # time to a converged E0 through the public API (prepare included):
         # E_ref is the FP64 oracle's converged E0 where it is stored, else this
         # run's own converged value
         ctx2 = _context(stream, sys_)
+        if gw:
+            ctx2.set_self_energy("gw")
         run = _timed_solve(ctx2, sys_, prec, sys_.tol, 200)
         ref = E_ref if E_ref is not None else run["E"][-1]
         k = _first_within(run["E"], ref)
