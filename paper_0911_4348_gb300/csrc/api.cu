@@ -124,6 +124,13 @@ int build_mesh(fedvr_ctx *ctx, double beta, int u, int p, bool coef) {
   return FEDVR_OK;
 }
 
+// Scratch of the FP64 first convolution's mesh-range splits (small launches).
+int ensure_c1f(fedvr_ctx *ctx, int n, int M) {
+  const int sp = conv1_fp64_splits(n, M);
+  ENSURE(ctx, w_c1f, dsz((size_t)(sp > 1 ? sp - 1 : 1) * M * n * n));
+  return FEDVR_OK;
+}
+
 // GW screened interaction of g and Sigma^GW = spin g o w: the damped fixed-point
 // iteration w <- (1 - a) w + a (V Q V - spin V (Q * w)) from w (V Q V when
 // !w_valid) until max|w_new - w| < tol, with Q * w the periodic convolution of
@@ -142,7 +149,7 @@ int gw_solve(fedvr_ctx *ctx, int n, int M, const double *V, const double *G, dou
   double r = 0.0;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
-    FEDVR_CK(ctx, conv1_fp64(n, M, coef, dummy, Q, w, C, s));
+    FEDVR_CK(ctx, conv1_fp64(n, M, coef, dummy, Q, w, C, s, P<double>(ctx->w_c1f)));
     FEDVR_CK(ctx, launch_copy(stack, VQV, Nw, s));
     FEDVR_CK(ctx, dgemm(false, false, n, n, n, -ctx->spin, V, n, 0, C, n, nn, nullptr, 0, 1.0, Nw,
                         n, nn, M, s));
@@ -175,7 +182,7 @@ int gw_workspace(fedvr_ctx *ctx, int n, int M) {
   ENSURE(ctx, g_res, 16);
   ENSURE(ctx, w_t1, dsz(stack));
   ENSURE(ctx, w_t2, dsz(stack));
-  return FEDVR_OK;
+  return ensure_c1f(ctx, n, M);
 }
 
 // Tables of the fourth-order variant for the mesh in w_tau (M points).
@@ -530,17 +537,21 @@ int phase_mid(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
 
 // (3) FP64 first convolution (the split path launches its tensor-core kernel instead).
 int phase_conv1_fp64(fedvr_ctx *ctx, cudaStream_t s, int *launches) {
+  const int extra = conv1_fp64_splits(ctx->n, ctx->M) > 1 ? 1 : 0;  // the split sum
   if (ctx->quad_order == 4) {
     FEDVR_CK(ctx, conv1_fp64_q4(ctx->n, ctx->M, P<ConvCoef4>(ctx->w_q4coef), P<double>(ctx->w_dHF),
-                                P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s));
-    *launches += 1;
+                                P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s,
+                                P<double>(ctx->w_c1f)));
+    *launches += 1 + extra;
     return FEDVR_OK;
   }
   FEDVR_CK(ctx, conv1_fp64(ctx->n, ctx->M, P<ConvCoef>(ctx->w_coef), P<double>(ctx->w_dHF),
-                           P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s));
-  *launches += 1;
+                           P<double>(ctx->w_S), P<double>(ctx->w_G), P<double>(ctx->w_I1), s,
+                           P<double>(ctx->w_c1f)));
+  *launches += 1 + extra;
   return FEDVR_OK;
 }
+
 
 // (4) second convolution.
 int phase_conv2(fedvr_ctx *ctx, cudaStream_t s, int *launches, int *err) {
@@ -723,7 +734,8 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->w_q4coef, &ctx->w_q4W, &ctx->w_q4w, &ctx->k_L, &ctx->k_G,
                     &ctx->k_S, &ctx->k_T1, &ctx->k_R, &ctx->k_aux, &ctx->k_out,
                     &ctx->k_part, &ctx->k_sh, &ctx->k_aop, &ctx->k_o, &ctx->k_flag, &ctx->k_x,
-                    &ctx->g_w, &ctx->g_vqv, &ctx->g_c, &ctx->g_new, &ctx->g_coef, &ctx->g_res};
+                    &ctx->g_w, &ctx->g_vqv, &ctx->g_c, &ctx->g_new, &ctx->g_coef, &ctx->g_res,
+                    &ctx->w_c1f};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -1019,6 +1031,9 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   ENSURE(ctx, w_dHF, dsz(nn));
   ENSURE(ctx, w_part, dsz(4 * (size_t)M + 3 * (size_t)n));  // launch_energy's partials
   ENSURE(ctx, w_red, dsz(8));
+  if (!is_split(precision)) {
+    if (int r = ensure_c1f(ctx, n, M)) return r;
+  }
   if (is_split(precision)) {
     float *ws, *S32;
     int *err;
@@ -1897,10 +1912,14 @@ int fedvr_conv_sigma_g(fedvr_ctx *ctx, int n, double beta, int u, int p, const d
   if (ctx->quad_order == 4) {
     if (int r = check_quad(ctx, precision, M)) return r;
     if (int r = build_quad4(ctx, M, beta)) return r;
-    FEDVR_CK(ctx, conv1_fp64_q4(n, M, P<ConvCoef4>(ctx->w_q4coef), dHF, Sigma, G, I1, ctx->stream));
+    if (int r = ensure_c1f(ctx, n, M)) return r;
+    FEDVR_CK(ctx, conv1_fp64_q4(n, M, P<ConvCoef4>(ctx->w_q4coef), dHF, Sigma, G, I1, ctx->stream,
+                                P<double>(ctx->w_c1f)));
     return FEDVR_OK;
   }
-  FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), dHF, Sigma, G, I1, ctx->stream));
+  if (int r = ensure_c1f(ctx, n, M)) return r;
+  FEDVR_CK(ctx, conv1_fp64(n, M, P<ConvCoef>(ctx->w_coef), dHF, Sigma, G, I1, ctx->stream,
+                           P<double>(ctx->w_c1f)));
   return FEDVR_OK;
 }
 

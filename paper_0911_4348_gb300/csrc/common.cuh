@@ -99,6 +99,8 @@ struct fedvr_ctx {
   fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part, k_sh, k_aop, k_o, k_flag, k_x;
   // GW: screened interaction w, V Q V, convolution and update scratch, periodic table, flag
   fedvr::DevBuf g_w, g_vqv, g_c, g_new, g_coef, g_res;
+  // partial stacks of the FP64 first convolution's mesh-range splits (small launches)
+  fedvr::DevBuf w_c1f;
 };
 
 namespace fedvr {
@@ -214,10 +216,15 @@ cudaError_t launch_sigma_to_f32(int n, int M, const double *S, float *S32, cudaS
                                 unsigned *smax = nullptr);
 
 // conv.cu
+// part (may be NULL: one CTA per row tile and mesh point): scratch of
+// (conv1_fp64_splits(n, M) - 1) M n n doubles that lets a small launch split
+// the mesh-point range over more CTAs (partial sums added in split order).
+int conv1_fp64_splits(int n, int M);
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
-                       const double *G, double *I1, cudaStream_t s);
+                       const double *G, double *I1, cudaStream_t s, double *part = nullptr);
 cudaError_t conv1_fp64_q4(int n, int M, const ConvCoef4 *coef, const double *dHF,
-                          const double *A, const double *G, double *I1, cudaStream_t s);
+                          const double *A, const double *G, double *I1, cudaStream_t s,
+                          double *part = nullptr);
 // W (may be NULL): per-(i, j) weights replacing w_j (fourth-order variant;
 // wm, wp are then its end weights wL, wR).
 cudaError_t launch_conv2_kernel(int n, int M, double beta, const double *tau, const double *w,

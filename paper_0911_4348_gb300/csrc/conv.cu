@@ -55,20 +55,24 @@ __device__ __forceinline__ CoefView coef_view(const ConvCoef4 &cf, int M) {
   return v;
 }
 
-// First convolution, FP64. CTA (row tile, i): its rows x n outputs of I1_i are
-// spread over the 256 threads at up to kC1Q per thread (output o = tid + 256 q,
-// row a0 + o / n, column o % n), so no output is padded; for each j and each
-// 16-wide slice of c it stages B_ij[a][c] (the interpolated Sigma^corr, built
-// from up to four rows) [rows][16] and g_j[c][b] [16][n] in shared memory. Each
-// output adds its terms in the order j, c.
+// First convolution, FP64. CTA (row tile, i, split): its rows x n outputs of
+// I1_i are spread over the 256 threads at up to kC1Q per thread (output
+// o = tid + 256 q, row a0 + o / n, column o % n), so no output is padded; for
+// each j of its share of the mesh-point range and each 16-wide slice of c it
+// stages B_ij[a][c] (the interpolated Sigma^corr, built from up to four rows)
+// [rows][16] and g_j[c][b] [16][n] in shared memory. Each output adds its terms
+// in the order j, c. With splits > 1 (small launches) split k takes
+// j in [M k / S, M (k + 1) / S), split 0 writes I1 and split k > 0 the partial
+// stack part + (k - 1) M n n, added to I1 in split order afterwards.
 constexpr int kC1Q = 8, kC1K = 16;
 template <typename Coef>
-__global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M, int rows,
+__global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M, int rows, int splits,
                                                          const Coef *__restrict__ coef,
                                                          const double *__restrict__ dHF,
                                                          const double *__restrict__ A,
                                                          const double *__restrict__ G,
-                                                         double *__restrict__ I1) {
+                                                         double *__restrict__ I1,
+                                                         double *__restrict__ part) {
   extern __shared__ double c1s[];
   double *Xs = c1s, *Ys = c1s + rows * kC1K;
   const int i = blockIdx.y, a0 = blockIdx.x * rows;
@@ -86,7 +90,9 @@ __global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M, int rows,
     yo[q] = o < nout ? o % n : 0;
     nq += o < nout ? 1 : 0;
   }
-  for (int j = 0; j < M; ++j) {
+  const int sp = blockIdx.z;
+  const int j0 = (int)((long)M * sp / splits), j1 = (int)((long)M * (sp + 1) / splits);
+  for (int j = j0; j < j1; ++j) {
     const CoefView cv = coef_view(coef[(long)i * M + j], M);
     const double *g = G + (long)j * nn;
     for (int c0 = 0; c0 < n; c0 += kC1K) {
@@ -114,27 +120,44 @@ __global__ void __launch_bounds__(256) conv1_fp64_kernel(int n, int M, int rows,
       __syncthreads();
     }
   }
+  double *out = sp == 0 ? I1 : part + (long)(sp - 1) * M * nn;
 #pragma unroll
   for (int q = 0; q < kC1Q; ++q) {
     if (q >= nq) break;
     const int o = tid + 256 * q;
-    I1[(long)i * nn + (long)(a0 + o / n) * n + o % n] = acc[q];
+    out[(long)i * nn + (long)(a0 + o / n) * n + o % n] = acc[q];
   }
+}
+
+// I1 += the partial stacks of splits 1 .. parts, in split order.
+__global__ void c1_fp64_reduce_kernel(long count, int parts, const double *__restrict__ part,
+                                      double *__restrict__ I1) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  double v = I1[e];
+  for (int k = 0; k < parts; ++k) v += part[(long)k * count + e];
+  I1[e] = v;
 }
 
 inline int c1_rows(int n) { return n < 256 * kC1Q / n ? n : 256 * kC1Q / n; }
 
 template <typename Coef>
 cudaError_t launch_conv1_fp64(int n, int M, const Coef *coef, const double *dHF, const double *A,
-                              const double *G, double *I1, cudaStream_t s) {
+                              const double *G, double *I1, double *part, cudaStream_t s) {
   const int rows = c1_rows(n);
   if (rows < 1) return cudaErrorInvalidValue;
   const size_t sm = (size_t)(rows * kC1K + kC1K * n) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(conv1_fp64_kernel<Coef>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((n + rows - 1) / rows), (unsigned)M);
-  conv1_fp64_kernel<Coef><<<grid, 256, sm, s>>>(n, M, rows, coef, dHF, A, G, I1);
+  const int tiles = (n + rows - 1) / rows;
+  const int splits = part ? conv1_fp64_splits(n, M) : 1;
+  dim3 grid((unsigned)tiles, (unsigned)M, (unsigned)splits);
+  conv1_fp64_kernel<Coef><<<grid, 256, sm, s>>>(n, M, rows, splits, coef, dHF, A, G, I1, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const long count = (long)M * n * n;
+  c1_fp64_reduce_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, splits - 1, part, I1);
   return cudaGetLastError();
 }
 
@@ -346,15 +369,25 @@ cudaError_t conv2_apply_f32(int n, int M, const float *K32, const double *C, con
   return conv2_tc(n, M, K32, C, I1, I2, t1, t2, err, s);
 }
 
+int conv1_fp64_splits(int n, int M) {
+  // about four CTAs per SM of a 152-SM GPU, at most 8 splits of the mesh-point range
+  const int rows = c1_rows(n);
+  const long ctas = (long)((n + rows - 1) / rows) * M;
+  long sp = (608 + ctas - 1) / ctas;
+  sp = sp < 1 ? 1 : (sp > 8 ? 8 : sp);
+  return (int)(sp > M ? M : sp);
+}
+
 cudaError_t conv1_fp64(int n, int M, const ConvCoef *coef, const double *dHF, const double *A,
-                       const double *G, double *I1, cudaStream_t s) {
-  return launch_conv1_fp64<ConvCoef>(n, M, coef, dHF, A, G, I1, s);
+                       const double *G, double *I1, cudaStream_t s, double *part) {
+  return launch_conv1_fp64<ConvCoef>(n, M, coef, dHF, A, G, I1, part, s);
 }
 
 cudaError_t conv1_fp64_q4(int n, int M, const ConvCoef4 *coef, const double *dHF,
-                          const double *A, const double *G, double *I1, cudaStream_t s) {
+                          const double *A, const double *G, double *I1, cudaStream_t s,
+                          double *part) {
   if (M < 4) return cudaErrorInvalidValue;
-  return launch_conv1_fp64<ConvCoef4>(n, M, coef, dHF, A, G, I1, s);
+  return launch_conv1_fp64<ConvCoef4>(n, M, coef, dHF, A, G, I1, part, s);
 }
 
 cudaError_t launch_quad4_tables(int M, double beta, const double *tau, ConvCoef4 *coef,
