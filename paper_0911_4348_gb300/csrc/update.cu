@@ -120,14 +120,18 @@ __global__ void energy_part_kernel(int n, int M, const double *__restrict__ G,
   const long lo = nn * c / kE, hi = nn * (c + 1) / kE;
   const double *g = G + (long)j * nn;
   const double *s = A + (long)(M - 1 - j) * nn;
-  double acc0 = 0.0, acc1 = 0.0;
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
   long e = lo + threadIdx.x;
-  for (; e + 256 < hi; e += 512) {  // two independent loads in flight per thread
-    acc0 = fma(s[e], g[e], acc0);
-    acc1 = fma(s[e + 256], g[e + 256], acc1);
+  for (; e + 768 < hi; e += 1024) {  // four independent load pairs in flight per thread
+    const double s0 = s[e], s1 = s[e + 256], s2 = s[e + 512], s3 = s[e + 768];
+    const double g0 = g[e], g1 = g[e + 256], g2 = g[e + 512], g3 = g[e + 768];
+    acc0 = fma(s0, g0, acc0);
+    acc1 = fma(s1, g1, acc1);
+    acc2 = fma(s2, g2, acc2);
+    acc3 = fma(s3, g3, acc3);
   }
-  if (e < hi) acc0 = fma(s[e], g[e], acc0);
-  const double acc = block_sum256(acc0 + acc1);
+  for (; e < hi; e += 256) acc0 = fma(s[e], g[e], acc0);
+  const double acc = block_sum256((acc0 + acc1) + (acc2 + acc3));
   if (threadIdx.x == 0) part[(long)j * kE + c] = acc;
 }
 
