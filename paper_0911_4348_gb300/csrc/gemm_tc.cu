@@ -26,6 +26,10 @@
 // largest group among its rows (a block-triangular B: the rows of group g need
 // k < (g + 1) k_tri); a tile whose slice lies beyond that writes zeros.
 //
+// Producers take one row of A and 16 consecutive k per thread; in MC mode the 32
+// lanes of a warp hold 32 consecutive rows, so every load instruction is
+// coalesced along the rows.
+//
 // One CTA per 128 x Nt output tile (Nt <= 256, a multiple of 16): warps 0-3
 // drain TMEM, warps 4-11 load, convert, split and store both operands of a
 // 32-wide k chunk into the K-major 128-byte-swizzled stage layout, warp 12
@@ -196,29 +200,22 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
       const TA *A = reinterpret_cast<const TA *>(p.A) + (long)z * p.a_sz;
       const TA *A2 = reinterpret_cast<const TA *>(p.A2);
       const TB *B = reinterpret_cast<const TB *>(p.B) + (long)z * p.b_sz;
-      // A rows of this thread: MC 16 consecutive rows (one k per lane), KC one row
-      const int ra = A_MC ? (pt >> 5) * 16 : (pt >> 1);
-      const int nra = A_MC ? 16 : 1;
-      int aoff[16], aoff2[16];
-      bool alive[16];
+      // A: one row and 16 consecutive k per thread. MC: warp w takes rows
+      // (w & 3) * 32 + lane and k half w >> 2, so each load instruction reads 32
+      // consecutive rows at one k (rows are contiguous in MC); KC: row pt / 2, k half
+      // pt & 1 (k is contiguous in KC)
+      const int wp = pt >> 5;
+      const int ra = A_MC ? (wp & 3) * 32 + lane : (pt >> 1);
+      const int kh = A_MC ? (wp >> 2) * 16 : (pt & 1) * 16;
+      int aoff0 = 0, aoff20 = 0;
+      bool alive0;
       {
-        int r = row0 + ra;
-        int g = r / p.G, w = r % p.G;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (i < nra) {
-            alive[i] = r < p.R;
-            aoff[i] = alive[i] ? g * p.a_sg + w * (A_MC ? 1 : p.a_sw) : 0;
-            aoff2[i] = (MUL2 && alive[i]) ? (p.nG - 1 - g) * p.a_sg + w : 0;
-            ++r;
-            if (++w == p.G) {
-              w = 0;
-              ++g;
-            }
-          } else {
-            alive[i] = false;
-            aoff[i] = aoff2[i] = 0;
-          }
+        const int r = row0 + ra;
+        const int g = r / p.G, w = r % p.G;
+        alive0 = r < p.R;
+        if (alive0) {
+          aoff0 = g * p.a_sg + w * (A_MC ? 1 : p.a_sw);
+          if (MUL2) aoff20 = (p.nG - 1 - g) * p.a_sg + w;
         }
       }
       // B columns of this thread: MC 32 consecutive local columns (one k per lane),
@@ -228,21 +225,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
         const int k0 = kbeg + kc * 32;
         float av[16], bv[32];
         if (A_MC) {
-          const int k = k0 + lane;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
+            const int k = k0 + kh + i;
             float x = 0.f;
-            if (alive[i] && k < kend) {
-              x = (float)A[aoff[i] + k * p.a_sk];
-              if (MUL2) x *= (float)A2[aoff2[i] + k * p.a_sk];
+            if (alive0 && k < kend) {
+              x = (float)A[aoff0 + k * p.a_sk];
+              if (MUL2) x *= (float)A2[aoff20 + k * p.a_sk];
             }
             av[i] = x;
           }
         } else {
-          const int kb = k0 + (pt & 1) * 16;
+          const int kb = k0 + kh;
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            av[i] = (alive[0] && kb + i < kend) ? (float)A[aoff[0] + kb + i] : 0.f;
+            av[i] = (alive0 && kb + i < kend) ? (float)A[aoff0 + kb + i] : 0.f;
         }
         if (B_MC) {
           const int k = k0 + lane;
@@ -265,13 +262,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tf32x3_kernel(GemmArgs p) {
           break;
         }
         uint8_t *st = smem + s * stage_bytes;
-        if (A_MC) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) put1(st, kTileA, ra + i, lane, av[i]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) put4(st, kTileA, ra, (pt & 1) * 16 + 4 * q, av + 4 * q);
-        }
+        for (int q = 0; q < 4; ++q) put4(st, kTileA, ra, kh + 4 * q, av + 4 * q);
         uint8_t *sb = st + 2 * kTileA;
         if (B_MC) {
 #pragma unroll
