@@ -509,8 +509,10 @@ int fedvr_selftest_wait(fedvr_ctx *ctx, int release, double limit_seconds);
  * split-TF32 tensor-core products (three TF32 products per product, FP32
  * accumulation, about 2^-21 relative per product) over FP32 copies of L, Gt
  * and the weighted L - Gt kept beside the FP64 matrices (3 x 8 (T n_b)^2
- * more bytes; needs T n_b <= 32750); the -i h_HF F term, the energy, the
- * self-energy and the stepping stay FP64.
+ * more bytes; needs T n_b <= 32750); for n_b <= 64 the second-Born
+ * self-energy's exchange products run the same way and its direct term and
+ * exchange k-sum in FP32; the -i h_HF F term, the energy, the HF self-energy
+ * and the stepping stay FP64.
  *
  * rho0: host [n_b][n_b] complex (interleaved re, im; 16 bytes per entry), or
  * NULL for the real HF density rho0 of the last solve_hf. dv: host

@@ -1,6 +1,7 @@
 // Real-time two-time Kadanoff-Baym propagation (Sec. 2, Eqs. kbe, skkbe,
 // skkbesigma with the HF part of Eq. sigmahf and the second-Born part of Eq.
-// sigma2ndb), from an uncorrelated initial state, in complex FP64.
+// sigma2ndb), from an uncorrelated initial state: complex FP64, or with the
+// dense contractions as split-TF32 tensor-core products (precision 1, below).
 //
 // Functions and layout. L = -i G^< and Gt = -i G^> (so L(t, t) = rho(t),
 // Gt(t, t) = rho(t) - 1, F(t', t) = F(t, t')^H) on the uniform grid
@@ -36,11 +37,12 @@
 // s <= j, block-triangular in (s, j)). The left factors of both integrals are
 // laid out as real [2n][2 T n] matrices (rows re/im of the output, columns
 // (s, p, b)) that turn each complex product into one real product. The
-// -i h_HF F term, the energy's K_L(t, t), the self-energy and the stepping stay
-// in FP64. In the same mode (n_b <= 64) the exchange term's products
-// P^(b)_ak = sum_l g_al V_bl gb_lk of all entries of a row run as one batched
-// split-TF32 product, and the exchange's k-sum and the direct term V Q V run in
-// FP32 on the CUDA cores (their inputs carry the products' precision).
+// -i h_HF F term, the energy's K_L(t, t), the HF self-energy and the stepping
+// stay in FP64. For n_b <= 64 the mode also runs the second-Born self-energy
+// row on cheaper arithmetic: the exchange products P^(b)_ak = sum_l g_al V_bl
+// gb_lk of all entries as one batched split-TF32 product, the exchange's k-sum
+// and the direct term V Q V in FP32 on the CUDA cores (their inputs carry the
+// products' precision); for n_b > 64 the self-energy stays FP64.
 #include <algorithm>
 
 #include "common.cuh"
