@@ -298,10 +298,11 @@ int check_precision(fedvr_ctx *ctx, int precision, int n) {
   return fail(ctx, FEDVR_ERR_ARG, "precision %d is not available in this build", precision);
 }
 
-// FP16-split workspace: the hi and lo FP16 stacks of g ([M][n][ld16] each),
-// then the operand scales. NULL pointers when the context is not in that mode.
+// FP16-split workspace: the hi and lo FP16 stacks of g ([M][n][ld16] each) and
+// the first convolution's packed tail, then the operand scales. NULL pointers
+// when the context is not in that mode.
 int f16_workspace(fedvr_ctx *ctx, int n, int M, void **h16, TcScale **scale) {
-  const size_t halves = 2 * (size_t)M * n * ld16_of(n);
+  const size_t halves = f16_split_halves(n, M);
   const size_t off = (halves * 2 + 255) / 256 * 256;
   ENSURE(ctx, w_h16, off + 256);
   *h16 = ctx->w_h16.ptr;

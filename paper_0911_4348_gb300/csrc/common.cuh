@@ -200,6 +200,9 @@ cudaError_t launch_conv_coef_bose(int M, double beta, const double *tau, const d
 cudaError_t make_tmap_rows(CUtensorMap *map, const float *base, int n, int M, int ld, int rows,
                            int box_cols = 32);
 cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, int ld16, int rows);
+// 2-D map over FP16 rows [n][pitch] of `cols` used columns, box 64 halves x rows.
+cudaError_t make_tmap_tail16(CUtensorMap *map, const void *base, int n, int cols, int pitch,
+                             int rows);
 
 // sigma2_tc.cu (tensor cores, split TF32): the split workspace of a system
 // holds 4 * M*n*ld + n*ld floats (g32, gh, gl, VQ, V32; ld = n rounded up to 32).

@@ -506,12 +506,13 @@ __global__ void __launch_bounds__(kThreadsH, 1)
         ia[k] = live[k] ? (int)(r / n) : 0;
         aa[k] = live[k] ? (int)(r % n) : 0;
       }
-      const int JB = S.JB;
+      const int JB = S.JB, TU = S.TU, KCf = TU ? KC - 1 : KC;
       // chunks in the order (accumulation block, 64-wide column slice, mesh point),
-      // the two bracket rows of each row held in registers while the bracket stays
+      // the two bracket rows of each row held in registers while the bracket stays;
+      // with a packed tail the last slice follows as chunks of 8 / TU mesh points
       for (int j0 = it.j_lo; j0 < it.j_hi && !tc::warp_flag(abort_flag); j0 += JB) {
         const int j1 = min(it.j_hi, j0 + JB);
-        for (int kc = 0; kc < KC && !tc::warp_flag(abort_flag); ++kc) {
+        for (int kc = 0; kc < KCf && !tc::warp_flag(abort_flag); ++kc) {
           const int l0 = kc * 64 + 8 * c;
           const bool in = l0 < n;  // units starting past n are zero padding: not fetched
           int k1[2], k2[2];        // S32 rows held in a1, a2 (-1: none)
@@ -582,6 +583,62 @@ __global__ void __launch_bounds__(kThreadsH, 1)
             tc::warp_arrive(&full[s]);
           }
         }
+        if (TU) {
+          // packed tail: unit c holds 8 columns of mesh point jt + c / TU
+          const int jpc = 8 / TU, jo = c / TU;
+          const int l0 = (KC - 1) * 64 + 8 * (c % TU);
+          for (int jt = j0; jt < j1 && !tc::warp_flag(abort_flag); jt += jpc, ++cc) {
+            const int j = jt + jo;
+            const bool jin = jo < jpc && j < j1 && l0 < n;
+            float4 p1[2][2], p2[2][2];
+            float c1[2], c2[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              c1[k] = c2[k] = 0.f;
+              p1[k][0] = p1[k][1] = p2[k][0] = p2[k][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (live[k] && jin) {
+                const int4 cf = coef32[(long)ia[k] * M + j];
+                c1[k] = __int_as_float(cf.z) * fA;
+                c2[k] = __int_as_float(cf.w) * fA;
+                const float *q1 = S32 + (uint32_t)((cf.x * n + aa[k]) * ld + l0);
+                p1[k][0] = *reinterpret_cast<const float4 *>(q1);
+                p1[k][1] = *reinterpret_cast<const float4 *>(q1 + 4);
+                if (cf.y != cf.x) {
+                  const float *q2 = S32 + (uint32_t)((cf.y * n + aa[k]) * ld + l0);
+                  p2[k][0] = *reinterpret_cast<const float4 *>(q2);
+                  p2[k][1] = *reinterpret_cast<const float4 *>(q2 + 4);
+                } else {
+                  p2[k][0] = p1[k][0];
+                  p2[k][1] = p1[k][1];
+                }
+              }
+            }
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::warp_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            uint8_t *st = smem + s * stage_bytes;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const uint64_t C1 = tc::f2_pack(c1[k], c1[k]), C2 = tc::f2_pack(c2[k], c2[k]);
+              const ulonglong2 p1a = *reinterpret_cast<const ulonglong2 *>(&p1[k][0]);
+              const ulonglong2 p1b = *reinterpret_cast<const ulonglong2 *>(&p1[k][1]);
+              const ulonglong2 p2a = *reinterpret_cast<const ulonglong2 *>(&p2[k][0]);
+              const ulonglong2 p2b = *reinterpret_cast<const ulonglong2 *>(&p2[k][1]);
+              uint4 hi, lo;
+              tc::f16_split2p(tc::f2_fma(C1, p1a.x, tc::f2_mul(C2, p2a.x)), hi.x, lo.x);
+              tc::f16_split2p(tc::f2_fma(C1, p1a.y, tc::f2_mul(C2, p2a.y)), hi.y, lo.y);
+              tc::f16_split2p(tc::f2_fma(C1, p1b.x, tc::f2_mul(C2, p2b.x)), hi.z, lo.z);
+              tc::f16_split2p(tc::f2_fma(C1, p1b.y, tc::f2_mul(C2, p2b.y)), hi.w, lo.w);
+              *reinterpret_cast<uint4 *>(st + off[k]) = hi;
+              *reinterpret_cast<uint4 *>(st + kTileA + off[k]) = lo;
+            }
+            tc::fence_smem_to_async();
+            tc::warp_arrive(&full[s]);
+          }
+        }
       }
     }
   } else if (warp == 20) {
@@ -595,10 +652,10 @@ __global__ void __launch_bounds__(kThreadsH, 1)
         const uint32_t bytes = 2u * (uint32_t)S.g.Np * 128u;
         const int NT = S.g.NT, KC = (S.g.n + 63) / 64, n00 = S.g.n0[0], n01 = S.g.n0[1];
         const CUtensorMap *th0 = &S.hh[0], *th1 = &S.hh[1], *tl0 = &S.hl[0], *tl1 = &S.hl[1];
-        const int JB = S.JB;
+        const int JB = S.JB, TU = S.TU, KCf = TU ? KC - 1 : KC;
         for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB) {
           const int j1 = min(it.j_hi, j0 + JB);
-          for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
+          for (int kc = 0; kc < KCf && !*abort_flag; ++kc) {
             for (int j = j0; j < j1; ++j, ++cc) {
               const int s = cc & 1;
               const uint32_t use = cc >> 1;
@@ -615,6 +672,22 @@ __global__ void __launch_bounds__(kThreadsH, 1)
               }
             }
           }
+          // packed tail: columns jt 8 TU .. + 63 (16-byte aligned; past the end zero-filled)
+          for (int jt = j0; TU && jt < j1 && !*abort_flag; jt += 8 / TU, ++cc) {
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            uint8_t *st = smem + s * stage_bytes + 2 * kTileA;
+            tc::mbar_arrive_expect_tx(&full[s], bytes);
+            for (int nt = 0; nt < NT; ++nt) {
+              const int r = nt ? n01 : n00;
+              tc::tma_load_2d(st + r * 128, &S.th16[nt], jt * 8 * TU, r, &full[s]);
+              tc::tma_load_2d(st + tileB + r * 128, &S.tl16[nt], jt * 8 * TU, r, &full[s]);
+            }
+          }
         }
       }
     }
@@ -626,7 +699,8 @@ __global__ void __launch_bounds__(kThreadsH, 1)
         while (cur + 1 < n_sys && w >= prefix[cur + 1]) ++cur;
         const C1Sys &S = sys[cur];
         const C1Item it = c1_item(S, w - prefix[cur]);
-        const int n = S.g.n, KC = (n + 63) / 64, NT = S.g.NT, JB = S.JB;
+        const int n = S.g.n, KC = (n + 63) / 64, NT = S.g.NT, JB = S.JB, TU = S.TU;
+        const int KCf = TU ? KC - 1 : KC;
         const uint32_t n00 = (uint32_t)S.g.n0[0], n01 = (uint32_t)S.g.n0[1];
         const uint32_t id0 = tc::idesc_f16(128, S.g.nsz[0]), id1 = tc::idesc_f16(128, S.g.nsz[1]);
         for (int j0 = it.j_lo; j0 < it.j_hi && !*abort_flag; j0 += JB, ++tcount) {
@@ -644,36 +718,43 @@ __global__ void __launch_bounds__(kThreadsH, 1)
           }
           tc::fence_after_sync();
           const uint32_t dbase = tmem + (nbuf == 2 ? (uint32_t)(buf * 256) : 0u);
-          for (int kc = 0; kc < KC && !*abort_flag; ++kc) {
-            const int ksteps = min(4, (n - kc * 64 + 15) / 16);
-            for (int j = j0; j < j1; ++j, ++cc) {
-              const int s = cc & 1;
-              const uint32_t use = cc >> 1;
-              if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
-                *abort_flag = 1;
-                break;
-              }
-              tc::fence_after_sync();
-              const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
-              const bool fresh = (j == j0 && kc == 0);
-              for (int kk = 0; kk < ksteps; ++kk) {
-                const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
-                const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
-                for (int nt = 0; nt < NT; ++nt) {
-                  const uint32_t r = nt ? n01 : n00;
-                  const uint32_t boff = 2 * kTileA + r * 128 + kk * 32;
-                  const uint64_t bh = tc::sdesc_k128(sa + boff);
-                  const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
-                  const uint32_t d = dbase + r;
-                  const uint32_t idesc = nt ? id1 : id0;
-                  tc::mma_f16(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
-                  tc::mma_f16(d, ah, bl, idesc, 1u);
-                  tc::mma_f16(d, al, bh, idesc, 1u);
-                }
-              }
-              tc::mma_commit(&empty[s]);
-              issued = true;
+          bool fresh = true;  // the block's first chunk overwrites the accumulator
+          // full slices, mesh point by mesh point, then the packed tail's chunks
+          const int nch = KCf * (j1 - j0) + (TU ? (j1 - j0 + 8 / TU - 1) / (8 / TU) : 0);
+          for (int q = 0; q < nch && !*abort_flag; ++q, ++cc) {
+            int ksteps;
+            if (q < KCf * (j1 - j0)) {
+              ksteps = min(4, (n - (q / (j1 - j0)) * 64 + 15) / 16);
+            } else {
+              const int jt = j0 + (q - KCf * (j1 - j0)) * (8 / TU);
+              ksteps = min(4, (min(8 / TU, j1 - jt) * 8 * TU + 15) / 16);
             }
+            const int s = cc & 1;
+            const uint32_t use = cc >> 1;
+            if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+              *abort_flag = 1;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(smem + s * stage_bytes);
+            for (int kk = 0; kk < ksteps; ++kk) {
+              const uint64_t ah = tc::sdesc_k128(sa + kk * 32);
+              const uint64_t al = tc::sdesc_k128(sa + kTileA + kk * 32);
+              for (int nt = 0; nt < NT; ++nt) {
+                const uint32_t r = nt ? n01 : n00;
+                const uint32_t boff = 2 * kTileA + r * 128 + kk * 32;
+                const uint64_t bh = tc::sdesc_k128(sa + boff);
+                const uint64_t bl = tc::sdesc_k128(sa + boff + tileB);
+                const uint32_t d = dbase + r;
+                const uint32_t idesc = nt ? id1 : id0;
+                tc::mma_f16(d, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
+                tc::mma_f16(d, ah, bl, idesc, 1u);
+                tc::mma_f16(d, al, bh, idesc, 1u);
+              }
+            }
+            fresh = false;
+            tc::mma_commit(&empty[s]);
+            issued = true;
           }
           tc::mma_commit(&accf[buf]);
         }
@@ -750,10 +831,15 @@ __global__ void __launch_bounds__(kThreadsH, 1)
 // (value 2) of *flag and the caller reports the input as out of range. With
 // g32 the same pass also writes the FP32 copy of g (pitch ld32, zero padded):
 // one read of g and one FP64-to-FP32 conversion per entry serve both, the
-// scaling then being an exact FP32 multiplication by 2^kScaleG.
+// scaling then being an exact FP32 multiplication by 2^kScaleG. With tw > 0
+// the first tw columns of the last 64-wide slice of row (j, a) are written a
+// second time at column j tw of row a of the packed tail (thi, tlo; pitch
+// tpitch halves, columns from M tw on zero).
 __global__ void split_f16_kernel(int n, long rows, int ld16, const double *__restrict__ G,
                                  uint32_t *__restrict__ hi, uint32_t *__restrict__ lo,
-                                 int *flag, float *__restrict__ g32, int ld32) {
+                                 int *flag, float *__restrict__ g32, int ld32,
+                                 uint32_t *__restrict__ thi, uint32_t *__restrict__ tlo,
+                                 int tpitch, int tw) {
   const int lane = threadIdx.x & 31;
   const long wpb = blockDim.x >> 5, nw = (long)gridDim.x * wpb;
   const float sc = (float)(1 << kScaleG);
@@ -774,6 +860,18 @@ __global__ void split_f16_kernel(int n, long rows, int ld16, const double *__res
       tc::f16_split2(y0, y1, h, l);
       hi[o + c / 2] = h;
       lo[o + c / 2] = l;
+      if (c0 == ld16 - 64 && 2 * lane < tw) {
+        const long to = ((row % n) * tpitch + (row / n) * tw) / 2 + lane;
+        thi[to] = h;
+        tlo[to] = l;
+      }
+    }
+    if (tw && row / n == rows / n - 1) {  // zero the tail row's padding past column M tw
+      const long mt = (rows / n) * tw;
+      for (long p = lane; p < (tpitch - mt) / 2; p += 32) {
+        thi[((row % n) * tpitch + mt) / 2 + p] = 0u;
+        tlo[((row % n) * tpitch + mt) / 2 + p] = 0u;
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0 && flag) atomicOr(flag, 2);
@@ -845,17 +943,30 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
       if (e == cudaSuccess) e = make_tmap_rows16(&d->hl[t], hl, n, M, ld16, d->g.nsz[t]);
       if (e != cudaSuccess) return e;
     }
+    d->TU = c1_tail_units(n);
+    if (d->TU) {
+      const int tp = c1_tail_pitch(n, M);
+      const uint16_t *th = hl + (size_t)M * n * ld16, *tl = th + (size_t)n * tp;
+      for (int t = 0; t < 2; ++t) {
+        // the whole pitch is mapped (at least one 64-wide box; the padding is zero)
+        cudaError_t e = make_tmap_tail16(&d->th16[t], th, n, tp, tp, d->g.nsz[t]);
+        if (e == cudaSuccess) e = make_tmap_tail16(&d->tl16[t], tl, n, tp, tp, d->g.nsz[t]);
+        if (e != cudaSuccess) return e;
+      }
+    }
   }
   return cudaSuccess;
 }
 
 cudaError_t launch_split_f16(int n, int M, const double *G, void *h16, cudaStream_t s,
                              int *flag, float *g32) {
-  const int ld16 = ld16_of(n);
+  const int ld16 = ld16_of(n), tp = c1_tail_pitch(n, M);
   uint32_t *hi = reinterpret_cast<uint32_t *>(h16);
   uint32_t *lo = hi + (size_t)M * n * ld16 / 2;
+  uint32_t *thi = lo + (size_t)M * n * ld16 / 2, *tlo = thi + (size_t)n * tp / 2;
   split_f16_kernel<<<1024, 256, 0, s>>>(n, (long)M * n, ld16, G, hi, lo, flag, g32,
-                                        (n + 31) / 32 * 32);
+                                        (n + 31) / 32 * 32, thi, tlo, tp,
+                                        8 * c1_tail_units(n));
   return cudaGetLastError();
 }
 

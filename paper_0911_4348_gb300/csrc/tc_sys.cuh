@@ -55,8 +55,10 @@ struct XSys {
 struct C1Sys {
   CUtensorMap th[2], tl[2];   // g_j split, per N tile
   CUtensorMap hh[2], hl[2];   // g_j FP16 split (scaled by 2^kScaleG), per N tile
+  CUtensorMap th16[2], tl16[2];  // FP16 path, packed tail (c1_tail_units > 0): per N tile
   const TcScale *scale;       // FP16 path: operand scales
   TcGeom g;
+  int TU;                     // FP16 path: 16-byte units per mesh point in the packed tail (0: off)
   int JB;                     // mesh points per FP32 accumulation block
   int S;                      // splits of the mesh-point range per row tile
   int RT;                     // 128-row tiles of the stacked (i, a) rows
@@ -90,8 +92,29 @@ cudaError_t c1sys_fill(C1Sys *d, int n, int M, int splits, const float *ws, cons
                        const void *h16 = nullptr, const TcScale *scale = nullptr);
 // Pitch (elements) of the FP16 split rows: n rounded up to 64 (128-byte rows).
 inline int ld16_of(int n) { return (n + 63) / 64 * 64; }
+// Packed tail of the FP16 first convolution. The last 64-wide column slice of
+// g_j holds r = n - ld16 + 64 values; when r <= 32 the slices of 8 / TU
+// consecutive mesh points (TU = ceil(r / 8) 16-byte units each) share one
+// 64-wide contraction chunk instead of taking one mostly-zero chunk each. The
+// split writes those columns a second time into tail arrays [n][pitch] (hi,
+// then lo), column j * 8 TU + t holding g_j(a, ld16 - 64 + t) (zero past n).
+inline int c1_tail_units(int n) {
+  const int r = n - (ld16_of(n) - 64);
+  const int u = (r + 7) / 8;
+  return u <= 4 ? u : 0;
+}
+inline int c1_tail_pitch(int n, int M) {
+  const int u = c1_tail_units(n);
+  return u ? (M * 8 * u + 63) / 64 * 64 : 0;
+}
+// Halves of the FP16 split of g: the hi and lo stacks [M][n][ld16], then the
+// packed tail's hi and lo arrays [n][c1_tail_pitch].
+inline size_t f16_split_halves(int n, int M) {
+  return 2 * (size_t)M * n * ld16_of(n) + 2 * (size_t)n * c1_tail_pitch(n, M);
+}
 // FP16 split of g (scaled by 2^kScaleG) into h16 = [hi stack][lo stack],
-// [M][n][ld16] halves each, padding zero. An entry the split cannot hold
+// [M][n][ld16] halves each, padding zero, followed by the packed tail's hi and
+// lo arrays when c1_tail_units(n) > 0. An entry the split cannot hold
 // (|g| >= 65504 / 2^kScaleG or not finite) raises bit 1 (value 2) of *flag
 // (the tensor-core error flag; may be NULL). With g32 (may be NULL) the same
 // pass writes the FP32 copy of g ([M][n][ld], ld = n rounded up to 32).

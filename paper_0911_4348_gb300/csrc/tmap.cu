@@ -3,9 +3,10 @@
 // or 16 columns (64-byte swizzle) x `rows` rows x 1 matrix, rows and columns
 // beyond n zero-filled (the map's column extent is n, so the padding is not
 // fetched). make_tmap_rows16 is the same over FP16 rows of ld16 halves
-// (a multiple of 64), box 64 halves (128 bytes) wide. The encoder comes from
-// the driver through the runtime's entry-point lookup, so no link against
-// libcuda is needed.
+// (a multiple of 64), box 64 halves (128 bytes) wide; make_tmap_tail16 is the
+// 2-D form over [n][pitch] FP16 rows (the first convolution's packed tail).
+// The encoder comes from the driver through the runtime's entry-point lookup,
+// so no link against libcuda is needed.
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -61,6 +62,23 @@ cudaError_t make_tmap_rows16(CUtensorMap *map, const void *base, int n, int M, i
   const cuuint32_t box[3] = {64, (cuuint32_t)rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_tmap_tail16(CUtensorMap *map, const void *base, int n, int cols, int pitch,
+                             int rows) {
+  std::call_once(g_encode_once, load_encoder);
+  if (!g_encode) return cudaErrorNotSupported;
+  if (rows < 1 || rows > 256 || (pitch % 64) != 0 || cols < 1 || cols > pitch)
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
