@@ -245,7 +245,13 @@ def test_conv1_measured_split_choice_is_a_candidate():
 
 
 @pytest.mark.parametrize("n,u,p,beta,seed", [(8, 2, 3, 10.0, 0), (37, 2, 3, 25.0, 1),
-                                             (130, 1, 3, 100.0, 2), (257, 1, 2, 100.0, 3)])
+                                             (130, 1, 3, 100.0, 2), (257, 1, 2, 100.0, 3),
+                                             # packed last column slice: 8 / TU mesh points
+                                             # per chunk, TU = 2, 3, 4 and 4 with no full
+                                             # slice, accumulation blocks of 26, 9, 10 and 13
+                                             # mesh points (partial last groups)
+                                             (74, 4, 16, 40.0, 4), (84, 2, 16, 40.0, 5),
+                                             (93, 2, 16, 40.0, 6), (31, 4, 16, 40.0, 7)])
 def test_conv1_f16_random(ctx, n, u, p, beta, seed):
     # FP16-split operands scaled into FP16's range carry 22 significant bits,
     # like the TF32 split (and half the accumulation steps): the same bound
