@@ -26,6 +26,8 @@ representation in nonequilibrium Green's function calculations" (arXiv
   in ``conv1``, ``conv2``, ``energy``, ``solve_2b``.
 * Sec. 2.3 and 3.2 observables: ``density`` (one-electron density from
   g(0^-)) and ``nuclear_repulsion`` (the internuclear term of Eq. h3pv).
+* Sec. 4 (T-matrix named beside GW): ``pair_conv``, ``ladder_t``,
+  ``sigma_tmatrix`` and ``solve_2b(self_energy="tmatrix")``.
 * Sec. 4 (GW named as a further approximation the FE-DVR form simplifies):
   ``bose_lag_table``, ``conv_bose``, ``screened_w``, ``sigma_gw`` and
   ``solve_2b(..., self_energy="gw")`` (the screened interaction of the
@@ -939,6 +941,80 @@ def sigma_gw(G: np.ndarray, V: np.ndarray, sigma: float, mesh: dict, blag: dict,
     return sw
 
 
+def pair_conv(G: np.ndarray, t: np.ndarray, mesh: dict, blag: dict) -> np.ndarray:
+    """(K * t)(tau_i) for the particle-particle propagator K(tau) = g(tau) (x) g(tau)
+    acting on the row pair of a pair-space function t[j, a, k, b, l] (rows
+    (a, k), columns (b, l)):
+
+        (K * t)_i[a, k, b, l] = sum_j w_j sum_{a' k'} K(tau_i - tau_j)_{(a k),(a' k')} t_j[a', k', b, l],
+        K(x)_{(a k),(a' k')} = g_{a a'}(x) g_{k k'}(x).
+
+    K is periodic (the product of two anti-periodic functions), so the lag is
+    wrapped as for the bubble (``bose_lag_table``) and K at the lag is the
+    linear interpolation of K between the bracketing mesh points."""
+    M = G.shape[0]
+    w = mesh["w"]
+    # (g_r (x) g_r) t_j for every mesh point r and j: Z[r, j] = g_r X g_r^T per column (b, l)
+    Z = np.einsum("rac,rkd,jcdbl->rjakbl", G, G, t, optimize=True)
+    jj = np.arange(M)[None, :]
+    kk, tt = blag["k"], blag["t"]
+    lower = (w[None, :] * (1.0 - tt))[:, :, None, None, None, None] * Z[kk, jj]
+    upper = (w[None, :] * tt)[:, :, None, None, None, None] * Z[kk + 1, jj]
+    return (lower + upper).sum(axis=1)
+
+
+def ladder_t(G: np.ndarray, V: np.ndarray, sigma: float, mesh: dict, blag: dict, t0=None,
+             mixing: float = 0.3, tol: float = 1e-12, max_iter: int = 500) -> dict:
+    """Correlated particle-particle T-matrix of the two-index interaction.
+
+    Reading (the paper names the T-matrix approximation without equations;
+    this follows the Matsubara Feynman rules in this code's g > 0 convention,
+    G(tau) = g(tau) and G(-tau) = -gb(tau) on [-beta, 0]): a pair of particles
+    at the nodes (a, k) scatters through V_ak without changing nodes, so the
+    ladder lives on node pairs with the pair propagator K = g (x) g, and with
+    V^ the diagonal pair-space matrix of the V_ak the correlated part of the
+    T-matrix, T^c = -V^ K V^ - V^ (K * T^c), is -t with
+
+        t = V^ K V^ - V^ (K * t),      t_j[a, k, b, l] = V_ak g_ab g_kl V_bl - V_ak (K * t)_j[a, k, b, l].
+
+    No spin factor enters (no closed loop). Solved like the screened
+    interaction: damped fixed-point iteration from t0 (default the lowest
+    order V^ K V^) until max|t_new - t| < tol. Pair-space arrays are
+    [M][n][n][n][n]; small n only."""
+    M = G.shape[0]
+    S = np.einsum("ak,jab,jkl,bl->jakbl", V, G, G, V)
+    t = S.copy() if t0 is None else np.array(t0, dtype=np.float64)
+    r = np.inf
+    it = 0
+    for it in range(1, max_iter + 1):
+        C = pair_conv(G, t, mesh, blag)
+        new = S - V[None, :, :, None, None] * C
+        r = float(np.max(np.abs(new - t)))
+        t = (1.0 - mixing) * t + mixing * new
+        if r < tol:
+            break
+    return dict(t=t, iters=it, res=r, S=S)
+
+
+def sigma_tmatrix(G: np.ndarray, V: np.ndarray, sigma: float, mesh: dict, blag: dict, t0=None,
+                  mixing: float = 0.3, tol: float = 1e-12, max_iter: int = 500) -> dict:
+    """T-matrix correlation self-energy: the ladder closed with a hole line, the
+    direct term with the spin factor and the exchange term without,
+
+        Sigma^T_ab(tau_j) = sum_kl [sigma t_j[a, k, b, l] - t_j[a, k, l, b]] gb_j[l, k],
+
+    gb_j = g(-beta - tau_j) (``ladder_t``). At lowest order (t = V^ K V^) this
+    is Eq. sigma2ndb term by term: the direct term sigma g_ab (V Q V)_ab and the
+    exchange sum_kl V_ak V_bl g_al gb_lk g_kb."""
+    lt = ladder_t(G, V, sigma, mesh, blag, t0, mixing, tol, max_iter)
+    t = lt["t"]
+    M = G.shape[0]
+    gb = G[::-1]
+    lt["Sigma"] = (sigma * np.einsum("jakbl,jlk->jab", t, gb)
+                   - np.einsum("jaklb,jlk->jab", t, gb))
+    return lt
+
+
 def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
              sigma_init=None, quad: str = "trap", self_energy: str = "2b",
              gw_mixing: float = 0.3, gw_tol: float = 1e-12, gw_max_iter: int = 500) -> dict:
@@ -953,10 +1029,12 @@ def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
     self_energy="gw": Sigma^corr = ``sigma_gw`` instead of second Born; the
     inner iteration for w starts from the previous outer iteration's w (V Q V
     at the first) and ``gw_inner`` lists its iterations per outer step.
+    self_energy="tmatrix": Sigma^corr = ``sigma_tmatrix``, its ladder iteration
+    warm-started the same way (``gw_*`` name the inner iteration's controls).
     """
     mesh = power_mesh(beta, u, p)
     lag = lag_table(mesh["tau"], beta)
-    blag = bose_lag_table(mesh["tau"], beta) if self_energy == "gw" else None
+    blag = bose_lag_table(mesh["tau"], beta) if self_energy in ("gw", "tmatrix") else None
     G0 = g0_mesh(hf["eps"], hf["C"], hf["mu"], mesh["tau"], beta)
     G = G0.copy()
     hist = []
@@ -969,6 +1047,10 @@ def solve_2b(h, V, sigma, hf, beta, u, p, mixing=0.5, tol=1e-8, max_iter=200,
         if A is None and self_energy == "gw":
             sg = sigma_gw(G, V, sigma, mesh, blag, w_state, gw_mixing, gw_tol, gw_max_iter)
             A, w_state = sg["Sigma"], sg["w"]
+            gw_inner.append(sg["iters"])
+        elif A is None and self_energy == "tmatrix":
+            sg = sigma_tmatrix(G, V, sigma, mesh, blag, w_state, gw_mixing, gw_tol, gw_max_iter)
+            A, w_state = sg["Sigma"], sg["t"]
             gw_inner.append(sg["iters"])
         step = dyson_iteration(h, V, sigma, hf, mesh, lag, beta, G0, G, mixing, A=A, quad=quad)
         hist.append((it, step["res"], step["E0"], step["N"]))
