@@ -798,8 +798,9 @@ def main():
                     help="time steps of one propagation of the kbe workload")
     ap.add_argument("--kbe-precision", choices=("fp64", "tf32"), default="fp64",
                     help="kbe workload: collision integrals in FP64 or as split-TF32 products")
-    ap.add_argument("--self-energy", choices=("2b", "gw"), default="2b",
-                    help="correlation self-energy of the Matsubara iteration (gw: FP64 path)")
+    ap.add_argument("--self-energy", choices=("2b", "gw", "tmatrix"), default="2b",
+                    help="correlation self-energy of the Matsubara iteration (gw, tmatrix: "
+                         "FP64 path; tmatrix: n_b <= 32, e.g. --workload he_small)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -831,11 +832,14 @@ def main():
     ctx.set_potential(sys_.Z, sys_.R, sys_.soft_en, sys_.soft_ee, sys_.n_elec)
     E_hf, _ = ctx.solve_hf(sys_.beta, tol=1e-12)
     ctx.use_graphs(not args.no_graphs)
-    gw = args.self_energy == "gw"
+    gw = args.self_energy in ("gw", "tmatrix")  # an inner iteration per outer step
     if gw:
         if prec != 0:
-            raise SystemExit("--self-energy gw runs on the FP64 path: add --precision fp64")
-        ctx.set_self_energy("gw")
+            raise SystemExit(f"--self-energy {args.self_energy} runs on the FP64 path: "
+                             "add --precision fp64")
+        if args.self_energy == "tmatrix" and sys_.n_b > 32:
+            raise SystemExit("--self-energy tmatrix needs n_b <= 32 (e.g. --workload he_small)")
+        ctx.set_self_energy(args.self_energy)
         args.no_fp64_compare = True   # the FP64 path is the one timed
         args.no_cpu_baseline = True   # the oracle sample below is second Born's
     ctx.prepare_2b(sys_.beta, sys_.u, sys_.p, prec)
@@ -896,7 +900,7 @@ def main():
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     dom = max(("sigma2", "conv1", "conv2"), key=lambda k: avg.get(k, 0.0))
     if gw:
-        dom = "sigma2"  # the screened interaction's periodic convolutions
+        dom = "sigma2"  # the inner iteration's periodic convolutions
     peaks = load_peaks()
     if prec == 0:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -922,8 +926,12 @@ def main():
             peak = base / 2.0
             bound, punit, psrc = "tensor", "TFLOP/s", f"measured bf16 {kind} x 1/2 (tf32 ratio)"
     dom_flops = algorithmic(dom, n, M)
-    if gw:  # one periodic convolution (2 M^2 n^3) per inner iteration
+    if args.self_energy == "gw":  # one periodic convolution (2 M^2 n^3) per inner iteration
         dom_flops = float(np.mean(inner)) * algorithmic("conv1", n, M)
+    elif args.self_energy == "tmatrix":
+        # per inner iteration the ladder's convolution applies, for every (i, j)
+        # and column pair, the two interpolation points' g_r X g_r^T: 8 M^2 n^5
+        dom_flops = float(np.mean(inner)) * 8.0 * M * M * float(n) ** 5
     achieved = dom_flops / (avg[dom] / 1000.0) / 1e12
     # keys of profiles/ncu_traffic.json: the kernel of the stage in this precision
     kernel_name = {("conv1", "f16"): "conv1_f16_kernel", ("conv1", "tf32"): "conv1_tc_kernel",
@@ -935,8 +943,10 @@ def main():
             "algorithmic_flops_per_launch": dom_flops, "peak_source": psrc,
             "stage_ms": avg}
     if gw:
-        roof["kernel"] = "GW screened interaction (conv1_fp64_kernel, periodic table)"
-        roof["gw_inner_iterations_mean"] = float(np.mean(inner))
+        roof["kernel"] = ("GW screened interaction (conv1_fp64_kernel, periodic table)"
+                          if args.self_energy == "gw" else
+                          "T-matrix ladder (tm_ladder_kernel, periodic table)")
+        roof["inner_iterations_mean"] = float(np.mean(inner))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
@@ -958,7 +968,7 @@ def main():
         # run's own converged value
         ctx2 = _context(stream, sys_)
         if gw:
-            ctx2.set_self_energy("gw")
+            ctx2.set_self_energy(args.self_energy)
         run = _timed_solve(ctx2, sys_, prec, sys_.tol, 200)
         ref = E_ref if E_ref is not None else run["E"][-1]
         k = _first_within(run["E"], ref)

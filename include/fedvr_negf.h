@@ -282,12 +282,24 @@ int fedvr_set_quadrature(fedvr_ctx *ctx, int order);
  * FEDVR_ERR_ARG at prepare) and eagerly (one host readback per inner
  * iteration, no graph replay). An inner iteration that has not converged in
  * w_max_iter steps ends the step with FEDVR_ERR_NOCONV. Drops a prepared run.
- * Errors: FEDVR_ERR_ARG for another kind or for w_mixing outside (0, 1],
- * w_tol <= 0 or w_max_iter < 1 (kind 1). */
+ * kind 2 = T-matrix, the other approximation Sec. 4 names: the
+ * particle-particle ladder of the two-index interaction. A pair of particles
+ * at the nodes (a, k) scatters through V_ak without changing nodes, so with
+ * the pair propagator K(tau) = g(tau) (x) g(tau) and V^ the diagonal pair-space
+ * matrix of the V_ak the correlated ladder solves
+ *   t = V^ K V^ - V^ (K * t)      (K * t periodic, as Q * w above),
+ * and Sigma^T_ab(tau_j) = sum_kl [sigma t_j(ak; bl) - t_j(ak; lb)] g_{M-1-j}(l, k)
+ * (its lowest order is Eq. sigma2ndb, direct and exchange terms). Pair space
+ * holds n_b^2 x n_b^2 values per mesh point, so kind 2 needs n_b <= 32
+ * (FEDVR_ERR_ARG at prepare otherwise) and three such stacks of device
+ * memory; the inner iteration, its parameters, warm start and errors are as
+ * for GW. Errors: FEDVR_ERR_ARG for a kind outside 0..2 or for w_mixing
+ * outside (0, 1], w_tol <= 0 or w_max_iter < 1 (kinds 1 and 2). */
 int fedvr_set_self_energy(fedvr_ctx *ctx, int kind, double w_mixing, double w_tol,
                           int w_max_iter);
 
-/* Inner iterations of the last GW screened-interaction solve of the context. */
+/* Inner iterations of the last GW screened-interaction or T-matrix ladder
+ * solve of the context. */
 int fedvr_gw_last_inner(const fedvr_ctx *ctx, int *iters);
 
 /* Stage-level GW on caller device buffers (the context's stream): Sigma^GW
@@ -301,6 +313,20 @@ int fedvr_gw_last_inner(const fedvr_ctx *ctx, int *iters);
 int fedvr_sigma_gw(fedvr_ctx *ctx, int n, double beta, int u, int p, double spin, const double *V,
                    const double *G, double *Sigma, double *w_io, int w_valid, double w_mixing,
                    double w_tol, int w_max_iter, int *iters);
+
+/* Stage-level T-matrix self-energy on caller device buffers (the context's
+ * stream): Sigma^T [M][n][n] of G [M][n][n] on the power mesh (beta, u, p),
+ * V [n][n], spin factor spin, 1 <= n <= 32 (see fedvr_set_self_energy, kind
+ * 2). t_io (device, M n^4 doubles, or NULL) is the ladder in the layout
+ * t[j][b][l][a][k] = t_j(ak; bl): with t_valid != 0 the iteration starts from
+ * it (else from V^ K V^); the converged ladder is written back when given.
+ * iters (host, may be NULL): inner iterations. Synchronises the stream.
+ * Errors: FEDVR_ERR_ARG for invalid sizes, mesh or iteration parameters;
+ * FEDVR_ERR_NOCONV if the ladder does not converge in t_max_iter steps;
+ * FEDVR_ERR_NAN if it diverges. */
+int fedvr_sigma_tmatrix(fedvr_ctx *ctx, int n, double beta, int u, int p, double spin,
+                        const double *V, const double *G, double *Sigma, double *t_io,
+                        int t_valid, double t_mixing, double t_tol, int t_max_iter, int *iters);
 
 /* Start the next solve_2b from this Sigma^corr (warm start). Sigma0 is
  * [M][n_b][n_b] on host or device; M must match the next solve's mesh; copied

@@ -220,9 +220,9 @@ class Context:
         self._check(self._lib.fedvr_set_mu(self._h, float(mu)))
 
     def set_self_energy(self, kind, w_mixing=0.3, w_tol=1e-12, w_max_iter=500):
-        """Correlation self-energy of the next prepare/solve: "2b" (second Born)
-        or "gw" (``fedvr_set_self_energy``)."""
-        k = {"2b": 0, "gw": 1}.get(kind, kind)
+        """Correlation self-energy of the next prepare/solve: "2b" (second Born),
+        "gw" or "tmatrix" (``fedvr_set_self_energy``)."""
+        k = {"2b": 0, "gw": 1, "tmatrix": 2}.get(kind, kind)
         self._check(self._lib.fedvr_set_self_energy(self._h, int(k), float(w_mixing),
                                                     float(w_tol), int(w_max_iter)))
 
@@ -242,6 +242,21 @@ class Context:
             self._h, n, float(beta), int(u), int(p), float(spin), _dev(V, (n, n)),
             _dev(G, (M, n, n)), _dev(Sigma, (M, n, n)), _dev(w, (M, n, n)) if w is not None else None,
             1 if w_valid else 0, float(w_mixing), float(w_tol), int(w_max_iter), C.byref(it)))
+        return it.value
+
+    def sigma_tmatrix(self, beta, u, p, V, G, Sigma, spin=2.0, t=None, t_valid=False,
+                      t_mixing=0.3, t_tol=1e-12, t_max_iter=500):
+        """Stage-level T-matrix self-energy of the CUDA stack G into Sigma
+        (``fedvr_sigma_tmatrix``); t (optional) is the ladder [M][n][n][n][n] in
+        the library's layout t[j][b][l][a][k]; returns the inner iterations."""
+        M, n = G.shape[0], G.shape[1]
+        assert M == 2 * u * p + 1
+        it = C.c_int()
+        self._check(self._lib.fedvr_sigma_tmatrix(
+            self._h, n, float(beta), int(u), int(p), float(spin), _dev(V, (n, n)),
+            _dev(G, (M, n, n)), _dev(Sigma, (M, n, n)),
+            _dev(t, (M, n, n, n, n)) if t is not None else None, 1 if t_valid else 0,
+            float(t_mixing), float(t_tol), int(t_max_iter), C.byref(it)))
         return it.value
 
     def set_quadrature(self, order):

@@ -78,6 +78,9 @@ SIGNATURES = {
     "fedvr_gw_last_inner": (C.c_int, [_vp, _ip]),
     "fedvr_sigma_gw": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double, _vp, _vp,
                                  _vp, _vp, C.c_int, C.c_double, C.c_double, C.c_int, _ip]),
+    "fedvr_sigma_tmatrix": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double,
+                                      _vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_double,
+                                      C.c_int, _ip]),
 }
 
 _lib = None

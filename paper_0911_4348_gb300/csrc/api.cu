@@ -172,6 +172,49 @@ int gw_solve(fedvr_ctx *ctx, int n, int M, const double *V, const double *G, dou
   return FEDVR_OK;
 }
 
+// T-matrix ladder of g and Sigma^T: the damped fixed-point iteration
+// t <- (1 - a) t + a (V^ K V^ - V^ (K * t)) from t (the source V^ K V^ when
+// !t_valid) until max|t_new - t| < tol, with K * t the periodic convolution of
+// the pair propagator (bosonic table coef). One host readback of the residual
+// per inner iteration.
+int tm_solve(fedvr_ctx *ctx, int n, int M, const double *V, const double *G, double *Sigma,
+             const ConvCoef *coef, double *t, bool t_valid, double *src, double *Y,
+             unsigned long long *res_d, double mixing, double tol, int max_iter, int *iters) {
+  cudaStream_t s = ctx->stream;
+  const size_t pstack = (size_t)M * n * n * n * n;
+  FEDVR_CK(ctx, tm_source(n, M, V, G, src, s));
+  if (!t_valid) FEDVR_CK(ctx, launch_copy(pstack, src, t, s));
+  double r = 0.0;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    FEDVR_CK(ctx, tm_ladder(n, M, coef, G, t, Y, s));
+    FEDVR_CK(ctx, cudaMemsetAsync(res_d, 0, sizeof(unsigned long long), s));
+    FEDVR_CK(ctx, tm_update(n, M, V, src, Y, t, mixing, res_d, s));
+    unsigned long long bits = 0;
+    FEDVR_CK(ctx, cudaMemcpyAsync(&bits, res_d, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    if (int rr = sync(ctx)) return rr;
+    memcpy(&r, &bits, sizeof(r));
+    if (!is_fin(r)) return fail(ctx, FEDVR_ERR_NAN, "T-matrix ladder is not finite");
+    if (r < tol) break;
+  }
+  if (it > max_iter)
+    return fail(ctx, FEDVR_ERR_NOCONV, "T-matrix ladder not converged in %d iterations (residual %.3e)",
+                max_iter, r);
+  FEDVR_CK(ctx, tm_sigma(n, M, ctx->spin, G, t, Sigma, s));
+  *iters = it;
+  return FEDVR_OK;
+}
+
+int tm_workspace(fedvr_ctx *ctx, int n, int M) {
+  const size_t pstack = (size_t)M * n * n * n * n;
+  ENSURE(ctx, m_t, dsz(pstack));
+  ENSURE(ctx, m_src, dsz(pstack));
+  ENSURE(ctx, m_y, dsz(pstack));
+  ENSURE(ctx, g_coef, (size_t)M * M * sizeof(ConvCoef));
+  ENSURE(ctx, g_res, 16);
+  return FEDVR_OK;
+}
+
 int gw_workspace(fedvr_ctx *ctx, int n, int M) {
   const size_t stack = (size_t)M * n * n;
   ENSURE(ctx, g_w, dsz(stack));
@@ -501,6 +544,16 @@ int phase_sigma_pre(fedvr_ctx *ctx, bool warm, cudaStream_t s, int *launches, in
     ctx->gw_w_valid = true;
     ctx->gw_last_inner = it;
     *launches += 3 + 6 * it;
+  } else if (ctx->self_energy == 2) {
+    int it = 0;
+    if (int r = tm_solve(ctx, n, M, V, G, S, P<ConvCoef>(ctx->g_coef), P<double>(ctx->m_t),
+                         ctx->gw_w_valid, P<double>(ctx->m_src), P<double>(ctx->m_y),
+                         P<unsigned long long>(ctx->g_res), ctx->gw_mixing, ctx->gw_tol,
+                         ctx->gw_max_iter, &it))
+      return r;
+    ctx->gw_w_valid = true;
+    ctx->gw_last_inner = it;
+    *launches += 2 + 2 * it;
   } else {
     FEDVR_CK(ctx, sigma2_fp64(n, M, ctx->spin, V, G, S, P<double>(ctx->w_t1), P<double>(ctx->w_t2),
                               P<double>(ctx->w_t3), s));
@@ -736,7 +789,7 @@ void fedvr_destroy(fedvr_ctx *ctx) {
                     &ctx->k_S, &ctx->k_T1, &ctx->k_R, &ctx->k_aux, &ctx->k_out,
                     &ctx->k_part, &ctx->k_sh, &ctx->k_aop, &ctx->k_o, &ctx->k_flag, &ctx->k_x,
                     &ctx->g_w, &ctx->g_vqv, &ctx->g_c, &ctx->g_new, &ctx->g_coef, &ctx->g_res,
-                    &ctx->w_c1f};
+                    &ctx->m_t, &ctx->m_src, &ctx->m_y, &ctx->w_c1f};
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (DevBuf *b : bufs) release(*b);
@@ -1013,8 +1066,10 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   if (int r = check_quad(ctx, precision, M)) return r;
   if (ctx->sigma_init_M && ctx->sigma_init_M != M)
     return fail(ctx, FEDVR_ERR_ARG, "initial Sigma has M = %d, mesh has %d", ctx->sigma_init_M, M);
-  if (ctx->self_energy == 1 && (precision != FEDVR_FP64 || ctx->quad_order != 2))
-    return fail(ctx, FEDVR_ERR_ARG, "GW runs on the FP64 path with the trapezoid rule");
+  if (ctx->self_energy != 0 && (precision != FEDVR_FP64 || ctx->quad_order != 2))
+    return fail(ctx, FEDVR_ERR_ARG, "GW and the T-matrix run on the FP64 path with the trapezoid rule");
+  if (ctx->self_energy == 2 && ctx->n > 32)
+    return fail(ctx, FEDVR_ERR_ARG, "the T-matrix ladder needs n_b <= 32 (pair space n_b^2)");
   ctx->prepared = false;
   drop_graph(ctx);
   const size_t nn = (size_t)n * n, stack = (size_t)M * nn;
@@ -1050,11 +1105,14 @@ int fedvr_2b_prepare(fedvr_ctx *ctx, double beta, int u, int p, int precision) {
   if (ctx->quad_order == 4) {
     if (int r = build_quad4(ctx, M, beta)) return r;
   }
-  if (ctx->self_energy == 1) {
-    if (int r = gw_workspace(ctx, n, M)) return r;
+  if (ctx->self_energy != 0) {
+    if (int r = ctx->self_energy == 1 ? gw_workspace(ctx, n, M) : tm_workspace(ctx, n, M))
+      return r;
     FEDVR_CK(ctx, launch_conv_coef_bose(M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
                                         P<ConvCoef>(ctx->g_coef), s));
-    ctx->gw_w_valid = false;  // the first outer step starts the inner iteration from V Q V
+    // the first outer step starts the inner iteration from its lowest order
+    // (V Q V, or the ladder's V^ K V^)
+    ctx->gw_w_valid = false;
   }
   double *tau = P<double>(ctx->w_tau), *w = P<double>(ctx->w_w);
   const double *eps = P<double>(ctx->b_eps), *C = P<double>(ctx->b_C);
@@ -1183,12 +1241,13 @@ int fedvr_set_mu(fedvr_ctx *ctx, double mu) {
 int fedvr_set_self_energy(fedvr_ctx *ctx, int kind, double w_mixing, double w_tol,
                           int w_max_iter) {
   CHECK_CTX(ctx);
-  if (kind != 0 && kind != 1) return fail(ctx, FEDVR_ERR_ARG, "self-energy kind must be 0 or 1");
-  if (kind == 1 && (!(w_mixing > 0.0 && w_mixing <= 1.0) || !(w_tol > 0.0) || !is_fin(w_tol) ||
+  if (kind < 0 || kind > 2) return fail(ctx, FEDVR_ERR_ARG, "self-energy kind must be 0, 1 or 2");
+  if (kind != 0 && (!(w_mixing > 0.0 && w_mixing <= 1.0) || !(w_tol > 0.0) || !is_fin(w_tol) ||
                     w_max_iter < 1))
-    return fail(ctx, FEDVR_ERR_ARG, "GW needs 0 < w_mixing <= 1, w_tol > 0, w_max_iter >= 1");
+    return fail(ctx, FEDVR_ERR_ARG,
+                "GW and the T-matrix need 0 < w_mixing <= 1, w_tol > 0, w_max_iter >= 1");
   ctx->self_energy = kind;
-  if (kind == 1) {
+  if (kind != 0) {
     ctx->gw_mixing = w_mixing;
     ctx->gw_tol = w_tol;
     ctx->gw_max_iter = w_max_iter;
@@ -1236,6 +1295,41 @@ int fedvr_sigma_gw(fedvr_ctx *ctx, int n, double beta, int u, int p, double spin
   ctx->spin = spin0;
   if (r) return r;
   if (w_io) FEDVR_CK(ctx, cudaMemcpyAsync(w_io, w, dsz(stack), cudaMemcpyDeviceToDevice, s));
+  if (iters) *iters = it;
+  return sync(ctx);
+}
+
+int fedvr_sigma_tmatrix(fedvr_ctx *ctx, int n, double beta, int u, int p, double spin,
+                        const double *V, const double *G, double *Sigma, double *t_io,
+                        int t_valid, double t_mixing, double t_tol, int t_max_iter, int *iters) {
+  CHECK_CTX(ctx);
+  if (int r = check_mesh_args(ctx, beta, u, p)) return r;
+  if (n < 1 || n > 32 || !V || !G || !Sigma || !is_fin(spin) || spin < 0.0)
+    return fail(ctx, FEDVR_ERR_ARG, "need 1 <= n <= 32, spin >= 0 and device buffers");
+  if (!(t_mixing > 0.0 && t_mixing <= 1.0) || !(t_tol > 0.0) || t_max_iter < 1 ||
+      (t_valid && !t_io))
+    return fail(ctx, FEDVR_ERR_ARG,
+                "the T-matrix needs 0 < t_mixing <= 1, t_tol > 0, t_max_iter >= 1");
+  ctx->prepared = false;  // the workspace below is shared with a prepared run
+  drop_graph(ctx);
+  if (int r = build_mesh(ctx, beta, u, p, false)) return r;
+  const int M = 2 * u * p + 1;
+  const size_t pstack = (size_t)M * n * n * n * n;
+  if (int r = tm_workspace(ctx, n, M)) return r;
+  cudaStream_t s = ctx->stream;
+  FEDVR_CK(ctx, launch_conv_coef_bose(M, beta, P<double>(ctx->w_tau), P<double>(ctx->w_w),
+                                      P<ConvCoef>(ctx->g_coef), s));
+  double *t = P<double>(ctx->m_t);
+  if (t_valid) FEDVR_CK(ctx, cudaMemcpyAsync(t, t_io, dsz(pstack), cudaMemcpyDeviceToDevice, s));
+  const double spin0 = ctx->spin;
+  ctx->spin = spin;
+  int it = 0;
+  int r = tm_solve(ctx, n, M, V, G, Sigma, P<ConvCoef>(ctx->g_coef), t, t_valid != 0,
+                   P<double>(ctx->m_src), P<double>(ctx->m_y), P<unsigned long long>(ctx->g_res),
+                   t_mixing, t_tol, t_max_iter, &it);
+  ctx->spin = spin0;
+  if (r) return r;
+  if (t_io) FEDVR_CK(ctx, cudaMemcpyAsync(t_io, t, dsz(pstack), cudaMemcpyDeviceToDevice, s));
   if (iters) *iters = it;
   return sync(ctx);
 }

@@ -69,8 +69,9 @@ struct fedvr_ctx {
   // quadrature of the Dyson integrals: 2 = split trapezoid with linear lag
   // interpolation (default), 4 = the fourth-order variant (FP64 path)
   int quad_order = 2;
-  // correlation self-energy: 0 second Born, 1 GW (FP64 path); the screened
-  // interaction's damped inner iteration and its state across outer steps
+  // correlation self-energy: 0 second Born, 1 GW, 2 T-matrix (FP64 path); the
+  // damped inner iteration (screened interaction or ladder) and its state
+  // across outer steps
   int self_energy = 0;
   double gw_mixing = 0.3, gw_tol = 1e-12;
   int gw_max_iter = 500, gw_last_inner = 0;
@@ -99,6 +100,8 @@ struct fedvr_ctx {
   fedvr::DevBuf k_L, k_G, k_S, k_T1, k_R, k_aux, k_out, k_part, k_sh, k_aop, k_o, k_flag, k_x;
   // GW: screened interaction w, V Q V, convolution and update scratch, periodic table, flag
   fedvr::DevBuf g_w, g_vqv, g_c, g_new, g_coef, g_res;
+  // T-matrix: the ladder t, its source V^ K V^ and the convolution (pair-space stacks)
+  fedvr::DevBuf m_t, m_src, m_y;
   // partial stacks of the FP64 first convolution's mesh-range splits (small launches)
   fedvr::DevBuf w_c1f;
 };
@@ -191,6 +194,18 @@ cudaError_t gw_bubble(int n, int M, const double *V, const double *G, double *Q,
                       double *VQV, cudaStream_t s);
 cudaError_t launch_gw_sigma(long count, double spin, const double *G, const double *w,
                             double *Sigma, cudaStream_t s);
+// tmatrix.cu: the particle-particle ladder on pair-space stacks t[j][b][l][a][k]
+// (n <= 32): source V_ak g_ab g_kl V_bl, the periodic convolution of the pair
+// propagator g (x) g with t (bosonic table coef), the damped update
+// t <- (1 - m) t + m (S - V^ Y) with *res = max|t_new - t| (double bits), and
+// Sigma^T = sum_kl [spin t(ak; bl) - t(ak; lb)] g_{M-1-j}(l, k).
+cudaError_t tm_source(int n, int M, const double *V, const double *G, double *S, cudaStream_t s);
+cudaError_t tm_ladder(int n, int M, const ConvCoef *coef, const double *G, const double *T,
+                      double *Y, cudaStream_t s);
+cudaError_t tm_update(int n, int M, const double *V, const double *S, const double *Y, double *T,
+                      double mixing, unsigned long long *res, cudaStream_t s);
+cudaError_t tm_sigma(int n, int M, double spin, const double *G, const double *T, double *Sigma,
+                     cudaStream_t s);
 // basis.cu: periodic convolution coefficients (every (i, j), no diagonal case)
 cudaError_t launch_conv_coef_bose(int M, double beta, const double *tau, const double *w,
                                   ConvCoef *coef, cudaStream_t s);

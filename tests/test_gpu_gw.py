@@ -58,7 +58,8 @@ def test_gw_argument_errors():
     _need_gpu()
     from paper_0911_4348_gb300 import FedvrError
     s, h, V, hf, ctx = _he_small()
-    for bad in ((2, 0.3, 1e-12, 10), (1, 0.0, 1e-12, 10), (1, 1.5, 1e-12, 10), (1, 0.3, 0.0, 10),
+    # (kind 2 is the T-matrix; 3 is no kind)
+    for bad in ((3, 0.3, 1e-12, 10), (1, 0.0, 1e-12, 10), (1, 1.5, 1e-12, 10), (1, 0.3, 0.0, 10),
                 (1, 0.3, 1e-12, 0)):
         with pytest.raises(FedvrError) as e:
             ctx.set_self_energy(*bad)
